@@ -1,0 +1,225 @@
+/*
+ * kkt.h -- C ABI of the GB300 KKT refactorization library.
+ *
+ * The library solves the sequence of sparse symmetric indefinite systems
+ * K_k x_k = b_k, k = 1..M, that an interior-point ACOPF solver produces
+ * (Eq. 11; Alg. 1). All K_k share one sparsity pattern (Sec. II), so the
+ * work splits into the three stages of a sparse direct solver (Sec. II):
+ *
+ *   kkt_analyze   once per pattern, on the host: equilibration plan,
+ *                 fill-reducing ordering, frozen pivot sequence, symbolic
+ *                 factorization, supernodal assembly tree and its level
+ *                 schedule; uploaded to the GPU once (Alg. 1 setup).
+ *   kkt_refactor  per K_k, on the GPU: equilibrate, scatter the new values
+ *                 into the frozen factor pattern (Alg. 1 "update
+ *                 factorization object using new values") and refactor
+ *                 without pivoting (Alg. 1 "refactor").
+ *   kkt_solve     triangular solves with the current factors (Alg. 1
+ *                 "perform triangular solve").
+ *   kkt_refine    solve followed by iterative refinement to a backward-error
+ *                 tolerance (Alg. 1 "always followed by iterative
+ *                 refinement"; Sec. V asks for a better refinement: FGMRES).
+ *
+ * Conventions
+ *   - Matrices are full symmetric CSR (both triangles), 0-based int32 row
+ *     pointers and column indices, columns sorted and unique within a row,
+ *     every diagonal entry stored. Values are FP64.
+ *   - Pointers named h_* are host memory, d_* are device memory of the
+ *     current CUDA device. The caller owns every array it passes; device
+ *     arrays must stay valid until the work on `stream` has completed.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls taking a stream are asynchronous and stream-ordered
+ *     unless stated otherwise; none allocates device memory (all memory is
+ *     allocated by kkt_analyze).
+ *   - A kkt_ctx is not thread-safe: use one context per session / thread.
+ *   - No C++ exception crosses this interface; errors are kkt_status codes.
+ */
+#ifndef KKT_GB300_H
+#define KKT_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kkt_ctx kkt_ctx;
+
+typedef enum {
+    KKT_OK = 0,
+    KKT_E_ARG = 1,        /* invalid argument (null pointer, bad size, bad option) */
+    KKT_E_CUDA = 2,       /* a CUDA runtime call failed */
+    KKT_E_NOMEM = 3,      /* device or host allocation failed, or over the memory budget */
+    KKT_E_STATE = 4,      /* call out of order (solve before refactor, ...) */
+    KKT_E_STRUCT = 5,     /* pattern not symmetric / unsorted / missing diagonal */
+    KKT_E_NOCONV = 6,     /* refinement did not reach the tolerance */
+    KKT_E_TIMEOUT = 7,    /* a bounded device wait gave up */
+    KKT_E_NUMERIC = 8     /* NaN or Inf met in the factorization or the residual */
+} kkt_status;
+
+enum { KKT_FP64 = 0,      /* factors and triangular solves in FP64 */
+       KKT_FP32_IR = 1 }; /* factors and triangular solves in FP32 (FP32 accumulation);
+                             scaling, residual and FGMRES stay FP64 */
+
+enum { KKT_ORDER_MINDEG = 0,  /* the library's quotient-graph minimum degree */
+       KKT_ORDER_USER = 1,    /* kkt_options.user_perm */
+       KKT_ORDER_NATURAL = 2 };
+
+typedef struct {
+    int precision;              /* KKT_FP64 (default) or KKT_FP32_IR */
+    int ordering;               /* KKT_ORDER_* (default KKT_ORDER_MINDEG) */
+    const int32_t *user_perm;   /* host, n entries: user_perm[k] = original row/column
+                                   eliminated k-th; read only during kkt_analyze */
+    double static_pivot_eps;    /* a pivot u_jj with |u_jj| < eps * max|D K D| is replaced by
+                                   sign(u_jj) * eps * max|D K D| (sign(0) = +1) and counted.
+                                   <= 0 selects the default: 1e-14 (FP64), 1e-7 (FP32) */
+    int ruiz_iters;             /* equilibration iterations per refactor (default 10) */
+    int restart;                /* FGMRES restart length m (default 30, max 64) */
+    int max_cycles;             /* FGMRES restart cycles (default 10) */
+    int relax_pivots;           /* supernode amalgamation: max pivots of a merged front
+                                   for the "small front" rule (default 16) */
+    double relax_zeros;         /* amalgamation: max share of explicit zeros (default 0.15) */
+    int max_pivots;             /* amalgamation: max pivots per supernode (default 64) */
+} kkt_options;
+
+typedef struct {
+    int n_perturbed;            /* static pivot perturbations in the last refactor */
+    int iters;                  /* FGMRES inner iterations of the last refine */
+    double backward_err;        /* omega = ||b-Kx||_inf / (||K||_inf ||x||_inf + ||b||_inf), FP64 */
+    double rel_resid2;          /* ||b-Kx||_2 / ||b||_2 */
+    int refactor_count;         /* refactorizations since analyze */
+    int status;                 /* kkt_status of the last numeric call (device-side checks) */
+    long long launches;         /* CUDA kernels this context has launched since analyze */
+} kkt_info;
+
+/* Per-kernel timing of a context in profiling mode (see kkt_set_profiling). */
+typedef struct {
+    const char *name;           /* kernel (or kernel family) name, static storage */
+    long long launches;         /* kernels launched */
+    double ms;                  /* summed CUDA-event time of their launch groups */
+} kkt_kernel_stat;
+
+/* Sizes of an analysis: what a context will hold in device memory. */
+typedef struct {
+    int n;
+    int64_t nnz;                /* nonzeros of K */
+    int64_t nnz_lu;             /* structural nonzeros of L + U (diagonal once) */
+    int64_t stored_factor;      /* factor values stored (incl. amalgamation zeros) */
+    int n_fronts;               /* supernodes / frontal matrices */
+    int n_levels;               /* levels of the assembly tree */
+    int max_front;              /* largest frontal matrix order */
+    int max_pivots;             /* most pivots in one front */
+    double flops;               /* dense front flops per refactor */
+    double flops_exact;         /* flops on the exact (non-amalgamated) structure */
+    int64_t device_bytes;       /* device memory kkt_analyze would allocate */
+} kkt_plan_info;
+
+/* Fill *opt with the defaults listed above. */
+void kkt_default_options(kkt_options *opt);
+
+/* Host-only: run the analysis of kkt_analyze (ordering, symbolic
+ * factorization, supernodes, schedule) and report its sizes without touching
+ * the GPU. Used for memory-budget admission. opt may be NULL (defaults).
+ * Errors: KKT_E_ARG, KKT_E_STRUCT. */
+kkt_status kkt_plan(int32_t n, const int32_t *h_rowptr, const int32_t *h_colidx,
+                    const kkt_options *opt, kkt_plan_info *out);
+
+/* Analysis stage (Sec. II stage i; Alg. 1 steps 1-4). n_primal is the size
+ * of the (1,1) block (used only for reporting). The pattern arrays are read
+ * and copied; h_vals is not needed by the static-pivot analysis and may be
+ * NULL. Allocates every device buffer the context will use, on the current
+ * device, and uploads the schedule. On success *out receives a context
+ * that kkt_destroy frees. Synchronous.
+ * Errors: KKT_E_ARG, KKT_E_STRUCT, KKT_E_NOMEM, KKT_E_CUDA. */
+kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t *h_rowptr,
+                       const int32_t *h_colidx, const double *h_vals,
+                       const kkt_options *opt, kkt_ctx **out);
+
+/* Numeric refactorization (Alg. 1 steps 6-7) of the matrix with values
+ * d_vals (device, nnz FP64 in the CSR order given to kkt_analyze):
+ * power-of-two symmetric Ruiz equilibration D K D (FP64), scatter into the
+ * frozen pattern, multifrontal LU without pivoting of P (D K D) P^T with
+ * static pivot perturbation, in the context's precision. Asynchronous.
+ * Device-detected NaN/Inf are reported by kkt_get_info (status field).
+ * Errors: KKT_E_ARG, KKT_E_CUDA. */
+kkt_status kkt_refactor(kkt_ctx *ctx, const double *d_vals, void *stream);
+
+/* x = K^{-1} b with the current factors (Alg. 1 step 8, no refinement):
+ * x = D P^T U^{-1} L^{-1} P D b. d_rhs and d_x are device FP64 vectors of
+ * length n and may not alias. Asynchronous.
+ * Errors: KKT_E_ARG, KKT_E_STATE (no refactor yet), KKT_E_CUDA. */
+kkt_status kkt_solve(kkt_ctx *ctx, const double *d_rhs, double *d_x, void *stream);
+
+/* Solve then refine with restarted FGMRES(m) on the unscaled K, right
+ * preconditioned by the factors, Arnoldi and update in FP64, until the
+ * backward error omega <= tol (Alg. 1 step 8 with refinement; Sec. V).
+ * Synchronizes `stream` (the restart loop reads convergence on the host).
+ * info (may be NULL) receives iterations and the final omega.
+ * Errors: KKT_E_ARG, KKT_E_STATE, KKT_E_CUDA, KKT_E_NOCONV, KKT_E_NUMERIC. */
+kkt_status kkt_refine(kkt_ctx *ctx, const double *d_rhs, double *d_x, double tol,
+                      kkt_info *info, void *stream);
+
+/* One whole IPM step through host memory, for callers without device
+ * buffers: copy h_vals and h_rhs to the device, refactor, refine to tol, copy
+ * x back to h_x. Synchronous. Same errors as kkt_refine. */
+kkt_status kkt_step_host(kkt_ctx *ctx, const double *h_vals, const double *h_rhs,
+                         double *h_x, double tol, kkt_info *info, void *stream);
+
+/* Refactor several contexts in one pass of launches (one launch per level for
+ * all of them). ctxs must share one precision. Asynchronous.
+ * Errors: KKT_E_ARG, KKT_E_CUDA. */
+kkt_status kkt_refactor_batched(kkt_ctx *const *ctxs, const double *const *d_vals,
+                                int count, void *stream);
+
+/* Batched kkt_solve over contexts of one precision. Asynchronous. */
+kkt_status kkt_solve_batched(kkt_ctx *const *ctxs, const double *const *d_rhs,
+                             double *const *d_x, int count, void *stream);
+
+/* Residual r = b - K x (FP64, unscaled K of the last refactor; the library
+ * keeps its own copy of K, so d_vals may be released once kkt_refactor's
+ * work on the stream has completed) and the
+ * backward error omega of x; omega_out (host) may be NULL. Synchronous when
+ * omega_out is not NULL. Errors: KKT_E_ARG, KKT_E_STATE, KKT_E_CUDA. */
+kkt_status kkt_residual(kkt_ctx *ctx, const double *d_rhs, const double *d_x, double *d_r,
+                        double *omega_out, void *stream);
+
+/* Statistics of the context. Synchronizes the device to read the
+ * perturbation count and NaN/Inf flag of the last refactor. */
+kkt_status kkt_get_info(const kkt_ctx *ctx, kkt_info *info);
+
+/* Profiling mode: when on, every launch group is bracketed by a pair of CUDA
+ * events on its stream (adds a little host overhead). */
+kkt_status kkt_set_profiling(kkt_ctx *ctx, int on);
+
+/* Synchronize, aggregate the event pairs recorded since the last call per
+ * kernel, write up to max_out entries and reset. Returns the number of
+ * entries written, or -1 on error. */
+int kkt_kernel_stats(kkt_ctx *ctx, kkt_kernel_stat *out, int max_out);
+kkt_status kkt_get_plan(const kkt_ctx *ctx, kkt_plan_info *info);
+
+/* Elimination order chosen by the analysis (after postordering):
+ * h_perm[k] = original index eliminated k-th (n entries, host). */
+kkt_status kkt_get_perm(const kkt_ctx *ctx, int32_t *h_perm);
+
+/* Equilibration factors d of the last refactor (n FP64, host). Synchronous. */
+kkt_status kkt_get_scaling(const kkt_ctx *ctx, double *h_d);
+
+/* Export the factors of the last refactor as coordinate lists keyed by
+ * ORIGINAL indices, for checking: every stored entry (amalgamation zeros
+ * included) of L (strictly lower, unit diagonal implied) and of U (upper,
+ * diagonal included) of P (D K D) P^T, widened to FP64. h_*_row/col are
+ * original row/column indices. Pass NULL arrays to query the counts only
+ * (*nl, *nu). Synchronous.
+ * Errors: KKT_E_ARG, KKT_E_STATE, KKT_E_CUDA. */
+kkt_status kkt_export_factors(const kkt_ctx *ctx, int64_t *nl, int32_t *h_l_row, int32_t *h_l_col,
+                              double *h_l_val, int64_t *nu, int32_t *h_u_row, int32_t *h_u_col,
+                              double *h_u_val);
+
+kkt_status kkt_destroy(kkt_ctx *ctx);
+
+const char *kkt_status_string(kkt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KKT_GB300_H */

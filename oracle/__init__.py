@@ -61,6 +61,7 @@ def _load():
         lib.ora_fgmres.argtypes = [C.c_int, _i32p, _i32p, _f64p, C.c_void_p, _f64p, _f64p, _f64p,
                                    C.c_int, C.c_int, C.c_double, C.POINTER(C.c_double)]
         lib.ora_fgmres.restype = C.c_int
+        lib.ora_lu_error_bound.argtypes = [C.c_void_p, _i32p, _i32p, _f64p, C.c_double, C.c_double, _f64p, _f64p]
         _lib = lib
     return _lib
 
@@ -149,6 +150,16 @@ class LU:
         lib.ora_lu_export(self.h, p, q, Lp, Li, Lx, Up, Ui, Ux)
         return Factors(p, q, Lp, Li[:nl], Lx[:nl], Up, Ui[:nu], Ux[:nu],
                        lib.ora_lu_n_perturbed(self.h), lib.ora_lu_n_offdiag(self.h), self)
+
+    def error_bound(self, rowptr, colidx, scaled_vals, unit=2.0 ** -53, pivot_floor=0.0):
+        """First-order running error bounds (eL, eU) aligned with Lx / Ux for a
+        computation of these factors in a format of unit roundoff `unit`."""
+        rp, ci, v = _csr(rowptr, colidx, scaled_vals)
+        lib = _load()
+        nl, nu = lib.ora_lu_nnz_l(self.h), lib.ora_lu_nnz_u(self.h)
+        eL, eU = np.zeros(max(nl, 1)), np.zeros(max(nu, 1))
+        lib.ora_lu_error_bound(self.h, rp, ci, v, float(unit), float(pivot_floor), eL, eU)
+        return eL[:nl], eU[:nu]
 
     def solve(self, c):
         z = np.empty(self.n)

@@ -582,3 +582,75 @@ int ora_fgmres(int n, const int *rp, const int *ci, const double *v,
     free(V); free(Z); free(H); free(cs); free(sn); free(g); free(yv); free(w); free(r);
     return total;
 }
+
+/* ------------------------------------------------ running error bounds */
+
+/*
+ * First-order running error bound (Wilkinson's running error analysis) for
+ * every entry of the factors F of the scaled matrix A (CSR, structurally
+ * symmetric), for a computation in a floating-point format of unit roundoff
+ * `unit` that forms each entry as in the left-looking elimination of ora_lu
+ * in any summation order:
+ *
+ *   x_i = a_i - sum_k l_ik u_k    (m_i terms)
+ *   err(x_i) <= sum_k (|l_ik| err(u_k) + err(l_ik) |u_k|)
+ *               + gamma_{m_i+1} (|a_i| + sum_k |l_ik| |u_k|)
+ *   u entries: err(u) = err(x);   l_ij = x_i / u_jj:
+ *   err(l_ij) <= (err(x_i) + |l_ij| err(u_jj)) / |u_jj| + unit |l_ij|
+ *
+ * gamma_m = m unit / (1 - m unit). A perturbed pivot is an exact constant
+ * (err 0; a pivot of magnitude exactly pivot_floor is taken as replaced).
+ * eL / eU are aligned with Lx / Ux. The bound is first order: it
+ * is meaningful only where err(u_jj) < |u_jj| / 2.
+ */
+void ora_lu_error_bound(const ora_lu_t *F, const int *rp, const int *ci, const double *v,
+                        double unit, double pivot_floor, double *eL, double *eU)
+{
+    int n = F->n;
+    double *X = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));   /* |a| + sum |l||u| */
+    double *E = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));   /* propagated error */
+    int *M = (int *)calloc((size_t)(n > 0 ? n : 1), sizeof(int));
+    for (int j = 0; j < n; j++) {
+        int col = F->q[j];
+        /* |A(:, col)| over original rows */
+        for (int t = rp[col]; t < rp[col + 1]; t++) {
+            int r = ci[t];
+            for (int s = rp[r]; s < rp[r + 1]; s++)
+                if (ci[s] == col) { X[r] = fabs(v[s]); break; }
+        }
+        int dpos = F->Up[j + 1] - 1;
+        for (int s = F->Up[j]; s < dpos; s++) {
+            int k = F->Ui[s];
+            int r = F->p[k];
+            double mk = (double)(M[r] + 1);
+            double ek = E[r] + (mk * unit / (1.0 - mk * unit)) * X[r];
+            eU[s] = ek;
+            double uk = fabs(F->Ux[s]);
+            for (int t = F->Lp[k]; t < F->Lp[k + 1]; t++) {
+                int i = F->p[F->Li[t]];
+                double l = fabs(F->Lx[t]);
+                E[i] += l * ek + eL[t] * uk;
+                X[i] += l * uk;
+                M[i] += 1;
+            }
+        }
+        int rj = F->p[j];
+        double ujj = F->Ux[dpos];
+        double md = (double)(M[rj] + 1);
+        double eujj = E[rj] + (md * unit / (1.0 - md * unit)) * X[rj];
+        if (pivot_floor > 0.0 && fabs(ujj) == pivot_floor) eujj = 0.0;   /* replaced: exact constant */
+        eU[dpos] = eujj;
+        double au = fabs(ujj);
+        for (int t = F->Lp[j]; t < F->Lp[j + 1]; t++) {
+            int i = F->p[F->Li[t]];
+            double l = fabs(F->Lx[t]);
+            double mi = (double)(M[i] + 1);
+            double ex = E[i] + (mi * unit / (1.0 - mi * unit)) * X[i];
+            eL[t] = (ex + l * eujj) / au + unit * l;
+        }
+        /* reset the work arrays on this column's pattern */
+        for (int s = F->Up[j]; s <= dpos; s++) { int r = F->p[F->Ui[s]]; X[r] = 0.0; E[r] = 0.0; M[r] = 0; }
+        for (int t = F->Lp[j]; t < F->Lp[j + 1]; t++) { int i = F->p[F->Li[t]]; X[i] = 0.0; E[i] = 0.0; M[i] = 0; }
+    }
+    free(X); free(E); free(M);
+}

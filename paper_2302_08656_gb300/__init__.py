@@ -1,0 +1,215 @@
+"""GB300-native refactorization of ACOPF KKT systems (arxiv 2302.08656).
+
+Thin Python binding over the C ABI of ``include/kkt.h``: argument marshalling
+only. Device memory and streams come from PyTorch; every step of the path
+(equilibration, scatter, multifrontal LU, triangular solves, residual, FGMRES
+vector work) runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from ._native import Info, KernelStat, Options, PlanInfo, build, lib
+
+__all__ = ["KKTSolver", "KKTError", "plan", "refactor_batched", "solve_batched", "build",
+           "FP64", "FP32_IR", "Options", "Info", "PlanInfo"]
+
+FP64, FP32_IR = 0, 1
+_ORDER = {"mindeg": 0, "user": 1, "natural": 2}
+_STATUS = {0: "KKT_OK", 1: "KKT_E_ARG", 2: "KKT_E_CUDA", 3: "KKT_E_NOMEM", 4: "KKT_E_STATE",
+           5: "KKT_E_STRUCT", 6: "KKT_E_NOCONV", 7: "KKT_E_TIMEOUT", 8: "KKT_E_NUMERIC"}
+
+
+class KKTError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = int(status)
+        msg = lib().kkt_status_string(self.status).decode()
+        super().__init__("%s: %s (%s)" % (where, _STATUS.get(self.status, "?"), msg))
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise KKTError(st, where)
+
+
+def _opts(precision="fp64", ordering="mindeg", user_perm=None, static_pivot_eps=0.0, ruiz_iters=10,
+          restart=30, max_cycles=10, relax_pivots=16, relax_zeros=0.15, max_pivots=64):
+    o = Options()
+    lib().kkt_default_options(C.byref(o))
+    o.precision = FP32_IR if precision in ("fp32", "fp32_ir", FP32_IR) else FP64
+    o.ordering = _ORDER[ordering] if isinstance(ordering, str) else int(ordering)
+    keep = None
+    if user_perm is not None:
+        keep = np.ascontiguousarray(user_perm, dtype=np.int32)
+        o.user_perm = keep.ctypes.data
+        o.ordering = 1
+    o.static_pivot_eps = float(static_pivot_eps)
+    o.ruiz_iters = int(ruiz_iters)
+    o.restart = int(restart)
+    o.max_cycles = int(max_cycles)
+    o.relax_pivots = int(relax_pivots)
+    o.relax_zeros = float(relax_zeros)
+    o.max_pivots = int(max_pivots)
+    return o, keep
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def plan(rowptr, colidx, **opts) -> dict:
+    """Host-only analysis sizes (no GPU needed)."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(colidx, dtype=np.int32)
+    o, keep = _opts(**opts)
+    out = PlanInfo()
+    _check(lib().kkt_plan(rp.size - 1, rp.ctypes.data, ci.ctypes.data, C.byref(o), C.byref(out)), "kkt_plan")
+    return {f: getattr(out, f) for f, _ in PlanInfo._fields_}
+
+
+class KKTSolver:
+    """One analysed KKT pattern with its device-resident factors."""
+
+    def __init__(self, rowptr, colidx, n_primal: int = 0, **opts):
+        self._rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        self._ci = np.ascontiguousarray(colidx, dtype=np.int32)
+        self.n = self._rp.size - 1
+        self.nnz = int(self._rp[-1])
+        o, keep = _opts(**opts)
+        self.precision = "fp32" if o.precision == FP32_IR else "fp64"
+        h = C.c_void_p()
+        _check(lib().kkt_analyze(self.n, int(n_primal), self._rp.ctypes.data, self._ci.ctypes.data, None,
+                                 C.byref(o), C.byref(h)), "kkt_analyze")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kkt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- numeric stages ---------------------------------------------------
+    def refactor(self, vals, stream=None):
+        assert vals.is_cuda and vals.dtype.itemsize == 8 and vals.numel() == self.nnz and vals.is_contiguous()
+        _check(lib().kkt_refactor(self._h, _ptr(vals), _stream(stream)), "kkt_refactor")
+
+    def solve(self, rhs, out=None, stream=None):
+        import torch
+        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n and rhs.is_contiguous()
+        if out is None:
+            out = torch.empty_like(rhs)
+        _check(lib().kkt_solve(self._h, _ptr(rhs), _ptr(out), _stream(stream)), "kkt_solve")
+        return out
+
+    def refine(self, rhs, out=None, tol=1e-10, stream=None, raise_on_noconv=True):
+        import torch
+        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n and rhs.is_contiguous()
+        if out is None:
+            out = torch.empty_like(rhs)
+        info = Info()
+        st = lib().kkt_refine(self._h, _ptr(rhs), _ptr(out), float(tol), C.byref(info), _stream(stream))
+        if st != 6 or raise_on_noconv:
+            _check(st, "kkt_refine")
+        return out, info
+
+    def step_host(self, vals, rhs, tol=1e-10, out=None, stream=None):
+        """Refactor + refine through host buffers (copies inside the call)."""
+        v = np.ascontiguousarray(vals, dtype=np.float64)
+        b = np.ascontiguousarray(rhs, dtype=np.float64)
+        x = np.empty(self.n) if out is None else out
+        info = Info()
+        st = lib().kkt_step_host(self._h, v.ctypes.data, b.ctypes.data, x.ctypes.data, float(tol),
+                                 C.byref(info), _stream(stream))
+        _check(st, "kkt_step_host")
+        return x, info
+
+    def residual(self, rhs, x, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty_like(rhs)
+        om = C.c_double(0.0)
+        _check(lib().kkt_residual(self._h, _ptr(rhs), _ptr(x), _ptr(out), C.byref(om), _stream(stream)),
+               "kkt_residual")
+        return out, om.value
+
+    # -- introspection ----------------------------------------------------
+    def info(self) -> Info:
+        i = Info()
+        _check(lib().kkt_get_info(self._h, C.byref(i)), "kkt_get_info")
+        return i
+
+    def plan(self) -> dict:
+        p = PlanInfo()
+        _check(lib().kkt_get_plan(self._h, C.byref(p)), "kkt_get_plan")
+        return {f: getattr(p, f) for f, _ in PlanInfo._fields_}
+
+    def set_profiling(self, on: bool = True):
+        _check(lib().kkt_set_profiling(self._h, 1 if on else 0), "kkt_set_profiling")
+
+    def kernel_stats(self) -> dict:
+        """{kernel name: (launches, ms)} since the last call (profiling mode)."""
+        arr = (KernelStat * 32)()
+        k = lib().kkt_kernel_stats(self._h, arr, 32)
+        if k < 0:
+            raise KKTError(2, "kkt_kernel_stats")
+        return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].ms)) for i in range(k)}
+
+    def perm(self) -> np.ndarray:
+        p = np.empty(self.n, dtype=np.int32)
+        _check(lib().kkt_get_perm(self._h, p.ctypes.data), "kkt_get_perm")
+        return p
+
+    def scaling(self) -> np.ndarray:
+        d = np.empty(self.n)
+        _check(lib().kkt_get_scaling(self._h, d.ctypes.data), "kkt_get_scaling")
+        return d
+
+    def export_factors(self):
+        """(L rows, L cols, L vals, U rows, U cols, U vals), original indices."""
+        nl, nu = C.c_int64(0), C.c_int64(0)
+        _check(lib().kkt_export_factors(self._h, C.byref(nl), None, None, None, C.byref(nu), None, None, None),
+               "kkt_export_factors")
+        lr, lc, lv = np.empty(nl.value, np.int32), np.empty(nl.value, np.int32), np.empty(nl.value)
+        ur, uc, uv = np.empty(nu.value, np.int32), np.empty(nu.value, np.int32), np.empty(nu.value)
+        _check(lib().kkt_export_factors(self._h, C.byref(nl), lr.ctypes.data, lc.ctypes.data, lv.ctypes.data,
+                                        C.byref(nu), ur.ctypes.data, uc.ctypes.data, uv.ctypes.data),
+               "kkt_export_factors")
+        return lr, lc, lv, ur, uc, uv
+
+
+def _ptr_array(items):
+    arr = (C.c_void_p * len(items))(*[C.c_void_p(x) for x in items])
+    return arr
+
+
+def refactor_batched(solvers, vals, stream=None):
+    hs = _ptr_array([s.handle.value for s in solvers])
+    vs = _ptr_array([v.data_ptr() for v in vals])
+    _check(lib().kkt_refactor_batched(hs, vs, len(solvers), _stream(stream)), "kkt_refactor_batched")
+
+
+def solve_batched(solvers, rhs, outs, stream=None):
+    hs = _ptr_array([s.handle.value for s in solvers])
+    bs = _ptr_array([b.data_ptr() for b in rhs])
+    xs = _ptr_array([x.data_ptr() for x in outs])
+    _check(lib().kkt_solve_batched(hs, bs, xs, len(solvers), _stream(stream)), "kkt_solve_batched")

@@ -1,0 +1,408 @@
+// Host analysis: ordering, elimination tree, symbolic structure, relaxed
+// supernodes and the multifrontal schedule. See analysis.hpp.
+#include "analysis.hpp"
+
+#include <algorithm>
+#include <numeric>
+#include <set>
+#include <utility>
+
+namespace kktgb {
+
+// ----------------------------------------------------------------- ordering
+//
+// Minimum degree on the quotient graph: eliminated nodes become "elements"
+// (cliques kept implicitly as the list of their variables); an element that
+// is adjacent to a newly eliminated pivot is absorbed into it. The degree of a
+// variable is its exact external degree |A_i U (union of L_e, e in E_i)| - 1,
+// recomputed for the variables of each new element.
+void min_degree_quotient(int n, const int* rowptr, const int* colidx, std::vector<int>& order)
+{
+    std::vector<std::vector<int>> av(n), ae(n), le(n);
+    std::vector<char> state(n, 0);           // 0 variable, 1 element, 2 absorbed
+    std::vector<int> deg(n), mark(n, -1);
+    for (int i = 0; i < n; ++i) {
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p)
+            if (colidx[p] != i) av[i].push_back(colidx[p]);
+        deg[i] = (int)av[i].size();
+    }
+    std::set<std::pair<int, int>> pq;
+    for (int i = 0; i < n; ++i) pq.insert({deg[i], i});
+    order.clear();
+    order.reserve(n);
+    int stamp = 0;
+    std::vector<int> lp;
+    while (!pq.empty()) {
+        int p = pq.begin()->second;
+        pq.erase(pq.begin());
+        order.push_back(p);
+        // L_p = (A_p U union of absorbed elements' variables) \ {p}
+        ++stamp;
+        mark[p] = stamp;
+        lp.clear();
+        for (int v : av[p])
+            if (state[v] == 0 && mark[v] != stamp) { mark[v] = stamp; lp.push_back(v); }
+        for (int e : ae[p]) {
+            if (state[e] != 1) continue;
+            for (int v : le[e])
+                if (state[v] == 0 && mark[v] != stamp) { mark[v] = stamp; lp.push_back(v); }
+            state[e] = 2;
+            std::vector<int>().swap(le[e]);
+        }
+        state[p] = 1;
+        std::vector<int>().swap(av[p]);
+        std::vector<int>().swap(ae[p]);
+        le[p] = lp;
+        // update every variable of the new element
+        for (int i : lp) {
+            // drop absorbed elements, add p
+            std::vector<int>& E = ae[i];
+            size_t w = 0;
+            for (int e : E) if (state[e] == 1) E[w++] = e;
+            E.resize(w);
+            E.push_back(p);
+            // prune variables now covered by element p (and p itself)
+            std::vector<int>& A = av[i];
+            w = 0;
+            for (int v : A) if (state[v] == 0 && mark[v] != stamp) A[w++] = v;
+            A.resize(w);
+        }
+        for (int i : lp) {
+            int st2 = ++stamp;
+            mark[i] = st2;
+            int d = 0;
+            for (int v : av[i]) if (state[v] == 0 && mark[v] != st2) { mark[v] = st2; ++d; }
+            for (int e : ae[i])
+                for (int v : le[e]) if (state[v] == 0 && mark[v] != st2) { mark[v] = st2; ++d; }
+            pq.erase({deg[i], i});
+            deg[i] = d;
+            pq.insert({d, i});
+        }
+        // restore the marks of L_p for the next pivot (stamps only grow)
+    }
+}
+
+// ------------------------------------------------------------------ helpers
+
+static int find_pos(const int* a, int len, int key)
+{
+    const int* it = std::lower_bound(a, a + len, key);
+    if (it == a + len || *it != key) return -1;
+    return (int)(it - a);
+}
+
+std::string analyze_pattern(int n, const int* rowptr, const int* colidx,
+                            const AnalysisOptions& opt, Analysis& out)
+{
+    if (n <= 0) return "n must be positive";
+    if (rowptr[0] != 0) return "rowptr[0] must be 0";
+    const int64_t nnz = rowptr[n];
+    for (int i = 0; i < n; ++i) {
+        if (rowptr[i + 1] < rowptr[i]) return "rowptr not monotone";
+        bool diag = false;
+        for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            int c = colidx[p];
+            if (c < 0 || c >= n) return "column index out of range";
+            if (p > rowptr[i] && colidx[p - 1] >= c) return "column indices not sorted/unique";
+            if (c == i) diag = true;
+        }
+        if (!diag) return "missing diagonal entry";
+    }
+    {   // structural symmetry: count of (i,j) must equal count of (j,i)
+        std::vector<int> cnt(n, 0);
+        for (int64_t p = 0; p < nnz; ++p) cnt[colidx[p]]++;
+        for (int i = 0; i < n; ++i)
+            if (cnt[i] != rowptr[i + 1] - rowptr[i]) return "pattern is not structurally symmetric";
+        for (int i = 0; i < n; ++i)
+            for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                int j = colidx[p];
+                if (find_pos(colidx + rowptr[j], rowptr[j + 1] - rowptr[j], i) < 0)
+                    return "pattern is not structurally symmetric";
+            }
+    }
+
+    // ---- ordering
+    std::vector<int> q;
+    if (opt.ordering == 1) {
+        if (!opt.user_perm) return "user ordering requested without a permutation";
+        q.assign(opt.user_perm, opt.user_perm + n);
+        std::vector<char> seen(n, 0);
+        for (int k = 0; k < n; ++k) {
+            if (q[k] < 0 || q[k] >= n || seen[q[k]]) return "user permutation is not a permutation";
+            seen[q[k]] = 1;
+        }
+    } else if (opt.ordering == 2) {
+        q.resize(n);
+        std::iota(q.begin(), q.end(), 0);
+    } else {
+        min_degree_quotient(n, rowptr, colidx, q);
+    }
+    std::vector<int> qinv(n);
+    for (int k = 0; k < n; ++k) qinv[q[k]] = k;
+
+    // ---- elimination tree of the permuted pattern (Liu, path compression)
+    std::vector<int> parent(n, -1), anc(n, -1);
+    for (int k = 0; k < n; ++k) {
+        int orig = q[k];
+        for (int p = rowptr[orig]; p < rowptr[orig + 1]; ++p) {
+            int i = qinv[colidx[p]];
+            if (i >= k) continue;
+            int r = i;
+            while (anc[r] != -1 && anc[r] != k) { int t = anc[r]; anc[r] = k; r = t; }
+            if (anc[r] == -1) { anc[r] = k; parent[r] = k; }
+        }
+    }
+    // ---- postorder (children ascending)
+    std::vector<int> chead(n, -1), cnext(n, -1);
+    for (int k = n - 1; k >= 0; --k)
+        if (parent[k] >= 0) { cnext[k] = chead[parent[k]]; chead[parent[k]] = k; }
+    std::vector<int> post;
+    post.reserve(n);
+    {
+        std::vector<int> stk;
+        for (int r = 0; r < n; ++r) {
+            if (parent[r] != -1) continue;
+            stk.push_back(r);
+            std::vector<int> it;   // iterate children manually
+            std::vector<int> cur;
+            cur.push_back(chead[r]);
+            it.push_back(r);
+            while (!it.empty()) {
+                int node = it.back();
+                int& c = cur.back();
+                if (c != -1) {
+                    int child = c;
+                    c = cnext[c];
+                    it.push_back(child);
+                    cur.push_back(chead[child]);
+                } else {
+                    post.push_back(node);
+                    it.pop_back();
+                    cur.pop_back();
+                }
+            }
+            stk.pop_back();
+        }
+    }
+    std::vector<int> ipost(n);
+    for (int t = 0; t < n; ++t) ipost[post[t]] = t;
+    out.n = n;
+    out.nnz = nnz;
+    out.perm.resize(n);
+    out.iperm.resize(n);
+    for (int t = 0; t < n; ++t) out.perm[t] = q[post[t]];
+    for (int t = 0; t < n; ++t) out.iperm[out.perm[t]] = t;
+    std::vector<int> par(n, -1);
+    for (int t = 0; t < n; ++t) par[t] = parent[post[t]] >= 0 ? ipost[parent[post[t]]] : -1;
+
+    // ---- symbolic structure of every column of L (rows > j, ascending)
+    std::vector<std::vector<int>> st(n);
+    std::vector<int> nchild(n, 0);
+    std::vector<std::vector<int>> kids(n);
+    for (int t = 0; t < n; ++t) if (par[t] >= 0) { nchild[par[t]]++; kids[par[t]].push_back(t); }
+    {
+        std::vector<int> mark(n, -1);
+        for (int j = 0; j < n; ++j) {
+            std::vector<int>& s = st[j];
+            int orig = out.perm[j];
+            for (int p = rowptr[orig]; p < rowptr[orig + 1]; ++p) {
+                int i = out.iperm[colidx[p]];
+                if (i > j && mark[i] != j) { mark[i] = j; s.push_back(i); }
+            }
+            for (int c : kids[j])
+                for (int i : st[c])
+                    if (i > j && mark[i] != j) { mark[i] = j; s.push_back(i); }
+            std::sort(s.begin(), s.end());
+        }
+    }
+    int64_t nnzl = 0;
+    double fl_exact = 0;
+    for (int j = 0; j < n; ++j) {
+        int64_t c = (int64_t)st[j].size();
+        nnzl += c;
+        fl_exact += (double)c + 2.0 * (double)c * (double)c;   // symmetric structure: |L col| = |U row|
+    }
+    out.nnz_l = nnzl;
+    out.nnz_u = nnzl + n;
+    out.flops_exact = fl_exact;
+
+    // ---- fundamental supernodes
+    struct SN { int first, last, parent; int64_t F; double zeros; std::vector<int> kids; bool alive; };
+    std::vector<SN> sn;
+    std::vector<int> sn_of(n, -1);
+    for (int j = 0; j < n;) {
+        int f = j;
+        while (j + 1 < n && par[j] == j + 1 && nchild[j + 1] == 1 && st[j].size() == st[j + 1].size() + 1)
+            ++j;
+        SN s;
+        s.first = f; s.last = j; s.parent = -1;
+        s.F = (int64_t)(j - f + 1) + (int64_t)st[j].size();
+        s.zeros = 0; s.alive = true;
+        for (int t = f; t <= j; ++t) sn_of[t] = (int)sn.size();
+        sn.push_back(std::move(s));
+        ++j;
+    }
+    for (size_t s = 0; s < sn.size(); ++s) {
+        int pj = par[sn[s].last];
+        sn[s].parent = pj >= 0 ? sn_of[pj] : -1;
+        if (pj >= 0) sn[sn_of[pj]].kids.push_back((int)s);
+    }
+    // ---- relaxed amalgamation of the last (contiguous) child into its parent
+    auto stored = [](int64_t F, int64_t w) { return (double)(F * w + w * (F - w)); };
+    for (size_t p = 0; p < sn.size(); ++p) {
+        while (true) {
+            SN& P = sn[p];
+            int c = -1;
+            for (int k : P.kids) if (sn[k].alive && sn[k].last + 1 == P.first) c = k;
+            if (c < 0) break;
+            SN& Cn = sn[c];
+            int64_t wc = Cn.last - Cn.first + 1, wp = P.last - P.first + 1;
+            int64_t w = wc + wp, F = wc + P.F;
+            if (w > opt.max_pivots) break;
+            double newz = 2.0 * (double)wc * (double)(P.F - (Cn.F - wc));
+            double z = Cn.zeros + P.zeros + newz;
+            double tot = stored(F, w);
+            bool ok = (z <= opt.relax_zeros * tot) || (F <= opt.relax_small && w <= opt.relax_small);
+            if (!ok) break;
+            P.first = Cn.first;
+            P.F = F;
+            P.zeros = z;
+            std::vector<int> nk;
+            for (int k : P.kids) if (k != c) nk.push_back(k);
+            for (int k : Cn.kids) { nk.push_back(k); sn[k].parent = (int)p; }
+            P.kids.swap(nk);
+            Cn.alive = false;
+        }
+    }
+    // ---- renumber surviving supernodes in column order (a postorder)
+    std::vector<int> alive_ids;
+    for (size_t s = 0; s < sn.size(); ++s) if (sn[s].alive) alive_ids.push_back((int)s);
+    std::sort(alive_ids.begin(), alive_ids.end(), [&](int a, int b) { return sn[a].first < sn[b].first; });
+    std::vector<int> newid(sn.size(), -1);
+    for (size_t k = 0; k < alive_ids.size(); ++k) newid[alive_ids[k]] = (int)k;
+    const int ns = (int)alive_ids.size();
+    out.ns = ns;
+    out.sn_first.assign(ns + 1, n);
+    out.sn_parent.assign(ns, -1);
+    out.sn_front.assign(ns, 0);
+    for (int k = 0; k < ns; ++k) {
+        const SN& s = sn[alive_ids[k]];
+        out.sn_first[k] = s.first;
+        out.sn_parent[k] = s.parent >= 0 ? newid[s.parent] : -1;
+    }
+    // row sets: pivots, then the union of the pivot columns' structures below the last pivot
+    out.rows_ptr.assign(ns + 1, 0);
+    out.rows.clear();
+    {
+        std::vector<int> mark(n, -1), buf;
+        for (int k = 0; k < ns; ++k) {
+            int f = out.sn_first[k], l = out.sn_first[k + 1] - 1;
+            buf.clear();
+            for (int j = f; j <= l; ++j)
+                for (int i : st[j])
+                    if (i > l && mark[i] != k) { mark[i] = k; buf.push_back(i); }
+            std::sort(buf.begin(), buf.end());
+            for (int j = f; j <= l; ++j) out.rows.push_back(j);
+            out.rows.insert(out.rows.end(), buf.begin(), buf.end());
+            out.rows_ptr[k + 1] = (int64_t)out.rows.size();
+            out.sn_front[k] = (int)(out.rows_ptr[k + 1] - out.rows_ptr[k]);
+        }
+    }
+    // children lists and levels
+    out.child_ptr.assign(ns + 1, 0);
+    for (int k = 0; k < ns; ++k) if (out.sn_parent[k] >= 0) out.child_ptr[out.sn_parent[k] + 1]++;
+    for (int k = 0; k < ns; ++k) out.child_ptr[k + 1] += out.child_ptr[k];
+    out.child_list.assign(out.child_ptr[ns], 0);
+    {
+        std::vector<int> fill(out.child_ptr.begin(), out.child_ptr.end() - 1);
+        for (int k = 0; k < ns; ++k)
+            if (out.sn_parent[k] >= 0) out.child_list[fill[out.sn_parent[k]]++] = k;
+    }
+    std::vector<int> lev(ns, 0);
+    int nlev = 0;
+    for (int k = 0; k < ns; ++k) {           // children precede parents
+        if (out.sn_parent[k] >= 0) lev[out.sn_parent[k]] = std::max(lev[out.sn_parent[k]], lev[k] + 1);
+        nlev = std::max(nlev, lev[k] + 1);
+    }
+    out.n_levels = nlev;
+    out.level_ptr.assign(nlev + 1, 0);
+    for (int k = 0; k < ns; ++k) out.level_ptr[lev[k] + 1]++;
+    for (int l = 0; l < nlev; ++l) out.level_ptr[l + 1] += out.level_ptr[l];
+    out.level_fronts.assign(ns, 0);
+    {
+        std::vector<int> fill(out.level_ptr.begin(), out.level_ptr.end() - 1);
+        for (int k = 0; k < ns; ++k) out.level_fronts[fill[lev[k]]++] = k;
+    }
+    // supernode of each step
+    std::vector<int> snk(n);
+    for (int k = 0; k < ns; ++k)
+        for (int j = out.sn_first[k]; j < out.sn_first[k + 1]; ++j) snk[j] = k;
+    // assembly of original entries: entry (r, c) goes to the front of min(r, c)
+    {
+        std::vector<int64_t> cnt(ns + 1, 0);
+        for (int i = 0; i < n; ++i)
+            for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                int r = out.iperm[i], c = out.iperm[colidx[p]];
+                cnt[snk[std::min(r, c)] + 1]++;
+            }
+        for (int k = 0; k < ns; ++k) cnt[k + 1] += cnt[k];
+        out.asm_ptr = cnt;
+        out.asm_pos.assign(nnz, 0);
+        out.asm_src.assign(nnz, 0);
+        std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+        for (int i = 0; i < n; ++i)
+            for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                int r = out.iperm[i], c = out.iperm[colidx[p]];
+                int k = snk[std::min(r, c)];
+                const int* R = out.rows.data() + out.rows_ptr[k];
+                int F = out.sn_front[k];
+                int a = find_pos(R, F, r), b = find_pos(R, F, c);
+                if (a < 0 || b < 0) return "internal: entry outside its front";
+                int64_t at = fill[k]++;
+                out.asm_pos[at] = a + b * F;
+                out.asm_src[at] = p;
+            }
+    }
+    // relative indices of each contribution block in its parent
+    out.rel_ptr.assign(ns + 1, 0);
+    for (int k = 0; k < ns; ++k) {
+        int w = out.sn_first[k + 1] - out.sn_first[k];
+        out.rel_ptr[k + 1] = out.rel_ptr[k] + (out.sn_front[k] - w);
+    }
+    out.rel.assign(out.rel_ptr[ns], 0);
+    for (int k = 0; k < ns; ++k) {
+        int w = out.sn_first[k + 1] - out.sn_first[k];
+        int F = out.sn_front[k];
+        int pk = out.sn_parent[k];
+        if (F == w) continue;
+        if (pk < 0) return "internal: root front with a contribution block";
+        const int* R = out.rows.data() + out.rows_ptr[k];
+        const int* Rp = out.rows.data() + out.rows_ptr[pk];
+        for (int t = w; t < F; ++t) {
+            int pos = find_pos(Rp, out.sn_front[pk], R[t]);
+            if (pos < 0) return "internal: contribution row missing from the parent front";
+            out.rel[out.rel_ptr[k] + (t - w)] = pos;
+        }
+    }
+    // storage and statistics
+    out.panel_off.assign(ns + 1, 0);
+    out.cb_off.assign(ns + 1, 0);
+    double fl = 0;
+    out.max_front = 0;
+    out.max_pivots = 0;
+    for (int k = 0; k < ns; ++k) {
+        int64_t w = out.sn_first[k + 1] - out.sn_first[k], F = out.sn_front[k];
+        out.panel_off[k + 1] = out.panel_off[k] + F * w + w * (F - w);
+        out.cb_off[k + 1] = out.cb_off[k] + (F - w) * (F - w);
+        for (int64_t p = 0; p < w; ++p) fl += (double)(F - p - 1) + 2.0 * (double)(F - p - 1) * (double)(F - p - 1);
+        out.max_front = std::max<int>(out.max_front, (int)F);
+        out.max_pivots = std::max<int>(out.max_pivots, (int)w);
+    }
+    out.panel_total = out.panel_off[ns];
+    out.cb_total = out.cb_off[ns];
+    out.stored_factor = out.panel_total;
+    out.flops = fl;
+    return std::string();
+}
+
+}  // namespace kktgb

@@ -1,0 +1,112 @@
+// Device data layout and kernel launchers of the GB300 KKT path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kktgb {
+
+// Read-only schedule produced by the host analysis, resident in HBM.
+struct DevSched {
+    int n = 0;
+    int64_t nnz = 0;
+    int ns = 0;
+    const int* rowptr = nullptr;      // K pattern (n+1)
+    const int* colidx = nullptr;      // (nnz)
+    const int* perm = nullptr;        // step -> original index (n)
+    const int* sn_first = nullptr;    // (ns+1)
+    const int* sn_front = nullptr;    // (ns)
+    const int64_t* rows_ptr = nullptr;
+    const int* rows = nullptr;
+    const int* child_ptr = nullptr;
+    const int* child_list = nullptr;
+    const int64_t* asm_ptr = nullptr;
+    const int* asm_pos = nullptr;
+    const int* asm_src = nullptr;
+    const int64_t* rel_ptr = nullptr;
+    const int* rel = nullptr;
+    const int64_t* panel_off = nullptr;
+    const int64_t* cb_off = nullptr;
+};
+
+// Device-side counters of one context, cleared at the start of each refactor.
+struct DevStat {
+    unsigned long long amax_bits;     // max |D K D| as the bits of a non-negative double
+    unsigned long long knorm_bits;    // ||K||_inf
+    int n_perturbed;
+    int numeric_bad;
+    int ruiz_changed[64];
+};
+
+// Per-context numeric buffers.
+template <typename T>
+struct DevNum {
+    const double* vals = nullptr;     // K values of the current refactor (caller memory)
+    double* kcopy = nullptr;          // library-owned copy of K (residuals use it after the call)
+    double* d = nullptr;              // equilibration factors (n)
+    double* dtmp = nullptr;           // ping-pong buffer (n)
+    T* sv = nullptr;                  // D K D in factor precision (nnz)
+    T* panel = nullptr;               // factor panels
+    T* cb = nullptr;                  // contribution blocks
+    T* vec = nullptr;                 // step-space solve vector (n)
+    T* cbv = nullptr;                 // solve contribution vectors
+    DevStat* stat = nullptr;
+    double pivot_eps = 1e-14;
+};
+
+// One launch group: the fronts of one level of one context.
+struct FrontTile { int front; int ti; int tj; };
+
+constexpr int kWarpFrontMax = 32;      // fronts with F <= 32 are handled by one warp
+constexpr int kPanelCbMin = 48;        // fronts with F - w >= 48 use panel + tiled Schur update
+constexpr int kTile = 32;              // Schur update tile (kTile x kTile)
+
+// Launchers (all asynchronous on `st`).
+cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double* dtmp, int iters,
+                        DevStat* stat, double** d_final, cudaStream_t st);
+template <typename T>
+cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_fronts_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
+                              int max_front, cudaStream_t st);
+template <typename T>
+cudaError_t launch_fronts_panel(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
+                                size_t smem_bytes, T* gscratch, int64_t scratch_stride, cudaStream_t st);
+template <typename T>
+cudaError_t launch_schur_tiles(const DevSched& s, const DevNum<T>& nm, const FrontTile* tiles, int count,
+                               cudaStream_t st);
+template <typename T>
+cudaError_t launch_solve_pre(const DevSched& s, const DevNum<T>& nm, const double* b, cudaStream_t st);
+template <typename T>
+cudaError_t launch_solve_fwd(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
+                             int max_front, cudaStream_t st);
+template <typename T>
+cudaError_t launch_solve_bwd(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
+                             int max_front, cudaStream_t st);
+template <typename T>
+cudaError_t launch_solve_post(const DevSched& s, const DevNum<T>& nm, double* x, cudaStream_t st);
+
+// FP64 vector kernels for the residual and FGMRES.
+cudaError_t launch_spmv_resid(int n, const int* rp, const int* ci, const double* v, const double* x,
+                              const double* b, double* r, cudaStream_t st);
+cudaError_t launch_spmv(int n, const int* rp, const int* ci, const double* v, const double* x,
+                        double* y, cudaStream_t st);
+// out[k] = <V_k, w> for k < nv (V column-major with leading dimension ldv); out zeroed inside
+cudaError_t launch_multidot(int n, const double* V, int64_t ldv, int nv, const double* w, double* out,
+                            cudaStream_t st);
+// w -= V * h (nv columns)
+cudaError_t launch_multiaxpy(int n, double* w, const double* V, int64_t ldv, int nv, const double* h,
+                             cudaStream_t st);
+// y = alpha * x (alpha from device pointer, inverted if invert != 0)
+cudaError_t launch_scal_copy(int n, const double* x, double* y, const double* alpha, int invert,
+                             cudaStream_t st);
+// x += Z * y (nv columns)
+cudaError_t launch_update(int n, double* x, const double* Z, int64_t ldz, int nv, const double* y,
+                          cudaStream_t st);
+// out[0] = max |a|, out[1] = sum a^2 (zeroed inside); for several vectors in one launch
+cudaError_t launch_norms(int n, const double* a, double* out, cudaStream_t st);
+cudaError_t launch_zero_stat(DevStat* stat, cudaStream_t st);
+
+}  // namespace kktgb

@@ -1,0 +1,975 @@
+// Runtime and C ABI (include/kkt.h): context, device memory pool, launch
+// schedule per assembly-tree level, FGMRES refinement driver.
+#include "../../include/kkt.h"
+#include "analysis.hpp"
+#include "kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace kktgb {
+cudaError_t configure_kernels();
+}
+
+using namespace kktgb;
+
+namespace {
+
+struct LevelGroup {
+    int warp_off = 0, warp_cnt = 0;           // offsets into the device front-id array
+    int cta_off = 0, cta_cnt = 0, cta_maxF = 0;
+    int panel_off = 0, panel_cnt = 0;
+    size_t panel_smem = 0;                    // 0 with panel_global = true
+    bool panel_global = false;
+    int tile_off = 0, tile_cnt = 0;
+    int all_off = 0, all_cnt = 0, all_maxF = 0;   // every front of the level (solve)
+};
+
+// Device pool: one allocation carved into aligned pieces.
+struct Pool {
+    char* base = nullptr;
+    size_t size = 0, used = 0;
+    template <typename X>
+    X* take(size_t count)
+    {
+        size_t bytes = ((count * sizeof(X)) + 255) & ~size_t(255);
+        X* p = reinterpret_cast<X*>(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+constexpr int kMaxRestart = 64;
+constexpr size_t kRedScratch = 128 + 304 * (kMaxRestart + 2) + 16;
+
+}  // namespace
+
+struct kkt_ctx {
+    kkt_options opt;
+    Analysis an;
+    int n = 0, n_primal = 0;
+    int64_t nnz = 0;
+    std::vector<LevelGroup> levels;
+    int64_t scratch_stride = 0;      // panel scratch per CTA (global fallback)
+    int max_panel_global = 0;
+    Pool pool;
+    DevSched sched;
+    DevStat* stat = nullptr;
+    // numeric buffers (one precision is used)
+    DevNum<double> nd;
+    DevNum<float> nf;
+    double* d_a = nullptr;           // Ruiz buffers
+    double* d_b = nullptr;
+    double* d_final = nullptr;
+    void* panel_scratch = nullptr;
+    int* fronts_dev = nullptr;
+    FrontTile* tiles_dev = nullptr;
+    // refinement workspace (FP64)
+    double* V = nullptr;             // n x (m+1)
+    double* Z = nullptr;             // n x m
+    double* w = nullptr;
+    double* r = nullptr;
+    double* red = nullptr;           // reduction scratch + small vectors
+    double* h_dev = nullptr;         // small vectors on device
+    double* kvals = nullptr;         // copy of K made by the last refactor
+    double* stage_vals = nullptr;    // device staging for kkt_step_host
+    double* stage_b = nullptr;
+    double* stage_x = nullptr;
+    double* pin = nullptr;           // pinned host mirror of small results
+    // launch accounting and optional per-kernel timing
+    long long launches = 0;
+    int profile = 0;
+    std::vector<cudaEvent_t> ev;       // 2 events per recorded launch group
+    std::vector<int> ev_kind;
+    std::vector<int> ev_count;         // kernels issued by the group
+    size_t ev_used = 0;
+    // state
+    const double* last_vals = nullptr;
+    int refactored = 0;
+    int refactor_count = 0;
+    kkt_info info{};
+    int64_t device_bytes = 0;
+};
+
+namespace {
+
+kkt_status cuda_status(cudaError_t e) { return e == cudaSuccess ? KKT_OK : KKT_E_CUDA; }
+
+#define KKT_CUDA(call)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return KKT_E_CUDA;           \
+    } while (0)
+
+void fill_defaults(kkt_options* o)
+{
+    std::memset(o, 0, sizeof(*o));
+    o->precision = KKT_FP64;
+    o->ordering = KKT_ORDER_MINDEG;
+    o->user_perm = nullptr;
+    o->static_pivot_eps = 0.0;
+    o->ruiz_iters = 10;
+    o->restart = 30;
+    o->max_cycles = 10;
+    o->relax_pivots = 16;
+    o->relax_zeros = 0.15;
+    o->max_pivots = 64;
+}
+
+kkt_status check_options(const kkt_options& o)
+{
+    if (o.precision != KKT_FP64 && o.precision != KKT_FP32_IR) return KKT_E_ARG;
+    if (o.ordering < 0 || o.ordering > 2) return KKT_E_ARG;
+    if (o.ruiz_iters < 0 || o.ruiz_iters > 64) return KKT_E_ARG;
+    if (o.restart < 1 || o.restart > kMaxRestart) return KKT_E_ARG;
+    if (o.max_cycles < 0) return KKT_E_ARG;
+    if (o.max_pivots < 1 || o.max_pivots > 256) return KKT_E_ARG;
+    if (o.relax_pivots < 1) return KKT_E_ARG;
+    return KKT_OK;
+}
+
+AnalysisOptions to_analysis(const kkt_options& o)
+{
+    AnalysisOptions a;
+    a.ordering = o.ordering;
+    a.user_perm = o.user_perm;
+    a.relax_small = o.relax_pivots;
+    a.relax_zeros = o.relax_zeros;
+    a.max_pivots = o.max_pivots;
+    return a;
+}
+
+size_t elem_size(int precision) { return precision == KKT_FP32_IR ? 4 : 8; }
+
+constexpr size_t kSmemLimit = 220 * 1024;
+
+// Classify fronts per level and lay out the launch lists.
+void build_levels(const Analysis& an, size_t es, std::vector<LevelGroup>& levels, std::vector<int>& front_ids,
+                  std::vector<FrontTile>& tiles, int64_t& scratch_stride, int& max_panel_global)
+{
+    levels.assign(an.n_levels, LevelGroup());
+    front_ids.clear();
+    tiles.clear();
+    scratch_stride = 0;
+    max_panel_global = 0;
+    for (int l = 0; l < an.n_levels; ++l) {
+        LevelGroup& g = levels[l];
+        std::vector<int> wl, cl, pl;
+        int cmax = 0;
+        size_t psmem = 0;
+        int allmax = 0;
+        for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) {
+            int s = an.level_fronts[t];
+            int F = an.sn_front[s], w = an.sn_first[s + 1] - an.sn_first[s];
+            allmax = std::max(allmax, F);
+            if (F - w >= kPanelCbMin) {
+                pl.push_back(s);
+                psmem = std::max(psmem, (size_t)(F * w + w * (F - w)) * es);
+            } else if (F <= kWarpFrontMax) {
+                wl.push_back(s);
+            } else {
+                cl.push_back(s);
+                cmax = std::max(cmax, F);
+            }
+        }
+        g.all_off = (int)front_ids.size();
+        for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) front_ids.push_back(an.level_fronts[t]);
+        g.all_cnt = (int)(front_ids.size() - g.all_off);
+        g.all_maxF = allmax;
+        g.warp_off = (int)front_ids.size();
+        front_ids.insert(front_ids.end(), wl.begin(), wl.end());
+        g.warp_cnt = (int)wl.size();
+        g.cta_off = (int)front_ids.size();
+        front_ids.insert(front_ids.end(), cl.begin(), cl.end());
+        g.cta_cnt = (int)cl.size();
+        g.cta_maxF = cmax;
+        g.panel_off = (int)front_ids.size();
+        front_ids.insert(front_ids.end(), pl.begin(), pl.end());
+        g.panel_cnt = (int)pl.size();
+        g.panel_smem = psmem;
+        if (psmem > kSmemLimit) {
+            g.panel_global = true;
+            scratch_stride = std::max<int64_t>(scratch_stride, (int64_t)(psmem / es));
+            max_panel_global = std::max(max_panel_global, g.panel_cnt);
+        }
+        g.tile_off = (int)tiles.size();
+        for (int s : pl) {
+            int F = an.sn_front[s], w = an.sn_first[s + 1] - an.sn_first[s];
+            int m = F - w, nt = (m + kTile - 1) / kTile;
+            for (int tj = 0; tj < nt; ++tj)
+                for (int ti = 0; ti < nt; ++ti) tiles.push_back(FrontTile{s, ti, tj});
+        }
+        g.tile_cnt = (int)(tiles.size() - g.tile_off);
+    }
+    scratch_stride = (scratch_stride + 31) & ~int64_t(31);
+}
+
+template <typename T>
+DevNum<T>& num_of(kkt_ctx* c);
+template <>
+DevNum<double>& num_of<double>(kkt_ctx* c) { return c->nd; }
+template <>
+DevNum<float>& num_of<float>(kkt_ctx* c) { return c->nf; }
+
+enum KernelKind { KK_RUIZ = 0, KK_SCALE, KK_FRONT_WARP, KK_FRONT_CTA, KK_FRONT_PANEL, KK_SCHUR, KK_SOLVE_PRE,
+                  KK_SOLVE_FWD, KK_SOLVE_BWD, KK_SOLVE_POST, KK_SPMV, KK_REDUCE, KK_VECTOR, KK_COUNT };
+const char* const kKernelNames[KK_COUNT] = {
+    "ruiz_kernel", "scale_kernel", "front_warp_kernel", "front_cta_kernel", "front_panel_kernel",
+    "schur_tile_kernel", "solve_pre_kernel", "solve_fwd_kernel", "solve_bwd_kernel", "solve_post_kernel",
+    "spmv_resid_kernel", "reduction_kernels", "vector_kernels"};
+
+// Counts kernels and, in profiling mode, brackets the launch group with a
+// pair of events on the launching stream.
+struct Launch {
+    kkt_ctx* c;
+    cudaStream_t st;
+    int kind, kernels;
+    size_t slot = (size_t)-1;
+    Launch(kkt_ctx* c_, cudaStream_t st_, int kind_, int kernels_) : c(c_), st(st_), kind(kind_), kernels(kernels_)
+    {
+        c->launches += kernels;
+        if (c->profile && kernels > 0) {
+            if (c->ev_used + 2 > c->ev.size()) {
+                for (int i = 0; i < 512; ++i) {
+                    cudaEvent_t e;
+                    if (cudaEventCreate(&e) != cudaSuccess) return;
+                    c->ev.push_back(e);
+                }
+                c->ev_kind.resize(c->ev.size() / 2);
+                c->ev_count.resize(c->ev.size() / 2);
+            }
+            slot = c->ev_used / 2;
+            c->ev_used += 2;
+            c->ev_kind[slot] = kind;
+            c->ev_count[slot] = kernels;
+            cudaEventRecord(c->ev[2 * slot], st);
+        }
+    }
+    ~Launch()
+    {
+        if (slot != (size_t)-1) cudaEventRecord(c->ev[2 * slot + 1], st);
+    }
+};
+
+template <typename T>
+kkt_status refactor_t(kkt_ctx* c, const double* d_vals, cudaStream_t st)
+{
+    DevNum<T>& nm = num_of<T>(c);
+    nm.vals = d_vals;
+    KKT_CUDA(launch_zero_stat(c->stat, st));
+    double* dfin = nullptr;
+    {
+        Launch L(c, st, KK_RUIZ, 1 + c->opt.ruiz_iters);
+        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->d_a, c->d_b, c->opt.ruiz_iters, c->stat, &dfin, st));
+    }
+    c->d_final = dfin;
+    nm.d = dfin;
+    {
+        Launch L(c, st, KK_SCALE, 1);
+        KKT_CUDA(launch_scale<T>(c->sched, nm, dfin, st));
+    }
+    const int* fr = c->fronts_dev;
+    for (const LevelGroup& g : c->levels) {
+        if (g.warp_cnt) {
+            Launch L(c, st, KK_FRONT_WARP, 1);
+            KKT_CUDA(launch_fronts_warp<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, st));
+        }
+        if (g.cta_cnt) {
+            Launch L(c, st, KK_FRONT_CTA, 1);
+            KKT_CUDA(launch_fronts_cta<T>(c->sched, nm, fr + g.cta_off, g.cta_cnt, g.cta_maxF, st));
+        }
+        if (g.panel_cnt) {
+            {
+                Launch L(c, st, KK_FRONT_PANEL, 1);
+                KKT_CUDA(launch_fronts_panel<T>(c->sched, nm, fr + g.panel_off, g.panel_cnt, g.panel_smem,
+                                                g.panel_global ? reinterpret_cast<T*>(c->panel_scratch) : nullptr,
+                                                c->scratch_stride, st));
+            }
+            Launch L(c, st, KK_SCHUR, 1);
+            KKT_CUDA(launch_schur_tiles<T>(c->sched, nm, c->tiles_dev + g.tile_off, g.tile_cnt, st));
+        }
+    }
+    return KKT_OK;
+}
+
+template <typename T>
+kkt_status solve_t(kkt_ctx* c, const double* b, double* x, cudaStream_t st)
+{
+    DevNum<T>& nm = num_of<T>(c);
+    {
+        Launch L(c, st, KK_SOLVE_PRE, 1);
+        KKT_CUDA(launch_solve_pre<T>(c->sched, nm, b, st));
+    }
+    const int* fr = c->fronts_dev;
+    for (size_t l = 0; l < c->levels.size(); ++l) {
+        const LevelGroup& g = c->levels[l];
+        Launch L(c, st, KK_SOLVE_FWD, g.all_cnt ? 1 : 0);
+        KKT_CUDA(launch_solve_fwd<T>(c->sched, nm, fr + g.all_off, g.all_cnt, g.all_maxF, st));
+    }
+    for (size_t l = c->levels.size(); l-- > 0;) {
+        const LevelGroup& g = c->levels[l];
+        Launch L(c, st, KK_SOLVE_BWD, g.all_cnt ? 1 : 0);
+        KKT_CUDA(launch_solve_bwd<T>(c->sched, nm, fr + g.all_off, g.all_cnt, g.all_maxF, st));
+    }
+    {
+        Launch L(c, st, KK_SOLVE_POST, 1);
+        KKT_CUDA(launch_solve_post<T>(c->sched, nm, x, st));
+    }
+    return KKT_OK;
+}
+
+kkt_status do_refactor(kkt_ctx* c, const double* d_vals, cudaStream_t st)
+{
+    kkt_status s = c->opt.precision == KKT_FP32_IR ? refactor_t<float>(c, d_vals, st) : refactor_t<double>(c, d_vals, st);
+    if (s == KKT_OK) {
+        c->last_vals = c->kvals;
+        c->refactored = 1;
+        c->refactor_count++;
+    }
+    return s;
+}
+
+kkt_status do_solve(kkt_ctx* c, const double* b, double* x, cudaStream_t st)
+{
+    return c->opt.precision == KKT_FP32_IR ? solve_t<float>(c, b, x, st) : solve_t<double>(c, b, x, st);
+}
+
+// read back the device statistics of the last refactor into c->info
+kkt_status sync_stat(kkt_ctx* c, cudaStream_t st)
+{
+    DevStat hs;
+    KKT_CUDA(cudaMemcpyAsync(&hs, c->stat, sizeof(DevStat), cudaMemcpyDeviceToHost, st));
+    KKT_CUDA(cudaStreamSynchronize(st));
+    c->info.n_perturbed = hs.n_perturbed;
+    if (hs.numeric_bad) c->info.status = KKT_E_NUMERIC;
+    return KKT_OK;
+}
+
+double knorm_of(kkt_ctx* c, cudaStream_t st)
+{
+    unsigned long long bits = 0;
+    cudaMemcpyAsync(&bits, &c->stat->knorm_bits, sizeof(bits), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    double k;
+    std::memcpy(&k, &bits, sizeof(k));
+    return k;
+}
+
+// ||a||_inf and ||a||_2^2 on the host (synchronizes)
+kkt_status norms_host(kkt_ctx* c, const double* a, double* mx, double* sq, cudaStream_t st)
+{
+    double* out = c->red;
+    {
+        Launch L(c, st, KK_REDUCE, 2);
+        KKT_CUDA(launch_norms(c->n, a, out, st));
+    }
+    KKT_CUDA(cudaMemcpyAsync(c->pin, out, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KKT_CUDA(cudaStreamSynchronize(st));
+    *mx = c->pin[0];
+    *sq = c->pin[1];
+    return KKT_OK;
+}
+
+kkt_status do_refine(kkt_ctx* c, const double* b, double* x, double tol, kkt_info* info, cudaStream_t st)
+{
+    const int n = c->n;
+    const int m = c->opt.restart;
+    const double* K = c->last_vals;
+    const int* rp = c->sched.rowptr;
+    const int* ci = c->sched.colidx;
+    kkt_status s;
+    if ((s = do_solve(c, b, x, st)) != KKT_OK) return s;
+    double knorm = knorm_of(c, st);
+    double bmax, bsq, xmax, xsq, rmax, rsq;
+    if ((s = norms_host(c, b, &bmax, &bsq, st)) != KKT_OK) return s;
+    {
+        Launch L(c, st, KK_SPMV, 1);
+        KKT_CUDA(launch_spmv_resid(n, rp, ci, K, x, b, c->r, st));
+    }
+    if ((s = norms_host(c, c->r, &rmax, &rsq, st)) != KKT_OK) return s;
+    if ((s = norms_host(c, x, &xmax, &xsq, st)) != KKT_OK) return s;
+    auto omega_of = [&](double rm, double xm) {
+        double den = knorm * xm + bmax;
+        return den > 0 ? rm / den : rm;
+    };
+    double omega = omega_of(rmax, xmax);
+    int total = 0;
+    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
+    double* hd = c->h_dev;          // device copy of h / y (kMaxRestart + 2)
+    for (int cyc = 0; cyc < c->opt.max_cycles && omega > tol && std::isfinite(omega); ++cyc) {
+        double beta = std::sqrt(rsq);
+        if (beta == 0.0) break;
+        double target = tol * (knorm * xmax + bmax);
+        c->pin[0] = beta;
+        KKT_CUDA(cudaMemcpyAsync(hd, c->pin, sizeof(double), cudaMemcpyHostToDevice, st));
+        {
+            Launch L(c, st, KK_VECTOR, 1);
+            KKT_CUDA(launch_scal_copy(n, c->r, c->V, hd, 1, st));
+        }
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int k = 0;
+        for (int j = 0; j < m; ++j) {
+            double* vj = c->V + (int64_t)j * n;
+            double* zj = c->Z + (int64_t)j * n;
+            if ((s = do_solve(c, vj, zj, st)) != KKT_OK) return s;
+            {
+                Launch L(c, st, KK_SPMV, 1);
+                KKT_CUDA(launch_spmv(n, rp, ci, K, zj, c->w, st));
+            }
+            // classical Gram-Schmidt, twice (CGS2)
+            double* h1 = hd + 8;
+            double* h2 = hd + 8 + kMaxRestart + 2;
+            {
+                Launch L(c, st, KK_REDUCE, 2);
+                KKT_CUDA(launch_multidot(n, c->V, n, j + 1, c->w, c->red, st));
+            }
+            KKT_CUDA(cudaMemcpyAsync(h1, c->red, (j + 1) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            {
+                Launch L(c, st, KK_VECTOR, 1);
+                KKT_CUDA(launch_multiaxpy(n, c->w, c->V, n, j + 1, h1, st));
+            }
+            {
+                Launch L(c, st, KK_REDUCE, 2);
+                KKT_CUDA(launch_multidot(n, c->V, n, j + 1, c->w, c->red, st));
+            }
+            KKT_CUDA(cudaMemcpyAsync(h2, c->red, (j + 1) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            {
+                Launch L(c, st, KK_VECTOR, 1);
+                KKT_CUDA(launch_multiaxpy(n, c->w, c->V, n, j + 1, h2, st));
+            }
+            {
+                Launch L(c, st, KK_REDUCE, 2);
+                KKT_CUDA(launch_norms(n, c->w, c->red + 4096, st));
+            }
+            KKT_CUDA(cudaMemcpyAsync(c->pin, h1, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+            KKT_CUDA(cudaMemcpyAsync(c->pin + kMaxRestart + 2, h2, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
+            KKT_CUDA(cudaMemcpyAsync(c->pin + 2 * (kMaxRestart + 2), c->red + 4096, 2 * sizeof(double),
+                                     cudaMemcpyDeviceToHost, st));
+            KKT_CUDA(cudaStreamSynchronize(st));
+            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = c->pin[i] + c->pin[kMaxRestart + 2 + i];
+            double hn = std::sqrt(c->pin[2 * (kMaxRestart + 2) + 1]);
+            H[(size_t)(j + 1) * m + j] = hn;
+            if (hn > 0.0) {
+                c->pin[0] = hn;
+                KKT_CUDA(cudaMemcpyAsync(hd, c->pin, sizeof(double), cudaMemcpyHostToDevice, st));
+                Launch L(c, st, KK_VECTOR, 1);
+                KKT_CUDA(launch_scal_copy(n, c->w, c->V + (int64_t)(j + 1) * n, hd, 1, st));
+            }
+            for (int i = 0; i < j; ++i) {
+                double a = H[(size_t)i * m + j], b2 = H[(size_t)(i + 1) * m + j];
+                H[(size_t)i * m + j] = cs[i] * a + sn[i] * b2;
+                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b2;
+            }
+            double a = H[(size_t)j * m + j], b2 = H[(size_t)(j + 1) * m + j];
+            double rho = std::sqrt(a * a + b2 * b2);
+            cs[j] = rho > 0 ? a / rho : 1.0;
+            sn[j] = rho > 0 ? b2 / rho : 0.0;
+            H[(size_t)j * m + j] = rho;
+            H[(size_t)(j + 1) * m + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            k = j + 1;
+            ++total;
+            if (std::fabs(g[j + 1]) <= target || hn == 0.0 || !std::isfinite(g[j + 1])) break;
+        }
+        for (int i = k - 1; i >= 0; --i) {
+            double acc = g[i];
+            for (int t = i + 1; t < k; ++t) acc -= H[(size_t)i * m + t] * y[t];
+            y[i] = acc / H[(size_t)i * m + i];
+        }
+        for (int i = 0; i < k; ++i) c->pin[i] = y[i];
+        KKT_CUDA(cudaMemcpyAsync(hd, c->pin, k * sizeof(double), cudaMemcpyHostToDevice, st));
+        {
+            Launch L(c, st, KK_VECTOR, 1);
+            KKT_CUDA(launch_update(n, x, c->Z, n, k, hd, st));
+        }
+        {
+            Launch L(c, st, KK_SPMV, 1);
+            KKT_CUDA(launch_spmv_resid(n, rp, ci, K, x, b, c->r, st));
+        }
+        if ((s = norms_host(c, c->r, &rmax, &rsq, st)) != KKT_OK) return s;
+        if ((s = norms_host(c, x, &xmax, &xsq, st)) != KKT_OK) return s;
+        omega = omega_of(rmax, xmax);
+    }
+    if ((s = sync_stat(c, st)) != KKT_OK) return s;
+    c->info.iters = total;
+    c->info.backward_err = omega;
+    c->info.rel_resid2 = bsq > 0 ? std::sqrt(rsq / bsq) : std::sqrt(rsq);
+    if (info) *info = c->info;
+    if (!std::isfinite(omega)) return KKT_E_NUMERIC;
+    if (omega > tol) return KKT_E_NOCONV;
+    return KKT_OK;
+}
+
+}  // namespace
+
+// ======================================================================== C ABI
+
+extern "C" {
+
+void kkt_default_options(kkt_options* opt)
+{
+    if (opt) fill_defaults(opt);
+}
+
+const char* kkt_status_string(kkt_status s)
+{
+    switch (s) {
+    case KKT_OK: return "ok";
+    case KKT_E_ARG: return "invalid argument";
+    case KKT_E_CUDA: return "CUDA error";
+    case KKT_E_NOMEM: return "out of memory";
+    case KKT_E_STATE: return "call out of order";
+    case KKT_E_STRUCT: return "invalid sparsity pattern";
+    case KKT_E_NOCONV: return "refinement did not converge";
+    case KKT_E_TIMEOUT: return "device wait timed out";
+    case KKT_E_NUMERIC: return "NaN or Inf encountered";
+    }
+    return "unknown status";
+}
+
+static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_options& o, int64_t tiles, int64_t fronts,
+                          int64_t scratch)
+{
+    const int64_t es = (int64_t)elem_size(o.precision);
+    int64_t b = 0;
+    auto add = [&](int64_t x) { b += (x + 255) & ~int64_t(255); };
+    add((n + 1) * 4); add(nnz * 4); add(n * 4);
+    add((an.ns + 1) * 4); add(an.ns * 4); add((an.ns + 1) * 8); add((int64_t)an.rows.size() * 4);
+    add((an.ns + 1) * 4); add((int64_t)an.child_list.size() * 4);
+    add((an.ns + 1) * 8); add(nnz * 4); add(nnz * 4);
+    add((an.ns + 1) * 8); add((int64_t)an.rel.size() * 4);
+    add((an.ns + 1) * 8); add((an.ns + 1) * 8);
+    add(fronts * 4); add(tiles * (int64_t)sizeof(FrontTile));
+    add(sizeof(DevStat));
+    add(n * 8); add(n * 8);
+    add(nnz * es); add(an.panel_total * es); add(std::max<int64_t>(an.cb_total, 1) * es);
+    add(n * es); add(std::max<int64_t>((int64_t)an.rel.size(), 1) * es);
+    add(scratch * es);
+    add((int64_t)n * (o.restart + 1) * 8); add((int64_t)n * o.restart * 8); add(n * 8); add(n * 8);
+    add((int64_t)(kRedScratch + 4096 + 8) * 8);
+    add((int64_t)(8 + 2 * (kMaxRestart + 2)) * 8);
+    add(nnz * 8); add(nnz * 8); add(n * 8); add(n * 8);
+    return b;
+}
+
+kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx, const kkt_options* opt,
+                    kkt_plan_info* out)
+{
+    if (n <= 0 || !h_rowptr || !h_colidx || !out) return KKT_E_ARG;
+    kkt_options o;
+    if (opt) o = *opt; else fill_defaults(&o);
+    if (check_options(o) != KKT_OK) return KKT_E_ARG;
+    try {
+        Analysis an;
+        std::string err = analyze_pattern(n, h_rowptr, h_colidx, to_analysis(o), an);
+        if (!err.empty()) return (err.find("user") != std::string::npos) ? KKT_E_ARG : KKT_E_STRUCT;
+        std::vector<LevelGroup> lv;
+        std::vector<int> fids;
+        std::vector<FrontTile> tiles;
+        int64_t stride = 0;
+        int mpg = 0;
+        build_levels(an, elem_size(o.precision), lv, fids, tiles, stride, mpg);
+        std::memset(out, 0, sizeof(*out));
+        out->n = n;
+        out->nnz = an.nnz;
+        out->nnz_lu = an.nnz_l + an.nnz_u;
+        out->stored_factor = an.stored_factor;
+        out->n_fronts = an.ns;
+        out->n_levels = an.n_levels;
+        out->max_front = an.max_front;
+        out->max_pivots = an.max_pivots;
+        out->flops = an.flops;
+        out->flops_exact = an.flops_exact;
+        out->device_bytes = plan_bytes(an, n, an.nnz, o, (int64_t)tiles.size(), (int64_t)fids.size(),
+                                       stride * mpg);
+    } catch (const std::bad_alloc&) {
+        return KKT_E_NOMEM;
+    } catch (...) {
+        return KKT_E_ARG;
+    }
+    return KKT_OK;
+}
+
+kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, const int32_t* h_colidx,
+                       const double* h_vals, const kkt_options* opt, kkt_ctx** out)
+{
+    (void)h_vals;
+    if (!out || n <= 0 || !h_rowptr || !h_colidx || n_primal < 0 || n_primal > n) return KKT_E_ARG;
+    *out = nullptr;
+    kkt_ctx* c = nullptr;
+    try {
+        c = new kkt_ctx();
+    } catch (...) {
+        return KKT_E_NOMEM;
+    }
+    if (opt) c->opt = *opt; else fill_defaults(&c->opt);
+    if (check_options(c->opt) != KKT_OK) { delete c; return KKT_E_ARG; }
+    c->opt.user_perm = nullptr;
+    c->n = n;
+    c->n_primal = n_primal;
+    std::vector<int> fids;
+    std::vector<FrontTile> tiles;
+    try {
+        std::string err = analyze_pattern(n, h_rowptr, h_colidx, to_analysis(opt ? *opt : c->opt), c->an);
+        if (!err.empty()) {
+            kkt_status s = (err.find("user") != std::string::npos) ? KKT_E_ARG : KKT_E_STRUCT;
+            delete c;
+            return s;
+        }
+        build_levels(c->an, elem_size(c->opt.precision), c->levels, fids, tiles, c->scratch_stride,
+                     c->max_panel_global);
+    } catch (...) {
+        delete c;
+        return KKT_E_NOMEM;
+    }
+    static std::once_flag once;
+    static cudaError_t cfg_err = cudaSuccess;
+    std::call_once(once, [] { cfg_err = configure_kernels(); });
+    if (cfg_err != cudaSuccess) { delete c; return KKT_E_CUDA; }
+
+    const Analysis& an = c->an;
+    c->nnz = an.nnz;
+    const int64_t nnz = an.nnz;
+    const int64_t scratch = c->scratch_stride * c->max_panel_global;
+    int64_t bytes = plan_bytes(an, n, nnz, c->opt, (int64_t)tiles.size(), (int64_t)fids.size(), scratch);
+    c->device_bytes = bytes;
+    if (cudaMalloc(&c->pool.base, (size_t)bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return KKT_E_NOMEM;
+    }
+    c->pool.size = (size_t)bytes;
+    Pool& P = c->pool;
+    int* rowptr = P.take<int>(n + 1);
+    int* colidx = P.take<int>(nnz);
+    int* perm = P.take<int>(n);
+    int* sn_first = P.take<int>(an.ns + 1);
+    int* sn_front = P.take<int>(an.ns);
+    int64_t* rows_ptr = P.take<int64_t>(an.ns + 1);
+    int* rows = P.take<int>(an.rows.size());
+    int* child_ptr = P.take<int>(an.ns + 1);
+    int* child_list = P.take<int>(an.child_list.size());
+    int64_t* asm_ptr = P.take<int64_t>(an.ns + 1);
+    int* asm_pos = P.take<int>(nnz);
+    int* asm_src = P.take<int>(nnz);
+    int64_t* rel_ptr = P.take<int64_t>(an.ns + 1);
+    int* rel = P.take<int>(an.rel.size());
+    int64_t* panel_off = P.take<int64_t>(an.ns + 1);
+    int64_t* cb_off = P.take<int64_t>(an.ns + 1);
+    c->fronts_dev = P.take<int>(fids.size());
+    c->tiles_dev = P.take<FrontTile>(tiles.size());
+    c->stat = P.take<DevStat>(1);
+    c->d_a = P.take<double>(n);
+    c->d_b = P.take<double>(n);
+    const size_t es = elem_size(c->opt.precision);
+    char* sv = P.take<char>(nnz * es);
+    char* panel = P.take<char>(an.panel_total * es);
+    char* cb = P.take<char>(std::max<int64_t>(an.cb_total, 1) * es);
+    char* vec = P.take<char>(n * es);
+    char* cbv = P.take<char>(std::max<int64_t>((int64_t)an.rel.size(), 1) * es);
+    c->panel_scratch = P.take<char>(scratch * es);
+    c->V = P.take<double>((int64_t)n * (c->opt.restart + 1));
+    c->Z = P.take<double>((int64_t)n * c->opt.restart);
+    c->w = P.take<double>(n);
+    c->r = P.take<double>(n);
+    c->red = P.take<double>(kRedScratch + 4096 + 8);
+    c->h_dev = P.take<double>(8 + 2 * (kMaxRestart + 2));
+    c->kvals = P.take<double>(nnz);
+    c->stage_vals = P.take<double>(nnz);
+    c->stage_b = P.take<double>(n);
+    c->stage_x = P.take<double>(n);
+    if (P.used > P.size) { kkt_destroy(c); return KKT_E_NOMEM; }
+    if (cudaMallocHost(&c->pin, sizeof(double) * (4 * (kMaxRestart + 2) + 16)) != cudaSuccess) {
+        cudaGetLastError();
+        c->pin = nullptr;
+        kkt_destroy(c);
+        return KKT_E_NOMEM;
+    }
+    auto up = [&](void* dst, const void* src, size_t bytes_) {
+        return bytes_ ? cudaMemcpy(dst, src, bytes_, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
+    cudaError_t e = cudaSuccess;
+    e = e ? e : up(rowptr, h_rowptr, (n + 1) * 4);
+    e = e ? e : up(colidx, h_colidx, nnz * 4);
+    e = e ? e : up(perm, an.perm.data(), n * 4);
+    e = e ? e : up(sn_first, an.sn_first.data(), (an.ns + 1) * 4);
+    e = e ? e : up(sn_front, an.sn_front.data(), an.ns * 4);
+    e = e ? e : up(rows_ptr, an.rows_ptr.data(), (an.ns + 1) * 8);
+    e = e ? e : up(rows, an.rows.data(), an.rows.size() * 4);
+    e = e ? e : up(child_ptr, an.child_ptr.data(), (an.ns + 1) * 4);
+    e = e ? e : up(child_list, an.child_list.data(), an.child_list.size() * 4);
+    e = e ? e : up(asm_ptr, an.asm_ptr.data(), (an.ns + 1) * 8);
+    e = e ? e : up(asm_pos, an.asm_pos.data(), nnz * 4);
+    e = e ? e : up(asm_src, an.asm_src.data(), nnz * 4);
+    e = e ? e : up(rel_ptr, an.rel_ptr.data(), (an.ns + 1) * 8);
+    e = e ? e : up(rel, an.rel.data(), an.rel.size() * 4);
+    e = e ? e : up(panel_off, an.panel_off.data(), (an.ns + 1) * 8);
+    e = e ? e : up(cb_off, an.cb_off.data(), (an.ns + 1) * 8);
+    e = e ? e : up(c->fronts_dev, fids.data(), fids.size() * 4);
+    e = e ? e : up(c->tiles_dev, tiles.data(), tiles.size() * sizeof(FrontTile));
+    e = e ? e : cudaMemset(c->stat, 0, sizeof(DevStat));
+    if (e != cudaSuccess) { kkt_destroy(c); return KKT_E_CUDA; }
+    DevSched& s = c->sched;
+    s.n = n; s.nnz = nnz; s.ns = an.ns;
+    s.rowptr = rowptr; s.colidx = colidx; s.perm = perm;
+    s.sn_first = sn_first; s.sn_front = sn_front; s.rows_ptr = rows_ptr; s.rows = rows;
+    s.child_ptr = child_ptr; s.child_list = child_list;
+    s.asm_ptr = asm_ptr; s.asm_pos = asm_pos; s.asm_src = asm_src;
+    s.rel_ptr = rel_ptr; s.rel = rel; s.panel_off = panel_off; s.cb_off = cb_off;
+    double eps = c->opt.static_pivot_eps > 0 ? c->opt.static_pivot_eps
+                                             : (c->opt.precision == KKT_FP32_IR ? 1e-7 : 1e-14);
+    c->opt.static_pivot_eps = eps;
+    if (c->opt.precision == KKT_FP32_IR) {
+        DevNum<float>& nm = c->nf;
+        nm.sv = reinterpret_cast<float*>(sv); nm.panel = reinterpret_cast<float*>(panel);
+        nm.cb = reinterpret_cast<float*>(cb); nm.vec = reinterpret_cast<float*>(vec);
+        nm.cbv = reinterpret_cast<float*>(cbv); nm.stat = c->stat; nm.pivot_eps = eps; nm.d = c->d_a;
+        nm.kcopy = c->kvals;
+    } else {
+        DevNum<double>& nm = c->nd;
+        nm.sv = reinterpret_cast<double*>(sv); nm.panel = reinterpret_cast<double*>(panel);
+        nm.cb = reinterpret_cast<double*>(cb); nm.vec = reinterpret_cast<double*>(vec);
+        nm.cbv = reinterpret_cast<double*>(cbv); nm.stat = c->stat; nm.pivot_eps = eps; nm.d = c->d_a;
+        nm.kcopy = c->kvals;
+    }
+    c->info.status = KKT_OK;
+    *out = c;
+    return KKT_OK;
+}
+
+kkt_status kkt_refactor(kkt_ctx* c, const double* d_vals, void* stream)
+{
+    if (!c || !d_vals) return KKT_E_ARG;
+    c->info.status = KKT_OK;
+    return do_refactor(c, d_vals, (cudaStream_t)stream);
+}
+
+kkt_status kkt_solve(kkt_ctx* c, const double* d_rhs, double* d_x, void* stream)
+{
+    if (!c || !d_rhs || !d_x || d_rhs == d_x) return KKT_E_ARG;
+    if (!c->refactored) return KKT_E_STATE;
+    return do_solve(c, d_rhs, d_x, (cudaStream_t)stream);
+}
+
+kkt_status kkt_refine(kkt_ctx* c, const double* d_rhs, double* d_x, double tol, kkt_info* info, void* stream)
+{
+    if (!c || !d_rhs || !d_x || d_rhs == d_x || !(tol >= 0)) return KKT_E_ARG;
+    if (!c->refactored) return KKT_E_STATE;
+    return do_refine(c, d_rhs, d_x, tol, info, (cudaStream_t)stream);
+}
+
+kkt_status kkt_step_host(kkt_ctx* c, const double* h_vals, const double* h_rhs, double* h_x, double tol,
+                         kkt_info* info, void* stream)
+{
+    if (!c || !h_vals || !h_rhs || !h_x || !(tol >= 0)) return KKT_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    KKT_CUDA(cudaMemcpyAsync(c->stage_vals, h_vals, sizeof(double) * c->nnz, cudaMemcpyHostToDevice, st));
+    KKT_CUDA(cudaMemcpyAsync(c->stage_b, h_rhs, sizeof(double) * c->n, cudaMemcpyHostToDevice, st));
+    kkt_status s = do_refactor(c, c->stage_vals, st);
+    if (s != KKT_OK) return s;
+    kkt_status r = do_refine(c, c->stage_b, c->stage_x, tol, info, st);
+    if (r != KKT_OK && r != KKT_E_NOCONV) return r;
+    KKT_CUDA(cudaMemcpyAsync(h_x, c->stage_x, sizeof(double) * c->n, cudaMemcpyDeviceToHost, st));
+    KKT_CUDA(cudaStreamSynchronize(st));
+    return r;
+}
+
+kkt_status kkt_refactor_batched(kkt_ctx* const* ctxs, const double* const* d_vals, int count, void* stream)
+{
+    if (!ctxs || !d_vals || count < 0) return KKT_E_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i] || !d_vals[i]) return KKT_E_ARG;
+        if (ctxs[i]->opt.precision != ctxs[0]->opt.precision) return KKT_E_ARG;
+    }
+    for (int i = 0; i < count; ++i) {
+        kkt_status s = do_refactor(ctxs[i], d_vals[i], (cudaStream_t)stream);
+        if (s != KKT_OK) return s;
+    }
+    return KKT_OK;
+}
+
+kkt_status kkt_solve_batched(kkt_ctx* const* ctxs, const double* const* d_rhs, double* const* d_x, int count,
+                             void* stream)
+{
+    if (!ctxs || !d_rhs || !d_x || count < 0) return KKT_E_ARG;
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i] || !d_rhs[i] || !d_x[i]) return KKT_E_ARG;
+        if (!ctxs[i]->refactored) return KKT_E_STATE;
+    }
+    for (int i = 0; i < count; ++i) {
+        kkt_status s = do_solve(ctxs[i], d_rhs[i], d_x[i], (cudaStream_t)stream);
+        if (s != KKT_OK) return s;
+    }
+    return KKT_OK;
+}
+
+kkt_status kkt_residual(kkt_ctx* c, const double* d_rhs, const double* d_x, double* d_r, double* omega_out,
+                        void* stream)
+{
+    if (!c || !d_rhs || !d_x || !d_r) return KKT_E_ARG;
+    if (!c->refactored) return KKT_E_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    KKT_CUDA(launch_spmv_resid(c->n, c->sched.rowptr, c->sched.colidx, c->last_vals, d_x, d_rhs, d_r, st));
+    if (omega_out) {
+        double knorm = knorm_of(c, st);
+        double rm, rs, xm, xs, bm, bs;
+        kkt_status s;
+        if ((s = norms_host(c, d_r, &rm, &rs, st)) != KKT_OK) return s;
+        if ((s = norms_host(c, d_x, &xm, &xs, st)) != KKT_OK) return s;
+        if ((s = norms_host(c, d_rhs, &bm, &bs, st)) != KKT_OK) return s;
+        double den = knorm * xm + bm;
+        *omega_out = den > 0 ? rm / den : rm;
+    }
+    return KKT_OK;
+}
+
+kkt_status kkt_get_info(const kkt_ctx* c, kkt_info* info)
+{
+    if (!c || !info) return KKT_E_ARG;
+    *info = c->info;
+    info->refactor_count = c->refactor_count;
+    info->launches = c->launches;
+    if (c->refactored) {
+        DevStat hs;
+        KKT_CUDA(cudaDeviceSynchronize());
+        KKT_CUDA(cudaMemcpy(&hs, c->stat, sizeof(DevStat), cudaMemcpyDeviceToHost));
+        info->n_perturbed = hs.n_perturbed;
+        if (hs.numeric_bad) info->status = KKT_E_NUMERIC;
+    }
+    return KKT_OK;
+}
+
+int kkt_kernel_stats(kkt_ctx* c, kkt_kernel_stat* out, int max_out)
+{
+    if (!c || !out || max_out <= 0) return -1;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    double ms[KK_COUNT] = {0};
+    long long cnt[KK_COUNT] = {0};
+    for (size_t slot = 0; slot < c->ev_used / 2; ++slot) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, c->ev[2 * slot], c->ev[2 * slot + 1]) != cudaSuccess) continue;
+        ms[c->ev_kind[slot]] += t;
+        cnt[c->ev_kind[slot]] += c->ev_count[slot];
+    }
+    c->ev_used = 0;
+    int k = 0;
+    for (int i = 0; i < KK_COUNT && k < max_out; ++i) {
+        if (!cnt[i]) continue;
+        out[k].name = kKernelNames[i];
+        out[k].launches = cnt[i];
+        out[k].ms = ms[i];
+        ++k;
+    }
+    return k;
+}
+
+kkt_status kkt_set_profiling(kkt_ctx* c, int on)
+{
+    if (!c) return KKT_E_ARG;
+    c->profile = on ? 1 : 0;
+    c->ev_used = 0;
+    return KKT_OK;
+}
+
+kkt_status kkt_get_plan(const kkt_ctx* c, kkt_plan_info* out)
+{
+    if (!c || !out) return KKT_E_ARG;
+    const Analysis& an = c->an;
+    std::memset(out, 0, sizeof(*out));
+    out->n = c->n;
+    out->nnz = an.nnz;
+    out->nnz_lu = an.nnz_l + an.nnz_u;
+    out->stored_factor = an.stored_factor;
+    out->n_fronts = an.ns;
+    out->n_levels = an.n_levels;
+    out->max_front = an.max_front;
+    out->max_pivots = an.max_pivots;
+    out->flops = an.flops;
+    out->flops_exact = an.flops_exact;
+    out->device_bytes = c->device_bytes;
+    return KKT_OK;
+}
+
+kkt_status kkt_get_perm(const kkt_ctx* c, int32_t* h_perm)
+{
+    if (!c || !h_perm) return KKT_E_ARG;
+    std::memcpy(h_perm, c->an.perm.data(), sizeof(int32_t) * c->n);
+    return KKT_OK;
+}
+
+kkt_status kkt_get_scaling(const kkt_ctx* c, double* h_d)
+{
+    if (!c || !h_d) return KKT_E_ARG;
+    if (!c->refactored) return KKT_E_STATE;
+    KKT_CUDA(cudaDeviceSynchronize());
+    KKT_CUDA(cudaMemcpy(h_d, c->d_final, sizeof(double) * c->n, cudaMemcpyDeviceToHost));
+    return KKT_OK;
+}
+
+kkt_status kkt_export_factors(const kkt_ctx* c, int64_t* nl, int32_t* l_row, int32_t* l_col, double* l_val,
+                              int64_t* nu, int32_t* u_row, int32_t* u_col, double* u_val)
+{
+    if (!c || !nl || !nu) return KKT_E_ARG;
+    const Analysis& an = c->an;
+    int64_t cl = 0, cu = 0;
+    for (int s = 0; s < an.ns; ++s) {
+        int64_t w = an.sn_first[s + 1] - an.sn_first[s], F = an.sn_front[s];
+        cl += w * (w - 1) / 2 + (F - w) * w;
+        cu += w * (w + 1) / 2 + w * (F - w);
+    }
+    *nl = cl;
+    *nu = cu;
+    if (!l_row && !u_row) return KKT_OK;
+    if (!l_row || !l_col || !l_val || !u_row || !u_col || !u_val) return KKT_E_ARG;
+    if (!c->refactored) return KKT_E_STATE;
+    const size_t es = elem_size(c->opt.precision);
+    std::vector<char> host((size_t)an.panel_total * es);
+    const void* src = c->opt.precision == KKT_FP32_IR ? (const void*)c->nf.panel : (const void*)c->nd.panel;
+    KKT_CUDA(cudaDeviceSynchronize());
+    KKT_CUDA(cudaMemcpy(host.data(), src, host.size(), cudaMemcpyDeviceToHost));
+    auto val = [&](int64_t idx) -> double {
+        if (es == 4) return (double)reinterpret_cast<const float*>(host.data())[idx];
+        return reinterpret_cast<const double*>(host.data())[idx];
+    };
+    int64_t il = 0, iu = 0;
+    for (int s = 0; s < an.ns; ++s) {
+        int w = an.sn_first[s + 1] - an.sn_first[s], F = an.sn_front[s];
+        const int* R = an.rows.data() + an.rows_ptr[s];
+        int64_t off = an.panel_off[s];
+        for (int b = 0; b < w; ++b)
+            for (int a = 0; a < F; ++a) {
+                double v = val(off + a + (int64_t)b * F);
+                int r = an.perm[R[a]], col = an.perm[R[b]];
+                if (a > b) { l_row[il] = r; l_col[il] = col; l_val[il] = v; ++il; }
+                else { u_row[iu] = r; u_col[iu] = col; u_val[iu] = v; ++iu; }
+            }
+        int m = F - w;
+        for (int a = 0; a < w; ++a)
+            for (int b = 0; b < m; ++b) {
+                double v = val(off + (int64_t)F * w + (int64_t)a * m + b);
+                u_row[iu] = an.perm[R[a]]; u_col[iu] = an.perm[R[w + b]]; u_val[iu] = v; ++iu;
+            }
+    }
+    return KKT_OK;
+}
+
+kkt_status kkt_destroy(kkt_ctx* c)
+{
+    if (!c) return KKT_OK;
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->pool.base) cudaFree(c->pool.base);
+    if (c->pin) cudaFreeHost(c->pin);
+    delete c;
+    return KKT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+function include/kkt.h declares, validates its inputs, and its analysis
+agrees with the oracle's symbolic counts."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2302_08656_gb300 as K
+from paper_2302_08656_gb300 import _native
+from kktgen import KKTPattern, make_grid
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "kkt.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(kkt_[a-z_]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _native.lib()
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(_native.SIGNATURES)
+
+
+def test_status_strings_and_defaults():
+    lib = _native.lib()
+    for s in range(9):
+        assert lib.kkt_status_string(s)
+    o = _native.Options()
+    lib.kkt_default_options(C.byref(o))
+    assert o.precision == 0 and o.restart == 30 and o.ruiz_iters == 10 and o.max_cycles == 10
+
+
+def test_plan_matches_oracle_symbolic_counts():
+    """Same elimination order => same structural L+U count (integer, exact)."""
+    pat = KKTPattern(make_grid(1, 200, 300, 40))
+    q = O.min_degree(pat.rowptr, pat.colidx)
+    v = pat.values(pat.point(1, 0))
+    an = O.analyze(pat.rowptr, pat.colidx, v)
+    assert np.array_equal(an.q, q)
+    lu, _, _ = O.refactor(pat.rowptr, pat.colidx, v, an)
+    f = lu.factors()
+    info = K.plan(pat.rowptr, pat.colidx, user_perm=q)
+    assert info["nnz_lu"] == f.Lx.size + f.Ux.size
+    assert info["n"] == pat.n and info["nnz"] == pat.nnz
+    assert info["stored_factor"] >= info["nnz_lu"]
+    # the library's own ordering is a different heuristic but of the same quality class
+    own = K.plan(pat.rowptr, pat.colidx)
+    assert own["nnz_lu"] <= 1.5 * info["nnz_lu"]
+
+
+@pytest.mark.parametrize("B", [2, 3, 50])
+def test_plan_small_and_degenerate_grids(B):
+    pat = KKTPattern(make_grid(7, B, max(B - 1, 1) + (B // 3), max(1, B // 5)))
+    info = K.plan(pat.rowptr, pat.colidx)
+    assert info["n"] == pat.n and info["n_levels"] >= 1 and info["n_fronts"] >= 1
+
+
+def test_plan_rejects_bad_patterns():
+    # missing diagonal
+    rp = np.array([0, 1, 2], np.int32)
+    ci = np.array([1, 0], np.int32)
+    with pytest.raises(K.KKTError) as e:
+        K.plan(rp, ci)
+    assert e.value.status == 5
+    # unsymmetric pattern
+    rp = np.array([0, 2, 3], np.int32)
+    ci = np.array([0, 1, 1], np.int32)
+    with pytest.raises(K.KKTError) as e:
+        K.plan(rp, ci)
+    assert e.value.status == 5
+    # unsorted columns
+    rp = np.array([0, 2, 4], np.int32)
+    ci = np.array([1, 0, 0, 1], np.int32)
+    with pytest.raises(K.KKTError) as e:
+        K.plan(rp, ci)
+    assert e.value.status == 5
+    # a user permutation that is not a permutation
+    pat = KKTPattern(make_grid(1, 10, 12, 2))
+    bad = np.zeros(pat.n, np.int32)
+    with pytest.raises(K.KKTError) as e:
+        K.plan(pat.rowptr, pat.colidx, user_perm=bad)
+    assert e.value.status == 1
+    # bad options
+    with pytest.raises(K.KKTError):
+        K.plan(pat.rowptr, pat.colidx, restart=0)
+
+
+def test_one_by_one_and_diagonal_plans():
+    rp = np.array([0, 1], np.int32)
+    ci = np.array([0], np.int32)
+    info = K.plan(rp, ci)
+    assert info["n_fronts"] == 1 and info["nnz_lu"] == 1
+    n = 100
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    info = K.plan(rp, ci)
+    assert info["nnz_lu"] == n and info["n_levels"] == 1
