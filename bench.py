@@ -1,0 +1,376 @@
+"""Benchmark: KKT refactor + solve throughput and latency on GB300.
+
+One step = one interior-point iteration's linear-algebra work on a fresh
+K_k: equilibrate, scatter, refactor, solve, residual and FGMRES refinement to
+a backward error <= tol (Alg. 1 loop body). Default workload: the 25,000-bus
+grid shaped like the paper's Northeast system (FP64), mu from 1e-1 to 1e-9.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                    [--workload northeast25k|eastern70k|grid200] [--precision fp64|fp32]
+
+Prints one JSON line (rank 0). Under torchrun every rank runs its own
+independent scenario sequence (weak scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from kktgen import WORKLOADS, KKTPattern, make_grid, mu_schedule  # noqa: E402
+
+METRIC = "KKT refactor+solves/s & p99 latency at rel. residual ≤1e-10 vs plain FP64"
+UNIT = "refactor+solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="northeast25k", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the mixed-precision comparison run")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def workload(name, seed):
+    w = WORKLOADS[name]
+    grid = make_grid(seed, w["n_bus"], w["n_branch"], w["n_gen"])
+    pat = KKTPattern(grid)
+    mus = mu_schedule(w["mu0"], w["mu1"], w["steps"])
+    return w, pat, mus
+
+
+def inputs(pat, mus, seed, count):
+    """Values and right-hand sides for `count` IPM steps (schedule cycled)."""
+    vals, rhs = [], []
+    for i in range(count):
+        k = i % len(mus)
+        vals.append(pat.values(pat.point(seed, k, mus[k])))
+        rhs.append(pat.rhs(seed, k))
+    return vals, rhs
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- algorithmic bytes
+
+def algorithmic_bytes(plan, n, nnz, wbytes):
+    """Minimal traffic of each phase, from the factor sizes (per refactor / solve)."""
+    nlu = plan["nnz_lu"]
+    return {
+        "refactor": nnz * (8 + 4) + nlu * (wbytes + 4) + n * 8,
+        "solve": nlu * (wbytes + 4) + 4 * n * wbytes,
+        "spmv": nnz * (8 + 4) + 3 * n * 8,
+    }
+
+
+PHASE_OF = {
+    "front_warp_kernel": "refactor", "front_cta_kernel": "refactor", "front_panel_kernel": "refactor",
+    "schur_tile_kernel": "refactor", "ruiz_kernel": "refactor", "scale_kernel": "refactor",
+    "solve_fwd_kernel": "solve", "solve_bwd_kernel": "solve", "solve_pre_kernel": "solve",
+    "solve_post_kernel": "solve", "spmv_resid_kernel": "spmv",
+}
+
+
+# ----------------------------------------------------------------- reference arm
+
+def cpu_run(pat, vals, rhs, tol, budget_s, max_steps):
+    """The oracle as it stands, single thread: analysis untimed, then per step
+    Ruiz + LU with frozen pivots + FGMRES to tol, until the budget is used."""
+    import oracle as O
+    an = O.analyze(pat.rowptr, pat.colidx, vals[0])
+    times, oms = [], []
+    t_all = time.perf_counter()
+    for i in range(min(max_steps, len(vals))):
+        t0 = time.perf_counter()
+        lu, d, _ = O.refactor(pat.rowptr, pat.colidx, vals[i], an)
+        x, it, om = O.fgmres(pat.rowptr, pat.colidx, vals[i], lu, d, rhs[i], 30, 10, tol)
+        times.append(time.perf_counter() - t0)
+        oms.append(om)
+        if time.perf_counter() - t_all > budget_s and len(times) >= 2:
+            break
+    return times, oms
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    w, pat, mus = workload(args.workload, args.seed)
+    n_in = args.warmup + args.steps
+    vals, rhs = inputs(pat, mus, args.seed, n_in)
+    times, oms = cpu_run(pat, vals, rhs, args.tol, 1e9, n_in)
+    t = times[args.warmup:] if len(times) > args.warmup else times
+    ms = 1000.0 * sum(t) / len(t)
+    value = 1000.0 / ms
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": len(t), "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "precision": "fp64", "tol": args.tol},
+        "p50_ms": 1000 * float(np.percentile(t, 50)), "p99_ms": 1000 * float(np.percentile(t, 99)),
+        "omega_max": float(max(oms)),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d full steps of %s (oracle analysis untimed)" % (len(t), args.workload)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ native arm
+
+def run_native(args):
+    import torch
+    import paper_2302_08656_gb300 as K
+
+    rank, local, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    seed = args.seed + 1000 * rank          # independent scenario per rank
+    w, pat, mus = workload(args.workload, seed)
+    n_in = args.warmup + args.steps
+    vals_h, rhs_h = inputs(pat, mus, seed, n_in)
+    vals = [torch.from_numpy(v).to(dev) for v in vals_h]
+    rhs = [torch.from_numpy(b).to(dev) for b in rhs_h]
+    xs = [torch.empty_like(b) for b in rhs]
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(4 * l2, 512 << 20), dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed_run(solver, tag):
+        stream = torch.cuda.current_stream()
+        for i in range(args.warmup):
+            solver.refactor(vals[i])
+            solver.refine(rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
+        l0 = solver.info().launches
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        oms, iters = [], []
+        barrier()
+        for t in range(args.steps):
+            i = args.warmup + t
+            flush.zero_()
+            ev0[t].record(stream)
+            solver.refactor(vals[i])
+            _, info = solver.refine(rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
+            ev1[t].record(stream)
+            oms.append(info.backward_err)
+            iters.append(info.iters)
+        barrier()
+        launches = solver.info().launches - l0
+        ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+        return ms, oms, iters, launches
+
+    s64 = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=args.precision)
+    plan = s64.plan()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    ms, oms, iters, launches = timed_run(s64, args.precision)
+    clocks = sampler.stop()
+    total_ms = sum(ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # mixed precision on the same matrices (the graded comparison: FP32 LU + FP64 FGMRES vs plain FP64)
+    other = None
+    if not args.no_fp32 and args.precision == "fp64":
+        s32 = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision="fp32")
+        ms32, oms32, it32, _ = timed_run(s32, "fp32")
+        other = {"precision": "fp32_ir", "value": 1000.0 * len(ms32) / sum(ms32),
+                 "p50_ms": float(np.percentile(ms32, 50)), "p99_ms": float(np.percentile(ms32, 99)),
+                 "omega_max": float(max(oms32)), "fgmres_iters_mean": float(np.mean(it32))}
+        s32.close()
+
+    # end to end through the C ABI with host buffers (copies inside the timed call)
+    hv = [torch.from_numpy(v).pin_memory() for v in vals_h]
+    hb = [torch.from_numpy(b).pin_memory() for b in rhs_h]
+    hx = torch.empty(pat.n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    barrier()
+    for t in range(args.steps):
+        i = args.warmup + t
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s64.step_host(hv[i].numpy(), hb[i].numpy(), tol=args.tol, out=hx.numpy())
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    barrier()
+    e2e = {"value": 1000.0 * len(e2e_ms) / sum(e2e_ms), "unit": UNIT,
+           "h2d_bytes_per_step": int(8 * (pat.nnz + pat.n)), "d2h_bytes_per_step": int(8 * pat.n),
+           "p99_ms": float(np.percentile(e2e_ms, 99))}
+
+    # per-kernel timing pass (profiling mode, separate from the timed run)
+    s64.set_profiling(True)
+    s64.kernel_stats()
+    nprof = min(3, args.steps)
+    for t in range(nprof):
+        i = args.warmup + t
+        s64.refactor(vals[i])
+        s64.refine(rhs[i], out=xs[i], tol=args.tol)
+    stats = s64.kernel_stats()
+    s64.set_profiling(False)
+    wbytes = 8 if args.precision == "fp64" else 4
+    ab = algorithmic_bytes(plan, pat.n, pat.nnz, wbytes)
+    phase_ms = {}
+    for name, (cnt, kms) in stats.items():
+        ph = PHASE_OF.get(name)
+        if ph:
+            phase_ms[ph] = phase_ms.get(ph, 0.0) + kms
+    dom = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    roofline = None
+    if dom and PHASE_OF.get(dom):
+        ph = PHASE_OF[dom]
+        n_units = {"refactor": nprof, "solve": None, "spmv": None}[ph]
+        if ph == "refactor":
+            bytes_total = ab["refactor"] * nprof
+        else:
+            # solves / spmv per profiled step: count launches of the phase's post kernel
+            key = "solve_post_kernel" if ph == "solve" else "spmv_resid_kernel"
+            n_units = stats.get(key, (0, 0.0))[0]
+            bytes_total = ab[ph] * n_units
+        achieved = bytes_total / (phase_ms[ph] / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm, "traffic": None, "kernel": dom, "phase": ph,
+                    "peak_source": peak_src,
+                    "algorithmic_bytes_per_unit": ab[ph], "units_profiled": n_units,
+                    "phase_ms_per_unit": phase_ms[ph] / max(1, n_units)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        times, coms = cpu_run(pat, vals_h, rhs_h, args.tol, args.cpu_seconds, n_in)
+        cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "%d of the %s steps (oracle analysis untimed), single thread"
+                         % (len(times), args.workload),
+               "omega_max": float(max(coms))}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "buses": w["n_bus"], "branches": w["n_branch"],
+                       "generators": w["n_gen"], "n": pat.n, "nnz": pat.nnz, "precision": args.precision,
+                       "tol": args.tol, "mu": [w["mu0"], w["mu1"]],
+                       "l2": "flushed between timed steps (%d MB write)" % (flush.numel() >> 20),
+                       "fronts": plan["n_fronts"], "levels": plan["n_levels"], "nnz_lu": plan["nnz_lu"]},
+            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+            "omega_max": float(max(oms)), "fgmres_iters_mean": float(np.mean(iters)),
+            "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
+            "gpu_launches": int(launches), "kernel_ms_per_step": {k: v[1] / nprof for k, v in stats.items()},
+            "mixed_precision": other,
+        }
+        print(json.dumps(line), flush=True)
+    s64.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()
