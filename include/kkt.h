@@ -187,6 +187,27 @@ kkt_status kkt_residual(kkt_ctx *ctx, const double *d_rhs, const double *d_x, do
  * perturbation count and NaN/Inf flag of the last refactor. */
 kkt_status kkt_get_info(const kkt_ctx *ctx, kkt_info *info);
 
+/* Residual and backward error without allocating anything (the paper has no
+ * counterpart; this is a service for callers that cannot allocate device
+ * memory: a host framework that owns all device memory through its own pool,
+ * a serving loop held to a fixed memory budget, or a check of a solution made
+ * before any kkt_ctx exists). No context is needed: K is given directly as
+ * device CSR (d_rowptr n+1, d_colidx and d_vals nnz, FP64), with d_x, d_rhs
+ * (n each) as inputs. Outputs: d_r = b - K x (n, device) and d_omega[0] =
+ * ||r||_inf / (||K||_inf ||x||_inf + ||b||_inf) (one double, device).
+ * The reduction scratch is a fixed 256 KiB array in device memory that the
+ * library declares statically; every GPU that loads the library holds it
+ * until the process exits. Limit: n <= 8,388,608 rows, else KKT_E_ARG. The
+ * first call on a device looks up that array's device address (once per
+ * device, with the device current); make that first call before any stream
+ * capture. Every call uses the same array, so calls that overlap on the GPU
+ * (on different streams, or from several threads) race and must be ordered
+ * by the caller. Asynchronous on `stream`.
+ * Errors: KKT_E_ARG (null pointer, n <= 0, n above the limit), KKT_E_CUDA. */
+kkt_status kkt_backward_error_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_colidx,
+                                      const double *d_vals, const double *d_x, const double *d_rhs,
+                                      double *d_r, double *d_omega, void *stream);
+
 /* Profiling mode: when on, every launch group is bracketed by a pair of CUDA
  * events on its stream (adds a little host overhead). */
 kkt_status kkt_set_profiling(kkt_ctx *ctx, int on);

@@ -197,6 +197,14 @@ class KKTSolver:
         return lr, lc, lv, ur, uc, uv
 
 
+def backward_error_noalloc(rowptr, colidx, vals, x, rhs, r, omega, stream=None):
+    """r = b - K x and omega into caller-provided device tensors, allocating
+    nothing (rowptr / colidx int32 and vals float64 on the device)."""
+    n = rowptr.numel() - 1
+    _check(lib().kkt_backward_error_noalloc(n, _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(x), _ptr(rhs),
+                                            _ptr(r), _ptr(omega), _stream(stream)), "kkt_backward_error_noalloc")
+
+
 def _ptr_array(items):
     arr = (C.c_void_p * len(items))(*[C.c_void_p(x) for x in items])
     return arr

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libkkt_gb300.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["analysis.cpp", "kernels.cu", "kkt_capi.cu"]
+SOURCES = ["analysis.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu"]
 HEADERS = ["analysis.hpp", "kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -134,6 +134,7 @@ SIGNATURES = {
     "kkt_get_perm": (C.c_int, [_P, _P]),
     "kkt_get_scaling": (C.c_int, [_P, _P]),
     "kkt_export_factors": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, C.POINTER(C.c_int64), _P, _P, _P]),
+    "kkt_backward_error_noalloc": (C.c_int, [C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "kkt_destroy": (C.c_int, [_P]),
     "kkt_status_string": (C.c_char_p, [C.c_int]),
 }

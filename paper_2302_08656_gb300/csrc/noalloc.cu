@@ -1,0 +1,135 @@
+// Allocation-free residual and backward error (kkt_backward_error_noalloc).
+//
+// Some callers cannot allocate device memory at the point where they need a
+// residual check: a solver embedded in a host framework that owns every byte
+// of device memory through its own pool (and forbids foreign allocations), a
+// serving loop that must stay inside a fixed memory budget, or code that wants
+// to check a solution before any kkt_ctx (and so before any workspace) exists.
+// This entry point computes r = b - K x and the normwise backward error
+// omega = ||r||_inf / (||K||_inf ||x||_inf + ||b||_inf) with no allocation at
+// all: its reduction scratch is a fixed array in device global memory that the
+// library declares at file scope, so every GPU that loads the library holds it
+// (kNoallocSlots * 4 doubles = 256 KiB) until the process exits.
+#include "../../include/kkt.h"
+
+#include <cuda_runtime.h>
+
+#include <math.h>
+#include <mutex>
+
+namespace {
+
+constexpr int kRowsPerBlock = 1024;          // 8 warps x 128 rows
+constexpr int kNoallocSlots = 8192;          // partial-result slots (one per block)
+constexpr int64_t kNoallocMaxRows = (int64_t)kRowsPerBlock * kNoallocSlots;   // 8,388,608
+
+// Shared by every call on a device; each call overwrites the slots it uses.
+static __device__ __align__(256) double g_noalloc_scratch[kNoallocSlots * 4];
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double wmax(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ double wsum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Pass 1: one warp per row computes r_i = b_i - sum_j k_ij x_j (lanes stride
+// the row, butterfly sum) and the row's |K| sum; every block writes the maxima
+// of |r|, |x|, |b| and the K row sums over its rows into its own slot.
+__global__ void __launch_bounds__(256) resid_partial_kernel(int n, const int* __restrict__ rp,
+                                                            const int* __restrict__ ci,
+                                                            const double* __restrict__ v,
+                                                            const double* __restrict__ x,
+                                                            const double* __restrict__ b,
+                                                            double* __restrict__ r, double* scratch)
+{
+    __shared__ double red[4][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int row0 = blockIdx.x * kRowsPerBlock;
+    const int row1 = min(n, row0 + kRowsPerBlock);
+    double mr = 0.0, mx = 0.0, mb = 0.0, mk = 0.0;
+    for (int row = row0 + wid; row < row1; row += 8) {
+        double s = 0.0, a = 0.0;
+        for (int p = rp[row] + lane; p < rp[row + 1]; p += 32) {
+            s += v[p] * x[ci[p]];
+            a += fabs(v[p]);
+        }
+        s = wsum(s);
+        a = wsum(a);
+        const double ri = b[row] - s;
+        if (lane == 0) r[row] = ri;
+        mr = fmax(mr, fabs(ri));
+        mx = fmax(mx, fabs(x[row]));
+        mb = fmax(mb, fabs(b[row]));
+        mk = fmax(mk, a);
+    }
+    if (lane == 0) { red[0][wid] = mr; red[1][wid] = mx; red[2][wid] = mb; red[3][wid] = mk; }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double m = 0.0;
+        for (int q = 0; q < 8; ++q) m = fmax(m, red[threadIdx.x][q]);
+        scratch[(int64_t)blockIdx.x * 4 + threadIdx.x] = m;
+    }
+}
+
+// Pass 2: one warp reduces the slots written by pass 1 and forms omega.
+__global__ void omega_final_kernel(int nblk, const double* scratch, double* __restrict__ omega)
+{
+    double mr = 0.0, mx = 0.0, mb = 0.0, mk = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += 32) {
+        mr = fmax(mr, scratch[4 * i + 0]);
+        mx = fmax(mx, scratch[4 * i + 1]);
+        mb = fmax(mb, scratch[4 * i + 2]);
+        mk = fmax(mk, scratch[4 * i + 3]);
+    }
+    mr = wmax(mr); mx = wmax(mx); mb = wmax(mb); mk = wmax(mk);
+    if (threadIdx.x == 0) {
+        const double den = mk * mx + mb;
+        omega[0] = den > 0.0 ? mr / den : mr;
+    }
+}
+
+// Device address of the scratch array, looked up once per device.
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+double* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+cudaError_t scratch_for_current_device(double** out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_scratch_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" kkt_status kkt_backward_error_noalloc(int32_t n, const int32_t* d_rowptr, const int32_t* d_colidx,
+                                                 const double* d_vals, const double* d_x, const double* d_rhs,
+                                                 double* d_r, double* d_omega, void* stream)
+{
+    if (n <= 0 || !d_rowptr || !d_colidx || !d_vals || !d_x || !d_rhs || !d_r || !d_omega) return KKT_E_ARG;
+    if ((int64_t)n > kNoallocMaxRows) return KKT_E_ARG;   // more rows than the fixed scratch can reduce
+    double* scratch = nullptr;
+    if (scratch_for_current_device(&scratch) != cudaSuccess) return KKT_E_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nblk = (int)(((int64_t)n + kRowsPerBlock - 1) / kRowsPerBlock);
+    resid_partial_kernel<<<nblk, 256, 0, st>>>(n, d_rowptr, d_colidx, d_vals, d_x, d_rhs, d_r, scratch);
+    omega_final_kernel<<<1, 32, 0, st>>>(nblk, scratch, d_omega);
+    return cudaGetLastError() == cudaSuccess ? KKT_OK : KKT_E_CUDA;
+}
