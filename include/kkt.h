@@ -10,15 +10,13 @@
  *                 fill-reducing ordering, frozen pivot sequence, symbolic
  *                 factorization, supernodal assembly tree and its level
  *                 schedule; uploaded to the GPU once (Alg. 1 setup).
- *   kkt_refactor  per K_k, on the GPU: equilibrate, scatter the new values
- *                 into the frozen factor pattern (Alg. 1 "update
- *                 factorization object using new values") and refactor
- *                 without pivoting (Alg. 1 "refactor").
- *   kkt_solve     triangular solves with the current factors (Alg. 1
- *                 "perform triangular solve").
+ *   kkt_refactor  per K_k, on the GPU: equilibrate, load the new values
+ *                 into the frozen factor pattern and refactor without
+ *                 pivoting (Alg. 1).
+ *   kkt_solve     triangular solves with the current factors (Alg. 1).
  *   kkt_refine    solve followed by iterative refinement to a backward-error
- *                 tolerance (Alg. 1 "always followed by iterative
- *                 refinement"; Sec. V asks for a better refinement: FGMRES).
+ *                 tolerance (Alg. 1 refines every solve; Sec. V calls for a
+ *                 better refinement: FGMRES here).
  *
  * Conventions
  *   - Matrices are full symmetric CSR (both triangles), 0-based int32 row
@@ -124,7 +122,7 @@ void kkt_default_options(kkt_options *opt);
 kkt_status kkt_plan(int32_t n, const int32_t *h_rowptr, const int32_t *h_colidx,
                     const kkt_options *opt, kkt_plan_info *out);
 
-/* Analysis stage (Sec. II stage i; Alg. 1 steps 1-4). n_primal is the size
+/* Analysis stage (Sec. II, first of the three stages; Alg. 1 setup). n_primal is the size
  * of the (1,1) block (used only for reporting). The pattern arrays are read
  * and copied; h_vals is not needed by the static-pivot analysis and may be
  * NULL. Allocates every device buffer the context will use, on the current
@@ -135,7 +133,7 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t *h_rowptr,
                        const int32_t *h_colidx, const double *h_vals,
                        const kkt_options *opt, kkt_ctx **out);
 
-/* Numeric refactorization (Alg. 1 steps 6-7) of the matrix with values
+/* Numeric refactorization (Alg. 1) of the matrix with values
  * d_vals (device, nnz FP64 in the CSR order given to kkt_analyze):
  * power-of-two symmetric Ruiz equilibration D K D (FP64), scatter into the
  * frozen pattern, multifrontal LU without pivoting of P (D K D) P^T with
@@ -144,7 +142,7 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t *h_rowptr,
  * Errors: KKT_E_ARG, KKT_E_CUDA. */
 kkt_status kkt_refactor(kkt_ctx *ctx, const double *d_vals, void *stream);
 
-/* x = K^{-1} b with the current factors (Alg. 1 step 8, no refinement):
+/* x = K^{-1} b with the current factors (Alg. 1, without refinement):
  * x = D P^T U^{-1} L^{-1} P D b. d_rhs and d_x are device FP64 vectors of
  * length n and may not alias. Asynchronous.
  * Errors: KKT_E_ARG, KKT_E_STATE (no refactor yet), KKT_E_CUDA. */
@@ -152,7 +150,7 @@ kkt_status kkt_solve(kkt_ctx *ctx, const double *d_rhs, double *d_x, void *strea
 
 /* Solve then refine with restarted FGMRES(m) on the unscaled K, right
  * preconditioned by the factors, Arnoldi and update in FP64, until the
- * backward error omega <= tol (Alg. 1 step 8 with refinement; Sec. V).
+ * backward error omega <= tol (Alg. 1 with refinement; Sec. V).
  * Synchronizes `stream` (the restart loop reads convergence on the host).
  * info (may be NULL) receives iterations and the final omega.
  * Errors: KKT_E_ARG, KKT_E_STATE, KKT_E_CUDA, KKT_E_NOCONV, KKT_E_NUMERIC. */

@@ -4,8 +4,8 @@ The paper evaluates on the TAMU synthetic Northeast (25,000 buses, 32,230
 branches, 4,834 generators) and Eastern (70,000 buses, 88,270 branches,
 10,390 generators) grids (Table I). Those data sets are not available here, so
 this module draws grids with the same bus / branch / generator counts and the
-sparse, irregular, nearly planar connectivity the paper describes (Sec. II,
-"very sparse with an irregular non-zero pattern").
+sparse, irregular, nearly planar connectivity the paper describes for these
+KKT matrices (Sec. II).
 
 Recipe (the paper is silent on every constant; these are the readings used):
 

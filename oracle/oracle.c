@@ -11,23 +11,24 @@
  * Every routine is written for a reader to check against the paper by eye:
  * no blocking, no fusion, no parallelism, single thread, double precision.
  *
- *   ora_ruiz         equilibration (Sec. II: "the system is equilibrated");
- *                    reading: symmetric Ruiz iterations rounded to powers of 2
- *   ora_min_degree   fill-reducing ordering (Sec. II: "column and row
- *                    permutations are set"); reading: exact minimum degree on
+ *   ora_ruiz         equilibration, the first task of the analysis stage
+ *                    (Sec. II); reading: symmetric Ruiz iterations rounded to
+ *                    powers of 2
+ *   ora_min_degree   fill-reducing ordering, part of the analysis stage
+ *                    (Sec. II); reading: exact minimum degree on
  *                    the explicit elimination graph, ties to the lowest index
- *   ora_lu           left-looking LU of P*A*Q (Alg. 1 "use KLU to solve" for
- *                    the first system, Alg. 1 "refactor" for the later ones):
+ *   ora_lu           left-looking LU of P*A*Q (Alg. 1: a pivoting LU of the
+ *                    first system, then refactorizations of the later ones):
  *                    with p_in == NULL the row order is chosen by threshold
  *                    partial pivoting with diagonal preference; with p_in given
  *                    the pivot sequence is frozen and tiny pivots are replaced
  *                    by static perturbation (reading after Li & Demmel's
  *                    static pivoting)
- *   ora_solve        triangular solves (Alg. 1 "perform triangular solve")
+ *   ora_solve        forward and backward substitution (Alg. 1)
  *   ora_spmv_resid   r = b - K x
  *   ora_backward_error   normwise backward error of x
- *   ora_fgmres       iterative refinement (Alg. 1 "always followed by
- *                    iterative refinement"; Sec. V asks for a better one):
+ *   ora_fgmres       iterative refinement after every solve (Alg. 1; Sec. V
+ *                    calls for a better refinement than the library one):
  *                    restarted FGMRES(m), modified Gram-Schmidt, Givens,
  *                    right-preconditioned by the LU solve
  *
