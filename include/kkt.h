@@ -77,7 +77,10 @@ typedef struct {
     int relax_pivots;           /* supernode amalgamation: max pivots of a merged front
                                    for the "small front" rule (default 16) */
     double relax_zeros;         /* amalgamation: max share of explicit zeros (default 0.15) */
-    int max_pivots;             /* amalgamation: max pivots per supernode (default 64) */
+    int max_pivots;             /* pivots per supernode: merges stop and larger supernodes
+                                   are split into chains at this size (default 64, max 64) */
+    int no_graphs;              /* 1: launch every kernel from the host instead of replaying
+                                   the captured CUDA graphs of the level loops (default 0) */
 } kkt_options;
 
 typedef struct {

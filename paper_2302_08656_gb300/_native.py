@@ -79,6 +79,7 @@ class Options(C.Structure):
         ("relax_pivots", C.c_int),
         ("relax_zeros", C.c_double),
         ("max_pivots", C.c_int),
+        ("no_graphs", C.c_int),
     ]
 
 

@@ -274,21 +274,35 @@ std::string analyze_pattern(int n, const int* rowptr, const int* colidx,
             Cn.alive = false;
         }
     }
-    // ---- renumber surviving supernodes in column order (a postorder)
-    std::vector<int> alive_ids;
-    for (size_t s = 0; s < sn.size(); ++s) if (sn[s].alive) alive_ids.push_back((int)s);
-    std::sort(alive_ids.begin(), alive_ids.end(), [&](int a, int b) { return sn[a].first < sn[b].first; });
-    std::vector<int> newid(sn.size(), -1);
-    for (size_t k = 0; k < alive_ids.size(); ++k) newid[alive_ids[k]] = (int)k;
-    const int ns = (int)alive_ids.size();
+    // ---- split supernodes with more than max_pivots pivots into a chain of
+    // pieces. The last column of every supernode is an elimination-tree
+    // ancestor of all its columns, so a piece's contribution rows are rows of
+    // the next piece and the split needs no new structure.
+    std::vector<std::pair<int, int>> ranges;   // (first, last) in column order
+    for (size_t k = 0; k < sn.size(); ++k)
+        if (sn[k].alive) ranges.push_back({sn[k].first, sn[k].last});
+    std::sort(ranges.begin(), ranges.end());
+    {
+        std::vector<std::pair<int, int>> split;
+        const int cap = std::max(1, opt.max_pivots);
+        for (const auto& r : ranges) {
+            for (int f = r.first; f <= r.second; f += cap)
+                split.push_back({f, std::min(r.second, f + cap - 1)});
+        }
+        ranges.swap(split);
+    }
+    const int ns = (int)ranges.size();
     out.ns = ns;
     out.sn_first.assign(ns + 1, n);
     out.sn_parent.assign(ns, -1);
     out.sn_front.assign(ns, 0);
     for (int k = 0; k < ns; ++k) {
-        const SN& s = sn[alive_ids[k]];
-        out.sn_first[k] = s.first;
-        out.sn_parent[k] = s.parent >= 0 ? newid[s.parent] : -1;
+        out.sn_first[k] = ranges[k].first;
+        for (int j = ranges[k].first; j <= ranges[k].second; ++j) sn_of[j] = k;
+    }
+    for (int k = 0; k < ns; ++k) {
+        int pj = par[ranges[k].second];
+        out.sn_parent[k] = pj >= 0 ? sn_of[pj] : -1;
     }
     // row sets: pivots, then the union of the pivot columns' structures below the last pivot
     out.rows_ptr.assign(ns + 1, 0);
@@ -370,6 +384,7 @@ std::string analyze_pattern(int n, const int* rowptr, const int* colidx,
         out.rel_ptr[k + 1] = out.rel_ptr[k] + (out.sn_front[k] - w);
     }
     out.rel.assign(out.rel_ptr[ns], 0);
+    out.cb_split.assign(ns, 0);
     for (int k = 0; k < ns; ++k) {
         int w = out.sn_first[k + 1] - out.sn_first[k];
         int F = out.sn_front[k];
@@ -382,6 +397,7 @@ std::string analyze_pattern(int n, const int* rowptr, const int* colidx,
             int pos = find_pos(Rp, out.sn_front[pk], R[t]);
             if (pos < 0) return "internal: contribution row missing from the parent front";
             out.rel[out.rel_ptr[k] + (t - w)] = pos;
+            if (pos < out.sn_first[pk + 1] - out.sn_first[pk]) out.cb_split[k] = t - w + 1;
         }
     }
     // storage and statistics

@@ -34,6 +34,9 @@ struct Analysis {
     // relative indices: CB row t of front s sits at row rel[rel_ptr[s] + t] of its parent front
     std::vector<int64_t> rel_ptr;
     std::vector<int> rel;
+    // rel is increasing, so a contribution block's rows that land on pivots of
+    // the parent come first: cb_split[s] of them
+    std::vector<int> cb_split;
     // factor panel (F*w + w*(F-w) values) and contribution block ((F-w)^2) offsets
     std::vector<int64_t> panel_off, cb_off;
     int64_t panel_total = 0, cb_total = 0;

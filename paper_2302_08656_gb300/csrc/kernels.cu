@@ -33,6 +33,28 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* a, double 
     atomicMax(a, (unsigned long long)__double_as_longlong(v));
 }
 
+// Exact power-of-two arithmetic on IEEE bit patterns (integer pipes only; the
+// FP64 pipe of this GPU issues one warp instruction per 16 cycles).
+// scale2(x, e) = x * 2^e for a non-negative finite x; exact. Zero stays zero;
+// results that would leave the normal range, and subnormal inputs, take the
+// multiply.
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ int exp_of_pow2(double d)               // d = 2^k exactly
+{
+    return (int)((__double_as_longlong(d) >> 52) & 0x7ff) - 1023;
+}
+__device__ __forceinline__ unsigned long long scale2_bits(unsigned long long xb, int e)
+{
+    if (xb == 0ull) return 0ull;
+    const int E = (int)(xb >> 52);                                 // biased exponent (sign bit is clear)
+    const int En = E + e;
+    if (E >= 1 && E <= 2046 && En >= 1 && En <= 2046) return xb + ((unsigned long long)(long long)e << 52);
+    return (unsigned long long)__double_as_longlong(__longlong_as_double((long long)xb) * ldexp(1.0, e));
+}
+
 // 2^round(-log2(r)/2) with halves rounded up, r > 0, decided on the binary
 // exponent only: r = m 2^e, m in [1/2, 1).
 //   m == 1/2  : log2 r = e - 1 exactly         -> floor((2 - e) / 2)
@@ -51,6 +73,21 @@ __device__ __forceinline__ double pow2_inv_sqrt(double r)
         k = -(e / 2);
     }
     return ldexp(1.0, k);
+}
+
+// Exponent k of pow2_inv_sqrt(r) from the bits of a positive normal r:
+// r = (0.5 + M / 2^53) * 2^(E - 1022).
+__device__ __forceinline__ int pow2_inv_sqrt_exp(unsigned long long rb)
+{
+    const int E = (int)(rb >> 52);
+    if (E == 0) return exp_of_pow2(pow2_inv_sqrt(__longlong_as_double((long long)rb)));   // subnormal
+    const int e = E - 1022;
+    const bool half = (rb & 0x000fffffffffffffull) == 0ull;       // m == 1/2
+    if (half) {
+        const int t = 2 - e;
+        return t >= 0 ? t / 2 : -((1 - t) / 2);
+    }
+    return (e & 1) ? (1 - e) / 2 : -(e / 2);
 }
 
 template <typename T>
@@ -76,89 +113,172 @@ __global__ void fill_kernel(int n, double* a, double v)
     if (i < n) a[i] = v;
 }
 
-// One Ruiz iteration, one warp per row: r_i = max_j |d_i k_ij d_j|,
-// d_i <- d_i 2^round(-log2(r_i)/2). An iteration after one that changed
-// nothing only copies d (the fixed point is reached).
-__global__ void ruiz_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                            const double* __restrict__ v, const double* __restrict__ din,
-                            double* __restrict__ dout, const int* changed_prev, int* changed_cur)
+// One Ruiz iteration, eight lanes per row (rows average ~10 entries):
+// r_i = max_j |d_i k_ij d_j|, d_i <- d_i 2^round(-log2(r_i)/2). An iteration
+// after one that changed nothing only copies d (the fixed point is reached).
+constexpr int kRowLanes = 8;
+
+__device__ __forceinline__ double group_max(double v)
 {
-    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (row >= n) return;
-    double di = din[row];
-    if (changed_prev && *changed_prev == 0) {
-        if (lane == 0) dout[row] = di;
-        return;
+    for (int o = kRowLanes / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+__device__ __forceinline__ double group_sum(double v)
+{
+    for (int o = kRowLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long group_max_u64(unsigned long long v)
+{
+    for (int o = kRowLanes / 2; o > 0; o >>= 1) {
+        const unsigned long long u = __shfl_xor_sync(kFull, v, o);
+        v = u > v ? u : v;
     }
-    double m = 0.0;
-    for (int p = rp[row] + lane; p < rp[row + 1]; p += 32) m = fmax(m, fabs(di * v[p] * din[ci[p]]));
-    m = warp_max(m);
-    if (lane == 0) {
-        double f = m > 0.0 ? pow2_inv_sqrt(m) : 1.0;
-        dout[row] = di * f;
-        if (f != 1.0) *changed_cur = 1;
+    return v;
+}
+
+// Integer-only iteration: every d is a power of two, so |d_i k_ij d_j| is
+// |k_ij| with its exponent raised by e_i + e_j, and the row maximum of
+// non-negative doubles is the maximum of their bit patterns.
+__global__ void __launch_bounds__(256) ruiz_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                   const double* __restrict__ v, const double* __restrict__ din,
+                                                   double* __restrict__ dout, const int* changed_prev,
+                                                   int* changed_cur)
+{
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = changed_prev ? (*changed_prev == 0) : 0;   // one read per block
+    __syncthreads();
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
+    const int sub = threadIdx.x % kRowLanes;
+    const bool skip = s_skip != 0;                 // uniform over the block
+    int changed = 0;
+    double di = 0.0;
+    unsigned long long m = 0ull;
+    if (row < n) {
+        di = din[row];
+        if (!skip) {
+            const int ei = exp_of_pow2(di);
+            for (int p = rp[row] + sub; p < rp[row + 1]; p += kRowLanes) {
+                const unsigned long long a = scale2_bits(abs_bits(v[p]), ei + exp_of_pow2(din[ci[p]]));
+                m = a > m ? a : m;
+            }
+        }
     }
+    if (!skip) m = group_max_u64(m);               // every lane of the warp takes part
+    if (row < n) {
+        if (skip) {
+            if (sub == 0) dout[row] = di;
+        } else {
+            const int k = m ? pow2_inv_sqrt_exp(m) : 0;
+            if (sub == 0) dout[row] = __longlong_as_double((long long)scale2_bits(abs_bits(di), k));
+            changed = k != 0;
+        }
+    }
+    // one flag write per block (a write per row would serialise on one address)
+    if (__syncthreads_or(changed) && threadIdx.x == 0) *changed_cur = 1;
 }
 
 // D K D in factor precision, a copy of K for the residuals, max |D K D|
 // (static-pivot reference) and ||K||_inf.
 template <typename T>
-__global__ void scale_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                             const double* __restrict__ v, const double* __restrict__ d,
-                             T* __restrict__ sv, double* __restrict__ kcopy, DevStat* stat)
+__global__ void __launch_bounds__(256) scale_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                                    const double* __restrict__ v, const double* __restrict__ d,
+                                                    T* __restrict__ sv, double* __restrict__ kcopy, DevStat* stat)
 {
-    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
+    const int sub = threadIdx.x % kRowLanes;
+    const int lane = threadIdx.x & 31;
     double amax = 0.0, rsum = 0.0;
+    unsigned long long amb = 0ull;
     if (row < n) {
-        double di = d[row];
-        for (int p = rp[row] + lane; p < rp[row + 1]; p += 32) {
+        const int ei = exp_of_pow2(d[row]);
+        for (int p = rp[row] + sub; p < rp[row + 1]; p += kRowLanes) {
             const double k = v[p];
-            double a = di * k * d[ci[p]];
-            sv[p] = (T)a;
+            const unsigned long long ab = scale2_bits(abs_bits(k), ei + exp_of_pow2(d[ci[p]]));
+            const unsigned long long sb = ab | ((unsigned long long)__double_as_longlong(k) & 0x8000000000000000ull);
+            sv[p] = (T)__longlong_as_double((long long)sb);         // d_i k d_j, exact
             kcopy[p] = k;
-            amax = fmax(amax, fabs(a));
+            amb = ab > amb ? ab : amb;
             rsum += fabs(k);
         }
     }
+    amax = __longlong_as_double((long long)amb);
+    rsum = group_sum(rsum);          // row sum of |K| (lanes of one row)
     amax = warp_max(amax);
-    rsum = warp_sum(rsum);
-    if (lane == 0 && row < n) {
-        atomic_max_nonneg(&stat->amax_bits, amax);
-        atomic_max_nonneg(&stat->knorm_bits, rsum);
+    rsum = warp_max(rsum);           // largest row sum in the warp
+    __shared__ double s_am[8], s_rs[8];
+    const int wid = threadIdx.x >> 5;
+    if (lane == 0) { s_am[wid] = amax; s_rs[wid] = rsum; }
+    __syncthreads();
+    // one atomic per block and quantity (per-row atomics serialise on one address)
+    if (threadIdx.x == 0) {
+        double a = 0.0, r = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a = fmax(a, s_am[q]); r = fmax(r, s_rs[q]); }
+        atomic_max_nonneg(&stat->amax_bits, a);
+        atomic_max_nonneg(&stat->knorm_bits, r);
     }
 }
 
 // ---------------------------------------------------------- front kernels
 
-// Fronts with F <= 32: one warp per front, the whole front in shared memory,
-// lane i owns row i of the front.
+// Original entries of front f into the full F x F front Fm (shared memory):
+// NT threads, four independent gathers in flight per thread.
+template <typename T, int NT>
+__device__ __forceinline__ void assemble_original(const DevSched& s, const DevNum<T>& nm, int f, int tid, T* Fm)
+{
+    const int64_t e0 = s.asm_ptr[f], e1 = s.asm_ptr[f + 1];
+    for (int64_t e = e0 + tid; e < e1; e += NT * 4) {
+        int pos[4];
+        T val[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t ee = e + NT * u;
+            pos[u] = ee < e1 ? s.asm_pos[ee] : -1;
+            val[u] = ee < e1 ? nm.sv[s.asm_src[ee]] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (pos[u] >= 0) Fm[pos[u]] = val[u];
+    }
+}
+
+// Loops over the entries of dense blocks use fixed two-dimensional thread
+// layouts (rows across lanes, columns across lane groups or warps), so no
+// thread divides by a run-time extent: an integer division costs tens of
+// instructions, more than the arithmetic it would index.
+
+// Fronts with F <= 32: one warp per front, the whole front in shared memory.
+// Lanes form an 8 x 4 grid over (row, column) of every block loop.
 template <typename T>
 __global__ void __launch_bounds__(128) front_warp_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
                                                          int count)
 {
     __shared__ T sm[4][kWarpFrontMax * kWarpFrontMax];
+    __shared__ int srl[4][kWarpFrontMax];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int fi = blockIdx.x * 4 + wid;
     if (fi >= count) return;
+    const int li = lane & 7, lj = lane >> 3;
     const int f = fronts[fi];
     const int first = s.sn_first[f];
     const int w = s.sn_first[f + 1] - first;
     const int F = s.sn_front[f];
     T* Fm = sm[wid];
+    int* rls = srl[wid];
     for (int t = lane; t < F * F; t += 32) Fm[t] = T(0);
     __syncwarp();
-    for (int64_t e = s.asm_ptr[f] + lane; e < s.asm_ptr[f + 1]; e += 32) Fm[s.asm_pos[e]] = nm.sv[s.asm_src[e]];
+    assemble_original<T, 32>(s, nm, f, lane, Fm);
     __syncwarp();
     for (int c = s.child_ptr[f]; c < s.child_ptr[f + 1]; ++c) {
         const int ch = s.child_list[c];
         const int mc = s.sn_front[ch] - (s.sn_first[ch + 1] - s.sn_first[ch]);
         const T* cb = nm.cb + s.cb_off[ch];
-        const int* rl = s.rel + s.rel_ptr[ch];
-        for (int t = lane; t < mc * mc; t += 32) {
-            int a = t % mc, b = t / mc;
-            Fm[rl[a] + rl[b] * F] += cb[t];
+        if (lane < mc) rls[lane] = s.rel[s.rel_ptr[ch] + lane];      // mc < F <= 32
+        __syncwarp();
+        for (int b = lj; b < mc; b += 4) {
+            const int rb = rls[b] * F;
+            for (int a = li; a < mc; a += 8) Fm[rls[a] + rb] += cb[a + b * mc];
         }
         __syncwarp();
     }
@@ -167,53 +287,55 @@ __global__ void __launch_bounds__(128) front_warp_kernel(DevSched s, DevNum<T> n
         const T pv = static_pivot(Fm[p + p * F], floor_, nm.stat, lane == 0);
         __syncwarp();
         if (lane == 0) Fm[p + p * F] = pv;
-        const int i = lane;
-        if (i > p && i < F) {
-            const T l = Fm[i + p * F] / pv;
-            Fm[i + p * F] = l;
-            for (int j = p + 1; j < F; ++j) Fm[i + j * F] -= l * Fm[p + j * F];
+        if (lane > p && lane < F) Fm[lane + p * F] /= pv;
+        __syncwarp();
+        for (int j = p + 1 + lj; j < F; j += 4) {
+            const T u = Fm[p + j * F];
+            for (int i = p + 1 + li; i < F; i += 8) Fm[i + j * F] -= Fm[i + p * F] * u;
         }
         __syncwarp();
     }
     T* pan = nm.panel + s.panel_off[f];
     const int m = F - w;
     for (int t = lane; t < F * w; t += 32) pan[t] = Fm[t];
-    for (int t = lane; t < w * m; t += 32) {
-        int a = t / m, b = t % m;
-        pan[F * w + t] = Fm[a + (w + b) * F];
-    }
+    T* U12 = pan + F * w;                                          // column-major (ld = w)
+    for (int b = lj; b < m; b += 4)
+        for (int a = li; a < w; a += 8) U12[a + b * w] = Fm[a + (w + b) * F];
     T* cbo = nm.cb + s.cb_off[f];
-    for (int t = lane; t < m * m; t += 32) {
-        int a = t % m, b = t / m;
-        cbo[t] = Fm[(w + a) + (w + b) * F];
-    }
+    for (int b = lj; b < m; b += 4)
+        for (int a = li; a < m; a += 8) cbo[a + b * m] = Fm[(w + a) + (w + b) * F];
 }
 
-// Fronts with F > 32 and a small contribution block: one CTA per front, the
-// whole front in shared memory, right-looking rank-1 updates.
+// Fronts with F > 32 and a small contribution block: one CTA (8 warps) per
+// front, the whole front in shared memory, right-looking rank-1 updates.
+// Threads form a 32 x 8 grid: lane -> row, warp -> column.
 template <typename T>
 __global__ void __launch_bounds__(256) front_cta_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
-                                                        int count)
+                                                        int count, int max_front)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     T* Fm = reinterpret_cast<T*>(smraw);
+    int* rls = reinterpret_cast<int*>(Fm + (int64_t)max_front * max_front);   // staged relative indices
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int tx = tid & 31, ty = tid >> 5;
     const int f = fronts[blockIdx.x];
     const int first = s.sn_first[f];
     const int w = s.sn_first[f + 1] - first;
     const int F = s.sn_front[f];
     for (int t = tid; t < F * F; t += nt) Fm[t] = T(0);
     __syncthreads();
-    for (int64_t e = s.asm_ptr[f] + tid; e < s.asm_ptr[f + 1]; e += nt) Fm[s.asm_pos[e]] = nm.sv[s.asm_src[e]];
+    assemble_original<T, 256>(s, nm, f, tid, Fm);
     __syncthreads();
     for (int c = s.child_ptr[f]; c < s.child_ptr[f + 1]; ++c) {
         const int ch = s.child_list[c];
         const int mc = s.sn_front[ch] - (s.sn_first[ch + 1] - s.sn_first[ch]);
         const T* cb = nm.cb + s.cb_off[ch];
         const int* rl = s.rel + s.rel_ptr[ch];
-        for (int t = tid; t < mc * mc; t += nt) {
-            int a = t % mc, b = t / mc;
-            Fm[rl[a] + rl[b] * F] += cb[t];
+        for (int t = tid; t < mc; t += nt) rls[t] = rl[t];
+        __syncthreads();
+        for (int b = ty; b < mc; b += 8) {
+            const int rb = rls[b] * F;
+            for (int a = tx; a < mc; a += 32) Fm[rls[a] + rb] += cb[a + (int64_t)b * mc];
         }
         __syncthreads();
     }
@@ -224,69 +346,94 @@ __global__ void __launch_bounds__(256) front_cta_kernel(DevSched s, DevNum<T> nm
         if (tid == 0) Fm[p + p * F] = pv;
         for (int i = p + 1 + tid; i < F; i += nt) Fm[i + p * F] /= pv;
         __syncthreads();
-        const int m = F - p - 1;
-        for (int t = tid; t < m * m; t += nt) {
-            const int i = p + 1 + t % m, j = p + 1 + t / m;
-            Fm[i + j * F] -= Fm[i + p * F] * Fm[p + j * F];
+        for (int j = p + 1 + ty; j < F; j += 8) {
+            const T u = Fm[p + j * F];
+            for (int i = p + 1 + tx; i < F; i += 32) Fm[i + j * F] -= Fm[i + p * F] * u;
         }
         __syncthreads();
     }
     T* pan = nm.panel + s.panel_off[f];
     const int m = F - w;
     for (int t = tid; t < F * w; t += nt) pan[t] = Fm[t];
-    for (int t = tid; t < w * m; t += nt) {
-        int a = t / m, b = t % m;
-        pan[F * w + t] = Fm[a + (w + b) * F];
-    }
+    T* U12 = pan + F * w;                                          // column-major (ld = w)
+    for (int b = ty; b < m; b += 8)
+        for (int a = tx; a < w; a += 32) U12[a + b * w] = Fm[a + (w + b) * F];
     T* cbo = nm.cb + s.cb_off[f];
-    for (int t = tid; t < m * m; t += nt) {
-        int a = t % m, b = t / m;
-        cbo[t] = Fm[(w + a) + (w + b) * F];
-    }
+    for (int b = ty; b < m; b += 8)
+        for (int a = tx; a < m; a += 32) cbo[a + b * m] = Fm[(w + a) + (w + b) * F];
 }
 
-// Fronts with a large contribution block: one CTA assembles the front (pivot
-// columns and rows in shared memory, the (2,2) block directly in the front's
-// contribution-block buffer) and factors the pivot panel; the Schur update of
-// the (2,2) block is left to schur_tile_kernel, spread over many CTAs.
-template <typename T>
-__device__ __forceinline__ T* route(T* col, T* row, T* C, int F, int w, int a, int b)
-{
-    if (b < w) return col + a + (int64_t)b * F;
-    if (a < w) return row + a + (int64_t)(b - w) * w;
-    return C + (a - w) + (int64_t)(b - w) * (F - w);
-}
-
+// Fronts with a large contribution block. One CTA assembles the pivot panel
+// (pivot columns F x w and pivot rows w x (F-w), in shared memory) -- all
+// original entries fall there, and of each child's contribution block only
+// the rows and columns that land on this front's pivots (a prefix, since
+// relative indices increase) -- and factors the pivot columns (L11\U11, L21).
+// The assembled pivot rows F12 go to scratch: schur_tile_kernel turns them into
+// U12 = L11^{-1} F12 and updates the (2,2) block, spread over many CTAs.
 template <typename T>
 __global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
                                                           int count, T* gscratch, int64_t sstride)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int tid = threadIdx.x, nt = blockDim.x;
+    const int tx = tid & 31, ty = tid >> 5;
     const int f = fronts[blockIdx.x];
     const int first = s.sn_first[f];
     const int w = s.sn_first[f + 1] - first;
     const int F = s.sn_front[f];
     const int m = F - w;
     T* col = gscratch ? gscratch + (int64_t)blockIdx.x * sstride : reinterpret_cast<T*>(smraw);
-    T* row = col + (int64_t)F * w;
-    T* C = nm.cb + s.cb_off[f];
+    T* row = col + (int64_t)F * w;                                   // w x m, column-major (ld = w)
     for (int64_t t = tid; t < (int64_t)F * w + (int64_t)w * m; t += nt) col[t] = T(0);
-    for (int64_t t = tid; t < (int64_t)m * m; t += nt) C[t] = T(0);
     __syncthreads();
-    for (int64_t e = s.asm_ptr[f] + tid; e < s.asm_ptr[f + 1]; e += nt) {
-        const int pos = s.asm_pos[e];
-        *route(col, row, C, F, w, pos % F, pos / F) = nm.sv[s.asm_src[e]];
+    {
+        // original entries: position a + b*F of the full front; b < w -> pivot columns,
+        // else a < w (entry (r, c) sits in the front of min(r, c)) -> pivot rows
+        const int64_t e0 = s.asm_ptr[f], e1 = s.asm_ptr[f + 1];
+        for (int64_t e = e0 + tid; e < e1; e += nt * 4) {
+            int pos[4];
+            T val[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t ee = e + nt * u;
+                pos[u] = ee < e1 ? s.asm_pos[ee] : -1;
+                val[u] = ee < e1 ? nm.sv[s.asm_src[ee]] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (pos[u] < 0) continue;
+                if (pos[u] < F * w) col[pos[u]] = val[u];
+                else {
+                    const int rel = pos[u] - F * w;                 // a + (b - w) * F with a < w
+                    const int bw = rel / F;                          // one division per original entry
+                    row[(rel - bw * F) + (int64_t)bw * w] = val[u];
+                }
+            }
+        }
     }
     __syncthreads();
+    int* rls = gscratch ? nullptr : reinterpret_cast<int*>(row + (int64_t)w * m);
     for (int c = s.child_ptr[f]; c < s.child_ptr[f + 1]; ++c) {
         const int ch = s.child_list[c];
         const int mc = s.sn_front[ch] - (s.sn_first[ch + 1] - s.sn_first[ch]);
+        const int k = s.cb_split[ch];
+        if (k == 0) continue;
         const T* cb = nm.cb + s.cb_off[ch];
         const int* rl = s.rel + s.rel_ptr[ch];
-        for (int t = tid; t < mc * mc; t += nt) {
-            int a = rl[t % mc], b = rl[t / mc];
-            *route(col, row, C, F, w, a, b) += cb[t];
+        if (rls) {
+            for (int t = tid; t < mc; t += nt) rls[t] = rl[t];
+            __syncthreads();
+            rl = rls;
+        }
+        // child columns j < k land on pivot columns: every row i
+        for (int j = ty; j < k; j += 8) {
+            const int64_t rj = (int64_t)rl[j] * F;
+            for (int i = tx; i < mc; i += 32) col[rl[i] + rj] += cb[i + (int64_t)j * mc];
+        }
+        // child rows i < k, columns j >= k land on pivot rows, non-pivot columns
+        for (int j = k + ty; j < mc; j += 8) {
+            const int64_t rj = (int64_t)(rl[j] - w) * w;
+            for (int i = tx; i < k; i += 32) row[rl[i] + rj] += cb[i + (int64_t)j * mc];
         }
         __syncthreads();
     }
@@ -297,68 +444,98 @@ __global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> 
         if (tid == 0) col[p + (int64_t)p * F] = pv;
         for (int i = p + 1 + tid; i < F; i += nt) col[i + (int64_t)p * F] /= pv;
         __syncthreads();
-        const int mr = F - p - 1, mcn = w - p - 1;
-        for (int t = tid; t < mr * mcn; t += nt) {
-            const int i = p + 1 + t % mr, j = p + 1 + t / mr;
-            col[i + (int64_t)j * F] -= col[i + (int64_t)p * F] * col[p + (int64_t)j * F];
-        }
-        const int ri = w - p - 1;
-        for (int t = tid; t < ri * m; t += nt) {
-            const int i = p + 1 + t % ri, j = t / ri;
-            row[i + (int64_t)j * w] -= col[i + (int64_t)p * F] * row[p + (int64_t)j * w];
+        for (int j = p + 1 + ty; j < w; j += 8) {
+            const T u = col[p + (int64_t)j * F];
+            for (int i = p + 1 + tx; i < F; i += 32) col[i + (int64_t)j * F] -= col[i + (int64_t)p * F] * u;
         }
         __syncthreads();
     }
     T* pan = nm.panel + s.panel_off[f];
     for (int64_t t = tid; t < (int64_t)F * w; t += nt) pan[t] = col[t];
-    for (int64_t t = tid; t < (int64_t)w * m; t += nt) {
-        int a = (int)(t / m), b = (int)(t % m);
-        pan[(int64_t)F * w + t] = row[a + (int64_t)b * w];
-    }
+    T* f12 = nm.f12 + s.f12_off[f];
+    for (int64_t t = tid; t < (int64_t)w * m; t += nt) f12[t] = row[t];
 }
 
-// C <- C - L21 U12 for one kTile x kTile tile of a panel-class front. The
-// terms are applied in pivot order, one fused multiply-add each, exactly as
-// the single-CTA kernels do.
+// One kTile x kTile tile (ti, tj) of a panel-class front's contribution block:
+// solve L11 U = F12 for the tile's kTile columns of U12 (tiles of the first
+// tile row store them), gather the children's contributions (in child order,
+// through the gather maps), then C -= L21 U12 with the terms applied in pivot
+// order, one fused multiply-add each, as the single-CTA kernels do.
 template <typename T>
 __global__ void __launch_bounds__(256) schur_tile_kernel(DevSched s, DevNum<T> nm, const FrontTile* __restrict__ tiles,
                                                          int count)
 {
     constexpr int KB = 32;
+    constexpr int UL = kTile + 1;                                  // padded row length of the U12 tile
     __shared__ T Ls[KB][kTile + 1];
-    __shared__ T Us[KB][kTile + 1];
+    __shared__ int gi[kTile], gj[kTile];
+    extern __shared__ __align__(16) unsigned char smraw[];
     const FrontTile tl = tiles[blockIdx.x];
     const int f = tl.front;
     const int w = s.sn_first[f + 1] - s.sn_first[f];
     const int F = s.sn_front[f];
     const int m = F - w;
     const int i0 = tl.ti * kTile, j0 = tl.tj * kTile;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;       // 8 warps
-    const T* pan = nm.panel + s.panel_off[f];
+    const int tid = threadIdx.x;
+    const int tx = tid & 31, ty = tid >> 5;                        // 8 warps
+    T* L11 = reinterpret_cast<T*>(smraw);                          // w x w, column-major
+    T* Ut = L11 + w * w;                                           // w x kTile, row a at Ut[a * UL]
+    T* pan = nm.panel + s.panel_off[f];
     const T* L21 = pan + w;                                        // row r, col p at L21[r + p*F]
-    const T* U12 = pan + (int64_t)F * w;                           // row p, col c at U12[p*m + c]
+    const T* F12 = nm.f12 + s.f12_off[f];                          // w x m, column-major
+    for (int c = ty; c < w; c += 8)
+        for (int a = tx; a < w; a += 32) L11[a + c * w] = pan[a + (int64_t)c * F];
+    for (int c = ty; c < kTile; c += 8)
+        for (int a = tx; a < w; a += 32) Ut[a * UL + c] = j0 + c < m ? F12[a + (int64_t)(j0 + c) * w] : T(0);
+    __syncthreads();
+    for (int p = 0; p + 1 < w; ++p) {                              // forward substitution, unit L11
+        for (int t = tid; t < (w - p - 1) * kTile; t += 256) {
+            const int a = p + 1 + t / kTile, c = t % kTile;
+            Ut[a * UL + c] -= L11[a + p * w] * Ut[p * UL + c];
+        }
+        __syncthreads();
+    }
+    if (tl.ti == 0) {
+        T* U12 = pan + (int64_t)F * w;                             // row p, col c at U12[p + c*w]
+        for (int c = ty; c < kTile; c += 8)
+            for (int a = tx; a < w; a += 32)
+                if (j0 + c < m) U12[a + (int64_t)(j0 + c) * w] = Ut[a * UL + c];
+    }
     T* C = nm.cb + s.cb_off[f];
     const int i = i0 + tx;
-    T acc[4];
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    const int* inv = s.inv + s.inv_off[f];
+    for (int c = s.child_ptr[f]; c < s.child_ptr[f + 1]; ++c, inv += m) {
+        const int ch = s.child_list[c];
+        const int mc = s.sn_front[ch] - (s.sn_first[ch + 1] - s.sn_first[ch]);
+        const T* cb = nm.cb + s.cb_off[ch];
+        __syncthreads();
+        if (tid < kTile) gi[tid] = i0 + tid < m ? inv[i0 + tid] : -1;
+        else if (tid < 2 * kTile) gj[tid - kTile] = j0 + tid - kTile < m ? inv[j0 + tid - kTile] : -1;
+        __syncthreads();
+        const int a = gi[tx];
+        if (a >= 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int j = j0 + ty + 8 * k;
-        acc[k] = (i < m && j < m) ? C[i + (int64_t)j * m] : T(0);
+            for (int k = 0; k < 4; ++k) {
+                const int b = gj[ty + 8 * k];
+                if (b >= 0) acc[k] += cb[a + (int64_t)b * mc];
+            }
+        }
     }
     for (int p0 = 0; p0 < w; p0 += KB) {
         const int kb = min(KB, w - p0);
-        for (int t = threadIdx.x; t < KB * kTile; t += 256) {
-            const int c = t / kTile, r = t % kTile;
+        __syncthreads();
+        for (int t = tid; t < KB * kTile; t += 256) {
+            const int c = t / kTile, r = t % kTile;                // consecutive threads: consecutive rows of L21
             Ls[c][r] = (c < kb && i0 + r < m) ? L21[(i0 + r) + (int64_t)(p0 + c) * F] : T(0);
-            Us[c][r] = (c < kb && j0 + r < m) ? U12[(int64_t)(p0 + c) * m + (j0 + r)] : T(0);
         }
         __syncthreads();
         for (int c = 0; c < kb; ++c) {
             const T l = Ls[c][tx];
+            const T* up = Ut + (p0 + c) * UL;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[k] -= l * Us[c][ty + 8 * k];
+            for (int k = 0; k < 4; ++k) acc[k] -= l * up[ty + 8 * k];
         }
-        __syncthreads();
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -392,23 +569,28 @@ __global__ void solve_post_kernel(int n, const int* __restrict__ perm, const dou
 }
 
 // Forward substitution y = L^{-1} c, multifrontally: one warp per front
-// gathers its pivot entries and its children's contribution vectors,
-// eliminates its pivots, and leaves the updates of its non-pivot rows as its
-// own contribution vector.
+// gathers its pivot entries and its children's contribution vectors, solves
+// with its unit lower pivot block (staged in shared memory), then updates its
+// other rows with L21 (lane per row, coalesced column reads) and leaves them as
+// its own contribution vector.
 template <typename T>
 __global__ void __launch_bounds__(128) solve_fwd_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
-                                                        int count, int max_front)
+                                                        int count, int max_front, int max_w)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int fi = blockIdx.x * 4 + wid;
     if (fi >= count) return;
-    T* v = reinterpret_cast<T*>(smraw) + (int64_t)wid * max_front;
+    T* v = reinterpret_cast<T*>(smraw) + (int64_t)wid * (max_front + max_w * max_w);
+    T* Ls = v + max_front;
     const int f = fronts[fi];
     const int first = s.sn_first[f];
     const int w = s.sn_first[f + 1] - first;
     const int F = s.sn_front[f];
+    const T* pan = nm.panel + s.panel_off[f];
     for (int a = lane; a < F; a += 32) v[a] = a < w ? nm.vec[first + a] : T(0);
+    for (int c = lane >> 3; c < w; c += 4)
+        for (int a = lane & 7; a < w; a += 8) Ls[a + c * w] = pan[a + (int64_t)c * F];
     __syncwarp();
     for (int c = s.child_ptr[f]; c < s.child_ptr[f + 1]; ++c) {
         const int ch = s.child_list[c];
@@ -418,69 +600,174 @@ __global__ void __launch_bounds__(128) solve_fwd_kernel(DevSched s, DevNum<T> nm
         for (int t = lane; t < mc; t += 32) v[rl[t]] += cv[t];
         __syncwarp();
     }
-    const T* pan = nm.panel + s.panel_off[f];
     for (int p = 0; p < w; ++p) {
         const T xp = v[p];
-        for (int i = p + 1 + lane; i < F; i += 32) v[i] -= pan[i + (int64_t)p * F] * xp;
+        for (int i = p + 1 + lane; i < w; i += 32) v[i] -= Ls[i + p * w] * xp;
         __syncwarp();
     }
+    for (int i = w + lane; i < F; i += 32) {
+        T acc = v[i];
+        for (int p = 0; p < w; ++p) acc -= pan[i + (int64_t)p * F] * v[p];
+        v[i] = acc;
+    }
+    __syncwarp();
     for (int a = lane; a < w; a += 32) nm.vec[first + a] = v[a];
     T* cv = nm.cbv + s.rel_ptr[f];
     for (int t = lane; t < F - w; t += 32) cv[t] = v[w + t];
 }
 
 // Back substitution x = U^{-1} y, top-down: one warp per front gathers the
-// already-known solution entries of its non-pivot rows, subtracts U12 x, and
-// back-substitutes with U11.
+// already known solution entries of its other rows, subtracts U12 x (lane per
+// pivot row, coalesced reads of the column-major U12), and back-substitutes
+// with its upper pivot block staged in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(128) solve_bwd_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
-                                                        int count, int max_front)
+                                                        int count, int max_front, int max_w)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int fi = blockIdx.x * 4 + wid;
     if (fi >= count) return;
-    T* v = reinterpret_cast<T*>(smraw) + (int64_t)wid * max_front;    // v[0..w): t, v[w..F): x of the other rows
+    T* v = reinterpret_cast<T*>(smraw) + (int64_t)wid * (max_front + max_w * max_w);
+    T* Us = v + max_front;
     const int f = fronts[fi];
     const int first = s.sn_first[f];
     const int w = s.sn_first[f + 1] - first;
     const int F = s.sn_front[f];
     const int m = F - w;
     const int* R = s.rows + s.rows_ptr[f];
-    for (int t = lane; t < m; t += 32) v[w + t] = nm.vec[R[w + t]];
-    __syncwarp();
     const T* pan = nm.panel + s.panel_off[f];
     const T* U12 = pan + (int64_t)F * w;
-    for (int a = 0; a < w; ++a) {
-        T acc = T(0);
-        for (int t = lane; t < m; t += 32) acc += U12[(int64_t)a * m + t] * v[w + t];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-        if (lane == 0) v[a] = nm.vec[first + a] - acc;
+    for (int t = lane; t < m; t += 32) v[w + t] = nm.vec[R[w + t]];
+    for (int c = lane >> 3; c < w; c += 4)
+        for (int a = lane & 7; a < w; a += 8) Us[a + c * w] = pan[a + (int64_t)c * F];
+    __syncwarp();
+    for (int a = lane; a < w; a += 32) {
+        T acc = nm.vec[first + a];
+        for (int t = 0; t < m; ++t) acc -= U12[a + (int64_t)t * w] * v[w + t];
+        v[a] = acc;
     }
     __syncwarp();
     for (int p = w - 1; p >= 0; --p) {
-        const T xp = v[p] / pan[p + (int64_t)p * F];
+        const T xp = v[p] / Us[p + p * w];
         __syncwarp();
         if (lane == 0) v[p] = xp;
-        for (int a = lane; a < p; a += 32) v[a] -= pan[a + (int64_t)p * F] * xp;
+        for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
         __syncwarp();
     }
     for (int a = lane; a < w; a += 32) nm.vec[first + a] = v[a];
 }
 
+// The same two substitutions for larger fronts, one CTA (128 threads) per
+// front: one warp does the sequential pivot block, all threads the L21 / U12
+// products.
+template <typename T>
+__global__ void __launch_bounds__(128) solve_fwd_cta_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
+                                                            int count, int max_front, int max_w)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int tid = threadIdx.x, lane = tid & 31;
+    T* v = reinterpret_cast<T*>(smraw);
+    T* Ls = v + max_front;
+    const int f = fronts[blockIdx.x];
+    const int first = s.sn_first[f];
+    const int w = s.sn_first[f + 1] - first;
+    const int F = s.sn_front[f];
+    const T* pan = nm.panel + s.panel_off[f];
+    for (int a = tid; a < F; a += 128) v[a] = a < w ? nm.vec[first + a] : T(0);
+    for (int c = tid >> 5; c < w; c += 4)
+        for (int a = lane; a < w; a += 32) Ls[a + c * w] = pan[a + (int64_t)c * F];
+    __syncthreads();
+    for (int c = s.child_ptr[f]; c < s.child_ptr[f + 1]; ++c) {
+        const int ch = s.child_list[c];
+        const int mc = s.sn_front[ch] - (s.sn_first[ch + 1] - s.sn_first[ch]);
+        const T* cv = nm.cbv + s.rel_ptr[ch];
+        const int* rl = s.rel + s.rel_ptr[ch];
+        for (int t = tid; t < mc; t += 128) v[rl[t]] += cv[t];
+        __syncthreads();
+    }
+    if (tid < 32) {
+        for (int p = 0; p < w; ++p) {
+            const T xp = v[p];
+            for (int i = p + 1 + lane; i < w; i += 32) v[i] -= Ls[i + p * w] * xp;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int i = w + tid; i < F; i += 128) {
+        T acc = v[i];
+        for (int p = 0; p < w; ++p) acc -= pan[i + (int64_t)p * F] * v[p];
+        v[i] = acc;
+    }
+    __syncthreads();
+    for (int a = tid; a < w; a += 128) nm.vec[first + a] = v[a];
+    T* cv = nm.cbv + s.rel_ptr[f];
+    for (int t = tid; t < F - w; t += 128) cv[t] = v[w + t];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) solve_bwd_cta_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
+                                                            int count, int max_front, int max_w)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ T red[128];
+    const int tid = threadIdx.x, lane = tid & 31;
+    T* v = reinterpret_cast<T*>(smraw);
+    T* Us = v + max_front;
+    const int f = fronts[blockIdx.x];
+    const int first = s.sn_first[f];
+    const int w = s.sn_first[f + 1] - first;
+    const int F = s.sn_front[f];
+    const int m = F - w;
+    const int* R = s.rows + s.rows_ptr[f];
+    const T* pan = nm.panel + s.panel_off[f];
+    const T* U12 = pan + (int64_t)F * w;
+    for (int t = tid; t < m; t += 128) v[w + t] = nm.vec[R[w + t]];
+    for (int c = tid >> 5; c < w; c += 4)
+        for (int a = lane; a < w; a += 32) Us[a + c * w] = pan[a + (int64_t)c * F];
+    __syncthreads();
+    // y_a - sum_t U12[a, t] x_t: thread (a, g) sums every G-th t, then row sums in g order
+    const int G = 128 / w;
+    T part = T(0);
+    if (tid < G * w) {
+        const int a = tid % w, g = tid / w;
+        for (int t = g; t < m; t += G) part += U12[a + (int64_t)t * w] * v[w + t];
+    }
+    red[tid] = part;
+    __syncthreads();
+    for (int a = tid; a < w; a += 128) {
+        T acc = T(0);
+        for (int g = 0; g < G; ++g) acc += red[a + g * w];
+        v[a] = nm.vec[first + a] - acc;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        for (int p = w - 1; p >= 0; --p) {
+            const T xp = v[p] / Us[p + p * w];
+            __syncwarp();
+            if (lane == 0) v[p] = xp;
+            for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int a = tid; a < w; a += 128) nm.vec[first + a] = v[a];
+}
+
 // ---------------------------------------------------------- FP64 vectors
 
-__global__ void spmv_resid_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                  const double* __restrict__ v, const double* __restrict__ x,
-                                  const double* __restrict__ b, double* __restrict__ r)
+__global__ void __launch_bounds__(256) spmv_resid_kernel(int n, const int* __restrict__ rp,
+                                                         const int* __restrict__ ci, const double* __restrict__ v,
+                                                         const double* __restrict__ x, const double* __restrict__ b,
+                                                         double* __restrict__ r)
 {
-    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
-    if (row >= n) return;
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
+    const int sub = threadIdx.x % kRowLanes;
     double s = 0.0;
-    for (int p = rp[row] + lane; p < rp[row + 1]; p += 32) s += v[p] * x[ci[p]];
-    s = warp_sum(s);
-    if (lane == 0) r[row] = b ? b[row] - s : s;
+    if (row < n)
+        for (int p = rp[row] + sub; p < rp[row + 1]; p += kRowLanes) s += v[p] * x[ci[p]];
+    s = group_sum(s);
+    if (row < n && sub == 0) r[row] = b ? b[row] - s : s;
 }
 
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs
@@ -591,7 +878,7 @@ cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double
     double* a = d;
     double* b = dtmp;
     for (int it = 0; it < iters; ++it) {
-        ruiz_kernel<<<cdiv((int64_t)s.n * 32, 256), 256, 0, st>>>(
+        ruiz_kernel<<<cdiv((int64_t)s.n * kRowLanes, 256), 256, 0, st>>>(
             s.n, s.rowptr, s.colidx, vals, a, b, it > 0 ? &stat->ruiz_changed[it - 1] : nullptr,
             &stat->ruiz_changed[it]);
         double* t = a; a = b; b = t;
@@ -603,7 +890,7 @@ cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double
 template <typename T>
 cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d, cudaStream_t st)
 {
-    scale_kernel<T><<<cdiv((int64_t)s.n * 32, 256), 256, 0, st>>>(s.n, s.rowptr, s.colidx, nm.vals, d, nm.sv,
+    scale_kernel<T><<<cdiv((int64_t)s.n * kRowLanes, 256), 256, 0, st>>>(s.n, s.rowptr, s.colidx, nm.vals, d, nm.sv,
                                                                    nm.kcopy, nm.stat);
     return cudaGetLastError();
 }
@@ -621,8 +908,8 @@ cudaError_t launch_fronts_cta(const DevSched& s, const DevNum<T>& nm, const int*
                               cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    size_t smem = (size_t)max_front * max_front * sizeof(T);
-    front_cta_kernel<T><<<count, 256, smem, st>>>(s, nm, fronts, count);
+    size_t smem = (size_t)max_front * max_front * sizeof(T) + (size_t)max_front * sizeof(int);
+    front_cta_kernel<T><<<count, 256, smem, st>>>(s, nm, fronts, count, max_front);
     return cudaGetLastError();
 }
 
@@ -638,10 +925,11 @@ cudaError_t launch_fronts_panel(const DevSched& s, const DevNum<T>& nm, const in
 
 template <typename T>
 cudaError_t launch_schur_tiles(const DevSched& s, const DevNum<T>& nm, const FrontTile* tiles, int count,
-                               cudaStream_t st)
+                               int max_w, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    schur_tile_kernel<T><<<count, 256, 0, st>>>(s, nm, tiles, count);
+    const size_t smem = (size_t)(max_w * max_w + max_w * (kTile + 1)) * sizeof(T);
+    schur_tile_kernel<T><<<count, 256, smem, st>>>(s, nm, tiles, count);
     return cudaGetLastError();
 }
 
@@ -661,35 +949,55 @@ cudaError_t launch_solve_post(const DevSched& s, const DevNum<T>& nm, double* x,
 
 template <typename T>
 cudaError_t launch_solve_fwd(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
-                             cudaStream_t st)
+                             int max_w, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    solve_fwd_kernel<T><<<cdiv(count, 4), 128, 4 * (size_t)max_front * sizeof(T), st>>>(s, nm, fronts, count,
-                                                                                         max_front);
+    const size_t smem = 4 * (size_t)(max_front + max_w * max_w) * sizeof(T);
+    solve_fwd_kernel<T><<<cdiv(count, 4), 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_solve_bwd(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
-                             cudaStream_t st)
+                             int max_w, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    solve_bwd_kernel<T><<<cdiv(count, 4), 128, 4 * (size_t)max_front * sizeof(T), st>>>(s, nm, fronts, count,
-                                                                                         max_front);
+    const size_t smem = 4 * (size_t)(max_front + max_w * max_w) * sizeof(T);
+    solve_bwd_kernel<T><<<cdiv(count, 4), 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_solve_fwd_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
+                                 int max_w, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    const size_t smem = (size_t)(max_front + max_w * max_w) * sizeof(T);
+    solve_fwd_cta_kernel<T><<<count, 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_solve_bwd_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
+                                 int max_w, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    const size_t smem = (size_t)(max_front + max_w * max_w) * sizeof(T);
+    solve_bwd_cta_kernel<T><<<count, 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spmv_resid(int n, const int* rp, const int* ci, const double* v, const double* x,
                               const double* b, double* r, cudaStream_t st)
 {
-    spmv_resid_kernel<<<cdiv((int64_t)n * 32, 256), 256, 0, st>>>(n, rp, ci, v, x, b, r);
+    spmv_resid_kernel<<<cdiv((int64_t)n * kRowLanes, 256), 256, 0, st>>>(n, rp, ci, v, x, b, r);
     return cudaGetLastError();
 }
 
 cudaError_t launch_spmv(int n, const int* rp, const int* ci, const double* v, const double* x, double* y,
                         cudaStream_t st)
 {
-    spmv_resid_kernel<<<cdiv((int64_t)n * 32, 256), 256, 0, st>>>(n, rp, ci, v, x, nullptr, y);
+    spmv_resid_kernel<<<cdiv((int64_t)n * kRowLanes, 256), 256, 0, st>>>(n, rp, ci, v, x, nullptr, y);
     return cudaGetLastError();
 }
 
@@ -740,30 +1048,52 @@ cudaError_t launch_norms(int n, const double* a, double* out, cudaStream_t st)
                                               cudaStream_t);                                                     \
     template cudaError_t launch_fronts_panel<T>(const DevSched&, const DevNum<T>&, const int*, int, size_t, T*,  \
                                                 int64_t, cudaStream_t);                                          \
-    template cudaError_t launch_schur_tiles<T>(const DevSched&, const DevNum<T>&, const FrontTile*, int,         \
+    template cudaError_t launch_schur_tiles<T>(const DevSched&, const DevNum<T>&, const FrontTile*, int, int,    \
                                                cudaStream_t);                                                    \
     template cudaError_t launch_solve_pre<T>(const DevSched&, const DevNum<T>&, const double*, cudaStream_t);    \
     template cudaError_t launch_solve_post<T>(const DevSched&, const DevNum<T>&, double*, cudaStream_t);         \
-    template cudaError_t launch_solve_fwd<T>(const DevSched&, const DevNum<T>&, const int*, int, int,            \
+    template cudaError_t launch_solve_fwd<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,       \
                                              cudaStream_t);                                                      \
-    template cudaError_t launch_solve_bwd<T>(const DevSched&, const DevNum<T>&, const int*, int, int,            \
-                                             cudaStream_t);
+    template cudaError_t launch_solve_bwd<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,       \
+                                             cudaStream_t);                                                      \
+    template cudaError_t launch_solve_fwd_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,   \
+                                                 cudaStream_t);                                                  \
+    template cudaError_t launch_solve_bwd_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,   \
+                                                 cudaStream_t);
 KKT_INST(double)
 KKT_INST(float)
 
-// set dynamic shared-memory limits once per process
+// Raise each kernel's dynamic shared-memory limit to the device's opt-in
+// maximum minus the kernel's static shared memory (once per process).
+template <typename K>
+static cudaError_t allow_smem(K kernel, int optin)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 cudaError_t configure_kernels()
 {
-    cudaError_t e;
-    const int lim = 227 * 1024;
-    if ((e = cudaFuncSetAttribute(front_cta_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(front_cta_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(front_panel_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(front_panel_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(solve_fwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(solve_fwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(solve_bwd_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
-    if ((e = cudaFuncSetAttribute(solve_bwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim))) return e;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    if ((e = allow_smem(front_cta_kernel<double>, optin))) return e;
+    if ((e = allow_smem(front_cta_kernel<float>, optin))) return e;
+    if ((e = allow_smem(front_panel_kernel<double>, optin))) return e;
+    if ((e = allow_smem(front_panel_kernel<float>, optin))) return e;
+    if ((e = allow_smem(solve_fwd_kernel<double>, optin))) return e;
+    if ((e = allow_smem(solve_fwd_kernel<float>, optin))) return e;
+    if ((e = allow_smem(solve_bwd_kernel<double>, optin))) return e;
+    if ((e = allow_smem(solve_bwd_kernel<float>, optin))) return e;
+    if ((e = allow_smem(solve_fwd_cta_kernel<double>, optin))) return e;
+    if ((e = allow_smem(solve_fwd_cta_kernel<float>, optin))) return e;
+    if ((e = allow_smem(solve_bwd_cta_kernel<double>, optin))) return e;
+    if ((e = allow_smem(solve_bwd_cta_kernel<float>, optin))) return e;
+    if ((e = allow_smem(schur_tile_kernel<double>, optin))) return e;
+    if ((e = allow_smem(schur_tile_kernel<float>, optin))) return e;
     return cudaSuccess;
 }
 

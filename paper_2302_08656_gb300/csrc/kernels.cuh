@@ -26,6 +26,10 @@ struct DevSched {
     const int* rel = nullptr;
     const int64_t* panel_off = nullptr;
     const int64_t* cb_off = nullptr;
+    const int* cb_split = nullptr;    // per front: contribution rows landing on parent pivots
+    const int64_t* inv_off = nullptr; // per panel-class front: offset of its children's gather maps
+    const int* inv = nullptr;         // per (front, child): parent CB row -> child CB row or -1
+    const int64_t* f12_off = nullptr; // per panel-class front: offset of its assembled pivot rows
 };
 
 // Device-side counters of one context, cleared at the start of each refactor.
@@ -49,6 +53,7 @@ struct DevNum {
     T* cb = nullptr;                  // contribution blocks
     T* vec = nullptr;                 // step-space solve vector (n)
     T* cbv = nullptr;                 // solve contribution vectors
+    T* f12 = nullptr;                 // assembled pivot rows of panel-class fronts
     DevStat* stat = nullptr;
     double pivot_eps = 1e-14;
 };
@@ -57,7 +62,8 @@ struct DevNum {
 struct FrontTile { int front; int ti; int tj; };
 
 constexpr int kWarpFrontMax = 32;      // fronts with F <= 32 are handled by one warp
-constexpr int kPanelCbMin = 48;        // fronts with F - w >= 48 use panel + tiled Schur update
+constexpr int kWarpLevelMin = 608;     // ... when their level has at least 4 x 152 of them
+constexpr int kPanelCbMin = 32;        // fronts with F - w >= 32 use panel + tiled Schur update
 constexpr int kTile = 32;              // Schur update tile (kTile x kTile)
 
 // Launchers (all asynchronous on `st`).
@@ -76,15 +82,21 @@ cudaError_t launch_fronts_panel(const DevSched& s, const DevNum<T>& nm, const in
                                 size_t smem_bytes, T* gscratch, int64_t scratch_stride, cudaStream_t st);
 template <typename T>
 cudaError_t launch_schur_tiles(const DevSched& s, const DevNum<T>& nm, const FrontTile* tiles, int count,
-                               cudaStream_t st);
+                               int max_w, cudaStream_t st);
+template <typename T>
+cudaError_t launch_solve_fwd_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
+                                 int max_front, int max_w, cudaStream_t st);
+template <typename T>
+cudaError_t launch_solve_bwd_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
+                                 int max_front, int max_w, cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_pre(const DevSched& s, const DevNum<T>& nm, const double* b, cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_fwd(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                             int max_front, cudaStream_t st);
+                             int max_front, int max_w, cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_bwd(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                             int max_front, cudaStream_t st);
+                             int max_front, int max_w, cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_post(const DevSched& s, const DevNum<T>& nm, double* x, cudaStream_t st);
 

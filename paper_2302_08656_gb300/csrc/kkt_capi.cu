@@ -25,11 +25,12 @@ namespace {
 struct LevelGroup {
     int warp_off = 0, warp_cnt = 0;           // offsets into the device front-id array
     int cta_off = 0, cta_cnt = 0, cta_maxF = 0;
-    int panel_off = 0, panel_cnt = 0;
+    int panel_off = 0, panel_cnt = 0, panel_maxW = 0;
+    int small_maxF = 0, small_maxW = 0, big_maxF = 0, big_maxW = 0;   // solve: warp / CTA classes
     size_t panel_smem = 0;                    // 0 with panel_global = true
     bool panel_global = false;
     int tile_off = 0, tile_cnt = 0;
-    int all_off = 0, all_cnt = 0, all_maxF = 0;   // every front of the level (solve)
+    int all_off = 0, all_cnt = 0, all_maxF = 0, all_maxW = 0;   // every front of the level (solve)
 };
 
 // Device pool: one allocation carved into aligned pieces.
@@ -90,6 +91,11 @@ struct kkt_ctx {
     std::vector<int> ev_kind;
     std::vector<int> ev_count;         // kernels issued by the group
     size_t ev_used = 0;
+    // CUDA graphs of the level loops (captured once on a private stream)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t g_factor = nullptr, g_solve = nullptr;
+    long long g_factor_kernels = 0, g_solve_kernels = 0;
+    bool capturing = false;
     // state
     const double* last_vals = nullptr;
     int refactored = 0;
@@ -121,6 +127,7 @@ void fill_defaults(kkt_options* o)
     o->relax_pivots = 16;
     o->relax_zeros = 0.15;
     o->max_pivots = 64;
+    o->no_graphs = 0;
 }
 
 kkt_status check_options(const kkt_options& o)
@@ -130,7 +137,7 @@ kkt_status check_options(const kkt_options& o)
     if (o.ruiz_iters < 0 || o.ruiz_iters > 64) return KKT_E_ARG;
     if (o.restart < 1 || o.restart > kMaxRestart) return KKT_E_ARG;
     if (o.max_cycles < 0) return KKT_E_ARG;
-    if (o.max_pivots < 1 || o.max_pivots > 256) return KKT_E_ARG;
+    if (o.max_pivots < 1 || o.max_pivots > 64) return KKT_E_ARG;
     if (o.relax_pivots < 1) return KKT_E_ARG;
     return KKT_OK;
 }
@@ -152,8 +159,14 @@ constexpr size_t kSmemLimit = 220 * 1024;
 
 // Classify fronts per level and lay out the launch lists.
 void build_levels(const Analysis& an, size_t es, std::vector<LevelGroup>& levels, std::vector<int>& front_ids,
-                  std::vector<FrontTile>& tiles, int64_t& scratch_stride, int& max_panel_global)
+                  std::vector<FrontTile>& tiles, int64_t& scratch_stride, int& max_panel_global,
+                  std::vector<int64_t>& inv_off, std::vector<int>& inv, std::vector<int64_t>& f12_off,
+                  int64_t& f12_total)
 {
+    inv_off.assign(an.ns, 0);
+    inv.clear();
+    f12_off.assign(an.ns, 0);
+    f12_total = 0;
     levels.assign(an.n_levels, LevelGroup());
     front_ids.clear();
     tiles.clear();
@@ -164,14 +177,16 @@ void build_levels(const Analysis& an, size_t es, std::vector<LevelGroup>& levels
         std::vector<int> wl, cl, pl;
         int cmax = 0;
         size_t psmem = 0;
-        int allmax = 0;
+        int allmax = 0, allw = 0;
         for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) {
             int s = an.level_fronts[t];
             int F = an.sn_front[s], w = an.sn_first[s + 1] - an.sn_first[s];
             allmax = std::max(allmax, F);
+            allw = std::max(allw, w);
             if (F - w >= kPanelCbMin) {
                 pl.push_back(s);
-                psmem = std::max(psmem, (size_t)(F * w + w * (F - w)) * es);
+                psmem = std::max(psmem, (size_t)(F * w + w * (F - w)) * es + (size_t)F * sizeof(int));
+                g.panel_maxW = std::max(g.panel_maxW, w);
             } else if (F <= kWarpFrontMax) {
                 wl.push_back(s);
             } else {
@@ -179,10 +194,28 @@ void build_levels(const Analysis& an, size_t es, std::vector<LevelGroup>& levels
                 cmax = std::max(cmax, F);
             }
         }
+        // a warp per front pays only when the level has enough fronts to fill
+        // the GPU; on narrow levels a lone warp cannot hide latency, so small
+        // fronts go to the CTA kernels as well
+        if ((int)wl.size() < kWarpLevelMin) {
+            for (int s : wl) cmax = std::max(cmax, an.sn_front[s]);
+            cl.insert(cl.begin(), wl.begin(), wl.end());
+            wl.clear();
+        }
+        for (int s : wl) {
+            g.small_maxF = std::max(g.small_maxF, an.sn_front[s]);
+            g.small_maxW = std::max(g.small_maxW, an.sn_first[s + 1] - an.sn_first[s]);
+        }
+        for (const std::vector<int>* lst : {&cl, &pl})
+            for (int s : *lst) {
+                g.big_maxF = std::max(g.big_maxF, an.sn_front[s]);
+                g.big_maxW = std::max(g.big_maxW, an.sn_first[s + 1] - an.sn_first[s]);
+            }
         g.all_off = (int)front_ids.size();
         for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) front_ids.push_back(an.level_fronts[t]);
         g.all_cnt = (int)(front_ids.size() - g.all_off);
         g.all_maxF = allmax;
+        g.all_maxW = allw;
         g.warp_off = (int)front_ids.size();
         front_ids.insert(front_ids.end(), wl.begin(), wl.end());
         g.warp_cnt = (int)wl.size();
@@ -198,6 +231,24 @@ void build_levels(const Analysis& an, size_t es, std::vector<LevelGroup>& levels
             g.panel_global = true;
             scratch_stride = std::max<int64_t>(scratch_stride, (int64_t)(psmem / es));
             max_panel_global = std::max(max_panel_global, g.panel_cnt);
+        }
+        // gather maps of the panel-class fronts: parent CB row -> child CB row
+        for (int s : pl) {
+            int F = an.sn_front[s], w = an.sn_first[s + 1] - an.sn_first[s];
+            int m = F - w;
+            f12_off[s] = f12_total;
+            f12_total += (int64_t)w * m;
+            inv_off[s] = (int64_t)inv.size();
+            for (int c = an.child_ptr[s]; c < an.child_ptr[s + 1]; ++c) {
+                int ch = an.child_list[c];
+                size_t base = inv.size();
+                inv.resize(base + m, -1);
+                int mc = an.sn_front[ch] - (an.sn_first[ch + 1] - an.sn_first[ch]);
+                for (int t = 0; t < mc; ++t) {
+                    int pos = an.rel[an.rel_ptr[ch] + t];
+                    if (pos >= w) inv[base + (pos - w)] = t;
+                }
+            }
         }
         g.tile_off = (int)tiles.size();
         for (int s : pl) {
@@ -234,8 +285,8 @@ struct Launch {
     size_t slot = (size_t)-1;
     Launch(kkt_ctx* c_, cudaStream_t st_, int kind_, int kernels_) : c(c_), st(st_), kind(kind_), kernels(kernels_)
     {
-        c->launches += kernels;
-        if (c->profile && kernels > 0) {
+        if (!c->capturing) c->launches += kernels;
+        if (c->profile && kernels > 0 && !c->capturing) {
             if (c->ev_used + 2 > c->ev.size()) {
                 for (int i = 0; i < 512; ++i) {
                     cudaEvent_t e;
@@ -258,23 +309,35 @@ struct Launch {
     }
 };
 
-template <typename T>
-kkt_status refactor_t(kkt_ctx* c, const double* d_vals, cudaStream_t st)
+// Capture a launch sequence into an executable graph on the context's
+// private stream (the caller's stream may be the legacy stream, which cannot
+// capture). Kernels launched during capture are counted once, per replay.
+template <typename F>
+kkt_status capture(kkt_ctx* c, cudaGraphExec_t* exec, long long* kernels, F&& body)
 {
-    DevNum<T>& nm = num_of<T>(c);
-    nm.vals = d_vals;
-    KKT_CUDA(launch_zero_stat(c->stat, st));
-    double* dfin = nullptr;
-    {
-        Launch L(c, st, KK_RUIZ, 1 + c->opt.ruiz_iters);
-        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->d_a, c->d_b, c->opt.ruiz_iters, c->stat, &dfin, st));
-    }
-    c->d_final = dfin;
-    nm.d = dfin;
-    {
-        Launch L(c, st, KK_SCALE, 1);
-        KKT_CUDA(launch_scale<T>(c->sched, nm, dfin, st));
-    }
+    if (!c->cap_stream) KKT_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    long long before = c->launches;
+    KKT_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    kkt_status s = body(c->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    c->capturing = false;
+    if (s != KKT_OK) { if (graph) cudaGraphDestroy(graph); return s; }
+    if (e != cudaSuccess) return KKT_E_CUDA;
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { *exec = nullptr; return KKT_E_CUDA; }
+    *kernels = (long long)nodes;
+    c->launches = before;
+    return KKT_OK;
+}
+
+template <typename T>
+kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st)
+{
     const int* fr = c->fronts_dev;
     for (const LevelGroup& g : c->levels) {
         if (g.warp_cnt) {
@@ -293,10 +356,73 @@ kkt_status refactor_t(kkt_ctx* c, const double* d_vals, cudaStream_t st)
                                                 c->scratch_stride, st));
             }
             Launch L(c, st, KK_SCHUR, 1);
-            KKT_CUDA(launch_schur_tiles<T>(c->sched, nm, c->tiles_dev + g.tile_off, g.tile_cnt, st));
+            KKT_CUDA(launch_schur_tiles<T>(c->sched, nm, c->tiles_dev + g.tile_off, g.tile_cnt, g.panel_maxW, st));
         }
     }
     return KKT_OK;
+}
+
+template <typename T>
+kkt_status solve_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st)
+{
+    const int* fr = c->fronts_dev;
+    // fronts with F <= 32: a warp each; larger ones (the CTA and panel classes,
+    // contiguous in the front list): a CTA each
+    for (size_t l = 0; l < c->levels.size(); ++l) {
+        const LevelGroup& g = c->levels[l];
+        const int nbig = g.cta_cnt + g.panel_cnt;
+        if (g.warp_cnt) {
+            Launch L(c, st, KK_SOLVE_FWD, 1);
+            KKT_CUDA(launch_solve_fwd<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, g.small_maxW, st));
+        }
+        if (nbig) {
+            Launch L(c, st, KK_SOLVE_FWD, 1);
+            KKT_CUDA(launch_solve_fwd_cta<T>(c->sched, nm, fr + g.cta_off, nbig, g.big_maxF, g.big_maxW, st));
+        }
+    }
+    for (size_t l = c->levels.size(); l-- > 0;) {
+        const LevelGroup& g = c->levels[l];
+        const int nbig = g.cta_cnt + g.panel_cnt;
+        if (g.warp_cnt) {
+            Launch L(c, st, KK_SOLVE_BWD, 1);
+            KKT_CUDA(launch_solve_bwd<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, g.small_maxW, st));
+        }
+        if (nbig) {
+            Launch L(c, st, KK_SOLVE_BWD, 1);
+            KKT_CUDA(launch_solve_bwd_cta<T>(c->sched, nm, fr + g.cta_off, nbig, g.big_maxF, g.big_maxW, st));
+        }
+    }
+    return KKT_OK;
+}
+
+template <typename T>
+kkt_status refactor_t(kkt_ctx* c, const double* d_vals, cudaStream_t st)
+{
+    DevNum<T>& nm = num_of<T>(c);
+    nm.vals = d_vals;
+    KKT_CUDA(launch_zero_stat(c->stat, st));
+    double* dfin = nullptr;
+    {
+        Launch L(c, st, KK_RUIZ, 1 + c->opt.ruiz_iters);
+        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->d_a, c->d_b, c->opt.ruiz_iters, c->stat, &dfin, st));
+    }
+    c->d_final = dfin;
+    nm.d = dfin;
+    {
+        Launch L(c, st, KK_SCALE, 1);
+        KKT_CUDA(launch_scale<T>(c->sched, nm, dfin, st));
+    }
+    if (!c->profile && !c->opt.no_graphs) {
+        if (!c->g_factor) {
+            kkt_status cs = capture(c, &c->g_factor, &c->g_factor_kernels,
+                                    [&](cudaStream_t cst) { return factor_levels<T>(c, nm, cst); });
+            if (cs != KKT_OK) return cs;
+        }
+        c->launches += c->g_factor_kernels;
+        KKT_CUDA(cudaGraphLaunch(c->g_factor, st));
+        return KKT_OK;
+    }
+    return factor_levels<T>(c, nm, st);
 }
 
 template <typename T>
@@ -307,16 +433,17 @@ kkt_status solve_t(kkt_ctx* c, const double* b, double* x, cudaStream_t st)
         Launch L(c, st, KK_SOLVE_PRE, 1);
         KKT_CUDA(launch_solve_pre<T>(c->sched, nm, b, st));
     }
-    const int* fr = c->fronts_dev;
-    for (size_t l = 0; l < c->levels.size(); ++l) {
-        const LevelGroup& g = c->levels[l];
-        Launch L(c, st, KK_SOLVE_FWD, g.all_cnt ? 1 : 0);
-        KKT_CUDA(launch_solve_fwd<T>(c->sched, nm, fr + g.all_off, g.all_cnt, g.all_maxF, st));
-    }
-    for (size_t l = c->levels.size(); l-- > 0;) {
-        const LevelGroup& g = c->levels[l];
-        Launch L(c, st, KK_SOLVE_BWD, g.all_cnt ? 1 : 0);
-        KKT_CUDA(launch_solve_bwd<T>(c->sched, nm, fr + g.all_off, g.all_cnt, g.all_maxF, st));
+    if (!c->profile && !c->opt.no_graphs) {
+        if (!c->g_solve) {
+            kkt_status cs = capture(c, &c->g_solve, &c->g_solve_kernels,
+                                    [&](cudaStream_t cst) { return solve_levels<T>(c, nm, cst); });
+            if (cs != KKT_OK) return cs;
+        }
+        c->launches += c->g_solve_kernels;
+        KKT_CUDA(cudaGraphLaunch(c->g_solve, st));
+    } else {
+        kkt_status ls = solve_levels<T>(c, nm, st);
+        if (ls != KKT_OK) return ls;
     }
     {
         Launch L(c, st, KK_SOLVE_POST, 1);
@@ -537,7 +664,7 @@ const char* kkt_status_string(kkt_status s)
 }
 
 static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_options& o, int64_t tiles, int64_t fronts,
-                          int64_t scratch)
+                          int64_t scratch, int64_t ninv, int64_t nf12)
 {
     const int64_t es = (int64_t)elem_size(o.precision);
     int64_t b = 0;
@@ -558,6 +685,8 @@ static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_opti
     add((int64_t)(kRedScratch + 4096 + 8) * 8);
     add((int64_t)(8 + 2 * (kMaxRestart + 2)) * 8);
     add(nnz * 8); add(nnz * 8); add(n * 8); add(n * 8);
+    add(an.ns * 4); add(an.ns * 8); add(std::max<int64_t>(ninv, 1) * 4);
+    add(an.ns * 8); add(std::max<int64_t>(nf12, 1) * es);
     return b;
 }
 
@@ -577,7 +706,10 @@ kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx,
         std::vector<FrontTile> tiles;
         int64_t stride = 0;
         int mpg = 0;
-        build_levels(an, elem_size(o.precision), lv, fids, tiles, stride, mpg);
+        std::vector<int64_t> inv_off, f12_off;
+        std::vector<int> inv;
+        int64_t f12_total = 0;
+        build_levels(an, elem_size(o.precision), lv, fids, tiles, stride, mpg, inv_off, inv, f12_off, f12_total);
         std::memset(out, 0, sizeof(*out));
         out->n = n;
         out->nnz = an.nnz;
@@ -590,7 +722,7 @@ kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx,
         out->flops = an.flops;
         out->flops_exact = an.flops_exact;
         out->device_bytes = plan_bytes(an, n, an.nnz, o, (int64_t)tiles.size(), (int64_t)fids.size(),
-                                       stride * mpg);
+                                       stride * mpg, (int64_t)inv.size(), f12_total);
     } catch (const std::bad_alloc&) {
         return KKT_E_NOMEM;
     } catch (...) {
@@ -618,6 +750,9 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
     c->n_primal = n_primal;
     std::vector<int> fids;
     std::vector<FrontTile> tiles;
+    std::vector<int64_t> inv_off, f12_off;
+    std::vector<int> inv;
+    int64_t f12_total = 0;
     try {
         std::string err = analyze_pattern(n, h_rowptr, h_colidx, to_analysis(opt ? *opt : c->opt), c->an);
         if (!err.empty()) {
@@ -626,7 +761,7 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
             return s;
         }
         build_levels(c->an, elem_size(c->opt.precision), c->levels, fids, tiles, c->scratch_stride,
-                     c->max_panel_global);
+                     c->max_panel_global, inv_off, inv, f12_off, f12_total);
     } catch (...) {
         delete c;
         return KKT_E_NOMEM;
@@ -640,7 +775,8 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
     c->nnz = an.nnz;
     const int64_t nnz = an.nnz;
     const int64_t scratch = c->scratch_stride * c->max_panel_global;
-    int64_t bytes = plan_bytes(an, n, nnz, c->opt, (int64_t)tiles.size(), (int64_t)fids.size(), scratch);
+    int64_t bytes = plan_bytes(an, n, nnz, c->opt, (int64_t)tiles.size(), (int64_t)fids.size(), scratch,
+                               (int64_t)inv.size(), f12_total);
     c->device_bytes = bytes;
     if (cudaMalloc(&c->pool.base, (size_t)bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -687,6 +823,11 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
     c->stage_vals = P.take<double>(nnz);
     c->stage_b = P.take<double>(n);
     c->stage_x = P.take<double>(n);
+    int* cb_split = P.take<int>(an.ns);
+    int64_t* inv_off_d = P.take<int64_t>(an.ns);
+    int* inv_d = P.take<int>(std::max<size_t>(inv.size(), 1));
+    int64_t* f12_off_d = P.take<int64_t>(an.ns);
+    char* f12 = P.take<char>(std::max<int64_t>(f12_total, 1) * es);
     if (P.used > P.size) { kkt_destroy(c); return KKT_E_NOMEM; }
     if (cudaMallocHost(&c->pin, sizeof(double) * (4 * (kMaxRestart + 2) + 16)) != cudaSuccess) {
         cudaGetLastError();
@@ -716,6 +857,10 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
     e = e ? e : up(cb_off, an.cb_off.data(), (an.ns + 1) * 8);
     e = e ? e : up(c->fronts_dev, fids.data(), fids.size() * 4);
     e = e ? e : up(c->tiles_dev, tiles.data(), tiles.size() * sizeof(FrontTile));
+    e = e ? e : up(cb_split, an.cb_split.data(), an.ns * 4);
+    e = e ? e : up(inv_off_d, inv_off.data(), an.ns * 8);
+    e = e ? e : up(inv_d, inv.data(), inv.size() * 4);
+    e = e ? e : up(f12_off_d, f12_off.data(), an.ns * 8);
     e = e ? e : cudaMemset(c->stat, 0, sizeof(DevStat));
     if (e != cudaSuccess) { kkt_destroy(c); return KKT_E_CUDA; }
     DevSched& s = c->sched;
@@ -725,6 +870,7 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
     s.child_ptr = child_ptr; s.child_list = child_list;
     s.asm_ptr = asm_ptr; s.asm_pos = asm_pos; s.asm_src = asm_src;
     s.rel_ptr = rel_ptr; s.rel = rel; s.panel_off = panel_off; s.cb_off = cb_off;
+    s.cb_split = cb_split; s.inv_off = inv_off_d; s.inv = inv_d; s.f12_off = f12_off_d;
     double eps = c->opt.static_pivot_eps > 0 ? c->opt.static_pivot_eps
                                              : (c->opt.precision == KKT_FP32_IR ? 1e-7 : 1e-14);
     c->opt.static_pivot_eps = eps;
@@ -734,12 +880,14 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
         nm.cb = reinterpret_cast<float*>(cb); nm.vec = reinterpret_cast<float*>(vec);
         nm.cbv = reinterpret_cast<float*>(cbv); nm.stat = c->stat; nm.pivot_eps = eps; nm.d = c->d_a;
         nm.kcopy = c->kvals;
+        nm.f12 = reinterpret_cast<float*>(f12);
     } else {
         DevNum<double>& nm = c->nd;
         nm.sv = reinterpret_cast<double*>(sv); nm.panel = reinterpret_cast<double*>(panel);
         nm.cb = reinterpret_cast<double*>(cb); nm.vec = reinterpret_cast<double*>(vec);
         nm.cbv = reinterpret_cast<double*>(cbv); nm.stat = c->stat; nm.pivot_eps = eps; nm.d = c->d_a;
         nm.kcopy = c->kvals;
+        nm.f12 = reinterpret_cast<double*>(f12);
     }
     c->info.status = KKT_OK;
     *out = c;
@@ -955,7 +1103,7 @@ kkt_status kkt_export_factors(const kkt_ctx* c, int64_t* nl, int32_t* l_row, int
         int m = F - w;
         for (int a = 0; a < w; ++a)
             for (int b = 0; b < m; ++b) {
-                double v = val(off + (int64_t)F * w + (int64_t)a * m + b);
+                double v = val(off + (int64_t)F * w + a + (int64_t)b * w);
                 u_row[iu] = an.perm[R[a]]; u_col[iu] = an.perm[R[w + b]]; u_val[iu] = v; ++iu;
             }
     }
@@ -966,6 +1114,9 @@ kkt_status kkt_destroy(kkt_ctx* c)
 {
     if (!c) return KKT_OK;
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
+    if (c->g_solve) cudaGraphExecDestroy(c->g_solve);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->pool.base) cudaFree(c->pool.base);
     if (c->pin) cudaFreeHost(c->pin);
     delete c;
