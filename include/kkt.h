@@ -78,7 +78,7 @@ typedef struct {
                                    for the "small front" rule (default 16) */
     double relax_zeros;         /* amalgamation: max share of explicit zeros (default 0.15) */
     int max_pivots;             /* pivots per supernode: merges stop and larger supernodes
-                                   are split into chains at this size (default 64, max 64) */
+                                   are split into chains at this size (default 16, max 64) */
     int no_graphs;              /* 1: launch every kernel from the host instead of replaying
                                    the captured CUDA graphs of the level loops (default 0) */
 } kkt_options;

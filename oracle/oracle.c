@@ -596,8 +596,9 @@ int ora_fgmres(int n, const int *rp, const int *ci, const double *v,
  *   x_i = a_i - sum_k l_ik u_k    (m_i terms)
  *   err(x_i) <= sum_k (|l_ik| err(u_k) + err(l_ik) |u_k|)
  *               + gamma_{m_i+1} (|a_i| + sum_k |l_ik| |u_k|)
- *   u entries: err(u) = err(x);   l_ij = x_i / u_jj:
- *   err(l_ij) <= (err(x_i) + |l_ij| err(u_jj)) / |u_jj| + unit |l_ij|
+ *   u entries: err(u) = err(x);   l_ij = x_i / u_jj, formed either as a
+ *   quotient or as x_i * fl(1 / u_jj) (two roundings):
+ *   err(l_ij) <= (err(x_i) + |l_ij| err(u_jj)) / |u_jj| + 2 unit |l_ij|
  *
  * gamma_m = m unit / (1 - m unit). A perturbed pivot is an exact constant
  * (err 0; a pivot of magnitude exactly pivot_floor is taken as replaced).
@@ -647,7 +648,7 @@ void ora_lu_error_bound(const ora_lu_t *F, const int *rp, const int *ci, const d
             double l = fabs(F->Lx[t]);
             double mi = (double)(M[i] + 1);
             double ex = E[i] + (mi * unit / (1.0 - mi * unit)) * X[i];
-            eL[t] = (ex + l * eujj) / au + unit * l;
+            eL[t] = (ex + l * eujj) / au + 2.0 * unit * l;
         }
         /* reset the work arrays on this column's pattern */
         for (int s = F->Up[j]; s <= dpos; s++) { int r = F->p[F->Ui[s]]; X[r] = 0.0; E[r] = 0.0; M[r] = 0; }

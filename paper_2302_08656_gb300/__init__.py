@@ -35,7 +35,7 @@ def _check(st: int, where: str):
 
 
 def _opts(precision="fp64", ordering="mindeg", user_perm=None, static_pivot_eps=0.0, ruiz_iters=10,
-          restart=30, max_cycles=10, relax_pivots=16, relax_zeros=0.15, max_pivots=64, graphs=True):
+          restart=30, max_cycles=10, relax_pivots=16, relax_zeros=0.15, max_pivots=16, graphs=True):
     o = Options()
     lib().kkt_default_options(C.byref(o))
     o.precision = FP32_IR if precision in ("fp32", "fp32_ir", FP32_IR) else FP64

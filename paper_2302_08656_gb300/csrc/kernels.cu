@@ -283,11 +283,15 @@ __global__ void __launch_bounds__(128) front_warp_kernel(DevSched s, DevNum<T> n
         __syncwarp();
     }
     const double floor_ = nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits);
+    __shared__ T srinv[4];
     for (int p = 0; p < w; ++p) {
-        const T pv = static_pivot(Fm[p + p * F], floor_, nm.stat, lane == 0);
+        if (lane == 0) {                                          // one reciprocal per pivot
+            const T pv = static_pivot(Fm[p + p * F], floor_, nm.stat, true);
+            Fm[p + p * F] = pv;
+            srinv[wid] = T(1) / pv;
+        }
         __syncwarp();
-        if (lane == 0) Fm[p + p * F] = pv;
-        if (lane > p && lane < F) Fm[lane + p * F] /= pv;
+        if (lane > p && lane < F) Fm[lane + p * F] *= srinv[wid];
         __syncwarp();
         for (int j = p + 1 + lj; j < F; j += 4) {
             const T u = Fm[p + j * F];
@@ -340,11 +344,16 @@ __global__ void __launch_bounds__(256) front_cta_kernel(DevSched s, DevNum<T> nm
         __syncthreads();
     }
     const double floor_ = nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits);
+    __shared__ T srinv;
     for (int p = 0; p < w; ++p) {
-        const T pv = static_pivot(Fm[p + p * F], floor_, nm.stat, tid == 0);
+        if (tid == 0) {                                           // one reciprocal per pivot
+            const T pv = static_pivot(Fm[p + p * F], floor_, nm.stat, true);
+            Fm[p + p * F] = pv;
+            srinv = T(1) / pv;
+        }
         __syncthreads();
-        if (tid == 0) Fm[p + p * F] = pv;
-        for (int i = p + 1 + tid; i < F; i += nt) Fm[i + p * F] /= pv;
+        const T rinv = srinv;
+        for (int i = p + 1 + tid; i < F; i += nt) Fm[i + p * F] *= rinv;
         __syncthreads();
         for (int j = p + 1 + ty; j < F; j += 8) {
             const T u = Fm[p + j * F];
@@ -438,11 +447,16 @@ __global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> 
         __syncthreads();
     }
     const double floor_ = nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits);
+    __shared__ T srinv;
     for (int p = 0; p < w; ++p) {
-        const T pv = static_pivot(col[p + (int64_t)p * F], floor_, nm.stat, tid == 0);
+        if (tid == 0) {                                           // one reciprocal per pivot
+            const T pv = static_pivot(col[p + (int64_t)p * F], floor_, nm.stat, true);
+            col[p + (int64_t)p * F] = pv;
+            srinv = T(1) / pv;
+        }
         __syncthreads();
-        if (tid == 0) col[p + (int64_t)p * F] = pv;
-        for (int i = p + 1 + tid; i < F; i += nt) col[i + (int64_t)p * F] /= pv;
+        const T rinv = srinv;
+        for (int i = p + 1 + tid; i < F; i += nt) col[i + (int64_t)p * F] *= rinv;
         __syncthreads();
         for (int j = p + 1 + ty; j < w; j += 8) {
             const T u = col[p + (int64_t)j * F];
@@ -456,16 +470,19 @@ __global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> 
     for (int64_t t = tid; t < (int64_t)w * m; t += nt) f12[t] = row[t];
 }
 
-// One kTile x kTile tile (ti, tj) of a panel-class front's contribution block:
-// solve L11 U = F12 for the tile's kTile columns of U12 (tiles of the first
-// tile row store them), gather the children's contributions (in child order,
-// through the gather maps), then C -= L21 U12 with the terms applied in pivot
-// order, one fused multiply-add each, as the single-CTA kernels do.
+// One kTile x kTile tile (ti, tj) of a panel-class front's contribution block
+// (kTile = 16: small tiles spread a narrow level over many SMs; one output
+// per thread): solve L11 U = F12 for the tile's kTile columns of U12 (tiles
+// of the first tile row store them), gather the children's contributions (in
+// child order, through the gather maps), then C -= L21 U12 with the terms
+// applied in pivot order, one fused multiply-add each, as the single-CTA
+// kernels do.
 template <typename T>
 __global__ void __launch_bounds__(256) schur_tile_kernel(DevSched s, DevNum<T> nm, const FrontTile* __restrict__ tiles,
                                                          int count)
 {
-    constexpr int KB = 32;
+    static_assert(kTile * kTile == 256, "one output per thread");
+    constexpr int KB = 64;
     constexpr int UL = kTile + 1;                                  // padded row length of the U12 tile
     __shared__ T Ls[KB][kTile + 1];
     __shared__ int gi[kTile], gj[kTile];
@@ -477,33 +494,30 @@ __global__ void __launch_bounds__(256) schur_tile_kernel(DevSched s, DevNum<T> n
     const int m = F - w;
     const int i0 = tl.ti * kTile, j0 = tl.tj * kTile;
     const int tid = threadIdx.x;
-    const int tx = tid & 31, ty = tid >> 5;                        // 8 warps
+    const int tx = tid & (kTile - 1), ty = tid / kTile;           // output (i0 + tx, j0 + ty)
     T* L11 = reinterpret_cast<T*>(smraw);                          // w x w, column-major
     T* Ut = L11 + w * w;                                           // w x kTile, row a at Ut[a * UL]
     T* pan = nm.panel + s.panel_off[f];
     const T* L21 = pan + w;                                        // row r, col p at L21[r + p*F]
     const T* F12 = nm.f12 + s.f12_off[f];                          // w x m, column-major
-    for (int c = ty; c < w; c += 8)
-        for (int a = tx; a < w; a += 32) L11[a + c * w] = pan[a + (int64_t)c * F];
-    for (int c = ty; c < kTile; c += 8)
-        for (int a = tx; a < w; a += 32) Ut[a * UL + c] = j0 + c < m ? F12[a + (int64_t)(j0 + c) * w] : T(0);
+    for (int c = ty; c < w; c += 256 / kTile)
+        for (int a = tx; a < w; a += kTile) L11[a + c * w] = pan[a + (int64_t)c * F];
+    for (int c = ty; c < kTile; c += 256 / kTile)
+        for (int a = tx; a < w; a += kTile) Ut[a * UL + c] = j0 + c < m ? F12[a + (int64_t)(j0 + c) * w] : T(0);
     __syncthreads();
     for (int p = 0; p + 1 < w; ++p) {                              // forward substitution, unit L11
-        for (int t = tid; t < (w - p - 1) * kTile; t += 256) {
-            const int a = p + 1 + t / kTile, c = t % kTile;
-            Ut[a * UL + c] -= L11[a + p * w] * Ut[p * UL + c];
-        }
+        for (int a = p + 1 + ty; a < w; a += 256 / kTile) Ut[a * UL + tx] -= L11[a + p * w] * Ut[p * UL + tx];
         __syncthreads();
     }
     if (tl.ti == 0) {
         T* U12 = pan + (int64_t)F * w;                             // row p, col c at U12[p + c*w]
-        for (int c = ty; c < kTile; c += 8)
-            for (int a = tx; a < w; a += 32)
+        for (int c = ty; c < kTile; c += 256 / kTile)
+            for (int a = tx; a < w; a += kTile)
                 if (j0 + c < m) U12[a + (int64_t)(j0 + c) * w] = Ut[a * UL + c];
     }
     T* C = nm.cb + s.cb_off[f];
-    const int i = i0 + tx;
-    T acc[4] = {T(0), T(0), T(0), T(0)};
+    const int i = i0 + tx, j = j0 + ty;
+    T acc = T(0);
     const int* inv = s.inv + s.inv_off[f];
     for (int c = s.child_ptr[f]; c < s.child_ptr[f + 1]; ++c, inv += m) {
         const int ch = s.child_list[c];
@@ -513,35 +527,18 @@ __global__ void __launch_bounds__(256) schur_tile_kernel(DevSched s, DevNum<T> n
         if (tid < kTile) gi[tid] = i0 + tid < m ? inv[i0 + tid] : -1;
         else if (tid < 2 * kTile) gj[tid - kTile] = j0 + tid - kTile < m ? inv[j0 + tid - kTile] : -1;
         __syncthreads();
-        const int a = gi[tx];
-        if (a >= 0) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int b = gj[ty + 8 * k];
-                if (b >= 0) acc[k] += cb[a + (int64_t)b * mc];
-            }
-        }
+        const int a = gi[tx], b = gj[ty];
+        if (a >= 0 && b >= 0) acc += cb[a + (int64_t)b * mc];
     }
     for (int p0 = 0; p0 < w; p0 += KB) {
         const int kb = min(KB, w - p0);
         __syncthreads();
-        for (int t = tid; t < KB * kTile; t += 256) {
-            const int c = t / kTile, r = t % kTile;                // consecutive threads: consecutive rows of L21
-            Ls[c][r] = (c < kb && i0 + r < m) ? L21[(i0 + r) + (int64_t)(p0 + c) * F] : T(0);
-        }
+        for (int c = ty; c < kb; c += 256 / kTile)
+            Ls[c][tx] = i0 + tx < m ? L21[(i0 + tx) + (int64_t)(p0 + c) * F] : T(0);
         __syncthreads();
-        for (int c = 0; c < kb; ++c) {
-            const T l = Ls[c][tx];
-            const T* up = Ut + (p0 + c) * UL;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[k] -= l * up[ty + 8 * k];
-        }
+        for (int c = 0; c < kb; ++c) acc -= Ls[c][tx] * Ut[(p0 + c) * UL + ty];
     }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int j = j0 + ty + 8 * k;
-        if (i < m && j < m) C[i + (int64_t)j * m] = acc[k];
-    }
+    if (i < m && j < m) C[i + (int64_t)j * m] = acc;
 }
 
 // ------------------------------------------------------------ solve kernels

@@ -64,7 +64,7 @@ struct FrontTile { int front; int ti; int tj; };
 constexpr int kWarpFrontMax = 32;      // fronts with F <= 32 are handled by one warp
 constexpr int kWarpLevelMin = 608;     // ... when their level has at least 4 x 152 of them
 constexpr int kPanelCbMin = 32;        // fronts with F - w >= 32 use panel + tiled Schur update
-constexpr int kTile = 32;              // Schur update tile (kTile x kTile)
+constexpr int kTile = 16;              // Schur update tile (kTile x kTile)
 
 // Launchers (all asynchronous on `st`).
 cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double* dtmp, int iters,

@@ -126,7 +126,7 @@ void fill_defaults(kkt_options* o)
     o->max_cycles = 10;
     o->relax_pivots = 16;
     o->relax_zeros = 0.15;
-    o->max_pivots = 64;
+    o->max_pivots = 16;
     o->no_graphs = 0;
 }
 
