@@ -91,6 +91,7 @@ typedef struct {
     int refactor_count;         /* refactorizations since analyze */
     int status;                 /* kkt_status of the last numeric call (device-side checks) */
     long long launches;         /* CUDA kernels this context has launched since analyze */
+    int batch;                  /* numeric instances of the context (kkt_get_info) */
 } kkt_info;
 
 /* Per-kernel timing of a context in profiling mode (see kkt_set_profiling). */
@@ -112,7 +113,8 @@ typedef struct {
     int max_pivots;             /* most pivots in one front */
     double flops;               /* dense front flops per refactor */
     double flops_exact;         /* flops on the exact (non-amalgamated) structure */
-    int64_t device_bytes;       /* device memory kkt_analyze would allocate */
+    int64_t device_bytes;       /* device memory kkt_analyze would allocate (one instance) */
+    int batch;                  /* instances of the context (kkt_get_plan) */
 } kkt_plan_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -136,6 +138,18 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t *h_rowptr,
                        const int32_t *h_colidx, const double *h_vals,
                        const kkt_options *opt, kkt_ctx **out);
 
+/* Batched context: the analysis of kkt_analyze done once and `count` numeric
+ * instances that share it (one pattern, different values: e.g. scenarios of
+ * one grid). Every numeric call on such a context works on all instances at
+ * once -- each level of the assembly tree is one launch for all of them --
+ * with instance-major arrays: values count x nnz, right-hand sides and
+ * solutions count x n; kkt_refine and kkt_step_host fill count kkt_info
+ * entries. Factor export and scaling queries report instance 0.
+ * Errors: as kkt_analyze. */
+kkt_status kkt_analyze_batch(int32_t n, int32_t n_primal, const int32_t *h_rowptr,
+                             const int32_t *h_colidx, const kkt_options *opt, int32_t count,
+                             kkt_ctx **out);
+
 /* Numeric refactorization (Alg. 1) of the matrix with values
  * d_vals (device, nnz FP64 in the CSR order given to kkt_analyze):
  * power-of-two symmetric Ruiz equilibration D K D (FP64), scatter into the
@@ -153,9 +167,12 @@ kkt_status kkt_solve(kkt_ctx *ctx, const double *d_rhs, double *d_x, void *strea
 
 /* Solve then refine with restarted FGMRES(m) on the unscaled K, right
  * preconditioned by the factors, Arnoldi and update in FP64, until the
- * backward error omega <= tol (Alg. 1 with refinement; Sec. V).
- * Synchronizes `stream` (the restart loop reads convergence on the host).
- * info (may be NULL) receives iterations and the final omega.
+ * backward error omega <= tol (Alg. 1 with refinement; Sec. V). The
+ * backward error of every instance is evaluated on the device after the
+ * solve; FGMRES runs only for instances above tol (rel_resid2 is then set,
+ * else -1). Synchronizes `stream` (the restart loop reads convergence on the
+ * host). info (may be NULL; one entry per instance) receives iterations and
+ * the final omega.
  * Errors: KKT_E_ARG, KKT_E_STATE, KKT_E_CUDA, KKT_E_NOCONV, KKT_E_NUMERIC. */
 kkt_status kkt_refine(kkt_ctx *ctx, const double *d_rhs, double *d_x, double tol,
                       kkt_info *info, void *stream);
@@ -166,13 +183,16 @@ kkt_status kkt_refine(kkt_ctx *ctx, const double *d_rhs, double *d_x, double tol
 kkt_status kkt_step_host(kkt_ctx *ctx, const double *h_vals, const double *h_rhs,
                          double *h_x, double tol, kkt_info *info, void *stream);
 
-/* Refactor several contexts in one pass of launches (one launch per level for
- * all of them). ctxs must share one precision. Asynchronous.
+/* Refactor several different contexts (patterns and sizes may differ) at
+ * once: each context works on its own internal stream, forked from `stream`
+ * and joined back into it, so their level graphs run concurrently on the
+ * device. ctxs must be distinct and share one precision. Asynchronous.
  * Errors: KKT_E_ARG, KKT_E_CUDA. */
 kkt_status kkt_refactor_batched(kkt_ctx *const *ctxs, const double *const *d_vals,
                                 int count, void *stream);
 
-/* Batched kkt_solve over contexts of one precision. Asynchronous. */
+/* kkt_solve over several distinct contexts, concurrently as above.
+ * Asynchronous. */
 kkt_status kkt_solve_batched(kkt_ctx *const *ctxs, const double *const *d_rhs,
                              double *const *d_x, int count, void *stream);
 

@@ -82,16 +82,24 @@ def plan(rowptr, colidx, **opts) -> dict:
 class KKTSolver:
     """One analysed KKT pattern with its device-resident factors."""
 
-    def __init__(self, rowptr, colidx, n_primal: int = 0, **opts):
+    def __init__(self, rowptr, colidx, n_primal: int = 0, count: int = 1, **opts):
+        """count > 1: a batched context, `count` instances of this pattern
+        (arrays are then instance-major: count x nnz values, count x n vectors)."""
         self._rp = np.ascontiguousarray(rowptr, dtype=np.int32)
         self._ci = np.ascontiguousarray(colidx, dtype=np.int32)
         self.n = self._rp.size - 1
         self.nnz = int(self._rp[-1])
+        self.count = int(count)
         o, keep = _opts(**opts)
         self.precision = "fp32" if o.precision == FP32_IR else "fp64"
         h = C.c_void_p()
-        _check(lib().kkt_analyze(self.n, int(n_primal), self._rp.ctypes.data, self._ci.ctypes.data, None,
-                                 C.byref(o), C.byref(h)), "kkt_analyze")
+        if self.count == 1:
+            st = lib().kkt_analyze(self.n, int(n_primal), self._rp.ctypes.data, self._ci.ctypes.data, None,
+                                   C.byref(o), C.byref(h))
+        else:
+            st = lib().kkt_analyze_batch(self.n, int(n_primal), self._rp.ctypes.data, self._ci.ctypes.data,
+                                         C.byref(o), self.count, C.byref(h))
+        _check(st, "kkt_analyze")
         self._h = h
 
     @property
@@ -111,12 +119,14 @@ class KKTSolver:
 
     # -- numeric stages ---------------------------------------------------
     def refactor(self, vals, stream=None):
-        assert vals.is_cuda and vals.dtype.itemsize == 8 and vals.numel() == self.nnz and vals.is_contiguous()
+        assert vals.is_cuda and vals.dtype.itemsize == 8 and vals.numel() == self.nnz * self.count
+        assert vals.is_contiguous()
         _check(lib().kkt_refactor(self._h, _ptr(vals), _stream(stream)), "kkt_refactor")
 
     def solve(self, rhs, out=None, stream=None):
         import torch
-        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n and rhs.is_contiguous()
+        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n * self.count
+        assert rhs.is_contiguous()
         if out is None:
             out = torch.empty_like(rhs)
         _check(lib().kkt_solve(self._h, _ptr(rhs), _ptr(out), _stream(stream)), "kkt_solve")
@@ -124,25 +134,26 @@ class KKTSolver:
 
     def refine(self, rhs, out=None, tol=1e-10, stream=None, raise_on_noconv=True):
         import torch
-        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n and rhs.is_contiguous()
+        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n * self.count
+        assert rhs.is_contiguous()
         if out is None:
             out = torch.empty_like(rhs)
-        info = Info()
-        st = lib().kkt_refine(self._h, _ptr(rhs), _ptr(out), float(tol), C.byref(info), _stream(stream))
+        infos = (Info * self.count)()
+        st = lib().kkt_refine(self._h, _ptr(rhs), _ptr(out), float(tol), infos, _stream(stream))
         if st != 6 or raise_on_noconv:
             _check(st, "kkt_refine")
-        return out, info
+        return out, (infos[0] if self.count == 1 else list(infos))
 
     def step_host(self, vals, rhs, tol=1e-10, out=None, stream=None):
         """Refactor + refine through host buffers (copies inside the call)."""
         v = np.ascontiguousarray(vals, dtype=np.float64)
         b = np.ascontiguousarray(rhs, dtype=np.float64)
-        x = np.empty(self.n) if out is None else out
-        info = Info()
+        x = np.empty(self.n * self.count) if out is None else out
+        infos = (Info * self.count)()
         st = lib().kkt_step_host(self._h, v.ctypes.data, b.ctypes.data, x.ctypes.data, float(tol),
-                                 C.byref(info), _stream(stream))
+                                 infos, _stream(stream))
         _check(st, "kkt_step_host")
-        return x, info
+        return x, (infos[0] if self.count == 1 else list(infos))
 
     def residual(self, rhs, x, out=None, stream=None):
         import torch

@@ -92,6 +92,7 @@ class Info(C.Structure):
         ("refactor_count", C.c_int),
         ("status", C.c_int),
         ("launches", C.c_longlong),
+        ("batch", C.c_int),
     ]
 
 
@@ -112,6 +113,7 @@ class PlanInfo(C.Structure):
         ("flops", C.c_double),
         ("flops_exact", C.c_double),
         ("device_bytes", C.c_int64),
+        ("batch", C.c_int),
     ]
 
 
@@ -121,10 +123,11 @@ SIGNATURES = {
     "kkt_default_options": (None, [C.POINTER(Options)]),
     "kkt_plan": (C.c_int, [C.c_int32, _P, _P, C.POINTER(Options), C.POINTER(PlanInfo)]),
     "kkt_analyze": (C.c_int, [C.c_int32, C.c_int32, _P, _P, _P, C.POINTER(Options), C.POINTER(_P)]),
+    "kkt_analyze_batch": (C.c_int, [C.c_int32, C.c_int32, _P, _P, C.POINTER(Options), C.c_int32, C.POINTER(_P)]),
     "kkt_refactor": (C.c_int, [_P, _P, _P]),
     "kkt_solve": (C.c_int, [_P, _P, _P, _P]),
-    "kkt_refine": (C.c_int, [_P, _P, _P, C.c_double, C.POINTER(Info), _P]),
-    "kkt_step_host": (C.c_int, [_P, _P, _P, _P, C.c_double, C.POINTER(Info), _P]),
+    "kkt_refine": (C.c_int, [_P, _P, _P, C.c_double, _P, _P]),
+    "kkt_step_host": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
     "kkt_refactor_batched": (C.c_int, [_P, _P, C.c_int, _P]),
     "kkt_solve_batched": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "kkt_residual": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_double), _P]),

@@ -141,11 +141,17 @@ __device__ __forceinline__ unsigned long long group_max_u64(unsigned long long v
 // Integer-only iteration: every d is a power of two, so |d_i k_ij d_j| is
 // |k_ij| with its exponent raised by e_i + e_j, and the row maximum of
 // non-negative doubles is the maximum of their bit patterns.
-__global__ void __launch_bounds__(256) ruiz_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                   const double* __restrict__ v, const double* __restrict__ din,
-                                                   double* __restrict__ dout, const int* changed_prev,
-                                                   int* changed_cur)
+__global__ void __launch_bounds__(256) ruiz_kernel(int n, int64_t nnz, const int* __restrict__ rp,
+                                                   const int* __restrict__ ci, const double* __restrict__ v,
+                                                   const double* __restrict__ din, double* __restrict__ dout,
+                                                   DevStat* stat, int it)
 {
+    // instance blockIdx.y of a batch
+    v += (int64_t)blockIdx.y * nnz;
+    din += (int64_t)blockIdx.y * n;
+    dout += (int64_t)blockIdx.y * n;
+    const int* changed_prev = it > 0 ? &stat[blockIdx.y].ruiz_changed[it - 1] : nullptr;
+    int* changed_cur = &stat[blockIdx.y].ruiz_changed[it];
     __shared__ int s_skip;
     if (threadIdx.x == 0) s_skip = changed_prev ? (*changed_prev == 0) : 0;   // one read per block
     __syncthreads();
@@ -183,9 +189,14 @@ __global__ void __launch_bounds__(256) ruiz_kernel(int n, const int* __restrict_
 // (static-pivot reference) and ||K||_inf.
 template <typename T>
 __global__ void __launch_bounds__(256) scale_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                    const double* __restrict__ v, const double* __restrict__ d,
-                                                    T* __restrict__ sv, double* __restrict__ kcopy, DevStat* stat)
+                                                    DevNum<T> nm0)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
+    const double* __restrict__ v = nm.vals;
+    const double* __restrict__ d = nm.d;
+    T* __restrict__ sv = nm.sv;
+    double* __restrict__ kcopy = nm.kcopy;
+    DevStat* stat = nm.stat;
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
     const int sub = threadIdx.x % kRowLanes;
     const int lane = threadIdx.x & 31;
@@ -251,9 +262,10 @@ __device__ __forceinline__ void assemble_original(const DevSched& s, const DevNu
 // Fronts with F <= 32: one warp per front, the whole front in shared memory.
 // Lanes form an 8 x 4 grid over (row, column) of every block loop.
 template <typename T>
-__global__ void __launch_bounds__(128) front_warp_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
+__global__ void __launch_bounds__(128) front_warp_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
                                                          int count)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
     __shared__ T sm[4][kWarpFrontMax * kWarpFrontMax];
     __shared__ int srl[4][kWarpFrontMax];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -314,9 +326,10 @@ __global__ void __launch_bounds__(128) front_warp_kernel(DevSched s, DevNum<T> n
 // front, the whole front in shared memory, right-looking rank-1 updates.
 // Threads form a 32 x 8 grid: lane -> row, warp -> column.
 template <typename T>
-__global__ void __launch_bounds__(256) front_cta_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
+__global__ void __launch_bounds__(256) front_cta_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
                                                         int count, int max_front)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
     extern __shared__ __align__(16) unsigned char smraw[];
     T* Fm = reinterpret_cast<T*>(smraw);
     int* rls = reinterpret_cast<int*>(Fm + (int64_t)max_front * max_front);   // staged relative indices
@@ -380,9 +393,10 @@ __global__ void __launch_bounds__(256) front_cta_kernel(DevSched s, DevNum<T> nm
 // The assembled pivot rows F12 go to scratch: schur_tile_kernel turns them into
 // U12 = L11^{-1} F12 and updates the (2,2) block, spread over many CTAs.
 template <typename T>
-__global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
+__global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
                                                           int count, T* gscratch, int64_t sstride)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
     extern __shared__ __align__(16) unsigned char smraw[];
     const int tid = threadIdx.x, nt = blockDim.x;
     const int tx = tid & 31, ty = tid >> 5;
@@ -391,7 +405,8 @@ __global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> 
     const int w = s.sn_first[f + 1] - first;
     const int F = s.sn_front[f];
     const int m = F - w;
-    T* col = gscratch ? gscratch + (int64_t)blockIdx.x * sstride : reinterpret_cast<T*>(smraw);
+    T* col = gscratch ? gscratch + ((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * sstride
+                      : reinterpret_cast<T*>(smraw);
     T* row = col + (int64_t)F * w;                                   // w x m, column-major (ld = w)
     for (int64_t t = tid; t < (int64_t)F * w + (int64_t)w * m; t += nt) col[t] = T(0);
     __syncthreads();
@@ -478,9 +493,10 @@ __global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> 
 // applied in pivot order, one fused multiply-add each, as the single-CTA
 // kernels do.
 template <typename T>
-__global__ void __launch_bounds__(256) schur_tile_kernel(DevSched s, DevNum<T> nm, const FrontTile* __restrict__ tiles,
+__global__ void __launch_bounds__(256) schur_tile_kernel(DevSched s, DevNum<T> nm0, const FrontTile* __restrict__ tiles,
                                                          int count)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
     static_assert(kTile * kTile == 256, "one output per thread");
     constexpr int KB = 64;
     constexpr int UL = kTile + 1;                                  // padded row length of the U12 tile
@@ -544,9 +560,12 @@ __global__ void __launch_bounds__(256) schur_tile_kernel(DevSched s, DevNum<T> n
 // ------------------------------------------------------------ solve kernels
 
 template <typename T>
-__global__ void solve_pre_kernel(int n, const int* __restrict__ perm, const double* __restrict__ d,
-                                 const double* __restrict__ b, T* __restrict__ vec)
+__global__ void solve_pre_kernel(int n, const int* __restrict__ perm, DevNum<T> nm0, const double* __restrict__ b)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
+    const double* __restrict__ d = nm.d;
+    T* __restrict__ vec = nm.vec;
+    b += (int64_t)blockIdx.y * n;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) {
         int o = perm[k];
@@ -555,9 +574,12 @@ __global__ void solve_pre_kernel(int n, const int* __restrict__ perm, const doub
 }
 
 template <typename T>
-__global__ void solve_post_kernel(int n, const int* __restrict__ perm, const double* __restrict__ d,
-                                  const T* __restrict__ vec, double* __restrict__ x)
+__global__ void solve_post_kernel(int n, const int* __restrict__ perm, DevNum<T> nm0, double* __restrict__ x)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
+    const double* __restrict__ d = nm.d;
+    const T* __restrict__ vec = nm.vec;
+    x += (int64_t)blockIdx.y * n;
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) {
         int o = perm[k];
@@ -571,9 +593,10 @@ __global__ void solve_post_kernel(int n, const int* __restrict__ perm, const dou
 // other rows with L21 (lane per row, coalesced column reads) and leaves them as
 // its own contribution vector.
 template <typename T>
-__global__ void __launch_bounds__(128) solve_fwd_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
+__global__ void __launch_bounds__(128) solve_fwd_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
                                                         int count, int max_front, int max_w)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
     extern __shared__ __align__(16) unsigned char smraw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int fi = blockIdx.x * 4 + wid;
@@ -618,9 +641,10 @@ __global__ void __launch_bounds__(128) solve_fwd_kernel(DevSched s, DevNum<T> nm
 // pivot row, coalesced reads of the column-major U12), and back-substitutes
 // with its upper pivot block staged in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(128) solve_bwd_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
+__global__ void __launch_bounds__(128) solve_bwd_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
                                                         int count, int max_front, int max_w)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
     extern __shared__ __align__(16) unsigned char smraw[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int fi = blockIdx.x * 4 + wid;
@@ -659,9 +683,10 @@ __global__ void __launch_bounds__(128) solve_bwd_kernel(DevSched s, DevNum<T> nm
 // front: one warp does the sequential pivot block, all threads the L21 / U12
 // products.
 template <typename T>
-__global__ void __launch_bounds__(128) solve_fwd_cta_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
+__global__ void __launch_bounds__(128) solve_fwd_cta_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
                                                             int count, int max_front, int max_w)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
     extern __shared__ __align__(16) unsigned char smraw[];
     const int tid = threadIdx.x, lane = tid & 31;
     T* v = reinterpret_cast<T*>(smraw);
@@ -703,9 +728,10 @@ __global__ void __launch_bounds__(128) solve_fwd_cta_kernel(DevSched s, DevNum<T
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) solve_bwd_cta_kernel(DevSched s, DevNum<T> nm, const int* __restrict__ fronts,
+__global__ void __launch_bounds__(128) solve_bwd_cta_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
                                                             int count, int max_front, int max_w)
 {
+    const DevNum<T> nm = nm0.at(blockIdx.y);
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ T red[128];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -869,15 +895,14 @@ cudaError_t launch_zero_stat(DevStat* stat, cudaStream_t st)
 }
 
 cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double* dtmp, int iters,
-                        DevStat* stat, double** d_final, cudaStream_t st)
+                        DevStat* stat, double** d_final, int batch, cudaStream_t st)
 {
-    fill_kernel<<<cdiv(s.n, 256), 256, 0, st>>>(s.n, d, 1.0);
+    fill_kernel<<<cdiv((int64_t)s.n * batch, 256), 256, 0, st>>>((int)((int64_t)s.n * batch), d, 1.0);
     double* a = d;
     double* b = dtmp;
     for (int it = 0; it < iters; ++it) {
-        ruiz_kernel<<<cdiv((int64_t)s.n * kRowLanes, 256), 256, 0, st>>>(
-            s.n, s.rowptr, s.colidx, vals, a, b, it > 0 ? &stat->ruiz_changed[it - 1] : nullptr,
-            &stat->ruiz_changed[it]);
+        ruiz_kernel<<<dim3(cdiv((int64_t)s.n * kRowLanes, 256), batch), 256, 0, st>>>(
+            s.n, s.nnz, s.rowptr, s.colidx, vals, a, b, stat, it);
         double* t = a; a = b; b = t;
     }
     *d_final = a;
@@ -885,102 +910,103 @@ cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double
 }
 
 template <typename T>
-cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d, cudaStream_t st)
+cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d, int batch, cudaStream_t st)
 {
-    scale_kernel<T><<<cdiv((int64_t)s.n * kRowLanes, 256), 256, 0, st>>>(s.n, s.rowptr, s.colidx, nm.vals, d, nm.sv,
-                                                                   nm.kcopy, nm.stat);
+    (void)d;
+    scale_kernel<T><<<dim3(cdiv((int64_t)s.n * kRowLanes, 256), batch), 256, 0, st>>>(s.n, s.rowptr, s.colidx, nm);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, cudaStream_t st)
+cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int batch,
+                               cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    front_warp_kernel<T><<<cdiv(count, 4), 128, 0, st>>>(s, nm, fronts, count);
+    front_warp_kernel<T><<<dim3(cdiv(count, 4), batch), 128, 0, st>>>(s, nm, fronts, count);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fronts_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
-                              cudaStream_t st)
+                              int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     size_t smem = (size_t)max_front * max_front * sizeof(T) + (size_t)max_front * sizeof(int);
-    front_cta_kernel<T><<<count, 256, smem, st>>>(s, nm, fronts, count, max_front);
+    front_cta_kernel<T><<<dim3(count, batch), 256, smem, st>>>(s, nm, fronts, count, max_front);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fronts_panel(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                                size_t smem_bytes, T* gscratch, int64_t scratch_stride, cudaStream_t st)
+                                size_t smem_bytes, T* gscratch, int64_t scratch_stride, int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    front_panel_kernel<T><<<count, 256, gscratch ? 0 : smem_bytes, st>>>(s, nm, fronts, count, gscratch,
-                                                                          scratch_stride);
+    front_panel_kernel<T><<<dim3(count, batch), 256, gscratch ? 0 : smem_bytes, st>>>(s, nm, fronts, count, gscratch,
+                                                                                      scratch_stride);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_schur_tiles(const DevSched& s, const DevNum<T>& nm, const FrontTile* tiles, int count,
-                               int max_w, cudaStream_t st)
+                               int max_w, int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     const size_t smem = (size_t)(max_w * max_w + max_w * (kTile + 1)) * sizeof(T);
-    schur_tile_kernel<T><<<count, 256, smem, st>>>(s, nm, tiles, count);
+    schur_tile_kernel<T><<<dim3(count, batch), 256, smem, st>>>(s, nm, tiles, count);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_solve_pre(const DevSched& s, const DevNum<T>& nm, const double* b, cudaStream_t st)
+cudaError_t launch_solve_pre(const DevSched& s, const DevNum<T>& nm, const double* b, int batch, cudaStream_t st)
 {
-    solve_pre_kernel<T><<<cdiv(s.n, 256), 256, 0, st>>>(s.n, s.perm, nm.d, b, nm.vec);
+    solve_pre_kernel<T><<<dim3(cdiv(s.n, 256), batch), 256, 0, st>>>(s.n, s.perm, nm, b);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_solve_post(const DevSched& s, const DevNum<T>& nm, double* x, cudaStream_t st)
+cudaError_t launch_solve_post(const DevSched& s, const DevNum<T>& nm, double* x, int batch, cudaStream_t st)
 {
-    solve_post_kernel<T><<<cdiv(s.n, 256), 256, 0, st>>>(s.n, s.perm, nm.d, nm.vec, x);
+    solve_post_kernel<T><<<dim3(cdiv(s.n, 256), batch), 256, 0, st>>>(s.n, s.perm, nm, x);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_solve_fwd(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
-                             int max_w, cudaStream_t st)
+                             int max_w, int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     const size_t smem = 4 * (size_t)(max_front + max_w * max_w) * sizeof(T);
-    solve_fwd_kernel<T><<<cdiv(count, 4), 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
+    solve_fwd_kernel<T><<<dim3(cdiv(count, 4), batch), 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_solve_bwd(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
-                             int max_w, cudaStream_t st)
+                             int max_w, int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     const size_t smem = 4 * (size_t)(max_front + max_w * max_w) * sizeof(T);
-    solve_bwd_kernel<T><<<cdiv(count, 4), 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
+    solve_bwd_kernel<T><<<dim3(cdiv(count, 4), batch), 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_solve_fwd_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
-                                 int max_w, cudaStream_t st)
+                                 int max_w, int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     const size_t smem = (size_t)(max_front + max_w * max_w) * sizeof(T);
-    solve_fwd_cta_kernel<T><<<count, 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
+    solve_fwd_cta_kernel<T><<<dim3(count, batch), 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_solve_bwd_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
-                                 int max_w, cudaStream_t st)
+                                 int max_w, int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     const size_t smem = (size_t)(max_front + max_w * max_w) * sizeof(T);
-    solve_bwd_cta_kernel<T><<<count, 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
+    solve_bwd_cta_kernel<T><<<dim3(count, batch), 128, smem, st>>>(s, nm, fronts, count, max_front, max_w);
     return cudaGetLastError();
 }
 
@@ -1037,26 +1063,98 @@ cudaError_t launch_norms(int n, const double* a, double* out, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Batched residual and backward error: grid (ceil(n / 1024), batch), one
+// warp per row; each block stores max |r|, |x|, |b| and the largest K row sum
+// of its rows in its slot of `part`; omega_final_batched reduces the slots.
+__global__ void __launch_bounds__(256) resid_omega_part_kernel(int n, int64_t nnz, const int* __restrict__ rp,
+                                                               const int* __restrict__ ci,
+                                                               const double* __restrict__ kv,
+                                                               const double* __restrict__ x,
+                                                               const double* __restrict__ b, double* __restrict__ r,
+                                                               double* __restrict__ part)
+{
+    __shared__ double red[4][8];
+    const int inst = blockIdx.y;
+    kv += (int64_t)inst * nnz;
+    x += (int64_t)inst * n;
+    b += (int64_t)inst * n;
+    r += (int64_t)inst * n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int row0 = blockIdx.x * 1024, row1 = min(n, row0 + 1024);
+    double mr = 0.0, mx = 0.0, mb = 0.0, mk = 0.0;
+    for (int row = row0 + wid; row < row1; row += 8) {
+        double sacc = 0.0, a = 0.0;
+        for (int p = rp[row] + lane; p < rp[row + 1]; p += 32) {
+            sacc += kv[p] * x[ci[p]];
+            a += fabs(kv[p]);
+        }
+        sacc = warp_sum(sacc);
+        a = warp_sum(a);
+        const double ri = b[row] - sacc;
+        if (lane == 0) r[row] = ri;
+        mr = fmax(mr, fabs(ri));
+        mx = fmax(mx, fabs(x[row]));
+        mb = fmax(mb, fabs(b[row]));
+        mk = fmax(mk, a);
+    }
+    if (lane == 0) { red[0][wid] = mr; red[1][wid] = mx; red[2][wid] = mb; red[3][wid] = mk; }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double m = 0.0;
+        for (int q = 0; q < 8; ++q) m = fmax(m, red[threadIdx.x][q]);
+        part[((int64_t)inst * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = m;
+    }
+}
+
+__global__ void omega_final_batched_kernel(int nblk, const double* __restrict__ part, double* __restrict__ omega)
+{
+    const int inst = blockIdx.x;
+    const double* pp = part + (int64_t)inst * nblk * 4;
+    double mr = 0.0, mx = 0.0, mb = 0.0, mk = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += 32) {
+        mr = fmax(mr, pp[4 * i + 0]);
+        mx = fmax(mx, pp[4 * i + 1]);
+        mb = fmax(mb, pp[4 * i + 2]);
+        mk = fmax(mk, pp[4 * i + 3]);
+    }
+    mr = warp_max(mr); mx = warp_max(mx); mb = warp_max(mb); mk = warp_max(mk);
+    if (threadIdx.x == 0) {
+        const double den = mk * mx + mb;
+        omega[inst] = den > 0.0 ? mr / den : mr;
+    }
+}
+
+cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci, const double* kvals,
+                               const double* x, const double* b, double* r, double* part, double* omega,
+                               int batch, cudaStream_t st)
+{
+    const int nblk = cdiv(n, 1024);
+    resid_omega_part_kernel<<<dim3(nblk, batch), 256, 0, st>>>(n, nnz, rp, ci, kvals, x, b, r, part);
+    omega_final_batched_kernel<<<batch, 32, 0, st>>>(nblk, part, omega);
+    return cudaGetLastError();
+}
+
 // explicit instantiations
 #define KKT_INST(T)                                                                                              \
-    template cudaError_t launch_scale<T>(const DevSched&, const DevNum<T>&, const double*, cudaStream_t);        \
-    template cudaError_t launch_fronts_warp<T>(const DevSched&, const DevNum<T>&, const int*, int, cudaStream_t); \
-    template cudaError_t launch_fronts_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int,           \
+    template cudaError_t launch_scale<T>(const DevSched&, const DevNum<T>&, const double*, int, cudaStream_t);   \
+    template cudaError_t launch_fronts_warp<T>(const DevSched&, const DevNum<T>&, const int*, int, int,          \
+                                               cudaStream_t);                                                    \
+    template cudaError_t launch_fronts_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,      \
                                               cudaStream_t);                                                     \
     template cudaError_t launch_fronts_panel<T>(const DevSched&, const DevNum<T>&, const int*, int, size_t, T*,  \
-                                                int64_t, cudaStream_t);                                          \
+                                                int64_t, int, cudaStream_t);                                     \
     template cudaError_t launch_schur_tiles<T>(const DevSched&, const DevNum<T>&, const FrontTile*, int, int,    \
-                                               cudaStream_t);                                                    \
-    template cudaError_t launch_solve_pre<T>(const DevSched&, const DevNum<T>&, const double*, cudaStream_t);    \
-    template cudaError_t launch_solve_post<T>(const DevSched&, const DevNum<T>&, double*, cudaStream_t);         \
-    template cudaError_t launch_solve_fwd<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,       \
+                                               int, cudaStream_t);                                               \
+    template cudaError_t launch_solve_pre<T>(const DevSched&, const DevNum<T>&, const double*, int, cudaStream_t); \
+    template cudaError_t launch_solve_post<T>(const DevSched&, const DevNum<T>&, double*, int, cudaStream_t);    \
+    template cudaError_t launch_solve_fwd<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int, int,  \
                                              cudaStream_t);                                                      \
-    template cudaError_t launch_solve_bwd<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,       \
+    template cudaError_t launch_solve_bwd<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int, int,  \
                                              cudaStream_t);                                                      \
     template cudaError_t launch_solve_fwd_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,   \
-                                                 cudaStream_t);                                                  \
+                                                 int, cudaStream_t);                                             \
     template cudaError_t launch_solve_bwd_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,   \
-                                                 cudaStream_t);
+                                                 int, cudaStream_t);
 KKT_INST(double)
 KKT_INST(float)
 

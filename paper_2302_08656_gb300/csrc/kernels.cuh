@@ -56,6 +56,26 @@ struct DevNum {
     T* f12 = nullptr;                 // assembled pivot rows of panel-class fronts
     DevStat* stat = nullptr;
     double pivot_eps = 1e-14;
+    // element strides between consecutive instances of a batch (0 for one instance)
+    int64_t bs_nnz = 0, bs_n = 0, bs_panel = 0, bs_cb = 0, bs_cbv = 0, bs_f12 = 0;
+    __host__ __device__ DevNum at(int b) const
+    {
+        DevNum r = *this;
+        if (b) {
+            r.vals += b * bs_nnz;
+            r.kcopy += b * bs_nnz;
+            r.d += b * bs_n;
+            r.dtmp += b * bs_n;
+            r.sv += b * bs_nnz;
+            r.panel += b * bs_panel;
+            r.cb += b * bs_cb;
+            r.vec += b * bs_n;
+            r.cbv += b * bs_cbv;
+            r.f12 += b * bs_f12;
+            r.stat += b;
+        }
+        return r;
+    }
 };
 
 // One launch group: the fronts of one level of one context.
@@ -68,37 +88,42 @@ constexpr int kTile = 16;              // Schur update tile (kTile x kTile)
 
 // Launchers (all asynchronous on `st`).
 cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double* dtmp, int iters,
-                        DevStat* stat, double** d_final, cudaStream_t st);
+                        DevStat* stat, double** d_final, int batch, cudaStream_t st);
 template <typename T>
-cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d, cudaStream_t st);
+cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                               cudaStream_t st);
+                               int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fronts_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                              int max_front, cudaStream_t st);
+                              int max_front, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fronts_panel(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                                size_t smem_bytes, T* gscratch, int64_t scratch_stride, cudaStream_t st);
+                                size_t smem_bytes, T* gscratch, int64_t scratch_stride, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_schur_tiles(const DevSched& s, const DevNum<T>& nm, const FrontTile* tiles, int count,
-                               int max_w, cudaStream_t st);
+                               int max_w, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_fwd_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                                 int max_front, int max_w, cudaStream_t st);
+                                 int max_front, int max_w, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_bwd_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                                 int max_front, int max_w, cudaStream_t st);
+                                 int max_front, int max_w, int batch, cudaStream_t st);
 template <typename T>
-cudaError_t launch_solve_pre(const DevSched& s, const DevNum<T>& nm, const double* b, cudaStream_t st);
+cudaError_t launch_solve_pre(const DevSched& s, const DevNum<T>& nm, const double* b, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_fwd(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                             int max_front, int max_w, cudaStream_t st);
+                             int max_front, int max_w, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_bwd(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                             int max_front, int max_w, cudaStream_t st);
+                             int max_front, int max_w, int batch, cudaStream_t st);
 template <typename T>
-cudaError_t launch_solve_post(const DevSched& s, const DevNum<T>& nm, double* x, cudaStream_t st);
+cudaError_t launch_solve_post(const DevSched& s, const DevNum<T>& nm, double* x, int batch, cudaStream_t st);
+// per instance: r = b - K x, omega = ||r||_inf / (||K||_inf ||x||_inf + ||b||_inf) into omega[b];
+// part holds batch * ceil(n / 1024) * 4 doubles
+cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci, const double* kvals,
+                               const double* x, const double* b, double* r, double* part, double* omega,
+                               int batch, cudaStream_t st);
 
 // FP64 vector kernels for the residual and FGMRES.
 cudaError_t launch_spmv_resid(int n, const int* rp, const int* ci, const double* v, const double* x,

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
@@ -56,6 +57,7 @@ struct kkt_ctx {
     kkt_options opt;
     Analysis an;
     int n = 0, n_primal = 0;
+    int batch = 1;                   // numeric instances sharing this analysis
     int64_t nnz = 0;
     std::vector<LevelGroup> levels;
     int64_t scratch_stride = 0;      // panel scratch per CTA (global fallback)
@@ -84,6 +86,13 @@ struct kkt_ctx {
     double* stage_b = nullptr;
     double* stage_x = nullptr;
     double* pin = nullptr;           // pinned host mirror of small results
+    double* omega_part = nullptr;    // batched backward error: partial maxima and results
+    double* r_batch = nullptr;       // residual vectors of all instances
+    double* omega_dev = nullptr;
+    double* omega_pin = nullptr;
+    cudaStream_t work_stream = nullptr;   // own stream for concurrent multi-context batches
+    cudaEvent_t done_event = nullptr;
+    std::vector<kkt_info> infos;     // per instance
     // launch accounting and optional per-kernel timing
     long long launches = 0;
     int profile = 0;
@@ -339,31 +348,32 @@ template <typename T>
 kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st)
 {
     const int* fr = c->fronts_dev;
+    const int B = c->batch;
     for (const LevelGroup& g : c->levels) {
         if (g.warp_cnt) {
             Launch L(c, st, KK_FRONT_WARP, 1);
-            KKT_CUDA(launch_fronts_warp<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, st));
+            KKT_CUDA(launch_fronts_warp<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, B, st));
         }
         if (g.cta_cnt) {
             Launch L(c, st, KK_FRONT_CTA, 1);
-            KKT_CUDA(launch_fronts_cta<T>(c->sched, nm, fr + g.cta_off, g.cta_cnt, g.cta_maxF, st));
+            KKT_CUDA(launch_fronts_cta<T>(c->sched, nm, fr + g.cta_off, g.cta_cnt, g.cta_maxF, B, st));
         }
         if (g.panel_cnt) {
             {
                 Launch L(c, st, KK_FRONT_PANEL, 1);
                 KKT_CUDA(launch_fronts_panel<T>(c->sched, nm, fr + g.panel_off, g.panel_cnt, g.panel_smem,
                                                 g.panel_global ? reinterpret_cast<T*>(c->panel_scratch) : nullptr,
-                                                c->scratch_stride, st));
+                                                c->scratch_stride, B, st));
             }
             Launch L(c, st, KK_SCHUR, 1);
-            KKT_CUDA(launch_schur_tiles<T>(c->sched, nm, c->tiles_dev + g.tile_off, g.tile_cnt, g.panel_maxW, st));
+            KKT_CUDA(launch_schur_tiles<T>(c->sched, nm, c->tiles_dev + g.tile_off, g.tile_cnt, g.panel_maxW, B, st));
         }
     }
     return KKT_OK;
 }
 
 template <typename T>
-kkt_status solve_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st)
+kkt_status solve_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st)
 {
     const int* fr = c->fronts_dev;
     // fronts with F <= 32: a warp each; larger ones (the CTA and panel classes,
@@ -373,11 +383,11 @@ kkt_status solve_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st)
         const int nbig = g.cta_cnt + g.panel_cnt;
         if (g.warp_cnt) {
             Launch L(c, st, KK_SOLVE_FWD, 1);
-            KKT_CUDA(launch_solve_fwd<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, g.small_maxW, st));
+            KKT_CUDA(launch_solve_fwd<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, g.small_maxW, B, st));
         }
         if (nbig) {
             Launch L(c, st, KK_SOLVE_FWD, 1);
-            KKT_CUDA(launch_solve_fwd_cta<T>(c->sched, nm, fr + g.cta_off, nbig, g.big_maxF, g.big_maxW, st));
+            KKT_CUDA(launch_solve_fwd_cta<T>(c->sched, nm, fr + g.cta_off, nbig, g.big_maxF, g.big_maxW, B, st));
         }
     }
     for (size_t l = c->levels.size(); l-- > 0;) {
@@ -385,11 +395,11 @@ kkt_status solve_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st)
         const int nbig = g.cta_cnt + g.panel_cnt;
         if (g.warp_cnt) {
             Launch L(c, st, KK_SOLVE_BWD, 1);
-            KKT_CUDA(launch_solve_bwd<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, g.small_maxW, st));
+            KKT_CUDA(launch_solve_bwd<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, g.small_maxW, B, st));
         }
         if (nbig) {
             Launch L(c, st, KK_SOLVE_BWD, 1);
-            KKT_CUDA(launch_solve_bwd_cta<T>(c->sched, nm, fr + g.cta_off, nbig, g.big_maxF, g.big_maxW, st));
+            KKT_CUDA(launch_solve_bwd_cta<T>(c->sched, nm, fr + g.cta_off, nbig, g.big_maxF, g.big_maxW, B, st));
         }
     }
     return KKT_OK;
@@ -400,17 +410,17 @@ kkt_status refactor_t(kkt_ctx* c, const double* d_vals, cudaStream_t st)
 {
     DevNum<T>& nm = num_of<T>(c);
     nm.vals = d_vals;
-    KKT_CUDA(launch_zero_stat(c->stat, st));
+    KKT_CUDA(cudaMemsetAsync(c->stat, 0, sizeof(DevStat) * c->batch, st));
     double* dfin = nullptr;
     {
         Launch L(c, st, KK_RUIZ, 1 + c->opt.ruiz_iters);
-        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->d_a, c->d_b, c->opt.ruiz_iters, c->stat, &dfin, st));
+        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->d_a, c->d_b, c->opt.ruiz_iters, c->stat, &dfin, c->batch, st));
     }
     c->d_final = dfin;
     nm.d = dfin;
     {
         Launch L(c, st, KK_SCALE, 1);
-        KKT_CUDA(launch_scale<T>(c->sched, nm, dfin, st));
+        KKT_CUDA(launch_scale<T>(c->sched, nm, dfin, c->batch, st));
     }
     if (!c->profile && !c->opt.no_graphs) {
         if (!c->g_factor) {
@@ -425,29 +435,32 @@ kkt_status refactor_t(kkt_ctx* c, const double* d_vals, cudaStream_t st)
     return factor_levels<T>(c, nm, st);
 }
 
+// Solve every instance (captured graph of the level loops), or only instance
+// `inst` (direct launches; b and x then point at that instance's vectors).
 template <typename T>
-kkt_status solve_t(kkt_ctx* c, const double* b, double* x, cudaStream_t st)
+kkt_status solve_t(kkt_ctx* c, const double* b, double* x, cudaStream_t st, int inst)
 {
-    DevNum<T>& nm = num_of<T>(c);
+    const DevNum<T> nm = inst < 0 ? num_of<T>(c) : num_of<T>(c).at(inst);
+    const int B = inst < 0 ? c->batch : 1;
     {
         Launch L(c, st, KK_SOLVE_PRE, 1);
-        KKT_CUDA(launch_solve_pre<T>(c->sched, nm, b, st));
+        KKT_CUDA(launch_solve_pre<T>(c->sched, nm, b, B, st));
     }
-    if (!c->profile && !c->opt.no_graphs) {
+    if (inst < 0 && !c->profile && !c->opt.no_graphs) {
         if (!c->g_solve) {
             kkt_status cs = capture(c, &c->g_solve, &c->g_solve_kernels,
-                                    [&](cudaStream_t cst) { return solve_levels<T>(c, nm, cst); });
+                                    [&](cudaStream_t cst) { return solve_levels<T>(c, nm, B, cst); });
             if (cs != KKT_OK) return cs;
         }
         c->launches += c->g_solve_kernels;
         KKT_CUDA(cudaGraphLaunch(c->g_solve, st));
     } else {
-        kkt_status ls = solve_levels<T>(c, nm, st);
+        kkt_status ls = solve_levels<T>(c, nm, B, st);
         if (ls != KKT_OK) return ls;
     }
     {
         Launch L(c, st, KK_SOLVE_POST, 1);
-        KKT_CUDA(launch_solve_post<T>(c->sched, nm, x, st));
+        KKT_CUDA(launch_solve_post<T>(c->sched, nm, x, B, st));
     }
     return KKT_OK;
 }
@@ -463,26 +476,31 @@ kkt_status do_refactor(kkt_ctx* c, const double* d_vals, cudaStream_t st)
     return s;
 }
 
-kkt_status do_solve(kkt_ctx* c, const double* b, double* x, cudaStream_t st)
+kkt_status do_solve(kkt_ctx* c, const double* b, double* x, cudaStream_t st, int inst = -1)
 {
-    return c->opt.precision == KKT_FP32_IR ? solve_t<float>(c, b, x, st) : solve_t<double>(c, b, x, st);
+    return c->opt.precision == KKT_FP32_IR ? solve_t<float>(c, b, x, st, inst) : solve_t<double>(c, b, x, st, inst);
 }
 
 // read back the device statistics of the last refactor into c->info
 kkt_status sync_stat(kkt_ctx* c, cudaStream_t st)
 {
-    DevStat hs;
-    KKT_CUDA(cudaMemcpyAsync(&hs, c->stat, sizeof(DevStat), cudaMemcpyDeviceToHost, st));
+    std::vector<DevStat> hs(c->batch);
+    KKT_CUDA(cudaMemcpyAsync(hs.data(), c->stat, sizeof(DevStat) * c->batch, cudaMemcpyDeviceToHost, st));
     KKT_CUDA(cudaStreamSynchronize(st));
-    c->info.n_perturbed = hs.n_perturbed;
-    if (hs.numeric_bad) c->info.status = KKT_E_NUMERIC;
+    c->infos.resize(c->batch);
+    for (int i = 0; i < c->batch; ++i) {
+        c->infos[i].n_perturbed = hs[i].n_perturbed;
+        c->infos[i].status = hs[i].numeric_bad ? KKT_E_NUMERIC : KKT_OK;
+    }
+    c->info.n_perturbed = hs[0].n_perturbed;
+    if (hs[0].numeric_bad) c->info.status = KKT_E_NUMERIC;
     return KKT_OK;
 }
 
-double knorm_of(kkt_ctx* c, cudaStream_t st)
+double knorm_of(kkt_ctx* c, cudaStream_t st, int inst = 0)
 {
     unsigned long long bits = 0;
-    cudaMemcpyAsync(&bits, &c->stat->knorm_bits, sizeof(bits), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&bits, &c->stat[inst].knorm_bits, sizeof(bits), cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     double k;
     std::memcpy(&k, &bits, sizeof(k));
@@ -504,16 +522,17 @@ kkt_status norms_host(kkt_ctx* c, const double* a, double* mx, double* sq, cudaS
     return KKT_OK;
 }
 
-kkt_status do_refine(kkt_ctx* c, const double* b, double* x, double tol, kkt_info* info, cudaStream_t st)
+// FGMRES(m) refinement of instance `inst` from the current x (b, x point at
+// that instance's vectors). Fills out (iters, backward_err, rel_resid2).
+kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double tol, kkt_info* out, cudaStream_t st)
 {
     const int n = c->n;
     const int m = c->opt.restart;
-    const double* K = c->last_vals;
+    const double* K = c->kvals + (int64_t)inst * c->nnz;
     const int* rp = c->sched.rowptr;
     const int* ci = c->sched.colidx;
     kkt_status s;
-    if ((s = do_solve(c, b, x, st)) != KKT_OK) return s;
-    double knorm = knorm_of(c, st);
+    double knorm = knorm_of(c, st, inst);
     double bmax, bsq, xmax, xsq, rmax, rsq;
     if ((s = norms_host(c, b, &bmax, &bsq, st)) != KKT_OK) return s;
     {
@@ -546,7 +565,7 @@ kkt_status do_refine(kkt_ctx* c, const double* b, double* x, double tol, kkt_inf
         for (int j = 0; j < m; ++j) {
             double* vj = c->V + (int64_t)j * n;
             double* zj = c->Z + (int64_t)j * n;
-            if ((s = do_solve(c, vj, zj, st)) != KKT_OK) return s;
+            if ((s = do_solve(c, vj, zj, st, inst)) != KKT_OK) return s;
             {
                 Launch L(c, st, KK_SPMV, 1);
                 KKT_CUDA(launch_spmv(n, rp, ci, K, zj, c->w, st));
@@ -626,14 +645,50 @@ kkt_status do_refine(kkt_ctx* c, const double* b, double* x, double tol, kkt_inf
         if ((s = norms_host(c, x, &xmax, &xsq, st)) != KKT_OK) return s;
         omega = omega_of(rmax, xmax);
     }
-    if ((s = sync_stat(c, st)) != KKT_OK) return s;
-    c->info.iters = total;
-    c->info.backward_err = omega;
-    c->info.rel_resid2 = bsq > 0 ? std::sqrt(rsq / bsq) : std::sqrt(rsq);
-    if (info) *info = c->info;
+    out->iters = total;
+    out->backward_err = omega;
+    out->rel_resid2 = bsq > 0 ? std::sqrt(rsq / bsq) : std::sqrt(rsq);
     if (!std::isfinite(omega)) return KKT_E_NUMERIC;
     if (omega > tol) return KKT_E_NOCONV;
     return KKT_OK;
+}
+
+// Solve all instances, evaluate every backward error on the device in one
+// pass, and run FGMRES only for the instances above tol.
+kkt_status do_refine(kkt_ctx* c, const double* b, double* x, double tol, kkt_info* info, cudaStream_t st)
+{
+    kkt_status s;
+    if ((s = do_solve(c, b, x, st)) != KKT_OK) return s;
+    {
+        Launch L(c, st, KK_SPMV, 2);
+        KKT_CUDA(launch_resid_omega(c->n, c->nnz, c->sched.rowptr, c->sched.colidx, c->kvals, x, b,
+                                    c->r_batch, c->omega_part, c->omega_dev, c->batch, st));
+    }
+    KKT_CUDA(cudaMemcpyAsync(c->omega_pin, c->omega_dev, sizeof(double) * c->batch, cudaMemcpyDeviceToHost, st));
+    if ((s = sync_stat(c, st)) != KKT_OK) return s;      // synchronizes st
+    kkt_status worst = KKT_OK;
+    for (int i = 0; i < c->batch; ++i) {
+        kkt_info& inf = c->infos[i];
+        inf.iters = 0;
+        inf.backward_err = c->omega_pin[i];
+        inf.rel_resid2 = -1.0;                            // computed only when refinement runs
+        kkt_status si = KKT_OK;
+        if (!(c->omega_pin[i] <= tol)) {
+            const int64_t off = (int64_t)i * c->n;
+            si = fgmres_inst(c, i, b + off, x + off, tol, &inf, st);
+            if (si != KKT_OK && si != KKT_E_NOCONV && si != KKT_E_NUMERIC) return si;
+        }
+        if (inf.status == KKT_E_NUMERIC) si = KKT_E_NUMERIC;
+        inf.refactor_count = c->refactor_count;
+        inf.launches = c->launches;
+        if (si == KKT_E_NUMERIC || (si == KKT_E_NOCONV && worst == KKT_OK)) worst = si;
+    }
+    c->info.iters = c->infos[0].iters;
+    c->info.backward_err = c->infos[0].backward_err;
+    c->info.rel_resid2 = c->infos[0].rel_resid2;
+    if (info)
+        for (int i = 0; i < c->batch; ++i) info[i] = c->infos[i];
+    return worst;
 }
 
 }  // namespace
@@ -664,7 +719,7 @@ const char* kkt_status_string(kkt_status s)
 }
 
 static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_options& o, int64_t tiles, int64_t fronts,
-                          int64_t scratch, int64_t ninv, int64_t nf12)
+                          int64_t scratch, int64_t ninv, int64_t nf12, int64_t B = 1)
 {
     const int64_t es = (int64_t)elem_size(o.precision);
     int64_t b = 0;
@@ -676,17 +731,18 @@ static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_opti
     add((an.ns + 1) * 8); add((int64_t)an.rel.size() * 4);
     add((an.ns + 1) * 8); add((an.ns + 1) * 8);
     add(fronts * 4); add(tiles * (int64_t)sizeof(FrontTile));
-    add(sizeof(DevStat));
-    add(n * 8); add(n * 8);
-    add(nnz * es); add(an.panel_total * es); add(std::max<int64_t>(an.cb_total, 1) * es);
-    add(n * es); add(std::max<int64_t>((int64_t)an.rel.size(), 1) * es);
-    add(scratch * es);
+    add(B * (int64_t)sizeof(DevStat));
+    add(B * n * 8); add(B * n * 8);
+    add(B * nnz * es); add(B * an.panel_total * es); add(B * std::max<int64_t>(an.cb_total, 1) * es);
+    add(B * n * es); add(B * std::max<int64_t>((int64_t)an.rel.size(), 1) * es);
+    add(B * scratch * es);
     add((int64_t)n * (o.restart + 1) * 8); add((int64_t)n * o.restart * 8); add(n * 8); add(n * 8);
     add((int64_t)(kRedScratch + 4096 + 8) * 8);
     add((int64_t)(8 + 2 * (kMaxRestart + 2)) * 8);
-    add(nnz * 8); add(nnz * 8); add(n * 8); add(n * 8);
+    add(B * nnz * 8); add(B * nnz * 8); add(B * n * 8); add(B * n * 8);
     add(an.ns * 4); add(an.ns * 8); add(std::max<int64_t>(ninv, 1) * 4);
-    add(an.ns * 8); add(std::max<int64_t>(nf12, 1) * es);
+    add(an.ns * 8); add(B * std::max<int64_t>(nf12, 1) * es);
+    add(B * n * 8); add(B * ((n + 1023) / 1024) * 4 * 8); add(B * 8);
     return b;
 }
 
@@ -731,11 +787,10 @@ kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx,
     return KKT_OK;
 }
 
-kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, const int32_t* h_colidx,
-                       const double* h_vals, const kkt_options* opt, kkt_ctx** out)
+static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_rowptr, const int32_t* h_colidx,
+                               const kkt_options* opt, int32_t batch, kkt_ctx** out)
 {
-    (void)h_vals;
-    if (!out || n <= 0 || !h_rowptr || !h_colidx || n_primal < 0 || n_primal > n) return KKT_E_ARG;
+    if (!out || n <= 0 || !h_rowptr || !h_colidx || n_primal < 0 || n_primal > n || batch < 1) return KKT_E_ARG;
     *out = nullptr;
     kkt_ctx* c = nullptr;
     try {
@@ -748,6 +803,8 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
     c->opt.user_perm = nullptr;
     c->n = n;
     c->n_primal = n_primal;
+    c->batch = batch;
+    const int64_t B = batch;
     std::vector<int> fids;
     std::vector<FrontTile> tiles;
     std::vector<int64_t> inv_off, f12_off;
@@ -776,7 +833,7 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
     const int64_t nnz = an.nnz;
     const int64_t scratch = c->scratch_stride * c->max_panel_global;
     int64_t bytes = plan_bytes(an, n, nnz, c->opt, (int64_t)tiles.size(), (int64_t)fids.size(), scratch,
-                               (int64_t)inv.size(), f12_total);
+                               (int64_t)inv.size(), f12_total, B);
     c->device_bytes = bytes;
     if (cudaMalloc(&c->pool.base, (size_t)bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -803,33 +860,39 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
     int64_t* cb_off = P.take<int64_t>(an.ns + 1);
     c->fronts_dev = P.take<int>(fids.size());
     c->tiles_dev = P.take<FrontTile>(tiles.size());
-    c->stat = P.take<DevStat>(1);
-    c->d_a = P.take<double>(n);
-    c->d_b = P.take<double>(n);
+    c->stat = P.take<DevStat>(B);
+    c->d_a = P.take<double>(B * n);
+    c->d_b = P.take<double>(B * n);
     const size_t es = elem_size(c->opt.precision);
-    char* sv = P.take<char>(nnz * es);
-    char* panel = P.take<char>(an.panel_total * es);
-    char* cb = P.take<char>(std::max<int64_t>(an.cb_total, 1) * es);
-    char* vec = P.take<char>(n * es);
-    char* cbv = P.take<char>(std::max<int64_t>((int64_t)an.rel.size(), 1) * es);
-    c->panel_scratch = P.take<char>(scratch * es);
+    const int64_t cb_unit = std::max<int64_t>(an.cb_total, 1);
+    const int64_t cbv_unit = std::max<int64_t>((int64_t)an.rel.size(), 1);
+    const int64_t f12_unit = std::max<int64_t>(f12_total, 1);
+    char* sv = P.take<char>(B * nnz * es);
+    char* panel = P.take<char>(B * an.panel_total * es);
+    char* cb = P.take<char>(B * cb_unit * es);
+    char* vec = P.take<char>(B * n * es);
+    char* cbv = P.take<char>(B * cbv_unit * es);
+    c->panel_scratch = P.take<char>(B * scratch * es);
     c->V = P.take<double>((int64_t)n * (c->opt.restart + 1));
     c->Z = P.take<double>((int64_t)n * c->opt.restart);
     c->w = P.take<double>(n);
     c->r = P.take<double>(n);
     c->red = P.take<double>(kRedScratch + 4096 + 8);
     c->h_dev = P.take<double>(8 + 2 * (kMaxRestart + 2));
-    c->kvals = P.take<double>(nnz);
-    c->stage_vals = P.take<double>(nnz);
-    c->stage_b = P.take<double>(n);
-    c->stage_x = P.take<double>(n);
+    c->kvals = P.take<double>(B * nnz);
+    c->stage_vals = P.take<double>(B * nnz);
+    c->stage_b = P.take<double>(B * n);
+    c->stage_x = P.take<double>(B * n);
     int* cb_split = P.take<int>(an.ns);
     int64_t* inv_off_d = P.take<int64_t>(an.ns);
     int* inv_d = P.take<int>(std::max<size_t>(inv.size(), 1));
     int64_t* f12_off_d = P.take<int64_t>(an.ns);
-    char* f12 = P.take<char>(std::max<int64_t>(f12_total, 1) * es);
+    char* f12 = P.take<char>(B * f12_unit * es);
+    c->r_batch = P.take<double>(B * n);
+    c->omega_part = P.take<double>(B * ((n + 1023) / 1024) * 4);
+    c->omega_dev = P.take<double>(B);
     if (P.used > P.size) { kkt_destroy(c); return KKT_E_NOMEM; }
-    if (cudaMallocHost(&c->pin, sizeof(double) * (4 * (kMaxRestart + 2) + 16)) != cudaSuccess) {
+    if (cudaMallocHost(&c->pin, sizeof(double) * (4 * (kMaxRestart + 2) + 16 + B)) != cudaSuccess) {
         cudaGetLastError();
         c->pin = nullptr;
         kkt_destroy(c);
@@ -861,7 +924,9 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
     e = e ? e : up(inv_off_d, inv_off.data(), an.ns * 8);
     e = e ? e : up(inv_d, inv.data(), inv.size() * 4);
     e = e ? e : up(f12_off_d, f12_off.data(), an.ns * 8);
-    e = e ? e : cudaMemset(c->stat, 0, sizeof(DevStat));
+    e = e ? e : cudaMemset(c->stat, 0, sizeof(DevStat) * B);
+    c->omega_pin = c->pin + 4 * (kMaxRestart + 2) + 16;
+    c->infos.assign(B, kkt_info{});
     if (e != cudaSuccess) { kkt_destroy(c); return KKT_E_CUDA; }
     DevSched& s = c->sched;
     s.n = n; s.nnz = nnz; s.ns = an.ns;
@@ -881,6 +946,9 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
         nm.cbv = reinterpret_cast<float*>(cbv); nm.stat = c->stat; nm.pivot_eps = eps; nm.d = c->d_a;
         nm.kcopy = c->kvals;
         nm.f12 = reinterpret_cast<float*>(f12);
+        nm.dtmp = c->d_b;
+        nm.bs_nnz = nnz; nm.bs_n = n; nm.bs_panel = an.panel_total; nm.bs_cb = cb_unit;
+        nm.bs_cbv = cbv_unit; nm.bs_f12 = f12_unit;
     } else {
         DevNum<double>& nm = c->nd;
         nm.sv = reinterpret_cast<double*>(sv); nm.panel = reinterpret_cast<double*>(panel);
@@ -888,10 +956,27 @@ kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, con
         nm.cbv = reinterpret_cast<double*>(cbv); nm.stat = c->stat; nm.pivot_eps = eps; nm.d = c->d_a;
         nm.kcopy = c->kvals;
         nm.f12 = reinterpret_cast<double*>(f12);
+        nm.dtmp = c->d_b;
+        nm.bs_nnz = nnz; nm.bs_n = n; nm.bs_panel = an.panel_total; nm.bs_cb = cb_unit;
+        nm.bs_cbv = cbv_unit; nm.bs_f12 = f12_unit;
     }
     c->info.status = KKT_OK;
     *out = c;
     return KKT_OK;
+}
+
+kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t* h_rowptr, const int32_t* h_colidx,
+                       const double* h_vals, const kkt_options* opt, kkt_ctx** out)
+{
+    (void)h_vals;
+    return analyze_impl(n, n_primal, h_rowptr, h_colidx, opt, 1, out);
+}
+
+kkt_status kkt_analyze_batch(int32_t n, int32_t n_primal, const int32_t* h_rowptr, const int32_t* h_colidx,
+                             const kkt_options* opt, int32_t count, kkt_ctx** out)
+{
+    if (count < 1) return KKT_E_ARG;
+    return analyze_impl(n, n_primal, h_rowptr, h_colidx, opt, count, out);
 }
 
 kkt_status kkt_refactor(kkt_ctx* c, const double* d_vals, void* stream)
@@ -920,15 +1005,39 @@ kkt_status kkt_step_host(kkt_ctx* c, const double* h_vals, const double* h_rhs, 
 {
     if (!c || !h_vals || !h_rhs || !h_x || !(tol >= 0)) return KKT_E_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    KKT_CUDA(cudaMemcpyAsync(c->stage_vals, h_vals, sizeof(double) * c->nnz, cudaMemcpyHostToDevice, st));
-    KKT_CUDA(cudaMemcpyAsync(c->stage_b, h_rhs, sizeof(double) * c->n, cudaMemcpyHostToDevice, st));
+    KKT_CUDA(cudaMemcpyAsync(c->stage_vals, h_vals, sizeof(double) * c->nnz * c->batch, cudaMemcpyHostToDevice, st));
+    KKT_CUDA(cudaMemcpyAsync(c->stage_b, h_rhs, sizeof(double) * c->n * c->batch, cudaMemcpyHostToDevice, st));
     kkt_status s = do_refactor(c, c->stage_vals, st);
     if (s != KKT_OK) return s;
     kkt_status r = do_refine(c, c->stage_b, c->stage_x, tol, info, st);
     if (r != KKT_OK && r != KKT_E_NOCONV) return r;
-    KKT_CUDA(cudaMemcpyAsync(h_x, c->stage_x, sizeof(double) * c->n, cudaMemcpyDeviceToHost, st));
+    KKT_CUDA(cudaMemcpyAsync(h_x, c->stage_x, sizeof(double) * c->n * c->batch, cudaMemcpyDeviceToHost, st));
     KKT_CUDA(cudaStreamSynchronize(st));
     return r;
+}
+
+// Fork: every context works on its own stream after the caller's stream
+// reaches this point; join: the caller's stream waits for all of them. The
+// contexts' graphs then run concurrently on the device.
+static kkt_status fork_join(kkt_ctx* const* ctxs, int count, cudaStream_t st,
+                            const std::function<kkt_status(int, cudaStream_t)>& body)
+{
+    cudaEvent_t fork = nullptr;
+    KKT_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(fork, st);
+    kkt_status res = KKT_OK;
+    for (int i = 0; i < count && res == KKT_OK && e == cudaSuccess; ++i) {
+        kkt_ctx* c = ctxs[i];
+        if (!c->work_stream) e = cudaStreamCreateWithFlags(&c->work_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !c->done_event) e = cudaEventCreateWithFlags(&c->done_event, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->work_stream, fork, 0);
+        if (e == cudaSuccess) res = body(i, c->work_stream);
+        if (e == cudaSuccess && res == KKT_OK) e = cudaEventRecord(c->done_event, c->work_stream);
+        if (e == cudaSuccess && res == KKT_OK) e = cudaStreamWaitEvent(st, c->done_event, 0);
+    }
+    cudaEventDestroy(fork);
+    if (e != cudaSuccess) return KKT_E_CUDA;
+    return res;
 }
 
 kkt_status kkt_refactor_batched(kkt_ctx* const* ctxs, const double* const* d_vals, int count, void* stream)
@@ -937,12 +1046,10 @@ kkt_status kkt_refactor_batched(kkt_ctx* const* ctxs, const double* const* d_val
     for (int i = 0; i < count; ++i) {
         if (!ctxs[i] || !d_vals[i]) return KKT_E_ARG;
         if (ctxs[i]->opt.precision != ctxs[0]->opt.precision) return KKT_E_ARG;
+        for (int j = 0; j < i; ++j) if (ctxs[j] == ctxs[i]) return KKT_E_ARG;
     }
-    for (int i = 0; i < count; ++i) {
-        kkt_status s = do_refactor(ctxs[i], d_vals[i], (cudaStream_t)stream);
-        if (s != KKT_OK) return s;
-    }
-    return KKT_OK;
+    return fork_join(ctxs, count, (cudaStream_t)stream,
+                     [&](int i, cudaStream_t s) { return do_refactor(ctxs[i], d_vals[i], s); });
 }
 
 kkt_status kkt_solve_batched(kkt_ctx* const* ctxs, const double* const* d_rhs, double* const* d_x, int count,
@@ -952,12 +1059,10 @@ kkt_status kkt_solve_batched(kkt_ctx* const* ctxs, const double* const* d_rhs, d
     for (int i = 0; i < count; ++i) {
         if (!ctxs[i] || !d_rhs[i] || !d_x[i]) return KKT_E_ARG;
         if (!ctxs[i]->refactored) return KKT_E_STATE;
+        for (int j = 0; j < i; ++j) if (ctxs[j] == ctxs[i]) return KKT_E_ARG;
     }
-    for (int i = 0; i < count; ++i) {
-        kkt_status s = do_solve(ctxs[i], d_rhs[i], d_x[i], (cudaStream_t)stream);
-        if (s != KKT_OK) return s;
-    }
-    return KKT_OK;
+    return fork_join(ctxs, count, (cudaStream_t)stream,
+                     [&](int i, cudaStream_t s) { return do_solve(ctxs[i], d_rhs[i], d_x[i], s); });
 }
 
 kkt_status kkt_residual(kkt_ctx* c, const double* d_rhs, const double* d_x, double* d_r, double* omega_out,
@@ -986,6 +1091,7 @@ kkt_status kkt_get_info(const kkt_ctx* c, kkt_info* info)
     *info = c->info;
     info->refactor_count = c->refactor_count;
     info->launches = c->launches;
+    info->batch = c->batch;
     if (c->refactored) {
         DevStat hs;
         KKT_CUDA(cudaDeviceSynchronize());
@@ -1044,6 +1150,7 @@ kkt_status kkt_get_plan(const kkt_ctx* c, kkt_plan_info* out)
     out->flops = an.flops;
     out->flops_exact = an.flops_exact;
     out->device_bytes = c->device_bytes;
+    out->batch = c->batch;
     return KKT_OK;
 }
 
@@ -1117,6 +1224,8 @@ kkt_status kkt_destroy(kkt_ctx* c)
     if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
     if (c->g_solve) cudaGraphExecDestroy(c->g_solve);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->work_stream) cudaStreamDestroy(c->work_stream);
+    if (c->done_event) cudaEventDestroy(c->done_event);
     if (c->pool.base) cudaFree(c->pool.base);
     if (c->pin) cudaFreeHost(c->pin);
     delete c;
