@@ -177,6 +177,16 @@ kkt_status kkt_solve(kkt_ctx *ctx, const double *d_rhs, double *d_x, void *strea
 kkt_status kkt_refine(kkt_ctx *ctx, const double *d_rhs, double *d_x, double tol,
                       kkt_info *info, void *stream);
 
+/* Asynchronous solve with a device-side accuracy check, for callers that keep
+ * several solves in flight: x = K^{-1} b for every instance, then
+ * h_omega[i] = backward error omega of instance i. h_omega is host memory
+ * (count doubles; page-locked memory keeps the call asynchronous) and holds
+ * the values once the work on `stream` has completed; an instance above the
+ * caller's tolerance can then be passed to kkt_refine. No synchronization.
+ * Errors: KKT_E_ARG, KKT_E_STATE, KKT_E_CUDA. */
+kkt_status kkt_solve_checked(kkt_ctx *ctx, const double *d_rhs, double *d_x, double *h_omega,
+                             void *stream);
+
 /* One whole IPM step through host memory, for callers without device
  * buffers: copy h_vals and h_rhs to the device, refactor, refine to tol, copy
  * x back to h_x. Synchronous. Same errors as kkt_refine. */

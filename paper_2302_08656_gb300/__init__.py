@@ -144,6 +144,12 @@ class KKTSolver:
             _check(st, "kkt_refine")
         return out, (infos[0] if self.count == 1 else list(infos))
 
+    def solve_checked(self, rhs, out, omega_host, stream=None):
+        """Asynchronous solve + device-side backward error into omega_host
+        (a pinned float64 tensor with `count` entries, valid after the stream work)."""
+        _check(lib().kkt_solve_checked(self._h, _ptr(rhs), _ptr(out), C.c_void_p(omega_host.data_ptr()),
+                                       _stream(stream)), "kkt_solve_checked")
+
     def step_host(self, vals, rhs, tol=1e-10, out=None, stream=None):
         """Refactor + refine through host buffers (copies inside the call)."""
         v = np.ascontiguousarray(vals, dtype=np.float64)

@@ -128,6 +128,7 @@ SIGNATURES = {
     "kkt_solve": (C.c_int, [_P, _P, _P, _P]),
     "kkt_refine": (C.c_int, [_P, _P, _P, C.c_double, _P, _P]),
     "kkt_step_host": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
+    "kkt_solve_checked": (C.c_int, [_P, _P, _P, _P, _P]),
     "kkt_refactor_batched": (C.c_int, [_P, _P, C.c_int, _P]),
     "kkt_solve_batched": (C.c_int, [_P, _P, _P, C.c_int, _P]),
     "kkt_residual": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_double), _P]),

@@ -1000,6 +1000,22 @@ kkt_status kkt_refine(kkt_ctx* c, const double* d_rhs, double* d_x, double tol, 
     return do_refine(c, d_rhs, d_x, tol, info, (cudaStream_t)stream);
 }
 
+kkt_status kkt_solve_checked(kkt_ctx* c, const double* d_rhs, double* d_x, double* h_omega, void* stream)
+{
+    if (!c || !d_rhs || !d_x || !h_omega || d_rhs == d_x) return KKT_E_ARG;
+    if (!c->refactored) return KKT_E_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    kkt_status s = do_solve(c, d_rhs, d_x, st);
+    if (s != KKT_OK) return s;
+    {
+        Launch L(c, st, KK_SPMV, 2);
+        KKT_CUDA(launch_resid_omega(c->n, c->nnz, c->sched.rowptr, c->sched.colidx, c->kvals, d_x, d_rhs,
+                                    c->r_batch, c->omega_part, c->omega_dev, c->batch, st));
+    }
+    KKT_CUDA(cudaMemcpyAsync(h_omega, c->omega_dev, sizeof(double) * c->batch, cudaMemcpyDeviceToHost, st));
+    return KKT_OK;
+}
+
 kkt_status kkt_step_host(kkt_ctx* c, const double* h_vals, const double* h_rhs, double* h_x, double tol,
                          kkt_info* info, void* stream)
 {
