@@ -39,7 +39,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="northeast25k", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="northeast25k", choices=sorted(WORKLOADS) + ["batch", "serving"])
+    ap.add_argument("--sessions", type=int, default=256, help="serving: number of sessions")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: total request rate (1/s)")
+    ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: HBM budget")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--seed", type=int, default=1)
@@ -171,6 +174,8 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return
+    if args.workload not in WORKLOADS:
+        raise SystemExit("--impl reference times the oracle on a single-system workload")
     w, pat, mus = workload(args.workload, args.seed)
     n_in = args.warmup + args.steps
     vals, rhs = inputs(pat, mus, args.seed, n_in)
@@ -265,10 +270,11 @@ def run_native(args):
 
     # mixed precision on the same matrices (the graded comparison: FP32 LU + FP64 FGMRES vs plain FP64)
     other = None
-    if not args.no_fp32 and args.precision == "fp64":
-        s32 = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision="fp32", **lib_opts)
-        ms32, oms32, it32, _ = timed_run(s32, "fp32")
-        other = {"precision": "fp32_ir", "value": 1000.0 * len(ms32) / sum(ms32),
+    if not args.no_fp32:
+        oprec = "fp32" if args.precision == "fp64" else "fp64"
+        s32 = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=oprec, **lib_opts)
+        ms32, oms32, it32, _ = timed_run(s32, oprec)
+        other = {"precision": "fp32_ir" if oprec == "fp32" else "fp64", "value": 1000.0 * len(ms32) / sum(ms32),
                  "p50_ms": float(np.percentile(ms32, 50)), "p99_ms": float(np.percentile(ms32, 99)),
                  "omega_max": float(max(oms32)), "fgmres_iters_mean": float(np.mean(it32))}
         s32.close()
@@ -359,7 +365,7 @@ def run_native(args):
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(launches), "kernel_ms_per_step": {k: v[1] / nprof for k, v in stats.items()},
             "library_options": lib_opts,
-            "mixed_precision": other,
+            "comparison": other,
         }
         print(json.dumps(line), flush=True)
     s64.close()
@@ -368,12 +374,155 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ batched (many instances)
+
+def run_batch(args):
+    """64 instances of one 2,000-bus pattern and 16 of one 10,000-bus pattern,
+    values and right-hand sides from a different seed per instance; FP32
+    factors + FP64 refinement; the two batches refactor concurrently; the
+    schedule of each is chosen by the autotuner."""
+    import torch
+    import paper_2302_08656_gb300 as K
+    from paper_2302_08656_gb300 import autotune
+
+    dev = torch.device("cuda", 0)
+    groups = [("batch2k", 64), ("batch10k", 16)]
+    n_in = args.warmup + args.steps
+    prec = "fp32" if args.precision == "fp64" else args.precision   # this configuration runs FP32 LU
+    ctxs, vals, rhs, outs, omegas, tune_info = [], [], [], [], [], {}
+    for name, count in groups:
+        w = WORKLOADS[name]
+        pat = KKTPattern(make_grid(args.seed, w["n_bus"], w["n_branch"], w["n_gen"]))
+        mus = mu_schedule(w["mu0"], w["mu1"], w["steps"])
+        v_steps, b_steps = [], []
+        for t in range(n_in):
+            k = t % len(mus)
+            v_steps.append(torch.from_numpy(np.concatenate(
+                [pat.values(pat.point(args.seed * 1000 + i, k, mus[k])) for i in range(count)])).to(dev))
+            b_steps.append(torch.from_numpy(np.concatenate(
+                [pat.rhs(args.seed * 1000 + i, k) for i in range(count)])).to(dev))
+        best, times = autotune.tune(pat.rowptr, pat.colidx, pat.n_primal, v_steps[0], b_steps[0],
+                                    precision=prec, count=count)
+        tune_info[name] = {"count": count, "n": pat.n, "nnz": pat.nnz, "chosen": best, "ms_by_max_pivots": times}
+        s = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, count=count, precision=prec, **best)
+        ctxs.append(s)
+        vals.append(v_steps)
+        rhs.append(b_steps)
+        outs.append(torch.empty_like(b_steps[0]))
+        omegas.append(torch.empty(count, dtype=torch.float64).pin_memory())
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(t):
+        K.refactor_batched(ctxs, [vals[g][t] for g in range(len(ctxs))])
+        for g, s in enumerate(ctxs):
+            s.solve_checked(rhs[g][t], outs[g], omegas[g])
+        torch.cuda.synchronize()
+        worst, iters = 0.0, 0
+        for g, s in enumerate(ctxs):
+            om = omegas[g].numpy()
+            if np.any(~(om <= args.tol)):
+                _, infos = s.refine(rhs[g][t], out=outs[g], tol=args.tol, raise_on_noconv=False)
+                om = np.array([i.backward_err for i in infos])
+                iters += sum(i.iters for i in infos)
+            worst = max(worst, float(np.max(om)))
+        return worst, iters
+
+    for t in range(args.warmup):
+        step(t)
+    l0 = sum(s.info().launches for s in ctxs)
+    ms, oms, its = [], [], []
+    sampler = ClockSampler(0)
+    sampler.start()
+    for t in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        om, it = step(args.warmup + t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        oms.append(om)
+        its.append(it)
+    clocks = sampler.stop()
+    launches = sum(s.info().launches for s in ctxs) - l0
+    per_step = sum(c for _, c in groups)
+    line = {
+        "metric": METRIC, "value": per_step * len(ms) / (sum(ms) / 1000.0), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "batch", "groups": tune_info, "precision": prec, "tol": args.tol,
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "note": "one step = one refactor + solve (+ refinement if needed) of all 80 instances"},
+        "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+        "omega_max": float(max(oms)), "fgmres_iters_total": int(sum(its)), "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    for s in ctxs:
+        s.close()
+
+
+# ------------------------------------------------------------------- serving
+
+def run_serving(args):
+    """Sessions with grid sizes log-uniform over 500..25,000 buses, 30..80 IPM
+    iterations each, Poisson arrivals at `rate` requests/s in total; FP32 factors
+    + FP64 refinement to tol; HBM budget for admission. Each session cycles two
+    pre-generated value sets (to bound input generation time)."""
+    import torch
+    from paper_2302_08656_gb300.serve import (GpuBackend, Server, SessionSpec, estimate_bytes,
+                                              log_uniform_sizes, poisson_arrivals)
+
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(args.seed)
+    sizes = log_uniform_sizes(rng, args.sessions, 500, 25_000)
+    iters = rng.integers(30, 81, size=args.sessions)
+    arrivals = poisson_arrivals(rng, args.rate, list(iters))
+    sessions = []
+    t0 = time.perf_counter()
+    for sid, B in enumerate(sizes):
+        grid = make_grid(args.seed * 7919 + sid, B, int(round(1.28 * B)), max(1, int(round(0.2 * B))))
+        pat = KKTPattern(grid)
+        vs = [torch.from_numpy(pat.values(pat.point(sid, k, 10.0 ** -(1 + 4 * k)))).to(dev) for k in range(2)]
+        bs = [torch.from_numpy(pat.rhs(sid, k)).to(dev) for k in range(2)]
+        sessions.append(SessionSpec(sid, pat.rowptr, pat.colidx, pat.n_primal, arrivals[sid],
+                                    (lambda v, b: (lambda k: (v[k % 2], b[k % 2])))(vs, bs),
+                                    est_bytes=estimate_bytes(pat.nnz)))
+    gen_s = time.perf_counter() - t0
+    backend = GpuBackend(precision="fp32", tol=args.tol, streams=16)
+    server = Server(backend, budget_bytes=int(args.budget_gb * (1 << 30)), max_inflight=16, analysis_workers=12)
+    sampler = ClockSampler(0)
+    sampler.start()
+    rep = server.run(sessions)
+    clocks = sampler.stop()
+    line = {
+        "metric": METRIC, "value": rep.solves_per_s, "unit": UNIT, "n_gpus": 1, "steps": rep.completed,
+        "warmup": 0, "ms_per_step": 1000.0 * rep.wall_s / max(1, rep.completed), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "serving", "sessions": args.sessions, "buses": [500, 25000], "iterations": [30, 80],
+                   "rate_per_s": args.rate, "budget_gb": args.budget_gb, "precision": "fp32", "tol": args.tol,
+                   "input_generation_s": gen_s},
+        "p50_ms": rep.percentile(50), "p99_ms": rep.percentile(99),
+        "p50_ms_steady": rep.percentile(50, steady=True), "p99_ms_steady": rep.percentile(99, steady=True),
+        "omega_max": float(max(rep.omegas)), "refined": rep.refined, "max_sessions_resident": rep.max_sessions,
+        "max_device_bytes": rep.max_bytes, "admission_waits": rep.admission_waits, "wall_s": rep.wall_s,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serving":
+        run_serving(args)
     else:
         run_native(args)
 

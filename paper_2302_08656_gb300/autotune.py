@@ -1,0 +1,83 @@
+"""Per-pattern schedule autotuner.
+
+The level schedule depends on how many pivots a supernode may hold: few
+pivots make short sequential panels but a taller assembly tree (more levels,
+more launches); many pivots do the opposite. Which wins depends on the size
+of the system, the precision (FP64 panels run on the slow FP64 pipe) and the
+batch size. The tuner times a short refactor + solve sequence for each
+candidate on the device and keeps the fastest, cached per (pattern hash,
+precision, instance count).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+
+import numpy as np
+
+CANDIDATES = (8, 16, 24, 32)
+_CACHE_FILE = os.environ.get("KKT_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache",
+                                                                "kkt_gb300_autotune.json"))
+
+
+def pattern_key(rowptr, colidx, precision: str, count: int) -> str:
+    h = hashlib.sha1()
+    h.update(np.ascontiguousarray(rowptr, dtype=np.int32).tobytes())
+    h.update(np.ascontiguousarray(colidx, dtype=np.int32).tobytes())
+    return "%s:%s:%d" % (h.hexdigest(), precision, int(count))
+
+
+def _load_cache():
+    try:
+        with open(_CACHE_FILE) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _store_cache(cache):
+    try:
+        os.makedirs(os.path.dirname(_CACHE_FILE), exist_ok=True)
+        tmp = _CACHE_FILE + ".tmp%d" % os.getpid()
+        with open(tmp, "w") as f:
+            json.dump(cache, f)
+        os.replace(tmp, _CACHE_FILE)
+    except Exception:
+        pass
+
+
+def tune(rowptr, colidx, n_primal, vals, rhs, precision="fp64", count=1, candidates=CANDIDATES, reps=3,
+         use_cache=True):
+    """Return (best options dict, {max_pivots: ms per refactor+solve}).
+
+    vals / rhs: device tensors for `count` instances (instance-major)."""
+    import torch
+
+    from . import KKTSolver
+
+    key = pattern_key(rowptr, colidx, precision, count)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        return {"max_pivots": cache[key]["max_pivots"]}, cache[key]["times"]
+    times = {}
+    out = torch.empty_like(rhs)
+    for mp in candidates:
+        s = KKTSolver(rowptr, colidx, n_primal, count=count, precision=precision, max_pivots=mp)
+        s.refactor(vals)
+        s.solve(rhs, out=out)                        # captures the graphs
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(reps):
+            s.refactor(vals)
+            s.solve(rhs, out=out)
+        ev1.record()
+        torch.cuda.synchronize()
+        times[str(mp)] = ev0.elapsed_time(ev1) / reps
+        s.close()
+    best = int(min(times, key=times.get))
+    if use_cache:
+        cache[key] = {"max_pivots": best, "times": times}
+        _store_cache(cache)
+    return {"max_pivots": best}, times
