@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--max-pivots", type=int, default=None, help="pivots per supernode (library default if unset)")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one instead of CUDA graphs")
+    ap.add_argument("--tree-min-fronts", type=int, default=None,
+                    help="levels with fewer fronts run in the persistent tree kernels (library default if unset)")
     return ap.parse_args()
 
 
@@ -146,7 +148,8 @@ PHASE_OF = {
     "front_warp_kernel": "refactor", "front_cta_kernel": "refactor", "front_panel_kernel": "refactor",
     "schur_tile_kernel": "refactor", "ruiz_kernel": "refactor", "scale_kernel": "refactor",
     "solve_fwd_kernel": "solve", "solve_bwd_kernel": "solve", "solve_pre_kernel": "solve",
-    "solve_post_kernel": "solve", "spmv_resid_kernel": "spmv",
+    "solve_post_kernel": "solve", "spmv_resid_kernel": "spmv", "tree_factor_kernel": "refactor",
+    "tree_fwd_kernel": "solve", "tree_bwd_kernel": "solve",
 }
 
 
@@ -254,6 +257,8 @@ def run_native(args):
     lib_opts = {"graphs": not args.no_graphs}
     if args.max_pivots:
         lib_opts["max_pivots"] = args.max_pivots
+    if args.tree_min_fronts is not None:
+        lib_opts["tree_min_fronts"] = args.tree_min_fronts
     s64 = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=args.precision, **lib_opts)
     plan = s64.plan()
     sampler = ClockSampler(dev.index)
@@ -359,7 +364,8 @@ def run_native(args):
                        "generators": w["n_gen"], "n": pat.n, "nnz": pat.nnz, "precision": args.precision,
                        "tol": args.tol, "mu": [w["mu0"], w["mu1"]],
                        "l2": "flushed between timed steps (%d MB write)" % (flush.numel() >> 20),
-                       "fronts": plan["n_fronts"], "levels": plan["n_levels"], "nnz_lu": plan["nnz_lu"]},
+                       "fronts": plan["n_fronts"], "levels": plan["n_levels"], "nnz_lu": plan["nnz_lu"],
+                       "tree_levels": plan["tree_levels"], "tree_units": plan["tree_units"]},
             "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
             "omega_max": float(max(oms)), "fgmres_iters_mean": float(np.mean(iters)),
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,

@@ -81,6 +81,14 @@ typedef struct {
                                    are split into chains at this size (default 16, max 64) */
     int no_graphs;              /* 1: launch every kernel from the host instead of replaying
                                    the captured CUDA graphs of the level loops (default 0) */
+    int tree_min_fronts;        /* the top levels of the assembly tree that hold fewer fronts
+                                   than this (and every level above them) are refactored and
+                                   solved by persistent, dependency-driven kernels instead of
+                                   one launch per level (default 2432; 0 = one launch per level
+                                   everywhere). Both schedules give bitwise identical results */
+    long long spin_limit;       /* polls (about 100 ns each) of a bounded device wait of those
+                                   kernels before it gives up and the call reports
+                                   KKT_E_TIMEOUT (default 1 << 23, about a second) */
 } kkt_options;
 
 typedef struct {
@@ -115,6 +123,8 @@ typedef struct {
     double flops_exact;         /* flops on the exact (non-amalgamated) structure */
     int64_t device_bytes;       /* device memory kkt_analyze would allocate (one instance) */
     int batch;                  /* instances of the context (kkt_get_plan) */
+    int tree_levels;            /* top levels run by the persistent tree kernels */
+    int tree_units;             /* refactorization work units of those kernels (one instance) */
 } kkt_plan_info;
 
 /* Fill *opt with the defaults listed above. */
@@ -238,6 +248,15 @@ kkt_status kkt_get_info(const kkt_ctx *ctx, kkt_info *info);
 kkt_status kkt_backward_error_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_colidx,
                                       const double *d_vals, const double *d_x, const double *d_rhs,
                                       double *d_r, double *d_omega, void *stream);
+
+/* Failure-injection hook for tests (no counterpart in the paper): the next
+ * refactorization's first unit of the persistent tree kernel waits on a flag
+ * that nothing sets, so its bounded wait (kkt_options.spin_limit polls)
+ * expires; the kernel then stops every other unit, and the refactorization
+ * reports KKT_E_TIMEOUT through kkt_get_info and kkt_refine. The context stays
+ * usable: the refactorization after it runs normally. Synchronous.
+ * Errors: KKT_E_ARG, KKT_E_STATE (the context has no tree part), KKT_E_CUDA. */
+kkt_status kkt_debug_stall(kkt_ctx *ctx);
 
 /* Profiling mode: when on, every launch group is bracketed by a pair of CUDA
  * events on its stream (adds a little host overhead). */

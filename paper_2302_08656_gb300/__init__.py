@@ -35,7 +35,8 @@ def _check(st: int, where: str):
 
 
 def _opts(precision="fp64", ordering="mindeg", user_perm=None, static_pivot_eps=0.0, ruiz_iters=10,
-          restart=30, max_cycles=10, relax_pivots=16, relax_zeros=0.15, max_pivots=16, graphs=True):
+          restart=30, max_cycles=10, relax_pivots=16, relax_zeros=0.15, max_pivots=16, graphs=True,
+          tree_min_fronts=None, spin_limit=None):
     o = Options()
     lib().kkt_default_options(C.byref(o))
     o.precision = FP32_IR if precision in ("fp32", "fp32_ir", FP32_IR) else FP64
@@ -53,6 +54,10 @@ def _opts(precision="fp64", ordering="mindeg", user_perm=None, static_pivot_eps=
     o.relax_zeros = float(relax_zeros)
     o.max_pivots = int(max_pivots)
     o.no_graphs = 0 if graphs else 1
+    if tree_min_fronts is not None:
+        o.tree_min_fronts = int(tree_min_fronts)
+    if spin_limit is not None:
+        o.spin_limit = int(spin_limit)
     return o, keep
 
 
@@ -180,6 +185,11 @@ class KKTSolver:
         p = PlanInfo()
         _check(lib().kkt_get_plan(self._h, C.byref(p)), "kkt_get_plan")
         return {f: getattr(p, f) for f, _ in PlanInfo._fields_}
+
+    def debug_stall(self):
+        """Failure injection for tests: the next refactor's bounded device wait
+        expires (KKT_E_TIMEOUT from info() / refine()); the context stays usable."""
+        _check(lib().kkt_debug_stall(self._h), "kkt_debug_stall")
 
     def set_profiling(self, on: bool = True):
         _check(lib().kkt_set_profiling(self._h, 1 if on else 0), "kkt_set_profiling")

@@ -16,8 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libkkt_gb300.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["analysis.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu"]
-HEADERS = ["analysis.hpp", "kernels.cuh"]
+SOURCES = ["analysis.cpp", "tree_plan.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu", "tree.cu"]
+HEADERS = ["analysis.hpp", "kernels.cuh", "tree_plan.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -80,6 +80,8 @@ class Options(C.Structure):
         ("relax_zeros", C.c_double),
         ("max_pivots", C.c_int),
         ("no_graphs", C.c_int),
+        ("tree_min_fronts", C.c_int),
+        ("spin_limit", C.c_longlong),
     ]
 
 
@@ -114,6 +116,8 @@ class PlanInfo(C.Structure):
         ("flops_exact", C.c_double),
         ("device_bytes", C.c_int64),
         ("batch", C.c_int),
+        ("tree_levels", C.c_int),
+        ("tree_units", C.c_int),
     ]
 
 
@@ -139,6 +143,7 @@ SIGNATURES = {
     "kkt_get_perm": (C.c_int, [_P, _P]),
     "kkt_get_scaling": (C.c_int, [_P, _P]),
     "kkt_export_factors": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, C.POINTER(C.c_int64), _P, _P, _P]),
+    "kkt_debug_stall": (C.c_int, [_P]),
     "kkt_backward_error_noalloc": (C.c_int, [C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "kkt_destroy": (C.c_int, [_P]),
     "kkt_status_string": (C.c_char_p, [C.c_int]),

@@ -90,21 +90,6 @@ __device__ __forceinline__ int pow2_inv_sqrt_exp(unsigned long long rb)
     return (e & 1) ? (1 - e) / 2 : -(e / 2);
 }
 
-template <typename T>
-__device__ __forceinline__ T static_pivot(T piv, double floor_, DevStat* stat, bool count)
-{
-    double a = fabs((double)piv);
-    if (!(a < 1e308)) {                       // NaN or Inf
-        if (count) atomicExch(&stat->numeric_bad, 1);
-        return piv;
-    }
-    if (a < floor_) {
-        if (count) atomicAdd(&stat->n_perturbed, 1);
-        return (T)(piv < T(0) ? -floor_ : floor_);
-    }
-    return piv;
-}
-
 // ------------------------------------------------------------------ Ruiz
 
 __global__ void fill_kernel(int n, double* a, double v)
@@ -294,11 +279,11 @@ __global__ void __launch_bounds__(128) front_warp_kernel(DevSched s, DevNum<T> n
         }
         __syncwarp();
     }
-    const double floor_ = nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits);
+    const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
     __shared__ T srinv[4];
     for (int p = 0; p < w; ++p) {
         if (lane == 0) {                                          // one reciprocal per pivot
-            const T pv = static_pivot(Fm[p + p * F], floor_, nm.stat, true);
+            const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
             Fm[p + p * F] = pv;
             srinv[wid] = T(1) / pv;
         }
@@ -356,11 +341,11 @@ __global__ void __launch_bounds__(256) front_cta_kernel(DevSched s, DevNum<T> nm
         }
         __syncthreads();
     }
-    const double floor_ = nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits);
+    const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
     __shared__ T srinv;
     for (int p = 0; p < w; ++p) {
         if (tid == 0) {                                           // one reciprocal per pivot
-            const T pv = static_pivot(Fm[p + p * F], floor_, nm.stat, true);
+            const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
             Fm[p + p * F] = pv;
             srinv = T(1) / pv;
         }
@@ -461,11 +446,11 @@ __global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> 
         }
         __syncthreads();
     }
-    const double floor_ = nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits);
+    const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
     __shared__ T srinv;
     for (int p = 0; p < w; ++p) {
         if (tid == 0) {                                           // one reciprocal per pivot
-            const T pv = static_pivot(col[p + (int64_t)p * F], floor_, nm.stat, true);
+            const T pv = static_pivot(col[p + (int64_t)p * F], floorT, nm.stat, true);
             col[p + (int64_t)p * F] = pv;
             srinv = T(1) / pv;
         }
@@ -663,6 +648,7 @@ __global__ void __launch_bounds__(128) solve_bwd_kernel(DevSched s, DevNum<T> nm
     for (int c = lane >> 3; c < w; c += 4)
         for (int a = lane & 7; a < w; a += 8) Us[a + c * w] = pan[a + (int64_t)c * F];
     __syncwarp();
+    // y_a - sum_t U12[a, t] x_t in sequence (m < 32 <= kSeqSum here: the order every backward kernel uses)
     for (int a = lane; a < w; a += 32) {
         T acc = nm.vec[first + a];
         for (int t = 0; t < m; ++t) acc -= U12[a + (int64_t)t * w] * v[w + t];
@@ -670,7 +656,7 @@ __global__ void __launch_bounds__(128) solve_bwd_kernel(DevSched s, DevNum<T> nm
     }
     __syncwarp();
     for (int p = w - 1; p >= 0; --p) {
-        const T xp = v[p] / Us[p + p * w];
+        const T xp = v[p] * (T(1) / Us[p + p * w]);        // x_p = v_p * (1 / u_pp), as every backward kernel
         __syncwarp();
         if (lane == 0) v[p] = xp;
         for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
@@ -749,24 +735,34 @@ __global__ void __launch_bounds__(128) solve_bwd_cta_kernel(DevSched s, DevNum<T
     for (int c = tid >> 5; c < w; c += 4)
         for (int a = lane; a < w; a += 32) Us[a + c * w] = pan[a + (int64_t)c * F];
     __syncthreads();
-    // y_a - sum_t U12[a, t] x_t: thread (a, g) sums every G-th t, then row sums in g order
-    const int G = 128 / w;
-    T part = T(0);
-    if (tid < G * w) {
-        const int a = tid % w, g = tid / w;
-        for (int t = g; t < m; t += G) part += U12[a + (int64_t)t * w] * v[w + t];
-    }
-    red[tid] = part;
-    __syncthreads();
-    for (int a = tid; a < w; a += 128) {
-        T acc = T(0);
-        for (int g = 0; g < G; ++g) acc += red[a + g * w];
-        v[a] = nm.vec[first + a] - acc;
+    // y_a - sum_t U12[a, t] x_t: in sequence for m <= kSeqSum, else thread (a, g)
+    // sums every G-th t and the row sums are added in g order (the order every
+    // backward kernel uses)
+    if (m <= kSeqSum) {
+        for (int a = tid; a < w; a += 128) {
+            T acc = nm.vec[first + a];
+            for (int t = 0; t < m; ++t) acc -= U12[a + (int64_t)t * w] * v[w + t];
+            v[a] = acc;
+        }
+    } else {
+        const int G = 128 / w;
+        T part = T(0);
+        if (tid < G * w) {
+            const int a = tid % w, g = tid / w;
+            for (int t = g; t < m; t += G) part += U12[a + (int64_t)t * w] * v[w + t];
+        }
+        red[tid] = part;
+        __syncthreads();
+        for (int a = tid; a < w; a += 128) {
+            T acc = T(0);
+            for (int g = 0; g < G; ++g) acc += red[a + g * w];
+            v[a] = nm.vec[first + a] - acc;
+        }
     }
     __syncthreads();
     if (tid < 32) {
         for (int p = w - 1; p >= 0; --p) {
-            const T xp = v[p] / Us[p + p * w];
+            const T xp = v[p] * (T(1) / Us[p + p * w]);    // x_p = v_p * (1 / u_pp), as every backward kernel
             __syncwarp();
             if (lane == 0) v[p] = xp;
             for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
@@ -1063,9 +1059,11 @@ cudaError_t launch_norms(int n, const double* a, double* out, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// Batched residual and backward error: grid (ceil(n / 1024), batch), one
-// warp per row; each block stores max |r|, |x|, |b| and the largest K row sum
-// of its rows in its slot of `part`; omega_final_batched reduces the slots.
+// Batched residual and backward error: grid (resid_blocks(n), batch), eight
+// lanes per row (rows hold ~10 entries), kResidRows rows per block, so that
+// thousands of blocks keep enough loads in flight; each block stores max |r|,
+// |x|, |b| and the largest K row sum of its rows in its slot of `part`;
+// omega_final_batched reduces the slots.
 __global__ void __launch_bounds__(256) resid_omega_part_kernel(int n, int64_t nnz, const int* __restrict__ rp,
                                                                const int* __restrict__ ci,
                                                                const double* __restrict__ kv,
@@ -1080,23 +1078,32 @@ __global__ void __launch_bounds__(256) resid_omega_part_kernel(int n, int64_t nn
     b += (int64_t)inst * n;
     r += (int64_t)inst * n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int row0 = blockIdx.x * 1024, row1 = min(n, row0 + 1024);
+    const int sub = threadIdx.x % kRowLanes;
+    const int row0 = blockIdx.x * kResidRows;
+    constexpr int kPass = 256 / kRowLanes;                          // rows per pass of the block
     double mr = 0.0, mx = 0.0, mb = 0.0, mk = 0.0;
-    for (int row = row0 + wid; row < row1; row += 8) {
+#pragma unroll
+    for (int q = 0; q < kResidRows / kPass; ++q) {
+        const int row = row0 + q * kPass + threadIdx.x / kRowLanes;
         double sacc = 0.0, a = 0.0;
-        for (int p = rp[row] + lane; p < rp[row + 1]; p += 32) {
-            sacc += kv[p] * x[ci[p]];
-            a += fabs(kv[p]);
+        if (row < n)
+            for (int p = rp[row] + sub; p < rp[row + 1]; p += kRowLanes) {
+                const double k = kv[p];
+                sacc += k * x[ci[p]];
+                a += fabs(k);
+            }
+        sacc = group_sum(sacc);
+        a = group_sum(a);
+        if (row < n) {
+            const double ri = b[row] - sacc;
+            if (sub == 0) r[row] = ri;
+            mr = fmax(mr, fabs(ri));
+            mx = fmax(mx, fabs(x[row]));
+            mb = fmax(mb, fabs(b[row]));
+            mk = fmax(mk, a);
         }
-        sacc = warp_sum(sacc);
-        a = warp_sum(a);
-        const double ri = b[row] - sacc;
-        if (lane == 0) r[row] = ri;
-        mr = fmax(mr, fabs(ri));
-        mx = fmax(mx, fabs(x[row]));
-        mb = fmax(mb, fabs(b[row]));
-        mk = fmax(mk, a);
     }
+    mr = warp_max(mr); mx = warp_max(mx); mb = warp_max(mb); mk = warp_max(mk);
     if (lane == 0) { red[0][wid] = mr; red[1][wid] = mx; red[2][wid] = mb; red[3][wid] = mk; }
     __syncthreads();
     if (threadIdx.x < 4) {
@@ -1106,21 +1113,32 @@ __global__ void __launch_bounds__(256) resid_omega_part_kernel(int n, int64_t nn
     }
 }
 
-__global__ void omega_final_batched_kernel(int nblk, const double* __restrict__ part, double* __restrict__ omega)
+__global__ void __launch_bounds__(256) omega_final_batched_kernel(int nblk, const double* __restrict__ part,
+                                                                  double* __restrict__ omega)
 {
+    __shared__ double red[4][8];
     const int inst = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const double* pp = part + (int64_t)inst * nblk * 4;
     double mr = 0.0, mx = 0.0, mb = 0.0, mk = 0.0;
-    for (int i = threadIdx.x; i < nblk; i += 32) {
+    for (int i = threadIdx.x; i < nblk; i += 256) {
         mr = fmax(mr, pp[4 * i + 0]);
         mx = fmax(mx, pp[4 * i + 1]);
         mb = fmax(mb, pp[4 * i + 2]);
         mk = fmax(mk, pp[4 * i + 3]);
     }
     mr = warp_max(mr); mx = warp_max(mx); mb = warp_max(mb); mk = warp_max(mk);
+    if (lane == 0) { red[0][wid] = mr; red[1][wid] = mx; red[2][wid] = mb; red[3][wid] = mk; }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const double den = mk * mx + mb;
-        omega[inst] = den > 0.0 ? mr / den : mr;
+        for (int q = 1; q < 8; ++q) {
+            red[0][0] = fmax(red[0][0], red[0][q]);
+            red[1][0] = fmax(red[1][0], red[1][q]);
+            red[2][0] = fmax(red[2][0], red[2][q]);
+            red[3][0] = fmax(red[3][0], red[3][q]);
+        }
+        const double den = red[3][0] * red[1][0] + red[2][0];
+        omega[inst] = den > 0.0 ? red[0][0] / den : red[0][0];
     }
 }
 
@@ -1128,9 +1146,9 @@ cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci,
                                const double* x, const double* b, double* r, double* part, double* omega,
                                int batch, cudaStream_t st)
 {
-    const int nblk = cdiv(n, 1024);
+    const int nblk = resid_blocks(n);
     resid_omega_part_kernel<<<dim3(nblk, batch), 256, 0, st>>>(n, nnz, rp, ci, kvals, x, b, r, part);
-    omega_final_batched_kernel<<<batch, 32, 0, st>>>(nblk, part, omega);
+    omega_final_batched_kernel<<<batch, 256, 0, st>>>(nblk, part, omega);
     return cudaGetLastError();
 }
 
@@ -1189,7 +1207,7 @@ cudaError_t configure_kernels()
     if ((e = allow_smem(solve_bwd_cta_kernel<float>, optin))) return e;
     if ((e = allow_smem(schur_tile_kernel<double>, optin))) return e;
     if ((e = allow_smem(schur_tile_kernel<float>, optin))) return e;
-    return cudaSuccess;
+    return configure_tree_kernels(optin);
 }
 
 }  // namespace kktgb

@@ -39,6 +39,7 @@ struct DevStat {
     int n_perturbed;
     int numeric_bad;
     int ruiz_changed[64];
+    int timeout;                      // a bounded wait of a tree kernel gave up
 };
 
 // Per-context numeric buffers.
@@ -78,6 +79,44 @@ struct DevNum {
     }
 };
 
+// Static pivoting, on the bit patterns (integer pipes only: FP64 compares
+// have long latency on this GPU and sit on the critical path of every pivot):
+// a pivot with |piv| < floorT (floorT >= 0, in the factor precision) is
+// replaced by sign(piv) * floorT (sign(0) = +1) and counted; NaN/Inf raise
+// the flag and are returned unchanged.
+#ifdef __CUDACC__
+__device__ __forceinline__ double static_pivot(double piv, double floorT, DevStat* stat, bool count)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(piv);
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    if (mag >= 0x7ff0000000000000ull) {
+        if (count) atomicExch(&stat->numeric_bad, 1);
+        return piv;
+    }
+    const unsigned long long fb = (unsigned long long)__double_as_longlong(floorT);
+    if (mag < fb && fb < 0x7ff0000000000000ull) {
+        if (count) atomicAdd(&stat->n_perturbed, 1);
+        return __longlong_as_double((long long)(fb | (mag ? (b & 0x8000000000000000ull) : 0ull)));
+    }
+    return piv;
+}
+__device__ __forceinline__ float static_pivot(float piv, float floorT, DevStat* stat, bool count)
+{
+    const unsigned b = __float_as_uint(piv);
+    const unsigned mag = b & 0x7fffffffu;
+    if (mag >= 0x7f800000u) {
+        if (count) atomicExch(&stat->numeric_bad, 1);
+        return piv;
+    }
+    const unsigned fb = __float_as_uint(floorT);
+    if (mag < fb && fb < 0x7f800000u) {
+        if (count) atomicAdd(&stat->n_perturbed, 1);
+        return __uint_as_float(fb | (mag ? (b & 0x80000000u) : 0u));
+    }
+    return piv;
+}
+#endif
+
 // One launch group: the fronts of one level of one context.
 struct FrontTile { int front; int ti; int tj; };
 
@@ -85,6 +124,54 @@ constexpr int kWarpFrontMax = 32;      // fronts with F <= 32 are handled by one
 constexpr int kWarpLevelMin = 608;     // ... when their level has at least 4 x 152 of them
 constexpr int kPanelCbMin = 32;        // fronts with F - w >= 32 use panel + tiled Schur update
 constexpr int kTile = 16;              // Schur update tile (kTile x kTile)
+constexpr int kSeqSum = 32;            // backward solve: U12 x summed in sequence up to this many terms
+
+// ---- narrow top of the assembly tree: persistent, dependency-driven kernels
+//
+// Levels from `split` upward (those with few fronts) are not launched level by
+// level: one persistent kernel per phase takes work units in dependency order
+// from an atomic ticket counter; a unit waits (bounded) until the units it
+// depends on have signalled completion, then runs. Every front of this part
+// is factored as nt x nt units; unit (ti, tj) eliminates the w pivots of the
+// "mini front" made of the pivot rows/columns and the ts-row (ts-column)
+// stripe ti (tj) of the contribution block: all units of a front repeat the
+// factorization of the pivot block (identical data, identical result) and
+// each produces its own tile of L21, U12 and the contribution block.
+struct TreeFront {
+    int f, first, w, F;          // supernode, first pivot step, pivots, front order
+    int ts, nt;                  // tile size and tiles per dimension of the contribution block
+    int kid_begin, kid_end;      // children (TreeKid range)
+    int parent;                  // tree index of the parent front, -1 at a root
+    int units;                   // nt * nt
+    int64_t asm_begin, asm_end;  // original entries (Analysis asm lists)
+    int64_t panel_off, cb_off, rel_ptr, rows_ptr;
+    int64_t inv_off;             // gather maps: child c (local) at inv_off + c * (F - w)
+};
+struct TreeKid {
+    int q;                       // tree index of the child, -1 if the child lies below the tree part
+    int mc, k;                   // child contribution-block order; its rows landing on parent pivots
+    int units;                   // units of the child (0 below the tree part)
+    int64_t cb_off, rel_ptr;
+};
+struct TreeSched {
+    int nq = 0;                  // fronts of the tree part (tree index = level-major order)
+    int nunits = 0;              // factorization units
+    const TreeFront* fr = nullptr;
+    const TreeKid* kid = nullptr;
+    const FrontTile* unit = nullptr;   // factorization units in dependency order (front = tree index)
+    const int* inv = nullptr;          // gather maps: parent CB row -> child CB row or -1
+    // shared-memory layout parameters (host computed)
+    int max_kids = 0, map_w = 0, m_elems = 0;
+    int max_F = 0, max_w = 0;
+    int fwd_stage = 0;           // 1: forward solve stages the F x w panel in shared memory
+    int bwd_stage = 0;           // 1: backward solve stages U12 in shared memory
+    int max_fw = 0, max_wm = 0;
+};
+constexpr int kTreeMaxKids = 48;       // fronts with more children stay level-launched
+constexpr int kTreeStage = 2048;       // staged child contribution entries per pass (forward solve)
+// Counter block of a tree kernel: [0] ticket, [1] abort flag, [2] forward-solve ticket
+// (solve block), [3] backward-solve ticket; then the per-(instance, front) completion counters.
+constexpr int kCtrHead = 4;
 
 // Launchers (all asynchronous on `st`).
 cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double* dtmp, int iters,
@@ -120,7 +207,9 @@ cudaError_t launch_solve_bwd(const DevSched& s, const DevNum<T>& nm, const int* 
 template <typename T>
 cudaError_t launch_solve_post(const DevSched& s, const DevNum<T>& nm, double* x, int batch, cudaStream_t st);
 // per instance: r = b - K x, omega = ||r||_inf / (||K||_inf ||x||_inf + ||b||_inf) into omega[b];
-// part holds batch * ceil(n / 1024) * 4 doubles
+// part holds batch * resid_blocks(n) * 4 doubles
+constexpr int kResidRows = 64;         // rows per block of the residual kernel
+inline int resid_blocks(int n) { return (n + kResidRows - 1) / kResidRows; }
 cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci, const double* kvals,
                                const double* x, const double* b, double* r, double* part, double* omega,
                                int batch, cudaStream_t st);
@@ -145,5 +234,20 @@ cudaError_t launch_update(int n, double* x, const double* Z, int64_t ldz, int nv
 // out[0] = max |a|, out[1] = sum a^2 (zeroed inside); for several vectors in one launch
 cudaError_t launch_norms(int n, const double* a, double* out, cudaStream_t st);
 cudaError_t launch_zero_stat(DevStat* stat, cudaStream_t st);
+
+// Tree kernels. grid = persistent CTAs; ctr = counter block (zeroed by the
+// caller before the launch); stall = optional test hook (see kkt_debug_stall).
+template <typename T>
+cudaError_t tree_grid(int kind, size_t smem, int* grid);   // kind 0 factor, 1 forward, 2 backward
+template <typename T>
+cudaError_t launch_tree_factor(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
+                               int* stall, long long spin_limit, int grid, size_t smem, cudaStream_t st);
+template <typename T>
+cudaError_t launch_tree_fwd(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
+                            long long spin_limit, int grid, size_t smem, cudaStream_t st);
+template <typename T>
+cudaError_t launch_tree_bwd(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
+                            long long spin_limit, int grid, size_t smem, cudaStream_t st);
+cudaError_t configure_tree_kernels(int optin);
 
 }  // namespace kktgb

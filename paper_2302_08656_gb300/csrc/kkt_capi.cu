@@ -3,6 +3,7 @@
 #include "../../include/kkt.h"
 #include "analysis.hpp"
 #include "kernels.cuh"
+#include "tree_plan.hpp"
 
 #include <cuda_runtime.h>
 
@@ -74,6 +75,14 @@ struct kkt_ctx {
     void* panel_scratch = nullptr;
     int* fronts_dev = nullptr;
     FrontTile* tiles_dev = nullptr;
+    // persistent kernels of the tree part
+    TreeSched tsched;
+    int tree_split = 0;
+    size_t tf_smem = 0, tfw_smem = 0, tbw_smem = 0;
+    int tf_grid = 0, tfw_grid = 0, tbw_grid = 0;
+    int* ctr_fac = nullptr;          // counter block of the refactorization kernel
+    int* ctr_sol = nullptr;          // counter block of the two solve kernels
+    int* stall = nullptr;            // failure-injection hook (two ints)
     // refinement workspace (FP64)
     double* V = nullptr;             // n x (m+1)
     double* Z = nullptr;             // n x m
@@ -137,6 +146,8 @@ void fill_defaults(kkt_options* o)
     o->relax_zeros = 0.15;
     o->max_pivots = 16;
     o->no_graphs = 0;
+    o->tree_min_fronts = 2432;                  // 16 fronts per SM of a 152-SM GB300
+    o->spin_limit = 1LL << 23;
 }
 
 kkt_status check_options(const kkt_options& o)
@@ -148,6 +159,7 @@ kkt_status check_options(const kkt_options& o)
     if (o.max_cycles < 0) return KKT_E_ARG;
     if (o.max_pivots < 1 || o.max_pivots > 64) return KKT_E_ARG;
     if (o.relax_pivots < 1) return KKT_E_ARG;
+    if (o.tree_min_fronts < 0 || o.spin_limit < 1) return KKT_E_ARG;
     return KKT_OK;
 }
 
@@ -167,21 +179,21 @@ size_t elem_size(int precision) { return precision == KKT_FP32_IR ? 4 : 8; }
 constexpr size_t kSmemLimit = 220 * 1024;
 
 // Classify fronts per level and lay out the launch lists.
-void build_levels(const Analysis& an, size_t es, std::vector<LevelGroup>& levels, std::vector<int>& front_ids,
-                  std::vector<FrontTile>& tiles, int64_t& scratch_stride, int& max_panel_global,
-                  std::vector<int64_t>& inv_off, std::vector<int>& inv, std::vector<int64_t>& f12_off,
-                  int64_t& f12_total)
+void build_levels(const Analysis& an, size_t es, int nlev, std::vector<LevelGroup>& levels,
+                  std::vector<int>& front_ids, std::vector<FrontTile>& tiles, int64_t& scratch_stride,
+                  int& max_panel_global, std::vector<int64_t>& inv_off, std::vector<int>& inv,
+                  std::vector<int64_t>& f12_off, int64_t& f12_total)
 {
     inv_off.assign(an.ns, 0);
     inv.clear();
     f12_off.assign(an.ns, 0);
     f12_total = 0;
-    levels.assign(an.n_levels, LevelGroup());
+    levels.assign(nlev, LevelGroup());
     front_ids.clear();
     tiles.clear();
     scratch_stride = 0;
     max_panel_global = 0;
-    for (int l = 0; l < an.n_levels; ++l) {
+    for (int l = 0; l < nlev; ++l) {
         LevelGroup& g = levels[l];
         std::vector<int> wl, cl, pl;
         int cmax = 0;
@@ -279,11 +291,13 @@ template <>
 DevNum<float>& num_of<float>(kkt_ctx* c) { return c->nf; }
 
 enum KernelKind { KK_RUIZ = 0, KK_SCALE, KK_FRONT_WARP, KK_FRONT_CTA, KK_FRONT_PANEL, KK_SCHUR, KK_SOLVE_PRE,
-                  KK_SOLVE_FWD, KK_SOLVE_BWD, KK_SOLVE_POST, KK_SPMV, KK_REDUCE, KK_VECTOR, KK_COUNT };
+                  KK_SOLVE_FWD, KK_SOLVE_BWD, KK_SOLVE_POST, KK_SPMV, KK_REDUCE, KK_VECTOR, KK_TREE_FACTOR,
+                  KK_TREE_FWD, KK_TREE_BWD, KK_COUNT };
 const char* const kKernelNames[KK_COUNT] = {
     "ruiz_kernel", "scale_kernel", "front_warp_kernel", "front_cta_kernel", "front_panel_kernel",
     "schur_tile_kernel", "solve_pre_kernel", "solve_fwd_kernel", "solve_bwd_kernel", "solve_post_kernel",
-    "spmv_resid_kernel", "reduction_kernels", "vector_kernels"};
+    "spmv_resid_kernel", "reduction_kernels", "vector_kernels", "tree_factor_kernel", "tree_fwd_kernel",
+    "tree_bwd_kernel"};
 
 // Counts kernels and, in profiling mode, brackets the launch group with a
 // pair of events on the launching stream.
@@ -349,6 +363,8 @@ kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st)
 {
     const int* fr = c->fronts_dev;
     const int B = c->batch;
+    const int nq = c->tsched.nq;
+    if (nq > 0) KKT_CUDA(cudaMemsetAsync(c->ctr_fac, 0, sizeof(int) * (kCtrHead + (size_t)B * nq), st));
     for (const LevelGroup& g : c->levels) {
         if (g.warp_cnt) {
             Launch L(c, st, KK_FRONT_WARP, 1);
@@ -369,6 +385,11 @@ kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st)
             KKT_CUDA(launch_schur_tiles<T>(c->sched, nm, c->tiles_dev + g.tile_off, g.tile_cnt, g.panel_maxW, B, st));
         }
     }
+    if (nq > 0) {
+        Launch L(c, st, KK_TREE_FACTOR, 1);
+        KKT_CUDA(launch_tree_factor<T>(c->sched, c->tsched, nm, B, c->ctr_fac, c->stall, c->opt.spin_limit,
+                                       c->tf_grid, c->tf_smem, st));
+    }
     return KKT_OK;
 }
 
@@ -376,8 +397,9 @@ template <typename T>
 kkt_status solve_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st)
 {
     const int* fr = c->fronts_dev;
+    const int nq = c->tsched.nq;
     // fronts with F <= 32: a warp each; larger ones (the CTA and panel classes,
-    // contiguous in the front list): a CTA each
+    // contiguous in the front list): a CTA each; then the tree part
     for (size_t l = 0; l < c->levels.size(); ++l) {
         const LevelGroup& g = c->levels[l];
         const int nbig = g.cta_cnt + g.panel_cnt;
@@ -389,6 +411,17 @@ kkt_status solve_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st)
             Launch L(c, st, KK_SOLVE_FWD, 1);
             KKT_CUDA(launch_solve_fwd_cta<T>(c->sched, nm, fr + g.cta_off, nbig, g.big_maxF, g.big_maxW, B, st));
         }
+    }
+    if (nq > 0) {
+        KKT_CUDA(cudaMemsetAsync(c->ctr_sol, 0, sizeof(int) * (kCtrHead + 2 * (size_t)B * nq), st));
+        {
+            Launch L(c, st, KK_TREE_FWD, 1);
+            KKT_CUDA(launch_tree_fwd<T>(c->sched, c->tsched, nm, B, c->ctr_sol, c->opt.spin_limit, c->tfw_grid,
+                                        c->tfw_smem, st));
+        }
+        Launch L(c, st, KK_TREE_BWD, 1);
+        KKT_CUDA(launch_tree_bwd<T>(c->sched, c->tsched, nm, B, c->ctr_sol, c->opt.spin_limit, c->tbw_grid,
+                                    c->tbw_smem, st));
     }
     for (size_t l = c->levels.size(); l-- > 0;) {
         const LevelGroup& g = c->levels[l];
@@ -467,6 +500,7 @@ kkt_status solve_t(kkt_ctx* c, const double* b, double* x, cudaStream_t st, int 
 
 kkt_status do_refactor(kkt_ctx* c, const double* d_vals, cudaStream_t st)
 {
+    c->info.status = KKT_OK;
     kkt_status s = c->opt.precision == KKT_FP32_IR ? refactor_t<float>(c, d_vals, st) : refactor_t<double>(c, d_vals, st);
     if (s == KKT_OK) {
         c->last_vals = c->kvals;
@@ -490,10 +524,12 @@ kkt_status sync_stat(kkt_ctx* c, cudaStream_t st)
     c->infos.resize(c->batch);
     for (int i = 0; i < c->batch; ++i) {
         c->infos[i].n_perturbed = hs[i].n_perturbed;
-        c->infos[i].status = hs[i].numeric_bad ? KKT_E_NUMERIC : KKT_OK;
+        c->infos[i].status = hs[i].timeout ? KKT_E_TIMEOUT : hs[i].numeric_bad ? KKT_E_NUMERIC : KKT_OK;
     }
     c->info.n_perturbed = hs[0].n_perturbed;
     if (hs[0].numeric_bad) c->info.status = KKT_E_NUMERIC;
+    for (int i = 0; i < c->batch; ++i)
+        if (hs[i].timeout) c->info.status = KKT_E_TIMEOUT;
     return KKT_OK;
 }
 
@@ -666,6 +702,16 @@ kkt_status do_refine(kkt_ctx* c, const double* b, double* x, double tol, kkt_inf
     }
     KKT_CUDA(cudaMemcpyAsync(c->omega_pin, c->omega_dev, sizeof(double) * c->batch, cudaMemcpyDeviceToHost, st));
     if ((s = sync_stat(c, st)) != KKT_OK) return s;      // synchronizes st
+    if (c->info.status == KKT_E_TIMEOUT) {                // a bounded device wait gave up: no valid x
+        for (int i = 0; i < c->batch; ++i) {
+            c->infos[i].iters = 0;
+            c->infos[i].backward_err = c->omega_pin[i];
+            c->infos[i].rel_resid2 = -1.0;
+        }
+        if (info)
+            for (int i = 0; i < c->batch; ++i) info[i] = c->infos[i];
+        return KKT_E_TIMEOUT;
+    }
     kkt_status worst = KKT_OK;
     for (int i = 0; i < c->batch; ++i) {
         kkt_info& inf = c->infos[i];
@@ -719,7 +765,7 @@ const char* kkt_status_string(kkt_status s)
 }
 
 static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_options& o, int64_t tiles, int64_t fronts,
-                          int64_t scratch, int64_t ninv, int64_t nf12, int64_t B = 1)
+                          int64_t scratch, int64_t ninv, int64_t nf12, const TreePlan& tp, int64_t B = 1)
 {
     const int64_t es = (int64_t)elem_size(o.precision);
     int64_t b = 0;
@@ -742,7 +788,11 @@ static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_opti
     add(B * nnz * 8); add(B * nnz * 8); add(B * n * 8); add(B * n * 8);
     add(an.ns * 4); add(an.ns * 8); add(std::max<int64_t>(ninv, 1) * 4);
     add(an.ns * 8); add(B * std::max<int64_t>(nf12, 1) * es);
-    add(B * n * 8); add(B * ((n + 1023) / 1024) * 4 * 8); add(B * 8);
+    add(B * n * 8); add(B * (int64_t)resid_blocks(n) * 4 * 8); add(B * 8);
+    const int64_t nq = (int64_t)tp.fr.size();
+    add(nq * (int64_t)sizeof(TreeFront)); add((int64_t)tp.kid.size() * (int64_t)sizeof(TreeKid));
+    add((int64_t)tp.unit.size() * (int64_t)sizeof(FrontTile)); add((int64_t)tp.inv.size() * 4);
+    add((kCtrHead + B * nq) * 4); add((kCtrHead + 2 * B * nq) * 4); add(2 * 4);
     return b;
 }
 
@@ -765,7 +815,10 @@ kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx,
         std::vector<int64_t> inv_off, f12_off;
         std::vector<int> inv;
         int64_t f12_total = 0;
-        build_levels(an, elem_size(o.precision), lv, fids, tiles, stride, mpg, inv_off, inv, f12_off, f12_total);
+        TreePlan tp;
+        build_tree(an, o.tree_min_fronts, elem_size(o.precision), tp);
+        build_levels(an, elem_size(o.precision), tp.split, lv, fids, tiles, stride, mpg, inv_off, inv, f12_off,
+                     f12_total);
         std::memset(out, 0, sizeof(*out));
         out->n = n;
         out->nnz = an.nnz;
@@ -778,7 +831,9 @@ kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx,
         out->flops = an.flops;
         out->flops_exact = an.flops_exact;
         out->device_bytes = plan_bytes(an, n, an.nnz, o, (int64_t)tiles.size(), (int64_t)fids.size(),
-                                       stride * mpg, (int64_t)inv.size(), f12_total);
+                                       stride * mpg, (int64_t)inv.size(), f12_total, tp);
+        out->tree_levels = an.n_levels - tp.split;
+        out->tree_units = (int)tp.unit.size();
     } catch (const std::bad_alloc&) {
         return KKT_E_NOMEM;
     } catch (...) {
@@ -810,6 +865,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     std::vector<int64_t> inv_off, f12_off;
     std::vector<int> inv;
     int64_t f12_total = 0;
+    TreePlan tp;
     try {
         std::string err = analyze_pattern(n, h_rowptr, h_colidx, to_analysis(opt ? *opt : c->opt), c->an);
         if (!err.empty()) {
@@ -817,7 +873,8 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
             delete c;
             return s;
         }
-        build_levels(c->an, elem_size(c->opt.precision), c->levels, fids, tiles, c->scratch_stride,
+        build_tree(c->an, c->opt.tree_min_fronts, elem_size(c->opt.precision), tp);
+        build_levels(c->an, elem_size(c->opt.precision), tp.split, c->levels, fids, tiles, c->scratch_stride,
                      c->max_panel_global, inv_off, inv, f12_off, f12_total);
     } catch (...) {
         delete c;
@@ -833,7 +890,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     const int64_t nnz = an.nnz;
     const int64_t scratch = c->scratch_stride * c->max_panel_global;
     int64_t bytes = plan_bytes(an, n, nnz, c->opt, (int64_t)tiles.size(), (int64_t)fids.size(), scratch,
-                               (int64_t)inv.size(), f12_total, B);
+                               (int64_t)inv.size(), f12_total, tp, B);
     c->device_bytes = bytes;
     if (cudaMalloc(&c->pool.base, (size_t)bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -889,8 +946,16 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     int64_t* f12_off_d = P.take<int64_t>(an.ns);
     char* f12 = P.take<char>(B * f12_unit * es);
     c->r_batch = P.take<double>(B * n);
-    c->omega_part = P.take<double>(B * ((n + 1023) / 1024) * 4);
+    c->omega_part = P.take<double>(B * (int64_t)resid_blocks(n) * 4);
     c->omega_dev = P.take<double>(B);
+    const int64_t nq = (int64_t)tp.fr.size();
+    TreeFront* tfr = P.take<TreeFront>(nq);
+    TreeKid* tkid = P.take<TreeKid>(tp.kid.size());
+    FrontTile* tunit = P.take<FrontTile>(tp.unit.size());
+    int* tinv = P.take<int>(tp.inv.size());
+    c->ctr_fac = P.take<int>(kCtrHead + B * nq);
+    c->ctr_sol = P.take<int>(kCtrHead + 2 * B * nq);
+    c->stall = P.take<int>(2);
     if (P.used > P.size) { kkt_destroy(c); return KKT_E_NOMEM; }
     if (cudaMallocHost(&c->pin, sizeof(double) * (4 * (kMaxRestart + 2) + 16 + B)) != cudaSuccess) {
         cudaGetLastError();
@@ -924,6 +989,11 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     e = e ? e : up(inv_off_d, inv_off.data(), an.ns * 8);
     e = e ? e : up(inv_d, inv.data(), inv.size() * 4);
     e = e ? e : up(f12_off_d, f12_off.data(), an.ns * 8);
+    e = e ? e : up(tfr, tp.fr.data(), nq * sizeof(TreeFront));
+    e = e ? e : up(tkid, tp.kid.data(), tp.kid.size() * sizeof(TreeKid));
+    e = e ? e : up(tunit, tp.unit.data(), tp.unit.size() * sizeof(FrontTile));
+    e = e ? e : up(tinv, tp.inv.data(), tp.inv.size() * 4);
+    e = e ? e : cudaMemset(c->stall, 0, 2 * sizeof(int));
     e = e ? e : cudaMemset(c->stat, 0, sizeof(DevStat) * B);
     c->omega_pin = c->pin + 4 * (kMaxRestart + 2) + 16;
     c->infos.assign(B, kkt_info{});
@@ -936,6 +1006,17 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     s.asm_ptr = asm_ptr; s.asm_pos = asm_pos; s.asm_src = asm_src;
     s.rel_ptr = rel_ptr; s.rel = rel; s.panel_off = panel_off; s.cb_off = cb_off;
     s.cb_split = cb_split; s.inv_off = inv_off_d; s.inv = inv_d; s.f12_off = f12_off_d;
+    c->tsched = tp.ts;
+    c->tsched.fr = tfr; c->tsched.kid = tkid; c->tsched.unit = tunit; c->tsched.inv = tinv;
+    c->tree_split = tp.split;
+    c->tf_smem = tp.fac_smem; c->tfw_smem = tp.fwd_smem; c->tbw_smem = tp.bwd_smem;
+    if (nq > 0) {
+        const bool f32 = c->opt.precision == KKT_FP32_IR;
+        e = f32 ? tree_grid<float>(0, c->tf_smem, &c->tf_grid) : tree_grid<double>(0, c->tf_smem, &c->tf_grid);
+        e = e ? e : f32 ? tree_grid<float>(1, c->tfw_smem, &c->tfw_grid) : tree_grid<double>(1, c->tfw_smem, &c->tfw_grid);
+        e = e ? e : f32 ? tree_grid<float>(2, c->tbw_smem, &c->tbw_grid) : tree_grid<double>(2, c->tbw_smem, &c->tbw_grid);
+        if (e != cudaSuccess) { kkt_destroy(c); return KKT_E_CUDA; }
+    }
     double eps = c->opt.static_pivot_eps > 0 ? c->opt.static_pivot_eps
                                              : (c->opt.precision == KKT_FP32_IR ? 1e-7 : 1e-14);
     c->opt.static_pivot_eps = eps;
@@ -1114,6 +1195,7 @@ kkt_status kkt_get_info(const kkt_ctx* c, kkt_info* info)
         KKT_CUDA(cudaMemcpy(&hs, c->stat, sizeof(DevStat), cudaMemcpyDeviceToHost));
         info->n_perturbed = hs.n_perturbed;
         if (hs.numeric_bad) info->status = KKT_E_NUMERIC;
+        if (hs.timeout) info->status = KKT_E_TIMEOUT;
     }
     return KKT_OK;
 }
@@ -1167,6 +1249,18 @@ kkt_status kkt_get_plan(const kkt_ctx* c, kkt_plan_info* out)
     out->flops_exact = an.flops_exact;
     out->device_bytes = c->device_bytes;
     out->batch = c->batch;
+    out->tree_levels = an.n_levels - c->tree_split;
+    out->tree_units = c->tsched.nunits;
+    return KKT_OK;
+}
+
+kkt_status kkt_debug_stall(kkt_ctx* c)
+{
+    if (!c) return KKT_E_ARG;
+    if (c->tsched.nq == 0) return KKT_E_STATE;
+    const int req[2] = {1, 0};
+    KKT_CUDA(cudaDeviceSynchronize());
+    KKT_CUDA(cudaMemcpy(c->stall, req, sizeof(req), cudaMemcpyHostToDevice));
     return KKT_OK;
 }
 

@@ -1,0 +1,699 @@
+// Persistent, dependency-driven kernels for the narrow top of the assembly
+// tree (refactorization, forward and backward substitution).
+//
+// Above a few hundred fronts per level the per-level launches of the
+// multifrontal refactorization (Alg. 1 refactor step) and of the triangular
+// solves are bound by latency: one CTA per front spends its time on chains of
+// dependent loads and on the launch boundary between levels. Here the whole
+// narrow part of the tree is one launch per phase. Work units are numbered in
+// a dependency order (level-major); CTAs take them from an atomic ticket
+// counter, load everything that does not depend on other units (descriptors,
+// original entries, gather maps, factor panels), then wait -- bounded, with
+// an error flag on expiry -- until the units they depend on have signalled
+// completion, and finish with the data those units produced.
+//
+// Forward progress: a CTA holding ticket t only waits for units with smaller
+// tickets, which are already held by running CTAs; by induction the smallest
+// unfinished ticket can always run, whatever the residency of the grid.
+//
+// Every entry is computed with the same operations in the same order as the
+// level-launched kernels (assembly: original entry, then the children in
+// order; elimination: updates in pivot order, one reciprocal per pivot), so
+// both paths give bitwise identical factors and solutions.
+#include "kernels.cuh"
+
+#include <algorithm>
+#include <cstdlib>
+
+namespace kktgb {
+
+namespace {
+
+__device__ __forceinline__ int ld_acquire(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until *p >= need, at most `limit` polls. Returns false if the wait
+// gave up or another CTA aborted the kernel; on expiry the abort flag is set.
+__device__ bool bounded_wait(const int* p, int need, int* abort_flag, long long limit)
+{
+    long long it = 0;
+    while (ld_acquire(p) < need) {
+        if (ld_acquire(abort_flag)) return false;
+        if (++it > limit) {
+            atomicExch(abort_flag, 1);
+            return false;
+        }
+        __nanosleep(100);
+    }
+    return true;
+}
+
+// Bounded wait of warp 0 for the children of a unit: lane l polls the
+// completion counters of children l, l + 32, ... (need = their unit count,
+// or 1 if `one`), so every child is checked in each round while the other
+// warps of the CTA stay parked at the next barrier. Returns 1 once all are
+// complete, 0 if the wait gave up (the abort flag is then set) or another CTA
+// aborted the kernel. Called by warp 0 only.
+__device__ int warp_wait_kids(const int* done_b, const TreeKid* kids, int nk, bool one, int* abort_flag,
+                              long long limit)
+{
+    const int lane = threadIdx.x & 31;
+    for (long long it = 0;; ++it) {
+        bool ok = true;
+        for (int c = lane; c < nk; c += 32)
+            if (kids[c].q >= 0 && ld_acquire(done_b + kids[c].q) < (one ? 1 : kids[c].units)) ok = false;
+        if (__all_sync(0xffffffffu, ok)) return 1;
+        if ((it & 31) == 31) {
+            int stop = 0;
+            if (lane == 0) {
+                stop = ld_acquire(abort_flag);
+                if (!stop && it > limit) {
+                    atomicExch(abort_flag, 1);
+                    stop = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) return 0;
+        }
+        __nanosleep(64);
+    }
+}
+
+// Signal completion of a unit: every thread's stores are made visible at GPU
+// scope before one thread bumps the counter.
+__device__ __forceinline__ void signal_done(int* counter)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(counter, 1);
+}
+
+// Take the next ticket (or `total` once the kernel was aborted).
+__device__ __forceinline__ int next_ticket(int* ticket, const int* abort_flag, int total, int* s_t)
+{
+    if (threadIdx.x == 0) *s_t = ld_acquire(abort_flag) ? total : atomicAdd(ticket, 1);
+    __syncthreads();
+    return *s_t;
+}
+
+constexpr int kTreeCtasPerSm = 4;
+
+__host__ __device__ __forceinline__ size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+template <typename X>
+__device__ __forceinline__ void copy_words(X* dst, const X* src, int count, int tid, int nt)
+{
+    static_assert(sizeof(X) % 4 == 0, "word copy");
+    const int words = count * (int)(sizeof(X) / 4);
+    for (int e = tid; e < words; e += nt)
+        reinterpret_cast<int*>(dst)[e] = reinterpret_cast<const int*>(src)[e];
+}
+
+// ------------------------------------------------------------- refactor
+
+// Unit (q, ti, tj) of instance b. Mini front M (Fr x Fc, column-major, ld Fr):
+// rows 0..w-1 / columns 0..w-1 are the pivots, rows w..Fr-1 the contribution
+// rows i0..i0+nr-1, columns w..Fc-1 the contribution columns j0..j0+nc-1.
+// Threads form a 32 x 8 grid (lane -> row, warp -> column).
+template <typename T>
+__global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
+                                                          int* stall, long long limit)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ TreeFront d;
+    __shared__ int s_t, s_ok;
+    __shared__ T s_rinv[64];                                   // reciprocal of every pivot (w <= 64)
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    const int total = ts.nunits * B;
+    int* done = ctr + kCtrHead;
+    T* M = reinterpret_cast<T*>(smraw);
+    const int W = ts.map_w;
+    const size_t off_map = align16(sizeof(T) * (size_t)ts.m_elems);
+    const size_t off_kid = off_map + align16(sizeof(int) * 2 * (size_t)ts.max_kids * W);
+    int* smap = reinterpret_cast<int*>(smraw + off_map);           // child c: rows at 2cW, columns at (2c+1)W
+    TreeKid* kids = reinterpret_cast<TreeKid*>(smraw + off_kid);
+    for (;;) {
+        const int t = next_ticket(ctr, ctr + 1, total, &s_t);
+        if (t >= total) break;
+        const int u = t / B, b = t - u * B;
+        const FrontTile ut = ts.unit[u];
+        const int q = ut.front;
+        copy_words(&d, ts.fr + q, 1, tid, 256);
+        __syncthreads();
+        const DevNum<T> nm = nm0.at(b);
+        const int w = d.w, F = d.F, m = F - w, tsz = d.ts;
+        const int i0 = ut.ti * tsz, j0 = ut.tj * tsz;
+        const int nr = min(tsz, m - i0), nc = min(tsz, m - j0);
+        const int Fr = w + nr, Fc = w + nc;
+        const int nk = d.kid_end - d.kid_begin;
+        const bool lead = ut.ti == 0 && ut.tj == 0;
+        // ---- everything that does not depend on the children
+        for (int e = tid; e < Fr * Fc; e += 256) M[e] = T(0);
+        copy_words(kids, ts.kid + d.kid_begin, nk, tid, 256);
+        for (int e = tid; e < nk * W; e += 256) {
+            const int c = e / W, i = e - c * W;
+            int vr = -1, vc = -1;
+            if (i >= w) {
+                const int* inv = ts.inv + d.inv_off + (int64_t)c * m;
+                if (i - w < nr) vr = inv[i0 + i - w];
+                if (i - w < nc) vc = inv[j0 + i - w];
+            }
+            smap[2 * c * W + i] = vr;
+            smap[(2 * c + 1) * W + i] = vc;
+        }
+        __syncthreads();
+        for (int64_t e = d.asm_begin + tid; e < d.asm_end; e += 256) {
+            const int pos = s.asm_pos[e];
+            const int bc = pos / F, a = pos - bc * F;
+            const int lr = a < w ? a : ((unsigned)(a - w - i0) < (unsigned)nr ? a - i0 : -1);
+            const int lc = bc < w ? bc : ((unsigned)(bc - w - j0) < (unsigned)nc ? bc - j0 : -1);
+            if (lr >= 0 && lc >= 0) M[lr + lc * Fr] = nm.sv[s.asm_src[e]];
+        }
+        for (int c = ty; c < nk; c += 8) {                         // child rows t < k land on pivots
+            const int k = kids[c].k;
+            const int* rl = s.rel + kids[c].rel_ptr;
+            for (int tt = tx; tt < k; tt += 32) {
+                const int r = rl[tt];
+                smap[2 * c * W + r] = tt;
+                smap[(2 * c + 1) * W + r] = tt;
+            }
+        }
+        // static-pivot floor (the scaling kernel's max |D K D|), loaded before the wait
+        const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
+        // ---- wait for the children (bounded; lane l of warp 0 polls children l, l + 32)
+        if (tid == 0) {
+            s_ok = 1;
+            if (stall && t == 0 && *stall) {                       // test hook: a wait nothing ends
+                s_ok = bounded_wait(stall + 1, 1, ctr + 1, limit);
+                *stall = 0;
+            }
+        }
+        __syncthreads();
+        if (s_ok && tid < 32) {
+            const int ok = warp_wait_kids(done + (int64_t)b * ts.nq, kids, nk, false, ctr + 1, limit);
+            if (tid == 0) s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) {
+            if (tid == 0) atomicExch(&nm.stat->timeout, 1);
+            break;
+        }
+        // ---- children's contributions, in child order for every entry; each
+        // thread holds four entries of one row and keeps up to 16 loads in flight
+        for (int i = tx; i < Fr; i += 32)
+            for (int jb = ty; jb < Fc; jb += 32) {
+                T acc[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[k] = jb + 8 * k < Fc ? M[i + (jb + 8 * k) * Fr] : T(0);
+                for (int c = 0; c < nk; c += 4) {
+                    T v[4][4];
+                    unsigned valid = 0u;
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        const int cc = c + g;
+                        const int sr = cc < nk ? smap[2 * cc * W + i] : -1;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int j = jb + 8 * k;
+                            const int sc = (cc < nk && j < Fc) ? smap[(2 * cc + 1) * W + j] : -1;
+                            const bool ok = sr >= 0 && sc >= 0;
+                            v[g][k] = ok ? __ldcg(nm.cb + kids[cc].cb_off + sr + (int64_t)sc * kids[cc].mc) : T(0);
+                            valid |= ok ? (1u << (4 * g + k)) : 0u;
+                        }
+                    }
+#pragma unroll
+                    for (int g = 0; g < 4; ++g)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            if (valid & (1u << (4 * g + k))) acc[k] += v[g][k];
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (jb + 8 * k < Fc) M[i + (jb + 8 * k) * Fr] = acc[k];
+            }
+        __syncthreads();
+        // ---- w pivot steps of right-looking elimination without pivoting, one
+        // barrier per pivot: step p forms l_ip = m_ip / u_pp on the fly (the
+        // value stored when column p is scaled one step later), updates the
+        // trailing entries, and the thread owning entry (p+1, p+1) finalizes
+        // the next pivot and its reciprocal (one reciprocal per pivot)
+        if (tid == 0 && w > 0) {
+            const T pv = static_pivot(M[0], floorT, nm.stat, lead);
+            M[0] = pv;
+            s_rinv[0] = T(1) / pv;
+        }
+        __syncthreads();
+        if (Fr <= 32 && Fc <= 32) {
+            // mini fronts of at most 32 x 32 (always when w <= 16): one row and
+            // four columns per thread, all loads issued before the updates; the
+            // owner of entry (p+1, p+1) (thread 0) finishes it first
+            for (int p = 0; p < w; ++p) {
+                const T rinv = s_rinv[p];
+                if (p > 0 && ty == (p - 1) % 8)                    // deferred scaling of column p-1
+                    for (int i = p + tx; i < Fr; i += 32) M[i + (p - 1) * Fr] *= s_rinv[p - 1];
+                const int i = p + 1 + tx;
+                if (i < Fr) {
+                    const T l = M[i + p * Fr] * rinv;
+                    T mv[4], uv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int j = p + 1 + ty + 8 * k;
+                        mv[k] = j < Fc ? M[i + j * Fr] : T(0);
+                        uv[k] = j < Fc ? M[p + j * Fr] : T(0);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mv[k] -= l * uv[k];
+                    if (tid == 0 && p + 1 < w) {
+                        const T pv = static_pivot(mv[0], floorT, nm.stat, lead);
+                        mv[0] = pv;
+                        s_rinv[p + 1] = T(1) / pv;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int j = p + 1 + ty + 8 * k;
+                        if (j < Fc) M[i + j * Fr] = mv[k];
+                    }
+                }
+                __syncthreads();
+            }
+        } else {
+            for (int p = 0; p < w; ++p) {
+                const T rinv = s_rinv[p];
+                if (p > 0 && ty == (p - 1) % 8)                    // deferred scaling of column p-1
+                    for (int i = p + tx; i < Fr; i += 32) M[i + (p - 1) * Fr] *= s_rinv[p - 1];
+                for (int i = p + 1 + tx; i < Fr; i += 32) {
+                    const T l = M[i + p * Fr] * rinv;
+                    for (int j = p + 1 + ty; j < Fc; j += 8) {
+                        const T a = M[i + j * Fr] - l * M[p + j * Fr];
+                        if (i == p + 1 && j == p + 1 && p + 1 < w) {
+                            const T pv = static_pivot(a, floorT, nm.stat, lead);
+                            M[i + j * Fr] = pv;
+                            s_rinv[p + 1] = T(1) / pv;
+                        } else {
+                            M[i + j * Fr] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (w > 0)
+            for (int i = w + tid; i < Fr; i += 256) M[i + (w - 1) * Fr] *= s_rinv[w - 1];
+        __syncthreads();
+        // ---- results: pivot block (lead unit), L21 rows (tj == 0), U12 columns (ti == 0), CB tile
+        T* pan = nm.panel + d.panel_off;
+        if (lead)
+            for (int c = ty; c < w; c += 8)
+                for (int a = tx; a < w; a += 32) pan[a + (int64_t)c * F] = M[a + c * Fr];
+        if (ut.tj == 0)
+            for (int c = ty; c < w; c += 8)
+                for (int r = tx; r < nr; r += 32) pan[(w + i0 + r) + (int64_t)c * F] = M[(w + r) + c * Fr];
+        if (ut.ti == 0) {
+            T* U12 = pan + (int64_t)F * w;
+            for (int c = ty; c < nc; c += 8)
+                for (int a = tx; a < w; a += 32) U12[a + (int64_t)(j0 + c) * w] = M[a + (w + c) * Fr];
+        }
+        T* C = nm.cb + d.cb_off;
+        for (int c = ty; c < nc; c += 8)
+            for (int r = tx; r < nr; r += 32) C[(i0 + r) + (int64_t)(j0 + c) * m] = M[(w + r) + (w + c) * Fr];
+        signal_done(done + (int64_t)b * ts.nq + q);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ forward substitution
+
+// Pivot-block substitutions by one warp (w <= 32), lane i holding entry i in a
+// register and the pivot entry broadcast with a shuffle: the same operations
+// in the same order as the shared-memory loops of every other solve kernel.
+// v (length >= w) and the blocks are in shared memory; called by warp 0.
+// Forward, unit lower L (column-major, leading dimension ld): for p ascending,
+// v_i -= l_ip v_p for i > p.
+template <typename T>
+__device__ __forceinline__ void warp_lower_solve(T* v, const T* L, int ld, int w)
+{
+    const int lane = threadIdx.x & 31;
+    T x = lane < w ? v[lane] : T(0);
+    T li[32];
+#pragma unroll
+    for (int p = 0; p < 32; ++p) li[p] = (p < w && lane < w) ? L[lane + p * ld] : T(0);
+#pragma unroll
+    for (int p = 0; p < 32; ++p) {
+        if (p >= w) break;
+        const T xp = __shfl_sync(0xffffffffu, x, p);
+        if (lane > p) x -= li[p] * xp;
+    }
+    if (lane < w) v[lane] = x;
+    __syncwarp();
+}
+
+// Backward, upper U (column-major, leading dimension w) with reciprocals
+// rcp_p = 1 / u_pp: for p descending, x_p = v_p * rcp_p, v_a -= u_ap x_p for a < p.
+template <typename T>
+__device__ __forceinline__ void warp_upper_solve(T* v, const T* U, const T* rcp, int w)
+{
+    const int lane = threadIdx.x & 31;
+    T x = lane < w ? v[lane] : T(0);
+    const T r = lane < w ? rcp[lane] : T(0);
+    T ua[32];
+#pragma unroll
+    for (int p = 0; p < 32; ++p) ua[p] = (p < w && lane < w) ? U[lane + p * w] : T(0);
+#pragma unroll
+    for (int p = 31; p >= 0; --p) {
+        if (p >= w) continue;
+        const T xp = __shfl_sync(0xffffffffu, x * r, p);
+        if (lane == p) x = xp;
+        else if (lane < p) x -= ua[p] * xp;
+    }
+    if (lane < w) v[lane] = x;
+    __syncwarp();
+}
+
+// Front q of instance b (128 threads): gather the pivot entries and the
+// children's contribution vectors, solve with the unit lower pivot block,
+// update the other rows with L21 and leave them as the contribution vector.
+template <typename T>
+__global__ void __launch_bounds__(128) tree_fwd_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
+                                                       long long limit)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ TreeFront d;
+    __shared__ TreeKid kids[kTreeMaxKids];
+    __shared__ int s_t, s_ok;
+    __shared__ int s_cut[kTreeMaxKids + 1];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int total = ts.nq * B;
+    int* done = ctr + kCtrHead;
+    T* v = reinterpret_cast<T*>(smraw);
+    T* P = v + ts.max_F;                                        // staged panel (F x w) or L11 (w x w)
+    T* sval = P + (ts.fwd_stage ? ts.max_fw : ts.max_w * ts.max_w);
+    int* spos = reinterpret_cast<int*>(sval + kTreeStage);
+    for (;;) {
+        const int t = next_ticket(ctr + 2, ctr + 1, total, &s_t);
+        if (t >= total) break;
+        const int q = t / B, b = t - q * B;
+        copy_words(&d, ts.fr + q, 1, tid, 128);
+        __syncthreads();
+        const DevNum<T> nm = nm0.at(b);
+        const int w = d.w, F = d.F, first = d.first;
+        const int nk = d.kid_end - d.kid_begin;
+        const T* pan = nm.panel + d.panel_off;
+        const int ldp = ts.fwd_stage ? F : w;
+        for (int a = tid; a < F; a += 128) v[a] = a < w ? nm.vec[first + a] : T(0);
+        if (ts.fwd_stage) {
+            for (int c = tid >> 5; c < w; c += 4)
+                for (int a = lane; a < F; a += 32) P[a + c * F] = pan[a + (int64_t)c * F];
+        } else {
+            for (int c = tid >> 5; c < w; c += 4)
+                for (int a = lane; a < w; a += 32) P[a + c * w] = pan[a + (int64_t)c * F];
+        }
+        copy_words(kids, ts.kid + d.kid_begin, nk, tid, 128);
+        __syncthreads();
+        if (tid == 0) {
+            // children's entries, staged in passes of at most kTreeStage
+            int acc = 0;
+            s_cut[0] = 0;
+            for (int c = 0; c < nk; ++c) {
+                acc += kids[c].mc;
+                s_cut[c + 1] = acc;
+            }
+        }
+        __syncthreads();
+        const bool one_pass = s_cut[nk] <= kTreeStage;
+        if (one_pass)                                             // positions do not depend on the children
+            for (int c = 0; c < nk; ++c) {
+                const int* rl = s.rel + kids[c].rel_ptr;
+                for (int tt = tid; tt < kids[c].mc; tt += 128) spos[s_cut[c] + tt] = rl[tt];
+            }
+        if (tid < 32) {
+            const int ok = warp_wait_kids(done + (int64_t)b * ts.nq, kids, nk, true, ctr + 1, limit);
+            if (tid == 0) s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) {
+            if (tid == 0) atomicExch(&nm.stat->timeout, 1);
+            break;
+        }
+        if (one_pass) {
+            for (int c = 0; c < nk; ++c) {
+                const T* cv = nm.cbv + kids[c].rel_ptr;
+                for (int tt = tid; tt < kids[c].mc; tt += 128) sval[s_cut[c] + tt] = __ldcg(cv + tt);
+            }
+            __syncthreads();
+            for (int c = 0; c < nk; ++c) {
+                for (int tt = tid; tt < kids[c].mc; tt += 128) v[spos[s_cut[c] + tt]] += sval[s_cut[c] + tt];
+                __syncthreads();
+            }
+        } else
+        for (int c0 = 0; c0 < nk;) {
+            int c1 = c0 + 1;                                      // at least one child per pass
+            while (c1 < nk && s_cut[c1 + 1] - s_cut[c0] <= kTreeStage) ++c1;
+            const int base = s_cut[c0];
+            // stage (position, value) of children c0..c1-1 in one round of loads
+            for (int c = c0; c < c1; ++c) {
+                const int mc = kids[c].mc;
+                const int* rl = s.rel + kids[c].rel_ptr;
+                const T* cv = nm.cbv + kids[c].rel_ptr;
+                const int off = s_cut[c] - base;
+                if (off + mc <= kTreeStage) {
+                    for (int tt = tid; tt < mc; tt += 128) {
+                        spos[off + tt] = rl[tt];
+                        sval[off + tt] = __ldcg(cv + tt);
+                    }
+                }
+            }
+            __syncthreads();
+            for (int c = c0; c < c1; ++c) {
+                const int mc = kids[c].mc;
+                const int off = s_cut[c] - base;
+                if (off + mc <= kTreeStage) {
+                    for (int tt = tid; tt < mc; tt += 128) v[spos[off + tt]] += sval[off + tt];
+                } else {                                          // a child larger than the stage
+                    const int* rl = s.rel + kids[c].rel_ptr;
+                    const T* cv = nm.cbv + kids[c].rel_ptr;
+                    for (int tt = tid; tt < mc; tt += 128) v[rl[tt]] += __ldcg(cv + tt);
+                }
+                __syncthreads();
+            }
+            c0 = c1;
+        }
+        if (tid < 32) {
+            if (w <= 32)
+                warp_lower_solve(v, P, ldp, w);
+            else
+                for (int p = 0; p < w; ++p) {
+                    const T xp = v[p];
+                    for (int i = p + 1 + lane; i < w; i += 32) v[i] -= P[i + p * ldp] * xp;
+                    __syncwarp();
+                }
+        }
+        __syncthreads();
+        for (int i = w + tid; i < F; i += 128) {
+            T acc = v[i];
+            if (ts.fwd_stage)
+                for (int p = 0; p < w; ++p) acc -= P[i + p * F] * v[p];
+            else
+                for (int p = 0; p < w; ++p) acc -= pan[i + (int64_t)p * F] * v[p];
+            v[i] = acc;
+        }
+        __syncthreads();
+        for (int a = tid; a < w; a += 128) nm.vec[first + a] = v[a];
+        T* cvo = nm.cbv + d.rel_ptr;
+        for (int tt = tid; tt < F - w; tt += 128) cvo[tt] = v[w + tt];
+        signal_done(done + (int64_t)b * ts.nq + q);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ backward substitution
+
+// Front q of instance b, tickets in reverse tree order (parents first): the
+// solution entries of the front's other rows belong to its ancestors, which
+// are complete once its parent is.
+template <typename T>
+__global__ void __launch_bounds__(128) tree_bwd_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
+                                                       long long limit)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ TreeFront d;
+    __shared__ int s_t, s_ok;
+    __shared__ T red[128];
+    __shared__ T rcp[64];                                       // 1 / u_pp of the pivot block (w <= 64)
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int total = ts.nq * B;
+    int* done = ctr + kCtrHead + ts.nq * B;                     // after the forward counters
+    T* v = reinterpret_cast<T*>(smraw);
+    T* y = v + ts.max_F;                                        // own pivot entries
+    T* Us = y + ts.max_w;
+    T* U12s = Us + ts.max_w * ts.max_w;
+    int* ridx = reinterpret_cast<int*>(U12s + (ts.bwd_stage ? ts.max_wm : 0));
+    for (;;) {
+        const int t = next_ticket(ctr + 3, ctr + 1, total, &s_t);
+        if (t >= total) break;
+        const int uq = t / B, b = t - uq * B;
+        const int q = ts.nq - 1 - uq;
+        copy_words(&d, ts.fr + q, 1, tid, 128);
+        __syncthreads();
+        const DevNum<T> nm = nm0.at(b);
+        const int w = d.w, F = d.F, first = d.first, m = F - w;
+        const T* pan = nm.panel + d.panel_off;
+        const T* U12 = pan + (int64_t)F * w;
+        const int* R = s.rows + d.rows_ptr;
+        for (int tt = tid; tt < m; tt += 128) ridx[tt] = R[w + tt];
+        for (int a = tid; a < w; a += 128) y[a] = nm.vec[first + a];
+        for (int c = tid >> 5; c < w; c += 4)
+            for (int a = lane; a < w; a += 32) Us[a + c * w] = pan[a + (int64_t)c * F];
+        for (int a = tid; a < w; a += 128) rcp[a] = T(1) / pan[a + (int64_t)a * F];
+        if (ts.bwd_stage)
+            for (int e = tid; e < w * m; e += 128) U12s[e] = U12[e];
+        if (tid < 32) {
+            TreeKid par{};
+            par.q = d.parent;
+            const int ok = warp_wait_kids(done + (int64_t)b * ts.nq, &par, 1, true, ctr + 1, limit);
+            if (tid == 0) s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) {
+            if (tid == 0) atomicExch(&nm.stat->timeout, 1);
+            break;
+        }
+        for (int tt = tid; tt < m; tt += 128) v[w + tt] = __ldcg(nm.vec + ridx[tt]);
+        __syncthreads();
+        // y_a - sum_t U12[a, t] x_t, in the order every backward kernel uses:
+        // in sequence for m <= kSeqSum, else 128 / w interleaved partial sums per row
+        if (m <= kSeqSum) {
+            for (int a = tid; a < w; a += 128) {
+                T acc = y[a];
+                for (int tt = 0; tt < m; ++tt) acc -= U12[a + (int64_t)tt * w] * v[w + tt];
+                v[a] = acc;
+            }
+        } else {
+            const int G = 128 / w;
+            T part = T(0);
+            if (tid < G * w) {
+                const int a = tid % w, g = tid / w;
+                if (ts.bwd_stage)
+                    for (int tt = g; tt < m; tt += G) part += U12s[a + tt * w] * v[w + tt];
+                else
+                    for (int tt = g; tt < m; tt += G) part += U12[a + (int64_t)tt * w] * v[w + tt];
+            }
+            red[tid] = part;
+            __syncthreads();
+            for (int a = tid; a < w; a += 128) {
+                T acc = T(0);
+                for (int g = 0; g < G; ++g) acc += red[a + g * w];
+                v[a] = y[a] - acc;
+            }
+        }
+        __syncthreads();
+        if (tid < 32) {
+            if (w <= 32)
+                warp_upper_solve(v, Us, rcp, w);
+            else
+                for (int p = w - 1; p >= 0; --p) {
+                    const T xp = v[p] * rcp[p];
+                    __syncwarp();
+                    if (lane == 0) v[p] = xp;
+                    for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
+                    __syncwarp();
+                }
+        }
+        __syncthreads();
+        for (int a = tid; a < w; a += 128) nm.vec[first + a] = v[a];
+        signal_done(done + (int64_t)b * ts.nq + q);
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t tree_grid(int kind, size_t smem, int* grid)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+    if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_factor_kernel<T>, 256, smem);
+    else if (kind == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_fwd_kernel<T>, 128, smem);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_bwd_kernel<T>, 128, smem);
+    if (e != cudaSuccess) return e;
+    // at most kTreeCtasPerSm resident CTAs per SM by default (measured: more
+    // share an SM's FP64 pipe without hiding more of the dependency waits);
+    // KKT_TREE_CTAS_PER_SM overrides the cap (a tuning knob)
+    int cap = kTreeCtasPerSm;
+    if (const char* env = std::getenv("KKT_TREE_CTAS_PER_SM")) {
+        const int c = std::atoi(env);
+        if (c > 0) cap = c;
+    }
+    per = std::min(per, cap);
+    *grid = sms * (per > 0 ? per : 1);
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_tree_factor(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
+                               int* stall, long long spin_limit, int grid, size_t smem, cudaStream_t st)
+{
+    const int g = std::min<long long>(grid, (long long)t.nunits * batch);
+    if (g <= 0) return cudaSuccess;
+    tree_factor_kernel<T><<<g, 256, smem, st>>>(s, t, nm, batch, ctr, stall, spin_limit);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tree_fwd(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
+                            long long spin_limit, int grid, size_t smem, cudaStream_t st)
+{
+    const int g = std::min<long long>(grid, (long long)t.nq * batch);
+    if (g <= 0) return cudaSuccess;
+    tree_fwd_kernel<T><<<g, 128, smem, st>>>(s, t, nm, batch, ctr, spin_limit);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tree_bwd(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
+                            long long spin_limit, int grid, size_t smem, cudaStream_t st)
+{
+    const int g = std::min<long long>(grid, (long long)t.nq * batch);
+    if (g <= 0) return cudaSuccess;
+    tree_bwd_kernel<T><<<g, 128, smem, st>>>(s, t, nm, batch, ctr, spin_limit);
+    return cudaGetLastError();
+}
+
+#define KKT_TREE_INST(T)                                                                                          \
+    template cudaError_t tree_grid<T>(int, size_t, int*);                                                          \
+    template cudaError_t launch_tree_factor<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,     \
+                                               int*, long long, int, size_t, cudaStream_t);                        \
+    template cudaError_t launch_tree_fwd<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,        \
+                                            long long, int, size_t, cudaStream_t);                                 \
+    template cudaError_t launch_tree_bwd<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,        \
+                                            long long, int, size_t, cudaStream_t);
+KKT_TREE_INST(double)
+KKT_TREE_INST(float)
+
+template <typename K>
+static cudaError_t allow_smem_tree(K kernel, int optin)
+{
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
+cudaError_t configure_tree_kernels(int optin)
+{
+    cudaError_t e;
+    if ((e = allow_smem_tree(tree_factor_kernel<double>, optin))) return e;
+    if ((e = allow_smem_tree(tree_factor_kernel<float>, optin))) return e;
+    if ((e = allow_smem_tree(tree_fwd_kernel<double>, optin))) return e;
+    if ((e = allow_smem_tree(tree_fwd_kernel<float>, optin))) return e;
+    if ((e = allow_smem_tree(tree_bwd_kernel<double>, optin))) return e;
+    if ((e = allow_smem_tree(tree_bwd_kernel<float>, optin))) return e;
+    return cudaSuccess;
+}
+
+}  // namespace kktgb

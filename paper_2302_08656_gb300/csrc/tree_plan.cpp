@@ -1,0 +1,117 @@
+// Host-side plan of the tree part (see tree_plan.hpp).
+#include "tree_plan.hpp"
+
+#include <algorithm>
+
+namespace kktgb {
+
+static size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
+
+void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp)
+{
+    tp = TreePlan();
+    int split = an.n_levels;
+    if (min_fronts > 0)
+        for (int l = an.n_levels - 1; l >= 0; --l) {
+            if (an.level_ptr[l + 1] - an.level_ptr[l] >= min_fronts) break;
+            split = l;
+        }
+    // a front with more children than the kernels stage keeps its level (and all below) level-launched
+    for (int l = split; l < an.n_levels; ++l)
+        for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) {
+            int s = an.level_fronts[t];
+            if (an.child_ptr[s + 1] - an.child_ptr[s] > kTreeMaxKids) split = l + 1;
+        }
+    std::vector<int> tq(an.ns, -1);
+    int nq = 0;
+    for (int l = split; l < an.n_levels; ++l)
+        for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) tq[an.level_fronts[t]] = nq++;
+    tp.split = split;
+    tp.fr.resize(nq);
+    TreeSched& ts = tp.ts;
+    ts.nq = nq;
+    for (int l = split; l < an.n_levels; ++l)
+        for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) {
+            const int s = an.level_fronts[t];
+            const int q = tq[s];
+            TreeFront& d = tp.fr[q];
+            d.f = s;
+            d.first = an.sn_first[s];
+            d.w = an.sn_first[s + 1] - d.first;
+            d.F = an.sn_front[s];
+            const int w = d.w, F = d.F, m = F - w;
+            d.ts = w < kTile ? 2 * kTile - w : kTile;            // 32 x 32 mini fronts when w <= 16
+            d.nt = m > 0 ? (m + d.ts - 1) / d.ts : 1;
+            d.units = d.nt * d.nt;
+            d.parent = an.sn_parent[s] >= 0 ? tq[an.sn_parent[s]] : -1;
+            d.asm_begin = an.asm_ptr[s];
+            d.asm_end = an.asm_ptr[s + 1];
+            d.panel_off = an.panel_off[s];
+            d.cb_off = an.cb_off[s];
+            d.rel_ptr = an.rel_ptr[s];
+            d.rows_ptr = an.rows_ptr[s];
+            d.inv_off = (int64_t)tp.inv.size();
+            d.kid_begin = (int)tp.kid.size();
+            for (int c = an.child_ptr[s]; c < an.child_ptr[s + 1]; ++c) {
+                const int ch = an.child_list[c];
+                TreeKid k{};
+                k.q = tq[ch];
+                k.mc = an.sn_front[ch] - (an.sn_first[ch + 1] - an.sn_first[ch]);
+                k.k = an.cb_split[ch];
+                k.units = k.q >= 0 ? tp.fr[k.q].units : 0;
+                k.cb_off = an.cb_off[ch];
+                k.rel_ptr = an.rel_ptr[ch];
+                tp.kid.push_back(k);
+                const size_t base = tp.inv.size();
+                tp.inv.resize(base + m, -1);
+                for (int r = 0; r < k.mc; ++r) {
+                    const int pos = an.rel[an.rel_ptr[ch] + r];
+                    if (pos >= w) tp.inv[base + (pos - w)] = r;
+                }
+            }
+            d.kid_end = (int)tp.kid.size();
+            for (int tj = 0; tj < d.nt; ++tj)
+                for (int ti = 0; ti < d.nt; ++ti) tp.unit.push_back(FrontTile{q, ti, tj});
+            const int side = w + std::min(d.ts, m);
+            ts.m_elems = std::max(ts.m_elems, side * side);
+            ts.map_w = std::max(ts.map_w, side);
+            ts.max_kids = std::max(ts.max_kids, d.kid_end - d.kid_begin);
+            ts.max_F = std::max(ts.max_F, F);
+            ts.max_w = std::max(ts.max_w, w);
+            ts.max_fw = std::max(ts.max_fw, F * w);
+            ts.max_wm = std::max(ts.max_wm, w * m);
+        }
+    ts.nunits = (int)tp.unit.size();
+    ts.max_kids = std::max(ts.max_kids, 1);
+    ts.fwd_stage = (size_t)ts.max_fw * es <= kStageLimit ? 1 : 0;
+    ts.bwd_stage = (size_t)ts.max_wm * es <= kStageLimit ? 1 : 0;
+    tp.fac_smem = tree_factor_smem(ts, es);
+    tp.fwd_smem = tree_fwd_smem(ts, es);
+    tp.bwd_smem = tree_bwd_smem(ts, es);
+    if (nq > 0 && (tp.fac_smem > kTreeSmemLimit || tp.fwd_smem > kTreeSmemLimit || tp.bwd_smem > kTreeSmemLimit)) {
+        TreePlan none;                                            // fronts too large: every level launched
+        none.split = an.n_levels;
+        tp = none;
+    }
+}
+
+
+size_t tree_factor_smem(const TreeSched& t, size_t es)
+{
+    return align16(es * (size_t)t.m_elems) + align16(sizeof(int) * 2 * (size_t)t.max_kids * t.map_w) +
+           sizeof(TreeKid) * (size_t)t.max_kids;
+}
+
+size_t tree_fwd_smem(const TreeSched& t, size_t es)
+{
+    size_t b = es * ((size_t)t.max_F + (t.fwd_stage ? (size_t)t.max_fw : (size_t)t.max_w * t.max_w) + kTreeStage);
+    return b + 4 * (size_t)kTreeStage;
+}
+
+size_t tree_bwd_smem(const TreeSched& t, size_t es)
+{
+    size_t b = es * ((size_t)t.max_F + t.max_w + (size_t)t.max_w * t.max_w + (t.bwd_stage ? (size_t)t.max_wm : 0));
+    return b + 4 * (size_t)t.max_F;
+}
+
+}  // namespace kktgb

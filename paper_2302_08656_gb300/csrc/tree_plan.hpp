@@ -1,0 +1,36 @@
+// Host-side plan of the tree part of the schedule: the top levels of the
+// assembly tree that the persistent kernels (tree.cu) refactor and solve.
+#pragma once
+#include "analysis.hpp"
+#include "kernels.cuh"
+
+#include <cstddef>
+#include <vector>
+
+namespace kktgb {
+
+constexpr size_t kTreeSmemLimit = 220 * 1024;   // dynamic shared memory of one CTA
+constexpr size_t kStageLimit = 96 * 1024;       // largest staged panel / U12 block
+
+// Fronts of the levels from `split` up, in level-major order (tree index q),
+// their children, factorization units and gather maps; shared-memory sizes
+// of the three kernels.
+struct TreePlan {
+    int split = 0;
+    std::vector<TreeFront> fr;
+    std::vector<TreeKid> kid;
+    std::vector<FrontTile> unit;
+    std::vector<int> inv;
+    TreeSched ts;
+    size_t fac_smem = 0, fwd_smem = 0, bwd_smem = 0;
+};
+
+// min_fronts: the top levels with fewer fronts than this go to the tree part
+// (0: none); es: bytes per factor value.
+void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp);
+
+size_t tree_factor_smem(const TreeSched& t, size_t es);
+size_t tree_fwd_smem(const TreeSched& t, size_t es);
+size_t tree_bwd_smem(const TreeSched& t, size_t es);
+
+}  // namespace kktgb

@@ -105,3 +105,21 @@ def test_one_by_one_and_diagonal_plans():
     ci = np.arange(n, dtype=np.int32)
     info = K.plan(rp, ci)
     assert info["nnz_lu"] == n and info["n_levels"] == 1
+
+
+def test_plan_tree_part_follows_the_option():
+    """The persistent kernels take the narrow top of the tree: none with
+    tree_min_fronts = 0, every level with a huge threshold, a contiguous top
+    part in between; the option is validated."""
+    pat = KKTPattern(make_grid(4, 2000, 2560, 400))
+    none = K.plan(pat.rowptr, pat.colidx, tree_min_fronts=0)
+    dflt = K.plan(pat.rowptr, pat.colidx)
+    full = K.plan(pat.rowptr, pat.colidx, tree_min_fronts=10 ** 9)
+    assert none["tree_levels"] == 0 and none["tree_units"] == 0
+    assert 0 < dflt["tree_levels"] < dflt["n_levels"]
+    assert full["tree_levels"] == full["n_levels"] and full["tree_units"] >= full["n_fronts"]
+    assert none["nnz_lu"] == dflt["nnz_lu"] == full["nnz_lu"]
+    with pytest.raises(K.KKTError):
+        K.plan(pat.rowptr, pat.colidx, tree_min_fronts=-1)
+    with pytest.raises(K.KKTError):
+        K.plan(pat.rowptr, pat.colidx, spin_limit=0)
