@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--max-pivots", type=int, default=None, help="pivots per supernode (library default if unset)")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one instead of CUDA graphs")
+    ap.add_argument("--assemble", action="store_true",
+                    help="each step also evaluates the model on the GPU (K values from the iterate)")
     ap.add_argument("--tree-min-fronts", type=int, default=None,
                     help="levels with fewer fronts run in the persistent tree kernels (library default if unset)")
     return ap.parse_args()
@@ -519,6 +521,93 @@ def run_serving(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ IPM step with GPU model evaluation
+
+def run_ipm(args):
+    """One step = GPU model evaluation of K_k from the iterate (V, theta,
+    lambda, Sigma) + refactor + solve + refinement; e2e copies the iterate
+    (not the nnz values of K) to the device and the solution back."""
+    import torch
+    import paper_2302_08656_gb300 as K
+
+    dev = torch.device("cuda", 0)
+    w = WORKLOADS[args.workload]
+    grid = make_grid(args.seed, w["n_bus"], w["n_branch"], w["n_gen"])
+    pat = KKTPattern(grid)
+    mus = mu_schedule(w["mu0"], w["mu1"], w["steps"])
+    n_in = args.warmup + args.steps
+    pts = [pat.point(args.seed, i % len(mus), mus[i % len(mus)]) for i in range(n_in)]
+    rhs_h = [pat.rhs(args.seed, i % len(mus)) for i in range(n_in)]
+    it_h = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (p.V, p.theta, p.lam, p.sigma)]
+            for p in pts]
+    b_h = [torch.from_numpy(b).pin_memory() for b in rhs_h]
+    it_d = [[a.to(dev) for a in it] for it in it_h]
+    b_d = [b.to(dev) for b in b_h]
+    model = K.KKTModel.from_grid(grid)
+    opts = {"precision": args.precision}
+    if args.tree_min_fronts is not None:
+        opts["tree_min_fronts"] = args.tree_min_fronts
+    s = K.KKTSolver(model.rowptr, model.colidx, model.n_primal, **opts)
+    vals = torch.empty(model.nnz, dtype=torch.float64, device=dev)
+    x = torch.empty(pat.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    pt0 = pts[0]
+
+    def step(i, V, th, lam, sig, b):
+        model.assemble(V, th, lam, sig, pt0.delta_w, pt0.delta_c, out=vals)
+        s.refactor(vals)
+        _, info = s.refine(b, out=x, tol=args.tol, raise_on_noconv=False)
+        return info
+
+    for i in range(args.warmup):
+        step(i, *it_d[i], b_d[i])
+    ms, oms = [], []
+    sampler = ClockSampler(0)
+    sampler.start()
+    for t in range(args.steps):
+        i = args.warmup + t
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = step(i, *it_d[i], b_d[i])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        oms.append(info.backward_err)
+    clocks = sampler.stop()
+    xh = torch.empty(pat.n, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for t in range(args.steps):
+        i = args.warmup + t
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dv = [a.to(dev, non_blocking=True) for a in it_h[i]]
+        db = b_h[i].to(dev, non_blocking=True)
+        step(i, *dv, db)
+        xh.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    h2d = int(sum(a.numel() * 8 for a in it_h[0]) + b_h[0].numel() * 8)
+    line = {
+        "metric": METRIC, "value": 1000.0 * len(ms) / sum(ms), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "assemble": True, "n": pat.n, "nnz": pat.nnz,
+                   "precision": args.precision, "tol": args.tol, "l2": "flushed between timed steps (512 MB write)",
+                   "note": "one step = GPU model evaluation + refactor + solve + refinement"},
+        "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+        "omega_max": float(max(oms)),
+        "e2e": {"value": 1000.0 * len(e2e_ms) / sum(e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": int(8 * pat.n), "p99_ms": float(np.percentile(e2e_ms, 99))},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+    model.close()
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -529,6 +618,8 @@ def main():
         run_batch(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.assemble:
+        run_ipm(args)
     else:
         run_native(args)
 

@@ -42,6 +42,7 @@ extern "C" {
 #endif
 
 typedef struct kkt_ctx kkt_ctx;
+typedef struct kkt_model kkt_model;
 
 typedef enum {
     KKT_OK = 0,
@@ -248,6 +249,60 @@ kkt_status kkt_get_info(const kkt_ctx *ctx, kkt_info *info);
 kkt_status kkt_backward_error_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_colidx,
                                       const double *d_vals, const double *d_x, const double *d_rhs,
                                       double *d_r, double *d_omega, void *stream);
+
+/* ---- GPU model evaluation: the KKT values of one interior-point iterate.
+ *
+ * The step before the linear solve in every Newton iteration: evaluating
+ * the Hessian of the Lagrangian and the constraint Jacobian of the ACOPF
+ * problem (Eqs. 1-4, 11) at the current iterate. The paper measures model
+ * evaluation at about 30 % of the CPU run time (Sec. III, cost breakdown) and
+ * projects a 2x overall speedup once it runs on the GPU (Sec. IV). Model:
+ * polar voltages, line flow leaving bus i on line (i, j) with admittance
+ * g + jb = 1 / (r + jx), no shunts, unit taps: P = g V_i^2 - V_i V_j (g cos t
+ * + b sin t), Q = -b V_i^2 - V_i V_j (g sin t - b cos t), t = theta_i -
+ * theta_j; active and reactive power balance per bus (flows leaving with a
+ * minus sign, generators with +1); optionally the apparent-power limits
+ * P^2 + Q^2 <= S^2 at both ends of every line; objective sum c2 Pg^2.
+ * Variables: x = (|V|_1..B, theta_1..B, Pg_1..G, Qg_1..G) (n_primal = 2B + 2G);
+ * constraint rows: P balance 1..B, Q balance 1..B, then (with limits) the
+ * from-end and to-end limit of every line. The assembled matrix is
+ * K = [[H + Sigma + dw I, J^T], [J, -dc I]] (full symmetric CSR). */
+
+enum { KKT_MODEL_FLOW_LIMITS = 1,   /* include the line-flow limit rows */
+       KKT_MODEL_HOST_ONLY = 2 };    /* build the pattern only: no device memory, no assembly */
+
+/* Build the model of a grid and its KKT sparsity pattern (host, once per
+ * grid). Lines: h_from / h_to bus indices (0-based, distinct ends), series
+ * resistance h_r and reactance h_x (pu, r^2 + x^2 > 0); generators: bus
+ * h_gen_bus and cost coefficient h_c2. All host arrays are read and copied.
+ * flags: KKT_MODEL_* bits. Unless KKT_MODEL_HOST_ONLY, allocates the model's
+ * device memory on the current device (line data, summation lists, one
+ * scratch array of 40 doubles per line).
+ * Errors: KKT_E_ARG (bad index, size or flag), KKT_E_NOMEM, KKT_E_CUDA. */
+kkt_status kkt_model_create(int32_t n_bus, int32_t n_branch, int32_t n_gen, const int32_t *h_from,
+                            const int32_t *h_to, const double *h_r, const double *h_x,
+                            const int32_t *h_gen_bus, const double *h_c2, int flags,
+                            kkt_model **out);
+
+/* The model's KKT pattern: *n rows, *n_primal, *nnz; h_rowptr (n + 1) and
+ * h_colidx (nnz) may be NULL to query the sizes. Columns sorted, unique,
+ * every diagonal stored (ready for kkt_analyze). Host only. */
+kkt_status kkt_model_pattern(const kkt_model *m, int32_t *n, int32_t *n_primal, int64_t *nnz,
+                             int32_t *h_rowptr, int32_t *h_colidx);
+
+/* Values of K at one iterate into d_vals (device, nnz, the pattern's order):
+ * d_V, d_theta (n_bus each), d_lambda (constraint multipliers, one per
+ * constraint row in the order above), d_sigma (barrier diagonal, n_primal;
+ * zero on angles) are device FP64 arrays; delta_w / delta_c are the primal and
+ * dual regularizations. Deterministic (fixed summation order, no atomics).
+ * Asynchronous on `stream`; calls on one model must not overlap (they share
+ * the model's scratch). Errors: KKT_E_ARG, KKT_E_STATE (host-only model),
+ * KKT_E_CUDA. */
+kkt_status kkt_model_assemble(const kkt_model *m, const double *d_V, const double *d_theta,
+                              const double *d_lambda, const double *d_sigma, double delta_w,
+                              double delta_c, double *d_vals, void *stream);
+
+kkt_status kkt_model_destroy(kkt_model *m);
 
 /* Failure-injection hook for tests (no counterpart in the paper): the next
  * refactorization's first unit of the persistent tree kernel waits on a flag

@@ -13,7 +13,7 @@ import numpy as np
 
 from ._native import Info, KernelStat, Options, PlanInfo, build, lib
 
-__all__ = ["KKTSolver", "KKTError", "plan", "refactor_batched", "solve_batched", "build",
+__all__ = ["KKTSolver", "KKTModel", "KKTError", "plan", "refactor_batched", "solve_batched", "build",
            "FP64", "FP32_IR", "Options", "Info", "PlanInfo"]
 
 FP64, FP32_IR = 0, 1
@@ -223,6 +223,64 @@ class KKTSolver:
                                         C.byref(nu), ur.ctypes.data, uc.ctypes.data, uv.ctypes.data),
                "kkt_export_factors")
         return lr, lc, lv, ur, uc, uv
+
+
+class KKTModel:
+    """GPU model evaluation of one grid: the KKT values of an interior-point
+    iterate (Hessian of the Lagrangian, constraint Jacobian, barrier and
+    regularization diagonals) in the model's own CSR pattern."""
+
+    FLOW_LIMITS, HOST_ONLY = 1, 2
+
+    def __init__(self, n_bus, f, t, r, x, gen_bus, c2, flow_limits=True, host_only=False):
+        self._keep = [np.ascontiguousarray(a, dtype=dt) for a, dt in
+                      ((f, np.int32), (t, np.int32), (r, np.float64), (x, np.float64), (gen_bus, np.int32),
+                       (c2, np.float64))]
+        ff, tt, rr, xx, gb, cc = self._keep
+        flags = (self.FLOW_LIMITS if flow_limits else 0) | (self.HOST_ONLY if host_only else 0)
+        h = C.c_void_p()
+        _check(lib().kkt_model_create(int(n_bus), ff.size, gb.size, ff.ctypes.data, tt.ctypes.data, rr.ctypes.data,
+                                      xx.ctypes.data, gb.ctypes.data, cc.ctypes.data, flags, C.byref(h)),
+               "kkt_model_create")
+        self._h = h
+        self.n_bus = int(n_bus)
+        n, npr, nnz = C.c_int32(0), C.c_int32(0), C.c_int64(0)
+        _check(lib().kkt_model_pattern(h, C.byref(n), C.byref(npr), C.byref(nnz), None, None), "kkt_model_pattern")
+        self.n, self.n_primal, self.nnz = n.value, npr.value, nnz.value
+        self.rowptr = np.empty(self.n + 1, np.int32)
+        self.colidx = np.empty(self.nnz, np.int32)
+        _check(lib().kkt_model_pattern(h, C.byref(n), C.byref(npr), C.byref(nnz), self.rowptr.ctypes.data,
+                                       self.colidx.ctypes.data), "kkt_model_pattern")
+
+    @classmethod
+    def from_grid(cls, grid, flow_limits=True, host_only=False):
+        """From any object with n_bus, f, t, r, x, gen_bus, c2 attributes."""
+        return cls(grid.n_bus, grid.f, grid.t, grid.r, grid.x, grid.gen_bus, grid.c2, flow_limits, host_only)
+
+    def assemble(self, V, theta, lam, sigma, delta_w=1e-8, delta_c=1e-10, out=None, stream=None):
+        """K values (device float64, nnz) from device float64 V, theta (n_bus),
+        lam (constraint rows) and sigma (n_primal)."""
+        import torch
+        for a in (V, theta, lam, sigma):
+            assert a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+        assert V.numel() == theta.numel() == self.n_bus and sigma.numel() == self.n_primal
+        assert lam.numel() == self.n - self.n_primal
+        if out is None:
+            out = torch.empty(self.nnz, dtype=torch.float64, device=V.device)
+        _check(lib().kkt_model_assemble(self._h, _ptr(V), _ptr(theta), _ptr(lam), _ptr(sigma), float(delta_w),
+                                        float(delta_c), _ptr(out), _stream(stream)), "kkt_model_assemble")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kkt_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def backward_error_noalloc(rowptr, colidx, vals, x, rhs, r, omega, stream=None):

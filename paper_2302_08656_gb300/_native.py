@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libkkt_gb300.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["analysis.cpp", "tree_plan.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu", "tree.cu"]
+SOURCES = ["analysis.cpp", "tree_plan.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu", "tree.cu", "model.cu"]
 HEADERS = ["analysis.hpp", "kernels.cuh", "tree_plan.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -144,6 +144,11 @@ SIGNATURES = {
     "kkt_get_scaling": (C.c_int, [_P, _P]),
     "kkt_export_factors": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, C.POINTER(C.c_int64), _P, _P, _P]),
     "kkt_debug_stall": (C.c_int, [_P]),
+    "kkt_model_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, C.c_int,
+                                   C.POINTER(_P)]),
+    "kkt_model_pattern": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64), _P, _P]),
+    "kkt_model_assemble": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, _P, _P]),
+    "kkt_model_destroy": (C.c_int, [_P]),
     "kkt_backward_error_noalloc": (C.c_int, [C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "kkt_destroy": (C.c_int, [_P]),
     "kkt_status_string": (C.c_char_p, [C.c_int]),
