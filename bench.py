@@ -63,6 +63,26 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", "1")))
 
 
+def rank_seed(base, rank):
+    """Every rank solves its own scenario sequence (replicas, weak scaling)."""
+    return base + 1000 * rank
+
+
+def reduce_max(x, device=None):
+    """Max over the ranks of a host float: one all-reduce, the only
+    collective of the bench (timing, not data path)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, steps, max_total_ms):
+    """Whole-job throughput: the steps of every rank over the slowest rank's time."""
+    return world * steps / (max_total_ms / 1000.0)
+
+
 def workload(name, seed):
     w = WORKLOADS[name]
     grid = make_grid(seed, w["n_bus"], w["n_branch"], w["n_gen"])
@@ -215,7 +235,7 @@ def run_native(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
-    seed = args.seed + 1000 * rank          # independent scenario per rank
+    seed = rank_seed(args.seed, rank)       # independent scenario per rank
     w, pat, mus = workload(args.workload, seed)
     n_in = args.warmup + args.steps
     vals_h, rhs_h = inputs(pat, mus, seed, n_in)
@@ -269,11 +289,8 @@ def run_native(args):
     clocks = sampler.stop()
     total_ms = sum(ms)
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+        total_ms = reduce_max(total_ms, device=dev)
+    value = aggregate_rate(world, args.steps, total_ms)
 
     # mixed precision on the same matrices (the graded comparison: FP32 LU + FP64 FGMRES vs plain FP64)
     other = None
