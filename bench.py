@@ -166,6 +166,13 @@ def algorithmic_bytes(plan, n, nnz, wbytes):
     }
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the same command (profiles/), keyed by (kernel, workload,
+# precision, tree levels); an entry is removed whenever the kernel changes.
+MEASURED_TRAFFIC = {
+    ("tree_factor_kernel", "northeast25k", "fp64", 58): 21335040 + 309504,
+}
+
 PHASE_OF = {
     "front_warp_kernel": "refactor", "front_cta_kernel": "refactor", "front_panel_kernel": "refactor",
     "schur_tile_kernel": "refactor", "ruiz_kernel": "refactor", "scale_kernel": "refactor",
@@ -348,22 +355,27 @@ def run_native(args):
     peak_src = "measured" if hbm else "fallback"
     hbm = hbm or 6800.0
     roofline = None
-    if dom and PHASE_OF.get(dom):
-        ph = PHASE_OF[dom]
-        n_units = {"refactor": nprof, "solve": None, "spmv": None}[ph]
-        if ph == "refactor":
-            bytes_total = ab["refactor"] * nprof
+    if dom:
+        ph = PHASE_OF.get(dom, "refactor")
+        if dom == "tree_factor_kernel":
+            # the kernel's own algorithmic bytes: original entries, panels, contribution blocks
+            n_units = stats[dom][0]
+            bytes_unit = plan["tree_bytes"]
+            kms = stats[dom][1] / max(1, n_units)
         else:
-            # solves / spmv per profiled step: count launches of the phase's post kernel
-            key = "solve_post_kernel" if ph == "solve" else "spmv_resid_kernel"
-            n_units = stats.get(key, (0, 0.0))[0]
-            bytes_total = ab[ph] * n_units
-        achieved = bytes_total / (phase_ms[ph] / 1000.0) / 1e9
+            n_units = nprof if ph == "refactor" else stats.get(
+                "solve_post_kernel" if ph == "solve" else "spmv_resid_kernel", (0, 0.0))[0]
+            bytes_unit = ab[ph]
+            kms = phase_ms[ph] / max(1, n_units)
+        achieved = bytes_unit / (kms / 1000.0) / 1e9
+        key = (dom, args.workload, args.precision, plan["tree_levels"])
+        traffic = MEASURED_TRAFFIC.get(key)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": None, "kernel": dom, "phase": ph,
-                    "peak_source": peak_src,
-                    "algorithmic_bytes_per_unit": ab[ph], "units_profiled": n_units,
-                    "phase_ms_per_unit": phase_ms[ph] / max(1, n_units)}
+                    "frac": achieved / hbm, "traffic": traffic, "kernel": dom, "peak_source": peak_src,
+                    "algorithmic_bytes_per_launch": bytes_unit, "launches_profiled": n_units,
+                    "ms_per_launch": kms,
+                    "refactor_phase": {"algorithmic_bytes": ab["refactor"], "ms": phase_ms.get("refactor", 0.0) / nprof,
+                                       "achieved_gbs": ab["refactor"] / (phase_ms.get("refactor", 1e-9) / nprof / 1000.0) / 1e9}}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:

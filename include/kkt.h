@@ -126,6 +126,9 @@ typedef struct {
     int batch;                  /* instances of the context (kkt_get_plan) */
     int tree_levels;            /* top levels run by the persistent tree kernels */
     int tree_units;             /* refactorization work units of those kernels (one instance) */
+    int64_t tree_bytes;         /* algorithmic bytes one refactorization by the tree kernel moves
+                                   (one instance): original entries (value, position, source),
+                                   factor panels written, contribution blocks written and read once */
 } kkt_plan_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -118,6 +118,7 @@ class PlanInfo(C.Structure):
         ("batch", C.c_int),
         ("tree_levels", C.c_int),
         ("tree_units", C.c_int),
+        ("tree_bytes", C.c_int64),
     ]
 
 

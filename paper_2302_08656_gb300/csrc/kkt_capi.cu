@@ -78,6 +78,7 @@ struct kkt_ctx {
     // persistent kernels of the tree part
     TreeSched tsched;
     int tree_split = 0;
+    int64_t tree_bytes = 0;
     size_t tf_smem = 0, tfw_smem = 0, tbw_smem = 0;
     int tf_grid = 0, tfw_grid = 0, tbw_grid = 0;
     int* ctr_fac = nullptr;          // counter block of the refactorization kernel
@@ -834,6 +835,7 @@ kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx,
                                        stride * mpg, (int64_t)inv.size(), f12_total, tp);
         out->tree_levels = an.n_levels - tp.split;
         out->tree_units = (int)tp.unit.size();
+        out->tree_bytes = tp.alg_bytes;
     } catch (const std::bad_alloc&) {
         return KKT_E_NOMEM;
     } catch (...) {
@@ -1009,6 +1011,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     c->tsched = tp.ts;
     c->tsched.fr = tfr; c->tsched.kid = tkid; c->tsched.unit = tunit; c->tsched.inv = tinv;
     c->tree_split = tp.split;
+    c->tree_bytes = tp.alg_bytes;
     c->tf_smem = tp.fac_smem; c->tfw_smem = tp.fwd_smem; c->tbw_smem = tp.bwd_smem;
     if (nq > 0) {
         const bool f32 = c->opt.precision == KKT_FP32_IR;
@@ -1251,6 +1254,7 @@ kkt_status kkt_get_plan(const kkt_ctx* c, kkt_plan_info* out)
     out->batch = c->batch;
     out->tree_levels = an.n_levels - c->tree_split;
     out->tree_units = c->tsched.nunits;
+    out->tree_bytes = c->tree_bytes;
     return KKT_OK;
 }
 

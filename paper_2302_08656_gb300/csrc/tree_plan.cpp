@@ -70,6 +70,10 @@ void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp)
                 }
             }
             d.kid_end = (int)tp.kid.size();
+            // original entries (value + position + source index), panel, own CB written, children's CB read
+            tp.alg_bytes += (d.asm_end - d.asm_begin) * (int64_t)(es + 8) + ((int64_t)F * w + (int64_t)w * m) * (int64_t)es +
+                            (int64_t)m * m * (int64_t)es;
+            for (int c = d.kid_begin; c < d.kid_end; ++c) tp.alg_bytes += (int64_t)tp.kid[c].mc * tp.kid[c].mc * (int64_t)es;
             for (int tj = 0; tj < d.nt; ++tj)
                 for (int ti = 0; ti < d.nt; ++ti) tp.unit.push_back(FrontTile{q, ti, tj});
             const int side = w + std::min(d.ts, m);

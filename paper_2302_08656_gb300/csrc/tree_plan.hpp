@@ -23,6 +23,7 @@ struct TreePlan {
     std::vector<int> inv;
     TreeSched ts;
     size_t fac_smem = 0, fwd_smem = 0, bwd_smem = 0;
+    int64_t alg_bytes = 0;              // algorithmic bytes of one refactorization of the tree part
 };
 
 // min_fronts: the top levels with fewer fronts than this go to the tree part
