@@ -60,6 +60,9 @@ enum { KKT_FP64 = 0,      /* factors and triangular solves in FP64 */
        KKT_FP32_IR = 1 }; /* factors and triangular solves in FP32 (FP32 accumulation);
                              scaling, residual and FGMRES stay FP64 */
 
+enum { KKT_PRECOND_LU = 0,       /* refinement preconditioned by the exact triangular solves */
+       KKT_PRECOND_JACOBI = 1 };  /* ... by Jacobi sweeps with the factors (approximate, Sec. V) */
+
 enum { KKT_ORDER_MINDEG = 0,  /* the library's quotient-graph minimum degree */
        KKT_ORDER_USER = 1,    /* kkt_options.user_perm */
        KKT_ORDER_NATURAL = 2 };
@@ -90,6 +93,10 @@ typedef struct {
     long long spin_limit;       /* polls (about 100 ns each) of a bounded device wait of those
                                    kernels before it gives up and the call reports
                                    KKT_E_TIMEOUT (default 1 << 23, about a second) */
+    int precond;                /* KKT_PRECOND_* for kkt_refine and kkt_precondition
+                                   (default KKT_PRECOND_LU) */
+    int jacobi_sweeps;          /* sweeps per triangular factor with KKT_PRECOND_JACOBI
+                                   (default 4, 1..1000000) */
 } kkt_options;
 
 typedef struct {
@@ -190,6 +197,15 @@ kkt_status kkt_solve(kkt_ctx *ctx, const double *d_rhs, double *d_x, void *strea
  * Errors: KKT_E_ARG, KKT_E_STATE, KKT_E_CUDA, KKT_E_NOCONV, KKT_E_NUMERIC. */
 kkt_status kkt_refine(kkt_ctx *ctx, const double *d_rhs, double *d_x, double tol,
                       kkt_info *info, void *stream);
+
+/* z = M^{-1} r with the context's preconditioner (kkt_options.precond): the
+ * exact triangular solves (as kkt_solve) or Jacobi sweeps with the factors,
+ * the approximate triangular solves the paper proposes instead of the
+ * level-scheduled ones (Sec. V): from y_0 = x_0 = 0, y_{s+1} = c - (L - I) y_s
+ * and x_{s+1} = diag(U)^{-1} (y - (U - diag(U)) x_s) on c = P D r, then
+ * z = D P^T x. d_rhs and d_z are device FP64 (count x n), may not alias.
+ * Asynchronous. Errors: KKT_E_ARG, KKT_E_STATE (no refactor yet), KKT_E_CUDA. */
+kkt_status kkt_precondition(kkt_ctx *ctx, const double *d_rhs, double *d_z, void *stream);
 
 /* Asynchronous solve with a device-side accuracy check, for callers that keep
  * several solves in flight: x = K^{-1} b for every instance, then

@@ -173,6 +173,33 @@ class LU:
         return x
 
 
+def jacobi_precondition(f: Factors, d, b, sweeps: int):
+    """Approximate solve of K x = b by Jacobi sweeps with the factors of the
+    scaled, permuted matrix (Sec. V proposes iterative triangular solves in
+    place of the exact ones), written as the plain definition:
+        c = P D b;   y_0 = 0,  y_{s+1} = c - (L - I) y_s;
+        x_0 = 0,  x_{s+1} = diag(U)^{-1} (y - (U - diag(U)) x_s);
+        result = D Q x.
+    f: factors of P (D K D) Q (L unit lower with its diagonal not stored, U
+    with its diagonal last in each column), d: the equilibration factors."""
+    import scipy.sparse as sp
+    n = f.n
+    Ls = sp.csc_matrix((f.Lx, f.Li, f.Lp), shape=(n, n))        # L - I
+    U = sp.csc_matrix((f.Ux, f.Ui, f.Up), shape=(n, n))
+    du = U.diagonal()
+    Us = (U - sp.diags(du)).tocsr()
+    c = (np.asarray(d) * np.asarray(b))[f.p]
+    y = np.zeros(n)
+    for _ in range(sweeps):
+        y = c - Ls @ y
+    x = np.zeros(n)
+    for _ in range(sweeps):
+        x = (y - Us @ x) / du
+    z = np.empty(n)
+    z[f.q] = x
+    return np.asarray(d) * z
+
+
 def spmv_resid(rowptr, colidx, vals, x, b):
     rp, ci, v = _csr(rowptr, colidx, vals)
     r = np.empty(rp.size - 1)

@@ -36,7 +36,7 @@ def _check(st: int, where: str):
 
 def _opts(precision="fp64", ordering="mindeg", user_perm=None, static_pivot_eps=0.0, ruiz_iters=10,
           restart=30, max_cycles=10, relax_pivots=16, relax_zeros=0.15, max_pivots=16, graphs=True,
-          tree_min_fronts=None, spin_limit=None):
+          tree_min_fronts=None, spin_limit=None, precond="lu", jacobi_sweeps=4):
     o = Options()
     lib().kkt_default_options(C.byref(o))
     o.precision = FP32_IR if precision in ("fp32", "fp32_ir", FP32_IR) else FP64
@@ -58,6 +58,8 @@ def _opts(precision="fp64", ordering="mindeg", user_perm=None, static_pivot_eps=
         o.tree_min_fronts = int(tree_min_fronts)
     if spin_limit is not None:
         o.spin_limit = int(spin_limit)
+    o.precond = {"lu": 0, "jacobi": 1}[precond] if isinstance(precond, str) else int(precond)
+    o.jacobi_sweeps = int(jacobi_sweeps)
     return o, keep
 
 
@@ -149,13 +151,22 @@ class KKTSolver:
             _check(st, "kkt_refine")
         return out, (infos[0] if self.count == 1 else list(infos))
 
+    def precondition(self, rhs, out=None, stream=None):
+        """z = M^{-1} rhs with the context's preconditioner (exact solves or Jacobi sweeps)."""
+        import torch
+        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n * self.count
+        if out is None:
+            out = torch.empty_like(rhs)
+        _check(lib().kkt_precondition(self._h, _ptr(rhs), _ptr(out), _stream(stream)), "kkt_precondition")
+        return out
+
     def solve_checked(self, rhs, out, omega_host, stream=None):
         """Asynchronous solve + device-side backward error into omega_host
         (a pinned float64 tensor with `count` entries, valid after the stream work)."""
         _check(lib().kkt_solve_checked(self._h, _ptr(rhs), _ptr(out), C.c_void_p(omega_host.data_ptr()),
                                        _stream(stream)), "kkt_solve_checked")
 
-    def step_host(self, vals, rhs, tol=1e-10, out=None, stream=None):
+    def step_host(self, vals, rhs, tol=1e-10, out=None, stream=None, raise_on_noconv=True):
         """Refactor + refine through host buffers (copies inside the call)."""
         v = np.ascontiguousarray(vals, dtype=np.float64)
         b = np.ascontiguousarray(rhs, dtype=np.float64)
@@ -163,7 +174,8 @@ class KKTSolver:
         infos = (Info * self.count)()
         st = lib().kkt_step_host(self._h, v.ctypes.data, b.ctypes.data, x.ctypes.data, float(tol),
                                  infos, _stream(stream))
-        _check(st, "kkt_step_host")
+        if st != 6 or raise_on_noconv:
+            _check(st, "kkt_step_host")
         return x, (infos[0] if self.count == 1 else list(infos))
 
     def residual(self, rhs, x, out=None, stream=None):

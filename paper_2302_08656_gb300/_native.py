@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libkkt_gb300.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["analysis.cpp", "tree_plan.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu", "tree.cu", "model.cu"]
+SOURCES = ["analysis.cpp", "tree_plan.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu", "tree.cu", "model.cu", "jacobi.cu"]
 HEADERS = ["analysis.hpp", "kernels.cuh", "tree_plan.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -82,6 +82,8 @@ class Options(C.Structure):
         ("no_graphs", C.c_int),
         ("tree_min_fronts", C.c_int),
         ("spin_limit", C.c_longlong),
+        ("precond", C.c_int),
+        ("jacobi_sweeps", C.c_int),
     ]
 
 
@@ -145,6 +147,7 @@ SIGNATURES = {
     "kkt_get_scaling": (C.c_int, [_P, _P]),
     "kkt_export_factors": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, C.POINTER(C.c_int64), _P, _P, _P]),
     "kkt_debug_stall": (C.c_int, [_P]),
+    "kkt_precondition": (C.c_int, [_P, _P, _P, _P]),
     "kkt_model_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, C.c_int,
                                    C.POINTER(_P)]),
     "kkt_model_pattern": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64), _P, _P]),

@@ -250,4 +250,11 @@ cudaError_t launch_tree_bwd(const DevSched& s, const TreeSched& t, const DevNum<
                             long long spin_limit, int grid, size_t smem, cudaStream_t st);
 cudaError_t configure_tree_kernels(int optin);
 
+// Jacobi-sweep preconditioner (jacobi.cu): `sweeps` sweeps with L then U on
+// the step-space vector nm.vec, result in nm.vec; lptr / lidx: per step row,
+// the contribution-vector offsets of the descendant fronts' L21 rows.
+template <typename T>
+cudaError_t launch_jacobi(const DevSched& s, const DevNum<T>& nm, int sweeps, const int* lptr, const int* lidx,
+                          T* ya, T* yb, T* xa, T* t, int* launches, cudaStream_t st);
+
 }  // namespace kktgb

@@ -84,6 +84,10 @@ struct kkt_ctx {
     int* ctr_fac = nullptr;          // counter block of the refactorization kernel
     int* ctr_sol = nullptr;          // counter block of the two solve kernels
     int* stall = nullptr;            // failure-injection hook (two ints)
+    // Jacobi-sweep preconditioner: row lists of L's off-front entries, work vectors (one instance)
+    int* jl_ptr = nullptr;
+    int* jl_idx = nullptr;
+    void* jac_buf = nullptr;         // 3 n + rel.size() values in factor precision
     // refinement workspace (FP64)
     double* V = nullptr;             // n x (m+1)
     double* Z = nullptr;             // n x m
@@ -149,6 +153,8 @@ void fill_defaults(kkt_options* o)
     o->no_graphs = 0;
     o->tree_min_fronts = 2432;                  // 16 fronts per SM of a 152-SM GB300
     o->spin_limit = 1LL << 23;
+    o->precond = KKT_PRECOND_LU;
+    o->jacobi_sweeps = 4;
 }
 
 kkt_status check_options(const kkt_options& o)
@@ -161,6 +167,8 @@ kkt_status check_options(const kkt_options& o)
     if (o.max_pivots < 1 || o.max_pivots > 64) return KKT_E_ARG;
     if (o.relax_pivots < 1) return KKT_E_ARG;
     if (o.tree_min_fronts < 0 || o.spin_limit < 1) return KKT_E_ARG;
+    if (o.precond != KKT_PRECOND_LU && o.precond != KKT_PRECOND_JACOBI) return KKT_E_ARG;
+    if (o.jacobi_sweeps < 1 || o.jacobi_sweeps > 1000000) return KKT_E_ARG;
     return KKT_OK;
 }
 
@@ -293,12 +301,12 @@ DevNum<float>& num_of<float>(kkt_ctx* c) { return c->nf; }
 
 enum KernelKind { KK_RUIZ = 0, KK_SCALE, KK_FRONT_WARP, KK_FRONT_CTA, KK_FRONT_PANEL, KK_SCHUR, KK_SOLVE_PRE,
                   KK_SOLVE_FWD, KK_SOLVE_BWD, KK_SOLVE_POST, KK_SPMV, KK_REDUCE, KK_VECTOR, KK_TREE_FACTOR,
-                  KK_TREE_FWD, KK_TREE_BWD, KK_COUNT };
+                  KK_TREE_FWD, KK_TREE_BWD, KK_JACOBI, KK_COUNT };
 const char* const kKernelNames[KK_COUNT] = {
     "ruiz_kernel", "scale_kernel", "front_warp_kernel", "front_cta_kernel", "front_panel_kernel",
     "schur_tile_kernel", "solve_pre_kernel", "solve_fwd_kernel", "solve_bwd_kernel", "solve_post_kernel",
     "spmv_resid_kernel", "reduction_kernels", "vector_kernels", "tree_factor_kernel", "tree_fwd_kernel",
-    "tree_bwd_kernel"};
+    "tree_bwd_kernel", "jacobi_kernels"};
 
 // Counts kernels and, in profiling mode, brackets the launch group with a
 // pair of events on the launching stream.
@@ -516,6 +524,47 @@ kkt_status do_solve(kkt_ctx* c, const double* b, double* x, cudaStream_t st, int
     return c->opt.precision == KKT_FP32_IR ? solve_t<float>(c, b, x, st, inst) : solve_t<double>(c, b, x, st, inst);
 }
 
+// Jacobi sweeps for instance inst (b, x: that instance's vectors)
+template <typename T>
+kkt_status jacobi_t(kkt_ctx* c, const double* b, double* x, cudaStream_t st, int inst)
+{
+    const DevNum<T> nm = num_of<T>(c).at(inst);
+    const int n = c->n;
+    const int64_t nrel = std::max<int64_t>((int64_t)c->an.rel.size(), 1);
+    T* ya = reinterpret_cast<T*>(c->jac_buf);
+    T* yb = ya + n;
+    T* xa = yb + n;
+    T* t = xa + n;
+    (void)nrel;
+    {
+        Launch L(c, st, KK_SOLVE_PRE, 1);
+        KKT_CUDA(launch_solve_pre<T>(c->sched, nm, b, 1, st));
+    }
+    {
+        const int k = 2 + 3 * c->opt.jacobi_sweeps;
+        Launch L(c, st, KK_JACOBI, k);
+        KKT_CUDA(launch_jacobi<T>(c->sched, nm, c->opt.jacobi_sweeps, c->jl_ptr, c->jl_idx, ya, yb, xa, t, nullptr,
+                                  st));
+    }
+    Launch L(c, st, KK_SOLVE_POST, 1);
+    KKT_CUDA(launch_solve_post<T>(c->sched, nm, x, 1, st));
+    return KKT_OK;
+}
+
+// z = M^{-1} r with the context's preconditioner; inst < 0: every instance
+kkt_status do_precond(kkt_ctx* c, const double* b, double* x, cudaStream_t st, int inst = -1)
+{
+    if (c->opt.precond != KKT_PRECOND_JACOBI) return do_solve(c, b, x, st, inst);
+    const int i0 = inst < 0 ? 0 : inst, i1 = inst < 0 ? c->batch : inst + 1;
+    for (int i = i0; i < i1; ++i) {
+        const int64_t off = inst < 0 ? (int64_t)i * c->n : 0;
+        kkt_status s = c->opt.precision == KKT_FP32_IR ? jacobi_t<float>(c, b + off, x + off, st, i)
+                                                        : jacobi_t<double>(c, b + off, x + off, st, i);
+        if (s != KKT_OK) return s;
+    }
+    return KKT_OK;
+}
+
 // read back the device statistics of the last refactor into c->info
 kkt_status sync_stat(kkt_ctx* c, cudaStream_t st)
 {
@@ -602,7 +651,7 @@ kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double 
         for (int j = 0; j < m; ++j) {
             double* vj = c->V + (int64_t)j * n;
             double* zj = c->Z + (int64_t)j * n;
-            if ((s = do_solve(c, vj, zj, st, inst)) != KKT_OK) return s;
+            if ((s = do_precond(c, vj, zj, st, inst)) != KKT_OK) return s;
             {
                 Launch L(c, st, KK_SPMV, 1);
                 KKT_CUDA(launch_spmv(n, rp, ci, K, zj, c->w, st));
@@ -695,7 +744,7 @@ kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double 
 kkt_status do_refine(kkt_ctx* c, const double* b, double* x, double tol, kkt_info* info, cudaStream_t st)
 {
     kkt_status s;
-    if ((s = do_solve(c, b, x, st)) != KKT_OK) return s;
+    if ((s = do_precond(c, b, x, st)) != KKT_OK) return s;
     {
         Launch L(c, st, KK_SPMV, 2);
         KKT_CUDA(launch_resid_omega(c->n, c->nnz, c->sched.rowptr, c->sched.colidx, c->kvals, x, b,
@@ -794,6 +843,8 @@ static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_opti
     add(nq * (int64_t)sizeof(TreeFront)); add((int64_t)tp.kid.size() * (int64_t)sizeof(TreeKid));
     add((int64_t)tp.unit.size() * (int64_t)sizeof(FrontTile)); add((int64_t)tp.inv.size() * 4);
     add((kCtrHead + B * nq) * 4); add((kCtrHead + 2 * B * nq) * 4); add(2 * 4);
+    add((n + 1) * 4); add(std::max<int64_t>((int64_t)an.rel.size(), 1) * 4);
+    add((3 * (int64_t)n + std::max<int64_t>((int64_t)an.rel.size(), 1)) * es);
     return b;
 }
 
@@ -958,6 +1009,9 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     c->ctr_fac = P.take<int>(kCtrHead + B * nq);
     c->ctr_sol = P.take<int>(kCtrHead + 2 * B * nq);
     c->stall = P.take<int>(2);
+    c->jl_ptr = P.take<int>(n + 1);
+    c->jl_idx = P.take<int>(std::max<size_t>(an.rel.size(), 1));
+    c->jac_buf = P.take<char>((3 * (size_t)n + std::max<size_t>(an.rel.size(), 1)) * es);
     if (P.used > P.size) { kkt_destroy(c); return KKT_E_NOMEM; }
     if (cudaMallocHost(&c->pin, sizeof(double) * (4 * (kMaxRestart + 2) + 16 + B)) != cudaSuccess) {
         cudaGetLastError();
@@ -996,6 +1050,23 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     e = e ? e : up(tunit, tp.unit.data(), tp.unit.size() * sizeof(FrontTile));
     e = e ? e : up(tinv, tp.inv.data(), tp.inv.size() * 4);
     e = e ? e : cudaMemset(c->stall, 0, 2 * sizeof(int));
+    {
+        // per step row i: contribution-vector offsets rel_ptr[f] + t of every front f whose
+        // contribution row t is i, in increasing order (the gather order of the Jacobi sweeps)
+        std::vector<int> jp(n + 1, 0), ji(an.rel.size());
+        for (int f = 0; f < an.ns; ++f) {
+            const int w = an.sn_first[f + 1] - an.sn_first[f], F = an.sn_front[f];
+            for (int t = w; t < F; ++t) jp[an.rows[an.rows_ptr[f] + t] + 1]++;
+        }
+        for (int i = 0; i < n; ++i) jp[i + 1] += jp[i];
+        std::vector<int> fill(jp.begin(), jp.end() - 1);
+        for (int f = 0; f < an.ns; ++f) {
+            const int w = an.sn_first[f + 1] - an.sn_first[f], F = an.sn_front[f];
+            for (int t = w; t < F; ++t) ji[fill[an.rows[an.rows_ptr[f] + t]]++] = (int)(an.rel_ptr[f] + (t - w));
+        }
+        e = e ? e : up(c->jl_ptr, jp.data(), (n + 1) * 4);
+        e = e ? e : up(c->jl_idx, ji.data(), ji.size() * 4);
+    }
     e = e ? e : cudaMemset(c->stat, 0, sizeof(DevStat) * B);
     c->omega_pin = c->pin + 4 * (kMaxRestart + 2) + 16;
     c->infos.assign(B, kkt_info{});
@@ -1082,6 +1153,13 @@ kkt_status kkt_refine(kkt_ctx* c, const double* d_rhs, double* d_x, double tol, 
     if (!c || !d_rhs || !d_x || d_rhs == d_x || !(tol >= 0)) return KKT_E_ARG;
     if (!c->refactored) return KKT_E_STATE;
     return do_refine(c, d_rhs, d_x, tol, info, (cudaStream_t)stream);
+}
+
+kkt_status kkt_precondition(kkt_ctx* c, const double* d_rhs, double* d_z, void* stream)
+{
+    if (!c || !d_rhs || !d_z || d_rhs == d_z) return KKT_E_ARG;
+    if (!c->refactored) return KKT_E_STATE;
+    return do_precond(c, d_rhs, d_z, (cudaStream_t)stream);
 }
 
 kkt_status kkt_solve_checked(kkt_ctx* c, const double* d_rhs, double* d_x, double* h_omega, void* stream)

@@ -349,3 +349,35 @@ def test_alg1_sequence_reaches_backward_error(kkt200):
         lu, d, _ = O.refactor(pat.rowptr, pat.colidx, v, an)
         x, it, om = O.fgmres(pat.rowptr, pat.colidx, v, lu, d, b, 30, 10, 1e-12)
         assert om <= 1e-12
+
+
+def test_jacobi_precondition_pins():
+    """Jacobi sweeps with the factors (Sec. V): one sweep per factor is the
+    closed form D Q diag(U)^-1 P D b; as many sweeps as unknowns reproduce the
+    exact solve (L - I and U - diag(U) are nilpotent); sweeps leave a
+    diagonal system's exact solution unchanged."""
+    import scipy.sparse as sp
+    pat = KKTPattern(make_grid(3, 30, 40, 6))
+    v = pat.values(pat.point(3, 0, 1e-1, delta_w=1.0, delta_c=1.0))
+    an = O.analyze(pat.rowptr, pat.colidx, v)
+    lu, d, sv = O.refactor(pat.rowptr, pat.colidx, v, an)
+    f = lu.factors()
+    b = pat.rhs(3, 0)
+    n = pat.n
+    U = sp.csc_matrix((f.Ux, f.Ui, f.Up), shape=(n, n))
+    one = O.jacobi_precondition(f, d, b, 1)
+    z = np.empty(n)
+    z[f.q] = ((d * b)[f.p]) / U.diagonal()
+    assert np.allclose(one, d * z, rtol=1e-15, atol=0)
+    full = O.jacobi_precondition(f, d, b, n)
+    exact = lu.solve_scaled(d, b)
+    assert np.linalg.norm(full - exact) <= 1e-10 * np.linalg.norm(exact)
+    few = O.jacobi_precondition(f, d, b, 3)
+    assert np.linalg.norm(few - exact) > 1e-6 * np.linalg.norm(exact)      # not exact after 3 sweeps
+    rp = np.arange(4, dtype=np.int32)
+    ci = np.arange(3, dtype=np.int32)
+    dv = np.array([2.0, -4.0, 0.5])
+    an3 = O.analyze(rp, ci, dv)
+    lu3, d3, _ = O.refactor(rp, ci, dv, an3)
+    bb = np.array([1.0, 2.0, 3.0])
+    assert np.allclose(O.jacobi_precondition(lu3.factors(), d3, bb, 1), bb / dv, rtol=1e-15)
