@@ -173,7 +173,6 @@ def algorithmic_bytes(plan, n, nnz, wbytes):
 # capture of the same command (profiles/), keyed by (kernel, workload,
 # precision, tree levels); an entry is removed whenever the kernel changes.
 MEASURED_TRAFFIC = {
-    ("tree_factor_kernel", "northeast25k", "fp64", 58): 21335040 + 309504,
 }
 
 PHASE_OF = {
@@ -265,8 +264,7 @@ def run_native(args):
     def timed_run(solver, tag):
         stream = torch.cuda.current_stream()
         for i in range(args.warmup):
-            solver.refactor(vals[i])
-            solver.refine(rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
+            solver.refactor_refine(vals[i], rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
         l0 = solver.info().launches
         ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -276,8 +274,7 @@ def run_native(args):
             i = args.warmup + t
             flush.zero_()
             ev0[t].record(stream)
-            solver.refactor(vals[i])
-            _, info = solver.refine(rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
+            _, info = solver.refactor_refine(vals[i], rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
             ev1[t].record(stream)
             oms.append(info.backward_err)
             iters.append(info.iters)
@@ -340,8 +337,7 @@ def run_native(args):
     nprof = min(3, args.steps)
     for t in range(nprof):
         i = args.warmup + t
-        s64.refactor(vals[i])
-        s64.refine(rhs[i], out=xs[i], tol=args.tol)
+        s64.refactor_refine(vals[i], rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
     stats = s64.kernel_stats()
     s64.set_profiling(False)
     wbytes = 8 if args.precision == "fp64" else 4
@@ -591,8 +587,7 @@ def run_ipm(args):
 
     def step(i, V, th, lam, sig, b):
         model.assemble(V, th, lam, sig, pt0.delta_w, pt0.delta_c, out=vals)
-        s.refactor(vals)
-        _, info = s.refine(b, out=x, tol=args.tol, raise_on_noconv=False)
+        _, info = s.refactor_refine(vals, b, out=x, tol=args.tol, raise_on_noconv=False)
         return info
 
     for i in range(args.warmup):

@@ -207,6 +207,15 @@ kkt_status kkt_refine(kkt_ctx *ctx, const double *d_rhs, double *d_x, double tol
  * Asynchronous. Errors: KKT_E_ARG, KKT_E_STATE (no refactor yet), KKT_E_CUDA. */
 kkt_status kkt_precondition(kkt_ctx *ctx, const double *d_rhs, double *d_z, void *stream);
 
+/* kkt_refactor followed by kkt_refine in one call (one interior-point
+ * iteration's linear algebra, Alg. 1 loop body): with the exact preconditioner
+ * the forward substitution of the first solve runs inside the refactorization
+ * (each front is forward-substituted as soon as it and its children are
+ * done), saving the separate forward pass. Same inputs, outputs, errors and
+ * synchronization as the two calls. */
+kkt_status kkt_refactor_refine(kkt_ctx *ctx, const double *d_vals, const double *d_rhs, double *d_x,
+                               double tol, kkt_info *info, void *stream);
+
 /* Asynchronous solve with a device-side accuracy check, for callers that keep
  * several solves in flight: x = K^{-1} b for every instance, then
  * h_omega[i] = backward error omega of instance i. h_omega is host memory

@@ -130,6 +130,20 @@ class KKTSolver:
         assert vals.is_contiguous()
         _check(lib().kkt_refactor(self._h, _ptr(vals), _stream(stream)), "kkt_refactor")
 
+    def refactor_refine(self, vals, rhs, out=None, tol=1e-10, stream=None, raise_on_noconv=True):
+        """refactor + refine in one call (the first solve's forward pass rides along the refactorization)."""
+        import torch
+        assert vals.is_cuda and vals.dtype.itemsize == 8 and vals.numel() == self.nnz * self.count
+        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n * self.count
+        if out is None:
+            out = torch.empty_like(rhs)
+        infos = (Info * self.count)()
+        st = lib().kkt_refactor_refine(self._h, _ptr(vals), _ptr(rhs), _ptr(out), float(tol), infos,
+                                       _stream(stream))
+        if st != 6 or raise_on_noconv:
+            _check(st, "kkt_refactor_refine")
+        return out, (infos[0] if self.count == 1 else list(infos))
+
     def solve(self, rhs, out=None, stream=None):
         import torch
         assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n * self.count

@@ -1061,17 +1061,26 @@ cudaError_t launch_norms(int n, const double* a, double* out, cudaStream_t st)
 
 // Batched residual and backward error: grid (resid_blocks(n), batch), eight
 // lanes per row (rows hold ~10 entries), kResidRows rows per block, so that
-// thousands of blocks keep enough loads in flight; each block stores max |r|,
-// |x|, |b| and the largest K row sum of its rows in its slot of `part`;
-// omega_final_batched reduces the slots.
+// thousands of blocks keep enough loads in flight. Maxima of non-negative
+// doubles are taken on their bit patterns (integer pipes: FP64 compares are
+// slow on this GPU); ||K||_inf comes from the refactorization's statistics.
+// Each block stores max |r|, |x|, |b| of its rows (as bits) in its slot of
+// `part`; omega_final_batched reduces the slots.
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(kFull, v, o));
+    return v;
+}
+
 __global__ void __launch_bounds__(256) resid_omega_part_kernel(int n, int64_t nnz, const int* __restrict__ rp,
                                                                const int* __restrict__ ci,
                                                                const double* __restrict__ kv,
                                                                const double* __restrict__ x,
                                                                const double* __restrict__ b, double* __restrict__ r,
-                                                               double* __restrict__ part)
+                                                               unsigned long long* __restrict__ part)
 {
-    __shared__ double red[4][8];
+    __shared__ unsigned long long red[3][8];
     const int inst = blockIdx.y;
     kv += (int64_t)inst * nnz;
     x += (int64_t)inst * n;
@@ -1081,74 +1090,72 @@ __global__ void __launch_bounds__(256) resid_omega_part_kernel(int n, int64_t nn
     const int sub = threadIdx.x % kRowLanes;
     const int row0 = blockIdx.x * kResidRows;
     constexpr int kPass = 256 / kRowLanes;                          // rows per pass of the block
-    double mr = 0.0, mx = 0.0, mb = 0.0, mk = 0.0;
+    unsigned long long mr = 0ull, mx = 0ull, mb = 0ull;
 #pragma unroll
     for (int q = 0; q < kResidRows / kPass; ++q) {
         const int row = row0 + q * kPass + threadIdx.x / kRowLanes;
-        double sacc = 0.0, a = 0.0;
+        double sacc = 0.0;
         if (row < n)
-            for (int p = rp[row] + sub; p < rp[row + 1]; p += kRowLanes) {
-                const double k = kv[p];
-                sacc += k * x[ci[p]];
-                a += fabs(k);
-            }
+            for (int p = rp[row] + sub; p < rp[row + 1]; p += kRowLanes) sacc += kv[p] * x[ci[p]];
         sacc = group_sum(sacc);
-        a = group_sum(a);
-        if (row < n) {
+        if (row < n && sub == 0) {
             const double ri = b[row] - sacc;
-            if (sub == 0) r[row] = ri;
-            mr = fmax(mr, fabs(ri));
-            mx = fmax(mx, fabs(x[row]));
-            mb = fmax(mb, fabs(b[row]));
-            mk = fmax(mk, a);
+            r[row] = ri;
+            mr = umax64(mr, abs_bits(ri));
+            mx = umax64(mx, abs_bits(x[row]));
+            mb = umax64(mb, abs_bits(b[row]));
         }
     }
-    mr = warp_max(mr); mx = warp_max(mx); mb = warp_max(mb); mk = warp_max(mk);
-    if (lane == 0) { red[0][wid] = mr; red[1][wid] = mx; red[2][wid] = mb; red[3][wid] = mk; }
+    mr = warp_umax(mr); mx = warp_umax(mx); mb = warp_umax(mb);
+    if (lane == 0) { red[0][wid] = mr; red[1][wid] = mx; red[2][wid] = mb; }
     __syncthreads();
-    if (threadIdx.x < 4) {
-        double m = 0.0;
-        for (int q = 0; q < 8; ++q) m = fmax(m, red[threadIdx.x][q]);
+    if (threadIdx.x < 3) {
+        unsigned long long m = 0ull;
+        for (int q = 0; q < 8; ++q) m = umax64(m, red[threadIdx.x][q]);
         part[((int64_t)inst * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = m;
     }
 }
 
-__global__ void __launch_bounds__(256) omega_final_batched_kernel(int nblk, const double* __restrict__ part,
+__global__ void __launch_bounds__(256) omega_final_batched_kernel(int nblk, const unsigned long long* __restrict__ part,
+                                                                  const DevStat* __restrict__ stat,
                                                                   double* __restrict__ omega)
 {
-    __shared__ double red[4][8];
+    __shared__ unsigned long long red[3][8];
     const int inst = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const double* pp = part + (int64_t)inst * nblk * 4;
-    double mr = 0.0, mx = 0.0, mb = 0.0, mk = 0.0;
+    const unsigned long long* pp = part + (int64_t)inst * nblk * 4;
+    unsigned long long mr = 0ull, mx = 0ull, mb = 0ull;
     for (int i = threadIdx.x; i < nblk; i += 256) {
-        mr = fmax(mr, pp[4 * i + 0]);
-        mx = fmax(mx, pp[4 * i + 1]);
-        mb = fmax(mb, pp[4 * i + 2]);
-        mk = fmax(mk, pp[4 * i + 3]);
+        mr = umax64(mr, pp[4 * i + 0]);
+        mx = umax64(mx, pp[4 * i + 1]);
+        mb = umax64(mb, pp[4 * i + 2]);
     }
-    mr = warp_max(mr); mx = warp_max(mx); mb = warp_max(mb); mk = warp_max(mk);
-    if (lane == 0) { red[0][wid] = mr; red[1][wid] = mx; red[2][wid] = mb; red[3][wid] = mk; }
+    mr = warp_umax(mr); mx = warp_umax(mx); mb = warp_umax(mb);
+    if (lane == 0) { red[0][wid] = mr; red[1][wid] = mx; red[2][wid] = mb; }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int q = 1; q < 8; ++q) {
-            red[0][0] = fmax(red[0][0], red[0][q]);
-            red[1][0] = fmax(red[1][0], red[1][q]);
-            red[2][0] = fmax(red[2][0], red[2][q]);
-            red[3][0] = fmax(red[3][0], red[3][q]);
+            red[0][0] = umax64(red[0][0], red[0][q]);
+            red[1][0] = umax64(red[1][0], red[1][q]);
+            red[2][0] = umax64(red[2][0], red[2][q]);
         }
-        const double den = red[3][0] * red[1][0] + red[2][0];
-        omega[inst] = den > 0.0 ? red[0][0] / den : red[0][0];
+        const double rmax = __longlong_as_double((long long)red[0][0]);
+        const double xmax = __longlong_as_double((long long)red[1][0]);
+        const double bmax = __longlong_as_double((long long)red[2][0]);
+        const double knorm = __longlong_as_double((long long)stat[inst].knorm_bits);
+        const double den = knorm * xmax + bmax;
+        omega[inst] = den > 0.0 ? rmax / den : rmax;
     }
 }
 
 cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci, const double* kvals,
-                               const double* x, const double* b, double* r, double* part, double* omega,
-                               int batch, cudaStream_t st)
+                               const double* x, const double* b, double* r, double* part, const DevStat* stat,
+                               double* omega, int batch, cudaStream_t st)
 {
     const int nblk = resid_blocks(n);
-    resid_omega_part_kernel<<<dim3(nblk, batch), 256, 0, st>>>(n, nnz, rp, ci, kvals, x, b, r, part);
-    omega_final_batched_kernel<<<batch, 256, 0, st>>>(nblk, part, omega);
+    unsigned long long* up = reinterpret_cast<unsigned long long*>(part);
+    resid_omega_part_kernel<<<dim3(nblk, batch), 256, 0, st>>>(n, nnz, rp, ci, kvals, x, b, r, up);
+    omega_final_batched_kernel<<<batch, 256, 0, st>>>(nblk, up, stat, omega);
     return cudaGetLastError();
 }
 

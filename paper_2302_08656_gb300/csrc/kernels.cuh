@@ -159,6 +159,9 @@ struct TreeSched {
     const TreeFront* fr = nullptr;
     const TreeKid* kid = nullptr;
     const FrontTile* unit = nullptr;   // factorization units in dependency order (front = tree index)
+    const FrontTile* unit_fused = nullptr;  // the same with a forward-solve unit (ti = -1) per front after its level
+    int nunits_fused = 0;
+    size_t kid_off = 0;                // shared-memory offset of the children's descriptors (factor kernel)
     const int* inv = nullptr;          // gather maps: parent CB row -> child CB row or -1
     // shared-memory layout parameters (host computed)
     int max_kids = 0, map_w = 0, m_elems = 0;
@@ -210,9 +213,10 @@ cudaError_t launch_solve_post(const DevSched& s, const DevNum<T>& nm, double* x,
 // part holds batch * resid_blocks(n) * 4 doubles
 constexpr int kResidRows = 64;         // rows per block of the residual kernel
 inline int resid_blocks(int n) { return (n + kResidRows - 1) / kResidRows; }
+// ||K||_inf of every instance is read from stat[inst].knorm_bits (the refactorization's scaling pass)
 cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci, const double* kvals,
-                               const double* x, const double* b, double* r, double* part, double* omega,
-                               int batch, cudaStream_t st);
+                               const double* x, const double* b, double* r, double* part, const DevStat* stat,
+                               double* omega, int batch, cudaStream_t st);
 
 // FP64 vector kernels for the residual and FGMRES.
 cudaError_t launch_spmv_resid(int n, const int* rp, const int* ci, const double* v, const double* x,
@@ -239,9 +243,11 @@ cudaError_t launch_zero_stat(DevStat* stat, cudaStream_t st);
 // caller before the launch); stall = optional test hook (see kkt_debug_stall).
 template <typename T>
 cudaError_t tree_grid(int kind, size_t smem, int* grid);   // kind 0 factor, 1 forward, 2 backward
+// fused != 0: the factor kernel also runs the forward substitution of every tree front (its counter
+// block then holds batch * nq factor counters followed by batch * nq forward counters)
 template <typename T>
 cudaError_t launch_tree_factor(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
-                               int* stall, long long spin_limit, int grid, size_t smem, cudaStream_t st);
+                               int* stall, long long spin_limit, int grid, size_t smem, int fused, cudaStream_t st);
 template <typename T>
 cudaError_t launch_tree_fwd(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
                             long long spin_limit, int grid, size_t smem, cudaStream_t st);

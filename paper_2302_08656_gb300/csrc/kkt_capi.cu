@@ -118,6 +118,8 @@ struct kkt_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t g_factor = nullptr, g_solve = nullptr;
     long long g_factor_kernels = 0, g_solve_kernels = 0;
+    cudaGraphExec_t g_ffwd = nullptr, g_bwd = nullptr;     // fused refactor + forward solve; backward solve
+    long long g_ffwd_kernels = 0, g_bwd_kernels = 0;
     bool capturing = false;
     // state
     const double* last_vals = nullptr;
@@ -368,12 +370,18 @@ kkt_status capture(kkt_ctx* c, cudaGraphExec_t* exec, long long* kernels, F&& bo
 }
 
 template <typename T>
-kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st)
+kkt_status fwd_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st);
+
+// fused: the forward substitution of the right-hand side staged in nm.vec
+// rides along (level-launched part after its factorization, tree part inside
+// the persistent kernel)
+template <typename T>
+kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused = false)
 {
     const int* fr = c->fronts_dev;
     const int B = c->batch;
     const int nq = c->tsched.nq;
-    if (nq > 0) KKT_CUDA(cudaMemsetAsync(c->ctr_fac, 0, sizeof(int) * (kCtrHead + (size_t)B * nq), st));
+    if (nq > 0) KKT_CUDA(cudaMemsetAsync(c->ctr_fac, 0, sizeof(int) * (kCtrHead + 2 * (size_t)B * nq), st));
     for (const LevelGroup& g : c->levels) {
         if (g.warp_cnt) {
             Launch L(c, st, KK_FRONT_WARP, 1);
@@ -394,21 +402,25 @@ kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st)
             KKT_CUDA(launch_schur_tiles<T>(c->sched, nm, c->tiles_dev + g.tile_off, g.tile_cnt, g.panel_maxW, B, st));
         }
     }
+    if (fused) {
+        kkt_status s = fwd_levels<T>(c, nm, B, st);
+        if (s != KKT_OK) return s;
+    }
     if (nq > 0) {
         Launch L(c, st, KK_TREE_FACTOR, 1);
         KKT_CUDA(launch_tree_factor<T>(c->sched, c->tsched, nm, B, c->ctr_fac, c->stall, c->opt.spin_limit,
-                                       c->tf_grid, c->tf_smem, st));
+                                       c->tf_grid, c->tf_smem, fused ? 1 : 0, st));
     }
     return KKT_OK;
 }
 
+// forward substitution of the level-launched part: fronts with F <= 32 a warp
+// each; larger ones (the CTA and panel classes, contiguous in the front
+// list) a CTA each
 template <typename T>
-kkt_status solve_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st)
+kkt_status fwd_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st)
 {
     const int* fr = c->fronts_dev;
-    const int nq = c->tsched.nq;
-    // fronts with F <= 32: a warp each; larger ones (the CTA and panel classes,
-    // contiguous in the front list): a CTA each; then the tree part
     for (size_t l = 0; l < c->levels.size(); ++l) {
         const LevelGroup& g = c->levels[l];
         const int nbig = g.cta_cnt + g.panel_cnt;
@@ -421,9 +433,20 @@ kkt_status solve_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st)
             KKT_CUDA(launch_solve_fwd_cta<T>(c->sched, nm, fr + g.cta_off, nbig, g.big_maxF, g.big_maxW, B, st));
         }
     }
+    return KKT_OK;
+}
+
+// backward substitution (tree part, then the level-launched part); with_fwd:
+// the tree part's forward substitution first (the solve path; the fused
+// refactorization has done it already)
+template <typename T>
+kkt_status bwd_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st, bool with_fwd)
+{
+    const int* fr = c->fronts_dev;
+    const int nq = c->tsched.nq;
     if (nq > 0) {
         KKT_CUDA(cudaMemsetAsync(c->ctr_sol, 0, sizeof(int) * (kCtrHead + 2 * (size_t)B * nq), st));
-        {
+        if (with_fwd) {
             Launch L(c, st, KK_TREE_FWD, 1);
             KKT_CUDA(launch_tree_fwd<T>(c->sched, c->tsched, nm, B, c->ctr_sol, c->opt.spin_limit, c->tfw_grid,
                                         c->tfw_smem, st));
@@ -445,6 +468,13 @@ kkt_status solve_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st)
         }
     }
     return KKT_OK;
+}
+
+template <typename T>
+kkt_status solve_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st)
+{
+    kkt_status s = fwd_levels<T>(c, nm, B, st);
+    return s != KKT_OK ? s : bwd_levels<T>(c, nm, B, st, true);
 }
 
 template <typename T>
@@ -504,6 +534,54 @@ kkt_status solve_t(kkt_ctx* c, const double* b, double* x, cudaStream_t st, int 
         Launch L(c, st, KK_SOLVE_POST, 1);
         KKT_CUDA(launch_solve_post<T>(c->sched, nm, x, B, st));
     }
+    return KKT_OK;
+}
+
+// Refactorization with the forward substitution of b riding along, then the
+// backward substitution into x: the first solve of kkt_refactor_refine.
+template <typename T>
+kkt_status refactor_solve_t(kkt_ctx* c, const double* d_vals, const double* b, double* x, cudaStream_t st)
+{
+    DevNum<T>& nm = num_of<T>(c);
+    nm.vals = d_vals;
+    const int B = c->batch;
+    KKT_CUDA(cudaMemsetAsync(c->stat, 0, sizeof(DevStat) * B, st));
+    double* dfin = nullptr;
+    {
+        Launch L(c, st, KK_RUIZ, 1 + c->opt.ruiz_iters);
+        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->d_a, c->d_b, c->opt.ruiz_iters, c->stat, &dfin, B, st));
+    }
+    c->d_final = dfin;
+    nm.d = dfin;
+    {
+        Launch L(c, st, KK_SCALE, 1);
+        KKT_CUDA(launch_scale<T>(c->sched, nm, dfin, B, st));
+    }
+    {
+        Launch L(c, st, KK_SOLVE_PRE, 1);
+        KKT_CUDA(launch_solve_pre<T>(c->sched, nm, b, B, st));
+    }
+    if (!c->profile && !c->opt.no_graphs) {
+        if (!c->g_ffwd) {
+            kkt_status cs = capture(c, &c->g_ffwd, &c->g_ffwd_kernels,
+                                    [&](cudaStream_t cst) { return factor_levels<T>(c, nm, cst, true); });
+            if (cs != KKT_OK) return cs;
+        }
+        if (!c->g_bwd) {
+            kkt_status cs = capture(c, &c->g_bwd, &c->g_bwd_kernels,
+                                    [&](cudaStream_t cst) { return bwd_levels<T>(c, nm, B, cst, false); });
+            if (cs != KKT_OK) return cs;
+        }
+        c->launches += c->g_ffwd_kernels + c->g_bwd_kernels;
+        KKT_CUDA(cudaGraphLaunch(c->g_ffwd, st));
+        KKT_CUDA(cudaGraphLaunch(c->g_bwd, st));
+    } else {
+        kkt_status s = factor_levels<T>(c, nm, st, true);
+        if (s == KKT_OK) s = bwd_levels<T>(c, nm, B, st, false);
+        if (s != KKT_OK) return s;
+    }
+    Launch L(c, st, KK_SOLVE_POST, 1);
+    KKT_CUDA(launch_solve_post<T>(c->sched, nm, x, B, st));
     return KKT_OK;
 }
 
@@ -741,14 +819,42 @@ kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double 
 
 // Solve all instances, evaluate every backward error on the device in one
 // pass, and run FGMRES only for the instances above tol.
+kkt_status refine_tail(kkt_ctx* c, const double* b, double* x, double tol, kkt_info* info, cudaStream_t st);
+
 kkt_status do_refine(kkt_ctx* c, const double* b, double* x, double tol, kkt_info* info, cudaStream_t st)
 {
     kkt_status s;
     if ((s = do_precond(c, b, x, st)) != KKT_OK) return s;
+    return refine_tail(c, b, x, tol, info, st);
+}
+
+// Refactor and refine in one call: with the exact preconditioner and a tree
+// part, the first solve's forward substitution rides along the
+// refactorization; then residual, backward error and FGMRES as kkt_refine.
+kkt_status do_refactor_refine(kkt_ctx* c, const double* d_vals, const double* b, double* x, double tol,
+                              kkt_info* info, cudaStream_t st)
+{
+    if (c->opt.precond == KKT_PRECOND_JACOBI || c->tsched.nq == 0) {
+        kkt_status s = do_refactor(c, d_vals, st);
+        return s != KKT_OK ? s : do_refine(c, b, x, tol, info, st);
+    }
+    c->info.status = KKT_OK;
+    kkt_status s = c->opt.precision == KKT_FP32_IR ? refactor_solve_t<float>(c, d_vals, b, x, st)
+                                                  : refactor_solve_t<double>(c, d_vals, b, x, st);
+    if (s != KKT_OK) return s;
+    c->last_vals = c->kvals;
+    c->refactored = 1;
+    c->refactor_count++;
+    return refine_tail(c, b, x, tol, info, st);
+}
+
+kkt_status refine_tail(kkt_ctx* c, const double* b, double* x, double tol, kkt_info* info, cudaStream_t st)
+{
+    kkt_status s;
     {
         Launch L(c, st, KK_SPMV, 2);
         KKT_CUDA(launch_resid_omega(c->n, c->nnz, c->sched.rowptr, c->sched.colidx, c->kvals, x, b,
-                                    c->r_batch, c->omega_part, c->omega_dev, c->batch, st));
+                                    c->r_batch, c->omega_part, c->stat, c->omega_dev, c->batch, st));
     }
     KKT_CUDA(cudaMemcpyAsync(c->omega_pin, c->omega_dev, sizeof(double) * c->batch, cudaMemcpyDeviceToHost, st));
     if ((s = sync_stat(c, st)) != KKT_OK) return s;      // synchronizes st
@@ -842,7 +948,8 @@ static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_opti
     const int64_t nq = (int64_t)tp.fr.size();
     add(nq * (int64_t)sizeof(TreeFront)); add((int64_t)tp.kid.size() * (int64_t)sizeof(TreeKid));
     add((int64_t)tp.unit.size() * (int64_t)sizeof(FrontTile)); add((int64_t)tp.inv.size() * 4);
-    add((kCtrHead + B * nq) * 4); add((kCtrHead + 2 * B * nq) * 4); add(2 * 4);
+    add((int64_t)tp.unit_fused.size() * (int64_t)sizeof(FrontTile));
+    add((kCtrHead + 2 * B * nq) * 4); add((kCtrHead + 2 * B * nq) * 4); add(2 * 4);
     add((n + 1) * 4); add(std::max<int64_t>((int64_t)an.rel.size(), 1) * 4);
     add((3 * (int64_t)n + std::max<int64_t>((int64_t)an.rel.size(), 1)) * es);
     return b;
@@ -1005,8 +1112,9 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     TreeFront* tfr = P.take<TreeFront>(nq);
     TreeKid* tkid = P.take<TreeKid>(tp.kid.size());
     FrontTile* tunit = P.take<FrontTile>(tp.unit.size());
+    FrontTile* tunit_fused = P.take<FrontTile>(tp.unit_fused.size());
     int* tinv = P.take<int>(tp.inv.size());
-    c->ctr_fac = P.take<int>(kCtrHead + B * nq);
+    c->ctr_fac = P.take<int>(kCtrHead + 2 * B * nq);
     c->ctr_sol = P.take<int>(kCtrHead + 2 * B * nq);
     c->stall = P.take<int>(2);
     c->jl_ptr = P.take<int>(n + 1);
@@ -1048,6 +1156,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     e = e ? e : up(tfr, tp.fr.data(), nq * sizeof(TreeFront));
     e = e ? e : up(tkid, tp.kid.data(), tp.kid.size() * sizeof(TreeKid));
     e = e ? e : up(tunit, tp.unit.data(), tp.unit.size() * sizeof(FrontTile));
+    e = e ? e : up(tunit_fused, tp.unit_fused.data(), tp.unit_fused.size() * sizeof(FrontTile));
     e = e ? e : up(tinv, tp.inv.data(), tp.inv.size() * 4);
     e = e ? e : cudaMemset(c->stall, 0, 2 * sizeof(int));
     {
@@ -1081,6 +1190,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     s.cb_split = cb_split; s.inv_off = inv_off_d; s.inv = inv_d; s.f12_off = f12_off_d;
     c->tsched = tp.ts;
     c->tsched.fr = tfr; c->tsched.kid = tkid; c->tsched.unit = tunit; c->tsched.inv = tinv;
+    c->tsched.unit_fused = tunit_fused;
     c->tree_split = tp.split;
     c->tree_bytes = tp.alg_bytes;
     c->tf_smem = tp.fac_smem; c->tfw_smem = tp.fwd_smem; c->tbw_smem = tp.bwd_smem;
@@ -1155,6 +1265,13 @@ kkt_status kkt_refine(kkt_ctx* c, const double* d_rhs, double* d_x, double tol, 
     return do_refine(c, d_rhs, d_x, tol, info, (cudaStream_t)stream);
 }
 
+kkt_status kkt_refactor_refine(kkt_ctx* c, const double* d_vals, const double* d_rhs, double* d_x, double tol,
+                               kkt_info* info, void* stream)
+{
+    if (!c || !d_vals || !d_rhs || !d_x || d_rhs == d_x || !(tol >= 0)) return KKT_E_ARG;
+    return do_refactor_refine(c, d_vals, d_rhs, d_x, tol, info, (cudaStream_t)stream);
+}
+
 kkt_status kkt_precondition(kkt_ctx* c, const double* d_rhs, double* d_z, void* stream)
 {
     if (!c || !d_rhs || !d_z || d_rhs == d_z) return KKT_E_ARG;
@@ -1172,7 +1289,7 @@ kkt_status kkt_solve_checked(kkt_ctx* c, const double* d_rhs, double* d_x, doubl
     {
         Launch L(c, st, KK_SPMV, 2);
         KKT_CUDA(launch_resid_omega(c->n, c->nnz, c->sched.rowptr, c->sched.colidx, c->kvals, d_x, d_rhs,
-                                    c->r_batch, c->omega_part, c->omega_dev, c->batch, st));
+                                    c->r_batch, c->omega_part, c->stat, c->omega_dev, c->batch, st));
     }
     KKT_CUDA(cudaMemcpyAsync(h_omega, c->omega_dev, sizeof(double) * c->batch, cudaMemcpyDeviceToHost, st));
     return KKT_OK;
@@ -1185,9 +1302,7 @@ kkt_status kkt_step_host(kkt_ctx* c, const double* h_vals, const double* h_rhs, 
     cudaStream_t st = (cudaStream_t)stream;
     KKT_CUDA(cudaMemcpyAsync(c->stage_vals, h_vals, sizeof(double) * c->nnz * c->batch, cudaMemcpyHostToDevice, st));
     KKT_CUDA(cudaMemcpyAsync(c->stage_b, h_rhs, sizeof(double) * c->n * c->batch, cudaMemcpyHostToDevice, st));
-    kkt_status s = do_refactor(c, c->stage_vals, st);
-    if (s != KKT_OK) return s;
-    kkt_status r = do_refine(c, c->stage_b, c->stage_x, tol, info, st);
+    kkt_status r = do_refactor_refine(c, c->stage_vals, c->stage_b, c->stage_x, tol, info, st);
     if (r != KKT_OK && r != KKT_E_NOCONV) return r;
     KKT_CUDA(cudaMemcpyAsync(h_x, c->stage_x, sizeof(double) * c->n * c->batch, cudaMemcpyDeviceToHost, st));
     KKT_CUDA(cudaStreamSynchronize(st));
@@ -1415,6 +1530,8 @@ kkt_status kkt_destroy(kkt_ctx* c)
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->g_factor) cudaGraphExecDestroy(c->g_factor);
     if (c->g_solve) cudaGraphExecDestroy(c->g_solve);
+    if (c->g_ffwd) cudaGraphExecDestroy(c->g_ffwd);
+    if (c->g_bwd) cudaGraphExecDestroy(c->g_bwd);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->work_stream) cudaStreamDestroy(c->work_stream);
     if (c->done_event) cudaEventDestroy(c->done_event);

@@ -59,13 +59,14 @@ __device__ bool bounded_wait(const int* p, int need, int* abort_flag, long long 
 // complete, 0 if the wait gave up (the abort flag is then set) or another CTA
 // aborted the kernel. Called by warp 0 only.
 __device__ int warp_wait_kids(const int* done_b, const TreeKid* kids, int nk, bool one, int* abort_flag,
-                              long long limit)
+                              long long limit, const int* extra = nullptr, int extra_need = 0)
 {
     const int lane = threadIdx.x & 31;
     for (long long it = 0;; ++it) {
         bool ok = true;
         for (int c = lane; c < nk; c += 32)
             if (kids[c].q >= 0 && ld_acquire(done_b + kids[c].q) < (one ? 1 : kids[c].units)) ok = false;
+        if (extra && lane == 0 && ld_acquire(extra) < extra_need) ok = false;
         if (__all_sync(0xffffffffu, ok)) return 1;
         if ((it & 31) == 31) {
             int stop = 0;
@@ -112,6 +113,11 @@ __device__ __forceinline__ void copy_words(X* dst, const X* src, int count, int 
         reinterpret_cast<int*>(dst)[e] = reinterpret_cast<const int*>(src)[e];
 }
 
+template <typename T, int NT>
+__device__ bool fwd_unit(const DevSched& s, const TreeSched& ts, const DevNum<T>& nm, const TreeFront& d, int q,
+                         TreeKid* kids, int* s_cut, int* s_ok, unsigned char* smraw, int* done_b,
+                         const int* fac_done, int* abort_flag, long long limit);
+
 // ------------------------------------------------------------- refactor
 
 // Unit (q, ti, tj) of instance b. Mini front M (Fr x Fc, column-major, ld Fr):
@@ -120,30 +126,41 @@ __device__ __forceinline__ void copy_words(X* dst, const X* src, int count, int 
 // Threads form a 32 x 8 grid (lane -> row, warp -> column).
 template <typename T>
 __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
-                                                          int* stall, long long limit)
+                                                          int* stall, long long limit, int fused)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ TreeFront d;
     __shared__ int s_t, s_ok;
     __shared__ T s_rinv[64];                                   // reciprocal of every pivot (w <= 64)
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    const int total = ts.nunits * B;
+    const int total = (fused ? ts.nunits_fused : ts.nunits) * B;
+    const FrontTile* units = fused ? ts.unit_fused : ts.unit;
     int* done = ctr + kCtrHead;
+    int* fwd_done = done + (int64_t)B * ts.nq;                     // fused mode: forward-unit counters
+    __shared__ int s_cut[kTreeMaxKids + 1];
     T* M = reinterpret_cast<T*>(smraw);
     const int W = ts.map_w;
     const size_t off_map = align16(sizeof(T) * (size_t)ts.m_elems);
-    const size_t off_kid = off_map + align16(sizeof(int) * 2 * (size_t)ts.max_kids * W);
     int* smap = reinterpret_cast<int*>(smraw + off_map);           // child c: rows at 2cW, columns at (2c+1)W
-    TreeKid* kids = reinterpret_cast<TreeKid*>(smraw + off_kid);
+    TreeKid* kids = reinterpret_cast<TreeKid*>(smraw + ts.kid_off);
     for (;;) {
         const int t = next_ticket(ctr, ctr + 1, total, &s_t);
         if (t >= total) break;
         const int u = t / B, b = t - u * B;
-        const FrontTile ut = ts.unit[u];
+        const FrontTile ut = units[u];
         const int q = ut.front;
         copy_words(&d, ts.fr + q, 1, tid, 256);
         __syncthreads();
         const DevNum<T> nm = nm0.at(b);
+        if (ut.ti < 0) {                                           // forward-solve unit (fused mode)
+            if (!fwd_unit<T, 256>(s, ts, nm, d, q, kids, s_cut, &s_ok, smraw, fwd_done + (int64_t)b * ts.nq,
+                                  done + (int64_t)b * ts.nq, ctr + 1, limit)) {
+                if (tid == 0) atomicExch(&nm.stat->timeout, 1);
+                break;
+            }
+            __syncthreads();
+            continue;
+        }
         const int w = d.w, F = d.F, m = F - w, tsz = d.ts;
         const int i0 = ut.ti * tsz, j0 = ut.tj * tsz;
         const int nr = min(tsz, m - i0), nc = min(tsz, m - j0);
@@ -375,79 +392,85 @@ __device__ __forceinline__ void warp_upper_solve(T* v, const T* U, const T* rcp,
 // Front q of instance b (128 threads): gather the pivot entries and the
 // children's contribution vectors, solve with the unit lower pivot block,
 // update the other rows with L21 and leave them as the contribution vector.
-template <typename T>
-__global__ void __launch_bounds__(128) tree_fwd_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
-                                                       long long limit)
+// Forward substitution of front q (already in d, its children in kids) by
+// NT threads: gather the pivot entries and the children's contribution
+// vectors, solve with the unit lower pivot block, update the other rows with
+// L21 and leave them as the contribution vector. fac_done (fused mode): the
+// front's own factorization units run in the same kernel; the unit then also
+// waits for them and reads the panel through L2 after the wait.
+// Returns false if a wait gave up (the caller stops).
+template <typename T, int NT>
+__device__ bool fwd_unit(const DevSched& s, const TreeSched& ts, const DevNum<T>& nm, const TreeFront& d, int q,
+                         TreeKid* kids, int* s_cut, int* s_ok, unsigned char* smraw, int* done_b,
+                         const int* fac_done, int* abort_flag, long long limit)
 {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ TreeFront d;
-    __shared__ TreeKid kids[kTreeMaxKids];
-    __shared__ int s_t, s_ok;
-    __shared__ int s_cut[kTreeMaxKids + 1];
+    constexpr int NW = NT / 32;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int total = ts.nq * B;
-    int* done = ctr + kCtrHead;
     T* v = reinterpret_cast<T*>(smraw);
     T* P = v + ts.max_F;                                        // staged panel (F x w) or L11 (w x w)
     T* sval = P + (ts.fwd_stage ? ts.max_fw : ts.max_w * ts.max_w);
     int* spos = reinterpret_cast<int*>(sval + kTreeStage);
-    for (;;) {
-        const int t = next_ticket(ctr + 2, ctr + 1, total, &s_t);
-        if (t >= total) break;
-        const int q = t / B, b = t - q * B;
-        copy_words(&d, ts.fr + q, 1, tid, 128);
-        __syncthreads();
-        const DevNum<T> nm = nm0.at(b);
-        const int w = d.w, F = d.F, first = d.first;
-        const int nk = d.kid_end - d.kid_begin;
-        const T* pan = nm.panel + d.panel_off;
-        const int ldp = ts.fwd_stage ? F : w;
-        for (int a = tid; a < F; a += 128) v[a] = a < w ? nm.vec[first + a] : T(0);
+    const int w = d.w, F = d.F, first = d.first;
+    const int nk = d.kid_end - d.kid_begin;
+    const T* pan = nm.panel + d.panel_off;
+    const int ldp = ts.fwd_stage ? F : w;
+    const bool fused = fac_done != nullptr;
+    for (int a = tid; a < F; a += NT) v[a] = a < w ? nm.vec[first + a] : T(0);
+    if (!fused) {
         if (ts.fwd_stage) {
-            for (int c = tid >> 5; c < w; c += 4)
+            for (int c = tid >> 5; c < w; c += NW)
                 for (int a = lane; a < F; a += 32) P[a + c * F] = pan[a + (int64_t)c * F];
         } else {
-            for (int c = tid >> 5; c < w; c += 4)
+            for (int c = tid >> 5; c < w; c += NW)
                 for (int a = lane; a < w; a += 32) P[a + c * w] = pan[a + (int64_t)c * F];
         }
-        copy_words(kids, ts.kid + d.kid_begin, nk, tid, 128);
-        __syncthreads();
-        if (tid == 0) {
-            // children's entries, staged in passes of at most kTreeStage
-            int acc = 0;
-            s_cut[0] = 0;
-            for (int c = 0; c < nk; ++c) {
-                acc += kids[c].mc;
-                s_cut[c + 1] = acc;
-            }
+    }
+    copy_words(kids, ts.kid + d.kid_begin, nk, tid, NT);
+    __syncthreads();
+    if (tid == 0) {
+        // children's entries, staged in passes of at most kTreeStage
+        int acc = 0;
+        s_cut[0] = 0;
+        for (int c = 0; c < nk; ++c) {
+            acc += kids[c].mc;
+            s_cut[c + 1] = acc;
+        }
+    }
+    __syncthreads();
+    const bool one_pass = s_cut[nk] <= kTreeStage;
+    if (one_pass)                                                 // positions do not depend on the children
+        for (int c = 0; c < nk; ++c) {
+            const int* rl = s.rel + kids[c].rel_ptr;
+            for (int tt = tid; tt < kids[c].mc; tt += NT) spos[s_cut[c] + tt] = rl[tt];
+        }
+    if (tid < 32) {
+        const int ok = warp_wait_kids(done_b, kids, nk, true, abort_flag, limit, fused ? fac_done + q : nullptr,
+                                      d.units);
+        if (tid == 0) *s_ok = ok;
+    }
+    __syncthreads();
+    if (!*s_ok) return false;
+    if (fused) {
+        if (ts.fwd_stage) {
+            for (int c = tid >> 5; c < w; c += NW)
+                for (int a = lane; a < F; a += 32) P[a + c * F] = __ldcg(pan + a + (int64_t)c * F);
+        } else {
+            for (int c = tid >> 5; c < w; c += NW)
+                for (int a = lane; a < w; a += 32) P[a + c * w] = __ldcg(pan + a + (int64_t)c * F);
+        }
+    }
+    if (one_pass) {
+        for (int c = 0; c < nk; ++c) {
+            const T* cv = nm.cbv + kids[c].rel_ptr;
+            for (int tt = tid; tt < kids[c].mc; tt += NT) sval[s_cut[c] + tt] = __ldcg(cv + tt);
         }
         __syncthreads();
-        const bool one_pass = s_cut[nk] <= kTreeStage;
-        if (one_pass)                                             // positions do not depend on the children
-            for (int c = 0; c < nk; ++c) {
-                const int* rl = s.rel + kids[c].rel_ptr;
-                for (int tt = tid; tt < kids[c].mc; tt += 128) spos[s_cut[c] + tt] = rl[tt];
-            }
-        if (tid < 32) {
-            const int ok = warp_wait_kids(done + (int64_t)b * ts.nq, kids, nk, true, ctr + 1, limit);
-            if (tid == 0) s_ok = ok;
-        }
-        __syncthreads();
-        if (!s_ok) {
-            if (tid == 0) atomicExch(&nm.stat->timeout, 1);
-            break;
-        }
-        if (one_pass) {
-            for (int c = 0; c < nk; ++c) {
-                const T* cv = nm.cbv + kids[c].rel_ptr;
-                for (int tt = tid; tt < kids[c].mc; tt += 128) sval[s_cut[c] + tt] = __ldcg(cv + tt);
-            }
+        for (int c = 0; c < nk; ++c) {
+            for (int tt = tid; tt < kids[c].mc; tt += NT) v[spos[s_cut[c] + tt]] += sval[s_cut[c] + tt];
             __syncthreads();
-            for (int c = 0; c < nk; ++c) {
-                for (int tt = tid; tt < kids[c].mc; tt += 128) v[spos[s_cut[c] + tt]] += sval[s_cut[c] + tt];
-                __syncthreads();
-            }
-        } else
+        }
+    } else {
+        __syncthreads();
         for (int c0 = 0; c0 < nk;) {
             int c1 = c0 + 1;                                      // at least one child per pass
             while (c1 < nk && s_cut[c1 + 1] - s_cut[c0] <= kTreeStage) ++c1;
@@ -459,7 +482,7 @@ __global__ void __launch_bounds__(128) tree_fwd_kernel(DevSched s, TreeSched ts,
                 const T* cv = nm.cbv + kids[c].rel_ptr;
                 const int off = s_cut[c] - base;
                 if (off + mc <= kTreeStage) {
-                    for (int tt = tid; tt < mc; tt += 128) {
+                    for (int tt = tid; tt < mc; tt += NT) {
                         spos[off + tt] = rl[tt];
                         sval[off + tt] = __ldcg(cv + tt);
                     }
@@ -470,40 +493,70 @@ __global__ void __launch_bounds__(128) tree_fwd_kernel(DevSched s, TreeSched ts,
                 const int mc = kids[c].mc;
                 const int off = s_cut[c] - base;
                 if (off + mc <= kTreeStage) {
-                    for (int tt = tid; tt < mc; tt += 128) v[spos[off + tt]] += sval[off + tt];
+                    for (int tt = tid; tt < mc; tt += NT) v[spos[off + tt]] += sval[off + tt];
                 } else {                                          // a child larger than the stage
                     const int* rl = s.rel + kids[c].rel_ptr;
                     const T* cv = nm.cbv + kids[c].rel_ptr;
-                    for (int tt = tid; tt < mc; tt += 128) v[rl[tt]] += __ldcg(cv + tt);
+                    for (int tt = tid; tt < mc; tt += NT) v[rl[tt]] += __ldcg(cv + tt);
                 }
                 __syncthreads();
             }
             c0 = c1;
         }
-        if (tid < 32) {
-            if (w <= 32)
-                warp_lower_solve(v, P, ldp, w);
-            else
-                for (int p = 0; p < w; ++p) {
-                    const T xp = v[p];
-                    for (int i = p + 1 + lane; i < w; i += 32) v[i] -= P[i + p * ldp] * xp;
-                    __syncwarp();
-                }
-        }
+    }
+    if (tid < 32) {
+        if (w <= 32)
+            warp_lower_solve(v, P, ldp, w);
+        else
+            for (int p = 0; p < w; ++p) {
+                const T xp = v[p];
+                for (int i = p + 1 + lane; i < w; i += 32) v[i] -= P[i + p * ldp] * xp;
+                __syncwarp();
+            }
+    }
+    __syncthreads();
+    for (int i = w + tid; i < F; i += NT) {
+        T acc = v[i];
+        if (ts.fwd_stage)
+            for (int p = 0; p < w; ++p) acc -= P[i + p * F] * v[p];
+        else if (fused)
+            for (int p = 0; p < w; ++p) acc -= __ldcg(pan + i + (int64_t)p * F) * v[p];
+        else
+            for (int p = 0; p < w; ++p) acc -= pan[i + (int64_t)p * F] * v[p];
+        v[i] = acc;
+    }
+    __syncthreads();
+    for (int a = tid; a < w; a += NT) nm.vec[first + a] = v[a];
+    T* cvo = nm.cbv + d.rel_ptr;
+    for (int tt = tid; tt < F - w; tt += NT) cvo[tt] = v[w + tt];
+    signal_done(done_b + q);
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) tree_fwd_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
+                                                       long long limit)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ TreeFront d;
+    __shared__ TreeKid kids[kTreeMaxKids];
+    __shared__ int s_t, s_ok;
+    __shared__ int s_cut[kTreeMaxKids + 1];
+    const int tid = threadIdx.x;
+    const int total = ts.nq * B;
+    int* done = ctr + kCtrHead;
+    for (;;) {
+        const int t = next_ticket(ctr + 2, ctr + 1, total, &s_t);
+        if (t >= total) break;
+        const int q = t / B, b = t - q * B;
+        copy_words(&d, ts.fr + q, 1, tid, 128);
         __syncthreads();
-        for (int i = w + tid; i < F; i += 128) {
-            T acc = v[i];
-            if (ts.fwd_stage)
-                for (int p = 0; p < w; ++p) acc -= P[i + p * F] * v[p];
-            else
-                for (int p = 0; p < w; ++p) acc -= pan[i + (int64_t)p * F] * v[p];
-            v[i] = acc;
+        const DevNum<T> nm = nm0.at(b);
+        if (!fwd_unit<T, 128>(s, ts, nm, d, q, kids, s_cut, &s_ok, smraw, done + (int64_t)b * ts.nq, nullptr,
+                              ctr + 1, limit)) {
+            if (tid == 0) atomicExch(&nm.stat->timeout, 1);
+            break;
         }
-        __syncthreads();
-        for (int a = tid; a < w; a += 128) nm.vec[first + a] = v[a];
-        T* cvo = nm.cbv + d.rel_ptr;
-        for (int tt = tid; tt < F - w; tt += 128) cvo[tt] = v[w + tt];
-        signal_done(done + (int64_t)b * ts.nq + q);
         __syncthreads();
     }
 }
@@ -636,11 +689,13 @@ cudaError_t tree_grid(int kind, size_t smem, int* grid)
 
 template <typename T>
 cudaError_t launch_tree_factor(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
-                               int* stall, long long spin_limit, int grid, size_t smem, cudaStream_t st)
+                               int* stall, long long spin_limit, int grid, size_t smem, int fused, cudaStream_t st)
 {
-    const int g = std::min<long long>(grid, (long long)t.nunits * batch);
+    const int g = std::min<long long>(grid, (long long)(fused ? t.nunits_fused : t.nunits) * batch);
     if (g <= 0) return cudaSuccess;
-    tree_factor_kernel<T><<<g, 256, smem, st>>>(s, t, nm, batch, ctr, stall, spin_limit);
+    if ((fused ? t.unit_fused : t.unit) == nullptr || t.fr == nullptr || t.kid == nullptr)
+        return cudaErrorInvalidValue;                         // schedule not uploaded: never launch on it
+    tree_factor_kernel<T><<<g, 256, smem, st>>>(s, t, nm, batch, ctr, stall, spin_limit, fused);
     return cudaGetLastError();
 }
 
@@ -650,6 +705,7 @@ cudaError_t launch_tree_fwd(const DevSched& s, const TreeSched& t, const DevNum<
 {
     const int g = std::min<long long>(grid, (long long)t.nq * batch);
     if (g <= 0) return cudaSuccess;
+    if (t.fr == nullptr || t.kid == nullptr) return cudaErrorInvalidValue;
     tree_fwd_kernel<T><<<g, 128, smem, st>>>(s, t, nm, batch, ctr, spin_limit);
     return cudaGetLastError();
 }
@@ -660,6 +716,7 @@ cudaError_t launch_tree_bwd(const DevSched& s, const TreeSched& t, const DevNum<
 {
     const int g = std::min<long long>(grid, (long long)t.nq * batch);
     if (g <= 0) return cudaSuccess;
+    if (t.fr == nullptr) return cudaErrorInvalidValue;
     tree_bwd_kernel<T><<<g, 128, smem, st>>>(s, t, nm, batch, ctr, spin_limit);
     return cudaGetLastError();
 }
@@ -667,7 +724,7 @@ cudaError_t launch_tree_bwd(const DevSched& s, const TreeSched& t, const DevNum<
 #define KKT_TREE_INST(T)                                                                                          \
     template cudaError_t tree_grid<T>(int, size_t, int*);                                                          \
     template cudaError_t launch_tree_factor<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,     \
-                                               int*, long long, int, size_t, cudaStream_t);                        \
+                                               int*, long long, int, size_t, int, cudaStream_t);                   \
     template cudaError_t launch_tree_fwd<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,        \
                                             long long, int, size_t, cudaStream_t);                                 \
     template cudaError_t launch_tree_bwd<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,        \

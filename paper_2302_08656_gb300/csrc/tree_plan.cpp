@@ -86,9 +86,18 @@ void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp)
             ts.max_wm = std::max(ts.max_wm, w * m);
         }
     ts.nunits = (int)tp.unit.size();
+    // fused order: level by level, the factorization units of the level, then its forward units
+    for (int l = split, u = 0; l < an.n_levels; ++l) {
+        const int q0 = tq[an.level_fronts[an.level_ptr[l]]];
+        const int q1 = q0 + (an.level_ptr[l + 1] - an.level_ptr[l]);
+        while (u < (int)tp.unit.size() && tp.unit[u].front < q1) tp.unit_fused.push_back(tp.unit[u++]);
+        for (int q = q0; q < q1; ++q) tp.unit_fused.push_back(FrontTile{q, -1, 0});
+    }
+    ts.nunits_fused = (int)tp.unit_fused.size();
     ts.max_kids = std::max(ts.max_kids, 1);
     ts.fwd_stage = (size_t)ts.max_fw * es <= kStageLimit ? 1 : 0;
     ts.bwd_stage = (size_t)ts.max_wm * es <= kStageLimit ? 1 : 0;
+    ts.kid_off = tree_kid_offset(ts, es);
     tp.fac_smem = tree_factor_smem(ts, es);
     tp.fwd_smem = tree_fwd_smem(ts, es);
     tp.bwd_smem = tree_bwd_smem(ts, es);
@@ -100,16 +109,28 @@ void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp)
 }
 
 
+// factor kernel: mini front and gather maps, or (forward units of the fused
+// mode) the forward unit's arrays; the children's descriptors after both
+static size_t fwd_arrays(const TreeSched& t, size_t es)
+{
+    return es * ((size_t)t.max_F + (t.fwd_stage ? (size_t)t.max_fw : (size_t)t.max_w * t.max_w) + kTreeStage) +
+           4 * (size_t)kTreeStage;
+}
+
+size_t tree_kid_offset(const TreeSched& t, size_t es)
+{
+    const size_t fac = align16(es * (size_t)t.m_elems) + align16(sizeof(int) * 2 * (size_t)t.max_kids * t.map_w);
+    return align16(std::max(fac, fwd_arrays(t, es)));
+}
+
 size_t tree_factor_smem(const TreeSched& t, size_t es)
 {
-    return align16(es * (size_t)t.m_elems) + align16(sizeof(int) * 2 * (size_t)t.max_kids * t.map_w) +
-           sizeof(TreeKid) * (size_t)t.max_kids;
+    return tree_kid_offset(t, es) + sizeof(TreeKid) * (size_t)t.max_kids;
 }
 
 size_t tree_fwd_smem(const TreeSched& t, size_t es)
 {
-    size_t b = es * ((size_t)t.max_F + (t.fwd_stage ? (size_t)t.max_fw : (size_t)t.max_w * t.max_w) + kTreeStage);
-    return b + 4 * (size_t)kTreeStage;
+    return fwd_arrays(t, es);
 }
 
 size_t tree_bwd_smem(const TreeSched& t, size_t es)

@@ -20,6 +20,7 @@ struct TreePlan {
     std::vector<TreeFront> fr;
     std::vector<TreeKid> kid;
     std::vector<FrontTile> unit;
+    std::vector<FrontTile> unit_fused;  // factor units and, after each level, its forward-solve units (ti = -1)
     std::vector<int> inv;
     TreeSched ts;
     size_t fac_smem = 0, fwd_smem = 0, bwd_smem = 0;
@@ -30,6 +31,7 @@ struct TreePlan {
 // (0: none); es: bytes per factor value.
 void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp);
 
+size_t tree_kid_offset(const TreeSched& t, size_t es);
 size_t tree_factor_smem(const TreeSched& t, size_t es);
 size_t tree_fwd_smem(const TreeSched& t, size_t es);
 size_t tree_bwd_smem(const TreeSched& t, size_t es);

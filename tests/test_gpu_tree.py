@@ -103,3 +103,29 @@ def test_no_tree_part_rejects_the_stall_hook():
         s.debug_stall()
     assert e.value.status == 4
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("count,tmf", [(1, 2432), (1, 10 ** 9), (3, 10 ** 9), (1, 0)])
+def test_fused_refactor_refine_equals_separate_calls(precision, count, tmf):
+    """kkt_refactor_refine (the forward substitution of the first solve inside
+    the refactorization) gives the same bits as kkt_refactor + kkt_refine."""
+    dev = _dev()
+    pat = KKTPattern(make_grid(4, 2000, 2560, 400))
+    vals = np.concatenate([pat.values(pat.point(40 + i, 3, 1e-5)) for i in range(count)])
+    rhs = np.concatenate([pat.rhs(40 + i, 3) for i in range(count)])
+    v = torch.from_numpy(vals).to(dev)
+    b = torch.from_numpy(rhs).to(dev)
+    a = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, count=count, precision=precision, tree_min_fronts=tmf)
+    f = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, count=count, precision=precision, tree_min_fronts=tmf)
+    for _ in range(2):                                 # second call replays the captured graphs
+        a.refactor(v)
+        xa, ia = a.refine(b, tol=1e-10)
+        xf, if_ = f.refactor_refine(v, b, tol=1e-10)
+        assert torch.equal(xa, xf)
+        ia = ia if count > 1 else [ia]
+        if_ = if_ if count > 1 else [if_]
+        for p, q in zip(ia, if_):
+            assert p.backward_err == q.backward_err and p.iters == q.iters and p.status == q.status == 0
+    a.close()
+    f.close()
