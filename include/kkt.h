@@ -86,7 +86,8 @@ typedef struct {
     int no_graphs;              /* 1: launch every kernel from the host instead of replaying
                                    the captured CUDA graphs of the level loops (default 0) */
     int tree_min_fronts;        /* the top levels of the assembly tree that hold fewer fronts
-                                   than this (and every level above them) are refactored and
+                                   than this (fronts x instances for a batched context; every
+                                   level above them included) are refactored and
                                    solved by persistent, dependency-driven kernels instead of
                                    one launch per level (default 2432; 0 = one launch per level
                                    everywhere). Both schedules give bitwise identical results */

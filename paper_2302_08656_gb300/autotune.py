@@ -1,12 +1,13 @@
 """Per-pattern schedule autotuner.
 
-The level schedule depends on how many pivots a supernode may hold: few
-pivots make short sequential panels but a taller assembly tree (more levels,
-more launches); many pivots do the opposite. Which wins depends on the size
-of the system, the precision (FP64 panels run on the slow FP64 pipe) and the
-batch size. The tuner times a short refactor + solve sequence for each
-candidate on the device and keeps the fastest, cached per (pattern hash,
-precision, instance count).
+The schedule depends on how many pivots a supernode may hold (few pivots:
+short sequential pivot blocks but a taller assembly tree; many: the
+opposite) and on how much of the narrow top of the tree the persistent tree
+kernels take (tree_min_fronts). Which wins depends on the size of the
+system, the precision (FP64 runs on the slow FP64 pipe) and the batch size.
+The tuner times a short refactor + refine sequence (the fused call of an
+interior-point iteration) for each candidate on the device and keeps the
+fastest, cached per (pattern hash, precision, instance count).
 """
 from __future__ import annotations
 
@@ -17,6 +18,7 @@ import os
 import numpy as np
 
 CANDIDATES = (8, 16, 24, 32)
+TREE_CANDIDATES = (0, 2432, 9728)
 _CACHE_FILE = os.environ.get("KKT_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache",
                                                                 "kkt_gb300_autotune.json"))
 
@@ -47,9 +49,9 @@ def _store_cache(cache):
         pass
 
 
-def tune(rowptr, colidx, n_primal, vals, rhs, precision="fp64", count=1, candidates=CANDIDATES, reps=3,
-         use_cache=True):
-    """Return (best options dict, {max_pivots: ms per refactor+solve}).
+def tune(rowptr, colidx, n_primal, vals, rhs, precision="fp64", count=1, candidates=CANDIDATES,
+         tree_candidates=TREE_CANDIDATES, reps=3, use_cache=True):
+    """Return (best options dict, {"max_pivots/tree_min_fronts": ms per refactor+refine}).
 
     vals / rhs: device tensors for `count` instances (instance-major)."""
     import torch
@@ -58,26 +60,28 @@ def tune(rowptr, colidx, n_primal, vals, rhs, precision="fp64", count=1, candida
 
     key = pattern_key(rowptr, colidx, precision, count)
     cache = _load_cache() if use_cache else {}
-    if key in cache:
-        return {"max_pivots": cache[key]["max_pivots"]}, cache[key]["times"]
+    if key in cache and "tree_min_fronts" in cache[key]:
+        return {"max_pivots": cache[key]["max_pivots"], "tree_min_fronts": cache[key]["tree_min_fronts"]}, \
+            cache[key]["times"]
     times = {}
     out = torch.empty_like(rhs)
     for mp in candidates:
-        s = KKTSolver(rowptr, colidx, n_primal, count=count, precision=precision, max_pivots=mp)
-        s.refactor(vals)
-        s.solve(rhs, out=out)                        # captures the graphs
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record()
-        for _ in range(reps):
-            s.refactor(vals)
-            s.solve(rhs, out=out)
-        ev1.record()
-        torch.cuda.synchronize()
-        times[str(mp)] = ev0.elapsed_time(ev1) / reps
-        s.close()
-    best = int(min(times, key=times.get))
+        for tmf in tree_candidates:
+            s = KKTSolver(rowptr, colidx, n_primal, count=count, precision=precision, max_pivots=mp,
+                          tree_min_fronts=tmf)
+            s.refactor_refine(vals, rhs, out=out, raise_on_noconv=False)     # captures the graphs
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            for _ in range(reps):
+                s.refactor_refine(vals, rhs, out=out, raise_on_noconv=False)
+            ev1.record()
+            torch.cuda.synchronize()
+            times["%d/%d" % (mp, tmf)] = ev0.elapsed_time(ev1) / reps
+            s.close()
+    best = min(times, key=times.get)
+    mp, tmf = (int(x) for x in best.split("/"))
     if use_cache:
-        cache[key] = {"max_pivots": best, "times": times}
+        cache[key] = {"max_pivots": mp, "tree_min_fronts": tmf, "times": times}
         _store_cache(cache)
-    return {"max_pivots": best}, times
+    return {"max_pivots": mp, "tree_min_fronts": tmf}, times

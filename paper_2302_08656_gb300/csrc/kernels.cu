@@ -247,12 +247,13 @@ __device__ __forceinline__ void assemble_original(const DevSched& s, const DevNu
 // Fronts with F <= 32: one warp per front, the whole front in shared memory.
 // Lanes form an 8 x 4 grid over (row, column) of every block loop.
 template <typename T>
-__global__ void __launch_bounds__(128) front_warp_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
-                                                         int count)
+__global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
+                                                            int count, int maxF)
 {
+    // shared memory sized by the launch's largest front (maxF <= 32): the
+    // small leaf fronts of the widest levels keep many more warps resident
+    extern __shared__ __align__(16) unsigned char smraw[];
     const DevNum<T> nm = nm0.at(blockIdx.y);
-    __shared__ T sm[4][kWarpFrontMax * kWarpFrontMax];
-    __shared__ int srl[4][kWarpFrontMax];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int fi = blockIdx.x * 4 + wid;
     if (fi >= count) return;
@@ -261,8 +262,8 @@ __global__ void __launch_bounds__(128) front_warp_kernel(DevSched s, DevNum<T> n
     const int first = s.sn_first[f];
     const int w = s.sn_first[f + 1] - first;
     const int F = s.sn_front[f];
-    T* Fm = sm[wid];
-    int* rls = srl[wid];
+    T* Fm = reinterpret_cast<T*>(smraw) + (int64_t)wid * maxF * maxF;
+    int* rls = reinterpret_cast<int*>(reinterpret_cast<T*>(smraw) + (int64_t)4 * maxF * maxF) + wid * maxF;
     for (int t = lane; t < F * F; t += 32) Fm[t] = T(0);
     __syncwarp();
     assemble_original<T, 32>(s, nm, f, lane, Fm);
@@ -914,11 +915,13 @@ cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d
 }
 
 template <typename T>
-cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int batch,
-                               cudaStream_t st)
+cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
+                               int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    front_warp_kernel<T><<<dim3(cdiv(count, 4), batch), 128, 0, st>>>(s, nm, fronts, count);
+    if (max_front < 1 || max_front > kWarpFrontMax) return cudaErrorInvalidValue;
+    const size_t smem = 4 * ((size_t)max_front * max_front * sizeof(T) + (size_t)max_front * sizeof(int));
+    front_warp_kernel<T><<<dim3(cdiv(count, 4), batch), 128, smem, st>>>(s, nm, fronts, count, max_front);
     return cudaGetLastError();
 }
 
@@ -1162,7 +1165,7 @@ cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci,
 // explicit instantiations
 #define KKT_INST(T)                                                                                              \
     template cudaError_t launch_scale<T>(const DevSched&, const DevNum<T>&, const double*, int, cudaStream_t);   \
-    template cudaError_t launch_fronts_warp<T>(const DevSched&, const DevNum<T>&, const int*, int, int,          \
+    template cudaError_t launch_fronts_warp<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,     \
                                                cudaStream_t);                                                    \
     template cudaError_t launch_fronts_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,      \
                                               cudaStream_t);                                                     \

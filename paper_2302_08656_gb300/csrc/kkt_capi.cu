@@ -385,7 +385,7 @@ kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused 
     for (const LevelGroup& g : c->levels) {
         if (g.warp_cnt) {
             Launch L(c, st, KK_FRONT_WARP, 1);
-            KKT_CUDA(launch_fronts_warp<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, B, st));
+            KKT_CUDA(launch_fronts_warp<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, B, st));
         }
         if (g.cta_cnt) {
             Launch L(c, st, KK_FRONT_CTA, 1);
@@ -1033,7 +1033,10 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
             delete c;
             return s;
         }
-        build_tree(c->an, c->opt.tree_min_fronts, elem_size(c->opt.precision), tp);
+        // a level of a batched context carries `batch` times the fronts of one
+        // instance: it stays level-launched once fronts x batch reach the threshold
+        const int per_instance = (c->opt.tree_min_fronts + batch - 1) / batch;
+        build_tree(c->an, per_instance, elem_size(c->opt.precision), tp);
         build_levels(c->an, elem_size(c->opt.precision), tp.split, c->levels, fids, tiles, c->scratch_stride,
                      c->max_panel_global, inv_off, inv, f12_off, f12_total);
     } catch (...) {
