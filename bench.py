@@ -173,6 +173,7 @@ def algorithmic_bytes(plan, n, nnz, wbytes):
 # capture of the same command (profiles/), keyed by (kernel, workload,
 # precision, tree levels); an entry is removed whenever the kernel changes.
 MEASURED_TRAFFIC = {
+    ("tree_factor_kernel", "northeast25k", "fp64", 58): 23317248 + 163584,
 }
 
 PHASE_OF = {
