@@ -264,20 +264,26 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
         }
         __syncthreads();
         if (Fr <= 32 && Fc <= 32) {
-            // mini fronts of at most 32 x 32 (always when w <= 16): one row and
-            // four columns per thread, all loads issued before the updates; the
-            // owner of entry (p+1, p+1) (thread 0) finishes it first
+            // mini fronts of at most 32 x 32 (always when w <= 16): lane -> row,
+            // warp -> four adjacent trailing columns, so a warp whose columns
+            // are all eliminated issues nothing (GB300 runs one FP64 warp
+            // instruction per ~64 cycles per sub-partition: the elimination
+            // is bound by FP64 instructions issued, masked lanes included).
+            // Warps 0-3 take groups 0-3, warps 5-7 groups 4-6 and warp 4, which
+            // shares a sub-partition with the pivot warp 0, the last group.
+            // The owner of entry (p+1, p+1) (thread 0) finishes it first.
+            const int g = ty == 0 ? 0 : (ty < 4 ? ty : (ty == 4 ? 7 : ty - 1));
             for (int p = 0; p < w; ++p) {
                 const T rinv = s_rinv[p];
-                if (p > 0 && ty == (p - 1) % 8)                    // deferred scaling of column p-1
+                if (p > 0 && ty == 7)                              // deferred scaling of column p-1
                     for (int i = p + tx; i < Fr; i += 32) M[i + (p - 1) * Fr] *= s_rinv[p - 1];
-                const int i = p + 1 + tx;
-                if (i < Fr) {
+                const int i = p + 1 + tx, jg = p + 1 + 4 * g;
+                if (jg < Fc && i < Fr) {
                     const T l = M[i + p * Fr] * rinv;
                     T mv[4], uv[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const int j = p + 1 + ty + 8 * k;
+                        const int j = jg + k;
                         mv[k] = j < Fc ? M[i + j * Fr] : T(0);
                         uv[k] = j < Fc ? M[p + j * Fr] : T(0);
                     }
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
                     }
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const int j = p + 1 + ty + 8 * k;
+                        const int j = jg + k;
                         if (j < Fc) M[i + j * Fr] = mv[k];
                     }
                 }
