@@ -253,56 +253,80 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
             }
         __syncthreads();
         // ---- w pivot steps of right-looking elimination without pivoting, one
-        // barrier per pivot: step p forms l_ip = m_ip / u_pp on the fly (the
-        // value stored when column p is scaled one step later), updates the
-        // trailing entries, and the thread owning entry (p+1, p+1) finalizes
-        // the next pivot and its reciprocal (one reciprocal per pivot)
-        if (tid == 0 && w > 0) {
-            const T pv = static_pivot(M[0], floorT, nm.stat, lead);
-            M[0] = pv;
-            s_rinv[0] = T(1) / pv;
-        }
-        __syncthreads();
+        // barrier per pivot, one reciprocal per pivot (l_ip = m_ip * (1 / u_pp))
         if (Fr <= 32 && Fc <= 32) {
-            // mini fronts of at most 32 x 32 (always when w <= 16): lane -> row,
-            // warp -> four adjacent trailing columns, so a warp whose columns
-            // are all eliminated issues nothing (GB300 runs one FP64 warp
-            // instruction per ~64 cycles per sub-partition: the elimination
-            // is bound by FP64 instructions issued, masked lanes included).
-            // Warps 0-3 take groups 0-3, warps 5-7 groups 4-6 and warp 4, which
-            // shares a sub-partition with the pivot warp 0, the last group.
-            // The owner of entry (p+1, p+1) (thread 0) finishes it first.
-            const int g = ty == 0 ? 0 : (ty < 4 ? ty : (ty == 4 ? 7 : ty - 1));
+            // mini fronts of at most 32 x 32 (always when w <= 16). GB300 runs
+            // one FP64 warp instruction per ~64 cycles per sub-partition, masked
+            // lanes included, so the elimination is bound by the FP64
+            // instructions issued. Warp 0 owns column p+1 only: at step p it
+            // finishes the next pivot (lane 0), broadcasts its reciprocal and
+            // stores column p+1 already scaled, so at step p+1 every other warp
+            // reads l_i,p+1 and issues FMAs alone. Warps 1-7 own five adjacent
+            // columns each from p+2 (lane -> row), a warp whose columns are all
+            // eliminated issues nothing, and warp 4, which shares a
+            // sub-partition with warp 0, takes the last group.
+            if (ty == 0 && w > 0) {
+                T r = T(0);
+                if (tx == 0) {
+                    const T pv = static_pivot(M[0], floorT, nm.stat, lead);
+                    M[0] = pv;
+                    r = T(1) / pv;
+                }
+                r = __shfl_sync(0xffffffffu, r, 0);
+                if (1 + tx < Fr) M[1 + tx] *= r;
+            }
+            __syncthreads();
+            const int g = ty < 4 ? ty - 1 : (ty == 4 ? 6 : ty - 2);
             for (int p = 0; p < w; ++p) {
-                const T rinv = s_rinv[p];
-                if (p > 0 && ty == 7)                              // deferred scaling of column p-1
-                    for (int i = p + tx; i < Fr; i += 32) M[i + (p - 1) * Fr] *= s_rinv[p - 1];
-                const int i = p + 1 + tx, jg = p + 1 + 4 * g;
-                if (jg < Fc && i < Fr) {
-                    const T l = M[i + p * Fr] * rinv;
-                    T mv[4], uv[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int j = jg + k;
-                        mv[k] = j < Fc ? M[i + j * Fr] : T(0);
-                        uv[k] = j < Fc ? M[p + j * Fr] : T(0);
+                const int i = p + 1 + tx;
+                if (ty == 0) {
+                    const int j = p + 1;
+                    const bool act = i < Fr && j < Fc;
+                    T mv = T(0);
+                    if (act) {
+                        const T l = M[i + p * Fr];
+                        mv = M[i + j * Fr];
+                        mv -= l * M[p + j * Fr];
                     }
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) mv[k] -= l * uv[k];
-                    if (tid == 0 && p + 1 < w) {
-                        const T pv = static_pivot(mv[0], floorT, nm.stat, lead);
-                        mv[0] = pv;
-                        s_rinv[p + 1] = T(1) / pv;
+                    if (p + 1 < w) {                               // warp-uniform
+                        T r = T(0);
+                        if (tx == 0) {
+                            mv = static_pivot(mv, floorT, nm.stat, lead);
+                            r = T(1) / mv;
+                        }
+                        r = __shfl_sync(0xffffffffu, r, 0);
+                        if (tx > 0) mv *= r;
                     }
+                    if (act) M[i + j * Fr] = mv;
+                } else {
+                    const int jg = p + 2 + 5 * g;
+                    if (jg < Fc && i < Fr) {
+                        const T l = M[i + p * Fr];
+                        T mv[5], uv[5];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int j = jg + k;
-                        if (j < Fc) M[i + j * Fr] = mv[k];
+                        for (int k = 0; k < 5; ++k) {
+                            const int j = jg + k;
+                            mv[k] = j < Fc ? M[i + j * Fr] : T(0);
+                            uv[k] = j < Fc ? M[p + j * Fr] : T(0);
+                        }
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) mv[k] -= l * uv[k];
+#pragma unroll
+                        for (int k = 0; k < 5; ++k) {
+                            const int j = jg + k;
+                            if (j < Fc) M[i + j * Fr] = mv[k];
+                        }
                     }
                 }
                 __syncthreads();
             }
         } else {
+            if (tid == 0 && w > 0) {
+                const T pv = static_pivot(M[0], floorT, nm.stat, lead);
+                M[0] = pv;
+                s_rinv[0] = T(1) / pv;
+            }
+            __syncthreads();
             for (int p = 0; p < w; ++p) {
                 const T rinv = s_rinv[p];
                 if (p > 0 && ty == (p - 1) % 8)                    // deferred scaling of column p-1
@@ -322,10 +346,10 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
                 }
                 __syncthreads();
             }
+            if (w > 0)
+                for (int i = w + tid; i < Fr; i += 256) M[i + (w - 1) * Fr] *= s_rinv[w - 1];
+            __syncthreads();
         }
-        if (w > 0)
-            for (int i = w + tid; i < Fr; i += 256) M[i + (w - 1) * Fr] *= s_rinv[w - 1];
-        __syncthreads();
         // ---- results: pivot block (lead unit), L21 rows (tj == 0), U12 columns (ti == 0), CB tile
         T* pan = nm.panel + d.panel_off;
         if (lead)
