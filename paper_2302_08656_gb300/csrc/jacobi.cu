@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(128) jacobi_u_kernel(DevSched s, DevNum<T> nm,
         T acc = y[first + a];
         for (int cc = a + 1; cc < w; ++cc) acc -= pan[a + (int64_t)cc * F] * x[first + cc];
         for (int tt = 0; tt < m; ++tt) acc -= U12[a + (int64_t)tt * w] * x[R[w + tt]];
-        xnew[first + a] = acc * (T(1) / pan[a + (int64_t)a * F]);
+        xnew[first + a] = acc * pivot_rcp(pan[a + (int64_t)a * F]);
     }
 }
 

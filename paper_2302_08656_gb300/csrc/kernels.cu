@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T
         if (lane == 0) {                                          // one reciprocal per pivot
             const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
             Fm[p + p * F] = pv;
-            srinv[wid] = T(1) / pv;
+            srinv[wid] = pivot_rcp(pv);
         }
         __syncwarp();
         if (lane > p && lane < F) Fm[lane + p * F] *= srinv[wid];
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(256) front_cta_kernel(DevSched s, DevNum<T> nm
         if (tid == 0) {                                           // one reciprocal per pivot
             const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
             Fm[p + p * F] = pv;
-            srinv = T(1) / pv;
+            srinv = pivot_rcp(pv);
         }
         __syncthreads();
         const T rinv = srinv;
@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> 
         if (tid == 0) {                                           // one reciprocal per pivot
             const T pv = static_pivot(col[p + (int64_t)p * F], floorT, nm.stat, true);
             col[p + (int64_t)p * F] = pv;
-            srinv = T(1) / pv;
+            srinv = pivot_rcp(pv);
         }
         __syncthreads();
         const T rinv = srinv;
@@ -657,7 +657,7 @@ __global__ void __launch_bounds__(128) solve_bwd_kernel(DevSched s, DevNum<T> nm
     }
     __syncwarp();
     for (int p = w - 1; p >= 0; --p) {
-        const T xp = v[p] * (T(1) / Us[p + p * w]);        // x_p = v_p * (1 / u_pp), as every backward kernel
+        const T xp = v[p] * pivot_rcp(Us[p + p * w]);        // x_p = v_p * (1 / u_pp), as every backward kernel
         __syncwarp();
         if (lane == 0) v[p] = xp;
         for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(128) solve_bwd_cta_kernel(DevSched s, DevNum<T
     __syncthreads();
     if (tid < 32) {
         for (int p = w - 1; p >= 0; --p) {
-            const T xp = v[p] * (T(1) / Us[p + p * w]);    // x_p = v_p * (1 / u_pp), as every backward kernel
+            const T xp = v[p] * pivot_rcp(Us[p + p * w]);    // x_p = v_p * (1 / u_pp), as every backward kernel
             __syncwarp();
             if (lane == 0) v[p] = xp;
             for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;

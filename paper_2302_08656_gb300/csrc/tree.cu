@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
                 if (tx == 0) {
                     const T pv = static_pivot(M[0], floorT, nm.stat, lead);
                     M[0] = pv;
-                    r = T(1) / pv;
+                    r = pivot_rcp(pv);
                 }
                 r = __shfl_sync(0xffffffffu, r, 0);
                 if (1 + tx < Fr) M[1 + tx] *= r;
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
                         T r = T(0);
                         if (tx == 0) {
                             mv = static_pivot(mv, floorT, nm.stat, lead);
-                            r = T(1) / mv;
+                            r = pivot_rcp(mv);
                         }
                         r = __shfl_sync(0xffffffffu, r, 0);
                         if (tx > 0) mv *= r;
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
             if (tid == 0 && w > 0) {
                 const T pv = static_pivot(M[0], floorT, nm.stat, lead);
                 M[0] = pv;
-                s_rinv[0] = T(1) / pv;
+                s_rinv[0] = pivot_rcp(pv);
             }
             __syncthreads();
             for (int p = 0; p < w; ++p) {
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
                         if (i == p + 1 && j == p + 1 && p + 1 < w) {
                             const T pv = static_pivot(a, floorT, nm.stat, lead);
                             M[i + j * Fr] = pv;
-                            s_rinv[p + 1] = T(1) / pv;
+                            s_rinv[p + 1] = pivot_rcp(pv);
                         } else {
                             M[i + j * Fr] = a;
                         }
@@ -629,7 +629,7 @@ __global__ void __launch_bounds__(128) tree_bwd_kernel(DevSched s, TreeSched ts,
         for (int a = tid; a < w; a += 128) y[a] = nm.vec[first + a];
         for (int c = tid >> 5; c < w; c += 4)
             for (int a = lane; a < w; a += 32) Us[a + c * w] = pan[a + (int64_t)c * F];
-        for (int a = tid; a < w; a += 128) rcp[a] = T(1) / pan[a + (int64_t)a * F];
+        for (int a = tid; a < w; a += 128) rcp[a] = pivot_rcp(pan[a + (int64_t)a * F]);
         if (ts.bwd_stage)
             for (int e = tid; e < w * m; e += 128) U12s[e] = U12[e];
         if (tid < 32) {
