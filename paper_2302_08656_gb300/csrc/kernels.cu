@@ -28,19 +28,22 @@ __device__ __forceinline__ double warp_sum(double v)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
-__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* a, double v)
-{
-    atomicMax(a, (unsigned long long)__double_as_longlong(v));
-}
 
 // Exact power-of-two arithmetic on IEEE bit patterns (integer pipes only; the
-// FP64 pipe of this GPU issues one warp instruction per 16 cycles).
+// FP64 pipe of this GPU issues one warp instruction per ~64 cycles in each
+// sub-partition).
 // scale2(x, e) = x * 2^e for a non-negative finite x; exact. Zero stays zero;
 // results that would leave the normal range, and subnormal inputs, take the
 // multiply.
 __device__ __forceinline__ unsigned long long abs_bits(double x)
 {
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
+__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(kFull, v, o));
+    return v;
 }
 __device__ __forceinline__ int exp_of_pow2(double d)               // d = 2^k exactly
 {
@@ -99,15 +102,14 @@ __global__ void fill_kernel(int n, double* a, double v)
 }
 
 // One Ruiz iteration, eight lanes per row (rows average ~10 entries):
-// r_i = max_j |d_i k_ij d_j|, d_i <- d_i 2^round(-log2(r_i)/2). An iteration
-// after one that changed nothing only copies d (the fixed point is reached).
+// r_i = max_j |d_i k_ij d_j|, d_i <- d_i 2^round(-log2(r_i)/2).
 constexpr int kRowLanes = 8;
+// Rows per thread group: a block covers 32 x kRuizRows rows and every thread
+// keeps the loads of its kRuizRows rows in flight together (the pass is bound
+// by the latency of rp -> (k, j) -> d_j, not by bandwidth), so northeast25k
+// runs in about one wave of blocks.
+constexpr int kRuizRows = 5;
 
-__device__ __forceinline__ double group_max(double v)
-{
-    for (int o = kRowLanes / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
 __device__ __forceinline__ double group_sum(double v)
 {
     for (int o = kRowLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
@@ -126,44 +128,67 @@ __device__ __forceinline__ unsigned long long group_max_u64(unsigned long long v
 // Integer-only iteration: every d is a power of two, so |d_i k_ij d_j| is
 // |k_ij| with its exponent raised by e_i + e_j, and the row maximum of
 // non-negative doubles is the maximum of their bit patterns.
+// Iteration 0 starts from d = 1 without reading din and writes 1 to din as
+// well as the new d to dout. An iteration that changes no d_i leaves dout
+// equal to din, bit for bit, so both buffers already hold the fixed point and
+// every later iteration returns at once.
 __global__ void __launch_bounds__(256) ruiz_kernel(int n, int64_t nnz, const int* __restrict__ rp,
                                                    const int* __restrict__ ci, const double* __restrict__ v,
-                                                   const double* __restrict__ din, double* __restrict__ dout,
-                                                   DevStat* stat, int it)
+                                                   double* din, double* __restrict__ dout, DevStat* stat, int it)
 {
     // instance blockIdx.y of a batch
     v += (int64_t)blockIdx.y * nnz;
     din += (int64_t)blockIdx.y * n;
     dout += (int64_t)blockIdx.y * n;
-    const int* changed_prev = it > 0 ? &stat[blockIdx.y].ruiz_changed[it - 1] : nullptr;
+    if (it > 0 && stat[blockIdx.y].ruiz_changed[it - 1] == 0) return;   // uniform over the grid
     int* changed_cur = &stat[blockIdx.y].ruiz_changed[it];
-    __shared__ int s_skip;
-    if (threadIdx.x == 0) s_skip = changed_prev ? (*changed_prev == 0) : 0;   // one read per block
-    __syncthreads();
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
     const int sub = threadIdx.x % kRowLanes;
-    const bool skip = s_skip != 0;                 // uniform over the block
-    int changed = 0;
-    double di = 0.0;
-    unsigned long long m = 0ull;
-    if (row < n) {
-        di = din[row];
-        if (!skip) {
-            const int ei = exp_of_pow2(di);
-            for (int p = rp[row] + sub; p < rp[row + 1]; p += kRowLanes) {
-                const unsigned long long a = scale2_bits(abs_bits(v[p]), ei + exp_of_pow2(din[ci[p]]));
-                m = a > m ? a : m;
-            }
-        }
+    const int base = blockIdx.x * (32 * kRuizRows) + threadIdx.x / kRowLanes;
+    int p[kRuizRows], pe[kRuizRows], ei[kRuizRows];
+    unsigned long long m[kRuizRows];
+#pragma unroll
+    for (int k = 0; k < kRuizRows; ++k) {
+        const int row = base + 32 * k;
+        p[k] = row < n ? rp[row] + sub : 0;
+        pe[k] = row < n ? rp[row + 1] : 0;
+        ei[k] = (row < n && it > 0) ? exp_of_pow2(din[row]) : 0;
+        m[k] = 0ull;
     }
-    if (!skip) m = group_max_u64(m);               // every lane of the warp takes part
-    if (row < n) {
-        if (skip) {
-            if (sub == 0) dout[row] = di;
-        } else {
-            const int k = m ? pow2_inv_sqrt_exp(m) : 0;
-            if (sub == 0) dout[row] = __longlong_as_double((long long)scale2_bits(abs_bits(di), k));
-            changed = k != 0;
+    // rounds of one entry per row and lane, the loads of all rows together
+    for (;;) {
+        bool any = false;
+        unsigned long long kb[kRuizRows];
+        int cj[kRuizRows];
+#pragma unroll
+        for (int k = 0; k < kRuizRows; ++k) {
+            const bool ok = p[k] < pe[k];
+            any |= ok;
+            kb[k] = ok ? abs_bits(v[p[k]]) : 0ull;
+            cj[k] = ok ? ci[p[k]] : -1;
+        }
+        if (!any) break;
+        int ej[kRuizRows];
+#pragma unroll
+        for (int k = 0; k < kRuizRows; ++k) ej[k] = (cj[k] >= 0 && it > 0) ? exp_of_pow2(din[cj[k]]) : 0;
+#pragma unroll
+        for (int k = 0; k < kRuizRows; ++k)
+            if (cj[k] >= 0) {
+                const unsigned long long a = scale2_bits(kb[k], ei[k] + ej[k]);
+                m[k] = a > m[k] ? a : m[k];
+                p[k] += kRowLanes;
+            }
+    }
+    int changed = 0;
+#pragma unroll
+    for (int k = 0; k < kRuizRows; ++k) {
+        const unsigned long long mk = group_max_u64(m[k]);   // every lane of the warp takes part
+        const int row = base + 32 * k;
+        if (row < n && sub == 0) {
+            const int e = mk ? pow2_inv_sqrt_exp(mk) : 0;
+            const unsigned long long dib = (unsigned long long)(ei[k] + 1023) << 52;   // d_i (1 in iteration 0)
+            dout[row] = __longlong_as_double((long long)scale2_bits(dib, e));
+            if (it == 0) din[row] = 1.0;
+            changed |= e != 0;
         }
     }
     // one flag write per block (a write per row would serialise on one address)
@@ -185,7 +210,7 @@ __global__ void __launch_bounds__(256) scale_kernel(int n, const int* __restrict
     const int row = (blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
     const int sub = threadIdx.x % kRowLanes;
     const int lane = threadIdx.x & 31;
-    double amax = 0.0, rsum = 0.0;
+    double rsum = 0.0;
     unsigned long long amb = 0ull;
     if (row < n) {
         const int ei = exp_of_pow2(d[row]);
@@ -199,20 +224,21 @@ __global__ void __launch_bounds__(256) scale_kernel(int n, const int* __restrict
             rsum += fabs(k);
         }
     }
-    amax = __longlong_as_double((long long)amb);
     rsum = group_sum(rsum);          // row sum of |K| (lanes of one row)
-    amax = warp_max(amax);
-    rsum = warp_max(rsum);           // largest row sum in the warp
-    __shared__ double s_am[8], s_rs[8];
+    // maxima of non-negative doubles as maxima of their bit patterns (integer
+    // shuffles: FP64 max instructions would queue on the slow FP64 pipe)
+    amb = warp_umax(amb);
+    const unsigned long long rsb = warp_umax(abs_bits(rsum));     // largest row sum in the warp
+    __shared__ unsigned long long s_am[8], s_rs[8];
     const int wid = threadIdx.x >> 5;
-    if (lane == 0) { s_am[wid] = amax; s_rs[wid] = rsum; }
+    if (lane == 0) { s_am[wid] = amb; s_rs[wid] = rsb; }
     __syncthreads();
     // one atomic per block and quantity (per-row atomics serialise on one address)
     if (threadIdx.x == 0) {
-        double a = 0.0, r = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a = fmax(a, s_am[q]); r = fmax(r, s_rs[q]); }
-        atomic_max_nonneg(&stat->amax_bits, a);
-        atomic_max_nonneg(&stat->knorm_bits, r);
+        unsigned long long a = 0ull, r = 0ull;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a = umax64(a, s_am[q]); r = umax64(r, s_rs[q]); }
+        atomicMax(&stat->amax_bits, a);
+        atomicMax(&stat->knorm_bits, r);
     }
 }
 
@@ -246,12 +272,141 @@ __device__ __forceinline__ void assemble_original(const DevSched& s, const DevNu
 
 // Fronts with F <= 32: one warp per front, the whole front in shared memory.
 // Lanes form an 8 x 4 grid over (row, column) of every block loop.
+constexpr int kWarpCbBatch = 8;        // contribution-block loads in flight per lane
+
+__device__ __forceinline__ void cp_async_word(void* smem_dst, const void* gsrc, int bytes)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Contribution block of one child (mc x mc, column-major, contiguous at cb)
+// into the front Fm (leading dimension F) at the child's relative indices:
+// Fm[rel[a] + rel[b] F] += cb[a + b mc]. The values come from vals (global
+// or shared), the indices from rl held by lanes 0..mc-1; every lane takes
+// entries e = lane + 32 t, kWarpCbBatch loads issued before any update.
+template <typename T>
+__device__ __forceinline__ void warp_add_child(const T* vals, int mc, int rl, int F, int lane, T* Fm)
+{
+    const int ne = mc * mc, q = 32 / mc, r = 32 - q * mc;
+    int a = lane % mc, b = lane / mc;                                 // entry lane = a + b mc
+    if (__isShared(vals)) {                                           // staged: no loads to batch
+        for (int e = lane; e - lane < ne; e += 32) {                  // warp-uniform trip count
+            const int ra = __shfl_sync(kFull, rl, a), rb = __shfl_sync(kFull, rl, b);
+            if (e < ne) Fm[ra + rb * F] += vals[e];
+            a += r;
+            b += q;
+            if (a >= mc) { a -= mc; ++b; }
+        }
+        return;
+    }
+    for (int e0 = 0; e0 < ne; e0 += 32 * kWarpCbBatch) {
+        T val[kWarpCbBatch];
+        int pos[kWarpCbBatch];
+#pragma unroll
+        for (int t = 0; t < kWarpCbBatch; ++t) {
+            const int e = e0 + lane + 32 * t;
+            val[t] = e < ne ? vals[e] : T(0);
+            pos[t] = e < ne ? -1 : -2;
+        }
+#pragma unroll
+        for (int t = 0; t < kWarpCbBatch; ++t) {
+            const int ra = __shfl_sync(kFull, rl, a), rb = __shfl_sync(kFull, rl, b);
+            if (pos[t] == -1) pos[t] = ra + rb * F;
+            a += r;
+            b += q;
+            if (a >= mc) { a -= mc; ++b; }
+        }
+#pragma unroll
+        for (int t = 0; t < kWarpCbBatch; ++t)
+            if (pos[t] >= 0) Fm[pos[t]] += val[t];
+    }
+}
+
+// The children of front f added to Fm in child order, one warp. Lane k holds
+// the descriptor of child k (32 at a time). Consecutive children whose
+// blocks fit the warp's staging area (stage_v values, stage_r relative
+// indices) are copied there by cp.async, all copies in flight together, so
+// a front with many children waits for memory about once instead of once per
+// child; a child too large for the staging area is read from global memory.
+template <typename T>
+__device__ __forceinline__ void warp_children(const DevSched& s, const DevNum<T>& nm, int f, int F, int lane, T* Fm,
+                                              T* sv, int stage_v, int* sr, int stage_r)
+{
+    const int c0 = s.child_ptr[f], nch = s.child_ptr[f + 1] - c0;
+    for (int k0 = 0; k0 < nch; k0 += 32) {
+        int my_mc = 0, my_rel = 0;
+        long long my_cb = 0;
+        if (k0 + lane < nch) {
+            const int ch = s.child_list[c0 + k0 + lane];
+            my_mc = s.sn_front[ch] - (s.sn_first[ch + 1] - s.sn_first[ch]);
+            my_cb = s.cb_off[ch];
+            my_rel = s.rel_ptr[ch];
+        }
+        const int nb = min(32, nch - k0);
+        // exclusive prefix sums over the lanes of mc^2 and mc
+        int vx = my_mc * my_mc, rx = my_mc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int vu = __shfl_up_sync(kFull, vx, o), ru = __shfl_up_sync(kFull, rx, o);
+            if (lane >= o) { vx += vu; rx += ru; }
+        }
+        vx -= my_mc * my_mc;
+        rx -= my_mc;
+        for (int k = 0; k < nb;) {
+            const int vk = __shfl_sync(kFull, vx, k), rk = __shfl_sync(kFull, rx, k);
+            // children k..k2-1 fit: prefix from k (sums grow with the lane)
+            const bool fits = lane >= k && lane < nb && vx + my_mc * my_mc - vk <= stage_v &&
+                              rx + my_mc - rk <= stage_r;
+            const int k2 = k + __popc(__ballot_sync(kFull, fits));
+            if (k2 == k) {                                            // too large: from global memory
+                const int mc = __shfl_sync(kFull, my_mc, k);
+                const T* cb = nm.cb + __shfl_sync(kFull, my_cb, k);
+                const int relp = __shfl_sync(kFull, my_rel, k);
+                const int rl = lane < mc ? s.rel[relp + lane] : 0;
+                if (mc > 0) warp_add_child<T>(cb, mc, rl, F, lane, Fm);
+                __syncwarp();
+                ++k;
+                continue;
+            }
+            for (int c = k; c < k2; ++c) {                            // every copy in flight together
+                const int mc = __shfl_sync(kFull, my_mc, c);
+                const T* cb = nm.cb + __shfl_sync(kFull, my_cb, c);
+                const int relp = __shfl_sync(kFull, my_rel, c);
+                const int vo = __shfl_sync(kFull, vx, c) - vk, ro = __shfl_sync(kFull, rx, c) - rk;
+                for (int e = lane; e < mc * mc; e += 32) cp_async_word(sv + vo + e, cb + e, (int)sizeof(T));
+                if (lane < mc) cp_async_word(sr + ro + lane, s.rel + relp + lane, 4);
+            }
+            cp_async_wait_all();
+            __syncwarp();
+            for (int c = k; c < k2; ++c) {                            // in child order
+                const int mc = __shfl_sync(kFull, my_mc, c);
+                const int vo = __shfl_sync(kFull, vx, c) - vk, ro = __shfl_sync(kFull, rx, c) - rk;
+                const int rl = lane < mc ? sr[ro + lane] : 0;
+                if (mc > 0) warp_add_child<T>(sv + vo, mc, rl, F, lane, Fm);
+                __syncwarp();
+            }
+            k = k2;
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
-                                                            int count, int maxF)
+                                                            int count, int maxF, int stage_v, int stage_r)
 {
-    // shared memory sized by the launch's largest front (maxF <= 32): the
-    // small leaf fronts of the widest levels keep many more warps resident
+    // shared memory sized by the launch's largest front (maxF <= 32) and the
+    // children's staging (per warp: stage_v values, stage_r relative
+    // indices): the small leaf fronts of the widest levels keep many more
+    // warps resident
     extern __shared__ __align__(16) unsigned char smraw[];
     const DevNum<T> nm = nm0.at(blockIdx.y);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -263,23 +418,14 @@ __global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T
     const int w = s.sn_first[f + 1] - first;
     const int F = s.sn_front[f];
     T* Fm = reinterpret_cast<T*>(smraw) + (int64_t)wid * maxF * maxF;
-    int* rls = reinterpret_cast<int*>(reinterpret_cast<T*>(smraw) + (int64_t)4 * maxF * maxF) + wid * maxF;
+    T* sv_base = reinterpret_cast<T*>(smraw) + (int64_t)4 * maxF * maxF;
+    int* sr_base = reinterpret_cast<int*>(sv_base + (int64_t)4 * stage_v);
     for (int t = lane; t < F * F; t += 32) Fm[t] = T(0);
     __syncwarp();
     assemble_original<T, 32>(s, nm, f, lane, Fm);
     __syncwarp();
-    for (int c = s.child_ptr[f]; c < s.child_ptr[f + 1]; ++c) {
-        const int ch = s.child_list[c];
-        const int mc = s.sn_front[ch] - (s.sn_first[ch + 1] - s.sn_first[ch]);
-        const T* cb = nm.cb + s.cb_off[ch];
-        if (lane < mc) rls[lane] = s.rel[s.rel_ptr[ch] + lane];      // mc < F <= 32
-        __syncwarp();
-        for (int b = lj; b < mc; b += 4) {
-            const int rb = rls[b] * F;
-            for (int a = li; a < mc; a += 8) Fm[rls[a] + rb] += cb[a + b * mc];
-        }
-        __syncwarp();
-    }
+    warp_children<T>(s, nm, f, F, lane, Fm, stage_v ? sv_base + (int64_t)wid * stage_v : nullptr, stage_v,
+                     sr_base + wid * stage_r, stage_r);
     const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
     __shared__ T srinv[4];
     for (int p = 0; p < w; ++p) {
@@ -894,12 +1040,12 @@ cudaError_t launch_zero_stat(DevStat* stat, cudaStream_t st)
 cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double* dtmp, int iters,
                         DevStat* stat, double** d_final, int batch, cudaStream_t st)
 {
-    fill_kernel<<<cdiv((int64_t)s.n * batch, 256), 256, 0, st>>>((int)((int64_t)s.n * batch), d, 1.0);
+    if (iters == 0) fill_kernel<<<cdiv((int64_t)s.n * batch, 256), 256, 0, st>>>((int)((int64_t)s.n * batch), d, 1.0);
     double* a = d;
     double* b = dtmp;
     for (int it = 0; it < iters; ++it) {
-        ruiz_kernel<<<dim3(cdiv((int64_t)s.n * kRowLanes, 256), batch), 256, 0, st>>>(
-            s.n, s.nnz, s.rowptr, s.colidx, vals, a, b, stat, it);
+        ruiz_kernel<<<dim3(cdiv(s.n, 32 * kRuizRows), batch), 256, 0, st>>>(s.n, s.nnz, s.rowptr, s.colidx, vals, a,
+                                                                            b, stat, it);
         double* t = a; a = b; b = t;
     }
     *d_final = a;
@@ -916,12 +1062,14 @@ cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d
 
 template <typename T>
 cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
-                               int batch, cudaStream_t st)
+                               int stage_v, int stage_r, int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    if (max_front < 1 || max_front > kWarpFrontMax) return cudaErrorInvalidValue;
-    const size_t smem = 4 * ((size_t)max_front * max_front * sizeof(T) + (size_t)max_front * sizeof(int));
-    front_warp_kernel<T><<<dim3(cdiv(count, 4), batch), 128, smem, st>>>(s, nm, fronts, count, max_front);
+    if (max_front < 1 || max_front > kWarpFrontMax || stage_v < 0 || stage_r < 0) return cudaErrorInvalidValue;
+    const size_t smem = 4 * ((size_t)max_front * max_front * sizeof(T) + (size_t)stage_v * sizeof(T) +
+                             (size_t)stage_r * sizeof(int));
+    front_warp_kernel<T><<<dim3(cdiv(count, 4), batch), 128, smem, st>>>(s, nm, fronts, count, max_front, stage_v,
+                                                                         stage_r);
     return cudaGetLastError();
 }
 
@@ -1069,12 +1217,6 @@ cudaError_t launch_norms(int n, const double* a, double* out, cudaStream_t st)
 // slow on this GPU); ||K||_inf comes from the refactorization's statistics.
 // Each block stores max |r|, |x|, |b| of its rows (as bits) in its slot of
 // `part`; omega_final_batched reduces the slots.
-__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) { return a > b ? a : b; }
-__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v)
-{
-    for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(kFull, v, o));
-    return v;
-}
 
 __global__ void __launch_bounds__(256) resid_omega_part_kernel(int n, int64_t nnz, const int* __restrict__ rp,
                                                                const int* __restrict__ ci,
@@ -1165,8 +1307,8 @@ cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci,
 // explicit instantiations
 #define KKT_INST(T)                                                                                              \
     template cudaError_t launch_scale<T>(const DevSched&, const DevNum<T>&, const double*, int, cudaStream_t);   \
-    template cudaError_t launch_fronts_warp<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,     \
-                                               cudaStream_t);                                                    \
+    template cudaError_t launch_fronts_warp<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int, int, \
+                                               int, cudaStream_t);                                               \
     template cudaError_t launch_fronts_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,      \
                                               cudaStream_t);                                                     \
     template cudaError_t launch_fronts_panel<T>(const DevSched&, const DevNum<T>&, const int*, int, size_t, T*,  \
@@ -1203,6 +1345,8 @@ cudaError_t configure_kernels()
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+    if ((e = allow_smem(front_warp_kernel<double>, optin))) return e;
+    if ((e = allow_smem(front_warp_kernel<float>, optin))) return e;
     if ((e = allow_smem(front_cta_kernel<double>, optin))) return e;
     if ((e = allow_smem(front_cta_kernel<float>, optin))) return e;
     if ((e = allow_smem(front_panel_kernel<double>, optin))) return e;

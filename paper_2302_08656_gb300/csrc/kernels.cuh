@@ -153,6 +153,8 @@ __device__ __forceinline__ float static_pivot(float piv, float floorT, DevStat* 
 struct FrontTile { int front; int ti; int tj; };
 
 constexpr int kWarpFrontMax = 32;      // fronts with F <= 32 are handled by one warp
+constexpr int kWarpStageV = 512;       // per warp: staged child-block values, at most
+constexpr int kWarpStageR = 192;       // ... and staged relative indices
 constexpr int kWarpLevelMin = 608;     // ... when their level has at least 4 x 152 of them
 constexpr int kPanelCbMin = 32;        // fronts with F - w >= 32 use panel + tiled Schur update
 constexpr int kTile = 16;              // Schur update tile (kTile x kTile)
@@ -215,7 +217,7 @@ template <typename T>
 cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                               int max_front, int batch, cudaStream_t st);
+                               int max_front, int stage_v, int stage_r, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fronts_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
                               int max_front, int batch, cudaStream_t st);

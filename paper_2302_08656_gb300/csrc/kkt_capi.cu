@@ -29,6 +29,7 @@ struct LevelGroup {
     int cta_off = 0, cta_cnt = 0, cta_maxF = 0;
     int panel_off = 0, panel_cnt = 0, panel_maxW = 0;
     int small_maxF = 0, small_maxW = 0, big_maxF = 0, big_maxW = 0;   // solve: warp / CTA classes
+    int warp_stage_v = 0, warp_stage_r = 0;   // warp kernel: children's staging per warp (values, indices)
     size_t panel_smem = 0;                    // 0 with panel_global = true
     bool panel_global = false;
     int tile_off = 0, tile_cnt = 0;
@@ -237,6 +238,15 @@ void build_levels(const Analysis& an, size_t es, int nlev, std::vector<LevelGrou
         for (int s : wl) {
             g.small_maxF = std::max(g.small_maxF, an.sn_front[s]);
             g.small_maxW = std::max(g.small_maxW, an.sn_first[s + 1] - an.sn_first[s]);
+            int vol = 0, rs = 0;                  // children's blocks of this front: values, rows
+            for (int c = an.child_ptr[s]; c < an.child_ptr[s + 1]; ++c) {
+                const int ch = an.child_list[c];
+                const int mc = an.sn_front[ch] - (an.sn_first[ch + 1] - an.sn_first[ch]);
+                vol += mc * mc;
+                rs += mc;
+            }
+            g.warp_stage_v = std::max(g.warp_stage_v, std::min(vol, kWarpStageV));
+            g.warp_stage_r = std::max(g.warp_stage_r, std::min(rs, kWarpStageR));
         }
         for (const std::vector<int>* lst : {&cl, &pl})
             for (int s : *lst) {
@@ -385,7 +395,8 @@ kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused 
     for (const LevelGroup& g : c->levels) {
         if (g.warp_cnt) {
             Launch L(c, st, KK_FRONT_WARP, 1);
-            KKT_CUDA(launch_fronts_warp<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, B, st));
+            KKT_CUDA(launch_fronts_warp<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, g.warp_stage_v,
+                                           g.warp_stage_r, B, st));
         }
         if (g.cta_cnt) {
             Launch L(c, st, KK_FRONT_CTA, 1);
@@ -485,7 +496,7 @@ kkt_status refactor_t(kkt_ctx* c, const double* d_vals, cudaStream_t st)
     KKT_CUDA(cudaMemsetAsync(c->stat, 0, sizeof(DevStat) * c->batch, st));
     double* dfin = nullptr;
     {
-        Launch L(c, st, KK_RUIZ, 1 + c->opt.ruiz_iters);
+        Launch L(c, st, KK_RUIZ, c->opt.ruiz_iters > 0 ? c->opt.ruiz_iters : 1);
         KKT_CUDA(launch_ruiz(c->sched, d_vals, c->d_a, c->d_b, c->opt.ruiz_iters, c->stat, &dfin, c->batch, st));
     }
     c->d_final = dfin;
@@ -548,7 +559,7 @@ kkt_status refactor_solve_t(kkt_ctx* c, const double* d_vals, const double* b, d
     KKT_CUDA(cudaMemsetAsync(c->stat, 0, sizeof(DevStat) * B, st));
     double* dfin = nullptr;
     {
-        Launch L(c, st, KK_RUIZ, 1 + c->opt.ruiz_iters);
+        Launch L(c, st, KK_RUIZ, c->opt.ruiz_iters > 0 ? c->opt.ruiz_iters : 1);
         KKT_CUDA(launch_ruiz(c->sched, d_vals, c->d_a, c->d_b, c->opt.ruiz_iters, c->stat, &dfin, B, st));
     }
     c->d_final = dfin;
