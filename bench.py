@@ -177,7 +177,8 @@ MEASURED_TRAFFIC = {
 }
 
 PHASE_OF = {
-    "front_warp_kernel": "refactor", "front_cta_kernel": "refactor", "front_panel_kernel": "refactor",
+    "front_warp_kernel": "refactor", "front_leaf_kernel": "refactor", "front_cta_kernel": "refactor",
+    "front_panel_kernel": "refactor",
     "schur_tile_kernel": "refactor", "ruiz_kernel": "refactor", "scale_kernel": "refactor",
     "solve_fwd_kernel": "solve", "solve_bwd_kernel": "solve", "solve_pre_kernel": "solve",
     "solve_post_kernel": "solve", "spmv_resid_kernel": "spmv", "tree_factor_kernel": "refactor",

@@ -454,6 +454,63 @@ __global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T
         for (int a = li; a < m; a += 8) cbo[a + b * m] = Fm[(w + a) + (w + b) * F];
 }
 
+// Childless fronts with F <= G (G = 8 or 16): G lanes per front, 32 / G
+// fronts per warp, so the widest leaf level (tens of thousands of fronts of
+// a handful of rows) needs a quarter or half of the warps, each going once
+// through the same chain of dependent loads. Lanes of a group form 8 rows x
+// G / 8 column groups; the arithmetic on every entry is that of
+// front_warp_kernel (original entries, then one reciprocal and the rank-1
+// updates per pivot, in pivot order).
+template <typename T, int G>
+__global__ void __launch_bounds__(128) front_leaf_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
+                                                         int count)
+{
+    constexpr int NG = 32 / G, LJ = G / 8;
+    __shared__ T Fall[4 * NG * G * G];
+    __shared__ T srinv[4 * NG];
+    const DevNum<T> nm = nm0.at(blockIdx.y);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gi = lane / G, gl = lane % G, slot = wid * NG + gi;
+    const unsigned gmask = (unsigned)(((1ull << G) - 1ull) << (gi * G));
+    const int fi = (blockIdx.x * 4 + wid) * NG + gi;
+    if (fi >= count) return;                                       // the whole group
+    const int li = gl & 7, lj = gl >> 3;
+    const int f = fronts[fi];
+    const int first = s.sn_first[f];
+    const int w = s.sn_first[f + 1] - first;
+    const int F = s.sn_front[f];
+    T* Fm = Fall + slot * G * G;                                   // leading dimension F <= G
+    for (int t = gl; t < F * F; t += G) Fm[t] = T(0);
+    __syncwarp(gmask);
+    assemble_original<T, G>(s, nm, f, gl, Fm);
+    __syncwarp(gmask);
+    const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
+    for (int p = 0; p < w; ++p) {
+        if (gl == 0) {                                             // one reciprocal per pivot
+            const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
+            Fm[p + p * F] = pv;
+            srinv[slot] = pivot_rcp(pv);
+        }
+        __syncwarp(gmask);
+        if (gl > p && gl < F) Fm[gl + p * F] *= srinv[slot];
+        __syncwarp(gmask);
+        for (int j = p + 1 + lj; j < F; j += LJ) {
+            const T u = Fm[p + j * F];
+            for (int i = p + 1 + li; i < F; i += 8) Fm[i + j * F] -= Fm[i + p * F] * u;
+        }
+        __syncwarp(gmask);
+    }
+    T* pan = nm.panel + s.panel_off[f];
+    const int m = F - w;
+    for (int t = gl; t < F * w; t += G) pan[t] = Fm[t];
+    T* U12 = pan + F * w;                                          // column-major (ld = w)
+    for (int b = lj; b < m; b += LJ)
+        for (int a = li; a < w; a += 8) U12[a + b * w] = Fm[a + (w + b) * F];
+    T* cbo = nm.cb + s.cb_off[f];
+    for (int b = lj; b < m; b += LJ)
+        for (int a = li; a < m; a += 8) cbo[a + b * m] = Fm[(w + a) + (w + b) * F];
+}
+
 // Fronts with F > 32 and a small contribution block: one CTA (8 warps) per
 // front, the whole front in shared memory, right-looking rank-1 updates.
 // Threads form a 32 x 8 grid: lane -> row, warp -> column.
@@ -1074,6 +1131,20 @@ cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int
 }
 
 template <typename T>
+cudaError_t launch_fronts_leaf(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int group,
+                               int batch, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    if (group == 8)
+        front_leaf_kernel<T, 8><<<dim3(cdiv(count, 16), batch), 128, 0, st>>>(s, nm, fronts, count);
+    else if (group == 16)
+        front_leaf_kernel<T, 16><<<dim3(cdiv(count, 8), batch), 128, 0, st>>>(s, nm, fronts, count);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_fronts_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
                               int batch, cudaStream_t st)
 {
@@ -1309,6 +1380,8 @@ cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci,
     template cudaError_t launch_scale<T>(const DevSched&, const DevNum<T>&, const double*, int, cudaStream_t);   \
     template cudaError_t launch_fronts_warp<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int, int, \
                                                int, cudaStream_t);                                               \
+    template cudaError_t launch_fronts_leaf<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,     \
+                                               cudaStream_t);                                                    \
     template cudaError_t launch_fronts_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,      \
                                               cudaStream_t);                                                     \
     template cudaError_t launch_fronts_panel<T>(const DevSched&, const DevNum<T>&, const int*, int, size_t, T*,  \

@@ -30,6 +30,10 @@ struct LevelGroup {
     int panel_off = 0, panel_cnt = 0, panel_maxW = 0;
     int small_maxF = 0, small_maxW = 0, big_maxF = 0, big_maxW = 0;   // solve: warp / CTA classes
     int warp_stage_v = 0, warp_stage_r = 0;   // warp kernel: children's staging per warp (values, indices)
+    // refactorization only: childless fronts with F <= 8 / F <= 16 (several per
+    // warp), then the rest of the warp class (the solves take the whole class)
+    int leaf8_off = 0, leaf8_cnt = 0, leaf16_off = 0, leaf16_cnt = 0;
+    int wfac_off = 0, wfac_cnt = 0, wfac_maxF = 0;
     size_t panel_smem = 0;                    // 0 with panel_global = true
     bool panel_global = false;
     int tile_off = 0, tile_cnt = 0;
@@ -235,9 +239,18 @@ void build_levels(const Analysis& an, size_t es, int nlev, std::vector<LevelGrou
             cl.insert(cl.begin(), wl.begin(), wl.end());
             wl.clear();
         }
+        std::vector<int> l8, l16, wrest;
+        for (int s : wl) {
+            const int F = an.sn_front[s];
+            const bool leaf = an.child_ptr[s + 1] == an.child_ptr[s];
+            (leaf && F <= 8 ? l8 : leaf && F <= 16 ? l16 : wrest).push_back(s);
+        }
         for (int s : wl) {
             g.small_maxF = std::max(g.small_maxF, an.sn_front[s]);
             g.small_maxW = std::max(g.small_maxW, an.sn_first[s + 1] - an.sn_first[s]);
+        }
+        for (int s : wrest) {
+            g.wfac_maxF = std::max(g.wfac_maxF, an.sn_front[s]);
             int vol = 0, rs = 0;                  // children's blocks of this front: values, rows
             for (int c = an.child_ptr[s]; c < an.child_ptr[s + 1]; ++c) {
                 const int ch = an.child_list[c];
@@ -261,6 +274,15 @@ void build_levels(const Analysis& an, size_t es, int nlev, std::vector<LevelGrou
         g.warp_off = (int)front_ids.size();
         front_ids.insert(front_ids.end(), wl.begin(), wl.end());
         g.warp_cnt = (int)wl.size();
+        g.leaf8_off = (int)front_ids.size();
+        front_ids.insert(front_ids.end(), l8.begin(), l8.end());
+        g.leaf8_cnt = (int)l8.size();
+        g.leaf16_off = (int)front_ids.size();
+        front_ids.insert(front_ids.end(), l16.begin(), l16.end());
+        g.leaf16_cnt = (int)l16.size();
+        g.wfac_off = (int)front_ids.size();
+        front_ids.insert(front_ids.end(), wrest.begin(), wrest.end());
+        g.wfac_cnt = (int)wrest.size();
         g.cta_off = (int)front_ids.size();
         front_ids.insert(front_ids.end(), cl.begin(), cl.end());
         g.cta_cnt = (int)cl.size();
@@ -313,12 +335,12 @@ DevNum<float>& num_of<float>(kkt_ctx* c) { return c->nf; }
 
 enum KernelKind { KK_RUIZ = 0, KK_SCALE, KK_FRONT_WARP, KK_FRONT_CTA, KK_FRONT_PANEL, KK_SCHUR, KK_SOLVE_PRE,
                   KK_SOLVE_FWD, KK_SOLVE_BWD, KK_SOLVE_POST, KK_SPMV, KK_REDUCE, KK_VECTOR, KK_TREE_FACTOR,
-                  KK_TREE_FWD, KK_TREE_BWD, KK_JACOBI, KK_COUNT };
+                  KK_TREE_FWD, KK_TREE_BWD, KK_JACOBI, KK_FRONT_LEAF, KK_COUNT };
 const char* const kKernelNames[KK_COUNT] = {
     "ruiz_kernel", "scale_kernel", "front_warp_kernel", "front_cta_kernel", "front_panel_kernel",
     "schur_tile_kernel", "solve_pre_kernel", "solve_fwd_kernel", "solve_bwd_kernel", "solve_post_kernel",
     "spmv_resid_kernel", "reduction_kernels", "vector_kernels", "tree_factor_kernel", "tree_fwd_kernel",
-    "tree_bwd_kernel", "jacobi_kernels"};
+    "tree_bwd_kernel", "jacobi_kernels", "front_leaf_kernel"};
 
 // Counts kernels and, in profiling mode, brackets the launch group with a
 // pair of events on the launching stream.
@@ -393,9 +415,17 @@ kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused 
     const int nq = c->tsched.nq;
     if (nq > 0) KKT_CUDA(cudaMemsetAsync(c->ctr_fac, 0, sizeof(int) * (kCtrHead + 2 * (size_t)B * nq), st));
     for (const LevelGroup& g : c->levels) {
-        if (g.warp_cnt) {
+        if (g.leaf8_cnt) {
+            Launch L(c, st, KK_FRONT_LEAF, 1);
+            KKT_CUDA(launch_fronts_leaf<T>(c->sched, nm, fr + g.leaf8_off, g.leaf8_cnt, 8, B, st));
+        }
+        if (g.leaf16_cnt) {
+            Launch L(c, st, KK_FRONT_LEAF, 1);
+            KKT_CUDA(launch_fronts_leaf<T>(c->sched, nm, fr + g.leaf16_off, g.leaf16_cnt, 16, B, st));
+        }
+        if (g.wfac_cnt) {
             Launch L(c, st, KK_FRONT_WARP, 1);
-            KKT_CUDA(launch_fronts_warp<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, g.warp_stage_v,
+            KKT_CUDA(launch_fronts_warp<T>(c->sched, nm, fr + g.wfac_off, g.wfac_cnt, g.wfac_maxF, g.warp_stage_v,
                                            g.warp_stage_r, B, st));
         }
         if (g.cta_cnt) {
