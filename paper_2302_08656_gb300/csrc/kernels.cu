@@ -331,15 +331,44 @@ __device__ __forceinline__ void warp_add_child(const T* vals, int mc, int rl, in
     }
 }
 
+// Forward step of front f with its factored front Fm (leading dimension F)
+// still in shared memory, nl lanes (lane l of them; sync: their mask): v holds
+// the pivot rows of the step vector plus the children's vectors. The
+// operations, in order, of solve_fwd_kernel: the unit lower solve with L11,
+// then each contribution row's sum over the pivots in sequence; the pivot
+// rows go back to the step vector and the contribution rows to the front's
+// vector for its parent.
+template <typename T>
+__device__ __forceinline__ void front_forward(const DevSched& s, const DevNum<T>& nm, int f, int first, int w, int F,
+                                              const T* Fm, T* v, int l, int nl, unsigned mask)
+{
+    for (int p = 0; p < w; ++p) {
+        const T xp = v[p];
+        for (int i = p + 1 + l; i < w; i += nl) v[i] -= Fm[i + p * F] * xp;
+        __syncwarp(mask);
+    }
+    for (int i = w + l; i < F; i += nl) {
+        T acc = v[i];
+        for (int p = 0; p < w; ++p) acc -= Fm[i + p * F] * v[p];
+        v[i] = acc;
+    }
+    __syncwarp(mask);
+    for (int a = l; a < w; a += nl) nm.vec[first + a] = v[a];
+    T* cv = nm.cbv + s.rel_ptr[f];
+    for (int t = l; t < F - w; t += nl) cv[t] = v[w + t];
+}
+
 // The children of front f added to Fm in child order, one warp. Lane k holds
 // the descriptor of child k (32 at a time). Consecutive children whose
 // blocks fit the warp's staging area (stage_v values, stage_r relative
 // indices) are copied there by cp.async, all copies in flight together, so
 // a front with many children waits for memory about once instead of once per
 // child; a child too large for the staging area is read from global memory.
+// With v (fused forward step) every child's vector is added to v as well,
+// staged in scv beside its relative indices.
 template <typename T>
 __device__ __forceinline__ void warp_children(const DevSched& s, const DevNum<T>& nm, int f, int F, int lane, T* Fm,
-                                              T* sv, int stage_v, int* sr, int stage_r)
+                                              T* sv, int stage_v, int* sr, int stage_r, T* v, T* scv)
 {
     const int c0 = s.child_ptr[f], nch = s.child_ptr[f + 1] - c0;
     for (int k0 = 0; k0 < nch; k0 += 32) {
@@ -373,6 +402,7 @@ __device__ __forceinline__ void warp_children(const DevSched& s, const DevNum<T>
                 const int relp = __shfl_sync(kFull, my_rel, k);
                 const int rl = lane < mc ? s.rel[relp + lane] : 0;
                 if (mc > 0) warp_add_child<T>(cb, mc, rl, F, lane, Fm);
+                if (v && lane < mc) v[rl] += nm.cbv[relp + lane];      // forward step: the child's vector
                 __syncwarp();
                 ++k;
                 continue;
@@ -384,6 +414,7 @@ __device__ __forceinline__ void warp_children(const DevSched& s, const DevNum<T>
                 const int vo = __shfl_sync(kFull, vx, c) - vk, ro = __shfl_sync(kFull, rx, c) - rk;
                 for (int e = lane; e < mc * mc; e += 32) cp_async_word(sv + vo + e, cb + e, (int)sizeof(T));
                 if (lane < mc) cp_async_word(sr + ro + lane, s.rel + relp + lane, 4);
+                if (v && lane < mc) cp_async_word(scv + ro + lane, nm.cbv + relp + lane, (int)sizeof(T));
             }
             cp_async_wait_all();
             __syncwarp();
@@ -392,6 +423,7 @@ __device__ __forceinline__ void warp_children(const DevSched& s, const DevNum<T>
                 const int vo = __shfl_sync(kFull, vx, c) - vk, ro = __shfl_sync(kFull, rx, c) - rk;
                 const int rl = lane < mc ? sr[ro + lane] : 0;
                 if (mc > 0) warp_add_child<T>(sv + vo, mc, rl, F, lane, Fm);
+                if (v && lane < mc) v[rl] += scv[ro + lane];
                 __syncwarp();
             }
             k = k2;
@@ -401,7 +433,7 @@ __device__ __forceinline__ void warp_children(const DevSched& s, const DevNum<T>
 
 template <typename T>
 __global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
-                                                            int count, int maxF, int stage_v, int stage_r)
+                                                            int count, int maxF, int stage_v, int stage_r, int fused)
 {
     // shared memory sized by the launch's largest front (maxF <= 32) and the
     // children's staging (per warp: stage_v values, stage_r relative
@@ -417,15 +449,20 @@ __global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T
     const int first = s.sn_first[f];
     const int w = s.sn_first[f + 1] - first;
     const int F = s.sn_front[f];
+    // per warp: front (maxF^2), staged child blocks (stage_v), forward-step
+    // vector (32) and staged child vectors (stage_r); then the indices
     T* Fm = reinterpret_cast<T*>(smraw) + (int64_t)wid * maxF * maxF;
     T* sv_base = reinterpret_cast<T*>(smraw) + (int64_t)4 * maxF * maxF;
-    int* sr_base = reinterpret_cast<int*>(sv_base + (int64_t)4 * stage_v);
+    T* v = sv_base + (int64_t)4 * stage_v + wid * 32;
+    T* scv = sv_base + (int64_t)4 * stage_v + 4 * 32 + (int64_t)wid * stage_r;
+    int* sr_base = reinterpret_cast<int*>(sv_base + (int64_t)4 * (stage_v + 32 + stage_r));
     for (int t = lane; t < F * F; t += 32) Fm[t] = T(0);
+    if (fused) v[lane] = lane < w ? nm.vec[first + lane] : T(0);  // F <= 32
     __syncwarp();
     assemble_original<T, 32>(s, nm, f, lane, Fm);
     __syncwarp();
     warp_children<T>(s, nm, f, F, lane, Fm, stage_v ? sv_base + (int64_t)wid * stage_v : nullptr, stage_v,
-                     sr_base + wid * stage_r, stage_r);
+                     sr_base + wid * stage_r, stage_r, fused ? v : nullptr, scv);
     const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
     __shared__ T srinv[4];
     for (int p = 0; p < w; ++p) {
@@ -443,6 +480,7 @@ __global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T
         }
         __syncwarp();
     }
+    if (fused) front_forward<T>(s, nm, f, first, w, F, Fm, v, lane, 32, kFull);
     T* pan = nm.panel + s.panel_off[f];
     const int m = F - w;
     for (int t = lane; t < F * w; t += 32) pan[t] = Fm[t];
@@ -460,13 +498,15 @@ __global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T
 // through the same chain of dependent loads. Lanes of a group form 8 rows x
 // G / 8 column groups; the arithmetic on every entry is that of
 // front_warp_kernel (original entries, then one reciprocal and the rank-1
-// updates per pivot, in pivot order).
+// updates per pivot, in pivot order); fused: the forward step of the
+// right-hand side follows (childless: v starts as the pivot rows).
 template <typename T, int G>
 __global__ void __launch_bounds__(128) front_leaf_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
-                                                         int count)
+                                                         int count, int fused)
 {
     constexpr int NG = 32 / G, LJ = G / 8;
     __shared__ T Fall[4 * NG * G * G];
+    __shared__ T Vall[4 * NG * G];                                 // fused: forward-step vectors
     __shared__ T srinv[4 * NG];
     const DevNum<T> nm = nm0.at(blockIdx.y);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -480,7 +520,9 @@ __global__ void __launch_bounds__(128) front_leaf_kernel(DevSched s, DevNum<T> n
     const int w = s.sn_first[f + 1] - first;
     const int F = s.sn_front[f];
     T* Fm = Fall + slot * G * G;                                   // leading dimension F <= G
+    T* v = Vall + slot * G;
     for (int t = gl; t < F * F; t += G) Fm[t] = T(0);
+    if (fused && gl < F) v[gl] = gl < w ? nm.vec[first + gl] : T(0);
     __syncwarp(gmask);
     assemble_original<T, G>(s, nm, f, gl, Fm);
     __syncwarp(gmask);
@@ -500,6 +542,7 @@ __global__ void __launch_bounds__(128) front_leaf_kernel(DevSched s, DevNum<T> n
         }
         __syncwarp(gmask);
     }
+    if (fused) front_forward<T>(s, nm, f, first, w, F, Fm, v, gl, G, gmask);
     T* pan = nm.panel + s.panel_off[f];
     const int m = F - w;
     for (int t = gl; t < F * w; t += G) pan[t] = Fm[t];
@@ -1119,26 +1162,26 @@ cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d
 
 template <typename T>
 cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
-                               int stage_v, int stage_r, int batch, cudaStream_t st)
+                               int stage_v, int stage_r, int fused, int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     if (max_front < 1 || max_front > kWarpFrontMax || stage_v < 0 || stage_r < 0) return cudaErrorInvalidValue;
-    const size_t smem = 4 * ((size_t)max_front * max_front * sizeof(T) + (size_t)stage_v * sizeof(T) +
+    const size_t smem = 4 * ((size_t)(max_front * max_front + stage_v + 32 + stage_r) * sizeof(T) +
                              (size_t)stage_r * sizeof(int));
     front_warp_kernel<T><<<dim3(cdiv(count, 4), batch), 128, smem, st>>>(s, nm, fronts, count, max_front, stage_v,
-                                                                         stage_r);
+                                                                         stage_r, fused);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fronts_leaf(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int group,
-                               int batch, cudaStream_t st)
+                               int fused, int batch, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     if (group == 8)
-        front_leaf_kernel<T, 8><<<dim3(cdiv(count, 16), batch), 128, 0, st>>>(s, nm, fronts, count);
+        front_leaf_kernel<T, 8><<<dim3(cdiv(count, 16), batch), 128, 0, st>>>(s, nm, fronts, count, fused);
     else if (group == 16)
-        front_leaf_kernel<T, 16><<<dim3(cdiv(count, 8), batch), 128, 0, st>>>(s, nm, fronts, count);
+        front_leaf_kernel<T, 16><<<dim3(cdiv(count, 8), batch), 128, 0, st>>>(s, nm, fronts, count, fused);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -1379,9 +1422,9 @@ cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci,
 #define KKT_INST(T)                                                                                              \
     template cudaError_t launch_scale<T>(const DevSched&, const DevNum<T>&, const double*, int, cudaStream_t);   \
     template cudaError_t launch_fronts_warp<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int, int, \
-                                               int, cudaStream_t);                                               \
+                                               int, int, cudaStream_t);                                          \
     template cudaError_t launch_fronts_leaf<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,     \
-                                               cudaStream_t);                                                    \
+                                               int, cudaStream_t);                                               \
     template cudaError_t launch_fronts_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,      \
                                               cudaStream_t);                                                     \
     template cudaError_t launch_fronts_panel<T>(const DevSched&, const DevNum<T>&, const int*, int, size_t, T*,  \

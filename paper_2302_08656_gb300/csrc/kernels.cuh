@@ -217,10 +217,10 @@ template <typename T>
 cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fronts_warp(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
-                               int max_front, int stage_v, int stage_r, int batch, cudaStream_t st);
+                               int max_front, int stage_v, int stage_r, int fused, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fronts_leaf(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int group,
-                               int batch, cudaStream_t st);
+                               int fused, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_fronts_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
                               int max_front, int batch, cudaStream_t st);

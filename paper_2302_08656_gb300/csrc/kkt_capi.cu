@@ -405,8 +405,9 @@ template <typename T>
 kkt_status fwd_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st);
 
 // fused: the forward substitution of the right-hand side staged in nm.vec
-// rides along (level-launched part after its factorization, tree part inside
-// the persistent kernel)
+// rides along (warp classes of the level-launched part inside their
+// factorization kernels, larger level fronts right after their level, tree
+// part inside the persistent kernel)
 template <typename T>
 kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused = false)
 {
@@ -415,18 +416,19 @@ kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused 
     const int nq = c->tsched.nq;
     if (nq > 0) KKT_CUDA(cudaMemsetAsync(c->ctr_fac, 0, sizeof(int) * (kCtrHead + 2 * (size_t)B * nq), st));
     for (const LevelGroup& g : c->levels) {
+        const int fz = fused ? 1 : 0;
         if (g.leaf8_cnt) {
             Launch L(c, st, KK_FRONT_LEAF, 1);
-            KKT_CUDA(launch_fronts_leaf<T>(c->sched, nm, fr + g.leaf8_off, g.leaf8_cnt, 8, B, st));
+            KKT_CUDA(launch_fronts_leaf<T>(c->sched, nm, fr + g.leaf8_off, g.leaf8_cnt, 8, fz, B, st));
         }
         if (g.leaf16_cnt) {
             Launch L(c, st, KK_FRONT_LEAF, 1);
-            KKT_CUDA(launch_fronts_leaf<T>(c->sched, nm, fr + g.leaf16_off, g.leaf16_cnt, 16, B, st));
+            KKT_CUDA(launch_fronts_leaf<T>(c->sched, nm, fr + g.leaf16_off, g.leaf16_cnt, 16, fz, B, st));
         }
         if (g.wfac_cnt) {
             Launch L(c, st, KK_FRONT_WARP, 1);
             KKT_CUDA(launch_fronts_warp<T>(c->sched, nm, fr + g.wfac_off, g.wfac_cnt, g.wfac_maxF, g.warp_stage_v,
-                                           g.warp_stage_r, B, st));
+                                           g.warp_stage_r, fz, B, st));
         }
         if (g.cta_cnt) {
             Launch L(c, st, KK_FRONT_CTA, 1);
@@ -442,10 +444,13 @@ kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused 
             Launch L(c, st, KK_SCHUR, 1);
             KKT_CUDA(launch_schur_tiles<T>(c->sched, nm, c->tiles_dev + g.tile_off, g.tile_cnt, g.panel_maxW, B, st));
         }
-    }
-    if (fused) {
-        kkt_status s = fwd_levels<T>(c, nm, B, st);
-        if (s != KKT_OK) return s;
+        // fused: the warp classes did their forward steps; the CTA and panel
+        // classes take theirs now, before the next level needs their vectors
+        const int nbig = g.cta_cnt + g.panel_cnt;
+        if (fused && nbig) {
+            Launch L(c, st, KK_SOLVE_FWD, 1);
+            KKT_CUDA(launch_solve_fwd_cta<T>(c->sched, nm, fr + g.cta_off, nbig, g.big_maxF, g.big_maxW, B, st));
+        }
     }
     if (nq > 0) {
         Launch L(c, st, KK_TREE_FACTOR, 1);
