@@ -912,6 +912,54 @@ __global__ void __launch_bounds__(128) solve_bwd_kernel(DevSched s, DevNum<T> nm
     for (int a = lane; a < w; a += 32) nm.vec[first + a] = v[a];
 }
 
+// Back substitution of childless fronts with F <= G (G = 8 or 16): G lanes per
+// front, 32 / G fronts per warp (the widest leaf level), the operations of
+// solve_bwd_kernel in its order.
+template <typename T, int G>
+__global__ void __launch_bounds__(128) solve_bwd_leaf_kernel(DevSched s, DevNum<T> nm0, const int* __restrict__ fronts,
+                                                             int count)
+{
+    constexpr int NG = 32 / G;
+    __shared__ T Vall[4 * NG * G];
+    __shared__ T Uall[4 * NG * G * G];
+    const DevNum<T> nm = nm0.at(blockIdx.y);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gi = lane / G, gl = lane % G, slot = wid * NG + gi;
+    const unsigned gmask = (unsigned)(((1ull << G) - 1ull) << (gi * G));
+    const int fi = (blockIdx.x * 4 + wid) * NG + gi;
+    if (fi >= count) return;                                       // the whole group
+    T* v = Vall + slot * G;
+    T* Us = Uall + slot * G * G;
+    const int f = fronts[fi];
+    const int first = s.sn_first[f];
+    const int w = s.sn_first[f + 1] - first;
+    const int F = s.sn_front[f];
+    const int m = F - w;
+    const int* R = s.rows + s.rows_ptr[f];
+    const T* pan = nm.panel + s.panel_off[f];
+    const T* U12 = pan + (int64_t)F * w;
+    for (int t = gl; t < m; t += G) v[w + t] = nm.vec[R[w + t]];
+    for (int e = gl; e < w * w; e += G) {
+        const int c = e / w, a = e - c * w;
+        Us[a + c * w] = pan[a + (int64_t)c * F];
+    }
+    __syncwarp(gmask);
+    for (int a = gl; a < w; a += G) {
+        T acc = nm.vec[first + a];
+        for (int t = 0; t < m; ++t) acc -= U12[a + (int64_t)t * w] * v[w + t];
+        v[a] = acc;
+    }
+    __syncwarp(gmask);
+    for (int p = w - 1; p >= 0; --p) {
+        const T xp = v[p] * pivot_rcp(Us[p + p * w]);            // x_p = v_p * (1 / u_pp), as every backward kernel
+        __syncwarp(gmask);
+        if (gl == 0) v[p] = xp;
+        for (int a = gl; a < p; a += G) v[a] -= Us[a + p * w] * xp;
+        __syncwarp(gmask);
+    }
+    for (int a = gl; a < w; a += G) nm.vec[first + a] = v[a];
+}
+
 // The same two substitutions for larger fronts, one CTA (128 threads) per
 // front: one warp does the sequential pivot block, all threads the L21 / U12
 // products.
@@ -1188,6 +1236,20 @@ cudaError_t launch_fronts_leaf(const DevSched& s, const DevNum<T>& nm, const int
 }
 
 template <typename T>
+cudaError_t launch_solve_bwd_leaf(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int group,
+                                  int batch, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    if (group == 8)
+        solve_bwd_leaf_kernel<T, 8><<<dim3(cdiv(count, 16), batch), 128, 0, st>>>(s, nm, fronts, count);
+    else if (group == 16)
+        solve_bwd_leaf_kernel<T, 16><<<dim3(cdiv(count, 8), batch), 128, 0, st>>>(s, nm, fronts, count);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_fronts_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int max_front,
                               int batch, cudaStream_t st)
 {
@@ -1425,6 +1487,8 @@ cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci,
                                                int, int, cudaStream_t);                                          \
     template cudaError_t launch_fronts_leaf<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,     \
                                                int, cudaStream_t);                                               \
+    template cudaError_t launch_solve_bwd_leaf<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,  \
+                                                  cudaStream_t);                                                 \
     template cudaError_t launch_fronts_cta<T>(const DevSched&, const DevNum<T>&, const int*, int, int, int,      \
                                               cudaStream_t);                                                     \
     template cudaError_t launch_fronts_panel<T>(const DevSched&, const DevNum<T>&, const int*, int, size_t, T*,  \

@@ -222,6 +222,9 @@ template <typename T>
 cudaError_t launch_fronts_leaf(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int group,
                                int fused, int batch, cudaStream_t st);
 template <typename T>
+cudaError_t launch_solve_bwd_leaf(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count, int group,
+                                  int batch, cudaStream_t st);
+template <typename T>
 cudaError_t launch_fronts_cta(const DevSched& s, const DevNum<T>& nm, const int* fronts, int count,
                               int max_front, int batch, cudaStream_t st);
 template <typename T>

@@ -504,9 +504,18 @@ kkt_status bwd_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st, b
     for (size_t l = c->levels.size(); l-- > 0;) {
         const LevelGroup& g = c->levels[l];
         const int nbig = g.cta_cnt + g.panel_cnt;
-        if (g.warp_cnt) {
+        // the warp class: small childless fronts several per warp, the rest a warp each
+        if (g.leaf8_cnt) {
             Launch L(c, st, KK_SOLVE_BWD, 1);
-            KKT_CUDA(launch_solve_bwd<T>(c->sched, nm, fr + g.warp_off, g.warp_cnt, g.small_maxF, g.small_maxW, B, st));
+            KKT_CUDA(launch_solve_bwd_leaf<T>(c->sched, nm, fr + g.leaf8_off, g.leaf8_cnt, 8, B, st));
+        }
+        if (g.leaf16_cnt) {
+            Launch L(c, st, KK_SOLVE_BWD, 1);
+            KKT_CUDA(launch_solve_bwd_leaf<T>(c->sched, nm, fr + g.leaf16_off, g.leaf16_cnt, 16, B, st));
+        }
+        if (g.wfac_cnt) {
+            Launch L(c, st, KK_SOLVE_BWD, 1);
+            KKT_CUDA(launch_solve_bwd<T>(c->sched, nm, fr + g.wfac_off, g.wfac_cnt, g.small_maxF, g.small_maxW, B, st));
         }
         if (nbig) {
             Launch L(c, st, KK_SOLVE_BWD, 1);
