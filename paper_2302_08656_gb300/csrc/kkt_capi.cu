@@ -1185,10 +1185,21 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
         kkt_destroy(c);
         return KKT_E_NOMEM;
     }
+    // Uploads and clears go through the context's own non-blocking stream and
+    // are waited for before kkt_analyze returns: a plain cudaMemcpy from
+    // pageable memory (or a cudaMemset) may return before the device holds the
+    // data, and is not ordered before work the caller then issues on a
+    // non-blocking stream of its own.
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        c->cap_stream = nullptr;
+        kkt_destroy(c);
+        return KKT_E_CUDA;
+    }
+    cudaStream_t ust = c->cap_stream;
     auto up = [&](void* dst, const void* src, size_t bytes_) {
-        return bytes_ ? cudaMemcpy(dst, src, bytes_, cudaMemcpyHostToDevice) : cudaSuccess;
+        return bytes_ ? cudaMemcpyAsync(dst, src, bytes_, cudaMemcpyHostToDevice, ust) : cudaSuccess;
     };
-    cudaError_t e = cudaSuccess;
     e = e ? e : up(rowptr, h_rowptr, (n + 1) * 4);
     e = e ? e : up(colidx, h_colidx, nnz * 4);
     e = e ? e : up(perm, an.perm.data(), n * 4);
@@ -1216,7 +1227,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     e = e ? e : up(tunit, tp.unit.data(), tp.unit.size() * sizeof(FrontTile));
     e = e ? e : up(tunit_fused, tp.unit_fused.data(), tp.unit_fused.size() * sizeof(FrontTile));
     e = e ? e : up(tinv, tp.inv.data(), tp.inv.size() * 4);
-    e = e ? e : cudaMemset(c->stall, 0, 2 * sizeof(int));
+    e = e ? e : cudaMemsetAsync(c->stall, 0, 2 * sizeof(int), ust);
     {
         // per step row i: contribution-vector offsets rel_ptr[f] + t of every front f whose
         // contribution row t is i, in increasing order (the gather order of the Jacobi sweeps)
@@ -1234,7 +1245,8 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
         e = e ? e : up(c->jl_ptr, jp.data(), (n + 1) * 4);
         e = e ? e : up(c->jl_idx, ji.data(), ji.size() * 4);
     }
-    e = e ? e : cudaMemset(c->stat, 0, sizeof(DevStat) * B);
+    e = e ? e : cudaMemsetAsync(c->stat, 0, sizeof(DevStat) * B, ust);
+    e = e ? e : cudaStreamSynchronize(ust);
     c->omega_pin = c->pin + 4 * (kMaxRestart + 2) + 16;
     c->infos.assign(B, kkt_info{});
     if (e != cudaSuccess) { kkt_destroy(c); return KKT_E_CUDA; }
@@ -1516,6 +1528,7 @@ kkt_status kkt_debug_stall(kkt_ctx* c)
     const int req[2] = {1, 0};
     KKT_CUDA(cudaDeviceSynchronize());
     KKT_CUDA(cudaMemcpy(c->stall, req, sizeof(req), cudaMemcpyHostToDevice));
+    KKT_CUDA(cudaDeviceSynchronize());                    // landed before any later launch, on any stream
     return KKT_OK;
 }
 

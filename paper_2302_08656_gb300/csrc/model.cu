@@ -260,8 +260,14 @@ kkt_status kkt_model_create(int32_t n_bus, int32_t n_branch, int32_t n_gen, cons
         m->d_b = (double*)p; p += sz[7];
         m->d_twoc2 = (double*)p; p += sz[8];
         m->d_terms = (double*)p;
-        cudaError_t e = cudaSuccess;
-        auto up = [&](void* d, const void* h, size_t b) { if (e == cudaSuccess && b) e = cudaMemcpy(d, h, b, cudaMemcpyHostToDevice); };
+        // through a private non-blocking stream, waited for before returning (a
+        // plain cudaMemcpy from pageable memory may return before the device
+        // holds the data, unordered with the caller's non-blocking streams)
+        cudaStream_t ust = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&ust, cudaStreamNonBlocking);
+        auto up = [&](void* d, const void* h, size_t b) {
+            if (e == cudaSuccess && b) e = cudaMemcpyAsync(d, h, b, cudaMemcpyHostToDevice, ust);
+        };
         up(m->d_f, h_from, 4 * (size_t)L);
         up(m->d_t, h_to, 4 * (size_t)L);
         up(m->d_tptr, tptr.data(), 4 * tptr.size());
@@ -271,6 +277,8 @@ kkt_status kkt_model_create(int32_t n_bus, int32_t n_branch, int32_t n_gen, cons
         up(m->d_g, g.data(), 8 * (size_t)L);
         up(m->d_b, bb.data(), 8 * (size_t)L);
         up(m->d_twoc2, twoc2.data(), 8 * (size_t)G);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ust);
+        if (ust) cudaStreamDestroy(ust);
         if (e != cudaSuccess) {
             kkt_model_destroy(m);
             return KKT_E_CUDA;
