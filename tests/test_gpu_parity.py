@@ -111,6 +111,44 @@ def test_ruiz_scaling_is_bitwise_equal(grid200):
     s.close()
 
 
+def test_ruiz_scaling_bitwise_over_wide_magnitudes(grid200):
+    """Symmetric row/column factors 10^U(-75, 75) spread |k| over ~300 decades:
+    many iterations change d (all after the first run on exponent keys) and the
+    result still equals the oracle's bit for bit."""
+    pat = grid200
+    rng = np.random.default_rng(11)
+    sc = 10.0 ** rng.uniform(-75, 75, size=pat.n)
+    rows = np.repeat(np.arange(pat.n), np.diff(pat.rowptr))
+    v = pat.values(pat.point(1, 2, 1e-3)) * sc[rows] * sc[pat.colidx]
+    s = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal)
+    s.refactor(_t(v))
+    torch.cuda.synchronize()
+    d_ora, it = O.ruiz(pat.rowptr, pat.colidx, v, 10)
+    assert it >= 4
+    assert np.array_equal(s.scaling(), d_ora)
+    s.close()
+
+
+def test_ruiz_scaling_bitwise_with_a_subnormal_entry(grid200):
+    """A subnormal entry (in a row whose maximum is a normal entry) sends every
+    iteration down the by-values path; d still equals the oracle's."""
+    pat = grid200
+    v = pat.values(pat.point(1, 1, 1e-2)).copy()
+    i = 7
+    lo, hi = pat.rowptr[i], pat.rowptr[i + 1]
+    q = lo + int(np.argmin(np.abs(v[lo:hi])))                  # not the row maximum
+    j = pat.colidx[q]
+    v[q] = 1e-310
+    qs = pat.rowptr[j] + int(np.searchsorted(pat.colidx[pat.rowptr[j]:pat.rowptr[j + 1]], i))
+    v[qs] = 1e-310                                              # keep K symmetric
+    s = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal)
+    s.refactor(_t(v))
+    torch.cuda.synchronize()
+    d_ora, _ = O.ruiz(pat.rowptr, pat.colidx, v, 10)
+    assert np.array_equal(s.scaling(), d_ora)
+    s.close()
+
+
 def _parity_case(pat, seed, steps, precision="fp64", point_kw=None, clip_sigma=None):
     v0 = pat.values(pat.point(seed, 0, 1e-1, **(point_kw or {})))
     an = O.analyze(pat.rowptr, pat.colidx, v0)
