@@ -136,8 +136,6 @@ struct kkt_ctx {
 
 namespace {
 
-kkt_status cuda_status(cudaError_t e) { return e == cudaSuccess ? KKT_OK : KKT_E_CUDA; }
-
 #define KKT_CUDA(call)                                      \
     do {                                                    \
         cudaError_t e_ = (call);                            \
@@ -400,9 +398,6 @@ kkt_status capture(kkt_ctx* c, cudaGraphExec_t* exec, long long* kernels, F&& bo
     c->launches = before;
     return KKT_OK;
 }
-
-template <typename T>
-kkt_status fwd_levels(kkt_ctx* c, const DevNum<T>& nm, int B, cudaStream_t st);
 
 // fused: the forward substitution of the right-hand side staged in nm.vec
 // rides along (warp classes of the level-launched part inside their
