@@ -287,7 +287,8 @@ cudaError_t tree_grid(int kind, size_t smem, int* grid);   // kind 0 factor, 1 f
 // block then holds batch * nq factor counters followed by batch * nq forward counters)
 template <typename T>
 cudaError_t launch_tree_factor(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
-                               int* stall, long long spin_limit, int grid, size_t smem, int fused, cudaStream_t st);
+                               int* stall, long long spin_limit, int grid, size_t smem, int fused, int u0, int nu,
+                               int tick, cudaStream_t st);
 template <typename T>
 cudaError_t launch_tree_fwd(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
                             long long spin_limit, int grid, size_t smem, cudaStream_t st);

@@ -86,6 +86,11 @@ struct kkt_ctx {
     int64_t tree_bytes = 0;
     size_t tf_smem = 0, tfw_smem = 0, tbw_smem = 0;
     int tf_grid = 0, tfw_grid = 0, tbw_grid = 0;
+    // refactorization of the tree part in two launches: the wide lower levels
+    // with tf_grid CTAs, then the narrow top levels (at most one unit per SM
+    // per level) with one CTA per SM, so no unit there shares an SM's FP64
+    // pipe; split points in the plain and the fused unit orders
+    int tf_split = 0, tf_split_fused = 0, tf_grid_narrow = 0;
     int* ctr_fac = nullptr;          // counter block of the refactorization kernel
     int* ctr_sol = nullptr;          // counter block of the two solve kernels
     int* stall = nullptr;            // failure-injection hook (two ints)
@@ -448,9 +453,18 @@ kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused 
         }
     }
     if (nq > 0) {
-        Launch L(c, st, KK_TREE_FACTOR, 1);
-        KKT_CUDA(launch_tree_factor<T>(c->sched, c->tsched, nm, B, c->ctr_fac, c->stall, c->opt.spin_limit,
-                                       c->tf_grid, c->tf_smem, fused ? 1 : 0, st));
+        const int nu = fused ? c->tsched.nunits_fused : c->tsched.nunits;
+        const int us = fused ? c->tf_split_fused : c->tf_split;
+        if (us > 0) {
+            Launch L(c, st, KK_TREE_FACTOR, 1);
+            KKT_CUDA(launch_tree_factor<T>(c->sched, c->tsched, nm, B, c->ctr_fac, c->stall, c->opt.spin_limit,
+                                           c->tf_grid, c->tf_smem, fused ? 1 : 0, 0, us, 0, st));
+        }
+        if (us < nu) {
+            Launch L(c, st, KK_TREE_FACTOR, 1);
+            KKT_CUDA(launch_tree_factor<T>(c->sched, c->tsched, nm, B, c->ctr_fac, c->stall, c->opt.spin_limit,
+                                           c->tf_grid_narrow, c->tf_smem, fused ? 1 : 0, us, nu - us, 3, st));
+        }
     }
     return KKT_OK;
 }
@@ -1264,7 +1278,26 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
         e = f32 ? tree_grid<float>(0, c->tf_smem, &c->tf_grid) : tree_grid<double>(0, c->tf_smem, &c->tf_grid);
         e = e ? e : f32 ? tree_grid<float>(1, c->tfw_smem, &c->tfw_grid) : tree_grid<double>(1, c->tfw_smem, &c->tfw_grid);
         e = e ? e : f32 ? tree_grid<float>(2, c->tbw_smem, &c->tbw_grid) : tree_grid<double>(2, c->tbw_smem, &c->tbw_grid);
+        int dev = 0, nsm = 0;
+        e = e ? e : cudaGetDevice(&dev);
+        e = e ? e : cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) { kkt_destroy(c); return KKT_E_CUDA; }
+        // narrow top: the lowest level from which every level has at most one
+        // unit (times the batch) per SM; tree index is level-major from tp.split
+        c->tf_grid_narrow = nsm;
+        std::vector<int> lev(nq), per_level(an.n_levels, 0);
+        for (int l = tp.split, q = 0; l < an.n_levels; ++l)
+            for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) lev[q++] = l;
+        for (const FrontTile& u : tp.unit) per_level[lev[u.front]]++;
+        int narrow = an.n_levels;
+        for (int l = an.n_levels - 1; l >= tp.split && (int64_t)per_level[l] * B <= nsm; --l) narrow = l;
+        auto first_at = [&](const std::vector<FrontTile>& order) {   // both orders ascend by level
+            int i = 0;
+            while (i < (int)order.size() && lev[order[i].front] < narrow) ++i;
+            return i;
+        };
+        c->tf_split = first_at(tp.unit);
+        c->tf_split_fused = first_at(tp.unit_fused);
     }
     double eps = c->opt.static_pivot_eps > 0 ? c->opt.static_pivot_eps
                                              : (c->opt.precision == KKT_FP32_IR ? 1e-7 : 1e-14);

@@ -126,14 +126,16 @@ __device__ bool fwd_unit(const DevSched& s, const TreeSched& ts, const DevNum<T>
 // Threads form a 32 x 8 grid (lane -> row, warp -> column).
 template <typename T>
 __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
-                                                          int* stall, long long limit, int fused)
+                                                          int* stall, long long limit, int fused, int u0, int nu,
+                                                          int tick)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ TreeFront d;
     __shared__ int s_t, s_ok;
     __shared__ T s_rinv[64];                                   // reciprocal of every pivot (w <= 64)
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    const int total = (fused ? ts.nunits_fused : ts.nunits) * B;
+    // units u0 .. u0 + nu - 1 of the chosen order, tickets from counter ctr[tick]
+    const int total = nu * B;
     const FrontTile* units = fused ? ts.unit_fused : ts.unit;
     int* done = ctr + kCtrHead;
     int* fwd_done = done + (int64_t)B * ts.nq;                     // fused mode: forward-unit counters
@@ -144,10 +146,10 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
     int* smap = reinterpret_cast<int*>(smraw + off_map);           // child c: rows at 2cW, columns at (2c+1)W
     TreeKid* kids = reinterpret_cast<TreeKid*>(smraw + ts.kid_off);
     for (;;) {
-        const int t = next_ticket(ctr, ctr + 1, total, &s_t);
+        const int t = next_ticket(ctr + tick, ctr + 1, total, &s_t);
         if (t >= total) break;
-        const int u = t / B, b = t - u * B;
-        const FrontTile ut = units[u];
+        const int ul = t / B, b = t - ul * B;
+        const FrontTile ut = units[u0 + ul];
         const int q = ut.front;
         copy_words(&d, ts.fr + q, 1, tid, 256);
         __syncthreads();
@@ -719,13 +721,16 @@ cudaError_t tree_grid(int kind, size_t smem, int* grid)
 
 template <typename T>
 cudaError_t launch_tree_factor(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
-                               int* stall, long long spin_limit, int grid, size_t smem, int fused, cudaStream_t st)
+                               int* stall, long long spin_limit, int grid, size_t smem, int fused, int u0, int nu,
+                               int tick, cudaStream_t st)
 {
-    const int g = std::min<long long>(grid, (long long)(fused ? t.nunits_fused : t.nunits) * batch);
+    const int g = std::min<long long>(grid, (long long)nu * batch);
     if (g <= 0) return cudaSuccess;
     if ((fused ? t.unit_fused : t.unit) == nullptr || t.fr == nullptr || t.kid == nullptr)
         return cudaErrorInvalidValue;                         // schedule not uploaded: never launch on it
-    tree_factor_kernel<T><<<g, 256, smem, st>>>(s, t, nm, batch, ctr, stall, spin_limit, fused);
+    if (u0 < 0 || nu < 0 || u0 + nu > (fused ? t.nunits_fused : t.nunits) || (tick != 0 && tick != 3))
+        return cudaErrorInvalidValue;
+    tree_factor_kernel<T><<<g, 256, smem, st>>>(s, t, nm, batch, ctr, stall, spin_limit, fused, u0, nu, tick);
     return cudaGetLastError();
 }
 
@@ -754,7 +759,7 @@ cudaError_t launch_tree_bwd(const DevSched& s, const TreeSched& t, const DevNum<
 #define KKT_TREE_INST(T)                                                                                          \
     template cudaError_t tree_grid<T>(int, size_t, int*);                                                          \
     template cudaError_t launch_tree_factor<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,     \
-                                               int*, long long, int, size_t, int, cudaStream_t);                   \
+                                               int*, long long, int, size_t, int, int, int, int, cudaStream_t);    \
     template cudaError_t launch_tree_fwd<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,        \
                                             long long, int, size_t, cudaStream_t);                                 \
     template cudaError_t launch_tree_bwd<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,        \
