@@ -169,12 +169,11 @@ def algorithmic_bytes(plan, n, nnz, wbytes):
     }
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# DRAM bytes (read + write) of the dominant kernel per unit of the roofline
+# (for tree_factor_kernel: its launches of one refactorization) from one ncu
 # capture of the same command (profiles/), keyed by (kernel, workload,
 # precision, tree levels); an entry is removed whenever the kernel changes.
-MEASURED_TRAFFIC = {
-    ("tree_factor_kernel", "northeast25k", "fp64", 58): 23325824 + 189952,
-}
+MEASURED_TRAFFIC = {}
 
 PHASE_OF = {
     "front_warp_kernel": "refactor", "front_leaf_kernel": "refactor", "front_cta_kernel": "refactor",
@@ -362,8 +361,10 @@ def run_native(args):
     if dom:
         ph = PHASE_OF.get(dom, "refactor")
         if dom == "tree_factor_kernel":
-            # the kernel's own algorithmic bytes: original entries, panels, contribution blocks
-            n_units = stats[dom][0]
+            # the kernel's own algorithmic bytes (original entries, panels,
+            # contribution blocks) per refactorization; the tree part runs as
+            # one or two launches of it (wide levels, then the narrow top)
+            n_units = nprof
             bytes_unit = plan["tree_bytes"]
             kms = stats[dom][1] / max(1, n_units)
         else:
@@ -376,8 +377,8 @@ def run_native(args):
         traffic = MEASURED_TRAFFIC.get(key)
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                     "frac": achieved / hbm, "traffic": traffic, "kernel": dom, "peak_source": peak_src,
-                    "algorithmic_bytes_per_launch": bytes_unit, "launches_profiled": n_units,
-                    "ms_per_launch": kms,
+                    "algorithmic_bytes_per_unit": bytes_unit, "units_profiled": n_units,
+                    "ms_per_unit": kms, "launches_per_unit": stats[dom][0] / max(1, n_units),
                     "refactor_phase": {"algorithmic_bytes": ab["refactor"], "ms": phase_ms.get("refactor", 0.0) / nprof,
                                        "achieved_gbs": ab["refactor"] / (phase_ms.get("refactor", 1e-9) / nprof / 1000.0) / 1e9}}
 
