@@ -255,8 +255,64 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
             }
         __syncthreads();
         // ---- w pivot steps of right-looking elimination without pivoting, one
-        // barrier per pivot, one reciprocal per pivot (l_ip = m_ip * (1 / u_pp))
-        if (Fr <= 32 && Fc <= 32) {
+        // reciprocal per pivot (l_ip = m_ip * (1 / u_pp))
+        if (sizeof(T) == 4 && Fr <= 32 && Fc <= 32) {
+            // single precision, blocked by kPanel pivots: warp 0 factors the
+            // panel (pivot columns p0 .. p0 + pk - 1, lane -> row p0 + lane) in
+            // registers without a CTA barrier; then every warp applies the
+            // panel to its trailing columns (lane -> row, one shuffle per pivot
+            // for the row's U entry). Each entry still receives its updates in
+            // pivot order with the same roundings as the one-pivot schedule.
+            // Two barriers per kPanel pivots instead of one per pivot.
+            constexpr int kPanel = 8;
+            for (int p0 = 0; p0 < w; p0 += kPanel) {
+                const int pk = min(kPanel, w - p0);
+                const int row = p0 + tx;
+                if (ty == 0) {
+                    T a[kPanel];
+#pragma unroll
+                    for (int k = 0; k < kPanel; ++k) a[k] = (k < pk && row < Fr) ? M[row + (p0 + k) * Fr] : T(0);
+#pragma unroll
+                    for (int k = 0; k < kPanel; ++k) {
+                        if (k < pk) {                                  // warp-uniform
+                            T r = T(0);
+                            if (tx == k) {
+                                a[k] = static_pivot(a[k], floorT, nm.stat, lead);
+                                r = pivot_rcp(a[k]);
+                            }
+                            r = __shfl_sync(0xffffffffu, r, k);
+                            if (tx > k) a[k] *= r;                     // l below the pivot
+#pragma unroll
+                            for (int kk = k + 1; kk < kPanel; ++kk) {
+                                const T u = __shfl_sync(0xffffffffu, a[kk], k);
+                                if (tx > k && kk < pk) a[kk] -= a[k] * u;
+                            }
+                        }
+                    }
+                    if (row < Fr)
+#pragma unroll
+                        for (int k = 0; k < kPanel; ++k)
+                            if (k < pk) M[row + (p0 + k) * Fr] = a[k];
+                }
+                __syncthreads();
+                // trailing columns j >= p0 + pk: warp ty takes j = p0 + pk + ty + 8 c
+                T lp[kPanel];
+#pragma unroll
+                for (int k = 0; k < kPanel; ++k) lp[k] = (k < pk && row < Fr) ? M[row + (p0 + k) * Fr] : T(0);
+                for (int j = p0 + pk + ty; j < Fc; j += 8) {
+                    T v = row < Fr ? M[row + j * Fr] : T(0);
+#pragma unroll
+                    for (int k = 0; k < kPanel; ++k) {
+                        if (k < pk) {                                  // warp-uniform
+                            const T u = __shfl_sync(0xffffffffu, v, k);  // row p0 + k: final at step k
+                            if (tx > k) v -= lp[k] * u;
+                        }
+                    }
+                    if (row < Fr) M[row + j * Fr] = v;
+                }
+                __syncthreads();
+            }
+        } else if (Fr <= 32 && Fc <= 32) {
             // mini fronts of at most 32 x 32 (always when w <= 16). GB300 runs
             // one FP64 warp instruction per ~64 cycles per sub-partition, masked
             // lanes included, so the elimination is bound by the FP64
