@@ -19,7 +19,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import paper_2302_08656_gb300 as K
-from kktgen import KKTPattern, make_grid
+from kktgen import KKTPattern, make_grid, WORKLOADS
 
 KKT_E_TIMEOUT = 7
 
@@ -129,3 +129,61 @@ def test_fused_refactor_refine_equals_separate_calls(precision, count, tmf):
             assert p.backward_err == q.backward_err and p.iters == q.iters and p.status == q.status == 0
     a.close()
     f.close()
+
+
+@pytest.fixture(scope="module")
+def grid8k():
+    return KKTPattern(make_grid(5, 8000, 10240, 1600))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_warp_class_staged_children_bitwise(grid8k, precision):
+    """8,000-bus grid: levels 1-2 (1,583 and 856 fronts) are factored a warp per
+    front with the children's blocks staged by cp.async, 67 of those fronts in
+    more than one staging chunk; the same bits as the all-tree schedule."""
+    pat = grid8k
+    v = pat.values(pat.point(8, 2, 1e-4))
+    b = pat.rhs(8, 2)
+    runs = [_run(pat, v, b, precision, t) for t in (0, 10 ** 9)]
+    for plan, f, x, info in runs:
+        assert info.status == 0
+    for a, c in zip(runs[0][1], runs[1][1]):
+        assert np.array_equal(a, c)
+    assert np.array_equal(runs[0][2], runs[1][2])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused_forward_in_the_warp_class_equals_separate(grid8k, precision):
+    """kkt_refactor_refine on the 8,000-bus grid with every level launched: the
+    forward step runs inside the leaf and warp kernels (children's vectors staged
+    with their blocks) and gives the bits of kkt_refactor + kkt_refine."""
+    dev = _dev()
+    pat = grid8k
+    v = torch.from_numpy(pat.values(pat.point(9, 3, 1e-5))).to(dev)
+    b = torch.from_numpy(pat.rhs(9, 3)).to(dev)
+    a = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=precision, tree_min_fronts=0)
+    f = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=precision, tree_min_fronts=0)
+    a.refactor(v)
+    xa, ia = a.refine(b, tol=1e-10)
+    xf, if_ = f.refactor_refine(v, b, tol=1e-10)
+    assert torch.equal(xa, xf)
+    assert ia.backward_err == if_.backward_err and ia.status == if_.status == 0
+    a.close()
+    f.close()
+
+
+def test_warp_class_child_past_the_staging_area_bitwise():
+    """The 70,000-bus system with every level launched: on levels 5-7 some warp-class
+    fronts have a child whose block exceeds the staging area and is read from
+    global memory; factors and solution equal the all-tree schedule's."""
+    w = WORKLOADS["eastern70k"]
+    pat = KKTPattern(make_grid(2, w["n_bus"], w["n_branch"], w["n_gen"]))
+    v = pat.values(pat.point(2, 1, 1e-3))
+    b = pat.rhs(2, 1)
+    runs = [_run(pat, v, b, "fp64", t) for t in (0, 10 ** 9)]
+    for plan, f, x, info in runs:
+        assert info.status == 0
+    assert runs[0][0]["tree_levels"] == 0
+    for a, c in zip(runs[0][1], runs[1][1]):
+        assert np.array_equal(a, c)
+    assert np.array_equal(runs[0][2], runs[1][2])
