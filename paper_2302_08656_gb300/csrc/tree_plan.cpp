@@ -22,17 +22,36 @@ void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp)
             int s = an.level_fronts[t];
             if (an.child_ptr[s + 1] - an.child_ptr[s] > kTreeMaxKids) split = l + 1;
         }
+    // tree index: level by level; within a level, fronts ordered by the last
+    // tree index among their children (stable), so the units that become
+    // ready first take the first tickets of their level
     std::vector<int> tq(an.ns, -1);
+    std::vector<std::vector<int>> order(an.n_levels);
     int nq = 0;
-    for (int l = split; l < an.n_levels; ++l)
-        for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) tq[an.level_fronts[t]] = nq++;
+    for (int l = split; l < an.n_levels; ++l) {
+        std::vector<int>& ord = order[l];
+        ord.assign(an.level_fronts.begin() + an.level_ptr[l], an.level_fronts.begin() + an.level_ptr[l + 1]);
+        if (l > split) {
+            std::vector<std::pair<int, int>> key;                 // (last child index, position)
+            for (int t = 0; t < (int)ord.size(); ++t) {
+                int last = -1;
+                for (int c = an.child_ptr[ord[t]]; c < an.child_ptr[ord[t] + 1]; ++c)
+                    last = std::max(last, tq[an.child_list[c]]);
+                key.emplace_back(last, t);
+            }
+            std::sort(key.begin(), key.end());
+            std::vector<int> sorted;
+            for (const auto& k : key) sorted.push_back(ord[k.second]);
+            ord.swap(sorted);
+        }
+        for (int s : ord) tq[s] = nq++;
+    }
     tp.split = split;
     tp.fr.resize(nq);
     TreeSched& ts = tp.ts;
     ts.nq = nq;
     for (int l = split; l < an.n_levels; ++l)
-        for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) {
-            const int s = an.level_fronts[t];
+        for (int s : order[l]) {
             const int q = tq[s];
             TreeFront& d = tp.fr[q];
             d.f = s;
@@ -88,7 +107,7 @@ void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp)
     ts.nunits = (int)tp.unit.size();
     // fused order: level by level, the factorization units of the level, then its forward units
     for (int l = split, u = 0; l < an.n_levels; ++l) {
-        const int q0 = tq[an.level_fronts[an.level_ptr[l]]];
+        const int q0 = tq[order[l].front()];
         const int q1 = q0 + (an.level_ptr[l + 1] - an.level_ptr[l]);
         while (u < (int)tp.unit.size() && tp.unit[u].front < q1) tp.unit_fused.push_back(tp.unit[u++]);
         for (int q = q0; q < q1; ++q) tp.unit_fused.push_back(FrontTile{q, -1, 0});
