@@ -154,7 +154,10 @@ kkt_status kkt_plan(int32_t n, const int32_t *h_rowptr, const int32_t *h_colidx,
  * and copied; h_vals is not needed by the static-pivot analysis and may be
  * NULL. Allocates every device buffer the context will use, on the current
  * device, and uploads the schedule. On success *out receives a context
- * that kkt_destroy frees. Synchronous.
+ * that kkt_destroy frees. Synchronous: the uploads go through the context's
+ * own non-blocking stream, which is waited for before the call returns, so
+ * the first refactorization may be issued on any stream of the caller
+ * (including a non-blocking one) without further synchronization.
  * Errors: KKT_E_ARG, KKT_E_STRUCT, KKT_E_NOMEM, KKT_E_CUDA. */
 kkt_status kkt_analyze(int32_t n, int32_t n_primal, const int32_t *h_rowptr,
                        const int32_t *h_colidx, const double *h_vals,
