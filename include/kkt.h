@@ -309,7 +309,8 @@ enum { KKT_MODEL_FLOW_LIMITS = 1,   /* include the line-flow limit rows */
  * h_gen_bus and cost coefficient h_c2. All host arrays are read and copied.
  * flags: KKT_MODEL_* bits. Unless KKT_MODEL_HOST_ONLY, allocates the model's
  * device memory on the current device (line data, summation lists, one
- * scratch array of 40 doubles per line).
+ * scratch array of 40 doubles per line) and uploads the line data through a
+ * private stream it waits for: synchronous, like kkt_analyze.
  * Errors: KKT_E_ARG (bad index, size or flag), KKT_E_NOMEM, KKT_E_CUDA. */
 kkt_status kkt_model_create(int32_t n_bus, int32_t n_branch, int32_t n_gen, const int32_t *h_from,
                             const int32_t *h_to, const double *h_r, const double *h_x,
