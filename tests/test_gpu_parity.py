@@ -340,3 +340,25 @@ def test_host_step_equals_device_path(grid200):
     assert np.array_equal(xh, xd.cpu().numpy())
     assert O.backward_error(pat.rowptr, pat.colidx, v, xh, b) <= 1e-12
     s.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_eastern70k_backward_error_through_the_timed_call(precision):
+    """Full size of the 70,000-bus workload through kkt_refactor_refine (the call
+    the benchmark times): the oracle's normwise backward error of the returned
+    x, computed on the host from K and b alone, meets the 1e-10 tolerance, and
+    the library's own figure (a different summation order of the residual)
+    meets it too."""
+    from kktgen import WORKLOADS
+    w = WORKLOADS["eastern70k"]
+    pat = KKTPattern(make_grid(3, w["n_bus"], w["n_branch"], w["n_gen"]))
+    s = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=precision)
+    for k, mu in ((0, 1e-1), (1, 1e-9)):
+        v = pat.values(pat.point(3, k, mu))
+        b = pat.rhs(3, k)
+        x, info = s.refactor_refine(_t(v), _t(b), tol=1e-10)
+        om = O.backward_error(pat.rowptr, pat.colidx, v, x.cpu().numpy(), b)
+        assert info.status == 0
+        assert om <= 1e-10, om
+        assert info.backward_err <= 1e-10, info.backward_err
+    s.close()
