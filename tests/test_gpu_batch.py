@@ -62,3 +62,31 @@ def test_concurrent_contexts_equal_sequential():
         assert np.array_equal(x.cpu().numpy(), xs.cpu().numpy())
     for c in ctxs:
         c.close()
+
+
+def test_full_batch_64x2k_equals_single_instances():
+    """The 64 x 2,000-bus batch of the benchmark (FP32 factors + FP64 refinement;
+    with 64 instances the tree threshold per instance drops to 38 fronts, a
+    different schedule from a single context's): every instance meets the
+    tolerance, and sampled instances equal single-context solves bit for bit
+    and meet it by the oracle's own backward error."""
+    dev = _dev()
+    pat = KKTPattern(make_grid(8, 2000, 2560, 400))
+    B, tol = 64, 1e-10
+    vals = [pat.values(pat.point(200 + i, i % 7, 10.0 ** -(1 + i % 7))) for i in range(B)]
+    rhs = [pat.rhs(200 + i, i % 7) for i in range(B)]
+    sb = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, count=B, precision="fp32")
+    vd = torch.from_numpy(np.concatenate(vals)).to(dev)
+    bd = torch.from_numpy(np.concatenate(rhs)).to(dev)
+    sb.refactor(vd)
+    xb, infos = sb.refine(bd, tol=tol)
+    xb = xb.cpu().numpy().reshape(B, pat.n)
+    assert all(i.status == 0 and i.backward_err <= tol for i in infos)
+    single = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision="fp32")
+    for i in (0, 17, 38, 63):
+        single.refactor(torch.from_numpy(vals[i]).to(dev))
+        xs, info = single.refine(torch.from_numpy(rhs[i]).to(dev), tol=tol)
+        assert np.array_equal(xb[i], xs.cpu().numpy()), i
+        assert O.backward_error(pat.rowptr, pat.colidx, vals[i], xb[i], rhs[i]) <= tol
+    sb.close()
+    single.close()
