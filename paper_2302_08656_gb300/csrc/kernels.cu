@@ -267,8 +267,9 @@ __device__ __forceinline__ void assemble_original(const DevSched& s, const DevNu
 
 // Loops over the entries of dense blocks use fixed two-dimensional thread
 // layouts (rows across lanes, columns across lane groups or warps), so no
-// thread divides by a run-time extent: an integer division costs tens of
-// instructions, more than the arithmetic it would index.
+// thread divides by a run-time extent inside a loop: an integer division
+// costs tens of instructions, more than the arithmetic it would index (the
+// child-block adds of the warp kernel divide once per child and then step).
 
 // Fronts with F <= 32: one warp per front, the whole front in shared memory.
 // Lanes form an 8 x 4 grid over (row, column) of every block loop.
