@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <numeric>
+#include <queue>
 #include <set>
 #include <utility>
 
@@ -15,7 +16,10 @@ namespace kktgb {
 // (cliques kept implicitly as the list of their variables); an element that
 // is adjacent to a newly eliminated pivot is absorbed into it. The degree of a
 // variable is its exact external degree |A_i U (union of L_e, e in E_i)| - 1,
-// recomputed for the variables of each new element.
+// recomputed for the variables of each new element. The next pivot is the
+// variable of least degree, the lowest index among equals: a binary heap of
+// (degree, index) pairs, an entry skipped when its variable is gone or its
+// degree has changed since it was pushed.
 void min_degree_quotient(int n, const int* rowptr, const int* colidx, std::vector<int>& order)
 {
     std::vector<std::vector<int>> av(n), ae(n), le(n);
@@ -26,15 +30,17 @@ void min_degree_quotient(int n, const int* rowptr, const int* colidx, std::vecto
             if (colidx[p] != i) av[i].push_back(colidx[p]);
         deg[i] = (int)av[i].size();
     }
-    std::set<std::pair<int, int>> pq;
-    for (int i = 0; i < n; ++i) pq.insert({deg[i], i});
+    std::priority_queue<std::pair<int, int>, std::vector<std::pair<int, int>>, std::greater<std::pair<int, int>>> pq;
+    for (int i = 0; i < n; ++i) pq.push({deg[i], i});
     order.clear();
     order.reserve(n);
     int stamp = 0;
     std::vector<int> lp;
     while (!pq.empty()) {
-        int p = pq.begin()->second;
-        pq.erase(pq.begin());
+        const std::pair<int, int> top = pq.top();
+        pq.pop();
+        const int p = top.second;
+        if (state[p] != 0 || deg[p] != top.first) continue;          // stale entry
         order.push_back(p);
         // L_p = (A_p U union of absorbed elements' variables) \ {p}
         ++stamp;
@@ -74,9 +80,10 @@ void min_degree_quotient(int n, const int* rowptr, const int* colidx, std::vecto
             for (int v : av[i]) if (state[v] == 0 && mark[v] != st2) { mark[v] = st2; ++d; }
             for (int e : ae[i])
                 for (int v : le[e]) if (state[v] == 0 && mark[v] != st2) { mark[v] = st2; ++d; }
-            pq.erase({deg[i], i});
-            deg[i] = d;
-            pq.insert({d, i});
+            if (d != deg[i]) {
+                deg[i] = d;
+                pq.push({d, i});
+            }
         }
         // restore the marks of L_p for the next pivot (stamps only grow)
     }
