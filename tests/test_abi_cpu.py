@@ -53,9 +53,20 @@ def test_plan_matches_oracle_symbolic_counts():
     assert info["nnz_lu"] == f.Lx.size + f.Ux.size
     assert info["n"] == pat.n and info["nnz"] == pat.nnz
     assert info["stored_factor"] >= info["nnz_lu"]
-    # the library's own ordering is a different heuristic but of the same quality class
+
+
+@pytest.mark.parametrize("B,L,G,seed", [(30, 40, 6, 3), (200, 300, 40, 1), (2000, 2560, 400, 4)])
+def test_own_ordering_equals_the_oracle_minimum_degree(B, L, G, seed):
+    """The library's minimum degree (quotient graph, binary heap) and the
+    oracle's (explicit elimination graph, degree buckets) are independent
+    implementations of one rule (exact degree, lowest index first): the plan
+    of the library's own ordering is the plan of the oracle's order."""
+    pat = KKTPattern(make_grid(seed, B, L, G))
+    q = O.min_degree(pat.rowptr, pat.colidx)
     own = K.plan(pat.rowptr, pat.colidx)
-    assert own["nnz_lu"] <= 1.5 * info["nnz_lu"]
+    given = K.plan(pat.rowptr, pat.colidx, user_perm=q)
+    for key in ("nnz_lu", "stored_factor", "n_fronts", "n_levels", "max_front", "flops"):
+        assert own[key] == given[key], key
 
 
 @pytest.mark.parametrize("B", [2, 3, 50])
