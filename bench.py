@@ -208,10 +208,12 @@ PHASE_OF = {
 
 def cpu_run(pat, vals, rhs, tol, budget_s, max_steps):
     """The oracle as it stands, single thread: analysis untimed, then per step
-    Ruiz + LU with frozen pivots + FGMRES to tol, until the budget is used."""
+    Ruiz + LU with frozen pivots + FGMRES to tol, until the budget is used.
+    Returns the step times, the backward errors and the solutions (inputs
+    0, 1, ... in order)."""
     import oracle as O
     an = O.analyze(pat.rowptr, pat.colidx, vals[0])
-    times, oms = [], []
+    times, oms, xs = [], [], []
     t_all = time.perf_counter()
     for i in range(min(max_steps, len(vals))):
         t0 = time.perf_counter()
@@ -219,9 +221,28 @@ def cpu_run(pat, vals, rhs, tol, budget_s, max_steps):
         x, it, om = O.fgmres(pat.rowptr, pat.colidx, vals[i], lu, d, rhs[i], 30, 10, tol)
         times.append(time.perf_counter() - t0)
         oms.append(om)
+        xs.append(x)
         if time.perf_counter() - t_all > budget_s and len(times) >= 2:
             break
-    return times, oms
+    return times, oms, xs
+
+
+def error_vs_oracle(x_oracle, results):
+    """Error of each GPU result against the oracle's FP64 solution of the same
+    system K_k x = b_k: |x - x_oracle|_inf / |x_oracle|_inf per input, for each
+    precision in `results` (name -> list of solutions, inputs 0, 1, ... in
+    order). Both sides stop at the same backward error, so the difference is
+    bounded by the condition number of K_k times that tolerance, not by it."""
+    out = {"inputs": len(x_oracle), "norm": "max|x - x_oracle| / max|x_oracle|"}
+    for name, xs in results.items():
+        if xs is None:
+            continue
+        errs = []
+        for a, o in zip(xs, x_oracle):
+            den = float(np.max(np.abs(o)))
+            errs.append(float(np.max(np.abs(np.asarray(a) - o))) / (den if den > 0 else 1.0))
+        out[name] = {"max": max(errs), "median": float(np.median(errs)), "per_result": errs}
+    return out
 
 
 def run_reference(args):
@@ -235,7 +256,7 @@ def run_reference(args):
     vals_p, rhs_p = inputs(pat, mus, args.seed, pool_size(args))
     vals = [vals_p[at(args, i)] for i in range(n_in)]
     rhs = [rhs_p[at(args, i)] for i in range(n_in)]
-    times, oms = cpu_run(pat, vals, rhs, args.tol, 1e9, n_in)
+    times, oms, _ = cpu_run(pat, vals, rhs, args.tol, 1e9, n_in)
     t = times[args.warmup:] if len(times) > args.warmup else times
     ms = 1000.0 * sum(t) / len(t)
     value = 1000.0 / ms
@@ -319,6 +340,8 @@ def run_native(args):
     sampler.start()
     ms, oms, iters, launches = timed_run(s64, args.precision)
     clocks = sampler.stop()
+    main_name = "fp64" if args.precision == "fp64" else "fp32_ir"
+    results = {main_name: [x.cpu().numpy() for x in xs]}     # one result per pool input, after the timed region
     total_ms = sum(ms)
     if world > 1:
         total_ms = reduce_max(total_ms, device=dev)
@@ -330,6 +353,7 @@ def run_native(args):
         oprec = "fp32" if args.precision == "fp64" else "fp64"
         s32 = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=oprec, **lib_opts)
         ms32, oms32, it32, _ = timed_run(s32, oprec)
+        results["fp32_ir" if oprec == "fp32" else "fp64"] = [x.cpu().numpy() for x in xs]
         other = {"precision": "fp32_ir" if oprec == "fp32" else "fp64", "value": 1000.0 * len(ms32) / sum(ms32),
                  "p50_ms": float(np.percentile(ms32, 50)), "p99_ms": float(np.percentile(ms32, 99)),
                  "omega_max": float(max(oms32)), "fgmres_iters_mean": float(np.mean(it32))}
@@ -404,12 +428,17 @@ def run_native(args):
                                        "achieved_gbs": ab["refactor"] / (phase_ms.get("refactor", 1e-9) / nprof / 1000.0) / 1e9}}
 
     cpu = None
+    accuracy = None
     if rank == 0 and not args.no_cpu_baseline:
-        times, coms = cpu_run(pat, vals_h, rhs_h, args.tol, args.cpu_seconds, n_in)
+        times, coms, xo = cpu_run(pat, vals_h, rhs_h, args.tol, args.cpu_seconds, n_in)
         cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "%d of the %s steps (oracle analysis untimed), single thread"
                          % (len(times), args.workload),
                "omega_max": float(max(coms))}
+        try:
+            accuracy = error_vs_oracle(xo, results)
+        except Exception as e:                     # reported in the line, never fatal to it
+            accuracy = {"error": repr(e)}
 
     if rank == 0:
         line = {
@@ -428,7 +457,7 @@ def run_native(args):
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(launches), "kernel_ms_per_step": {k: v[1] / nprof for k, v in stats.items()},
             "library_options": lib_opts, "converged_steps": int(sum(1 for o in oms if o <= args.tol)),
-            "comparison": other,
+            "comparison": other, "error_vs_oracle": accuracy,
         }
         print(json.dumps(line), flush=True)
     s64.close()
