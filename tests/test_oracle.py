@@ -381,3 +381,29 @@ def test_jacobi_precondition_pins():
     lu3, d3, _ = O.refactor(rp, ci, dv, an3)
     bb = np.array([1.0, 2.0, 3.0])
     assert np.allclose(O.jacobi_precondition(lu3.factors(), d3, bb, 1), bb / dv, rtol=1e-15)
+
+
+def test_solution_not_determined_at_fp64_on_the_literal_kkt(kkt200):
+    """With -dc = -1e-10 on every constraint row and more constraint rows than
+    primals (m = 2B + 2L > n = 2B + 2G), the null space of J^T is held by dc
+    alone: cond(K) is far beyond 1/eps_FP64. Two backward-stable FP64 solves
+    that differ only in the static-pivot threshold (1e-14 vs 1e-12 of max|DKD|)
+    both reach omega <= 1e-14, yet their solutions differ by more than 1 % of
+    max|x| in the dual block, whose entries reach ~|b| / dc. This is why the
+    parity gates are omega and the factor entries (running error bounds), and
+    why a result's difference from the oracle's x is stated, not gated."""
+    pat = kkt200
+    m = pat.n - pat.n_primal
+    assert m > pat.n_primal
+    v = pat.values(pat.point(1, 3, 1e-3))
+    b = pat.rhs(1, 3)
+    xs = []
+    for eps in (1e-14, 1e-12):
+        an = O.analyze(pat.rowptr, pat.colidx, v, pivot_eps=eps)
+        lu, d, _ = O.refactor(pat.rowptr, pat.colidx, v, an, pivot_eps=eps)
+        x, _, om = O.fgmres(pat.rowptr, pat.colidx, v, lu, d, b, 30, 10, 1e-14)
+        assert om <= 1e-14
+        xs.append(x)
+    y0, y1 = xs[0][pat.n_primal:], xs[1][pat.n_primal:]
+    assert np.abs(y0).max() > 1e8 * np.abs(b).max()
+    assert np.abs(y1 - y0).max() > 1e-2 * np.abs(y0).max()
