@@ -346,6 +346,18 @@ kkt_status kkt_model_destroy(kkt_model *m);
  * Errors: KKT_E_ARG, KKT_E_STATE (the context has no tree part), KKT_E_CUDA. */
 kkt_status kkt_debug_stall(kkt_ctx *ctx);
 
+/* Test hook for the pivot reciprocal (no counterpart in the paper): d_out[i] =
+ * the value every factorization and back-substitution kernel uses for 1 /
+ * d_in[i] (multiplying by it replaces the division by the pivot u_pp of Alg. 1's
+ * factorization and triangular solves). d_in, d_out: device arrays of n
+ * elements, FP64 for precision = KKT_FP64 and FP32 for KKT_FP32_IR; they may
+ * be the same array. Stated bound: within one unit in the last place of the
+ * correctly rounded 1 / d; the IEEE division itself for |d| outside
+ * [2^-1000, 2^1000] (FP32: [2^-100, 2^100]), zero, infinities and NaN.
+ * Asynchronous on `stream`. Errors: KKT_E_ARG (n < 0, a null pointer with n >
+ * 0, unknown precision, n beyond one launch), KKT_E_CUDA. */
+kkt_status kkt_debug_pivot_rcp(const void *d_in, void *d_out, int64_t n, int precision, void *stream);
+
 /* Profiling mode: when on, every launch group is bracketed by a pair of CUDA
  * events on its stream (adds a little host overhead). */
 kkt_status kkt_set_profiling(kkt_ctx *ctx, int on);

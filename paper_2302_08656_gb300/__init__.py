@@ -317,6 +317,18 @@ def backward_error_noalloc(rowptr, colidx, vals, x, rhs, r, omega, stream=None):
                                             _ptr(r), _ptr(omega), _stream(stream)), "kkt_backward_error_noalloc")
 
 
+def debug_pivot_rcp(d, out=None, stream=None):
+    """The pivot reciprocal the factorization and backward kernels use for
+    1 / d, elementwise over a float64 or float32 device tensor."""
+    import torch
+    if d.dtype not in (torch.float64, torch.float32) or not d.is_contiguous():
+        raise ValueError("d must be a contiguous float64 or float32 tensor")
+    out = torch.empty_like(d) if out is None else out
+    prec = 0 if d.dtype == torch.float64 else 1
+    _check(lib().kkt_debug_pivot_rcp(_ptr(d), _ptr(out), d.numel(), prec, _stream(stream)), "kkt_debug_pivot_rcp")
+    return out
+
+
 def _ptr_array(items):
     arr = (C.c_void_p * len(items))(*[C.c_void_p(x) for x in items])
     return arr

@@ -147,6 +147,7 @@ SIGNATURES = {
     "kkt_get_scaling": (C.c_int, [_P, _P]),
     "kkt_export_factors": (C.c_int, [_P, C.POINTER(C.c_int64), _P, _P, _P, C.POINTER(C.c_int64), _P, _P, _P]),
     "kkt_debug_stall": (C.c_int, [_P]),
+    "kkt_debug_pivot_rcp": (C.c_int, [_P, _P, C.c_int64, C.c_int, _P]),
     "kkt_precondition": (C.c_int, [_P, _P, _P, _P]),
     "kkt_refactor_refine": (C.c_int, [_P, _P, _P, _P, C.c_double, _P, _P]),
     "kkt_model_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, C.c_int,

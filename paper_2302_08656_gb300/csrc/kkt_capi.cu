@@ -957,6 +957,14 @@ kkt_status refine_tail(kkt_ctx* c, const double* b, double* x, double tol, kkt_i
     return worst;
 }
 
+// the pivot reciprocal of the factorization and backward kernels, elementwise
+template <typename T>
+__global__ void pivot_rcp_kernel(const T* __restrict__ in, T* __restrict__ out, int64_t n)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = pivot_rcp(in[i]);
+}
+
 }  // namespace
 
 // ======================================================================== C ABI
@@ -1557,6 +1565,23 @@ kkt_status kkt_debug_stall(kkt_ctx* c)
     KKT_CUDA(cudaDeviceSynchronize());
     KKT_CUDA(cudaMemcpy(c->stall, req, sizeof(req), cudaMemcpyHostToDevice));
     KKT_CUDA(cudaDeviceSynchronize());                    // landed before any later launch, on any stream
+    return KKT_OK;
+}
+
+kkt_status kkt_debug_pivot_rcp(const void* d_in, void* d_out, int64_t n, int precision, void* stream)
+{
+    if (n < 0 || (precision != KKT_FP64 && precision != KKT_FP32_IR)) return KKT_E_ARG;
+    if (n == 0) return KKT_OK;
+    if (!d_in || !d_out || (n + 255) / 256 > 0x7fffffff) return KKT_E_ARG;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == KKT_FP64)
+        pivot_rcp_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double*>(d_in),
+                                                         static_cast<double*>(d_out), n);
+    else
+        pivot_rcp_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(d_in),
+                                                        static_cast<float*>(d_out), n);
+    KKT_CUDA(cudaGetLastError());
     return KKT_OK;
 }
 
