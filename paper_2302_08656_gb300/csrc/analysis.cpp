@@ -18,29 +18,33 @@ namespace kktgb {
 // variable is its exact external degree |A_i U (union of L_e, e in E_i)| - 1,
 // recomputed for the variables of each new element. The next pivot is the
 // variable of least degree, the lowest index among equals: a binary heap of
-// (degree, index) pairs, an entry skipped when its variable is gone or its
-// degree has changed since it was pushed.
+// (degree, index) keys, an entry skipped when its variable is gone or its
+// degree has changed since it was pushed. Elements found inside a new element
+// are absorbed into it (they add nothing to any union), which leaves every
+// degree, and so the order, unchanged.
 void min_degree_quotient(int n, const int* rowptr, const int* colidx, std::vector<int>& order)
 {
     std::vector<std::vector<int>> av(n), ae(n), le(n);
     std::vector<char> state(n, 0);           // 0 variable, 1 element, 2 absorbed
-    std::vector<int> deg(n), mark(n, -1);
+    std::vector<int> deg(n), mark(n, -1), seen(n, -1), wmark(n, -1), wout(n, 0);
     for (int i = 0; i < n; ++i) {
         for (int p = rowptr[i]; p < rowptr[i + 1]; ++p)
             if (colidx[p] != i) av[i].push_back(colidx[p]);
         deg[i] = (int)av[i].size();
     }
-    std::priority_queue<std::pair<int, int>, std::vector<std::pair<int, int>>, std::greater<std::pair<int, int>>> pq;
-    for (int i = 0; i < n; ++i) pq.push({deg[i], i});
+    // heap keys (degree << 32) | index: the same order as the (degree, index) pairs
+    auto key = [](int d, int i) { return ((uint64_t)(uint32_t)d << 32) | (uint32_t)i; };
+    std::priority_queue<uint64_t, std::vector<uint64_t>, std::greater<uint64_t>> pq;
+    for (int i = 0; i < n; ++i) pq.push(key(deg[i], i));
     order.clear();
     order.reserve(n);
-    int stamp = 0;
+    int stamp = 0, stamp2 = 0;
     std::vector<int> lp;
     while (!pq.empty()) {
-        const std::pair<int, int> top = pq.top();
+        const uint64_t top = pq.top();
         pq.pop();
-        const int p = top.second;
-        if (state[p] != 0 || deg[p] != top.first) continue;          // stale entry
+        const int p = (int)(uint32_t)top;
+        if (state[p] != 0 || deg[p] != (int)(top >> 32)) continue;   // stale entry
         order.push_back(p);
         // L_p = (A_p U union of absorbed elements' variables) \ {p}
         ++stamp;
@@ -73,19 +77,59 @@ void min_degree_quotient(int n, const int* rowptr, const int* colidx, std::vecto
             for (int v : A) if (state[v] == 0 && mark[v] != stamp) A[w++] = v;
             A.resize(w);
         }
+        // exact external degree of each variable i of L_p: every element list
+        // of i contains L_p \ {i} (p is one of them), so d_i = |L_p| - 1 plus
+        // the variables of A_i and of i's other elements outside L_p, each
+        // counted once. First w(e) = |L_e \ L_p| for every other element e
+        // next to L_p (one scan per element, dropping dead variables, order
+        // kept): an element with w(e) = 0 lies inside L_p and is absorbed into
+        // p (every union it took part in is unchanged), and a variable whose
+        // only other neighbour is one element e has d_i = |L_p| - 1 + w(e).
+        // L_p keeps its marks (stamp); a second stamp array deduplicates per i.
+        const int lp_stamp = stamp;
+        const int lp_size = (int)lp.size();
+        for (int i : lp)
+            for (int e : ae[i]) {
+                if (e == p || wmark[e] == lp_stamp) continue;
+                wmark[e] = lp_stamp;
+                std::vector<int>& L = le[e];
+                size_t w2 = 0;
+                int out = 0;
+                for (int v : L) {
+                    if (state[v] != 0) continue;
+                    L[w2++] = v;
+                    if (mark[v] != lp_stamp) ++out;
+                }
+                L.resize(w2);
+                wout[e] = out;
+                if (out == 0) {
+                    state[e] = 2;
+                    std::vector<int>().swap(L);
+                }
+            }
         for (int i : lp) {
-            int st2 = ++stamp;
-            mark[i] = st2;
-            int d = 0;
-            for (int v : av[i]) if (state[v] == 0 && mark[v] != st2) { mark[v] = st2; ++d; }
-            for (int e : ae[i])
-                for (int v : le[e]) if (state[v] == 0 && mark[v] != st2) { mark[v] = st2; ++d; }
+            std::vector<int>& E = ae[i];
+            size_t w3 = 0;
+            for (int e : E) if (state[e] == 1) E[w3++] = e;
+            E.resize(w3);
+            int d = lp_size - 1;
+            if (av[i].empty() && E.size() == 2) {
+                d += wout[E[0] == p ? E[1] : E[0]];
+            } else {
+                const int st2 = ++stamp2;
+                for (int v : av[i])
+                    if (state[v] == 0 && mark[v] != lp_stamp && seen[v] != st2) { seen[v] = st2; ++d; }
+                for (int e : E) {
+                    if (e == p) continue;
+                    for (int v : le[e])
+                        if (mark[v] != lp_stamp && seen[v] != st2) { seen[v] = st2; ++d; }
+                }
+            }
             if (d != deg[i]) {
                 deg[i] = d;
-                pq.push({d, i});
+                pq.push(key(d, i));
             }
         }
-        // restore the marks of L_p for the next pivot (stamps only grow)
     }
 }
 
