@@ -4,7 +4,6 @@
 
 #include <algorithm>
 #include <numeric>
-#include <queue>
 #include <set>
 #include <utility>
 
@@ -18,8 +17,8 @@ namespace kktgb {
 // variable is its exact external degree |A_i U (union of L_e, e in E_i)| - 1,
 // recomputed for the variables of each new element. The next pivot is the
 // variable of least degree, the lowest index among equals: a binary heap of
-// (degree, index) keys, an entry skipped when its variable is gone or its
-// degree has changed since it was pushed. Elements found inside a new element
+// (degree, index) keys holding every live variable once, its key moved when
+// its degree changes. Elements found inside a new element
 // are absorbed into it (they add nothing to any union), which leaves every
 // degree, and so the order, unchanged.
 void min_degree_quotient(int n, const int* rowptr, const int* colidx, std::vector<int>& order)
@@ -32,19 +31,44 @@ void min_degree_quotient(int n, const int* rowptr, const int* colidx, std::vecto
             if (colidx[p] != i) av[i].push_back(colidx[p]);
         deg[i] = (int)av[i].size();
     }
-    // heap keys (degree << 32) | index: the same order as the (degree, index) pairs
+    // indexed binary min-heap of the live variables, keys (degree << 32) | index
+    // (unique; the same order as the (degree, index) pairs), hpos[i] = slot of i
     auto key = [](int d, int i) { return ((uint64_t)(uint32_t)d << 32) | (uint32_t)i; };
-    std::priority_queue<uint64_t, std::vector<uint64_t>, std::greater<uint64_t>> pq;
-    for (int i = 0; i < n; ++i) pq.push(key(deg[i], i));
+    std::vector<uint64_t> heap(n);
+    std::vector<int> hpos(n);
+    int hsize = n;
+    for (int i = 0; i < n; ++i) { heap[i] = key(deg[i], i); hpos[i] = i; }
+    auto place = [&](int k, uint64_t x) { heap[k] = x; hpos[(int)(uint32_t)x] = k; };
+    auto sift_up = [&](int k) {
+        const uint64_t x = heap[k];
+        while (k > 0) {
+            const int up = (k - 1) >> 1;
+            if (heap[up] <= x) break;
+            place(k, heap[up]);
+            k = up;
+        }
+        place(k, x);
+    };
+    auto sift_down = [&](int k) {
+        const uint64_t x = heap[k];
+        while (true) {
+            int c = 2 * k + 1;
+            if (c >= hsize) break;
+            if (c + 1 < hsize && heap[c + 1] < heap[c]) ++c;
+            if (x <= heap[c]) break;
+            place(k, heap[c]);
+            k = c;
+        }
+        place(k, x);
+    };
+    for (int k = n / 2 - 1; k >= 0; --k) sift_down(k);
     order.clear();
     order.reserve(n);
     int stamp = 0, stamp2 = 0;
     std::vector<int> lp;
-    while (!pq.empty()) {
-        const uint64_t top = pq.top();
-        pq.pop();
-        const int p = (int)(uint32_t)top;
-        if (state[p] != 0 || deg[p] != (int)(top >> 32)) continue;   // stale entry
+    while (hsize > 0) {
+        const int p = (int)(uint32_t)heap[0];
+        if (--hsize > 0) { place(0, heap[hsize]); sift_down(0); }
         order.push_back(p);
         // L_p = (A_p U union of absorbed elements' variables) \ {p}
         ++stamp;
@@ -126,8 +150,10 @@ void min_degree_quotient(int n, const int* rowptr, const int* colidx, std::vecto
                 }
             }
             if (d != deg[i]) {
+                const int k = hpos[i];
+                heap[k] = key(d, i);
+                if (d < deg[i]) sift_up(k); else sift_down(k);
                 deg[i] = d;
-                pq.push(key(d, i));
             }
         }
     }
@@ -415,18 +441,27 @@ std::string analyze_pattern(int n, const int* rowptr, const int* colidx,
         out.asm_pos.assign(nnz, 0);
         out.asm_src.assign(nnz, 0);
         std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+        std::vector<int> er(nnz), ec(nnz);              // permuted (row, column) of each slot
         for (int i = 0; i < n; ++i)
             for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
                 int r = out.iperm[i], c = out.iperm[colidx[p]];
-                int k = snk[std::min(r, c)];
-                const int* R = out.rows.data() + out.rows_ptr[k];
-                int F = out.sn_front[k];
-                int a = find_pos(R, F, r), b = find_pos(R, F, c);
-                if (a < 0 || b < 0) return "internal: entry outside its front";
-                int64_t at = fill[k]++;
-                out.asm_pos[at] = a + b * F;
+                int64_t at = fill[snk[std::min(r, c)]]++;
+                er[at] = r;
+                ec[at] = c;
                 out.asm_src[at] = p;
             }
+        // local positions through a row -> (front, position) map, one front at a time
+        std::vector<int> where(n, -1), owner(n, -1);
+        for (int k = 0; k < ns; ++k) {
+            const int* R = out.rows.data() + out.rows_ptr[k];
+            const int F = out.sn_front[k];
+            for (int t = 0; t < F; ++t) { where[R[t]] = t; owner[R[t]] = k; }
+            for (int64_t at = out.asm_ptr[k]; at < out.asm_ptr[k + 1]; ++at) {
+                const int r = er[at], c = ec[at];
+                if (owner[r] != k || owner[c] != k) return "internal: entry outside its front";
+                out.asm_pos[at] = where[r] + where[c] * F;
+            }
+        }
     }
     // relative indices of each contribution block in its parent
     out.rel_ptr.assign(ns + 1, 0);
