@@ -185,17 +185,17 @@ std::string analyze_pattern(int n, const int* rowptr, const int* colidx,
         }
         if (!diag) return "missing diagonal entry";
     }
-    {   // structural symmetry: count of (i,j) must equal count of (j,i)
+    {   // structural symmetry: with sorted rows and column counts equal to the
+        // row counts, the pattern is symmetric iff its transpose (rows built
+        // in ascending order by a counting sort) has the same column indices
         std::vector<int> cnt(n, 0);
         for (int64_t p = 0; p < nnz; ++p) cnt[colidx[p]]++;
         for (int i = 0; i < n; ++i)
             if (cnt[i] != rowptr[i + 1] - rowptr[i]) return "pattern is not structurally symmetric";
+        std::vector<int> tfill(rowptr, rowptr + n), tcol(nnz);
         for (int i = 0; i < n; ++i)
-            for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-                int j = colidx[p];
-                if (find_pos(colidx + rowptr[j], rowptr[j + 1] - rowptr[j], i) < 0)
-                    return "pattern is not structurally symmetric";
-            }
+            for (int p = rowptr[i]; p < rowptr[i + 1]; ++p) tcol[tfill[colidx[p]]++] = i;
+        if (!std::equal(tcol.begin(), tcol.end(), colidx)) return "pattern is not structurally symmetric";
     }
 
     // ---- ordering

@@ -89,6 +89,12 @@ def test_plan_rejects_bad_patterns():
     with pytest.raises(K.KKTError) as e:
         K.plan(rp, ci)
     assert e.value.status == 5
+    # unsymmetric with equal row and column counts (a 3-cycle off the diagonal)
+    rp = np.array([0, 2, 4, 6], np.int32)
+    ci = np.array([0, 1, 1, 2, 0, 2], np.int32)
+    with pytest.raises(K.KKTError) as e:
+        K.plan(rp, ci)
+    assert e.value.status == 5
     # unsorted columns
     rp = np.array([0, 2, 4], np.int32)
     ci = np.array([1, 0, 0, 1], np.int32)
