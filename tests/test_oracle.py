@@ -407,3 +407,77 @@ def test_solution_not_determined_at_fp64_on_the_literal_kkt(kkt200):
     y0, y1 = xs[0][pat.n_primal:], xs[1][pat.n_primal:]
     assert np.abs(y0).max() > 1e8 * np.abs(b).max()
     assert np.abs(y1 - y0).max() > 1e-2 * np.abs(y0).max()
+
+
+def _exact_doolittle(A):
+    """LU without pivoting of a dense float matrix over the rationals (every
+    double is an exact binary fraction): multipliers below the diagonal, U on
+    and above it."""
+    from fractions import Fraction
+    n = A.shape[0]
+    M = [[Fraction(float(x)) if x != 0 else Fraction(0) for x in row] for row in A]
+    for k in range(n):
+        piv = M[k][k]
+        rk = [(j, M[k][j]) for j in range(k + 1, n) if M[k][j] != 0]
+        for i in range(k + 1, n):
+            if M[i][k] != 0:
+                M[i][k] = M[i][k] / piv
+                lik = M[i][k]
+                for j, ukj in rk:
+                    M[i][j] -= lik * ukj
+    return M
+
+
+def _float32_doolittle(A):
+    """The same elimination in single precision (operands rounded to FP32,
+    every product, difference and quotient rounded to FP32)."""
+    M = A.astype(np.float32)
+    for k in range(M.shape[0]):
+        M[k + 1:, k] = M[k + 1:, k] / M[k, k]
+        M[k + 1:, k + 1:] -= np.outer(M[k + 1:, k], M[k, k + 1:]).astype(np.float32)
+    return M
+
+
+@pytest.mark.parametrize("seed,step,mu", [(1, 2, 1e-3), (2, 5, 1e-6), (3, 0, 1e-1), (4, 1, 1e-2), (5, 7, 1e-8)])
+def test_running_error_bound_holds_against_exact_factors(seed, step, mu):
+    """The first-order running error bound of every factor entry (Wilkinson's
+    running error analysis; the tolerance of the GPU factor parity) against
+    factors computed exactly over the rationals from the same scaled matrix
+    and order. Every entry of the oracle's FP64 factors, and of an FP32
+    elimination in the same order, lies within its bound for that format's
+    unit roundoff, in the columns before the first pivot where the bound
+    states its own invalidity (err(u_jj) >= |u_jj| / 2; here the
+    rounding-noise pivot of the angle-shift direction, near the root).
+    Left-looking column j depends only on columns < j, so those columns are
+    exactly the entries that do not depend on such a pivot. The bound is not
+    loose either: the FP32 errors reach more than half of it."""
+    from fractions import Fraction
+    pat = KKTPattern(make_grid(seed, 10, 14, 3))
+    v = pat.values(pat.point(seed, step, mu))
+    an = O.analyze(pat.rowptr, pat.colidx, v)
+    lu, d, sv = O.refactor(pat.rowptr, pat.colidx, v, an)
+    f = lu.factors()
+    assert f.n_perturbed == 0
+    A = sp.csr_matrix((sv, pat.colidx, pat.rowptr), shape=(pat.n, pat.n)).toarray()[np.ix_(f.p, f.q)]
+    M = _exact_doolittle(A)
+    M32 = _float32_doolittle(A)
+    for unit, got_L, got_U in [(2.0 ** -53, lambda s, i, j: f.Lx[s], lambda s, i, j: f.Ux[s]),
+                               (2.0 ** -24, lambda s, i, j: M32[i, j], lambda s, i, j: M32[i, j])]:
+        eL, eU = lu.error_bound(pat.rowptr, pat.colidx, sv, unit, 0.0)
+        invalid = [j for j in range(f.n) if not eU[f.Up[j + 1] - 1] < abs(f.Ux[f.Up[j + 1] - 1]) / 2]
+        cut = min(invalid) if invalid else f.n
+        assert cut >= f.n - 8                                   # only pivots near the root
+        worst = 0.0
+        for j in range(cut):
+            for lo, hi, idx, bound, got in [(f.Lp[j], f.Lp[j + 1], f.Li, eL, got_L),
+                                            (f.Up[j], f.Up[j + 1], f.Ui, eU, got_U)]:
+                for s in range(lo, hi):
+                    i = int(idx[s])
+                    err = abs(Fraction(float(got(s, i, j))) - M[i][j])
+                    assert err <= Fraction(float(bound[s])), (unit, i, j, float(err), bound[s])
+                    if bound[s] > 0:
+                        worst = max(worst, float(err / Fraction(float(bound[s]))))
+        if unit == 2.0 ** -24:
+            assert worst > 0.5
+        else:
+            assert worst > 0.05
