@@ -601,6 +601,7 @@ def run_serving(args):
         "p50_ms_steady": rep.percentile(50, steady=True), "p99_ms_steady": rep.percentile(99, steady=True),
         "omega_max": float(max(rep.omegas)), "refined": rep.refined, "max_sessions_resident": rep.max_sessions,
         "max_device_bytes": rep.max_bytes, "admission_waits": rep.admission_waits, "wall_s": rep.wall_s,
+        "failed": [[sid, k, err] for sid, k, err in rep.failed],
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -11,7 +11,11 @@ next free stream, so work of different sessions overlaps on the device.
 
 The scheduler is plain Python over a backend with five operations (open,
 issue, poll, finish, close); GpuBackend drives the library, and the tests
-drive the same scheduler with a fake backend on the CPU.
+drive the same scheduler with a fake backend on the CPU. A failure is
+confined to its session: when the analysis of a session, or the issue, poll
+or finish of one of its requests, raises, that session ends (its handle is
+closed, its memory returns to the budget, the error is recorded in
+Report.failed) and every other session carries on.
 """
 from __future__ import annotations
 
@@ -46,6 +50,7 @@ class Report:
     max_sessions: int = 0
     admission_waits: int = 0
     refined: int = 0
+    failed: list = field(default_factory=list)              # (session, request or -1 for analysis, error)
 
     @property
     def solves_per_s(self):
@@ -73,6 +78,7 @@ class Server:
 
     def run(self, sessions, clock=time.perf_counter) -> Report:
         rep = Report()
+        sessions = [s for s in sessions if len(s.arrivals) > 0]   # a session without requests is done
         waiting = [(s.arrivals[0], s.sid) for s in sessions]
         heapq.heapify(waiting)
         spec = {s.sid: s for s in sessions}
@@ -82,6 +88,19 @@ class Server:
         inflight = 0
         remaining = len(sessions)
         pool = ThreadPoolExecutor(max_workers=self.workers)
+
+        def drop(sid, k, err):
+            # end a failed session: close it, return its memory, record the error
+            nonlocal used, remaining
+            st = active.pop(sid)
+            try:
+                self.backend.close(st["handle"])
+            except Exception:
+                pass
+            used -= st["bytes"]
+            remaining -= 1
+            rep.failed.append((sid, k, repr(err)))
+
         t0 = clock()
         try:
             while remaining:
@@ -99,7 +118,14 @@ class Server:
                     opening[sid] = pool.submit(self.backend.open, spec[sid])
                     progressed = True
                 for sid in [s for s, f in opening.items() if f.done()]:
-                    handle = opening.pop(sid).result()
+                    fut = opening.pop(sid)
+                    progressed = True
+                    if fut.exception() is not None:
+                        used -= spec[sid].est_bytes
+                        remaining -= 1
+                        rep.failed.append((sid, -1, repr(fut.exception())))
+                        continue
+                    handle = fut.result()
                     real = self.backend.bytes_of(handle, spec[sid])
                     used += real - spec[sid].est_bytes
                     active[sid] = dict(handle=handle, k=0, ticket=None, release=spec[sid].arrivals[0],
@@ -110,9 +136,17 @@ class Server:
                 # completions
                 for sid, st in list(active.items()):
                     t = st["ticket"]
-                    if t is None or not self.backend.poll(t):
+                    if t is None:
                         continue
-                    omega, refined = self.backend.finish(t)
+                    try:
+                        if not self.backend.poll(t):
+                            continue
+                        omega, refined = self.backend.finish(t)
+                    except Exception as e:
+                        inflight -= 1
+                        drop(sid, st["k"], e)
+                        progressed = True
+                        continue
                     done_t = clock() - t0
                     lat = 1000.0 * (done_t - st["release"])
                     rep.latencies_ms.append(lat)
@@ -134,13 +168,21 @@ class Server:
                     else:
                         st["release"] = max(s.arrivals[st["k"]], done_t)
                 # issue every released request while the in-flight window has room
+                failed_issue = []
                 for sid, st in active.items():
                     if inflight >= self.max_inflight:
                         break
                     if st["ticket"] is None and st["release"] <= now:
-                        st["ticket"] = self.backend.issue(st["handle"], st["k"])
+                        try:
+                            st["ticket"] = self.backend.issue(st["handle"], st["k"])
+                        except Exception as e:
+                            failed_issue.append((sid, st["k"], e))
+                            continue
                         inflight += 1
                         progressed = True
+                for sid, k, e in failed_issue:
+                    drop(sid, k, e)
+                    progressed = True
                 if not progressed and self.poll_sleep_s:
                     time.sleep(self.poll_sleep_s)
         finally:

@@ -78,3 +78,65 @@ def test_inflight_window_is_respected():
     assert rep.completed == 20
     assert be.max_inflight == 3
     assert rep.max_sessions <= 10
+
+
+class FailingBackend(FakeBackend):
+    """Fails the analysis of one session and one request of two others."""
+
+    def __init__(self, fail_open=(), fail_issue=(), fail_finish=()):
+        super().__init__()
+        self.fail_open, self.fail_issue, self.fail_finish = set(fail_open), set(fail_issue), set(fail_finish)
+        self.closed = []
+
+    def open(self, spec):
+        if spec.sid in self.fail_open:
+            raise RuntimeError("analysis failed")
+        return super().open(spec)
+
+    def issue(self, h, k):
+        if (h["spec"].sid, k) in self.fail_issue:
+            raise RuntimeError("launch failed")
+        return super().issue(h, k)
+
+    def finish(self, t):
+        if (t["h"]["spec"].sid, t["k"]) in self.fail_finish:
+            self.inflight -= 1
+            raise RuntimeError("numeric failure")
+        return super().finish(t)
+
+    def close(self, h):
+        self.closed.append(h["spec"].sid)
+        super().close(h)
+
+
+def test_a_failure_ends_only_its_session():
+    be = FailingBackend(fail_open=[2], fail_issue=[(4, 1)], fail_finish=[(6, 2)])
+    sess = _sessions(8, 4, 4000.0, 10)
+    rep = Server(be, budget_bytes=10 ** 9, max_inflight=4).run(sess)
+    assert sorted((sid, k) for sid, k, _ in rep.failed) == [(2, -1), (4, 1), (6, 2)]
+    assert all(err.startswith("RuntimeError") for _, _, err in rep.failed)
+    assert rep.completed == 32 - 4 - 3 - 2                 # session 4 finished 1 request, session 6 two
+    assert be.open_now == 0 and sorted(be.closed) == [0, 1, 3, 4, 5, 6, 7]
+    for s in sess:
+        if s.sid in (2, 4, 6):
+            continue
+        assert [k for sid, k, _ in be.log if sid == s.sid] == [0, 1, 2, 3]
+
+
+def test_a_failed_session_returns_its_memory():
+    """With room for one session at a time, a session whose analysis fails and
+    one whose first request fails must not hold the budget: the rest run."""
+    be = FailingBackend(fail_open=[0], fail_issue=[(1, 0)])
+    sess = _sessions(4, 2, 10000.0, 100)
+    rep = Server(be, budget_bytes=150, max_inflight=4).run(sess)
+    assert sorted((sid, k) for sid, k, _ in rep.failed) == [(0, -1), (1, 0)]
+    assert rep.completed == 4
+    assert rep.max_bytes <= 150 and be.max_open <= 1
+
+
+def test_sessions_without_requests_are_done():
+    be = FakeBackend()
+    sess = _sessions(3, 2, 4000.0, 10)
+    sess.append(SessionSpec(99, None, None, 0, [], None, est_bytes=10))
+    rep = Server(be, budget_bytes=10 ** 9).run(sess)
+    assert rep.completed == 6 and not rep.failed
