@@ -49,6 +49,18 @@ def _store_cache(cache):
         pass
 
 
+def cached_choice(entry, candidates=CANDIDATES, tree_candidates=TREE_CANDIDATES):
+    """The fastest requested (max_pivots, tree_min_fronts) pair by the times of
+    a cache entry, or None unless the entry timed every requested pair."""
+    times = (entry or {}).get("times", {})
+    want = ["%d/%d" % (mp, tmf) for mp in candidates for tmf in tree_candidates]
+    if not want or any(k not in times for k in want):
+        return None
+    sub = {k: times[k] for k in want}
+    mp, tmf = (int(x) for x in min(sub, key=sub.get).split("/"))
+    return {"max_pivots": mp, "tree_min_fronts": tmf}, sub
+
+
 def tune(rowptr, colidx, n_primal, vals, rhs, precision="fp64", count=1, candidates=CANDIDATES,
          tree_candidates=TREE_CANDIDATES, reps=3, use_cache=True):
     """Return (best options dict, {"max_pivots/tree_min_fronts": ms per refactor+refine}).
@@ -60,9 +72,9 @@ def tune(rowptr, colidx, n_primal, vals, rhs, precision="fp64", count=1, candida
 
     key = pattern_key(rowptr, colidx, precision, count)
     cache = _load_cache() if use_cache else {}
-    if key in cache and "tree_min_fronts" in cache[key]:
-        return {"max_pivots": cache[key]["max_pivots"], "tree_min_fronts": cache[key]["tree_min_fronts"]}, \
-            cache[key]["times"]
+    hit = cached_choice(cache.get(key), candidates, tree_candidates)
+    if hit is not None:
+        return hit
     times = {}
     out = torch.empty_like(rhs)
     for mp in candidates:
@@ -82,6 +94,8 @@ def tune(rowptr, colidx, n_primal, vals, rhs, precision="fp64", count=1, candida
     best = min(times, key=times.get)
     mp, tmf = (int(x) for x in best.split("/"))
     if use_cache:
-        cache[key] = {"max_pivots": mp, "tree_min_fronts": tmf, "times": times}
+        merged = dict(cache.get(key, {}).get("times", {}))      # keep pairs timed by earlier calls
+        merged.update(times)
+        cache[key] = {"max_pivots": mp, "tree_min_fronts": tmf, "times": merged}
         _store_cache(cache)
     return {"max_pivots": mp, "tree_min_fronts": tmf}, times
