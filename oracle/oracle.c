@@ -31,9 +31,12 @@
  *                    calls for a better refinement than the library one):
  *                    restarted FGMRES(m), modified Gram-Schmidt, Givens,
  *                    right-preconditioned by the LU solve
+ *   ora_lu_error_bound   first-order running error bound of every factor
+ *                    entry (Wilkinson), the tolerance of the factor parity
  *
  * Parity is pinned by the tests (dense LAPACK LU, inertia, brute-force fill,
- * closed forms); see tests/test_oracle.py.
+ * closed forms, factors in exact rational arithmetic for the error bound);
+ * see tests/test_oracle.py.
  */
 #include <math.h>
 #include <stdlib.h>
