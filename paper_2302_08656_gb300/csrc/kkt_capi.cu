@@ -725,14 +725,14 @@ kkt_status sync_stat(kkt_ctx* c, cudaStream_t st)
     return KKT_OK;
 }
 
-double knorm_of(kkt_ctx* c, cudaStream_t st, int inst = 0)
+// ||K||_inf of instance inst from the device statistics (synchronizes)
+kkt_status knorm_of(kkt_ctx* c, cudaStream_t st, double* knorm, int inst = 0)
 {
     unsigned long long bits = 0;
-    cudaMemcpyAsync(&bits, &c->stat[inst].knorm_bits, sizeof(bits), cudaMemcpyDeviceToHost, st);
-    cudaStreamSynchronize(st);
-    double k;
-    std::memcpy(&k, &bits, sizeof(k));
-    return k;
+    KKT_CUDA(cudaMemcpyAsync(&bits, &c->stat[inst].knorm_bits, sizeof(bits), cudaMemcpyDeviceToHost, st));
+    KKT_CUDA(cudaStreamSynchronize(st));
+    std::memcpy(knorm, &bits, sizeof(*knorm));
+    return KKT_OK;
 }
 
 // ||a||_inf and ||a||_2^2 on the host (synchronizes)
@@ -760,7 +760,8 @@ kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double 
     const int* rp = c->sched.rowptr;
     const int* ci = c->sched.colidx;
     kkt_status s;
-    double knorm = knorm_of(c, st, inst);
+    double knorm = 0.0;
+    if ((s = knorm_of(c, st, &knorm, inst)) != KKT_OK) return s;
     double bmax, bsq, xmax, xsq, rmax, rsq;
     if ((s = norms_host(c, b, &bmax, &bsq, st)) != KKT_OK) return s;
     {
@@ -1472,9 +1473,9 @@ kkt_status kkt_residual(kkt_ctx* c, const double* d_rhs, const double* d_x, doub
     cudaStream_t st = (cudaStream_t)stream;
     KKT_CUDA(launch_spmv_resid(c->n, c->sched.rowptr, c->sched.colidx, c->last_vals, d_x, d_rhs, d_r, st));
     if (omega_out) {
-        double knorm = knorm_of(c, st);
-        double rm, rs, xm, xs, bm, bs;
+        double knorm = 0.0, rm, rs, xm, xs, bm, bs;
         kkt_status s;
+        if ((s = knorm_of(c, st, &knorm)) != KKT_OK) return s;
         if ((s = norms_host(c, d_r, &rm, &rs, st)) != KKT_OK) return s;
         if ((s = norms_host(c, d_x, &xm, &xs, st)) != KKT_OK) return s;
         if ((s = norms_host(c, d_rhs, &bm, &bs, st)) != KKT_OK) return s;
