@@ -43,3 +43,20 @@ def test_error_vs_oracle_per_result():
     # a zero oracle solution: the absolute difference is stated
     z = bench.error_vs_oracle([np.zeros(2)], {"fp64": [np.array([0.0, 3e-9])]})
     assert z["fp64"]["per_result"] == pytest.approx([3e-9])
+
+
+def test_timed_steps_cycle_the_input_pool():
+    """Warm-up steps use their own inputs; the timed steps cycle through the
+    remaining distinct inputs of the pool, every pool input used."""
+    from types import SimpleNamespace
+    for steps, warmup in [(400, 3), (5, 3), (24, 4), (25, 3)]:
+        a = SimpleNamespace(steps=steps, warmup=warmup)
+        n = bench.pool_size(a)
+        assert n == warmup + min(steps, bench.POOL_STEPS)
+        idx = [bench.at(a, i) for i in range(warmup + steps)]
+        assert idx[:warmup] == list(range(warmup))
+        timed = idx[warmup:]
+        assert all(warmup <= i < n for i in timed)
+        assert set(timed) == set(range(warmup, n))
+        # consecutive timed steps never repeat an input while the pool has more than one
+        assert all(x != y for x, y in zip(timed, timed[1:])) or n - warmup == 1
