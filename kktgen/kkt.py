@@ -100,6 +100,7 @@ class KKTPoint:
     mu: float
     delta_w: float
     delta_c: float
+    slack_inv: np.ndarray = None   # (m,) 1/sigma_s on inequality rows (0 elsewhere), or None
 
 
 class KKTPattern:
@@ -151,8 +152,15 @@ class KKTPattern:
 
     # ------------------------------------------------------------------ draws
     def point(self, seed: int, step: int, mu: float = 1e-1,
-              delta_w: float = 1e-8, delta_c: float = 1e-10) -> KKTPoint:
-        """Seeded iterate (V, theta, lambda, Sigma) for interior-point step ``step``."""
+              delta_w: float = 1e-8, delta_c: float = 1e-10, slack_range=None) -> KKTPoint:
+        """Seeded iterate (V, theta, lambda, Sigma) for interior-point step ``step``.
+
+        slack_range = (lo, hi): keep the inequality slacks' term in the (2,2)
+        block, -(dc + 1/sigma_s) on every flow-limit row instead of -dc, with
+        1/sigma_s = s_s / z_s log-uniform on [lo, hi] (the range of Sigma,
+        (1e-8, 1e8), is the reading that matches the barrier diagonal). None:
+        the literal -dc. Drawn from a stream of its own: every other value is
+        the same with or without it."""
         g = self.grid
         rng = np.random.default_rng(np.random.SeedSequence([int(seed), int(step), 0x6b6b74]))
         V = rng.uniform(0.95, 1.05, size=g.n_bus)
@@ -165,7 +173,13 @@ class KKTPattern:
         y = np.exp(rng.uniform(lo, hi, size=self.n_primal))
         sigma = mu / (y * y)
         sigma[g.n_bus:2 * g.n_bus] = 0.0
-        return KKTPoint(V, theta, lam, sigma, float(mu), float(delta_w), float(delta_c))
+        slack_inv = None
+        if slack_range is not None:
+            r2 = np.random.default_rng(np.random.SeedSequence([int(seed), int(step), 0x736c6b]))
+            slack_inv = np.zeros(self.n_dual)
+            a, b = np.log(float(slack_range[0])), np.log(float(slack_range[1]))
+            slack_inv[2 * g.n_bus:] = np.exp(r2.uniform(a, b, size=self.n_dual - 2 * g.n_bus))
+        return KKTPoint(V, theta, lam, sigma, float(mu), float(delta_w), float(delta_c), slack_inv)
 
     def rhs(self, seed: int, step: int) -> np.ndarray:
         rng = np.random.default_rng(np.random.SeedSequence([int(seed), int(step), 0x726873]))
@@ -213,7 +227,10 @@ class KKTPattern:
         trip.append(diag)
         jv = self.jacobian_blocks(pt.V, pt.theta)
         trip += [jv, jv]
-        trip.append(np.full(self.n_dual, -pt.delta_c))
+        dual = np.full(self.n_dual, -pt.delta_c)
+        if pt.slack_inv is not None:
+            dual -= pt.slack_inv
+        trip.append(dual)
         w = np.concatenate(trip)
         assert w.size == self._n_trip
         return np.bincount(self._inv, weights=w, minlength=self.nnz)

@@ -167,3 +167,21 @@ def test_seeded_values_are_reproducible():
     b = pat.values(pat.point(9, 4, 1e-3))
     c = pat.values(pat.point(9, 5, 1e-3))
     assert np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+def test_slack_range_changes_only_the_flow_rows_diagonal():
+    """With slack terms the (2,2) diagonal of every flow-limit row becomes
+    -(dc + 1/sigma_s), 1/sigma_s within the requested range; every other value
+    is bitwise the literal one (the slack draws use a stream of their own)."""
+    pat = KKTPattern(make_grid(1, 200, 300, 40))
+    B, n = 200, pat.n_primal
+    lit = pat.values(pat.point(1, 3, 1e-3))
+    sl = pat.values(pat.point(1, 3, 1e-3, slack_range=(1e-2, 1e2)))
+    K0, K1 = pat.to_scipy(lit), pat.to_scipy(sl)
+    D = (K1 - K0).tocoo()
+    D.eliminate_zeros()
+    rows = np.arange(n + 2 * B, pat.n)
+    assert sorted(zip(D.row.tolist(), D.col.tolist())) == [(r, r) for r in rows]
+    s = -(K1.diagonal()[rows] - K0.diagonal()[rows])
+    assert np.all(s >= 1e-2 * (1 - 1e-12)) and np.all(s <= 1e2 * (1 + 1e-12))
+    assert np.log10(s).std() > 0.5                      # spread over the range, not one value

@@ -481,3 +481,36 @@ def test_running_error_bound_holds_against_exact_factors(seed, step, mu):
             assert worst > 0.5
         else:
             assert worst > 0.05
+
+
+@pytest.mark.parametrize("step,mu", [(0, 1e-1), (3, 1e-3), (7, 1e-7)])
+def test_slack_terms_determine_x_and_the_fp32_threshold_needs_refinement(kkt200, step, mu):
+    """With the inequality slacks' term kept in the (2,2) block (1/sigma_s in
+    [1e-2, 1e2]) the solution is determined at FP64: solves without
+    equilibration agree with the default within 1e-2. Factors with the FP32
+    static-pivot threshold (eps = 1e-7, FP64 arithmetic) meet omega <= 1e-10
+    with no refinement step, yet differ from it by more than 10 %; refined to
+    omega <= 1e-15 they agree within 1e-2. Contrast with the literal matrix
+    (test_solution_not_determined_at_fp64_on_the_literal_kkt)."""
+    pat = kkt200
+    npr = pat.n_primal
+    v = pat.values(pat.point(1, step, mu, slack_range=(1e-2, 1e2)))
+    b = pat.rhs(1, step)
+
+    def solve(eps=1e-14, tol=1e-15, ruiz=10):
+        an = O.analyze(pat.rowptr, pat.colidx, v, ruiz_iters=ruiz, pivot_eps=eps)
+        lu, d, _ = O.refactor(pat.rowptr, pat.colidx, v, an, ruiz_iters=ruiz, pivot_eps=eps)
+        return O.fgmres(pat.rowptr, pat.colidx, v, lu, d, b, 30, 10, tol)
+
+    def diff(x, y):
+        return max(np.abs(x[:npr] - y[:npr]).max() / np.abs(y[:npr]).max(),
+                   np.abs(x[npr:] - y[npr:]).max() / np.abs(y[npr:]).max())
+
+    x0, _, om0 = solve()
+    assert om0 <= 1e-15
+    x1, _, _ = solve(ruiz=0)
+    assert diff(x1, x0) < 1e-2
+    xa, ita, oma = solve(eps=1e-7, tol=1e-10)
+    assert ita == 0 and oma <= 1e-10 and diff(xa, x0) > 0.1
+    xb, itb, omb = solve(eps=1e-7, tol=1e-15)
+    assert itb > 0 and omb <= 1e-15 and diff(xb, x0) < 1e-2
