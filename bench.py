@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--precond", default="lu", choices=["lu", "jacobi"],
                     help="refinement preconditioner: exact triangular solves or Jacobi sweeps")
     ap.add_argument("--sweeps", type=int, default=4, help="Jacobi sweeps per triangular factor")
+    ap.add_argument("--slack-range", type=float, nargs=2, default=None, metavar=("LO", "HI"),
+                    help="keep the inequality slacks' term -(1/sigma_s), 1/sigma_s log-uniform on [LO, HI], "
+                         "on the flow-limit rows (single-system workloads; off: the literal -dc)")
     ap.add_argument("--tree-min-fronts", type=int, default=None,
                     help="levels with fewer fronts run in the persistent tree kernels (library default if unset)")
     return ap.parse_args()
@@ -111,12 +114,13 @@ def at(args, i):
     return i if i < n else args.warmup + (i - args.warmup) % (n - args.warmup)
 
 
-def inputs(pat, mus, seed, count):
-    """Values and right-hand sides for `count` IPM steps (schedule cycled)."""
+def inputs(pat, mus, seed, count, slack_range=None):
+    """Values and right-hand sides for `count` IPM steps (schedule cycled);
+    slack_range: keep the inequality slacks' term in the (2,2) block."""
     vals, rhs = [], []
     for i in range(count):
         k = i % len(mus)
-        vals.append(pat.values(pat.point(seed, k, mus[k])))
+        vals.append(pat.values(pat.point(seed, k, mus[k], slack_range=slack_range)))
         rhs.append(pat.rhs(seed, k))
     return vals, rhs
 
@@ -253,7 +257,7 @@ def run_reference(args):
         raise SystemExit("--impl reference times the oracle on a single-system workload")
     w, pat, mus = workload(args.workload, args.seed)
     n_in = args.warmup + args.steps
-    vals_p, rhs_p = inputs(pat, mus, args.seed, pool_size(args))
+    vals_p, rhs_p = inputs(pat, mus, args.seed, pool_size(args), args.slack_range)
     vals = [vals_p[at(args, i)] for i in range(n_in)]
     rhs = [rhs_p[at(args, i)] for i in range(n_in)]
     times, oms, _ = cpu_run(pat, vals, rhs, args.tol, 1e9, n_in)
@@ -264,7 +268,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": len(t), "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "precision": "fp64", "tol": args.tol},
+        "config": {"workload": args.workload, "precision": "fp64", "tol": args.tol,
+                   "slack_range": args.slack_range},
         "p50_ms": 1000 * float(np.percentile(t, 50)), "p99_ms": 1000 * float(np.percentile(t, 99)),
         "omega_max": float(max(oms)),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -290,7 +295,7 @@ def run_native(args):
     seed = rank_seed(args.seed, rank)       # independent scenario per rank
     w, pat, mus = workload(args.workload, seed)
     n_in = pool_size(args)
-    vals_h, rhs_h = inputs(pat, mus, seed, n_in)
+    vals_h, rhs_h = inputs(pat, mus, seed, n_in, args.slack_range)
     vals = [torch.from_numpy(v).to(dev) for v in vals_h]
     rhs = [torch.from_numpy(b).to(dev) for b in rhs_h]
     xs = [torch.empty_like(b) for b in rhs]
@@ -448,7 +453,7 @@ def run_native(args):
             "data": "synthetic",
             "config": {"workload": args.workload, "buses": w["n_bus"], "branches": w["n_branch"],
                        "generators": w["n_gen"], "n": pat.n, "nnz": pat.nnz, "precision": args.precision,
-                       "tol": args.tol, "mu": [w["mu0"], w["mu1"]],
+                       "tol": args.tol, "mu": [w["mu0"], w["mu1"]], "slack_range": args.slack_range,
                        "l2": "flushed between timed steps (%d MB write)" % (flush.numel() >> 20),
                        "fronts": plan["n_fronts"], "levels": plan["n_levels"], "nnz_lu": plan["nnz_lu"],
                        "tree_levels": plan["tree_levels"], "tree_units": plan["tree_units"]},
