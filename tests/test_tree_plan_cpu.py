@@ -47,7 +47,8 @@ def _plan(tool, tmp_path, pat, max_pivots, min_fronts):
     np.asarray(pat.colidx, np.int32).tofile(src + ".ci")
     subprocess.run([tool, src, out, str(max_pivots), str(min_fronts)], check=True)
     r = {k: np.fromfile(out + "." + k, dtype=np.int64)
-         for k in ["head", "fr", "kid", "unit", "fused", "level", "sn_parent", "child_ptr", "child_list"]}
+         for k in ["head", "fr", "kid", "unit", "fused", "level", "sn_parent", "child_ptr", "child_list", "asm_ptr",
+                   "sn_first", "sn_front"]}
     r["fr"] = r["fr"].reshape(-1, 6)
     r["unit"] = r["unit"].reshape(-1, 3)
     r["fused"] = r["fused"].reshape(-1, 3)
@@ -59,7 +60,7 @@ def _plan(tool, tmp_path, pat, max_pivots, min_fronts):
 def test_tree_plan_orders_every_dependency_first(dump_tool, tmp_path, buses, max_pivots, min_fronts):
     pat = KKTPattern(make_grid(3, buses, int(1.28 * buses), buses // 5))
     P = _plan(dump_tool, tmp_path, pat, max_pivots, min_fronts)
-    split, n_levels, ns, nq = (int(x) for x in P["head"])
+    split, n_levels, ns, nq, alg_bytes = (int(x) for x in P["head"])
     fr, kid, level, sn_parent = P["fr"], P["kid"], P["level"], P["sn_parent"]
     if min_fronts == 0:
         assert nq == 0 and split == n_levels
@@ -125,3 +126,27 @@ def test_tree_plan_orders_every_dependency_first(dump_tool, tmp_path, buses, max
         for c in kid[fr[q, 4]:fr[q, 5]]:
             if c >= 0:
                 assert pos_fwd[c] < pos_fwd[q] and last_fac[c] < first_fac[q]
+
+
+@pytest.mark.parametrize("buses,max_pivots,min_fronts", [(2000, 16, 2432), (500, 8, 100000)])
+def test_tree_algorithmic_bytes_follow_their_definition(dump_tool, tmp_path, buses, max_pivots, min_fronts):
+    """The algorithmic bytes of one refactorization of the tree part (the
+    roofline numerator of tree_factor_kernel), recomputed from the fronts:
+    per front, its original entries (value + 8 bytes of position and source
+    index), its factor panel (F w + w m values), its own contribution block
+    written (m^2) and its children's contribution blocks read; 8-byte values."""
+    pat = KKTPattern(make_grid(5, buses, int(1.28 * buses), buses // 5))
+    P = _plan(dump_tool, tmp_path, pat, max_pivots, min_fronts)
+    split, n_levels, ns, nq, alg_bytes = (int(x) for x in P["head"])
+    assert nq > 0
+    es = 8
+    w = np.diff(P["sn_first"])
+    F = P["sn_front"]
+    m = F - w
+    expect = 0
+    for s in P["fr"][:, 0]:
+        expect += (P["asm_ptr"][s + 1] - P["asm_ptr"][s]) * (es + 8)
+        expect += (F[s] * w[s] + w[s] * m[s]) * es + m[s] * m[s] * es
+        for c in P["child_list"][P["child_ptr"][s]:P["child_ptr"][s + 1]]:
+            expect += m[c] * m[c] * es
+    assert alg_bytes == expect

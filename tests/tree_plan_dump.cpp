@@ -45,7 +45,7 @@ int main(int argc, char** argv)
     if (!err.empty()) { std::fprintf(stderr, "%s\n", err.c_str()); return 1; }
     TreePlan tp;
     build_tree(a, std::atoi(argv[4]), sizeof(double), tp);
-    std::vector<int64_t> head = {tp.split, a.n_levels, a.ns, (int64_t)tp.fr.size()};
+    std::vector<int64_t> head = {tp.split, a.n_levels, a.ns, (int64_t)tp.fr.size(), tp.alg_bytes};
     std::vector<int64_t> fr, kid, unit, fused, level(a.ns), sn_parent(a.sn_parent.begin(), a.sn_parent.end());
     for (int l = 0; l < a.n_levels; ++l)
         for (int t = a.level_ptr[l]; t < a.level_ptr[l + 1]; ++t) level[a.level_fronts[t]] = l;
@@ -65,5 +65,8 @@ int main(int argc, char** argv)
     write_all(out + ".sn_parent", sn_parent);
     write_all(out + ".child_ptr", child_ptr);
     write_all(out + ".child_list", child_list);
+    write_all(out + ".asm_ptr", std::vector<int64_t>(a.asm_ptr.begin(), a.asm_ptr.end()));
+    write_all(out + ".sn_first", std::vector<int64_t>(a.sn_first.begin(), a.sn_first.end()));
+    write_all(out + ".sn_front", std::vector<int64_t>(a.sn_front.begin(), a.sn_front.end()));
     return 0;
 }
