@@ -67,6 +67,37 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _check_tensor(t, numel, name, host=False):
+    """Raise unless t is a contiguous float64 torch tensor of `numel` elements
+    on a CUDA device (host=True: in host memory). Every pointer the library
+    reads or writes is checked here first, so a wrong argument never reaches
+    a kernel."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor, got %s" % (name, type(t).__name__))
+    if t.dtype != torch.float64:
+        raise ValueError("%s must be float64, got %s" % (name, t.dtype))
+    if t.numel() != numel:
+        raise ValueError("%s must have %d elements, got %d" % (name, numel, t.numel()))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if host and t.is_cuda:
+        raise ValueError("%s must be in host memory" % name)
+    if not host and not t.is_cuda:
+        raise ValueError("%s must be on a CUDA device" % name)
+
+
+def _check_array(a, numel, name, writeable=False):
+    """Raise unless a is a contiguous float64 numpy array of `numel` elements."""
+    if not isinstance(a, np.ndarray):
+        raise TypeError("%s must be a numpy array, got %s" % (name, type(a).__name__))
+    if a.dtype != np.float64 or a.size != numel or not a.flags.c_contiguous:
+        raise ValueError("%s must be a contiguous float64 array of %d elements, got %s %s"
+                         % (name, numel, a.dtype, a.shape))
+    if writeable and not a.flags.writeable:
+        raise ValueError("%s must be writeable" % name)
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -126,17 +157,17 @@ class KKTSolver:
 
     # -- numeric stages ---------------------------------------------------
     def refactor(self, vals, stream=None):
-        assert vals.is_cuda and vals.dtype.itemsize == 8 and vals.numel() == self.nnz * self.count
-        assert vals.is_contiguous()
+        _check_tensor(vals, self.nnz * self.count, "vals")
         _check(lib().kkt_refactor(self._h, _ptr(vals), _stream(stream)), "kkt_refactor")
 
     def refactor_refine(self, vals, rhs, out=None, tol=1e-10, stream=None, raise_on_noconv=True):
         """refactor + refine in one call (the first solve's forward pass rides along the refactorization)."""
         import torch
-        assert vals.is_cuda and vals.dtype.itemsize == 8 and vals.numel() == self.nnz * self.count
-        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n * self.count
+        _check_tensor(vals, self.nnz * self.count, "vals")
+        _check_tensor(rhs, self.n * self.count, "rhs")
         if out is None:
             out = torch.empty_like(rhs)
+        _check_tensor(out, self.n * self.count, "out")
         infos = (Info * self.count)()
         st = lib().kkt_refactor_refine(self._h, _ptr(vals), _ptr(rhs), _ptr(out), float(tol), infos,
                                        _stream(stream))
@@ -146,19 +177,19 @@ class KKTSolver:
 
     def solve(self, rhs, out=None, stream=None):
         import torch
-        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n * self.count
-        assert rhs.is_contiguous()
+        _check_tensor(rhs, self.n * self.count, "rhs")
         if out is None:
             out = torch.empty_like(rhs)
+        _check_tensor(out, self.n * self.count, "out")
         _check(lib().kkt_solve(self._h, _ptr(rhs), _ptr(out), _stream(stream)), "kkt_solve")
         return out
 
     def refine(self, rhs, out=None, tol=1e-10, stream=None, raise_on_noconv=True):
         import torch
-        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n * self.count
-        assert rhs.is_contiguous()
+        _check_tensor(rhs, self.n * self.count, "rhs")
         if out is None:
             out = torch.empty_like(rhs)
+        _check_tensor(out, self.n * self.count, "out")
         infos = (Info * self.count)()
         st = lib().kkt_refine(self._h, _ptr(rhs), _ptr(out), float(tol), infos, _stream(stream))
         if st != 6 or raise_on_noconv:
@@ -168,23 +199,30 @@ class KKTSolver:
     def precondition(self, rhs, out=None, stream=None):
         """z = M^{-1} rhs with the context's preconditioner (exact solves or Jacobi sweeps)."""
         import torch
-        assert rhs.is_cuda and rhs.dtype == torch.float64 and rhs.numel() == self.n * self.count
+        _check_tensor(rhs, self.n * self.count, "rhs")
         if out is None:
             out = torch.empty_like(rhs)
+        _check_tensor(out, self.n * self.count, "out")
         _check(lib().kkt_precondition(self._h, _ptr(rhs), _ptr(out), _stream(stream)), "kkt_precondition")
         return out
 
     def solve_checked(self, rhs, out, omega_host, stream=None):
         """Asynchronous solve + device-side backward error into omega_host
         (a pinned float64 tensor with `count` entries, valid after the stream work)."""
+        _check_tensor(rhs, self.n * self.count, "rhs")
+        _check_tensor(out, self.n * self.count, "out")
+        _check_tensor(omega_host, self.count, "omega_host", host=True)
         _check(lib().kkt_solve_checked(self._h, _ptr(rhs), _ptr(out), C.c_void_p(omega_host.data_ptr()),
                                        _stream(stream)), "kkt_solve_checked")
 
     def step_host(self, vals, rhs, tol=1e-10, out=None, stream=None, raise_on_noconv=True):
         """Refactor + refine through host buffers (copies inside the call)."""
-        v = np.ascontiguousarray(vals, dtype=np.float64)
-        b = np.ascontiguousarray(rhs, dtype=np.float64)
+        v = np.ascontiguousarray(vals, dtype=np.float64).reshape(-1)
+        b = np.ascontiguousarray(rhs, dtype=np.float64).reshape(-1)
+        _check_array(v, self.nnz * self.count, "vals")
+        _check_array(b, self.n * self.count, "rhs")
         x = np.empty(self.n * self.count) if out is None else out
+        _check_array(x, self.n * self.count, "out", writeable=True)
         infos = (Info * self.count)()
         st = lib().kkt_step_host(self._h, v.ctypes.data, b.ctypes.data, x.ctypes.data, float(tol),
                                  infos, _stream(stream))
@@ -193,9 +231,14 @@ class KKTSolver:
         return x, (infos[0] if self.count == 1 else list(infos))
 
     def residual(self, rhs, x, out=None, stream=None):
+        """r = rhs - K x and the backward error of x, for one system of n rows
+        (the first instance of a batched context)."""
         import torch
+        _check_tensor(rhs, self.n, "rhs")
+        _check_tensor(x, self.n, "x")
         if out is None:
             out = torch.empty_like(rhs)
+        _check_tensor(out, self.n, "out")
         om = C.c_double(0.0)
         _check(lib().kkt_residual(self._h, _ptr(rhs), _ptr(x), _ptr(out), C.byref(om), _stream(stream)),
                "kkt_residual")
@@ -287,12 +330,13 @@ class KKTModel:
         """K values (device float64, nnz) from device float64 V, theta (n_bus),
         lam (constraint rows) and sigma (n_primal)."""
         import torch
-        for a in (V, theta, lam, sigma):
-            assert a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
-        assert V.numel() == theta.numel() == self.n_bus and sigma.numel() == self.n_primal
-        assert lam.numel() == self.n - self.n_primal
+        _check_tensor(V, self.n_bus, "V")
+        _check_tensor(theta, self.n_bus, "theta")
+        _check_tensor(lam, self.n - self.n_primal, "lam")
+        _check_tensor(sigma, self.n_primal, "sigma")
         if out is None:
             out = torch.empty(self.nnz, dtype=torch.float64, device=V.device)
+        _check_tensor(out, self.nnz, "out")
         _check(lib().kkt_model_assemble(self._h, _ptr(V), _ptr(theta), _ptr(lam), _ptr(sigma), float(delta_w),
                                         float(delta_c), _ptr(out), _stream(stream)), "kkt_model_assemble")
         return out

@@ -1,0 +1,86 @@
+"""Argument checks of the Python binding, run without a GPU: every tensor or
+array the library would read or write is checked (type, float64, size,
+contiguity, device) before any call reaches it, so a wrong argument raises
+instead of reaching a kernel or a host copy."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2302_08656_gb300 as K
+
+
+def _solver(n=10, nnz=28, count=2):
+    s = object.__new__(K.KKTSolver)          # no analysis: the checks come first
+    s.n, s.nnz, s.count, s._h = n, nnz, count, None
+    return s
+
+
+@pytest.mark.parametrize("call", ["refactor", "solve", "refine", "precondition", "refactor_refine"])
+def test_device_arguments_are_checked(call):
+    s = _solver()
+    good_v, good_b = torch.zeros(56, dtype=torch.float64), torch.zeros(20, dtype=torch.float64)
+    cases = {
+        "float32": (torch.zeros(56, dtype=torch.float32), torch.zeros(20, dtype=torch.float32), "float64"),
+        "int64": (torch.zeros(56, dtype=torch.int64), torch.zeros(20, dtype=torch.int64), "float64"),
+        "size": (torch.zeros(55, dtype=torch.float64), torch.zeros(19, dtype=torch.float64), "elements"),
+        "strided": (torch.zeros(112, dtype=torch.float64)[::2], torch.zeros(40, dtype=torch.float64)[::2],
+                    "contiguous"),
+        "host": (good_v, good_b, "CUDA device"),
+    }
+    for _, (v, b, msg) in cases.items():
+        with pytest.raises(ValueError, match=msg):
+            if call == "refactor":
+                s.refactor(v)
+            elif call == "refactor_refine":
+                s.refactor_refine(v, good_b if msg == "CUDA device" else b)
+            else:
+                getattr(s, call)(b)
+    with pytest.raises(TypeError):
+        s.refactor(np.zeros(56))
+
+
+def test_residual_and_checked_solve_arguments():
+    s = _solver(count=1)
+    b = torch.zeros(10, dtype=torch.float64)
+    with pytest.raises(ValueError, match="elements"):
+        s.residual(torch.zeros(9, dtype=torch.float64), b)
+    with pytest.raises(ValueError, match="CUDA device"):
+        s.residual(b, b)
+    with pytest.raises(ValueError, match="CUDA device"):
+        s.solve_checked(b, b, torch.zeros(1, dtype=torch.float64))
+
+
+def test_host_step_arguments_are_checked():
+    s = _solver()
+    v, b = np.zeros(56), np.zeros(20)
+    with pytest.raises(ValueError, match="vals"):
+        s.step_host(np.zeros(55), b)
+    with pytest.raises(ValueError, match="rhs"):
+        s.step_host(v, np.zeros(21))
+    with pytest.raises(ValueError, match="out"):
+        s.step_host(v, b, out=np.zeros(20, dtype=np.float32))
+    with pytest.raises(ValueError, match="out"):
+        s.step_host(v, b, out=np.zeros(40)[::2])
+    ro = np.zeros(20)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError, match="writeable"):
+        s.step_host(v, b, out=ro)
+    with pytest.raises(TypeError):
+        s.step_host(v, b, out=[0.0] * 20)
+
+
+def test_model_assemble_arguments_are_checked():
+    from kktgen import make_grid
+    g = make_grid(1, 20, 26, 4)
+    m = K.KKTModel.from_grid(g, host_only=True)
+    f64 = lambda k: torch.zeros(k, dtype=torch.float64)      # noqa: E731
+    V, th, lam, sig = f64(m.n_bus), f64(m.n_bus), f64(m.n - m.n_primal), f64(m.n_primal)
+    # arguments are checked in order, each completely (device last)
+    with pytest.raises(ValueError, match="V must have"):
+        m.assemble(f64(m.n_bus + 1), th, lam, sig)
+    with pytest.raises(ValueError, match="V must be float64"):
+        m.assemble(torch.zeros(m.n_bus, dtype=torch.float32), th, lam, sig)
+    with pytest.raises(ValueError, match="V must be on a CUDA device"):
+        m.assemble(V, th, lam, sig)
+    m.close()
