@@ -379,12 +379,21 @@ def _ptr_array(items):
 
 
 def refactor_batched(solvers, vals, stream=None):
+    if len(vals) != len(solvers):
+        raise ValueError("one vals tensor per solver")
+    for i, (s, v) in enumerate(zip(solvers, vals)):
+        _check_tensor(v, s.nnz * s.count, "vals[%d]" % i)
     hs = _ptr_array([s.handle.value for s in solvers])
     vs = _ptr_array([v.data_ptr() for v in vals])
     _check(lib().kkt_refactor_batched(hs, vs, len(solvers), _stream(stream)), "kkt_refactor_batched")
 
 
 def solve_batched(solvers, rhs, outs, stream=None):
+    if not len(rhs) == len(outs) == len(solvers):
+        raise ValueError("one rhs and one out tensor per solver")
+    for i, (s, b, x) in enumerate(zip(solvers, rhs, outs)):
+        _check_tensor(b, s.n * s.count, "rhs[%d]" % i)
+        _check_tensor(x, s.n * s.count, "outs[%d]" % i)
     hs = _ptr_array([s.handle.value for s in solvers])
     bs = _ptr_array([b.data_ptr() for b in rhs])
     xs = _ptr_array([x.data_ptr() for x in outs])

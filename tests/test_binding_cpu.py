@@ -84,3 +84,18 @@ def test_model_assemble_arguments_are_checked():
     with pytest.raises(ValueError, match="V must be on a CUDA device"):
         m.assemble(V, th, lam, sig)
     m.close()
+
+
+def test_batched_calls_check_every_solver_argument():
+    a, b = _solver(count=2), _solver(n=12, nnz=34, count=1)
+    f64 = lambda k: torch.zeros(k, dtype=torch.float64)      # noqa: E731
+    with pytest.raises(ValueError, match="one vals"):
+        K.refactor_batched([a, b], [f64(56)])
+    with pytest.raises(ValueError, match=r"vals\[0\] must have 56"):
+        K.refactor_batched([a, b], [f64(55), f64(34)])
+    with pytest.raises(ValueError, match=r"vals\[0\] must be on a CUDA device"):
+        K.refactor_batched([a, b], [f64(56), f64(34)])
+    with pytest.raises(ValueError, match=r"rhs\[0\] must have 20"):
+        K.solve_batched([a, b], [f64(19), f64(12)], [f64(20), f64(12)])
+    with pytest.raises(ValueError, match="one rhs"):
+        K.solve_batched([a, b], [f64(20)], [f64(20), f64(12)])
