@@ -140,3 +140,17 @@ def test_sessions_without_requests_are_done():
     sess.append(SessionSpec(99, None, None, 0, [], None, est_bytes=10))
     rep = Server(be, budget_bytes=10 ** 9).run(sess)
     assert rep.completed == 6 and not rep.failed
+
+
+def test_admission_estimate_bounds_the_device_memory():
+    """Sessions are admitted on estimate_bytes(nnz) before their analysis
+    exists; the estimate must not fall below the context's device memory,
+    which the host-only plan reports exactly, over the serving sizes."""
+    import paper_2302_08656_gb300 as K
+    from paper_2302_08656_gb300.serve import estimate_bytes
+    from kktgen import KKTPattern, make_grid
+    for buses in (500, 3000, 25000):
+        pat = KKTPattern(make_grid(9, buses, int(1.28 * buses), buses // 5))
+        for prec in ("fp32", "fp64"):
+            exact = K.plan(pat.rowptr, pat.colidx, precision=prec)["device_bytes"]
+            assert exact <= estimate_bytes(pat.nnz, prec), (buses, prec, exact)
