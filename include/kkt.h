@@ -74,13 +74,15 @@ typedef struct {
                                    eliminated k-th; read only during kkt_analyze */
     double static_pivot_eps;    /* a pivot u_jj with |u_jj| < eps * max|D K D| is replaced by
                                    sign(u_jj) * eps * max|D K D| (sign(0) = +1) and counted.
-                                   <= 0 selects the default: 1e-14 (FP64), 1e-7 (FP32) */
+                                   <= 0 selects the default: 1e-14 (FP64), 1e-7 (FP32);
+                                   NaN or >= 1: KKT_E_ARG */
     int ruiz_iters;             /* equilibration iterations per refactor (default 10) */
     int restart;                /* FGMRES restart length m (default 30, max 64) */
     int max_cycles;             /* FGMRES restart cycles (default 10) */
     int relax_pivots;           /* supernode amalgamation: max pivots of a merged front
                                    for the "small front" rule (default 16) */
-    double relax_zeros;         /* amalgamation: max share of explicit zeros (default 0.15) */
+    double relax_zeros;         /* amalgamation: max share of explicit zeros (default 0.15;
+                                   outside [0, 1] or NaN: KKT_E_ARG) */
     int max_pivots;             /* pivots per supernode: merges stop and larger supernodes
                                    are split into chains at this size (default 16, max 64) */
     int no_graphs;              /* 1: launch every kernel from the host instead of replaying

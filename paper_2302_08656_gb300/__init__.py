@@ -39,7 +39,12 @@ def _opts(precision="fp64", ordering="mindeg", user_perm=None, static_pivot_eps=
           tree_min_fronts=None, spin_limit=None, precond="lu", jacobi_sweeps=4):
     o = Options()
     lib().kkt_default_options(C.byref(o))
-    o.precision = FP32_IR if precision in ("fp32", "fp32_ir", FP32_IR) else FP64
+    if precision in ("fp32", "fp32_ir", FP32_IR):
+        o.precision = FP32_IR
+    elif precision in ("fp64", FP64):
+        o.precision = FP64
+    else:
+        raise ValueError("precision must be 'fp64' or 'fp32', got %r" % (precision,))
     o.ordering = _ORDER[ordering] if isinstance(ordering, str) else int(ordering)
     keep = None
     if user_perm is not None:

@@ -179,6 +179,8 @@ kkt_status check_options(const kkt_options& o)
     if (o.tree_min_fronts < 0 || o.spin_limit < 1) return KKT_E_ARG;
     if (o.precond != KKT_PRECOND_LU && o.precond != KKT_PRECOND_JACOBI) return KKT_E_ARG;
     if (o.jacobi_sweeps < 1 || o.jacobi_sweeps > 1000000) return KKT_E_ARG;
+    if (std::isnan(o.static_pivot_eps) || o.static_pivot_eps >= 1.0) return KKT_E_ARG;   // <= 0: the default
+    if (!(o.relax_zeros >= 0.0 && o.relax_zeros <= 1.0)) return KKT_E_ARG;
     return KKT_OK;
 }
 

@@ -140,3 +140,24 @@ def test_plan_tree_part_follows_the_option():
         K.plan(pat.rowptr, pat.colidx, tree_min_fronts=-1)
     with pytest.raises(K.KKTError):
         K.plan(pat.rowptr, pat.colidx, spin_limit=0)
+
+
+def test_out_of_range_options_are_refused():
+    """Every option outside its documented range is refused with KKT_E_ARG by
+    the host-only plan (the same check runs in kkt_analyze)."""
+    pat = KKTPattern(make_grid(1, 10, 12, 2))
+    bad = [dict(ruiz_iters=-1), dict(ruiz_iters=65), dict(restart=0), dict(restart=10 ** 6), dict(max_cycles=-1),
+           dict(max_pivots=0), dict(max_pivots=65), dict(relax_pivots=0), dict(tree_min_fronts=-1),
+           dict(spin_limit=0), dict(precond=2), dict(jacobi_sweeps=0), dict(ordering=3),
+           dict(static_pivot_eps=float("nan")), dict(static_pivot_eps=1.0), dict(relax_zeros=-0.1),
+           dict(relax_zeros=float("nan")), dict(relax_zeros=1.5)]
+    for opts in bad:
+        with pytest.raises(K.KKTError) as e:
+            K.plan(pat.rowptr, pat.colidx, **opts)
+        assert e.value.status == 1, opts
+    # documented defaults-selecting values and the ends of the ranges are accepted
+    for opts in [dict(static_pivot_eps=-1.0), dict(static_pivot_eps=0.0), dict(relax_zeros=0.0),
+                 dict(relax_zeros=1.0), dict(max_pivots=64), dict(ruiz_iters=0)]:
+        K.plan(pat.rowptr, pat.colidx, **opts)
+    with pytest.raises(ValueError):
+        K.plan(pat.rowptr, pat.colidx, precision="fp16")
