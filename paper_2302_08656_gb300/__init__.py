@@ -311,6 +311,12 @@ class KKTModel:
                       ((f, np.int32), (t, np.int32), (r, np.float64), (x, np.float64), (gen_bus, np.int32),
                        (c2, np.float64))]
         ff, tt, rr, xx, gb, cc = self._keep
+        if not ff.ndim == tt.ndim == rr.ndim == xx.ndim == gb.ndim == cc.ndim == 1:
+            raise ValueError("grid arrays must be one-dimensional")
+        if not ff.size == tt.size == rr.size == xx.size:
+            raise ValueError("f, t, r and x must have one entry per branch")
+        if gb.size != cc.size:
+            raise ValueError("gen_bus and c2 must have one entry per generator")
         flags = (self.FLOW_LIMITS if flow_limits else 0) | (self.HOST_ONLY if host_only else 0)
         h = C.c_void_p()
         _check(lib().kkt_model_create(int(n_bus), ff.size, gb.size, ff.ctypes.data, tt.ctypes.data, rr.ctypes.data,

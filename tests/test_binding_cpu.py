@@ -99,3 +99,15 @@ def test_batched_calls_check_every_solver_argument():
         K.solve_batched([a, b], [f64(19), f64(12)], [f64(20), f64(12)])
     with pytest.raises(ValueError, match="one rhs"):
         K.solve_batched([a, b], [f64(20)], [f64(20), f64(12)])
+
+
+def test_model_grid_arrays_must_agree_in_length():
+    from kktgen import make_grid
+    g = make_grid(1, 20, 26, 4)
+    with pytest.raises(ValueError, match="per branch"):
+        K.KKTModel(g.n_bus, g.f, g.t[:-1], g.r, g.x, g.gen_bus, g.c2, host_only=True)
+    with pytest.raises(ValueError, match="per branch"):
+        K.KKTModel(g.n_bus, g.f, g.t, g.r, g.x[:-2], g.gen_bus, g.c2, host_only=True)
+    with pytest.raises(ValueError, match="per generator"):
+        K.KKTModel(g.n_bus, g.f, g.t, g.r, g.x, g.gen_bus, g.c2[:-1], host_only=True)
+    K.KKTModel(g.n_bus, g.f, g.t, g.r, g.x, g.gen_bus, g.c2, host_only=True).close()
