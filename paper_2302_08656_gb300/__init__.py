@@ -112,10 +112,28 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
-def plan(rowptr, colidx, **opts) -> dict:
-    """Host-only analysis sizes (no GPU needed)."""
+def _pattern(rowptr, colidx, user_perm=None):
+    """int32 copies of a CSR pattern, checked so that the library reads only
+    inside them: rowptr one-dimensional, starting at 0, non-decreasing, and
+    colidx holding exactly rowptr[-1] entries; a user permutation has one
+    entry per row. (Column ranges, order, symmetry and the permutation's
+    values are checked by the library.)"""
     rp = np.ascontiguousarray(rowptr, dtype=np.int32)
     ci = np.ascontiguousarray(colidx, dtype=np.int32)
+    if rp.ndim != 1 or ci.ndim != 1 or rp.size < 2:
+        raise ValueError("rowptr and colidx must be one-dimensional, rowptr with at least 2 entries")
+    if rp[0] != 0 or np.any(np.diff(rp) < 0):
+        raise ValueError("rowptr must start at 0 and be non-decreasing")
+    if ci.size != int(rp[-1]):
+        raise ValueError("colidx must have rowptr[-1] = %d entries, got %d" % (int(rp[-1]), ci.size))
+    if user_perm is not None and np.asarray(user_perm).size != rp.size - 1:
+        raise ValueError("user_perm must have one entry per row")
+    return rp, ci
+
+
+def plan(rowptr, colidx, **opts) -> dict:
+    """Host-only analysis sizes (no GPU needed)."""
+    rp, ci = _pattern(rowptr, colidx, opts.get("user_perm"))
     o, keep = _opts(**opts)
     out = PlanInfo()
     _check(lib().kkt_plan(rp.size - 1, rp.ctypes.data, ci.ctypes.data, C.byref(o), C.byref(out)), "kkt_plan")
@@ -128,8 +146,7 @@ class KKTSolver:
     def __init__(self, rowptr, colidx, n_primal: int = 0, count: int = 1, **opts):
         """count > 1: a batched context, `count` instances of this pattern
         (arrays are then instance-major: count x nnz values, count x n vectors)."""
-        self._rp = np.ascontiguousarray(rowptr, dtype=np.int32)
-        self._ci = np.ascontiguousarray(colidx, dtype=np.int32)
+        self._rp, self._ci = _pattern(rowptr, colidx, opts.get("user_perm"))
         self.n = self._rp.size - 1
         self.nnz = int(self._rp[-1])
         self.count = int(count)

@@ -111,3 +111,24 @@ def test_model_grid_arrays_must_agree_in_length():
     with pytest.raises(ValueError, match="per generator"):
         K.KKTModel(g.n_bus, g.f, g.t, g.r, g.x, g.gen_bus, g.c2[:-1], host_only=True)
     K.KKTModel(g.n_bus, g.f, g.t, g.r, g.x, g.gen_bus, g.c2, host_only=True).close()
+
+
+def test_pattern_arrays_are_checked_before_the_library_reads_them():
+    from kktgen import KKTPattern, make_grid
+    pat = KKTPattern(make_grid(1, 10, 12, 2))
+    rp, ci = pat.rowptr, pat.colidx
+    with pytest.raises(ValueError, match="rowptr"):
+        K.plan(rp[1:], ci)                                   # does not start at 0
+    with pytest.raises(ValueError, match="colidx must have"):
+        K.plan(rp, ci[:-1])                                  # shorter than rowptr[-1]
+    bad = rp.copy()
+    bad[3], bad[4] = bad[4], bad[3]
+    with pytest.raises(ValueError, match="non-decreasing"):
+        K.plan(bad, ci)
+    with pytest.raises(ValueError, match="one-dimensional"):
+        K.plan(rp.reshape(1, -1), ci)
+    with pytest.raises(ValueError, match="user_perm"):
+        K.plan(rp, ci, user_perm=np.arange(pat.n - 1))
+    with pytest.raises(ValueError, match="colidx must have"):
+        K.KKTSolver(rp, ci[:-1])                             # before any device work
+    assert K.plan(rp, ci)["n"] == pat.n
