@@ -72,17 +72,18 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def _check_tensor(t, numel, name, host=False):
-    """Raise unless t is a contiguous float64 torch tensor of `numel` elements
-    on a CUDA device (host=True: in host memory). Every pointer the library
-    reads or writes is checked here first, so a wrong argument never reaches
-    a kernel."""
+def _check_tensor(t, numel, name, host=False, dtype=None):
+    """Raise unless t is a contiguous torch tensor of `dtype` (float64 by
+    default) with `numel` elements (None: any number) on a CUDA device
+    (host=True: in host memory). Every pointer the library reads or writes is
+    checked here first, so a wrong argument never reaches a kernel."""
     import torch
+    dtype = torch.float64 if dtype is None else dtype
     if not isinstance(t, torch.Tensor):
         raise TypeError("%s must be a torch.Tensor, got %s" % (name, type(t).__name__))
-    if t.dtype != torch.float64:
-        raise ValueError("%s must be float64, got %s" % (name, t.dtype))
-    if t.numel() != numel:
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, str(dtype).replace("torch.", ""), t.dtype))
+    if numel is not None and t.numel() != numel:
         raise ValueError("%s must have %d elements, got %d" % (name, numel, t.numel()))
     if not t.is_contiguous():
         raise ValueError("%s must be contiguous" % name)
@@ -384,7 +385,14 @@ class KKTModel:
 def backward_error_noalloc(rowptr, colidx, vals, x, rhs, r, omega, stream=None):
     """r = b - K x and omega into caller-provided device tensors, allocating
     nothing (rowptr / colidx int32 and vals float64 on the device)."""
+    import torch
+    _check_tensor(rowptr, None, "rowptr", dtype=torch.int32)
     n = rowptr.numel() - 1
+    _check_tensor(colidx, None, "colidx", dtype=torch.int32)
+    _check_tensor(vals, colidx.numel(), "vals")
+    for t, name in ((x, "x"), (rhs, "rhs"), (r, "r")):
+        _check_tensor(t, n, name)
+    _check_tensor(omega, 1, "omega")
     _check(lib().kkt_backward_error_noalloc(n, _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(x), _ptr(rhs),
                                             _ptr(r), _ptr(omega), _stream(stream)), "kkt_backward_error_noalloc")
 

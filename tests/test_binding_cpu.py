@@ -132,3 +132,13 @@ def test_pattern_arrays_are_checked_before_the_library_reads_them():
     with pytest.raises(ValueError, match="colidx must have"):
         K.KKTSolver(rp, ci[:-1])                             # before any device work
     assert K.plan(rp, ci)["n"] == pat.n
+
+
+def test_allocation_free_backward_error_arguments():
+    i32 = lambda k: torch.zeros(k, dtype=torch.int32)        # noqa: E731
+    f64 = lambda k: torch.zeros(k, dtype=torch.float64)      # noqa: E731
+    rp, ci = i32(11), i32(30)
+    with pytest.raises(ValueError, match="rowptr must be int32"):
+        K.backward_error_noalloc(torch.zeros(11, dtype=torch.int64), ci, f64(30), f64(10), f64(10), f64(10), f64(1))
+    with pytest.raises(ValueError, match="rowptr must be on a CUDA device"):
+        K.backward_error_noalloc(rp, ci, f64(30), f64(10), f64(10), f64(10), f64(1))
