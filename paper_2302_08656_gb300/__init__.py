@@ -401,9 +401,11 @@ def debug_pivot_rcp(d, out=None, stream=None):
     """The pivot reciprocal the factorization and backward kernels use for
     1 / d, elementwise over a float64 or float32 device tensor."""
     import torch
-    if d.dtype not in (torch.float64, torch.float32) or not d.is_contiguous():
-        raise ValueError("d must be a contiguous float64 or float32 tensor")
+    if not isinstance(d, torch.Tensor) or d.dtype not in (torch.float64, torch.float32):
+        raise ValueError("d must be a float64 or float32 tensor")
+    _check_tensor(d, d.numel(), "d", dtype=d.dtype)
     out = torch.empty_like(d) if out is None else out
+    _check_tensor(out, d.numel(), "out", dtype=d.dtype)
     prec = 0 if d.dtype == torch.float64 else 1
     _check(lib().kkt_debug_pivot_rcp(_ptr(d), _ptr(out), d.numel(), prec, _stream(stream)), "kkt_debug_pivot_rcp")
     return out

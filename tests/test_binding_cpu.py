@@ -142,3 +142,12 @@ def test_allocation_free_backward_error_arguments():
         K.backward_error_noalloc(torch.zeros(11, dtype=torch.int64), ci, f64(30), f64(10), f64(10), f64(10), f64(1))
     with pytest.raises(ValueError, match="rowptr must be on a CUDA device"):
         K.backward_error_noalloc(rp, ci, f64(30), f64(10), f64(10), f64(10), f64(1))
+
+
+def test_pivot_reciprocal_hook_arguments():
+    with pytest.raises(ValueError, match="float64 or float32"):
+        K.debug_pivot_rcp(torch.zeros(4, dtype=torch.float16))
+    with pytest.raises(ValueError, match="contiguous"):
+        K.debug_pivot_rcp(torch.zeros(8, dtype=torch.float64)[::2])
+    with pytest.raises(ValueError, match="CUDA device"):
+        K.debug_pivot_rcp(torch.zeros(4, dtype=torch.float32))
