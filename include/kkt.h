@@ -271,6 +271,13 @@ kkt_status kkt_get_info(const kkt_ctx *ctx, kkt_info *info);
  * device CSR (d_rowptr n+1, d_colidx and d_vals nnz, FP64), with d_x, d_rhs
  * (n each) as inputs. Outputs: d_r = b - K x (n, device) and d_omega[0] =
  * ||r||_inf / (||K||_inf ||x||_inf + ||b||_inf) (one double, device).
+ * NaN anywhere in K, x or b makes omega NaN (the maxima are taken on the bit
+ * patterns, where NaN sorts above +Inf), so a NaN solution never passes a
+ * tolerance test.
+ * Preconditions: every pointer is memory of the current device; rowptr is
+ * non-decreasing from 0 with rowptr[n] <= nnz, and every column index lies in
+ * [0, n). The kernel checks both as it reads: a row that breaks them is not
+ * read outside its arrays, its r_i is set to NaN, and omega is NaN.
  * The reduction scratch is a fixed 256 KiB array in device memory that the
  * library declares statically; every GPU that loads the library holds it
  * until the process exits. Limit: n <= 8,388,608 rows, else KKT_E_ARG. The
@@ -279,10 +286,11 @@ kkt_status kkt_get_info(const kkt_ctx *ctx, kkt_info *info);
  * capture. Every call uses the same array, so calls that overlap on the GPU
  * (on different streams, or from several threads) race and must be ordered
  * by the caller. Asynchronous on `stream`.
- * Errors: KKT_E_ARG (null pointer, n <= 0, n above the limit), KKT_E_CUDA. */
-kkt_status kkt_backward_error_noalloc(int32_t n, const int32_t *d_rowptr, const int32_t *d_colidx,
-                                      const double *d_vals, const double *d_x, const double *d_rhs,
-                                      double *d_r, double *d_omega, void *stream);
+ * Errors: KKT_E_ARG (null pointer, n <= 0, nnz < 0, n above the limit), KKT_E_CUDA. */
+kkt_status kkt_backward_error_noalloc(int32_t n, int64_t nnz, const int32_t *d_rowptr,
+                                      const int32_t *d_colidx, const double *d_vals,
+                                      const double *d_x, const double *d_rhs, double *d_r,
+                                      double *d_omega, void *stream);
 
 /* ---- GPU model evaluation: the KKT values of one interior-point iterate.
  *

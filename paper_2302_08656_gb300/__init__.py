@@ -384,17 +384,28 @@ class KKTModel:
 
 def backward_error_noalloc(rowptr, colidx, vals, x, rhs, r, omega, stream=None):
     """r = b - K x and omega into caller-provided device tensors, allocating
-    nothing (rowptr / colidx int32 and vals float64 on the device)."""
+    nothing (rowptr / colidx int32 and vals float64, all seven tensors on one
+    CUDA device; the call is made with that device current). The library
+    checks the pattern as it reads it: rows out of range or column indices
+    outside [0, n) give NaN in r and omega, never a read outside the arrays."""
     import torch
     _check_tensor(rowptr, None, "rowptr", dtype=torch.int32)
     n = rowptr.numel() - 1
+    if n < 1:
+        raise ValueError("rowptr must have at least 2 entries")
     _check_tensor(colidx, None, "colidx", dtype=torch.int32)
     _check_tensor(vals, colidx.numel(), "vals")
     for t, name in ((x, "x"), (rhs, "rhs"), (r, "r")):
         _check_tensor(t, n, name)
     _check_tensor(omega, 1, "omega")
-    _check(lib().kkt_backward_error_noalloc(n, _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(x), _ptr(rhs),
-                                            _ptr(r), _ptr(omega), _stream(stream)), "kkt_backward_error_noalloc")
+    dev = rowptr.device
+    for t, name in ((colidx, "colidx"), (vals, "vals"), (x, "x"), (rhs, "rhs"), (r, "r"), (omega, "omega")):
+        if t.device != dev:
+            raise ValueError("%s is on %s, rowptr on %s: all tensors must be on one device" % (name, t.device, dev))
+    with torch.cuda.device(dev):
+        _check(lib().kkt_backward_error_noalloc(n, colidx.numel(), _ptr(rowptr), _ptr(colidx), _ptr(vals), _ptr(x),
+                                                _ptr(rhs), _ptr(r), _ptr(omega), _stream(stream)),
+               "kkt_backward_error_noalloc")
 
 
 def debug_pivot_rcp(d, out=None, stream=None):

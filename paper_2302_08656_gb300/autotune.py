@@ -23,11 +23,46 @@ _CACHE_FILE = os.environ.get("KKT_AUTOTUNE_CACHE", os.path.join(os.path.expandus
                                                                 "kkt_gb300_autotune.json"))
 
 
-def pattern_key(rowptr, colidx, precision: str, count: int) -> str:
+_BUILD_ID = None
+
+
+def build_id() -> str:
+    """Hash of the loaded library file: timings taken with other kernels are
+    not reused."""
+    global _BUILD_ID
+    if _BUILD_ID is None:
+        from ._native import LIB
+        h = hashlib.sha1()
+        try:
+            with open(LIB, "rb") as f:
+                for chunk in iter(lambda: f.read(1 << 20), b""):
+                    h.update(chunk)
+            _BUILD_ID = h.hexdigest()[:16]
+        except OSError:
+            _BUILD_ID = "unbuilt"
+    return _BUILD_ID
+
+
+def device_name() -> str:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.get_device_name()
+    except Exception:
+        pass
+    return "no-device"
+
+
+def pattern_key(rowptr, colidx, precision: str, count: int, device: str | None = None,
+                build: str | None = None) -> str:
+    """Cache key: the pattern, precision and instance count, plus the device
+    the times were taken on and the library build that was timed."""
     h = hashlib.sha1()
     h.update(np.ascontiguousarray(rowptr, dtype=np.int32).tobytes())
     h.update(np.ascontiguousarray(colidx, dtype=np.int32).tobytes())
-    return "%s:%s:%d" % (h.hexdigest(), precision, int(count))
+    dev = device_name() if device is None else device
+    bid = build_id() if build is None else build
+    return "%s:%s:%d:%s:%s" % (h.hexdigest(), precision, int(count), dev, bid)
 
 
 def _load_cache():

@@ -1144,35 +1144,45 @@ __global__ void scal_copy_kernel(int n, const double* __restrict__ x, double* __
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = x[i] * a;
 }
 
+// ||a||_inf and ||a||_2^2. The maximum is taken on the bit patterns of |a_i|
+// (the numeric order for non-negative doubles, with NaN above +Inf), so a NaN
+// entry makes the norm NaN instead of being dropped.
 __global__ void norms_part_kernel(int n, const double* __restrict__ a, double* __restrict__ part)
 {
-    __shared__ double smax[32], ssum[32];
+    __shared__ unsigned long long smax[32];
+    __shared__ double ssum[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    double mx = 0.0, sq = 0.0;
+    unsigned long long mx = 0ull;
+    double sq = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double v = a[i];
-        mx = fmax(mx, fabs(v));
+        mx = umax64(mx, abs_bits(v));
         sq += v * v;
     }
-    mx = warp_max(mx);
+    mx = warp_umax(mx);
     sq = warp_sum(sq);
     if (lane == 0) { smax[wid] = mx; ssum[wid] = sq; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double M = 0.0, S = 0.0;
-        for (int q = 0; q < nw; ++q) { M = fmax(M, smax[q]); S += ssum[q]; }
-        part[2 * blockIdx.x] = M;
+        unsigned long long M = 0ull;
+        double S = 0.0;
+        for (int q = 0; q < nw; ++q) { M = umax64(M, smax[q]); S += ssum[q]; }
+        part[2 * blockIdx.x] = __longlong_as_double((long long)M);
         part[2 * blockIdx.x + 1] = S;
     }
 }
 
 __global__ void norms_final_kernel(int nblk, const double* __restrict__ part, double* __restrict__ out)
 {
-    double M = 0.0, S = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += 32) { M = fmax(M, part[2 * b]); S += part[2 * b + 1]; }
-    M = warp_max(M);
+    unsigned long long M = 0ull;
+    double S = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 32) {
+        M = umax64(M, (unsigned long long)__double_as_longlong(part[2 * b]));
+        S += part[2 * b + 1];
+    }
+    M = warp_umax(M);
     S = warp_sum(S);
-    if (threadIdx.x == 0) { out[0] = M; out[1] = S; }
+    if (threadIdx.x == 0) { out[0] = __longlong_as_double((long long)M); out[1] = S; }
 }
 
 }  // namespace
@@ -1466,7 +1476,7 @@ __global__ void __launch_bounds__(256) omega_final_batched_kernel(int nblk, cons
         const double bmax = __longlong_as_double((long long)red[2][0]);
         const double knorm = __longlong_as_double((long long)stat[inst].knorm_bits);
         const double den = knorm * xmax + bmax;
-        omega[inst] = den > 0.0 ? rmax / den : rmax;
+        omega[inst] = den > 0.0 ? rmax / den : (den == 0.0 ? rmax : den);   // NaN stays NaN
     }
 }
 

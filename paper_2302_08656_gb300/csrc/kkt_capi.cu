@@ -774,7 +774,7 @@ kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double 
     if ((s = norms_host(c, x, &xmax, &xsq, st)) != KKT_OK) return s;
     auto omega_of = [&](double rm, double xm) {
         double den = knorm * xm + bmax;
-        return den > 0 ? rm / den : rm;
+        return den > 0 ? rm / den : (den == 0 ? rm : den);           // a NaN norm gives NaN
     };
     double omega = omega_of(rmax, xmax);
     int total = 0;
@@ -1482,7 +1482,7 @@ kkt_status kkt_residual(kkt_ctx* c, const double* d_rhs, const double* d_x, doub
         if ((s = norms_host(c, d_x, &xm, &xs, st)) != KKT_OK) return s;
         if ((s = norms_host(c, d_rhs, &bm, &bs, st)) != KKT_OK) return s;
         double den = knorm * xm + bm;
-        *omega_out = den > 0 ? rm / den : rm;
+        *omega_out = den > 0 ? rm / den : (den == 0 ? rm : den);     // a NaN norm gives NaN
     }
     return KKT_OK;
 }

@@ -21,6 +21,17 @@ def test_pattern_key_separates_pattern_precision_and_count():
     assert k not in others and len(others) == 3
 
 
+def test_pattern_key_separates_device_and_library_build():
+    a = KKTPattern(make_grid(1, 20, 26, 4))
+    k = autotune.pattern_key(a.rowptr, a.colidx, "fp64", 1, device="GPU A", build="b1")
+    assert k == autotune.pattern_key(a.rowptr, a.colidx, "fp64", 1, device="GPU A", build="b1")
+    assert k != autotune.pattern_key(a.rowptr, a.colidx, "fp64", 1, device="GPU B", build="b1")
+    assert k != autotune.pattern_key(a.rowptr, a.colidx, "fp64", 1, device="GPU A", build="b2")
+    # the defaults: this process's device and the loaded library file
+    assert autotune.pattern_key(a.rowptr, a.colidx, "fp64", 1).endswith(
+        ":%s:%s" % (autotune.device_name(), autotune.build_id()))
+
+
 def test_cached_choice_needs_every_requested_pair():
     entry = {"times": {"8/0": 2.0, "8/2432": 1.5, "16/0": 1.2, "16/2432": 1.7}}
     best, times = autotune.cached_choice(entry, (8, 16), (0, 2432))

@@ -362,3 +362,49 @@ def test_eastern70k_backward_error_through_the_timed_call(precision):
         assert om <= 1e-10, om
         assert info.backward_err <= 1e-10, info.backward_err
     s.close()
+
+
+@pytest.mark.parametrize("bad,where", [(np.nan, "offdiag"), (np.inf, "diag"), (-np.inf, "offdiag")])
+def test_nan_or_inf_in_k_reports_numeric(grid200, bad, where):
+    """A NaN or Inf planted in K's values (a host-made input; nothing faults):
+    the refactorization flags it (kkt_get_info status KKT_E_NUMERIC), refine
+    returns KKT_E_NUMERIC instead of a solution, and the next refactorization
+    with finite values runs normally on the same context."""
+    pat = grid200
+    v_ok = pat.values(pat.point(1, 0, 1e-1))
+    v = v_ok.copy()
+    i = 23
+    lo, hi = pat.rowptr[i], pat.rowptr[i + 1]
+    cols = pat.colidx[lo:hi]
+    j = i if where == "diag" else int(cols[cols != i][0])
+    v[lo + int(np.searchsorted(cols, j))] = bad
+    v[pat.rowptr[j] + int(np.searchsorted(pat.colidx[pat.rowptr[j]:pat.rowptr[j + 1]], i))] = bad
+    b = pat.rhs(1, 0)
+    for precision in ("fp64", "fp32"):
+        s = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=precision)
+        s.refactor(_t(v))
+        torch.cuda.synchronize()
+        assert s.info().status == 8
+        with pytest.raises(K.KKTError) as e:
+            s.refine(_t(b), tol=1e-10)
+        assert e.value.status == 8
+        with pytest.raises(K.KKTError) as e:
+            s.refactor_refine(_t(v), _t(b), tol=1e-10)
+        assert e.value.status == 8
+        x, info = s.refactor_refine(_t(v_ok), _t(b), tol=1e-10)
+        assert info.status == 0
+        assert O.backward_error(pat.rowptr, pat.colidx, v_ok, x.cpu().numpy(), b) <= 1e-10
+        s.close()
+
+
+def test_nan_solution_is_never_reported_converged(grid200):
+    """kkt_residual's omega of a NaN x is NaN (maxima on bit patterns), so a
+    tolerance test on it fails."""
+    pat = grid200
+    v = pat.values(pat.point(1, 2, 1e-3))
+    s = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal)
+    s.refactor(_t(v))
+    x = np.full(pat.n, np.nan)
+    _, om = s.residual(_t(pat.rhs(1, 2)), _t(x))
+    assert not (om <= 1e-10)
+    s.close()
