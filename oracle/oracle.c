@@ -603,8 +603,10 @@ int ora_fgmres(int n, const int *rp, const int *ci, const double *v,
  *   quotient or as x_i * fl(1 / u_jj) (two roundings):
  *   err(l_ij) <= (err(x_i) + |l_ij| err(u_jj)) / |u_jj| + 2 unit |l_ij|
  *
- * gamma_m = m unit / (1 - m unit). A perturbed pivot is an exact constant
- * (err 0; a pivot of magnitude exactly pivot_floor is taken as replaced).
+ * gamma_m = m unit / (1 - m unit). A perturbed pivot is the floor rounded
+ * once to the format (err unit * pivot_floor; a pivot of magnitude exactly
+ * pivot_floor is taken as replaced): FP32 factors hold the FP64 floor rounded
+ * to FP32.
  * eL / eU are aligned with Lx / Ux. The bound is first order: it
  * is meaningful only where err(u_jj) < |u_jj| / 2.
  */
@@ -643,7 +645,8 @@ void ora_lu_error_bound(const ora_lu_t *F, const int *rp, const int *ci, const d
         double ujj = F->Ux[dpos];
         double md = (double)(M[rj] + 1);
         double eujj = E[rj] + (md * unit / (1.0 - md * unit)) * X[rj];
-        if (pivot_floor > 0.0 && fabs(ujj) == pivot_floor) eujj = 0.0;   /* replaced: exact constant */
+        /* replaced pivot: the floor itself, rounded once to the format */
+        if (pivot_floor > 0.0 && fabs(ujj) == pivot_floor) eujj = unit * pivot_floor;
         eU[dpos] = eujj;
         double au = fabs(ujj);
         for (int t = F->Lp[j]; t < F->Lp[j + 1]; t++) {
