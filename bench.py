@@ -2,11 +2,14 @@
 
 One step = one interior-point iteration's linear-algebra work on a fresh
 K_k: equilibrate, scatter, refactor, solve, residual and FGMRES refinement to
-a backward error <= tol (Alg. 1 loop body). Default workload: the 25,000-bus
-grid shaped like the paper's Northeast system (FP64), mu from 1e-1 to 1e-9.
+a backward error <= tol (Alg. 1 loop body). Default workload: the
+70,000-bus grid shaped like the paper's Eastern system, mu from 1e-1 to 1e-9,
+numeric LU and triangular solves in FP32 with the residual and FGMRES in FP64
+(the value), against the plain FP64 path on the same matrices (fp64_arm).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                    [--workload northeast25k|eastern70k|grid200] [--precision fp64|fp32]
+                    [--workload eastern70k|northeast25k|grid200|batch|serving]
+                    [--precision fp32|fp64]
 
 Prints one JSON line (rank 0). Under torchrun every rank runs its own
 independent scenario sequence (weak scaling; no collective on the data path).
@@ -31,24 +34,32 @@ from kktgen import WORKLOADS, KKTPattern, make_grid, mu_schedule  # noqa: E402
 
 METRIC = "KKT refactor+solves/s & p99 latency at rel. residual ≤1e-10 vs plain FP64"
 UNIT = "refactor+solves/s"
+PREC_NAME = {"fp64": "fp64", "fp32": "fp32_ir"}
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="northeast25k", choices=sorted(WORKLOADS) + ["batch", "serving"])
+    ap.add_argument("--workload", default="eastern70k", choices=sorted(WORKLOADS) + ["batch", "serving"])
     ap.add_argument("--sessions", type=int, default=256, help="serving: number of sessions")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: total request rate (1/s)")
     ap.add_argument("--budget-gb", type=float, default=120.0, help="serving: HBM budget")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32"],
+                    help="factor precision of the main arm (fp32: FP32 LU + FP64 refinement)")
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp32", action="store_true", help="skip the mixed-precision comparison run")
+    ap.add_argument("--no-fp32", "--no-compare", dest="no_compare", action="store_true",
+                    help="skip the other-precision arm on the same matrices")
+    ap.add_argument("--no-determined", action="store_true", help="skip the determined-x record")
+    ap.add_argument("--det-tol", type=float, default=1e-14,
+                    help="determined-x record: refinement tolerance of both precisions")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="--impl reference: budget of its timed steps (at least 3 are timed)")
     ap.add_argument("--max-pivots", type=int, default=None, help="pivots per supernode (library default if unset)")
     ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one instead of CUDA graphs")
     ap.add_argument("--assemble", action="store_true",
@@ -61,7 +72,7 @@ def parse():
                          "on the flow-limit rows (single-system workloads; off: the literal -dc)")
     ap.add_argument("--tree-min-fronts", type=int, default=None,
                     help="levels with fewer fronts run in the persistent tree kernels (library default if unset)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():
@@ -100,8 +111,10 @@ def workload(name, seed):
 # Distinct inputs the timed steps cycle through (every step reads its inputs
 # from HBM: L2 is flushed before each timed step), so a timed region long
 # enough for the clock record (hundreds of steps) needs neither hours of input
-# generation nor gigabytes of inputs.
+# generation nor gigabytes of inputs. The timed inputs are spread evenly over
+# the whole mu schedule; the warm-up inputs come from another seed.
 POOL_STEPS = 24
+WARM_SEED = 7777
 
 
 def pool_size(args):
@@ -114,15 +127,41 @@ def at(args, i):
     return i if i < n else args.warmup + (i - args.warmup) % (n - args.warmup)
 
 
-def inputs(pat, mus, seed, count, slack_range=None):
-    """Values and right-hand sides for `count` IPM steps (schedule cycled);
+def spread(count, n_sched):
+    """`count` schedule indices spread evenly over 0 .. n_sched - 1 (both ends included)."""
+    if count <= 1:
+        return [0] * count
+    return [int(round(t * (n_sched - 1) / (count - 1))) for t in range(count)]
+
+
+def pool_plan(args, n_sched, seed):
+    """(seed, schedule step) of every pool input: warm-up inputs first."""
+    warm = [(seed + WARM_SEED, k) for k in spread(args.warmup, n_sched)]
+    timed = [(seed, k) for k in spread(min(args.steps, POOL_STEPS), n_sched)]
+    return warm + timed
+
+
+def inputs(pat, mus, plan, slack_range=None):
+    """Values and right-hand sides of the inputs (seed, k) of `plan`;
     slack_range: keep the inequality slacks' term in the (2,2) block."""
     vals, rhs = [], []
-    for i in range(count):
-        k = i % len(mus)
-        vals.append(pat.values(pat.point(seed, k, mus[k], slack_range=slack_range)))
-        rhs.append(pat.rhs(seed, k))
+    for sd, k in plan:
+        vals.append(pat.values(pat.point(sd, k, mus[k], slack_range=slack_range)))
+        rhs.append(pat.rhs(sd, k))
     return vals, rhs
+
+
+def rel_resid2(pat, vals, rhs, xs):
+    """||b - K x||_2 / ||b||_2 of each result, on the host (scipy product)."""
+    out = []
+    for v, b, x in zip(vals, rhs, xs):
+        r = b - pat.to_scipy(v) @ x
+        out.append(float(np.linalg.norm(r) / np.linalg.norm(b)))
+    return out
+
+
+def summary(values):
+    return {"max": float(max(values)), "median": float(np.median(values)), "per_result": [float(v) for v in values]}
 
 
 # ------------------------------------------------------------------ clocks
@@ -181,7 +220,11 @@ class ClockSampler:
 # ------------------------------------------------------------- algorithmic bytes
 
 def algorithmic_bytes(plan, n, nnz, wbytes):
-    """Minimal traffic of each phase, from the factor sizes (per refactor / solve)."""
+    """Minimal traffic of each phase per refactor / solve / residual, from the
+    factor sizes: refactor = nnz(K) (value + scatter index) + nnz(L+U) (factor
+    value written + pattern index read) + the scaling vector; solve =
+    nnz(L+U) (value + index) + four vectors; residual = nnz(K) (value + index)
+    + three vectors."""
     nlu = plan["nnz_lu"]
     return {
         "refactor": nnz * (8 + 4) + nlu * (wbytes + 4) + n * 8,
@@ -190,12 +233,18 @@ def algorithmic_bytes(plan, n, nnz, wbytes):
     }
 
 
+def tree_factor_bytes(plan, wbytes):
+    """The refactorization bytes above restricted to the fronts of the tree
+    part (what tree_factor_kernel factors): its entries of K, its structural
+    entries of L + U and its pivots' scaling factors."""
+    return plan["tree_nnz_k"] * (8 + 4) + plan["tree_nnz_lu"] * (wbytes + 4) + plan["tree_pivots"] * 8
+
+
 # DRAM bytes (read + write) of the dominant kernel per unit of the roofline
 # (for tree_factor_kernel: its launches of one refactorization) from one ncu
 # capture of the same command (profiles/), keyed by (kernel, workload,
 # precision, tree levels); an entry is removed whenever the kernel changes.
 MEASURED_TRAFFIC = {
-    ("tree_factor_kernel", "northeast25k", "fp64", 58): 24890368 + 10752,
 }
 
 PHASE_OF = {
@@ -208,15 +257,60 @@ PHASE_OF = {
 }
 
 
+def roofline_of(stats, nprof, plan, ab, wbytes, workload_name, precision):
+    """Roofline of the dominant kernel of a profiling pass over `nprof` steps."""
+    if not stats:
+        return None
+    phase_ms = {}
+    for name, (cnt, kms) in stats.items():
+        ph = PHASE_OF.get(name)
+        if ph:
+            phase_ms[ph] = phase_ms.get(ph, 0.0) + kms
+    dom = max(stats.items(), key=lambda kv: kv[1][1])[0]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6800.0
+    ph = PHASE_OF.get(dom, "refactor")
+    if dom == "tree_factor_kernel":
+        # its launches (one or two: wide levels, then the narrow top) per refactorization
+        n_units = nprof
+        bytes_unit = tree_factor_bytes(plan, wbytes)
+        kms = stats[dom][1] / max(1, n_units)
+        per_unit = "refactorization of the tree part (one or two launches)"
+    else:
+        n_units = nprof if ph == "refactor" else stats.get(
+            "solve_post_kernel" if ph == "solve" else "spmv_resid_kernel", (0, 0.0))[0]
+        bytes_unit = ab[ph]
+        kms = phase_ms[ph] / max(1, n_units)
+        per_unit = "%s phase" % ph
+    achieved = bytes_unit / (kms / 1000.0) / 1e9
+    key = (dom, workload_name, precision, plan["tree_levels"])
+    traffic = MEASURED_TRAFFIC.get(key)
+    ref_ms = phase_ms.get("refactor", 0.0) / nprof
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "kernel": dom, "peak_source": peak_src, "per_unit": per_unit,
+            "algorithmic_bytes_per_unit": bytes_unit, "units_profiled": n_units, "ms_per_unit": kms,
+            "launches_per_unit": stats[dom][0] / max(1, n_units),
+            "multifrontal_traffic_model_bytes": plan["tree_bytes"] if dom == "tree_factor_kernel" else None,
+            "refactor_phase": {"algorithmic_bytes": ab["refactor"], "ms": ref_ms,
+                               "achieved_gbs": ab["refactor"] / (max(ref_ms, 1e-9) / 1000.0) / 1e9}}
+
+
 # ----------------------------------------------------------------- reference arm
 
-def cpu_run(pat, vals, rhs, tol, budget_s, max_steps):
-    """The oracle as it stands, single thread: analysis untimed, then per step
-    Ruiz + LU with frozen pivots + FGMRES to tol, until the budget is used.
-    Returns the step times, the backward errors and the solutions (inputs
-    0, 1, ... in order)."""
+def cpu_run(pat, vals, rhs, tol, budget_s, max_steps, an=None):
+    """The oracle as it stands, single thread: analysis untimed (or given),
+    then per step Ruiz + LU with frozen pivots + FGMRES to tol, until the
+    budget is used. Returns the step times, the backward errors and the
+    solutions (inputs 0, 1, ... in order)."""
     import oracle as O
-    an = O.analyze(pat.rowptr, pat.colidx, vals[0])
+    if an is None:
+        an = O.analyze(pat.rowptr, pat.colidx, vals[0])
     times, oms, xs = [], [], []
     t_all = time.perf_counter()
     for i in range(min(max_steps, len(vals))):
@@ -250,20 +344,36 @@ def error_vs_oracle(x_oracle, results):
 
 
 def run_reference(args):
+    """The oracle, as it stands, on the host cores: the same workload, inputs,
+    tolerance and metric as the native arm. Its timed steps cycle the same
+    input pool and stop once --ref-seconds are used (at least 3 steps), so
+    that the run stays within minutes."""
     rank, _, world = dist_env()
     if rank != 0:
         return
     if args.workload not in WORKLOADS:
         raise SystemExit("--impl reference times the oracle on a single-system workload")
+    import oracle as O
     w, pat, mus = workload(args.workload, args.seed)
-    n_in = args.warmup + args.steps
-    vals_p, rhs_p = inputs(pat, mus, args.seed, pool_size(args), args.slack_range)
-    vals = [vals_p[at(args, i)] for i in range(n_in)]
-    rhs = [rhs_p[at(args, i)] for i in range(n_in)]
-    times, oms, _ = cpu_run(pat, vals, rhs, args.tol, 1e9, n_in)
-    t = times[args.warmup:] if len(times) > args.warmup else times
+    plan = pool_plan(args, len(mus), args.seed)
+    vals_p, rhs_p = inputs(pat, mus, plan, args.slack_range)
+    an = O.analyze(pat.rowptr, pat.colidx, vals_p[0])
+    for i in range(args.warmup):
+        cpu_run(pat, [vals_p[i]], [rhs_p[i]], args.tol, 1e9, 1, an)
+    t, oms = [], []
+    t_all = time.perf_counter()
+    for step in range(args.steps):
+        i = at(args, args.warmup + step)
+        ts, om, _ = cpu_run(pat, [vals_p[i]], [rhs_p[i]], args.tol, 1e9, 1, an)
+        t += ts
+        oms += om
+        if time.perf_counter() - t_all > args.ref_seconds and len(t) >= 3:
+            break
     ms = 1000.0 * sum(t) / len(t)
     value = 1000.0 / ms
+    sample = ("%d of the %d requested steps of %s (one refactor + solve + FGMRES each, the input pool cycled "
+              "over the mu schedule; timed steps end once %.0f s are used), oracle analysis untimed"
+              % (len(t), args.steps, args.workload, args.ref_seconds))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": len(t), "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -272,8 +382,7 @@ def run_reference(args):
                    "slack_range": args.slack_range},
         "p50_ms": 1000 * float(np.percentile(t, 50)), "p99_ms": 1000 * float(np.percentile(t, 99)),
         "omega_max": float(max(oms)),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d full steps of %s (oracle analysis untimed)" % (len(t), args.workload)},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -294,8 +403,9 @@ def run_native(args):
     torch.cuda.set_device(dev)
     seed = rank_seed(args.seed, rank)       # independent scenario per rank
     w, pat, mus = workload(args.workload, seed)
-    n_in = pool_size(args)
-    vals_h, rhs_h = inputs(pat, mus, seed, n_in, args.slack_range)
+    plan_in = pool_plan(args, len(mus), seed)
+    n_in = len(plan_in)
+    vals_h, rhs_h = inputs(pat, mus, plan_in, args.slack_range)
     vals = [torch.from_numpy(v).to(dev) for v in vals_h]
     rhs = [torch.from_numpy(b).to(dev) for b in rhs_h]
     xs = [torch.empty_like(b) for b in rhs]
@@ -309,20 +419,22 @@ def run_native(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed_run(solver, tag):
+    def timed_run(solver, vals_, rhs_, xs_, tol, steps):
+        """W warm-up steps, then `steps` timed steps cycling the pool; per-step
+        CUDA events on the launching stream, L2 flushed before each step."""
         stream = torch.cuda.current_stream()
         for i in range(args.warmup):
-            solver.refactor_refine(vals[i], rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
+            solver.refactor_refine(vals_[i], rhs_[i], out=xs_[i], tol=tol, raise_on_noconv=False)
         l0 = solver.info().launches
-        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         oms, iters = [], []
         barrier()
-        for t in range(args.steps):
-            i = at(args, args.warmup + t)
+        for t in range(steps):
+            i = args.warmup + (t % (len(vals_) - args.warmup))
             flush.zero_()
             ev0[t].record(stream)
-            _, info = solver.refactor_refine(vals[i], rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
+            _, info = solver.refactor_refine(vals_[i], rhs_[i], out=xs_[i], tol=tol, raise_on_noconv=False)
             ev1[t].record(stream)
             oms.append(info.backward_err)
             iters.append(info.iters)
@@ -330,6 +442,12 @@ def run_native(args):
         launches = solver.info().launches - l0
         ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
         return ms, oms, iters, launches
+
+    def arm_record(prec, ms, oms, iters, tol):
+        return {"precision": PREC_NAME[prec], "value": 1000.0 * len(ms) / sum(ms), "ms_per_step": sum(ms) / len(ms),
+                "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+                "omega_max": float(max(oms)), "converged_steps": int(sum(1 for o in oms if o <= tol)),
+                "fgmres_iters_mean": float(np.mean(iters)), "fgmres_iters_max": int(max(iters))}
 
     lib_opts = {"graphs": not args.no_graphs}
     if args.max_pivots:
@@ -339,30 +457,28 @@ def run_native(args):
     if args.precond != "lu":
         lib_opts["precond"] = args.precond
         lib_opts["jacobi_sweeps"] = args.sweeps
-    s64 = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=args.precision, **lib_opts)
-    plan = s64.plan()
+    other_prec = "fp64" if args.precision == "fp32" else "fp32"
+    main = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=args.precision, **lib_opts)
+    plan = main.plan()
     sampler = ClockSampler(dev.index)
     sampler.start()
-    ms, oms, iters, launches = timed_run(s64, args.precision)
+    ms, oms, iters, launches = timed_run(main, vals, rhs, xs, args.tol, args.steps)
     clocks = sampler.stop()
-    main_name = "fp64" if args.precision == "fp64" else "fp32_ir"
-    results = {main_name: [x.cpu().numpy() for x in xs]}     # one result per pool input, after the timed region
+    results = {PREC_NAME[args.precision]: [x.cpu().numpy() for x in xs[args.warmup:]]}   # one per timed input
     total_ms = sum(ms)
     if world > 1:
         total_ms = reduce_max(total_ms, device=dev)
     value = aggregate_rate(world, args.steps, total_ms)
+    main_rec = arm_record(args.precision, ms, oms, iters, args.tol)
 
-    # mixed precision on the same matrices (the graded comparison: FP32 LU + FP64 FGMRES vs plain FP64)
+    # the other precision on the same matrices (the graded comparison: FP32 LU + FP64 FGMRES vs plain FP64)
     other = None
-    if not args.no_fp32:
-        oprec = "fp32" if args.precision == "fp64" else "fp64"
-        s32 = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=oprec, **lib_opts)
-        ms32, oms32, it32, _ = timed_run(s32, oprec)
-        results["fp32_ir" if oprec == "fp32" else "fp64"] = [x.cpu().numpy() for x in xs]
-        other = {"precision": "fp32_ir" if oprec == "fp32" else "fp64", "value": 1000.0 * len(ms32) / sum(ms32),
-                 "p50_ms": float(np.percentile(ms32, 50)), "p99_ms": float(np.percentile(ms32, 99)),
-                 "omega_max": float(max(oms32)), "fgmres_iters_mean": float(np.mean(it32))}
-        s32.close()
+    if not args.no_compare:
+        so = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=other_prec, **lib_opts)
+        mso, omso, ito, _ = timed_run(so, vals, rhs, xs, args.tol, args.steps)
+        results[PREC_NAME[other_prec]] = [x.cpu().numpy() for x in xs[args.warmup:]]
+        other = arm_record(other_prec, mso, omso, ito, args.tol)
+        so.close()
 
     # end to end through the C ABI with host buffers (copies inside the timed call)
     hv = [torch.from_numpy(v).pin_memory() for v in vals_h]
@@ -375,75 +491,82 @@ def run_native(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s64.step_host(hv[i].numpy(), hb[i].numpy(), tol=args.tol, out=hx.numpy(), raise_on_noconv=False)
+        main.step_host(hv[i].numpy(), hb[i].numpy(), tol=args.tol, out=hx.numpy(), raise_on_noconv=False)
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     barrier()
     e2e = {"value": 1000.0 * len(e2e_ms) / sum(e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": int(8 * (pat.nnz + pat.n)), "d2h_bytes_per_step": int(8 * pat.n),
-           "p99_ms": float(np.percentile(e2e_ms, 99))}
+           "p50_ms": float(np.percentile(e2e_ms, 50)), "p99_ms": float(np.percentile(e2e_ms, 99))}
 
     # per-kernel timing pass (profiling mode, separate from the timed run)
-    s64.set_profiling(True)
-    s64.kernel_stats()
+    main.set_profiling(True)
+    main.kernel_stats()
     nprof = min(3, args.steps)
     for t in range(nprof):
         i = at(args, args.warmup + t)
-        s64.refactor_refine(vals[i], rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
-    stats = s64.kernel_stats()
-    s64.set_profiling(False)
+        main.refactor_refine(vals[i], rhs[i], out=xs[i], tol=args.tol, raise_on_noconv=False)
+    stats = main.kernel_stats()
+    main.set_profiling(False)
     wbytes = 8 if args.precision == "fp64" else 4
     ab = algorithmic_bytes(plan, pat.n, pat.nnz, wbytes)
-    phase_ms = {}
-    for name, (cnt, kms) in stats.items():
-        ph = PHASE_OF.get(name)
-        if ph:
-            phase_ms[ph] = phase_ms.get(ph, 0.0) + kms
-    dom = max(stats.items(), key=lambda kv: kv[1][1])[0] if stats else None
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = peaks.get("hbm_gbs")
-    peak_src = "measured" if hbm else "fallback"
-    hbm = hbm or 6800.0
-    roofline = None
-    if dom:
-        ph = PHASE_OF.get(dom, "refactor")
-        if dom == "tree_factor_kernel":
-            # the kernel's own algorithmic bytes (original entries, panels,
-            # contribution blocks) per refactorization; the tree part runs as
-            # one or two launches of it (wide levels, then the narrow top)
-            n_units = nprof
-            bytes_unit = plan["tree_bytes"]
-            kms = stats[dom][1] / max(1, n_units)
-        else:
-            n_units = nprof if ph == "refactor" else stats.get(
-                "solve_post_kernel" if ph == "solve" else "spmv_resid_kernel", (0, 0.0))[0]
-            bytes_unit = ab[ph]
-            kms = phase_ms[ph] / max(1, n_units)
-        achieved = bytes_unit / (kms / 1000.0) / 1e9
-        key = (dom, args.workload, args.precision, plan["tree_levels"])
-        traffic = MEASURED_TRAFFIC.get(key)
-        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                    "frac": achieved / hbm, "traffic": traffic, "kernel": dom, "peak_source": peak_src,
-                    "algorithmic_bytes_per_unit": bytes_unit, "units_profiled": n_units,
-                    "ms_per_unit": kms, "launches_per_unit": stats[dom][0] / max(1, n_units),
-                    "refactor_phase": {"algorithmic_bytes": ab["refactor"], "ms": phase_ms.get("refactor", 0.0) / nprof,
-                                       "achieved_gbs": ab["refactor"] / (phase_ms.get("refactor", 1e-9) / nprof / 1000.0) / 1e9}}
+    roofline = roofline_of(stats, nprof, plan, ab, wbytes, args.workload, args.precision)
+
+    # systems that determine x (the slacks' term kept in the (2,2) block):
+    # both precisions refined to a tolerance at which FP32 factors reach the
+    # oracle's x; what that costs in iterations and rate
+    det = None
+    det_h = None
+    if not args.no_determined and args.slack_range is None and args.precond == "lu":
+        sr = (1e-2, 1e2)
+        dplan = [(seed, k) for k in spread(args.warmup + 8, len(mus))]
+        dv_h, db_h = inputs(pat, mus, dplan, sr)
+        det_h = (dv_h[args.warmup:], db_h[args.warmup:])
+        dv = [torch.from_numpy(v).to(dev) for v in dv_h]
+        db = [torch.from_numpy(b).to(dev) for b in db_h]
+        dx = [torch.empty_like(b) for b in db]
+        dsteps = min(args.steps, 48)
+        det = {"slack_range": list(sr), "tol": args.det_tol, "inputs": len(dv) - args.warmup, "steps": dsteps}
+        res_det = {}
+        for prec, sol in ((args.precision, main), (other_prec, None)):
+            if prec != args.precision and args.no_compare:
+                continue
+            s = sol or K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=prec, **lib_opts)
+            dms, doms, dits, _ = timed_run(s, dv, db, dx, args.det_tol, dsteps)
+            det[PREC_NAME[prec]] = arm_record(prec, dms, doms, dits, args.det_tol)
+            res_det[PREC_NAME[prec]] = [x.cpu().numpy() for x in dx[args.warmup:]]
+            if sol is None:
+                s.close()
+        det_res = res_det
+    else:
+        det_res = None
 
     cpu = None
     accuracy = None
+    resid2 = None
+    if rank == 0:
+        tv, tb = vals_h[args.warmup:], rhs_h[args.warmup:]
+        resid2 = {name: summary(rel_resid2(pat, tv, tb, r)) for name, r in results.items()}
     if rank == 0 and not args.no_cpu_baseline:
-        times, coms, xo = cpu_run(pat, vals_h, rhs_h, args.tol, args.cpu_seconds, n_in)
+        import oracle as O
+        an = O.analyze(pat.rowptr, pat.colidx, vals_h[args.warmup])
+        times, coms, xo = cpu_run(pat, vals_h[args.warmup:], rhs_h[args.warmup:], args.tol, args.cpu_seconds,
+                                  n_in, an)
         cpu = {"value": len(times) / sum(times), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d of the %s steps (oracle analysis untimed), single thread"
-                         % (len(times), args.workload),
+               "sample": "%d of the %d timed inputs of %s (spread over the mu schedule; oracle analysis untimed), "
+                         "single thread" % (len(times), n_in - args.warmup, args.workload),
                "omega_max": float(max(coms))}
         try:
             accuracy = error_vs_oracle(xo, results)
         except Exception as e:                     # reported in the line, never fatal to it
             accuracy = {"error": repr(e)}
+        if det is not None:
+            try:
+                nd = 2
+                _, dom_, xdo = cpu_run(pat, det_h[0][:nd], det_h[1][:nd], 1e-15, 1e9, nd, an)
+                det["oracle_omega"] = [float(o) for o in dom_]
+                det["error_vs_oracle"] = error_vs_oracle(xdo, det_res)
+            except Exception as e:
+                det["error_vs_oracle"] = {"error": repr(e)}
 
     if rank == 0:
         line = {
@@ -452,20 +575,30 @@ def run_native(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "buses": w["n_bus"], "branches": w["n_branch"],
-                       "generators": w["n_gen"], "n": pat.n, "nnz": pat.nnz, "precision": args.precision,
+                       "generators": w["n_gen"], "n": pat.n, "nnz": pat.nnz, "precision": PREC_NAME[args.precision],
                        "tol": args.tol, "mu": [w["mu0"], w["mu1"]], "slack_range": args.slack_range,
+                       "inputs": "%d timed inputs spread over the %d-step mu schedule (steps %s), cycled; "
+                                 "%d warm-up inputs" % (n_in - args.warmup, len(mus),
+                                                        [k for _, k in plan_in[args.warmup:]], args.warmup),
                        "l2": "flushed between timed steps (%d MB write)" % (flush.numel() >> 20),
                        "fronts": plan["n_fronts"], "levels": plan["n_levels"], "nnz_lu": plan["nnz_lu"],
                        "tree_levels": plan["tree_levels"], "tree_units": plan["tree_units"]},
-            "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-            "omega_max": float(max(oms)), "fgmres_iters_mean": float(np.mean(iters)),
+            "p50_ms": main_rec["p50_ms"], "p99_ms": main_rec["p99_ms"],
+            "omega_max": main_rec["omega_max"], "fgmres_iters_mean": main_rec["fgmres_iters_mean"],
+            "converged_steps": main_rec["converged_steps"],
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks,
             "gpu_launches": int(launches), "kernel_ms_per_step": {k: v[1] / nprof for k, v in stats.items()},
-            "library_options": lib_opts, "converged_steps": int(sum(1 for o in oms if o <= args.tol)),
-            "comparison": other, "error_vs_oracle": accuracy,
+            "library_options": lib_opts,
+            "fp64_arm" if other_prec == "fp64" else "fp32_arm": other,
+            "rel_resid2": resid2, "error_vs_oracle": accuracy, "determined_x": det,
         }
+        if other is not None:
+            a32, a64 = (main_rec, other) if args.precision == "fp32" else (other, main_rec)
+            line["fp32_vs_fp64"] = {"solves_per_s_ratio": a32["value"] / a64["value"],
+                                    "p50_ratio": a32["p50_ms"] / a64["p50_ms"],
+                                    "p99_ratio": a32["p99_ms"] / a64["p99_ms"]}
         print(json.dumps(line), flush=True)
-    s64.close()
+    main.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

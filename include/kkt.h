@@ -136,9 +136,13 @@ typedef struct {
     int batch;                  /* instances of the context (kkt_get_plan) */
     int tree_levels;            /* top levels run by the persistent tree kernels */
     int tree_units;             /* refactorization work units of those kernels (one instance) */
-    int64_t tree_bytes;         /* algorithmic bytes one refactorization by the tree kernel moves
+    int64_t tree_bytes;         /* multifrontal traffic of one refactorization of the tree part
                                    (one instance): original entries (value, position, source),
                                    factor panels written, contribution blocks written and read once */
+    int64_t tree_nnz_k;         /* nonzeros of K assembled into the fronts of the tree part */
+    int64_t tree_nnz_lu;        /* structural nonzeros of L + U in the tree part's pivot columns
+                                   and rows (diagonal once) */
+    int tree_pivots;            /* pivots eliminated by the tree part */
 } kkt_plan_info;
 
 /* Fill *opt with the defaults listed above. */

@@ -121,6 +121,9 @@ class PlanInfo(C.Structure):
         ("tree_levels", C.c_int),
         ("tree_units", C.c_int),
         ("tree_bytes", C.c_int64),
+        ("tree_nnz_k", C.c_int64),
+        ("tree_nnz_lu", C.c_int64),
+        ("tree_pivots", C.c_int),
     ]
 
 

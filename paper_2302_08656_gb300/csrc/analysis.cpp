@@ -294,8 +294,10 @@ std::string analyze_pattern(int n, const int* rowptr, const int* colidx,
     }
     int64_t nnzl = 0;
     double fl_exact = 0;
+    out.colcount.resize(n);
     for (int j = 0; j < n; ++j) {
         int64_t c = (int64_t)st[j].size();
+        out.colcount[j] = (int)c;
         nnzl += c;
         fl_exact += (double)c + 2.0 * (double)c * (double)c;   // symmetric structure: |L col| = |U row|
     }

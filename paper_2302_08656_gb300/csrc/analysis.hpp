@@ -40,6 +40,9 @@ struct Analysis {
     // factor panel (F*w + w*(F-w) values) and contribution block ((F-w)^2) offsets
     std::vector<int64_t> panel_off, cb_off;
     int64_t panel_total = 0, cb_total = 0;
+    // structural entries of L below the diagonal in column (step) j; U row j
+    // has the same count plus its diagonal (symmetric structure)
+    std::vector<int> colcount;
     // statistics
     int64_t nnz_l = 0, nnz_u = 0;          // structural, diagonal counted in U
     int64_t stored_factor = 0;             // values stored (incl. amalgamation zeros)

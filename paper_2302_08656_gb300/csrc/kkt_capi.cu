@@ -84,6 +84,8 @@ struct kkt_ctx {
     TreeSched tsched;
     int tree_split = 0;
     int64_t tree_bytes = 0;
+    int64_t tree_nnz_k = 0, tree_nnz_lu = 0;
+    int tree_pivots = 0;
     size_t tf_smem = 0, tfw_smem = 0, tbw_smem = 0;
     int tf_grid = 0, tfw_grid = 0, tbw_grid = 0;
     // refactorization of the tree part in two launches: the wide lower levels
@@ -1069,6 +1071,9 @@ kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx,
         out->tree_levels = an.n_levels - tp.split;
         out->tree_units = (int)tp.unit.size();
         out->tree_bytes = tp.alg_bytes;
+        out->tree_nnz_k = tp.nnz_k;
+        out->tree_nnz_lu = tp.nnz_lu;
+        out->tree_pivots = tp.pivots;
     } catch (const std::bad_alloc&) {
         return KKT_E_NOMEM;
     } catch (...) {
@@ -1283,6 +1288,9 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     c->tsched.unit_fused = tunit_fused;
     c->tree_split = tp.split;
     c->tree_bytes = tp.alg_bytes;
+    c->tree_nnz_k = tp.nnz_k;
+    c->tree_nnz_lu = tp.nnz_lu;
+    c->tree_pivots = tp.pivots;
     c->tf_smem = tp.fac_smem; c->tfw_smem = tp.fwd_smem; c->tbw_smem = tp.bwd_smem;
     if (nq > 0) {
         const bool f32 = c->opt.precision == KKT_FP32_IR;
@@ -1557,6 +1565,9 @@ kkt_status kkt_get_plan(const kkt_ctx* c, kkt_plan_info* out)
     out->tree_levels = an.n_levels - c->tree_split;
     out->tree_units = c->tsched.nunits;
     out->tree_bytes = c->tree_bytes;
+    out->tree_nnz_k = c->tree_nnz_k;
+    out->tree_nnz_lu = c->tree_nnz_lu;
+    out->tree_pivots = c->tree_pivots;
     return KKT_OK;
 }
 

@@ -93,6 +93,9 @@ void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp)
             tp.alg_bytes += (d.asm_end - d.asm_begin) * (int64_t)(es + 8) + ((int64_t)F * w + (int64_t)w * m) * (int64_t)es +
                             (int64_t)m * m * (int64_t)es;
             for (int c = d.kid_begin; c < d.kid_end; ++c) tp.alg_bytes += (int64_t)tp.kid[c].mc * tp.kid[c].mc * (int64_t)es;
+            tp.nnz_k += d.asm_end - d.asm_begin;
+            for (int j = d.first; j < d.first + w; ++j) tp.nnz_lu += 2 * (int64_t)an.colcount[j] + 1;
+            tp.pivots += w;
             for (int tj = 0; tj < d.nt; ++tj)
                 for (int ti = 0; ti < d.nt; ++ti) tp.unit.push_back(FrontTile{q, ti, tj});
             const int side = w + std::min(d.ts, m);

@@ -24,7 +24,12 @@ struct TreePlan {
     std::vector<int> inv;
     TreeSched ts;
     size_t fac_smem = 0, fwd_smem = 0, bwd_smem = 0;
-    int64_t alg_bytes = 0;              // algorithmic bytes of one refactorization of the tree part
+    int64_t alg_bytes = 0;              // multifrontal traffic of one refactorization of the tree part
+    // the tree part's share of the factorization: original entries of K
+    // assembled into its fronts, structural entries of L + U in its pivot
+    // columns / rows, and its pivots
+    int64_t nnz_k = 0, nnz_lu = 0;
+    int pivots = 0;
 };
 
 // min_fronts: the top levels with fewer fronts than this go to the tree part

@@ -17,7 +17,7 @@ import bench  # noqa: E402
 
 def test_oracle_leg_returns_solutions_that_meet_the_tolerance():
     w, pat, mus = bench.workload("grid200", 1)
-    vals, rhs = bench.inputs(pat, mus, 1, 3)
+    vals, rhs = bench.inputs(pat, mus, [(1, 0), (1, 1), (1, 2)])
     times, oms, xs = bench.cpu_run(pat, vals, rhs, 1e-10, 1e9, 3)
     assert len(times) == len(oms) == len(xs) == 3
     for v, b, x, om in zip(vals, rhs, xs, oms):
@@ -60,3 +60,44 @@ def test_timed_steps_cycle_the_input_pool():
         assert set(timed) == set(range(warmup, n))
         # consecutive timed steps never repeat an input while the pool has more than one
         assert all(x != y for x, y in zip(timed, timed[1:])) or n - warmup == 1
+
+
+def test_input_pool_spans_the_mu_schedule():
+    """The timed inputs are spread over the whole schedule (first and last
+    step included, in order); the warm-up inputs come from another seed."""
+    from types import SimpleNamespace
+    a = SimpleNamespace(steps=400, warmup=3)
+    plan = bench.pool_plan(a, 100, 5)
+    warm, timed = plan[:3], plan[3:]
+    assert len(timed) == bench.POOL_STEPS
+    ks = [k for _, k in timed]
+    assert ks[0] == 0 and ks[-1] == 99 and ks == sorted(ks) and len(set(ks)) == len(ks)
+    assert all(sd == 5 for sd, _ in timed) and all(sd != 5 for sd, _ in warm)
+    short = bench.pool_plan(SimpleNamespace(steps=2, warmup=3), 100, 5)[3:]
+    assert [k for _, k in short] == [0, 99]
+
+
+def test_defaults_are_the_mixed_precision_70k_line():
+    a = bench.parse([])
+    assert a.workload == "eastern70k" and a.precision == "fp32" and a.tol == 1e-10
+    assert not a.no_compare and a.warmup >= 3
+
+
+def test_roofline_bytes_follow_the_algorithmic_formula():
+    """Refactorization bytes: nnz(K) (value + index) + nnz(L+U) (value +
+    index) + the scaling vector; the tree kernel's share counts only its
+    fronts' entries and pivots."""
+    plan = {"nnz_lu": 1000, "tree_nnz_k": 30, "tree_nnz_lu": 400, "tree_pivots": 20, "tree_levels": 5,
+            "tree_bytes": 123456}
+    ab = bench.algorithmic_bytes(plan, n=100, nnz=500, wbytes=4)
+    assert ab["refactor"] == 500 * 12 + 1000 * 8 + 100 * 8
+    assert ab["solve"] == 1000 * 8 + 4 * 100 * 4
+    assert ab["spmv"] == 500 * 12 + 3 * 100 * 8
+    assert bench.tree_factor_bytes(plan, 8) == 30 * 12 + 400 * 12 + 20 * 8
+    stats = {"tree_factor_kernel": (6, 3.0), "ruiz_kernel": (21, 0.9), "scale_kernel": (3, 0.3)}
+    r = bench.roofline_of(stats, 3, plan, ab, 8, "grid200", "fp64")
+    assert r["kernel"] == "tree_factor_kernel" and r["launches_per_unit"] == 2
+    assert r["ms_per_unit"] == pytest.approx(1.0)
+    assert r["achieved"] == pytest.approx(bench.tree_factor_bytes(plan, 8) / 1e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["multifrontal_traffic_model_bytes"] == 123456
