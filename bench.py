@@ -524,7 +524,7 @@ def run_native(args):
         dv = [torch.from_numpy(v).to(dev) for v in dv_h]
         db = [torch.from_numpy(b).to(dev) for b in db_h]
         dx = [torch.empty_like(b) for b in db]
-        dsteps = min(args.steps, 48)
+        dsteps = min(args.steps, 8)
         det = {"slack_range": list(sr), "tol": args.det_tol, "inputs": len(dv) - args.warmup, "steps": dsteps}
         res_det = {}
         for prec, sol in ((args.precision, main), (other_prec, None)):
