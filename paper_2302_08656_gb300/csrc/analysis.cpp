@@ -509,4 +509,44 @@ std::string analyze_pattern(int n, const int* rowptr, const int* colidx,
     return std::string();
 }
 
+void build_sell(int n, const int* rowptr, const int* colidx, int window, SellPlan& out)
+{
+    const int64_t nnz = rowptr[n];
+    out.nslices = (n + 31) / 32;
+    out.off.assign(out.nslices + 1, 0);
+    out.row.assign((size_t)out.nslices * 32, -1);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    for (int w0 = 0; w0 < n; w0 += window) {
+        const int w1 = std::min(n, w0 + window);
+        std::stable_sort(order.begin() + w0, order.begin() + w1, [&](int a, int b) {
+            return rowptr[a + 1] - rowptr[a] > rowptr[b + 1] - rowptr[b];
+        });
+    }
+    for (int s = 0; s < out.nslices; ++s) {
+        int width = 0;
+        for (int l = 0; l < 32 && s * 32 + l < n; ++l) {
+            const int r = order[s * 32 + l];
+            out.row[(size_t)s * 32 + l] = r;
+            width = std::max(width, rowptr[r + 1] - rowptr[r]);
+        }
+        out.off[s + 1] = out.off[s] + 32 * (int64_t)width;
+    }
+    out.slots = out.off[out.nslices];
+    out.ci.assign(out.slots, -1);
+    out.src.assign(out.slots, -1);
+    out.csr2sell.assign(nnz, -1);
+    for (int s = 0; s < out.nslices; ++s)
+        for (int l = 0; l < 32; ++l) {
+            const int r = out.row[(size_t)s * 32 + l];
+            if (r < 0) continue;
+            for (int p = rowptr[r], k = 0; p < rowptr[r + 1]; ++p, ++k) {
+                const int64_t slot = out.off[s] + 32 * (int64_t)k + l;
+                out.ci[slot] = colidx[p];
+                out.src[slot] = p;
+                out.csr2sell[p] = (int)slot;
+            }
+        }
+}
+
 }  // namespace kktgb

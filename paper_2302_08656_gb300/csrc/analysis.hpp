@@ -65,6 +65,28 @@ struct AnalysisOptions {
 std::string analyze_pattern(int n, const int* rowptr, const int* colidx,
                             const AnalysisOptions& opt, Analysis& out);
 
+// Sliced ELLPACK copy of a CSR pattern (slices of 32 rows, one row per warp
+// lane, entries of a row k = 0, 1, ... at slot off[s] + 32 k + lane, in their
+// CSR order). Rows are sorted by length (longest first, then by index) within
+// windows of `window` rows before they are cut into slices, so a slice's width
+// -- its longest row -- wastes few slots. Fixed for the pattern, like the
+// rest of the analysis; the per-refactor copies of K and D K D live in this
+// layout so that row sums, row maxima and residuals run one lane per row with
+// no cross-lane reduction.
+struct SellPlan {
+    int nslices = 0;
+    int64_t slots = 0;
+    std::vector<int64_t> off;         // nslices + 1 slot offsets (width of slice s = (off[s+1]-off[s]) / 32)
+    std::vector<int> row;             // nslices * 32: row of each lane, -1 for a lane past the last row
+    std::vector<int> ci;              // slots: column index, -1 for padding
+    std::vector<int> src;             // slots: CSR position of the entry, -1 for padding
+    std::vector<int> csr2sell;        // nnz: slot of each CSR position
+};
+
+constexpr int kSellWindow = 4096;
+
+void build_sell(int n, const int* rowptr, const int* colidx, int window, SellPlan& out);
+
 // Quotient-graph minimum-degree ordering (exact external degrees, element
 // absorption). order[k] = node eliminated k-th.
 void min_degree_quotient(int n, const int* rowptr, const int* colidx, std::vector<int>& order);

@@ -80,166 +80,252 @@ __device__ __forceinline__ double pow2_inv_sqrt(double r)
 
 // Exponent k of pow2_inv_sqrt(r) from the bits of a positive normal r:
 // r = (0.5 + M / 2^53) * 2^(E - 1022).
-__device__ __forceinline__ int pow2_inv_sqrt_exp(unsigned long long rb)
+// The same decision for a positive normal number given by its biased
+// exponent E and whether it is an exact power of two (m == 1/2).
+__device__ __forceinline__ int pow2_inv_sqrt_exp_of(int E, bool pow2)
 {
-    const int E = (int)(rb >> 52);
-    if (E == 0) return exp_of_pow2(pow2_inv_sqrt(__longlong_as_double((long long)rb)));   // subnormal
     const int e = E - 1022;
-    const bool half = (rb & 0x000fffffffffffffull) == 0ull;       // m == 1/2
-    if (half) {
+    if (pow2) {
         const int t = 2 - e;
         return t >= 0 ? t / 2 : -((1 - t) / 2);
     }
     return (e & 1) ? (1 - e) / 2 : -(e / 2);
 }
 
+__device__ __forceinline__ int pow2_inv_sqrt_exp(unsigned long long rb)
+{
+    const int E = (int)(rb >> 52);
+    if (E == 0) return exp_of_pow2(pow2_inv_sqrt(__longlong_as_double((long long)rb)));   // subnormal
+    return pow2_inv_sqrt_exp_of(E, (rb & 0x000fffffffffffffull) == 0ull);
+}
+
 // ------------------------------------------------------------------ Ruiz
 
-__global__ void fill_kernel(int n, double* a, double v)
+// ---------------------------------------------------------- equilibration
+
+// Every pass over K runs on its sliced copy (SellPlan): a warp per slice of 32
+// rows, a lane per row, the row's entries k = 0, 1, ... at slots
+// off + 32 k + lane (coalesced across the warp). Row maxima and row sums are
+// then formed by one lane in sequence, with no cross-lane reduction: on this
+// GPU an FP64 warp instruction costs the FP64 pipe the same whether 32 lanes or
+// one do useful work, so the eight-lanes-per-row layout with shuffle sums spent
+// most of its FP64 issue on the reductions.
+constexpr int kSellWarps = 8;                      // slices per 256-thread block
+constexpr unsigned kKeySpecial = 0xffffu;          // subnormal, infinite or NaN entry
+
+// Exponent key of |k|: 0 for zero, (E << 1) | (mantissa != 0) for a normal
+// number of biased exponent E, kKeySpecial otherwise.
+__device__ __forceinline__ unsigned exp_key(double k)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) a[i] = v;
+    const unsigned long long b = abs_bits(k);
+    if (b == 0ull) return 0u;
+    const unsigned E = (unsigned)(b >> 52);
+    if (E == 0u || E == 2047u) return kKeySpecial;
+    return (E << 1) | ((b & 0x000fffffffffffffull) != 0ull ? 1u : 0u);
 }
 
-// One Ruiz iteration, eight lanes per row (rows average ~10 entries):
-// r_i = max_j |d_i k_ij d_j|, d_i <- d_i 2^round(-log2(r_i)/2).
-constexpr int kRowLanes = 8;
-// Rows per thread group: a block covers 32 x kRuizRows rows and every thread
-// keeps the loads of its kRuizRows rows in flight together (the pass is bound
-// by the latency of rp -> (k, j) -> d_j, not by bandwidth), so northeast25k
-// runs in about one wave of blocks.
-constexpr int kRuizRows = 5;
+// Slots a lane loads ahead in the sliced kernels: its next kSellChunk keys
+// (or values) and column indices are loaded first, then the kSellChunk
+// gathers, then the arithmetic, so that every lane keeps that many independent
+// loads in flight instead of walking one key -> column -> gather chain at a time.
+constexpr int kSellChunk = 8;
 
-__device__ __forceinline__ double group_sum(double v)
+// One Ruiz iteration, r_i = max_j |d_i k_ij d_j|, d_i <- d_i 2^round(-log2(r_i)/2),
+// integer-only: every d is a power of two, so |d_i k_ij d_j| is |k_ij| with
+// its exponent raised by e_i + e_j. Iteration 0 first copies K from the
+// caller's CSR values into the sliced copy and writes the keys (load_only:
+// nothing else, d = 1). Later iterations read the 2-byte keys and the column
+// indices only: the row maximum has the largest shifted exponent, and a
+// nonzero mantissa at that exponent is all pow2_inv_sqrt's rounding needs to
+// know (the maximum is an exact power of two only if every entry at the top
+// exponent is). A row with a special key, or a shifted exponent outside the
+// normal range, is redone on the values (scale2_bits on the copy), the
+// arithmetic of the by-value definition. Iteration 0 starts from d = 1 without
+// reading din and writes 1 to din as well as the new d to dout. An iteration
+// that changes no d_i leaves dout equal to din, bit for bit, so both buffers
+// already hold the fixed point and every later iteration returns at once.
+__global__ void __launch_bounds__(256) ruiz_sell_kernel(DevSched s, const double* __restrict__ v, int64_t bs_nnz,
+                                                        double* kcopy, unsigned short* keys, int64_t bs_slot,
+                                                        double* din, double* __restrict__ dout, DevStat* stat,
+                                                        int it, int load_only)
 {
-    for (int o = kRowLanes / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long group_max_u64(unsigned long long v)
-{
-    for (int o = kRowLanes / 2; o > 0; o >>= 1) {
-        const unsigned long long u = __shfl_xor_sync(kFull, v, o);
-        v = u > v ? u : v;
-    }
-    return v;
-}
-
-// Integer-only iteration: every d is a power of two, so |d_i k_ij d_j| is
-// |k_ij| with its exponent raised by e_i + e_j, and the row maximum of
-// non-negative doubles is the maximum of their bit patterns.
-// Iteration 0 starts from d = 1 without reading din and writes 1 to din as
-// well as the new d to dout. An iteration that changes no d_i leaves dout
-// equal to din, bit for bit, so both buffers already hold the fixed point and
-// every later iteration returns at once.
-__global__ void __launch_bounds__(256) ruiz_kernel(int n, int64_t nnz, const int* __restrict__ rp,
-                                                   const int* __restrict__ ci, const double* __restrict__ v,
-                                                   double* din, double* __restrict__ dout, DevStat* stat, int it)
-{
-    // instance blockIdx.y of a batch
-    v += (int64_t)blockIdx.y * nnz;
-    din += (int64_t)blockIdx.y * n;
-    dout += (int64_t)blockIdx.y * n;
-    if (it > 0 && stat[blockIdx.y].ruiz_changed[it - 1] == 0) return;   // uniform over the grid
-    int* changed_cur = &stat[blockIdx.y].ruiz_changed[it];
-    const int sub = threadIdx.x % kRowLanes;
-    const int base = blockIdx.x * (32 * kRuizRows) + threadIdx.x / kRowLanes;
-    int p[kRuizRows], pe[kRuizRows], ei[kRuizRows];
-    unsigned long long m[kRuizRows];
-#pragma unroll
-    for (int k = 0; k < kRuizRows; ++k) {
-        const int row = base + 32 * k;
-        p[k] = row < n ? rp[row] + sub : 0;
-        pe[k] = row < n ? rp[row + 1] : 0;
-        ei[k] = (row < n && it > 0) ? exp_of_pow2(din[row]) : 0;
-        m[k] = 0ull;
-    }
-    // rounds of one entry per row and lane, the loads of all rows together
-    for (;;) {
-        bool any = false;
-        unsigned long long kb[kRuizRows];
-        int cj[kRuizRows];
-#pragma unroll
-        for (int k = 0; k < kRuizRows; ++k) {
-            const bool ok = p[k] < pe[k];
-            any |= ok;
-            kb[k] = ok ? abs_bits(v[p[k]]) : 0ull;
-            cj[k] = ok ? ci[p[k]] : -1;
-        }
-        if (!any) break;
-        int ej[kRuizRows];
-#pragma unroll
-        for (int k = 0; k < kRuizRows; ++k) ej[k] = (cj[k] >= 0 && it > 0) ? exp_of_pow2(din[cj[k]]) : 0;
-#pragma unroll
-        for (int k = 0; k < kRuizRows; ++k)
-            if (cj[k] >= 0) {
-                const unsigned long long a = scale2_bits(kb[k], ei[k] + ej[k]);
-                m[k] = a > m[k] ? a : m[k];
-                p[k] += kRowLanes;
-            }
-    }
+    const int inst = blockIdx.y;
+    if (it > 0 && stat[inst].ruiz_changed[it - 1] == 0) return;   // uniform over the grid
+    v += (int64_t)inst * bs_nnz;
+    kcopy += (int64_t)inst * bs_slot;
+    keys += (int64_t)inst * bs_slot;
+    din += (int64_t)inst * s.n;
+    dout += (int64_t)inst * s.n;
+    const int lane = threadIdx.x & 31;
+    const int slice = blockIdx.x * kSellWarps + (threadIdx.x >> 5);
     int changed = 0;
+    if (slice < s.nslices) {
+        const int row = s.sell_row[slice * 32 + lane];
+        const int64_t o0 = s.sell_off[slice] + lane, o1 = s.sell_off[slice + 1];
+        const int ei = (row >= 0 && it > 0) ? exp_of_pow2(din[row]) : 0;
+        unsigned m = 0u;
+        bool special = false;
+        if (it == 0) {
+            for (int64_t ob = o0; ob < o1; ob += 32 * kSellChunk) {
+                int src[kSellChunk];
 #pragma unroll
-    for (int k = 0; k < kRuizRows; ++k) {
-        const unsigned long long mk = group_max_u64(m[k]);   // every lane of the warp takes part
-        const int row = base + 32 * k;
-        if (row < n && sub == 0) {
-            const int e = mk ? pow2_inv_sqrt_exp(mk) : 0;
-            const unsigned long long dib = (unsigned long long)(ei[k] + 1023) << 52;   // d_i (1 in iteration 0)
+                for (int u = 0; u < kSellChunk; ++u) {
+                    const int64_t o = ob + 32 * u;
+                    src[u] = o < o1 ? s.sell_src[o] : -1;
+                }
+                double k[kSellChunk];
+#pragma unroll
+                for (int u = 0; u < kSellChunk; ++u) k[u] = src[u] >= 0 ? v[src[u]] : 0.0;
+#pragma unroll
+                for (int u = 0; u < kSellChunk; ++u) {
+                    const int64_t o = ob + 32 * u;
+                    if (o < o1) {
+                        const unsigned key = exp_key(k[u]);
+                        kcopy[o] = k[u];
+                        keys[o] = (unsigned short)key;
+                        if (key == kKeySpecial) special = true;
+                        else m = key > m ? key : m;
+                    }
+                }
+            }
+        } else {
+            for (int64_t ob = o0; ob < o1; ob += 32 * kSellChunk) {
+                unsigned key[kSellChunk];
+                int c[kSellChunk];
+#pragma unroll
+                for (int u = 0; u < kSellChunk; ++u) {
+                    const int64_t o = ob + 32 * u;
+                    key[u] = o < o1 ? keys[o] : 0u;
+                    c[u] = o < o1 ? s.sell_ci[o] : -1;
+                }
+                int ej[kSellChunk];
+#pragma unroll
+                for (int u = 0; u < kSellChunk; ++u)
+                    ej[u] = (key[u] != 0u && key[u] != kKeySpecial) ? exp_of_pow2(din[c[u]]) : 0;
+#pragma unroll
+                for (int u = 0; u < kSellChunk; ++u) {
+                    if (key[u] == 0u) continue;
+                    if (key[u] == kKeySpecial) { special = true; continue; }
+                    const int E = (int)(key[u] >> 1) + ei + ej[u];
+                    if (E < 1 || E > 2046) { special = true; continue; }
+                    const unsigned sk = ((unsigned)E << 1) | (key[u] & 1u);
+                    m = sk > m ? sk : m;
+                }
+            }
+        }
+        if (row >= 0 && !load_only) {
+            int e = 0;
+            if (special) {
+                unsigned long long mk = 0ull;
+                for (int64_t o = o0; o < o1; o += 32) {
+                    const int c = s.sell_ci[o];
+                    if (c < 0) continue;
+                    const int ej = it > 0 ? exp_of_pow2(din[c]) : 0;
+                    const unsigned long long a = scale2_bits(abs_bits(kcopy[o]), ei + ej);
+                    mk = a > mk ? a : mk;
+                }
+                e = mk ? pow2_inv_sqrt_exp(mk) : 0;
+            } else if (m) {
+                e = pow2_inv_sqrt_exp_of((int)(m >> 1), (m & 1u) == 0u);
+            }
+            const unsigned long long dib = (unsigned long long)(ei + 1023) << 52;   // d_i (1 in iteration 0)
             dout[row] = __longlong_as_double((long long)scale2_bits(dib, e));
             if (it == 0) din[row] = 1.0;
-            changed |= e != 0;
+            changed = e != 0;
+        } else if (row >= 0) {
+            dout[row] = 1.0;
+            din[row] = 1.0;
         }
     }
     // one flag write per block (a write per row would serialise on one address)
-    if (__syncthreads_or(changed) && threadIdx.x == 0) *changed_cur = 1;
+    if (__syncthreads_or(changed) && threadIdx.x == 0) stat[inst].ruiz_changed[it] = 1;
 }
 
-// D K D in factor precision, a copy of K for the residuals, max |D K D|
-// (static-pivot reference) and ||K||_inf.
+// D K D in factor precision (sliced layout: the assembly reads it through
+// asm_src), max |D K D| (static-pivot reference) and ||K||_inf, whose row sums
+// each lane forms in CSR order.
 template <typename T>
-__global__ void __launch_bounds__(256) scale_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                                                    DevNum<T> nm0)
+__global__ void __launch_bounds__(256) scale_sell_kernel(DevSched s, DevNum<T> nm0)
 {
     const DevNum<T> nm = nm0.at(blockIdx.y);
-    const double* __restrict__ v = nm.vals;
     const double* __restrict__ d = nm.d;
-    T* __restrict__ sv = nm.sv;
-    double* __restrict__ kcopy = nm.kcopy;
-    DevStat* stat = nm.stat;
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
-    const int sub = threadIdx.x % kRowLanes;
     const int lane = threadIdx.x & 31;
-    double rsum = 0.0;
-    unsigned long long amb = 0ull;
-    if (row < n) {
-        const int ei = exp_of_pow2(d[row]);
-        for (int p = rp[row] + sub; p < rp[row + 1]; p += kRowLanes) {
-            const double k = v[p];
-            const unsigned long long ab = scale2_bits(abs_bits(k), ei + exp_of_pow2(d[ci[p]]));
-            const unsigned long long sb = ab | ((unsigned long long)__double_as_longlong(k) & 0x8000000000000000ull);
-            sv[p] = (T)__longlong_as_double((long long)sb);         // d_i k d_j, exact
-            kcopy[p] = k;
-            amb = ab > amb ? ab : amb;
-            rsum += fabs(k);
+    const int slice = blockIdx.x * kSellWarps + (threadIdx.x >> 5);
+    unsigned long long amb = 0ull, rsb = 0ull;
+    if (slice < s.nslices) {
+        const int row = s.sell_row[slice * 32 + lane];
+        const int64_t o0 = s.sell_off[slice] + lane, o1 = s.sell_off[slice + 1];
+        const int ei = row >= 0 ? exp_of_pow2(d[row]) : 0;
+        double rsum = 0.0;
+        for (int64_t ob = o0; ob < o1; ob += 32 * kSellChunk) {
+            double k[kSellChunk];
+            int c[kSellChunk];
+#pragma unroll
+            for (int u = 0; u < kSellChunk; ++u) {
+                const int64_t o = ob + 32 * u;
+                c[u] = o < o1 ? s.sell_ci[o] : -1;
+                k[u] = o < o1 ? nm.kcopy[o] : 0.0;
+            }
+            int ej[kSellChunk];
+#pragma unroll
+            for (int u = 0; u < kSellChunk; ++u) ej[u] = c[u] >= 0 ? exp_of_pow2(d[c[u]]) : 0;
+#pragma unroll
+            for (int u = 0; u < kSellChunk; ++u) {
+                const int64_t o = ob + 32 * u;
+                if (o < o1) {
+                    T out = T(0);
+                    if (c[u] >= 0) {
+                        const unsigned long long ab = scale2_bits(abs_bits(k[u]), ei + ej[u]);
+                        const unsigned long long sb =
+                            ab | ((unsigned long long)__double_as_longlong(k[u]) & 0x8000000000000000ull);
+                        out = (T)__longlong_as_double((long long)sb);     // d_i k d_j, exact
+                        amb = ab > amb ? ab : amb;
+                        rsum += fabs(k[u]);
+                    }
+                    nm.sv[o] = out;
+                }
+            }
         }
+        rsb = abs_bits(rsum);
     }
-    rsum = group_sum(rsum);          // row sum of |K| (lanes of one row)
-    // maxima of non-negative doubles as maxima of their bit patterns (integer
-    // shuffles: FP64 max instructions would queue on the slow FP64 pipe)
+    // maxima of non-negative doubles as maxima of their bit patterns (integer shuffles)
     amb = warp_umax(amb);
-    const unsigned long long rsb = warp_umax(abs_bits(rsum));     // largest row sum in the warp
-    __shared__ unsigned long long s_am[8], s_rs[8];
+    rsb = warp_umax(rsb);
+    __shared__ unsigned long long s_am[kSellWarps], s_rs[kSellWarps];
     const int wid = threadIdx.x >> 5;
     if (lane == 0) { s_am[wid] = amb; s_rs[wid] = rsb; }
     __syncthreads();
     // one atomic per block and quantity (per-row atomics serialise on one address)
     if (threadIdx.x == 0) {
         unsigned long long a = 0ull, r = 0ull;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a = umax64(a, s_am[q]); r = umax64(r, s_rs[q]); }
-        atomicMax(&stat->amax_bits, a);
-        atomicMax(&stat->knorm_bits, r);
+        for (int q = 0; q < kSellWarps; ++q) { a = umax64(a, s_am[q]); r = umax64(r, s_rs[q]); }
+        atomicMax(&nm.stat->amax_bits, a);
+        atomicMax(&nm.stat->knorm_bits, r);
     }
+}
+
+// sum_k kv[o_k] x[c_k] over the slots of one lane's row, in slot (= CSR) order
+__device__ __forceinline__ double sell_row_dot(const DevSched& s, const double* __restrict__ kv,
+                                               const double* __restrict__ x, int64_t o0, int64_t o1)
+{
+    double acc = 0.0;
+    for (int64_t ob = o0; ob < o1; ob += 32 * kSellChunk) {
+        double k[kSellChunk];
+        int c[kSellChunk];
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) {
+            const int64_t o = ob + 32 * u;
+            c[u] = o < o1 ? s.sell_ci[o] : -1;
+            k[u] = o < o1 ? kv[o] : 0.0;
+        }
+        double xv[kSellChunk];
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u) xv[u] = c[u] >= 0 ? x[c[u]] : 0.0;
+#pragma unroll
+        for (int u = 0; u < kSellChunk; ++u)
+            if (c[u] >= 0) acc = fma(k[u], xv[u], acc);
+    }
+    return acc;
 }
 
 // ---------------------------------------------------------- front kernels
@@ -1071,18 +1157,18 @@ __global__ void __launch_bounds__(128) solve_bwd_cta_kernel(DevSched s, DevNum<T
 
 // ---------------------------------------------------------- FP64 vectors
 
-__global__ void __launch_bounds__(256) spmv_resid_kernel(int n, const int* __restrict__ rp,
-                                                         const int* __restrict__ ci, const double* __restrict__ v,
-                                                         const double* __restrict__ x, const double* __restrict__ b,
-                                                         double* __restrict__ r)
+// y = b - K x (b != nullptr) or y = K x on the sliced copy of K, a lane per
+// row summing its entries in CSR order.
+__global__ void __launch_bounds__(256) spmv_sell_kernel(DevSched s, const double* __restrict__ kv,
+                                                        const double* __restrict__ x, const double* __restrict__ b,
+                                                        double* __restrict__ y)
 {
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) / kRowLanes;
-    const int sub = threadIdx.x % kRowLanes;
-    double s = 0.0;
-    if (row < n)
-        for (int p = rp[row] + sub; p < rp[row + 1]; p += kRowLanes) s += v[p] * x[ci[p]];
-    s = group_sum(s);
-    if (row < n && sub == 0) r[row] = b ? b[row] - s : s;
+    const int lane = threadIdx.x & 31;
+    const int slice = blockIdx.x * kSellWarps + (threadIdx.x >> 5);
+    if (slice >= s.nslices) return;
+    const int row = s.sell_row[slice * 32 + lane];
+    const double acc = sell_row_dot(s, kv, x, s.sell_off[slice] + lane, s.sell_off[slice + 1]);
+    if (row >= 0) y[row] = b ? b[row] - acc : acc;
 }
 
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs
@@ -1196,15 +1282,22 @@ cudaError_t launch_zero_stat(DevStat* stat, cudaStream_t st)
     return cudaMemsetAsync(stat, 0, sizeof(DevStat), st);
 }
 
-cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double* dtmp, int iters,
-                        DevStat* stat, double** d_final, int batch, cudaStream_t st)
+static inline int sell_blocks(const DevSched& s) { return cdiv(s.nslices, kSellWarps); }
+
+cudaError_t launch_ruiz(const DevSched& s, const double* vals, int64_t bs_nnz, double* kcopy, unsigned short* keys,
+                        int64_t bs_slot, double* d, double* dtmp, int iters, DevStat* stat, double** d_final,
+                        int batch, cudaStream_t st)
 {
-    if (iters == 0) fill_kernel<<<cdiv((int64_t)s.n * batch, 256), 256, 0, st>>>((int)((int64_t)s.n * batch), d, 1.0);
+    const dim3 grid(sell_blocks(s), batch);
     double* a = d;
     double* b = dtmp;
+    if (iters == 0) {
+        ruiz_sell_kernel<<<grid, 256, 0, st>>>(s, vals, bs_nnz, kcopy, keys, bs_slot, a, b, stat, 0, 1);
+        *d_final = a;
+        return cudaGetLastError();
+    }
     for (int it = 0; it < iters; ++it) {
-        ruiz_kernel<<<dim3(cdiv(s.n, 32 * kRuizRows), batch), 256, 0, st>>>(s.n, s.nnz, s.rowptr, s.colidx, vals, a,
-                                                                            b, stat, it);
+        ruiz_sell_kernel<<<grid, 256, 0, st>>>(s, vals, bs_nnz, kcopy, keys, bs_slot, a, b, stat, it, 0);
         double* t = a; a = b; b = t;
     }
     *d_final = a;
@@ -1215,7 +1308,7 @@ template <typename T>
 cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d, int batch, cudaStream_t st)
 {
     (void)d;
-    scale_kernel<T><<<dim3(cdiv((int64_t)s.n * kRowLanes, 256), batch), 256, 0, st>>>(s.n, s.rowptr, s.colidx, nm);
+    scale_sell_kernel<T><<<dim3(sell_blocks(s), batch), 256, 0, st>>>(s, nm);
     return cudaGetLastError();
 }
 
@@ -1344,17 +1437,16 @@ cudaError_t launch_solve_bwd_cta(const DevSched& s, const DevNum<T>& nm, const i
     return cudaGetLastError();
 }
 
-cudaError_t launch_spmv_resid(int n, const int* rp, const int* ci, const double* v, const double* x,
-                              const double* b, double* r, cudaStream_t st)
+cudaError_t launch_spmv_resid(const DevSched& s, const double* kv, const double* x, const double* b, double* r,
+                              cudaStream_t st)
 {
-    spmv_resid_kernel<<<cdiv((int64_t)n * kRowLanes, 256), 256, 0, st>>>(n, rp, ci, v, x, b, r);
+    spmv_sell_kernel<<<sell_blocks(s), 256, 0, st>>>(s, kv, x, b, r);
     return cudaGetLastError();
 }
 
-cudaError_t launch_spmv(int n, const int* rp, const int* ci, const double* v, const double* x, double* y,
-                        cudaStream_t st)
+cudaError_t launch_spmv(const DevSched& s, const double* kv, const double* x, double* y, cudaStream_t st)
 {
-    spmv_resid_kernel<<<cdiv((int64_t)n * kRowLanes, 256), 256, 0, st>>>(n, rp, ci, v, x, nullptr, y);
+    spmv_sell_kernel<<<sell_blocks(s), 256, 0, st>>>(s, kv, x, nullptr, y);
     return cudaGetLastError();
 }
 
@@ -1397,45 +1489,36 @@ cudaError_t launch_norms(int n, const double* a, double* out, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// Batched residual and backward error: grid (resid_blocks(n), batch), eight
-// lanes per row (rows hold ~10 entries), kResidRows rows per block, so that
-// thousands of blocks keep enough loads in flight. Maxima of non-negative
-// doubles are taken on their bit patterns (integer pipes: FP64 compares are
-// slow on this GPU); ||K||_inf comes from the refactorization's statistics.
-// Each block stores max |r|, |x|, |b| of its rows (as bits) in its slot of
-// `part`; omega_final_batched reduces the slots.
-
-__global__ void __launch_bounds__(256) resid_omega_part_kernel(int n, int64_t nnz, const int* __restrict__ rp,
-                                                               const int* __restrict__ ci,
-                                                               const double* __restrict__ kv,
-                                                               const double* __restrict__ x,
+// Batched residual and backward error: grid (slice blocks, batch), a lane per
+// row on the sliced copy of K. Maxima of non-negative doubles are taken on
+// their bit patterns (integer pipes; NaN sorts above +Inf, so it reaches
+// omega); ||K||_inf comes from the refactorization's statistics. Each block
+// stores max |r|, |x|, |b| of its rows (as bits) in its slot of `part`;
+// omega_final_batched reduces the slots.
+__global__ void __launch_bounds__(256) resid_omega_part_kernel(DevSched s, const double* __restrict__ kv,
+                                                               int64_t bs_slot, const double* __restrict__ x,
                                                                const double* __restrict__ b, double* __restrict__ r,
                                                                unsigned long long* __restrict__ part)
 {
-    __shared__ unsigned long long red[3][8];
+    __shared__ unsigned long long red[3][kSellWarps];
     const int inst = blockIdx.y;
-    kv += (int64_t)inst * nnz;
+    const int n = s.n;
+    kv += (int64_t)inst * bs_slot;
     x += (int64_t)inst * n;
     b += (int64_t)inst * n;
     r += (int64_t)inst * n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int sub = threadIdx.x % kRowLanes;
-    const int row0 = blockIdx.x * kResidRows;
-    constexpr int kPass = 256 / kRowLanes;                          // rows per pass of the block
+    const int slice = blockIdx.x * kSellWarps + wid;
     unsigned long long mr = 0ull, mx = 0ull, mb = 0ull;
-#pragma unroll
-    for (int q = 0; q < kResidRows / kPass; ++q) {
-        const int row = row0 + q * kPass + threadIdx.x / kRowLanes;
-        double sacc = 0.0;
-        if (row < n)
-            for (int p = rp[row] + sub; p < rp[row + 1]; p += kRowLanes) sacc += kv[p] * x[ci[p]];
-        sacc = group_sum(sacc);
-        if (row < n && sub == 0) {
-            const double ri = b[row] - sacc;
+    if (slice < s.nslices) {
+        const int row = s.sell_row[slice * 32 + lane];
+        const double acc = sell_row_dot(s, kv, x, s.sell_off[slice] + lane, s.sell_off[slice + 1]);
+        if (row >= 0) {
+            const double ri = b[row] - acc;
             r[row] = ri;
-            mr = umax64(mr, abs_bits(ri));
-            mx = umax64(mx, abs_bits(x[row]));
-            mb = umax64(mb, abs_bits(b[row]));
+            mr = abs_bits(ri);
+            mx = abs_bits(x[row]);
+            mb = abs_bits(b[row]);
         }
     }
     mr = warp_umax(mr); mx = warp_umax(mx); mb = warp_umax(mb);
@@ -1443,7 +1526,7 @@ __global__ void __launch_bounds__(256) resid_omega_part_kernel(int n, int64_t nn
     __syncthreads();
     if (threadIdx.x < 3) {
         unsigned long long m = 0ull;
-        for (int q = 0; q < 8; ++q) m = umax64(m, red[threadIdx.x][q]);
+        for (int q = 0; q < kSellWarps; ++q) m = umax64(m, red[threadIdx.x][q]);
         part[((int64_t)inst * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = m;
     }
 }
@@ -1480,13 +1563,13 @@ __global__ void __launch_bounds__(256) omega_final_batched_kernel(int nblk, cons
     }
 }
 
-cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci, const double* kvals,
-                               const double* x, const double* b, double* r, double* part, const DevStat* stat,
-                               double* omega, int batch, cudaStream_t st)
+cudaError_t launch_resid_omega(const DevSched& s, const double* kvals, int64_t bs_slot, const double* x,
+                               const double* b, double* r, double* part, const DevStat* stat, double* omega,
+                               int batch, cudaStream_t st)
 {
-    const int nblk = resid_blocks(n);
+    const int nblk = sell_blocks(s);
     unsigned long long* up = reinterpret_cast<unsigned long long*>(part);
-    resid_omega_part_kernel<<<dim3(nblk, batch), 256, 0, st>>>(n, nnz, rp, ci, kvals, x, b, r, up);
+    resid_omega_part_kernel<<<dim3(nblk, batch), 256, 0, st>>>(s, kvals, bs_slot, x, b, r, up);
     omega_final_batched_kernel<<<batch, 256, 0, st>>>(nblk, up, stat, omega);
     return cudaGetLastError();
 }

@@ -30,6 +30,14 @@ struct DevSched {
     const int64_t* inv_off = nullptr; // per panel-class front: offset of its children's gather maps
     const int* inv = nullptr;         // per (front, child): parent CB row -> child CB row or -1
     const int64_t* f12_off = nullptr; // per panel-class front: offset of its assembled pivot rows
+    // sliced ELLPACK copy of K's pattern (SellPlan): per-refactor copies of K
+    // and D K D are stored in this layout; asm_src indexes it
+    int nslices = 0;
+    int64_t slots = 0;
+    const int64_t* sell_off = nullptr;    // nslices + 1
+    const int* sell_row = nullptr;        // nslices * 32 (-1: no row)
+    const int* sell_ci = nullptr;         // slots (-1: padding)
+    const int* sell_src = nullptr;        // slots: CSR position (-1: padding)
 };
 
 // Device-side counters of one context, cleared at the start of each refactor.
@@ -45,11 +53,12 @@ struct DevStat {
 // Per-context numeric buffers.
 template <typename T>
 struct DevNum {
-    const double* vals = nullptr;     // K values of the current refactor (caller memory)
-    double* kcopy = nullptr;          // library-owned copy of K (residuals use it after the call)
+    const double* vals = nullptr;     // K values of the current refactor (caller memory, CSR order)
+    double* kcopy = nullptr;          // library-owned copy of K in the sliced layout (residuals use it)
+    unsigned short* keys = nullptr;   // per slot: exponent key of |k| (equilibration passes)
     double* d = nullptr;              // equilibration factors (n)
     double* dtmp = nullptr;           // ping-pong buffer (n)
-    T* sv = nullptr;                  // D K D in factor precision (nnz)
+    T* sv = nullptr;                  // D K D in factor precision (sliced layout, slots)
     T* panel = nullptr;               // factor panels
     T* cb = nullptr;                  // contribution blocks
     T* vec = nullptr;                 // step-space solve vector (n)
@@ -58,16 +67,17 @@ struct DevNum {
     DevStat* stat = nullptr;
     double pivot_eps = 1e-14;
     // element strides between consecutive instances of a batch (0 for one instance)
-    int64_t bs_nnz = 0, bs_n = 0, bs_panel = 0, bs_cb = 0, bs_cbv = 0, bs_f12 = 0;
+    int64_t bs_nnz = 0, bs_slot = 0, bs_n = 0, bs_panel = 0, bs_cb = 0, bs_cbv = 0, bs_f12 = 0;
     __host__ __device__ DevNum at(int b) const
     {
         DevNum r = *this;
         if (b) {
             r.vals += b * bs_nnz;
-            r.kcopy += b * bs_nnz;
+            r.kcopy += b * bs_slot;
+            r.keys += b * bs_slot;
             r.d += b * bs_n;
             r.dtmp += b * bs_n;
-            r.sv += b * bs_nnz;
+            r.sv += b * bs_slot;
             r.panel += b * bs_panel;
             r.cb += b * bs_cb;
             r.vec += b * bs_n;
@@ -211,8 +221,12 @@ constexpr int kTreeStage = 2048;       // staged child contribution entries per 
 constexpr int kCtrHead = 4;
 
 // Launchers (all asynchronous on `st`).
-cudaError_t launch_ruiz(const DevSched& s, const double* vals, double* d, double* dtmp, int iters,
-                        DevStat* stat, double** d_final, int batch, cudaStream_t st);
+// Equilibration: iteration 0 copies K (caller's CSR values, instance stride
+// bs_nnz) into the sliced copy kcopy with its exponent keys (stride bs_slot);
+// iters = 0 makes only that copy and sets d = 1.
+cudaError_t launch_ruiz(const DevSched& s, const double* vals, int64_t bs_nnz, double* kcopy, unsigned short* keys,
+                        int64_t bs_slot, double* d, double* dtmp, int iters, DevStat* stat, double** d_final,
+                        int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_scale(const DevSched& s, const DevNum<T>& nm, const double* d, int batch, cudaStream_t st);
 template <typename T>
@@ -249,20 +263,19 @@ cudaError_t launch_solve_bwd(const DevSched& s, const DevNum<T>& nm, const int* 
                              int max_front, int max_w, int batch, cudaStream_t st);
 template <typename T>
 cudaError_t launch_solve_post(const DevSched& s, const DevNum<T>& nm, double* x, int batch, cudaStream_t st);
-// per instance: r = b - K x, omega = ||r||_inf / (||K||_inf ||x||_inf + ||b||_inf) into omega[b];
-// part holds batch * resid_blocks(n) * 4 doubles
-constexpr int kResidRows = 64;         // rows per block of the residual kernel
+// per instance: r = b - K x, omega = ||r||_inf / (||K||_inf ||x||_inf + ||b||_inf) into omega[b],
+// K the sliced copy (instance stride bs_slot); part holds batch * resid_blocks(n) * 4 doubles
+constexpr int kResidRows = 64;         // rows per block of the partial-maxima buffer (an upper bound)
 inline int resid_blocks(int n) { return (n + kResidRows - 1) / kResidRows; }
 // ||K||_inf of every instance is read from stat[inst].knorm_bits (the refactorization's scaling pass)
-cudaError_t launch_resid_omega(int n, int64_t nnz, const int* rp, const int* ci, const double* kvals,
-                               const double* x, const double* b, double* r, double* part, const DevStat* stat,
-                               double* omega, int batch, cudaStream_t st);
+cudaError_t launch_resid_omega(const DevSched& s, const double* kvals, int64_t bs_slot, const double* x,
+                               const double* b, double* r, double* part, const DevStat* stat, double* omega,
+                               int batch, cudaStream_t st);
 
-// FP64 vector kernels for the residual and FGMRES.
-cudaError_t launch_spmv_resid(int n, const int* rp, const int* ci, const double* v, const double* x,
-                              const double* b, double* r, cudaStream_t st);
-cudaError_t launch_spmv(int n, const int* rp, const int* ci, const double* v, const double* x,
-                        double* y, cudaStream_t st);
+// FP64 vector kernels for the residual and FGMRES (kv: one instance's sliced copy of K).
+cudaError_t launch_spmv_resid(const DevSched& s, const double* kv, const double* x, const double* b, double* r,
+                              cudaStream_t st);
+cudaError_t launch_spmv(const DevSched& s, const double* kv, const double* x, double* y, cudaStream_t st);
 // out[k] = <V_k, w> for k < nv (V column-major with leading dimension ldv); out zeroed inside
 cudaError_t launch_multidot(int n, const double* V, int64_t ldv, int nv, const double* w, double* out,
                             cudaStream_t st);

@@ -65,6 +65,7 @@ struct kkt_ctx {
     int n = 0, n_primal = 0;
     int batch = 1;                   // numeric instances sharing this analysis
     int64_t nnz = 0;
+    int64_t slots = 0;               // sliced copy of K (SellPlan): slots per instance
     std::vector<LevelGroup> levels;
     int64_t scratch_stride = 0;      // panel scratch per CTA (global fallback)
     int max_panel_global = 0;
@@ -107,7 +108,7 @@ struct kkt_ctx {
     double* r = nullptr;
     double* red = nullptr;           // reduction scratch + small vectors
     double* h_dev = nullptr;         // small vectors on device
-    double* kvals = nullptr;         // copy of K made by the last refactor
+    double* kvals = nullptr;         // copy of K made by the last refactor (sliced layout)
     double* stage_vals = nullptr;    // device staging for kkt_step_host
     double* stage_b = nullptr;
     double* stage_x = nullptr;
@@ -554,7 +555,8 @@ kkt_status refactor_t(kkt_ctx* c, const double* d_vals, cudaStream_t st)
     double* dfin = nullptr;
     {
         Launch L(c, st, KK_RUIZ, c->opt.ruiz_iters > 0 ? c->opt.ruiz_iters : 1);
-        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->d_a, c->d_b, c->opt.ruiz_iters, c->stat, &dfin, c->batch, st));
+        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->nnz, nm.kcopy, nm.keys, c->slots, c->d_a, c->d_b, c->opt.ruiz_iters,
+                             c->stat, &dfin, c->batch, st));
     }
     c->d_final = dfin;
     nm.d = dfin;
@@ -617,7 +619,8 @@ kkt_status refactor_solve_t(kkt_ctx* c, const double* d_vals, const double* b, d
     double* dfin = nullptr;
     {
         Launch L(c, st, KK_RUIZ, c->opt.ruiz_iters > 0 ? c->opt.ruiz_iters : 1);
-        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->d_a, c->d_b, c->opt.ruiz_iters, c->stat, &dfin, B, st));
+        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->nnz, nm.kcopy, nm.keys, c->slots, c->d_a, c->d_b, c->opt.ruiz_iters,
+                             c->stat, &dfin, B, st));
     }
     c->d_final = dfin;
     nm.d = dfin;
@@ -760,9 +763,7 @@ kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double 
 {
     const int n = c->n;
     const int m = c->opt.restart;
-    const double* K = c->kvals + (int64_t)inst * c->nnz;
-    const int* rp = c->sched.rowptr;
-    const int* ci = c->sched.colidx;
+    const double* K = c->kvals + (int64_t)inst * c->slots;
     kkt_status s;
     double knorm = 0.0;
     if ((s = knorm_of(c, st, &knorm, inst)) != KKT_OK) return s;
@@ -770,7 +771,7 @@ kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double 
     if ((s = norms_host(c, b, &bmax, &bsq, st)) != KKT_OK) return s;
     {
         Launch L(c, st, KK_SPMV, 1);
-        KKT_CUDA(launch_spmv_resid(n, rp, ci, K, x, b, c->r, st));
+        KKT_CUDA(launch_spmv_resid(c->sched, K, x, b, c->r, st));
     }
     if ((s = norms_host(c, c->r, &rmax, &rsq, st)) != KKT_OK) return s;
     if ((s = norms_host(c, x, &xmax, &xsq, st)) != KKT_OK) return s;
@@ -801,7 +802,7 @@ kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double 
             if ((s = do_precond(c, vj, zj, st, inst)) != KKT_OK) return s;
             {
                 Launch L(c, st, KK_SPMV, 1);
-                KKT_CUDA(launch_spmv(n, rp, ci, K, zj, c->w, st));
+                KKT_CUDA(launch_spmv(c->sched, K, zj, c->w, st));
             }
             // classical Gram-Schmidt, twice (CGS2)
             double* h1 = hd + 8;
@@ -872,7 +873,7 @@ kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double 
         }
         {
             Launch L(c, st, KK_SPMV, 1);
-            KKT_CUDA(launch_spmv_resid(n, rp, ci, K, x, b, c->r, st));
+            KKT_CUDA(launch_spmv_resid(c->sched, K, x, b, c->r, st));
         }
         if ((s = norms_host(c, c->r, &rmax, &rsq, st)) != KKT_OK) return s;
         if ((s = norms_host(c, x, &xmax, &xsq, st)) != KKT_OK) return s;
@@ -922,7 +923,7 @@ kkt_status refine_tail(kkt_ctx* c, const double* b, double* x, double tol, kkt_i
     kkt_status s;
     {
         Launch L(c, st, KK_SPMV, 2);
-        KKT_CUDA(launch_resid_omega(c->n, c->nnz, c->sched.rowptr, c->sched.colidx, c->kvals, x, b,
+        KKT_CUDA(launch_resid_omega(c->sched, c->kvals, c->slots, x, b,
                                     c->r_batch, c->omega_part, c->stat, c->omega_dev, c->batch, st));
     }
     KKT_CUDA(cudaMemcpyAsync(c->omega_pin, c->omega_dev, sizeof(double) * c->batch, cudaMemcpyDeviceToHost, st));
@@ -998,7 +999,8 @@ const char* kkt_status_string(kkt_status s)
 }
 
 static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_options& o, int64_t tiles, int64_t fronts,
-                          int64_t scratch, int64_t ninv, int64_t nf12, const TreePlan& tp, int64_t B = 1)
+                          int64_t scratch, int64_t ninv, int64_t nf12, const TreePlan& tp, const SellPlan& sp,
+                          int64_t B = 1)
 {
     const int64_t es = (int64_t)elem_size(o.precision);
     int64_t b = 0;
@@ -1012,13 +1014,13 @@ static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_opti
     add(fronts * 4); add(tiles * (int64_t)sizeof(FrontTile));
     add(B * (int64_t)sizeof(DevStat));
     add(B * n * 8); add(B * n * 8);
-    add(B * nnz * es); add(B * an.panel_total * es); add(B * std::max<int64_t>(an.cb_total, 1) * es);
+    add(B * sp.slots * es); add(B * an.panel_total * es); add(B * std::max<int64_t>(an.cb_total, 1) * es);
     add(B * n * es); add(B * std::max<int64_t>((int64_t)an.rel.size(), 1) * es);
     add(B * scratch * es);
     add((int64_t)n * (o.restart + 1) * 8); add((int64_t)n * o.restart * 8); add(n * 8); add(n * 8);
     add((int64_t)(kRedScratch + 4096 + 8) * 8);
     add((int64_t)(8 + 2 * (kMaxRestart + 2)) * 8);
-    add(B * nnz * 8); add(B * nnz * 8); add(B * n * 8); add(B * n * 8);
+    add(B * sp.slots * 8); add(B * nnz * 8); add(B * n * 8); add(B * n * 8);
     add(an.ns * 4); add(an.ns * 8); add(std::max<int64_t>(ninv, 1) * 4);
     add(an.ns * 8); add(B * std::max<int64_t>(nf12, 1) * es);
     add(B * n * 8); add(B * (int64_t)resid_blocks(n) * 4 * 8); add(B * 8);
@@ -1029,6 +1031,8 @@ static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_opti
     add((kCtrHead + 2 * B * nq) * 4); add((kCtrHead + 2 * B * nq) * 4); add(2 * 4);
     add((n + 1) * 4); add(std::max<int64_t>((int64_t)an.rel.size(), 1) * 4);
     add((3 * (int64_t)n + std::max<int64_t>((int64_t)an.rel.size(), 1)) * es);
+    add(((int64_t)sp.nslices + 1) * 8); add((int64_t)sp.nslices * 32 * 4); add(sp.slots * 4); add(sp.slots * 4);
+    add(B * sp.slots * 2);
     return b;
 }
 
@@ -1055,6 +1059,8 @@ kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx,
         build_tree(an, o.tree_min_fronts, elem_size(o.precision), tp);
         build_levels(an, elem_size(o.precision), tp.split, lv, fids, tiles, stride, mpg, inv_off, inv, f12_off,
                      f12_total);
+        SellPlan sp;
+        build_sell(n, h_rowptr, h_colidx, kSellWindow, sp);
         std::memset(out, 0, sizeof(*out));
         out->n = n;
         out->nnz = an.nnz;
@@ -1067,7 +1073,7 @@ kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx,
         out->flops = an.flops;
         out->flops_exact = an.flops_exact;
         out->device_bytes = plan_bytes(an, n, an.nnz, o, (int64_t)tiles.size(), (int64_t)fids.size(),
-                                       stride * mpg, (int64_t)inv.size(), f12_total, tp);
+                                       stride * mpg, (int64_t)inv.size(), f12_total, tp, sp);
         out->tree_levels = an.n_levels - tp.split;
         out->tree_units = (int)tp.unit.size();
         out->tree_bytes = tp.alg_bytes;
@@ -1106,6 +1112,8 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     std::vector<int> inv;
     int64_t f12_total = 0;
     TreePlan tp;
+    SellPlan sp;
+    std::vector<int> asm_src_sell;
     try {
         std::string err = analyze_pattern(n, h_rowptr, h_colidx, to_analysis(opt ? *opt : c->opt), c->an);
         if (!err.empty()) {
@@ -1119,6 +1127,10 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
         build_tree(c->an, per_instance, elem_size(c->opt.precision), tp);
         build_levels(c->an, elem_size(c->opt.precision), tp.split, c->levels, fids, tiles, c->scratch_stride,
                      c->max_panel_global, inv_off, inv, f12_off, f12_total);
+        // K's per-refactor copies live in the sliced layout: the assembly reads them at slots
+        build_sell(n, h_rowptr, h_colidx, kSellWindow, sp);
+        asm_src_sell.resize(c->an.asm_src.size());
+        for (size_t e = 0; e < asm_src_sell.size(); ++e) asm_src_sell[e] = sp.csr2sell[c->an.asm_src[e]];
     } catch (...) {
         delete c;
         return KKT_E_NOMEM;
@@ -1130,10 +1142,12 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
 
     const Analysis& an = c->an;
     c->nnz = an.nnz;
+    c->slots = sp.slots;
     const int64_t nnz = an.nnz;
+    const int64_t slots = sp.slots;
     const int64_t scratch = c->scratch_stride * c->max_panel_global;
     int64_t bytes = plan_bytes(an, n, nnz, c->opt, (int64_t)tiles.size(), (int64_t)fids.size(), scratch,
-                               (int64_t)inv.size(), f12_total, tp, B);
+                               (int64_t)inv.size(), f12_total, tp, sp, B);
     c->device_bytes = bytes;
     if (cudaMalloc(&c->pool.base, (size_t)bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -1167,7 +1181,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     const int64_t cb_unit = std::max<int64_t>(an.cb_total, 1);
     const int64_t cbv_unit = std::max<int64_t>((int64_t)an.rel.size(), 1);
     const int64_t f12_unit = std::max<int64_t>(f12_total, 1);
-    char* sv = P.take<char>(B * nnz * es);
+    char* sv = P.take<char>(B * slots * es);
     char* panel = P.take<char>(B * an.panel_total * es);
     char* cb = P.take<char>(B * cb_unit * es);
     char* vec = P.take<char>(B * n * es);
@@ -1179,7 +1193,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     c->r = P.take<double>(n);
     c->red = P.take<double>(kRedScratch + 4096 + 8);
     c->h_dev = P.take<double>(8 + 2 * (kMaxRestart + 2));
-    c->kvals = P.take<double>(B * nnz);
+    c->kvals = P.take<double>(B * slots);
     c->stage_vals = P.take<double>(B * nnz);
     c->stage_b = P.take<double>(B * n);
     c->stage_x = P.take<double>(B * n);
@@ -1203,6 +1217,11 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     c->jl_ptr = P.take<int>(n + 1);
     c->jl_idx = P.take<int>(std::max<size_t>(an.rel.size(), 1));
     c->jac_buf = P.take<char>((3 * (size_t)n + std::max<size_t>(an.rel.size(), 1)) * es);
+    int64_t* sell_off = P.take<int64_t>(sp.nslices + 1);
+    int* sell_row = P.take<int>((int64_t)sp.nslices * 32);
+    int* sell_ci = P.take<int>(slots);
+    int* sell_src = P.take<int>(slots);
+    unsigned short* keys = P.take<unsigned short>(B * slots);
     if (P.used > P.size) { kkt_destroy(c); return KKT_E_NOMEM; }
     if (cudaMallocHost(&c->pin, sizeof(double) * (4 * (kMaxRestart + 2) + 16 + B)) != cudaSuccess) {
         cudaGetLastError();
@@ -1236,7 +1255,11 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     e = e ? e : up(child_list, an.child_list.data(), an.child_list.size() * 4);
     e = e ? e : up(asm_ptr, an.asm_ptr.data(), (an.ns + 1) * 8);
     e = e ? e : up(asm_pos, an.asm_pos.data(), nnz * 4);
-    e = e ? e : up(asm_src, an.asm_src.data(), nnz * 4);
+    e = e ? e : up(asm_src, asm_src_sell.data(), nnz * 4);
+    e = e ? e : up(sell_off, sp.off.data(), (sp.nslices + 1) * 8);
+    e = e ? e : up(sell_row, sp.row.data(), (size_t)sp.nslices * 32 * 4);
+    e = e ? e : up(sell_ci, sp.ci.data(), slots * 4);
+    e = e ? e : up(sell_src, sp.src.data(), slots * 4);
     e = e ? e : up(rel_ptr, an.rel_ptr.data(), (an.ns + 1) * 8);
     e = e ? e : up(rel, an.rel.data(), an.rel.size() * 4);
     e = e ? e : up(panel_off, an.panel_off.data(), (an.ns + 1) * 8);
@@ -1283,6 +1306,8 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     s.asm_ptr = asm_ptr; s.asm_pos = asm_pos; s.asm_src = asm_src;
     s.rel_ptr = rel_ptr; s.rel = rel; s.panel_off = panel_off; s.cb_off = cb_off;
     s.cb_split = cb_split; s.inv_off = inv_off_d; s.inv = inv_d; s.f12_off = f12_off_d;
+    s.nslices = sp.nslices; s.slots = slots;
+    s.sell_off = sell_off; s.sell_row = sell_row; s.sell_ci = sell_ci; s.sell_src = sell_src;
     c->tsched = tp.ts;
     c->tsched.fr = tfr; c->tsched.kid = tkid; c->tsched.unit = tunit; c->tsched.inv = tinv;
     c->tsched.unit_fused = tunit_fused;
@@ -1327,9 +1352,10 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
         nm.cb = reinterpret_cast<float*>(cb); nm.vec = reinterpret_cast<float*>(vec);
         nm.cbv = reinterpret_cast<float*>(cbv); nm.stat = c->stat; nm.pivot_eps = eps; nm.d = c->d_a;
         nm.kcopy = c->kvals;
+        nm.keys = keys;
         nm.f12 = reinterpret_cast<float*>(f12);
         nm.dtmp = c->d_b;
-        nm.bs_nnz = nnz; nm.bs_n = n; nm.bs_panel = an.panel_total; nm.bs_cb = cb_unit;
+        nm.bs_nnz = nnz; nm.bs_slot = slots; nm.bs_n = n; nm.bs_panel = an.panel_total; nm.bs_cb = cb_unit;
         nm.bs_cbv = cbv_unit; nm.bs_f12 = f12_unit;
     } else {
         DevNum<double>& nm = c->nd;
@@ -1337,9 +1363,10 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
         nm.cb = reinterpret_cast<double*>(cb); nm.vec = reinterpret_cast<double*>(vec);
         nm.cbv = reinterpret_cast<double*>(cbv); nm.stat = c->stat; nm.pivot_eps = eps; nm.d = c->d_a;
         nm.kcopy = c->kvals;
+        nm.keys = keys;
         nm.f12 = reinterpret_cast<double*>(f12);
         nm.dtmp = c->d_b;
-        nm.bs_nnz = nnz; nm.bs_n = n; nm.bs_panel = an.panel_total; nm.bs_cb = cb_unit;
+        nm.bs_nnz = nnz; nm.bs_slot = slots; nm.bs_n = n; nm.bs_panel = an.panel_total; nm.bs_cb = cb_unit;
         nm.bs_cbv = cbv_unit; nm.bs_f12 = f12_unit;
     }
     c->info.status = KKT_OK;
@@ -1405,7 +1432,7 @@ kkt_status kkt_solve_checked(kkt_ctx* c, const double* d_rhs, double* d_x, doubl
     if (s != KKT_OK) return s;
     {
         Launch L(c, st, KK_SPMV, 2);
-        KKT_CUDA(launch_resid_omega(c->n, c->nnz, c->sched.rowptr, c->sched.colidx, c->kvals, d_x, d_rhs,
+        KKT_CUDA(launch_resid_omega(c->sched, c->kvals, c->slots, d_x, d_rhs,
                                     c->r_batch, c->omega_part, c->stat, c->omega_dev, c->batch, st));
     }
     KKT_CUDA(cudaMemcpyAsync(h_omega, c->omega_dev, sizeof(double) * c->batch, cudaMemcpyDeviceToHost, st));
@@ -1481,7 +1508,7 @@ kkt_status kkt_residual(kkt_ctx* c, const double* d_rhs, const double* d_x, doub
     if (!c || !d_rhs || !d_x || !d_r) return KKT_E_ARG;
     if (!c->refactored) return KKT_E_STATE;
     cudaStream_t st = (cudaStream_t)stream;
-    KKT_CUDA(launch_spmv_resid(c->n, c->sched.rowptr, c->sched.colidx, c->last_vals, d_x, d_rhs, d_r, st));
+    KKT_CUDA(launch_spmv_resid(c->sched, c->last_vals, d_x, d_rhs, d_r, st));
     if (omega_out) {
         double knorm = 0.0, rm, rs, xm, xs, bm, bs;
         kkt_status s;

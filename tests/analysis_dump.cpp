@@ -1,6 +1,7 @@
 // Test driver: runs the library's host analysis on a CSR pattern read from
 // binary files and writes every array of the plan as raw int64 little-endian
-// files, for the structural checks in test_analysis_cpu.py.
+// files (and the sliced copy of the pattern), for the structural checks in
+// test_analysis_cpu.py.
 //   analysis_dump <in-prefix> <out-prefix> <max_pivots>
 // reads <in>.n (int32 n), <in>.rp (int32 rowptr), <in>.ci (int32 colidx).
 #include "analysis.hpp"
@@ -65,5 +66,12 @@ int main(int argc, char** argv)
     const std::vector<int64_t> stats = {a.ns, a.n_levels, a.nnz_l, a.nnz_u, a.max_front, a.max_pivots,
                                         a.panel_total, a.cb_total};
     write_all(out + ".stats", stats);
+    SellPlan sp;
+    build_sell(nv[0], rp.data(), ci.data(), kSellWindow, sp);
+    write_all(out + ".sell_off", sp.off);
+    write_all(out + ".sell_row", sp.row);
+    write_all(out + ".sell_ci", sp.ci);
+    write_all(out + ".sell_src", sp.src);
+    write_all(out + ".csr2sell", sp.csr2sell);
     return 0;
 }

@@ -8,7 +8,10 @@ independently on the CPU:
   earlier step, at the local position of its row and column;
 * every contribution-block row maps to the same row of the parent front,
   children lists and levels are consistent, storage offsets match the
-  front sizes.
+  front sizes;
+* the sliced copy of the pattern holds every entry exactly once, a row's
+  entries in CSR order down its lane, slice widths equal to the longest row
+  of the slice, rows sorted by length within each window.
 """
 import os
 import shutil
@@ -42,7 +45,7 @@ def _plan(tool, tmp_path, rowptr, colidx, max_pivots):
     subprocess.run([tool, src, out, str(max_pivots)], check=True)
     names = ["perm", "sn_first", "sn_parent", "sn_front", "rows_ptr", "rows", "child_ptr", "child_list",
              "level_ptr", "level_fronts", "asm_ptr", "asm_pos", "asm_src", "rel_ptr", "rel", "cb_split",
-             "panel_off", "cb_off", "stats"]
+             "panel_off", "cb_off", "stats", "sell_off", "sell_row", "sell_ci", "sell_src", "csr2sell"]
     return {k: np.fromfile(out + "." + k, dtype=np.int64) for k in names}
 
 
@@ -170,3 +173,39 @@ def test_plan_structure(dump_tool, tmp_path, case, max_pivots):
     F, w = front.astype(np.int64), width.astype(np.int64)
     assert np.array_equal(np.diff(P["panel_off"]), F * w + w * (F - w))
     assert np.array_equal(np.diff(P["cb_off"]), (F - w) ** 2)
+
+
+@pytest.mark.parametrize("B,L,G,seed", [(2, 1, 1, 3), (37, 50, 8, 5), (1500, 1920, 300, 6)])
+def test_sliced_copy_of_the_pattern(dump_tool, tmp_path, B, L, G, seed):
+    pat = KKTPattern(make_grid(seed, B, L, G))
+    p = _plan(dump_tool, tmp_path, pat.rowptr, pat.colidx, 16)
+    n, nnz = pat.n, pat.nnz
+    off, row, ci, src, c2s = p["sell_off"], p["sell_row"], p["sell_ci"], p["sell_src"], p["csr2sell"]
+    ns = (n + 31) // 32
+    assert off.size == ns + 1 and row.size == 32 * ns and off[0] == 0
+    lens = np.diff(pat.rowptr)
+    # every row once, lanes past the last row empty
+    assert sorted(row[row >= 0].tolist()) == list(range(n)) and np.all(row[n:] == -1)
+    assert np.all(row[:n] >= 0)
+    slots = 0
+    for s_ in range(ns):
+        r = row[32 * s_:32 * s_ + 32]
+        width = (off[s_ + 1] - off[s_]) // 32
+        assert (off[s_ + 1] - off[s_]) % 32 == 0
+        assert width == max(lens[x] for x in r if x >= 0)
+        for l, x in enumerate(r):
+            for k in range(width):
+                o = off[s_] + 32 * k + l
+                if x >= 0 and k < lens[x]:
+                    assert src[o] == pat.rowptr[x] + k and ci[o] == pat.colidx[src[o]] and c2s[src[o]] == o
+                    slots += 1
+                else:
+                    assert src[o] == -1 and ci[o] == -1
+    assert slots == nnz and ci.size == off[-1]
+    # rows are sorted by decreasing length (then index) within each window of 4096 rows
+    order = row[:n]
+    for w0 in range(0, n, 4096):
+        seg = order[w0:w0 + 4096]
+        assert sorted(seg.tolist()) == list(range(w0, min(n, w0 + 4096)))
+        key = [(-lens[x], x) for x in seg]
+        assert key == sorted(key)
