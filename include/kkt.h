@@ -155,6 +155,17 @@ void kkt_default_options(kkt_options *opt);
 kkt_status kkt_plan(int32_t n, const int32_t *h_rowptr, const int32_t *h_colidx,
                     const kkt_options *opt, kkt_plan_info *out);
 
+/* Host-only: the supernodal fronts the analysis of kkt_plan builds, for
+ * inspection (the dense blocks of the factorization; Sec. II notes that these
+ * KKT matrices are sparse and irregular, with few dense blocks). On return
+ * *count = number of fronts; h_order (front order F, pivot rows plus
+ * contribution rows) and h_pivots (pivots w) receive min(*count, capacity)
+ * entries each, in assembly-tree postorder; both may be NULL with capacity 0
+ * to query the count. Errors: as kkt_plan. */
+kkt_status kkt_plan_fronts(int32_t n, const int32_t *h_rowptr, const int32_t *h_colidx,
+                           const kkt_options *opt, int32_t capacity, int32_t *h_order, int32_t *h_pivots,
+                           int32_t *count);
+
 /* Analysis stage (Sec. II, first of the three stages; Alg. 1 setup). n_primal is the size
  * of the (1,1) block (used only for reporting). The pattern arrays are read
  * and copied; h_vals is not needed by the static-pivot analysis and may be

@@ -13,7 +13,8 @@ import numpy as np
 
 from ._native import Info, KernelStat, Options, PlanInfo, build, lib
 
-__all__ = ["KKTSolver", "KKTModel", "KKTError", "plan", "refactor_batched", "solve_batched", "build",
+__all__ = ["KKTSolver", "KKTModel", "KKTError", "plan", "plan_fronts", "front_histogram", "refactor_batched",
+           "solve_batched", "build",
            "FP64", "FP32_IR", "Options", "Info", "PlanInfo"]
 
 FP64, FP32_IR = 0, 1
@@ -139,6 +140,42 @@ def plan(rowptr, colidx, **opts) -> dict:
     out = PlanInfo()
     _check(lib().kkt_plan(rp.size - 1, rp.ctypes.data, ci.ctypes.data, C.byref(o), C.byref(out)), "kkt_plan")
     return {f: getattr(out, f) for f, _ in PlanInfo._fields_}
+
+
+def plan_fronts(rowptr, colidx, **opts):
+    """Host-only: (front orders F, pivot counts w) of the supernodal fronts the
+    analysis builds, in assembly-tree postorder (no GPU needed)."""
+    rp, ci = _pattern(rowptr, colidx, opts.get("user_perm"))
+    o, keep = _opts(**opts)
+    cnt = C.c_int32(0)
+    _check(lib().kkt_plan_fronts(rp.size - 1, rp.ctypes.data, ci.ctypes.data, C.byref(o), 0, None, None,
+                                 C.byref(cnt)), "kkt_plan_fronts")
+    F = np.empty(cnt.value, np.int32)
+    w = np.empty(cnt.value, np.int32)
+    _check(lib().kkt_plan_fronts(rp.size - 1, rp.ctypes.data, ci.ctypes.data, C.byref(o), cnt.value, F.ctypes.data,
+                                 w.ctypes.data, C.byref(cnt)), "kkt_plan_fronts")
+    return F, w
+
+
+def front_histogram(rowptr, colidx, edges=(1, 9, 17, 33, 65, 129, 257, 513), **opts):
+    """Dense work of the fronts by front order: per bucket of F the number of
+    fronts and their flops (pivot block 2/3 w^3, panels 2 w^2 (F - w), Schur
+    update 2 w (F - w)^2), and the Schur-update flops of the fronts with
+    F - w >= 64 (those a tensor-core tile could take)."""
+    F, w = plan_fronts(rowptr, colidx, **opts)
+    F, w = F.astype(np.float64), w.astype(np.float64)
+    m = F - w
+    piv, pan, schur = 2.0 / 3.0 * w ** 3, 2.0 * w * w * m, 2.0 * w * m * m
+    tot = piv + pan + schur
+    rows = []
+    for a, b in zip(edges[:-1], edges[1:]):
+        sel = (F >= a) & (F < b)
+        rows.append({"F": [int(a), int(b) - 1], "fronts": int(sel.sum()), "flops": float(tot[sel].sum()),
+                     "schur_flops": float(schur[sel].sum())})
+    big = m >= 64
+    return {"fronts": int(F.size), "max_front": int(F.max()) if F.size else 0, "flops": float(tot.sum()),
+            "schur_flops": float(schur.sum()), "buckets": rows,
+            "tile_candidates": {"fronts": int(big.sum()), "schur_flops": float(schur[big].sum())}}
 
 
 class KKTSolver:

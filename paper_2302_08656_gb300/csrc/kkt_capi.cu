@@ -1088,6 +1088,31 @@ kkt_status kkt_plan(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx,
     return KKT_OK;
 }
 
+kkt_status kkt_plan_fronts(int32_t n, const int32_t* h_rowptr, const int32_t* h_colidx, const kkt_options* opt,
+                           int32_t capacity, int32_t* h_order, int32_t* h_pivots, int32_t* count)
+{
+    if (n <= 0 || !h_rowptr || !h_colidx || !count || capacity < 0) return KKT_E_ARG;
+    if (capacity > 0 && (!h_order || !h_pivots)) return KKT_E_ARG;
+    kkt_options o;
+    if (opt) o = *opt; else fill_defaults(&o);
+    if (check_options(o) != KKT_OK) return KKT_E_ARG;
+    try {
+        Analysis an;
+        std::string err = analyze_pattern(n, h_rowptr, h_colidx, to_analysis(o), an);
+        if (!err.empty()) return (err.find("user") != std::string::npos) ? KKT_E_ARG : KKT_E_STRUCT;
+        *count = an.ns;
+        for (int s = 0; s < an.ns && s < capacity; ++s) {
+            h_order[s] = an.sn_front[s];
+            h_pivots[s] = an.sn_first[s + 1] - an.sn_first[s];
+        }
+    } catch (const std::bad_alloc&) {
+        return KKT_E_NOMEM;
+    } catch (...) {
+        return KKT_E_ARG;
+    }
+    return KKT_OK;
+}
+
 static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_rowptr, const int32_t* h_colidx,
                                const kkt_options* opt, int32_t batch, kkt_ctx** out)
 {

@@ -161,3 +161,20 @@ def test_out_of_range_options_are_refused():
         K.plan(pat.rowptr, pat.colidx, **opts)
     with pytest.raises(ValueError):
         K.plan(pat.rowptr, pat.colidx, precision="fp16")
+
+
+def test_plan_fronts_matches_the_plan():
+    """The host-only front query: one entry per front, pivots summing to n,
+    every front at least as large as its pivot block, and the panels
+    (F w + w (F - w) values each) adding up to the plan's stored factor."""
+    pat = KKTPattern(make_grid(2, 300, 390, 60))
+    for mp in (8, 16, 32):
+        p = K.plan(pat.rowptr, pat.colidx, max_pivots=mp)
+        F, w = K.plan_fronts(pat.rowptr, pat.colidx, max_pivots=mp)
+        assert F.size == w.size == p["n_fronts"]
+        assert int(w.sum()) == pat.n and np.all(w >= 1) and np.all(F >= w) and int(w.max()) <= mp
+        assert int(F.max()) == p["max_front"]
+        assert int(np.sum(F.astype(np.int64) * w + w * (F - w))) == p["stored_factor"]
+        h = K.front_histogram(pat.rowptr, pat.colidx, max_pivots=mp)
+        assert h["fronts"] == F.size and sum(b["fronts"] for b in h["buckets"]) == F.size
+        assert abs(sum(b["flops"] for b in h["buckets"]) - h["flops"]) <= 1e-9 * h["flops"]
