@@ -604,13 +604,52 @@ def run_native(args):
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ oracle on every host core
+
+def _oracle_worker(task):
+    """One host core: the oracle as it stands on systems of one kind until its
+    time budget is used (analysis untimed). task = (n_bus, n_branch, n_gen,
+    grid seed, [(point seed, mu)], budget_s); returns (solves, seconds)."""
+    import oracle as O
+    n_bus, n_branch, n_gen, gseed, points, budget = task
+    pat = KKTPattern(make_grid(gseed, n_bus, n_branch, n_gen))
+    an = None
+    done, busy = 0, 0.0
+    for psd, mu in points:
+        v = pat.values(pat.point(psd, 0, mu))
+        b = pat.rhs(psd, 0)
+        if an is None:
+            an = O.analyze(pat.rowptr, pat.colidx, v)
+        t0 = time.perf_counter()
+        lu, d, _ = O.refactor(pat.rowptr, pat.colidx, v, an)
+        O.fgmres(pat.rowptr, pat.colidx, v, lu, d, b, 30, 10, 1e-10)
+        busy += time.perf_counter() - t0
+        done += 1
+        if busy > budget and done >= 1:
+            break
+    return done, busy
+
+
+def oracle_pool(tasks):
+    """Run the oracle tasks on every host core, one process per core, started
+    with spawn (never forked from a process that has used the GPU)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(cores, len(tasks))) as pool:
+        out = pool.map(_oracle_worker, tasks)
+    return out, cores
+
+
 # ------------------------------------------------------------ batched (many instances)
 
 def run_batch(args):
     """64 instances of one 2,000-bus pattern and 16 of one 10,000-bus pattern,
-    values and right-hand sides from a different seed per instance; FP32
-    factors + FP64 refinement; the two batches refactor concurrently; the
-    schedule of each is chosen by the autotuner."""
+    values and right-hand sides from a different seed per instance; the two
+    batches refactor concurrently, each one launch per level for all its
+    instances; the schedule of each is chosen by the autotuner. The value is
+    FP32 factors + FP64 refinement; fp64_arm repeats the same steps with FP64
+    factors."""
     import torch
     import paper_2302_08656_gb300 as K
     from paper_2302_08656_gb300 import autotune
@@ -618,89 +657,188 @@ def run_batch(args):
     dev = torch.device("cuda", 0)
     groups = [("batch2k", 64), ("batch10k", 16)]
     n_in = pool_size(args)
-    prec = "fp32" if args.precision == "fp64" else args.precision   # this configuration runs FP32 LU
-    ctxs, vals, rhs, outs, omegas, tune_info = [], [], [], [], [], {}
+    pats, vals, rhs, mus_of = [], [], [], []
     for name, count in groups:
         w = WORKLOADS[name]
         pat = KKTPattern(make_grid(args.seed, w["n_bus"], w["n_branch"], w["n_gen"]))
         mus = mu_schedule(w["mu0"], w["mu1"], w["steps"])
+        ks = spread(n_in, len(mus))
         v_steps, b_steps = [], []
-        for t in range(n_in):
-            k = t % len(mus)
+        for k in ks:
             v_steps.append(torch.from_numpy(np.concatenate(
                 [pat.values(pat.point(args.seed * 1000 + i, k, mus[k])) for i in range(count)])).to(dev))
             b_steps.append(torch.from_numpy(np.concatenate(
                 [pat.rhs(args.seed * 1000 + i, k) for i in range(count)])).to(dev))
-        best, times = autotune.tune(pat.rowptr, pat.colidx, pat.n_primal, v_steps[0], b_steps[0],
-                                    precision=prec, count=count)
-        tune_info[name] = {"count": count, "n": pat.n, "nnz": pat.nnz, "chosen": best, "ms_by_max_pivots": times}
-        s = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, count=count, precision=prec, **best)
-        ctxs.append(s)
+        pats.append(pat)
         vals.append(v_steps)
         rhs.append(b_steps)
-        outs.append(torch.empty_like(b_steps[0]))
-        omegas.append(torch.empty(count, dtype=torch.float64).pin_memory())
+        mus_of.append(mus)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step(t):
-        t = at(args, t)
-        K.refactor_batched(ctxs, [vals[g][t] for g in range(len(ctxs))])
-        for g, s in enumerate(ctxs):
-            s.solve_checked(rhs[g][t], outs[g], omegas[g])
-        torch.cuda.synchronize()
-        worst, iters = 0.0, 0
-        for g, s in enumerate(ctxs):
-            om = omegas[g].numpy()
-            if np.any(~(om <= args.tol)):
-                _, infos = s.refine(rhs[g][t], out=outs[g], tol=args.tol, raise_on_noconv=False)
-                om = np.array([i.backward_err for i in infos])
-                iters += sum(i.iters for i in infos)
-            worst = max(worst, float(np.max(om)))
-        return worst, iters
+    def arm(prec):
+        ctxs, outs, omegas, tune_info = [], [], [], {}
+        for (name, count), pat, v_steps, b_steps in zip(groups, pats, vals, rhs):
+            best, times = autotune.tune(pat.rowptr, pat.colidx, pat.n_primal, v_steps[0], b_steps[0],
+                                        precision=prec, count=count)
+            tune_info[name] = {"count": count, "n": pat.n, "nnz": pat.nnz, "chosen": best, "ms_by_schedule": times}
+            ctxs.append(K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, count=count, precision=prec, **best))
+            outs.append(torch.empty_like(b_steps[0]))
+            omegas.append(torch.empty(count, dtype=torch.float64).pin_memory())
 
-    for t in range(args.warmup):
-        step(t)
-    l0 = sum(s.info().launches for s in ctxs)
-    ms, oms, its = [], [], []
-    sampler = ClockSampler(0)
-    sampler.start()
-    for t in range(args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        om, it = step(args.warmup + t)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms.append(e0.elapsed_time(e1))
-        oms.append(om)
-        its.append(it)
-    clocks = sampler.stop()
-    launches = sum(s.info().launches for s in ctxs) - l0
-    per_step = sum(c for _, c in groups)
+        def step(t):
+            t = at(args, t)
+            K.refactor_batched(ctxs, [vals[g][t] for g in range(len(ctxs))])
+            for g, s in enumerate(ctxs):
+                s.solve_checked(rhs[g][t], outs[g], omegas[g])
+            torch.cuda.synchronize()
+            worst, iters = 0.0, 0
+            for g, s in enumerate(ctxs):
+                om = omegas[g].numpy()
+                if np.any(~(om <= args.tol)):
+                    _, infos = s.refine(rhs[g][t], out=outs[g], tol=args.tol, raise_on_noconv=False)
+                    om = np.array([i.backward_err for i in infos])
+                    iters += sum(i.iters for i in infos)
+                worst = max(worst, float(np.max(om)))
+            return worst, iters
+
+        for t in range(args.warmup):
+            step(t)
+        l0 = sum(s.info().launches for s in ctxs)
+        ms, oms, its = [], [], []
+        sampler = ClockSampler(0)
+        sampler.start()
+        for t in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            om, it = step(args.warmup + t)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            oms.append(om)
+            its.append(it)
+        clocks = sampler.stop()
+        launches = sum(s.info().launches for s in ctxs) - l0
+        # profiling pass: per-kernel time of every context, for the roofline
+        stats_all = {}
+        for s in ctxs:
+            s.set_profiling(True)
+            s.kernel_stats()
+        nprof = min(3, args.steps)
+        for t in range(nprof):
+            step(args.warmup + t)
+        plans = [s.plan() for s in ctxs]
+        per_ctx = []
+        for s in ctxs:
+            st = s.kernel_stats()
+            per_ctx.append(st)
+            s.set_profiling(False)
+            for k, (c, kms) in st.items():
+                a = stats_all.setdefault(k, [0, 0.0])
+                a[0] += c
+                a[1] += kms
+        for s in ctxs:
+            s.close()
+        per_step = sum(c for _, c in groups)
+        rec = {"precision": PREC_NAME[prec], "value": per_step * len(ms) / (sum(ms) / 1000.0),
+               "ms_per_step": float(np.mean(ms)), "p50_ms": float(np.percentile(ms, 50)),
+               "p99_ms": float(np.percentile(ms, 99)), "omega_max": float(max(oms)),
+               "fgmres_iters_total": int(sum(its)), "gpu_launches": int(launches), "clocks": clocks,
+               "groups": tune_info}
+        return rec, stats_all, per_ctx, plans, nprof
+
+    main_prec = "fp32" if args.precision == "fp64" else args.precision   # this configuration runs FP32 LU
+    main, stats, per_ctx, plans, nprof = arm(main_prec)
+    other = None if args.no_compare else arm("fp64" if main_prec == "fp32" else "fp32")[0]
+
+    # roofline of the dominant kernel over both patterns' contexts: the
+    # algorithmic bytes of every instance it processed per step
+    roofline = None
+    if stats:
+        wb = 4 if main_prec == "fp32" else 8
+        dom = max(stats.items(), key=lambda kv: kv[1][1])[0]
+        ph = PHASE_OF.get(dom, "refactor")
+        byts = 0
+        for (name, count), pat, plan in zip(groups, pats, plans):
+            ab = algorithmic_bytes(plan, pat.n, pat.nnz, wb)
+            byts += count * (tree_factor_bytes(plan, wb) if dom == "tree_factor_kernel" else ab[ph])
+        if dom == "tree_factor_kernel":
+            kms, what = stats[dom][1] / nprof, "the tree part of every instance's refactorization in one batch step"
+        else:
+            # a level kernel takes only some fronts of each level: the unit is
+            # then the whole phase it belongs to (its kernels' time summed)
+            kms = sum(v[1] for k, v in stats.items() if PHASE_OF.get(k) == ph) / nprof
+            what = "the %s phase of one batch step (all 80 instances), whose largest kernel is %s" % (ph, dom)
+        hbm, src = _hbm_peak()
+        achieved = byts / (kms / 1000.0) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": None, "kernel": dom, "peak_source": src, "per_unit": what,
+                    "algorithmic_bytes_per_unit": byts, "ms_per_unit": kms,
+                    "launches_per_unit": stats[dom][0] / nprof,
+                    "kernel_ms_per_step": {k: v[1] / nprof for k, v in stats.items()}}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        tasks = []
+        for i in range(cores):
+            name, count = groups[0] if i < max(1, (cores * 3) // 4) else groups[1]
+            w = WORKLOADS[name]
+            pts = [(args.seed * 1000 + j, float(mus_of[0][spread(8, len(mus_of[0]))[j % 8]])) for j in range(i, i + 40)]
+            tasks.append((w["n_bus"], w["n_branch"], w["n_gen"], args.seed, pts, args.cpu_seconds))
+        out, used = oracle_pool(tasks)
+        t_of = {}
+        for (name, _), res in zip([groups[0] if i < max(1, (cores * 3) // 4) else groups[1] for i in range(cores)], out):
+            a = t_of.setdefault(name, [0, 0.0])
+            a[0] += res[0]
+            a[1] += res[1]
+        per_inst = {name: t_of[name][1] / max(1, t_of[name][0]) for name in t_of}
+        core_s_per_step = sum(count * per_inst.get(name, float("nan")) for name, count in groups)
+        steps_per_s = used / core_s_per_step
+        cpu = {"value": steps_per_s * sum(c for _, c in groups), "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": "%s; one process per core (spawn), each timing refactor + solve + FGMRES of its own "
+                         "instances for %.0f s after an untimed analysis; batch rate = cores / (64 t_2k + 16 t_10k) "
+                         "x 80" % (", ".join("%s: %d solves, %.3f s each" % (k, t_of[k][0], per_inst[k])
+                                            for k in sorted(t_of)), args.cpu_seconds)}
+
     line = {
-        "metric": METRIC, "value": per_step * len(ms) / (sum(ms) / 1000.0), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": "batch", "groups": tune_info, "precision": prec, "tol": args.tol,
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if main_prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": "batch", "groups": main["groups"], "precision": PREC_NAME[main_prec], "tol": args.tol,
                    "l2": "flushed between timed steps (512 MB write)",
+                   "inputs": "%d inputs per instance spread over the 50-step mu schedule, cycled" % (n_in - args.warmup),
                    "note": "one step = one refactor + solve (+ refinement if needed) of all 80 instances"},
-        "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-        "omega_max": float(max(oms)), "fgmres_iters_total": int(sum(its)), "gpu_launches": int(launches),
-        "clocks": clocks,
+        "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "omega_max": main["omega_max"],
+        "fgmres_iters_total": main["fgmres_iters_total"], "gpu_launches": main["gpu_launches"],
+        "clocks": main["clocks"], "roofline": roofline, "cpu_baseline": cpu,
+        "fp64_arm" if main_prec == "fp32" else "fp32_arm": other,
     }
+    if other is not None:
+        line["fp32_vs_fp64"] = {"solves_per_s_ratio": main["value"] / other["value"],
+                                "p99_ratio": main["p99_ms"] / other["p99_ms"]}
     print(json.dumps(line), flush=True)
-    for s in ctxs:
-        s.close()
+
+
+def _hbm_peak():
+    try:
+        hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs")
+    except Exception:
+        hbm = None
+    return (hbm, "measured") if hbm else (6800.0, "fallback")
 
 
 # ------------------------------------------------------------------- serving
 
 def run_serving(args):
     """Sessions with grid sizes log-uniform over 500..25,000 buses, 30..80 IPM
-    iterations each, Poisson arrivals at `rate` requests/s in total; FP32 factors
-    + FP64 refinement to tol; HBM budget for admission. Each session cycles two
+    iterations each, Poisson arrivals at `rate` requests/s in total; factors
+    resident per session; HBM budget for admission. The value is FP32 factors
+    + FP64 refinement to tol; fp64_arm replays the same sessions and arrivals
+    with FP64 factors; budget_binding replays the FP32 run under a budget that
+    admits only part of the sessions at a time. Each session cycles two
     pre-generated value sets (to bound input generation time)."""
     import torch
     from paper_2302_08656_gb300.serve import (GpuBackend, Server, SessionSpec, estimate_bytes,
@@ -711,37 +849,82 @@ def run_serving(args):
     sizes = log_uniform_sizes(rng, args.sessions, 500, 25_000)
     iters = rng.integers(30, 81, size=args.sessions)
     arrivals = poisson_arrivals(rng, args.rate, list(iters))
-    sessions = []
+    specs = []
     t0 = time.perf_counter()
     for sid, B in enumerate(sizes):
         grid = make_grid(args.seed * 7919 + sid, B, int(round(1.28 * B)), max(1, int(round(0.2 * B))))
         pat = KKTPattern(grid)
         vs = [torch.from_numpy(pat.values(pat.point(sid, k, 10.0 ** -(1 + 4 * k)))).to(dev) for k in range(2)]
         bs = [torch.from_numpy(pat.rhs(sid, k)).to(dev) for k in range(2)]
-        sessions.append(SessionSpec(sid, pat.rowptr, pat.colidx, pat.n_primal, arrivals[sid],
-                                    (lambda v, b: (lambda k: (v[k % 2], b[k % 2])))(vs, bs),
-                                    est_bytes=estimate_bytes(pat.nnz)))
+        specs.append((sid, pat, vs, bs))
     gen_s = time.perf_counter() - t0
-    backend = GpuBackend(precision="fp32", tol=args.tol, streams=16)
-    server = Server(backend, budget_bytes=int(args.budget_gb * (1 << 30)), max_inflight=16, analysis_workers=12)
-    sampler = ClockSampler(0)
-    sampler.start()
-    rep = server.run(sessions)
-    clocks = sampler.stop()
+
+    def serve(prec, budget_gb):
+        sessions = [SessionSpec(sid, pat.rowptr, pat.colidx, pat.n_primal, arrivals[sid],
+                                (lambda v, b: (lambda k: (v[k % 2], b[k % 2])))(vs, bs),
+                                est_bytes=estimate_bytes(pat.nnz, prec))
+                    for sid, pat, vs, bs in specs]
+        backend = GpuBackend(precision=prec, tol=args.tol, streams=16)
+        server = Server(backend, budget_bytes=int(budget_gb * (1 << 30)), max_inflight=16, analysis_workers=12)
+        sampler = ClockSampler(0)
+        sampler.start()
+        rep = server.run(sessions)
+        clocks = sampler.stop()
+        return {"precision": PREC_NAME[prec], "budget_gb": budget_gb, "value": rep.solves_per_s,
+                "completed": rep.completed, "wall_s": rep.wall_s,
+                "p50_ms": rep.percentile(50), "p99_ms": rep.percentile(99),
+                "p50_ms_steady": rep.percentile(50, steady=True), "p99_ms_steady": rep.percentile(99, steady=True),
+                "omega_max": float(max(rep.omegas)) if rep.omegas else None, "refined": rep.refined,
+                "max_sessions_resident": rep.max_sessions, "max_device_bytes": rep.max_bytes,
+                "admission_waits": rep.admission_waits, "failed": [[sid, k, err] for sid, k, err in rep.failed],
+                "clocks": clocks}
+
+    main = serve("fp32", args.budget_gb)
+    other = None if args.no_compare else serve("fp64", args.budget_gb)
+    # a budget that admits only part of the sessions at a time: about a tenth of their estimated total
+    total_est = sum(estimate_bytes(pat.nnz, "fp32") for _, pat, _, _ in specs)
+    small_gb = max(1.0, round(total_est / 10 / (1 << 30), 1))
+    binding = None if args.no_compare else serve("fp32", small_gb)
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        # one session per core, taken evenly over the size order (so the sample spans the log-uniform mix)
+        order = np.argsort(sizes)
+        pick = [int(order[int(round(i * (len(order) - 1) / max(1, cores - 1)))]) for i in range(cores)]
+        tasks = []
+        for sid in pick:
+            B = sizes[sid]
+            tasks.append((B, int(round(1.28 * B)), max(1, int(round(0.2 * B))), args.seed * 7919 + sid,
+                          [(sid, 10.0 ** -(1 + 4 * (k % 2))) for k in range(40)], args.cpu_seconds))
+        out, used = oracle_pool(tasks)
+        # mean oracle time per request over the sessions, weighted by their request counts
+        t_req = np.array([res[1] / max(1, res[0]) for res in out])
+        wts = np.array([iters[sid] for sid in pick], dtype=np.float64)
+        mean_t = float(np.sum(t_req * wts) / np.sum(wts))
+        cpu = {"value": used / mean_t, "unit": UNIT, "cores": used, "kind": "oracle",
+               "sample": "%d sessions spread over the size order (%d..%d buses), one process per core (spawn), "
+                         "each timing its requests for %.0f s after an untimed analysis; rate = cores / mean time "
+                         "per request (weighted by the sessions' request counts)"
+                         % (len(pick), min(sizes[s] for s in pick), max(sizes[s] for s in pick), args.cpu_seconds)}
+
     line = {
-        "metric": METRIC, "value": rep.solves_per_s, "unit": UNIT, "n_gpus": 1, "steps": rep.completed,
-        "warmup": 0, "ms_per_step": 1000.0 * rep.wall_s / max(1, rep.completed), "higher_is_better": True,
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": 1, "steps": main["completed"],
+        "warmup": 0, "ms_per_step": 1000.0 * main["wall_s"] / max(1, main["completed"]), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "serving", "sessions": args.sessions, "buses": [500, 25000], "iterations": [30, 80],
-                   "rate_per_s": args.rate, "budget_gb": args.budget_gb, "precision": "fp32", "tol": args.tol,
+                   "rate_per_s": args.rate, "budget_gb": args.budget_gb, "precision": "fp32_ir", "tol": args.tol,
                    "input_generation_s": gen_s},
-        "p50_ms": rep.percentile(50), "p99_ms": rep.percentile(99),
-        "p50_ms_steady": rep.percentile(50, steady=True), "p99_ms_steady": rep.percentile(99, steady=True),
-        "omega_max": float(max(rep.omegas)), "refined": rep.refined, "max_sessions_resident": rep.max_sessions,
-        "max_device_bytes": rep.max_bytes, "admission_waits": rep.admission_waits, "wall_s": rep.wall_s,
-        "failed": [[sid, k, err] for sid, k, err in rep.failed],
-        "clocks": clocks,
+        "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"],
+        "p50_ms_steady": main["p50_ms_steady"], "p99_ms_steady": main["p99_ms_steady"],
+        "omega_max": main["omega_max"], "refined": main["refined"],
+        "max_sessions_resident": main["max_sessions_resident"], "max_device_bytes": main["max_device_bytes"],
+        "admission_waits": main["admission_waits"], "wall_s": main["wall_s"], "failed": main["failed"],
+        "clocks": main["clocks"], "fp64_arm": other, "budget_binding": binding, "cpu_baseline": cpu,
     }
+    if other is not None:
+        line["fp32_vs_fp64"] = {"solves_per_s_ratio": main["value"] / other["value"],
+                                "p99_steady_ratio": main["p99_ms_steady"] / other["p99_ms_steady"]}
     print(json.dumps(line), flush=True)
 
 

@@ -101,3 +101,13 @@ def test_roofline_bytes_follow_the_algorithmic_formula():
     assert r["achieved"] == pytest.approx(bench.tree_factor_bytes(plan, 8) / 1e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["multifrontal_traffic_model_bytes"] == 123456
+
+
+def test_oracle_pool_runs_one_process_per_task_and_counts_solves():
+    """The host-core baseline of the batch and serving workloads: spawned
+    processes (none forked from a GPU process), each timing the oracle on its
+    own systems within its budget."""
+    tasks = [(20, 26, 4, 1, [(1, 1e-2), (2, 1e-4)], 60.0), (30, 40, 6, 2, [(3, 1e-3)], 60.0)]
+    out, cores = bench.oracle_pool(tasks)
+    assert cores >= 1 and len(out) == 2
+    assert out[0][0] == 2 and out[1][0] == 1 and all(t > 0 for _, t in out)
