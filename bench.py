@@ -70,6 +70,9 @@ def parse(argv=None):
     ap.add_argument("--slack-range", type=float, nargs=2, default=None, metavar=("LO", "HI"),
                     help="keep the inequality slacks' term -(1/sigma_s), 1/sigma_s log-uniform on [LO, HI], "
                          "on the flow-limit rows (single-system workloads; off: the literal -dc)")
+    ap.add_argument("--group", action="store_true",
+                    help="batch: the value refactors the two patterns as one group (the tops of both assembly "
+                         "trees in one launch) instead of on forked streams")
     ap.add_argument("--tree-min-fronts", type=int, default=None,
                     help="levels with fewer fronts run in the persistent tree kernels (library default if unset)")
     return ap.parse_args(argv)
@@ -676,7 +679,7 @@ def run_batch(args):
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def arm(prec):
+    def arm(prec, use_group):
         ctxs, outs, omegas, tune_info = [], [], [], {}
         for (name, count), pat, v_steps, b_steps in zip(groups, pats, vals, rhs):
             best, times = autotune.tune(pat.rowptr, pat.colidx, pat.n_primal, v_steps[0], b_steps[0],
@@ -685,10 +688,14 @@ def run_batch(args):
             ctxs.append(K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, count=count, precision=prec, **best))
             outs.append(torch.empty_like(b_steps[0]))
             omegas.append(torch.empty(count, dtype=torch.float64).pin_memory())
+        group = K.KKTGroup(ctxs) if use_group else None
 
         def step(t):
             t = at(args, t)
-            K.refactor_batched(ctxs, [vals[g][t] for g in range(len(ctxs))])
+            if group is not None:
+                group.refactor([vals[g][t] for g in range(len(ctxs))])
+            else:
+                K.refactor_batched(ctxs, [vals[g][t] for g in range(len(ctxs))])
             for g, s in enumerate(ctxs):
                 s.solve_checked(rhs[g][t], outs[g], omegas[g])
             torch.cuda.synchronize()
@@ -739,19 +746,30 @@ def run_batch(args):
                 a = stats_all.setdefault(k, [0, 0.0])
                 a[0] += c
                 a[1] += kms
+        if group is not None:
+            group.close()
         for s in ctxs:
             s.close()
         per_step = sum(c for _, c in groups)
         rec = {"precision": PREC_NAME[prec], "value": per_step * len(ms) / (sum(ms) / 1000.0),
                "ms_per_step": float(np.mean(ms)), "p50_ms": float(np.percentile(ms, 50)),
                "p99_ms": float(np.percentile(ms, 99)), "omega_max": float(max(oms)),
-               "fgmres_iters_total": int(sum(its)), "gpu_launches": int(launches), "clocks": clocks,
-               "groups": tune_info}
+               "fgmres_iters_total": int(sum(its)), "gpu_launches": int(launches),
+               "launches_per_step": launches / max(1, args.steps), "clocks": clocks, "groups": tune_info,
+               "refactorization": "forked streams" if group is None else
+               "one group: level parts on forked streams, the tops of both trees in one launch"}
         return rec, stats_all, per_ctx, plans, nprof
 
     main_prec = "fp32" if args.precision == "fp64" else args.precision   # this configuration runs FP32 LU
-    main, stats, per_ctx, plans, nprof = arm(main_prec)
-    other = None if args.no_compare else arm("fp64" if main_prec == "fp32" else "fp32")[0]
+    main, stats, per_ctx, plans, nprof = arm(main_prec, args.group)
+    other = None if args.no_compare else arm("fp64" if main_prec == "fp32" else "fp32", args.group)[0]
+    # the other refactorization schedule on the same steps: forked streams
+    # (each pattern's whole refactorization on its own stream) against one
+    # group (level parts forked, the tops of both trees in one launch)
+    alt = None
+    if not args.no_compare:
+        a = arm(main_prec, not args.group)[0]
+        alt = {k: a[k] for k in ("refactorization", "value", "p50_ms", "p99_ms", "launches_per_step", "omega_max")}
 
     # roofline of the dominant kernel over both patterns' contexts: the
     # algorithmic bytes of every instance it processed per step
@@ -813,6 +831,8 @@ def run_batch(args):
                    "note": "one step = one refactor + solve (+ refinement if needed) of all 80 instances"},
         "p50_ms": main["p50_ms"], "p99_ms": main["p99_ms"], "omega_max": main["omega_max"],
         "fgmres_iters_total": main["fgmres_iters_total"], "gpu_launches": main["gpu_launches"],
+        "launches_per_step": main["launches_per_step"], "refactorization": main["refactorization"],
+        "other_refactorization_schedule": alt,
         "clocks": main["clocks"], "roofline": roofline, "cpu_baseline": cpu,
         "fp64_arm" if main_prec == "fp32" else "fp32_arm": other,
     }

@@ -43,6 +43,7 @@ extern "C" {
 
 typedef struct kkt_ctx kkt_ctx;
 typedef struct kkt_model kkt_model;
+typedef struct kkt_group kkt_group;
 
 typedef enum {
     KKT_OK = 0,
@@ -260,6 +261,26 @@ kkt_status kkt_step_host(kkt_ctx *ctx, const double *h_vals, const double *h_rhs
  * Errors: KKT_E_ARG, KKT_E_CUDA. */
 kkt_status kkt_refactor_batched(kkt_ctx *const *ctxs, const double *const *d_vals,
                                 int count, void *stream);
+
+/* Refactorization of many systems of uneven sizes in one launch (Alg. 1's
+ * refactor step for every member, batched across sessions or scenarios).
+ * kkt_group_create takes `count` distinct contexts of one precision (their
+ * patterns and sizes may differ, each may be batched) and allocates the
+ * group's small device tables (the one allocating call of the group API);
+ * the contexts must outlive the group. kkt_refactor_group(g, d_vals, stream)
+ * then refactors member i with the values d_vals[i] (device, instance-major
+ * as in kkt_refactor): equilibration and the level-launched lower levels of
+ * each member on its own internal stream (forked from `stream` and joined
+ * back), then the narrow tops of all members' assembly trees in ONE launch of
+ * the persistent tree kernel, whose work units interleave the members by
+ * height below their roots. Results are bitwise those of kkt_refactor on each
+ * member. Asynchronous; kkt_solve / kkt_refine etc. then work on each member
+ * as usual. The group's tree launch is counted in the first member's launch
+ * counter. Errors: KKT_E_ARG (null, duplicate, mixed precision), KKT_E_NOMEM,
+ * KKT_E_CUDA. */
+kkt_status kkt_group_create(kkt_ctx *const *ctxs, int count, kkt_group **out);
+kkt_status kkt_refactor_group(kkt_group *g, const double *const *d_vals, void *stream);
+kkt_status kkt_group_destroy(kkt_group *g);
 
 /* kkt_solve over several distinct contexts, concurrently as above.
  * Asynchronous. */

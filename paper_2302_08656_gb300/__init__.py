@@ -13,7 +13,8 @@ import numpy as np
 
 from ._native import Info, KernelStat, Options, PlanInfo, build, lib
 
-__all__ = ["KKTSolver", "KKTModel", "KKTError", "plan", "plan_fronts", "front_histogram", "refactor_batched",
+__all__ = ["KKTSolver", "KKTModel", "KKTGroup", "KKTError", "plan", "plan_fronts", "front_histogram",
+           "refactor_batched",
            "solve_batched", "build",
            "FP64", "FP32_IR", "Options", "Info", "PlanInfo"]
 
@@ -472,6 +473,44 @@ def refactor_batched(solvers, vals, stream=None):
     hs = _ptr_array([s.handle.value for s in solvers])
     vs = _ptr_array([v.data_ptr() for v in vals])
     _check(lib().kkt_refactor_batched(hs, vs, len(solvers), _stream(stream)), "kkt_refactor_batched")
+
+
+class KKTGroup:
+    """Solvers (patterns of any size, each possibly batched, one precision)
+    refactored together: level parts concurrently, the tops of all their
+    assembly trees in one launch."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        if not self.solvers:
+            raise ValueError("a group needs at least one solver")
+        if len({id(s) for s in self.solvers}) != len(self.solvers):
+            raise ValueError("a solver appears twice in the group")
+        if len({s.precision for s in self.solvers}) != 1:
+            raise ValueError("the solvers of a group share one precision")
+        hs = _ptr_array([s.handle.value for s in self.solvers])
+        h = C.c_void_p()
+        _check(lib().kkt_group_create(hs, len(self.solvers), C.byref(h)), "kkt_group_create")
+        self._h = h
+
+    def refactor(self, vals, stream=None):
+        if len(vals) != len(self.solvers):
+            raise ValueError("one vals tensor per solver")
+        for i, (s, v) in enumerate(zip(self.solvers, vals)):
+            _check_tensor(v, s.nnz * s.count, "vals[%d]" % i)
+        vs = _ptr_array([v.data_ptr() for v in vals])
+        _check(lib().kkt_refactor_group(self._h, vs, _stream(stream)), "kkt_refactor_group")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kkt_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve_batched(solvers, rhs, outs, stream=None):

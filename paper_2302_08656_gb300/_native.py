@@ -158,6 +158,9 @@ SIGNATURES = {
     "kkt_model_pattern": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64), _P, _P]),
     "kkt_model_assemble": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, _P, _P]),
     "kkt_model_destroy": (C.c_int, [_P]),
+    "kkt_group_create": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
+    "kkt_refactor_group": (C.c_int, [_P, _P, _P]),
+    "kkt_group_destroy": (C.c_int, [_P]),
     "kkt_plan_fronts": (C.c_int, [C.c_int32, _P, _P, C.POINTER(Options), C.c_int32, _P, _P,
                                   C.POINTER(C.c_int32)]),
     "kkt_backward_error_noalloc": (C.c_int, [C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),

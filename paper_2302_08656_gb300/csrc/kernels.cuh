@@ -214,6 +214,25 @@ struct TreeSched {
     int bwd_stage = 0;           // 1: backward solve stages U12 in shared memory
     int max_fw = 0, max_wm = 0;
 };
+// One context of a group whose tree parts run in one launch (see
+// tree_factor_kernel): its schedule, numeric buffers, instances and counter
+// block; and the segments of the group's ticket space: tickets start ..
+// (next start) - 1 are units ul0, ul0 + 1, ... (times the context's
+// instances) of context `job`.
+template <typename T>
+struct TreeJob {
+    DevSched s;
+    TreeSched ts;
+    DevNum<T> nm;
+    int B = 1;
+    int* ctr = nullptr;
+};
+struct TreeSeg {
+    int start;
+    int job;
+    int ul0;
+};
+
 constexpr int kTreeMaxKids = 48;       // fronts with more children stay level-launched
 constexpr int kTreeStage = 2048;       // staged child contribution entries per pass (forward solve)
 // Counter block of a tree kernel: [0] ticket, [1] abort flag, [2] forward-solve ticket
@@ -298,6 +317,11 @@ template <typename T>
 cudaError_t tree_grid(int kind, size_t smem, int* grid);   // kind 0 factor, 1 forward, 2 backward
 // fused != 0: the factor kernel also runs the forward substitution of every tree front (its counter
 // block then holds batch * nq factor counters followed by batch * nq forward counters)
+// The tree parts of a group of contexts in one launch; gctr: the group's
+// counter block (ticket, abort flag), cleared by the caller.
+template <typename T>
+cudaError_t launch_tree_factor_group(const TreeJob<T>* jobs, const TreeSeg* segs, int nseg, int total, int* gctr,
+                                     long long spin_limit, int grid, size_t smem, cudaStream_t st);
 template <typename T>
 cudaError_t launch_tree_factor(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
                                int* stall, long long spin_limit, int grid, size_t smem, int fused, int u0, int nu,

@@ -94,6 +94,7 @@ struct kkt_ctx {
     // per level) with one CTA per SM, so no unit there shares an SM's FP64
     // pipe; split points in the plain and the fused unit orders
     int tf_split = 0, tf_split_fused = 0, tf_grid_narrow = 0;
+    std::vector<int> tree_lvl_units; // factorization units per level of the tree part, lowest level first
     int* ctr_fac = nullptr;          // counter block of the refactorization kernel
     int* ctr_sol = nullptr;          // counter block of the two solve kernels
     int* stall = nullptr;            // failure-injection hook (two ints)
@@ -133,6 +134,8 @@ struct kkt_ctx {
     long long g_factor_kernels = 0, g_solve_kernels = 0;
     cudaGraphExec_t g_ffwd = nullptr, g_bwd = nullptr;     // fused refactor + forward solve; backward solve
     long long g_ffwd_kernels = 0, g_bwd_kernels = 0;
+    cudaGraphExec_t g_levels = nullptr;                     // level-launched part only (group refactorization)
+    long long g_levels_kernels = 0;
     bool capturing = false;
     // state
     const double* last_vals = nullptr;
@@ -140,6 +143,21 @@ struct kkt_ctx {
     int refactor_count = 0;
     kkt_info info{};
     int64_t device_bytes = 0;
+};
+
+// A group of contexts whose refactorizations run together: the level parts
+// on the contexts' own streams, the tree parts in one launch (TreeJob /
+// TreeSeg tables and the group's counter block in one device allocation).
+struct kkt_group {
+    std::vector<kkt_ctx*> ctxs;
+    int precision = 0;
+    void* dev = nullptr;
+    void* jobs = nullptr;
+    TreeSeg* segs = nullptr;
+    int* gctr = nullptr;
+    int nseg = 0, total = 0, grid = 0;
+    size_t smem = 0;
+    long long spin_limit = 0;
 };
 
 namespace {
@@ -413,8 +431,10 @@ kkt_status capture(kkt_ctx* c, cudaGraphExec_t* exec, long long* kernels, F&& bo
 // rides along (warp classes of the level-launched part inside their
 // factorization kernels, larger level fronts right after their level, tree
 // part inside the persistent kernel)
+// with_tree = false: the level-launched part only (a group launches the tree
+// parts of all its contexts together); the tree counters are cleared either way.
 template <typename T>
-kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused = false)
+kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused = false, bool with_tree = true)
 {
     const int* fr = c->fronts_dev;
     const int B = c->batch;
@@ -457,7 +477,7 @@ kkt_status factor_levels(kkt_ctx* c, DevNum<T>& nm, cudaStream_t st, bool fused 
             KKT_CUDA(launch_solve_fwd_cta<T>(c->sched, nm, fr + g.cta_off, nbig, g.big_maxF, g.big_maxW, B, st));
         }
     }
-    if (nq > 0) {
+    if (nq > 0 && with_tree) {
         const int nu = fused ? c->tsched.nunits_fused : c->tsched.nunits;
         const int us = fused ? c->tf_split_fused : c->tf_split;
         if (us > 0) {
@@ -575,6 +595,40 @@ kkt_status refactor_t(kkt_ctx* c, const double* d_vals, cudaStream_t st)
         return KKT_OK;
     }
     return factor_levels<T>(c, nm, st);
+}
+
+// Equilibration, scatter and the level-launched part of the refactorization,
+// without the tree part (a group launches the tree parts of its contexts
+// together, kkt_refactor_group).
+template <typename T>
+kkt_status refactor_levels_t(kkt_ctx* c, const double* d_vals, cudaStream_t st)
+{
+    DevNum<T>& nm = num_of<T>(c);
+    nm.vals = d_vals;
+    KKT_CUDA(cudaMemsetAsync(c->stat, 0, sizeof(DevStat) * c->batch, st));
+    double* dfin = nullptr;
+    {
+        Launch L(c, st, KK_RUIZ, c->opt.ruiz_iters > 0 ? c->opt.ruiz_iters : 1);
+        KKT_CUDA(launch_ruiz(c->sched, d_vals, c->nnz, nm.kcopy, nm.keys, c->slots, c->d_a, c->d_b, c->opt.ruiz_iters,
+                             c->stat, &dfin, c->batch, st));
+    }
+    c->d_final = dfin;
+    nm.d = dfin;
+    {
+        Launch L(c, st, KK_SCALE, 1);
+        KKT_CUDA(launch_scale<T>(c->sched, nm, dfin, c->batch, st));
+    }
+    if (!c->profile && !c->opt.no_graphs) {
+        if (!c->g_levels) {
+            kkt_status cs = capture(c, &c->g_levels, &c->g_levels_kernels,
+                                    [&](cudaStream_t cst) { return factor_levels<T>(c, nm, cst, false, false); });
+            if (cs != KKT_OK) return cs;
+        }
+        c->launches += c->g_levels_kernels;
+        KKT_CUDA(cudaGraphLaunch(c->g_levels, st));
+        return KKT_OK;
+    }
+    return factor_levels<T>(c, nm, st, false, false);
 }
 
 // Solve every instance (captured graph of the level loops), or only instance
@@ -961,6 +1015,73 @@ kkt_status refine_tail(kkt_ctx* c, const double* b, double* x, double tol, kkt_i
     if (info)
         for (int i = 0; i < c->batch; ++i) info[i] = c->infos[i];
     return worst;
+}
+
+template <typename T>
+kkt_status group_tables(kkt_group* g)
+{
+    std::vector<TreeJob<T>> jobs;
+    std::vector<int> job_ctx;
+    for (size_t i = 0; i < g->ctxs.size(); ++i) {
+        kkt_ctx* c = g->ctxs[i];
+        if (c->tsched.nq == 0 || c->tree_lvl_units.empty()) continue;
+        TreeJob<T> j;
+        j.s = c->sched;
+        j.ts = c->tsched;
+        j.nm = num_of<T>(c);
+        j.B = c->batch;
+        j.ctr = c->ctr_fac;
+        jobs.push_back(j);
+        job_ctx.push_back((int)i);
+        g->smem = std::max(g->smem, c->tf_smem);
+        g->spin_limit = std::max(g->spin_limit, c->opt.spin_limit);
+    }
+    // segments: one per (context, tree level), ordered by height below the
+    // context's root, the highest first; within a height, context order
+    std::vector<TreeSeg> segs;
+    std::vector<std::vector<int>> ul0(jobs.size());
+    int maxL = 0;
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        const std::vector<int>& u = g->ctxs[job_ctx[j]]->tree_lvl_units;
+        ul0[j].assign(u.size() + 1, 0);
+        for (size_t l = 0; l < u.size(); ++l) ul0[j][l + 1] = ul0[j][l] + u[l];
+        maxL = std::max(maxL, (int)u.size());
+    }
+    int64_t total = 0;
+    for (int h = maxL - 1; h >= 0; --h)
+        for (size_t j = 0; j < jobs.size(); ++j) {
+            const std::vector<int>& u = g->ctxs[job_ctx[j]]->tree_lvl_units;
+            const int L = (int)u.size();
+            if (h >= L) continue;
+            const int l = L - 1 - h;
+            if (u[l] == 0) continue;
+            segs.push_back(TreeSeg{(int)total, (int)j, ul0[j][l]});
+            total += (int64_t)u[l] * jobs[j].B;
+        }
+    if (total > INT32_MAX) return KKT_E_ARG;
+    g->nseg = (int)segs.size();
+    g->total = (int)total;
+    const size_t jb = (sizeof(TreeJob<T>) * std::max<size_t>(jobs.size(), 1) + 255) & ~size_t(255);
+    const size_t sb = (sizeof(TreeSeg) * std::max<size_t>(segs.size(), 1) + 255) & ~size_t(255);
+    if (cudaMalloc(&g->dev, jb + sb + 256) != cudaSuccess) {
+        cudaGetLastError();
+        g->dev = nullptr;
+        return KKT_E_NOMEM;
+    }
+    g->jobs = g->dev;
+    g->segs = reinterpret_cast<TreeSeg*>(static_cast<char*>(g->dev) + jb);
+    g->gctr = reinterpret_cast<int*>(static_cast<char*>(g->dev) + jb + sb);
+    cudaStream_t ust = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&ust, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !jobs.empty())
+        e = cudaMemcpyAsync(g->jobs, jobs.data(), sizeof(TreeJob<T>) * jobs.size(), cudaMemcpyHostToDevice, ust);
+    if (e == cudaSuccess && !segs.empty())
+        e = cudaMemcpyAsync(g->segs, segs.data(), sizeof(TreeSeg) * segs.size(), cudaMemcpyHostToDevice, ust);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->gctr, 0, 256, ust);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ust);
+    if (ust) cudaStreamDestroy(ust);
+    if (e == cudaSuccess && g->total > 0) e = tree_grid<T>(3, g->smem, &g->grid);
+    return e == cudaSuccess ? KKT_OK : KKT_E_CUDA;
 }
 
 // the pivot reciprocal of the factorization and backward kernels, elementwise
@@ -1358,6 +1479,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
         for (int l = tp.split, q = 0; l < an.n_levels; ++l)
             for (int t = an.level_ptr[l]; t < an.level_ptr[l + 1]; ++t) lev[q++] = l;
         for (const FrontTile& u : tp.unit) per_level[lev[u.front]]++;
+        c->tree_lvl_units.assign(per_level.begin() + tp.split, per_level.end());
         int narrow = an.n_levels;
         for (int l = an.n_levels - 1; l >= tp.split && (int64_t)per_level[l] * B <= nsm; --l) narrow = l;
         auto first_at = [&](const std::vector<FrontTile>& order) {   // both orders ascend by level
@@ -1512,6 +1634,72 @@ kkt_status kkt_refactor_batched(kkt_ctx* const* ctxs, const double* const* d_val
     }
     return fork_join(ctxs, count, (cudaStream_t)stream,
                      [&](int i, cudaStream_t s) { return do_refactor(ctxs[i], d_vals[i], s); });
+}
+
+kkt_status kkt_group_create(kkt_ctx* const* ctxs, int count, kkt_group** out)
+{
+    if (!out || !ctxs || count < 1) return KKT_E_ARG;
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        if (!ctxs[i]) return KKT_E_ARG;
+        if (ctxs[i]->opt.precision != ctxs[0]->opt.precision) return KKT_E_ARG;
+        for (int j = 0; j < i; ++j) if (ctxs[j] == ctxs[i]) return KKT_E_ARG;
+    }
+    kkt_group* g = nullptr;
+    try {
+        g = new kkt_group();
+        g->ctxs.assign(ctxs, ctxs + count);
+    } catch (...) {
+        delete g;
+        return KKT_E_NOMEM;
+    }
+    g->precision = ctxs[0]->opt.precision;
+    kkt_status s = g->precision == KKT_FP32_IR ? group_tables<float>(g) : group_tables<double>(g);
+    if (s != KKT_OK) {
+        kkt_group_destroy(g);
+        return s;
+    }
+    *out = g;
+    return KKT_OK;
+}
+
+kkt_status kkt_refactor_group(kkt_group* g, const double* const* d_vals, void* stream)
+{
+    if (!g || !d_vals) return KKT_E_ARG;
+    const int count = (int)g->ctxs.size();
+    for (int i = 0; i < count; ++i) if (!d_vals[i]) return KKT_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool f32 = g->precision == KKT_FP32_IR;
+    kkt_status s = fork_join(g->ctxs.data(), count, st, [&](int i, cudaStream_t ws) {
+        kkt_ctx* c = g->ctxs[i];
+        c->info.status = KKT_OK;
+        return f32 ? refactor_levels_t<float>(c, d_vals[i], ws) : refactor_levels_t<double>(c, d_vals[i], ws);
+    });
+    if (s != KKT_OK) return s;
+    if (g->total > 0) {
+        kkt_ctx* c0 = g->ctxs[0];
+        KKT_CUDA(cudaMemsetAsync(g->gctr, 0, kCtrHead * sizeof(int), st));
+        Launch L(c0, st, KK_TREE_FACTOR, 1);
+        KKT_CUDA(f32 ? launch_tree_factor_group<float>(static_cast<const TreeJob<float>*>(g->jobs), g->segs, g->nseg,
+                                                      g->total, g->gctr, g->spin_limit, g->grid, g->smem, st)
+                     : launch_tree_factor_group<double>(static_cast<const TreeJob<double>*>(g->jobs), g->segs,
+                                                        g->nseg, g->total, g->gctr, g->spin_limit, g->grid, g->smem,
+                                                        st));
+    }
+    for (kkt_ctx* c : g->ctxs) {
+        c->last_vals = c->kvals;
+        c->refactored = 1;
+        c->refactor_count++;
+    }
+    return KKT_OK;
+}
+
+kkt_status kkt_group_destroy(kkt_group* g)
+{
+    if (!g) return KKT_OK;
+    if (g->dev) cudaFree(g->dev);
+    delete g;
+    return KKT_OK;
 }
 
 kkt_status kkt_solve_batched(kkt_ctx* const* ctxs, const double* const* d_rhs, double* const* d_x, int count,
@@ -1722,6 +1910,7 @@ kkt_status kkt_destroy(kkt_ctx* c)
     if (c->g_solve) cudaGraphExecDestroy(c->g_solve);
     if (c->g_ffwd) cudaGraphExecDestroy(c->g_ffwd);
     if (c->g_bwd) cudaGraphExecDestroy(c->g_bwd);
+    if (c->g_levels) cudaGraphExecDestroy(c->g_levels);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->work_stream) cudaStreamDestroy(c->work_stream);
     if (c->done_event) cudaEventDestroy(c->done_event);

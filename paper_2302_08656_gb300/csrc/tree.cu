@@ -124,32 +124,76 @@ __device__ bool fwd_unit(const DevSched& s, const TreeSched& ts, const DevNum<T>
 // rows 0..w-1 / columns 0..w-1 are the pivots, rows w..Fr-1 the contribution
 // rows i0..i0+nr-1, columns w..Fc-1 the contribution columns j0..j0+nc-1.
 // Threads form a 32 x 8 grid (lane -> row, warp -> column).
-template <typename T>
-__global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
-                                                          int* stall, long long limit, int fused, int u0, int nu,
-                                                          int tick)
+//
+// MULTI: the tree parts of several contexts (patterns of different sizes,
+// each possibly batched) in one launch. Tickets 0 .. nu - 1 run through
+// segments (one per level of one context, ordered by height below that
+// context's root, the highest first, so that the tops of all trees finish
+// together); ticket t of segment g is unit ul0 + (t - start) / B, instance
+// (t - start) % B of context job: within a context the order is the
+// single-context order, so every unit still waits only for smaller tickets.
+// Tickets and the abort flag come from the group's counter block (ctr);
+// completion counters are each context's own. The descriptors of the current
+// unit's context are cached in shared memory.
+template <typename T, bool MULTI>
+__global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s_p, TreeSched ts_p, DevNum<T> nm0_p, int B_p,
+                                                          int* ctr, int* stall, long long limit, int fused, int u0,
+                                                          int nu, int tick, const TreeJob<T>* jobs,
+                                                          const TreeSeg* segs, int nseg)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ TreeFront d;
     __shared__ int s_t, s_ok;
     __shared__ T s_rinv[64];                                   // reciprocal of every pivot (w <= 64)
+    __shared__ __align__(16) unsigned char sj_raw[MULTI ? sizeof(TreeJob<T>) : 16];
+    __shared__ int s_seg, s_job, s_switch;
     const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    // units u0 .. u0 + nu - 1 of the chosen order, tickets from counter ctr[tick]
-    const int total = nu * B;
-    const FrontTile* units = fused ? ts.unit_fused : ts.unit;
-    int* done = ctr + kCtrHead;
-    int* fwd_done = done + (int64_t)B * ts.nq;                     // fused mode: forward-unit counters
+    // units u0 .. u0 + nu - 1 of the chosen order (MULTI: nu tickets), tickets from counter ctr[tick]
+    const int total = MULTI ? nu : nu * B_p;
     __shared__ int s_cut[kTreeMaxKids + 1];
-    T* M = reinterpret_cast<T*>(smraw);
-    const int W = ts.map_w;
-    const size_t off_map = align16(sizeof(T) * (size_t)ts.m_elems);
-    int* smap = reinterpret_cast<int*>(smraw + off_map);           // child c: rows at 2cW, columns at (2c+1)W
-    TreeKid* kids = reinterpret_cast<TreeKid*>(smraw + ts.kid_off);
+    if (MULTI && tid == 0) s_job = -1;
     for (;;) {
         const int t = next_ticket(ctr + tick, ctr + 1, total, &s_t);
         if (t >= total) break;
-        const int ul = t / B, b = t - ul * B;
-        const FrontTile ut = units[u0 + ul];
+        int ul, b;
+        if (MULTI) {
+            if (tid == 0) {                                        // segment of t (starts ascend)
+                int lo = 0, hi = nseg - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (segs[mid].start <= t) lo = mid; else hi = mid - 1;
+                }
+                s_seg = lo;
+                s_switch = segs[lo].job != s_job;
+                if (s_switch) s_job = segs[lo].job;
+            }
+            __syncthreads();
+            if (s_switch) {
+                copy_words(reinterpret_cast<TreeJob<T>*>(sj_raw), jobs + s_job, 1, tid, 256);
+                __syncthreads();
+            }
+            const TreeSeg sg = segs[s_seg];
+            const int jb = reinterpret_cast<const TreeJob<T>*>(sj_raw)->B;
+            ul = sg.ul0 + (t - sg.start) / jb;
+            b = (t - sg.start) % jb;
+        } else {
+            ul = t / B_p;
+            b = t - ul * B_p;
+        }
+        const TreeJob<T>* sj = reinterpret_cast<const TreeJob<T>*>(sj_raw);
+        const DevSched& s = MULTI ? sj->s : s_p;
+        const TreeSched& ts = MULTI ? sj->ts : ts_p;
+        const DevNum<T>& nm0 = MULTI ? sj->nm : nm0_p;
+        const int B = MULTI ? sj->B : B_p;
+        int* done = (MULTI ? sj->ctr : ctr) + kCtrHead;
+        int* fwd_done = done + (int64_t)B * ts.nq;                 // fused mode: forward-unit counters
+        const FrontTile* units = fused ? ts.unit_fused : ts.unit;
+        T* M = reinterpret_cast<T*>(smraw);
+        const int W = ts.map_w;
+        const size_t off_map = align16(sizeof(T) * (size_t)ts.m_elems);
+        int* smap = reinterpret_cast<int*>(smraw + off_map);       // child c: rows at 2cW, columns at (2c+1)W
+        TreeKid* kids = reinterpret_cast<TreeKid*>(smraw + ts.kid_off);
+        const FrontTile ut = units[(MULTI ? 0 : u0) + ul];
         const int q = ut.front;
         copy_words(&d, ts.fr + q, 1, tid, 256);
         __syncthreads();
@@ -205,7 +249,7 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched 
         // ---- wait for the children (bounded; lane l of warp 0 polls children l, l + 32)
         if (tid == 0) {
             s_ok = 1;
-            if (stall && t == 0 && *stall) {                       // test hook: a wait nothing ends
+            if (!MULTI && stall && t == 0 && *stall) {             // test hook: a wait nothing ends
                 s_ok = bounded_wait(stall + 1, 1, ctr + 1, limit);
                 *stall = 0;
             }
@@ -758,7 +802,8 @@ cudaError_t tree_grid(int kind, size_t smem, int* grid)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
-    if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_factor_kernel<T>, 256, smem);
+    if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_factor_kernel<T, false>, 256, smem);
+    else if (kind == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_factor_kernel<T, true>, 256, smem);
     else if (kind == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_fwd_kernel<T>, 128, smem);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_bwd_kernel<T>, 128, smem);
     if (e != cudaSuccess) return e;
@@ -786,7 +831,20 @@ cudaError_t launch_tree_factor(const DevSched& s, const TreeSched& t, const DevN
         return cudaErrorInvalidValue;                         // schedule not uploaded: never launch on it
     if (u0 < 0 || nu < 0 || u0 + nu > (fused ? t.nunits_fused : t.nunits) || (tick != 0 && tick != 3))
         return cudaErrorInvalidValue;
-    tree_factor_kernel<T><<<g, 256, smem, st>>>(s, t, nm, batch, ctr, stall, spin_limit, fused, u0, nu, tick);
+    tree_factor_kernel<T, false><<<g, 256, smem, st>>>(s, t, nm, batch, ctr, stall, spin_limit, fused, u0, nu, tick,
+                                                       nullptr, nullptr, 0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tree_factor_group(const TreeJob<T>* jobs, const TreeSeg* segs, int nseg, int total, int* gctr,
+                                     long long spin_limit, int grid, size_t smem, cudaStream_t st)
+{
+    const int g = std::min(grid, total);
+    if (g <= 0) return cudaSuccess;
+    if (!jobs || !segs || nseg <= 0 || !gctr) return cudaErrorInvalidValue;
+    tree_factor_kernel<T, true><<<g, 256, smem, st>>>(DevSched{}, TreeSched{}, DevNum<T>{}, 1, gctr, nullptr,
+                                                      spin_limit, 0, 0, total, 0, jobs, segs, nseg);
     return cudaGetLastError();
 }
 
@@ -819,7 +877,9 @@ cudaError_t launch_tree_bwd(const DevSched& s, const TreeSched& t, const DevNum<
     template cudaError_t launch_tree_fwd<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,        \
                                             long long, int, size_t, cudaStream_t);                                 \
     template cudaError_t launch_tree_bwd<T>(const DevSched&, const TreeSched&, const DevNum<T>&, int, int*,        \
-                                            long long, int, size_t, cudaStream_t);
+                                            long long, int, size_t, cudaStream_t);                                 \
+    template cudaError_t launch_tree_factor_group<T>(const TreeJob<T>*, const TreeSeg*, int, int, int*, long long, \
+                                                     int, size_t, cudaStream_t);
 KKT_TREE_INST(double)
 KKT_TREE_INST(float)
 
@@ -835,8 +895,10 @@ static cudaError_t allow_smem_tree(K kernel, int optin)
 cudaError_t configure_tree_kernels(int optin)
 {
     cudaError_t e;
-    if ((e = allow_smem_tree(tree_factor_kernel<double>, optin))) return e;
-    if ((e = allow_smem_tree(tree_factor_kernel<float>, optin))) return e;
+    if ((e = allow_smem_tree(tree_factor_kernel<double, false>, optin))) return e;
+    if ((e = allow_smem_tree(tree_factor_kernel<float, false>, optin))) return e;
+    if ((e = allow_smem_tree(tree_factor_kernel<double, true>, optin))) return e;
+    if ((e = allow_smem_tree(tree_factor_kernel<float, true>, optin))) return e;
     if ((e = allow_smem_tree(tree_fwd_kernel<double>, optin))) return e;
     if ((e = allow_smem_tree(tree_fwd_kernel<float>, optin))) return e;
     if ((e = allow_smem_tree(tree_bwd_kernel<double>, optin))) return e;
