@@ -373,13 +373,92 @@ kkt_status kkt_model_pattern(const kkt_model *m, int32_t *n, int32_t *n_primal, 
  * d_V, d_theta (n_bus each), d_lambda (constraint multipliers, one per
  * constraint row in the order above), d_sigma (barrier diagonal, n_primal;
  * zero on angles) are device FP64 arrays; delta_w / delta_c are the primal and
- * dual regularizations. Deterministic (fixed summation order, no atomics).
- * Asynchronous on `stream`; calls on one model must not overlap (they share
- * the model's scratch). Errors: KKT_E_ARG, KKT_E_STATE (host-only model),
- * KKT_E_CUDA. */
+ * dual regularizations. d_dual_diag (device, one per constraint row, or NULL)
+ * is added to delta_c on the (2,2) diagonal, -(delta_c + d_dual_diag[r]): the
+ * eliminated slacks' term s/w of the flow-limit rows in an interior-point
+ * step. Deterministic (fixed summation order, no atomics). Asynchronous on
+ * `stream`; calls on one model must not overlap (they share the model's
+ * scratch). Errors: KKT_E_ARG, KKT_E_STATE (host-only model), KKT_E_CUDA. */
 kkt_status kkt_model_assemble(const kkt_model *m, const double *d_V, const double *d_theta,
-                              const double *d_lambda, const double *d_sigma, double delta_w,
-                              double delta_c, double *d_vals, void *stream);
+                              const double *d_lambda, const double *d_sigma, const double *d_dual_diag,
+                              double delta_w, double delta_c, double *d_vals, void *stream);
+
+/* ---- The interior-point loop around the linear solver (Sec. II: Newton's
+ * method on the barrier problem, continuation mu -> 0; one K_k per iteration).
+ *
+ * Problem: min sum c2 Pg^2 + rho theta_ref^2 s.t. power balance c_E(x) = 0 with loads Pd, Qd,
+ * line limits |S|^2 <= Smax^2 at both ends (flow-limit models; slacks s >= 0),
+ * Vmin <= |V| <= Vmax, Pmin <= Pg <= Pmax, Qmin <= Qg <= Qmax (Eqs. 1-7). The
+ * term rho theta_ref^2 fixes the reference angle without changing the optimal
+ * cost (all else depends on angle differences), removing the uniform angle
+ * shift, a null direction of K otherwise held only by delta_w.
+ * Each iteration: model evaluation on the GPU (flows, constraints, K with the
+ * barrier diagonal Sigma_x = zL/(x - xL) + zU/(xU - x) and the slacks' term
+ * s/w), J^T lambda read off K, the optimality error
+ *   E_mu = max(||grad F + J^T lambda - zL + zU||, ||c_E||, ||c_I + s - u||,
+ *              ||lambda_I - w||, ||(x - xL) zL - mu||, ||(xU - x) zU - mu||,
+ *              ||s w - mu||)   (infinity norms),
+ * mu <- max(tol/10, min(kappa_mu mu, mu^theta_mu)) while E_mu <= kappa_eps mu,
+ * the Newton system refactored and refined by the library (kkt_refactor_refine
+ * to lin_tol), the bound and slack steps recovered, and the largest step
+ * <= 1 that keeps every distance to its bound above (1 - tau) times its
+ * value, tau = max(tau_min, 1 - mu), separately for the primal (x, s,
+ * lambda) and dual (zL, zU, w) variables. Stops when E_0 <= tol. Start: x0
+ * pushed into [xL + push (xU - xL), xU - push (xU - xL)], s0 = max(u - c_I,
+ * push u), lambda = 0, zL = mu0/(x - xL), zU = mu0/(xU - x), w = mu0/s0. */
+typedef struct {
+    double tol;          /* stop when E_0 <= tol (default 1e-7) */
+    int max_iter;        /* default 200 */
+    double mu0;          /* initial barrier parameter (default 0.1) */
+    double kappa_eps;    /* barrier subproblem tolerance factor (default 10) */
+    double kappa_mu;     /* linear decrease factor of mu (default 0.2) */
+    double theta_mu;     /* superlinear decrease exponent of mu (default 1.5) */
+    double tau_min;      /* fraction to the boundary, lower bound (default 0.99) */
+    double delta_w;      /* primal regularization of K (default 1e-8) */
+    double delta_c;      /* dual regularization of K (default 1e-8: with 1e-10 the balance rows'
+                            pivots grow the factors ~1e10 and the Newton solves stall) */
+    double push;         /* interior push of the starting point (default 1e-2) */
+    double lin_tol;      /* backward error of every Newton solve (default 1e-10) */
+    int angle_ref;       /* bus whose angle the term angle_pin * theta_ref^2 holds at 0 (default 0) */
+    double angle_pin;    /* weight of that term (default 1; 0 leaves the angle shift free) */
+} kkt_ipm_options;
+
+typedef struct {
+    int iters;           /* Newton iterations taken */
+    int status;          /* KKT_OK (converged), KKT_E_NOCONV (max_iter), KKT_E_NUMERIC, ... */
+    double objective;    /* sum c2 Pg^2 at the last iterate */
+    double err;          /* E_0 at the last iterate */
+    double mu;           /* final barrier parameter */
+    int lin_iters;       /* FGMRES iterations over all Newton solves */
+    double lin_omega_max;/* largest backward error of a Newton solve */
+    int lin_noconv;      /* Newton solves that stopped above lin_tol */
+} kkt_ipm_info;
+
+void kkt_ipm_default_options(kkt_ipm_options *opt);
+
+/* Loads and limits of the model's ACOPF instance (host arrays, read and
+ * copied): h_Pd, h_Qd, h_Vmin, h_Vmax (n_bus), h_Pmin, h_Pmax, h_Qmin, h_Qmax
+ * (n_gen), h_Smax (n_branch; used with flow limits). Allocates the loop's
+ * device workspace (the model's only allocation besides kkt_model_create);
+ * synchronous. Errors: KKT_E_ARG (null array, empty or non-finite bound
+ * interval, Vmin <= 0, Smax <= 0), KKT_E_STATE (host-only model),
+ * KKT_E_NOMEM, KKT_E_CUDA. */
+kkt_status kkt_model_set_limits(kkt_model *m, const double *h_Pd, const double *h_Qd, const double *h_Vmin,
+                                const double *h_Vmax, const double *h_Pmin, const double *h_Pmax,
+                                const double *h_Qmin, const double *h_Qmax, const double *h_Smax);
+
+/* Run the interior-point loop on the model (after kkt_model_set_limits).
+ * ctx: a single-instance context analysed for the model's own pattern
+ * (kkt_model_pattern), of either precision; every Newton system goes
+ * through kkt_refactor_refine on it. d_x (device, n_primal = (|V|, theta,
+ * Pg, Qg)): the starting point in, the last iterate out; d_lam (device, one
+ * per constraint row): the constraint multipliers out. info (may be NULL)
+ * receives the counts and errors. Synchronous on `stream`.
+ * Returns KKT_OK on convergence, KKT_E_NOCONV after max_iter, KKT_E_NUMERIC on
+ * NaN or a zero step, KKT_E_ARG (sizes of ctx and model differ, bad option),
+ * KKT_E_STATE (no limits set), or the status of a failed Newton solve. */
+kkt_status kkt_ipm_solve(kkt_model *m, kkt_ctx *ctx, const kkt_ipm_options *opt, double *d_x, double *d_lam,
+                         kkt_ipm_info *info, void *stream);
 
 kkt_status kkt_model_destroy(kkt_model *m);
 

@@ -380,6 +380,8 @@ class KKTModel:
                "kkt_model_create")
         self._h = h
         self.n_bus = int(n_bus)
+        self.n_gen = int(gb.size)
+        self.n_branch = int(ff.size)
         n, npr, nnz = C.c_int32(0), C.c_int32(0), C.c_int64(0)
         _check(lib().kkt_model_pattern(h, C.byref(n), C.byref(npr), C.byref(nnz), None, None), "kkt_model_pattern")
         self.n, self.n_primal, self.nnz = n.value, npr.value, nnz.value
@@ -393,20 +395,60 @@ class KKTModel:
         """From any object with n_bus, f, t, r, x, gen_bus, c2 attributes."""
         return cls(grid.n_bus, grid.f, grid.t, grid.r, grid.x, grid.gen_bus, grid.c2, flow_limits, host_only)
 
-    def assemble(self, V, theta, lam, sigma, delta_w=1e-8, delta_c=1e-10, out=None, stream=None):
+    def assemble(self, V, theta, lam, sigma, delta_w=1e-8, delta_c=1e-10, out=None, stream=None, dual_diag=None):
         """K values (device float64, nnz) from device float64 V, theta (n_bus),
-        lam (constraint rows) and sigma (n_primal)."""
+        lam (constraint rows) and sigma (n_primal); dual_diag (constraint rows,
+        optional) is added to delta_c on the (2,2) diagonal."""
         import torch
         _check_tensor(V, self.n_bus, "V")
         _check_tensor(theta, self.n_bus, "theta")
         _check_tensor(lam, self.n - self.n_primal, "lam")
         _check_tensor(sigma, self.n_primal, "sigma")
+        if dual_diag is not None:
+            _check_tensor(dual_diag, self.n - self.n_primal, "dual_diag")
         if out is None:
             out = torch.empty(self.nnz, dtype=torch.float64, device=V.device)
         _check_tensor(out, self.nnz, "out")
-        _check(lib().kkt_model_assemble(self._h, _ptr(V), _ptr(theta), _ptr(lam), _ptr(sigma), float(delta_w),
+        _check(lib().kkt_model_assemble(self._h, _ptr(V), _ptr(theta), _ptr(lam), _ptr(sigma),
+                                        _ptr(dual_diag) if dual_diag is not None else None, float(delta_w),
                                         float(delta_c), _ptr(out), _stream(stream)), "kkt_model_assemble")
         return out
+
+    def set_limits(self, data):
+        """Loads and limits (an object with Pd, Qd, Vmin, Vmax (buses), Pmin,
+        Pmax, Qmin, Qmax (generators), Smax (lines)); allocates the
+        interior-point loop's workspace."""
+        arrs = []
+        for name, size in (("Pd", self.n_bus), ("Qd", self.n_bus), ("Vmin", self.n_bus), ("Vmax", self.n_bus),
+                           ("Pmin", self.n_gen), ("Pmax", self.n_gen), ("Qmin", self.n_gen), ("Qmax", self.n_gen),
+                           ("Smax", self.n_branch)):
+            a = np.ascontiguousarray(getattr(data, name), dtype=np.float64).reshape(-1)
+            _check_array(a, size, name)
+            arrs.append(a)
+        self._limits = arrs
+        _check(lib().kkt_model_set_limits(self._h, *[a.ctypes.data for a in arrs]), "kkt_model_set_limits")
+
+    def ipm_solve(self, solver, x0, stream=None, **opts):
+        """The interior-point loop from the starting point x0 (device float64,
+        n_primal; overwritten with the last iterate). Returns (x, lam, info)."""
+        import torch
+        from ._native import IpmInfo, IpmOptions
+        if solver.n != self.n or solver.nnz != self.nnz or solver.count != 1:
+            raise ValueError("the solver must be a single-instance context of the model's pattern")
+        _check_tensor(x0, self.n_primal, "x0")
+        o = IpmOptions()
+        lib().kkt_ipm_default_options(C.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise ValueError("unknown interior-point option %r" % k)
+            setattr(o, k, type(getattr(o, k))(v))
+        lam = torch.empty(self.n - self.n_primal, dtype=torch.float64, device=x0.device)
+        info = IpmInfo()
+        st = lib().kkt_ipm_solve(self._h, solver.handle, C.byref(o), _ptr(x0), _ptr(lam), C.byref(info),
+                                 _stream(stream))
+        if st not in (0, 6):
+            _check(st, "kkt_ipm_solve")
+        return x0, lam, info
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

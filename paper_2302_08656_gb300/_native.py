@@ -16,8 +16,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libkkt_gb300.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["analysis.cpp", "tree_plan.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu", "tree.cu", "model.cu", "jacobi.cu"]
-HEADERS = ["analysis.hpp", "kernels.cuh", "tree_plan.hpp"]
+SOURCES = ["analysis.cpp", "tree_plan.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu", "tree.cu", "model.cu", "jacobi.cu",
+           "ipm.cu"]
+HEADERS = ["analysis.hpp", "kernels.cuh", "tree_plan.hpp", "model.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -66,6 +67,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 # ------------------------------------------------------------- ABI structs
+
+class IpmOptions(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int), ("mu0", C.c_double), ("kappa_eps", C.c_double),
+                ("kappa_mu", C.c_double), ("theta_mu", C.c_double), ("tau_min", C.c_double),
+                ("delta_w", C.c_double), ("delta_c", C.c_double), ("push", C.c_double), ("lin_tol", C.c_double),
+                ("angle_ref", C.c_int), ("angle_pin", C.c_double)]
+
+
+class IpmInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("objective", C.c_double), ("err", C.c_double),
+                ("mu", C.c_double), ("lin_iters", C.c_int), ("lin_omega_max", C.c_double),
+                ("lin_noconv", C.c_int)]
+
 
 class Options(C.Structure):
     _fields_ = [
@@ -156,7 +170,10 @@ SIGNATURES = {
     "kkt_model_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, _P, _P, _P, _P, C.c_int,
                                    C.POINTER(_P)]),
     "kkt_model_pattern": (C.c_int, [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64), _P, _P]),
-    "kkt_model_assemble": (C.c_int, [_P, _P, _P, _P, _P, C.c_double, C.c_double, _P, _P]),
+    "kkt_model_assemble": (C.c_int, [_P, _P, _P, _P, _P, _P, C.c_double, C.c_double, _P, _P]),
+    "kkt_model_set_limits": (C.c_int, [_P] + [_P] * 9),
+    "kkt_ipm_default_options": (None, [C.POINTER(IpmOptions)]),
+    "kkt_ipm_solve": (C.c_int, [_P, _P, C.POINTER(IpmOptions), _P, _P, C.POINTER(IpmInfo), _P]),
     "kkt_model_destroy": (C.c_int, [_P]),
     "kkt_group_create": (C.c_int, [_P, C.c_int, C.POINTER(_P)]),
     "kkt_refactor_group": (C.c_int, [_P, _P, _P]),

@@ -24,6 +24,7 @@
 // terms that land on it, in a fixed order, and adds its diagonal or constant
 // part. No atomics: the result is deterministic.
 #include "../../include/kkt.h"
+#include "model.hpp"
 
 #include <cuda_runtime.h>
 
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(256) gather_values_kernel(int64_t nnz, const i
                                                             const int* __restrict__ extra_arg,
                                                             const double* __restrict__ terms,
                                                             const double* __restrict__ sigma,
+                                                            const double* __restrict__ dual_diag,
                                                             const double* __restrict__ twoc2, int pg0, int ng,
                                                             double dw, double dc, double* __restrict__ vals)
 {
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(256) gather_values_kernel(int64_t nnz, const i
         if (i >= pg0 && i < pg0 + ng) d += twoc2[i - pg0];
         acc += d;
     } else if (kind == kExtraDual) {
-        acc -= dc;
+        acc -= dual_diag ? dc + dual_diag[extra_arg[e]] : dc;
     } else if (kind == kExtraOne) {
         acc += 1.0;
     }
@@ -138,15 +140,6 @@ __global__ void __launch_bounds__(256) gather_values_kernel(int64_t nnz, const i
 
 }  // namespace
 
-struct kkt_model {
-    int nb = 0, nl = 0, ng = 0, flow = 0;
-    int n_primal = 0, n = 0;
-    int64_t nnz = 0;
-    std::vector<int> rowptr, colidx;     // host copy of the pattern
-    char* base = nullptr;                // one device allocation
-    int *d_f = nullptr, *d_t = nullptr, *d_tptr = nullptr, *d_tidx = nullptr, *d_kind = nullptr, *d_arg = nullptr;
-    double *d_g = nullptr, *d_b = nullptr, *d_twoc2 = nullptr, *d_terms = nullptr;
-};
 
 extern "C" {
 
@@ -202,7 +195,7 @@ kkt_status kkt_model_create(int32_t n_bus, int32_t n_branch, int32_t n_gen, cons
             tr.push_back({rQ + bus, qg, -1, kExtraOne, 0});
             tr.push_back({qg, rQ + bus, -1, kExtraOne, 0});
         }
-        for (int i = m->n_primal; i < n; ++i) tr.push_back({i, i, -1, kExtraDual, 0});
+        for (int i = m->n_primal; i < n; ++i) tr.push_back({i, i, -1, kExtraDual, i - m->n_primal});
         std::stable_sort(tr.begin(), tr.end(), [](const Trip& a, const Trip& b) {
             return a.r != b.r ? a.r < b.r : a.c < b.c;
         });
@@ -233,6 +226,10 @@ kkt_status kkt_model_create(int32_t n_bus, int32_t n_branch, int32_t n_gen, cons
             bb[l] = -h_x[l] / z2;
         }
         for (int k = 0; k < G; ++k) twoc2[k] = 2.0 * h_c2[k];
+        m->from.assign(h_from, h_from + L);
+        m->to.assign(h_to, h_to + L);
+        m->gen_bus.assign(h_gen_bus, h_gen_bus + G);
+        m->c2.assign(h_c2, h_c2 + G);
         if (flags & KKT_MODEL_HOST_ONLY) {
             *out = m;
             return KKT_OK;
@@ -304,7 +301,8 @@ kkt_status kkt_model_pattern(const kkt_model* m, int32_t* n, int32_t* n_primal, 
 }
 
 kkt_status kkt_model_assemble(const kkt_model* m, const double* d_V, const double* d_theta, const double* d_lambda,
-                              const double* d_sigma, double delta_w, double delta_c, double* d_vals, void* stream)
+                              const double* d_sigma, const double* d_dual_diag, double delta_w, double delta_c,
+                              double* d_vals, void* stream)
 {
     if (!m || !d_V || !d_theta || !d_lambda || !d_sigma || !d_vals) return KKT_E_ARG;
     if (!m->base) return KKT_E_STATE;
@@ -314,7 +312,8 @@ kkt_status kkt_model_assemble(const kkt_model* m, const double* d_V, const doubl
                                                                d_V, d_theta, d_lambda, m->d_terms);
     const int blocks = (int)((m->nnz + 255) / 256);
     gather_values_kernel<<<blocks, 256, 0, st>>>(m->nnz, m->d_tptr, m->d_tidx, m->d_kind, m->d_arg, m->d_terms,
-                                                 d_sigma, m->d_twoc2, 2 * m->nb, m->ng, delta_w, delta_c, d_vals);
+                                                 d_sigma, d_dual_diag, m->d_twoc2, 2 * m->nb, m->ng, delta_w, delta_c,
+                                                 d_vals);
     return cudaGetLastError() == cudaSuccess ? KKT_OK : KKT_E_CUDA;
 }
 
@@ -322,6 +321,8 @@ kkt_status kkt_model_destroy(kkt_model* m)
 {
     if (!m) return KKT_OK;
     if (m->base) cudaFree(m->base);
+    if (m->ipm_base) cudaFree(m->ipm_base);
+    if (m->ipm_pin) cudaFreeHost(m->ipm_pin);
     delete m;
     return KKT_OK;
 }

@@ -97,3 +97,21 @@ def test_ipm_step_from_gpu_assembled_values():
         assert om <= 1e-10, om
     s.close()
     m.close()
+
+
+def test_assembled_values_with_the_slacks_term_match_generator():
+    """The (2,2) diagonal with the eliminated slacks' term s/w on the flow rows
+    (dual_diag): the generator's slack_inv assembly, within the same bound."""
+    dev = _dev()
+    g = make_grid(1, 200, 300, 40)
+    pat = KKTPattern(g)
+    m = K.KKTModel.from_grid(g)
+    pt = pat.point(1, 3, 1e-3, slack_range=(1e-2, 1e2))
+    ora = pat.values(pt)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(dev)   # noqa: E731
+    gpu = m.assemble(t(pt.V), t(pt.theta), t(pt.lam), t(pt.sigma), pt.delta_w, pt.delta_c,
+                     dual_diag=t(pt.slack_inv)).cpu().numpy()
+    tol = 64 * 2.0 ** -53 * (_term_bounds(pat, pt) + np.bincount(pat._inv[-pat.n_dual:], weights=pt.slack_inv,
+                                                                  minlength=pat.nnz))
+    assert np.all(np.abs(gpu - ora) <= tol)
+    m.close()

@@ -68,6 +68,7 @@ def test_first_order_conditions_with_finite_difference_jacobian(B, L, G, seed):
     r = ipm.solve(pat, data, flat_start(g, data))
     assert r.err <= 1e-7 and r.iters < 60
     x = r.x
+    assert abs(x[B + ipm.IPMOptions().angle_ref]) <= 1e-7          # the pin holds the reference angle at 0
     n = x.size
     # central differences of the constraints, column by column
     h = 1e-6
@@ -81,6 +82,8 @@ def test_first_order_conditions_with_finite_difference_jacobian(B, L, G, seed):
     Jfd = np.array(cols).T
     grad = np.zeros(n)
     grad[2 * B:2 * B + G] = 2.0 * g.c2 * x[2 * B:2 * B + G]
+    opt = ipm.IPMOptions()
+    grad[B + opt.angle_ref] = 2.0 * opt.angle_pin * x[B + opt.angle_ref]     # the reference-angle term
     stat = grad + Jfd.T @ r.lam - r.zL + r.zU
     assert np.max(np.abs(stat)) <= 1e-6 * max(1.0, np.max(np.abs(r.lam)))
     cE, cI = _cons(pat, data, x)
@@ -101,6 +104,6 @@ def test_a_planted_sign_error_breaks_convergence(monkeypatch):
     good = ipm.solve(pat, data, flat_start(pat.grid, data))
     assert good.err <= 1e-7
     orig_grad = ipm.gradient
-    monkeypatch.setattr(ipm, "gradient", lambda p, x: -orig_grad(p, x))
+    monkeypatch.setattr(ipm, "gradient", lambda p, x, o=ipm.IPMOptions(): -orig_grad(p, x, o))
     bad = ipm.solve(pat, data, flat_start(pat.grid, data), ipm.IPMOptions(max_iter=60))
     assert not (bad.err <= 1e-7 and abs(bad.objective - good.objective) <= 1e-6 * good.objective)
