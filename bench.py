@@ -64,6 +64,9 @@ def parse(argv=None):
     ap.add_argument("--no-graphs", action="store_true", help="launch kernels one by one instead of CUDA graphs")
     ap.add_argument("--assemble", action="store_true",
                     help="each step also evaluates the model on the GPU (K values from the iterate)")
+    ap.add_argument("--ipm-loop", action="store_true",
+                    help="each step is a whole interior-point solve (kkt_ipm_solve) of the workload's grid with "
+                         "seeded loads and limits, from the flat start")
     ap.add_argument("--precond", default="lu", choices=["lu", "jacobi"],
                     help="refinement preconditioner: exact triangular solves or Jacobi sweeps")
     ap.add_argument("--sweeps", type=int, default=4, help="Jacobi sweeps per triangular factor")
@@ -1034,6 +1037,86 @@ def run_ipm(args):
     model.close()
 
 
+def run_ipm_loop(args):
+    """The interior-point loop around the solver (Sec. II): one step = one whole
+    ACOPF solve from the flat start on the GPU (model evaluation, a refactor +
+    refine per Newton iteration, the vector steps), FP64 factors. value =
+    Newton iterations per second (each is one K refactor + solve); the oracle's
+    loop on the same instance is timed on one host core and its optimum is
+    compared with the GPU's."""
+    import torch
+    import paper_2302_08656_gb300 as K
+    from kktgen import flat_start, opf_data
+
+    dev = torch.device("cuda", 0)
+    w = WORKLOADS[args.workload]
+    grid = make_grid(args.seed, w["n_bus"], w["n_branch"], w["n_gen"])
+    data = opf_data(grid, args.seed)
+    m = K.KKTModel.from_grid(grid)
+    m.set_limits(data)
+    prec = args.precision if args.precision == "fp64" else "fp64"      # FP32 factors do not converge here
+    s = K.KKTSolver(m.rowptr, m.colidx, m.n_primal, precision=prec)
+    x0h = flat_start(grid, data)
+    x = torch.empty(m.n_primal, dtype=torch.float64, device=dev)
+    runs = min(args.steps, 20)
+    for _ in range(args.warmup):
+        x.copy_(torch.from_numpy(x0h))
+        m.ipm_solve(s, x)
+    l0 = s.info().launches
+    stream = torch.cuda.current_stream()
+    ms, its, infos = [], [], []
+    sampler = ClockSampler(0)
+    sampler.start()
+    for _ in range(runs):
+        x.copy_(torch.from_numpy(x0h))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, lam, info = m.ipm_solve(s, x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        its.append(info.iters)
+        infos.append(info)
+    clocks = sampler.stop()
+    launches = s.info().launches - l0
+    xg = x.cpu().numpy()
+    last = infos[-1]
+    cpu, agree = None, None
+    if not args.no_cpu_baseline:
+        from oracle import ipm as OI
+        pat = KKTPattern(grid)
+        t0 = time.perf_counter()
+        ref = OI.solve(pat, data, x0h)
+        t_ora = time.perf_counter() - t0
+        cpu = {"value": ref.iters / t_ora, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "one whole solve of the same instance by the oracle's loop (scipy sparse solves), "
+                         "%d Newton iterations in %.1f s" % (ref.iters, t_ora)}
+        B = grid.n_bus
+        th, tr = xg[B:2 * B], ref.x[B:2 * B]
+        agree = {"oracle_iterations": ref.iters, "oracle_objective": ref.objective,
+                 "objective_rel_diff": abs(last.objective - ref.objective) / abs(ref.objective),
+                 "max_abs_diff_V": float(np.max(np.abs(xg[:B] - ref.x[:B]))),
+                 "max_abs_diff_theta": float(np.max(np.abs(th - tr))),
+                 "max_abs_diff_dispatch": float(np.max(np.abs(xg[2 * B:] - ref.x[2 * B:])))}
+    total_it = int(sum(its))
+    line = {
+        "metric": METRIC, "value": 1000.0 * total_it / sum(ms), "unit": UNIT, "n_gpus": 1, "steps": runs,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload + " interior-point loop", "buses": w["n_bus"], "n": m.n, "nnz": m.nnz,
+                   "precision": prec, "loads_limits": "kktgen.opf_data (seeded)", "start": "flat",
+                   "note": "one step = one whole ACOPF solve; value = Newton iterations (K refactor + solve) per s"},
+        "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+        "newton_iterations_per_solve": its[-1], "objective": last.objective, "final_error": last.err,
+        "status": last.status, "fgmres_iters_per_solve": last.lin_iters, "newton_omega_max": last.lin_omega_max,
+        "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu, "oracle_agreement": agree,
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+    m.close()
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -1044,6 +1127,8 @@ def main():
         run_batch(args)
     elif args.workload == "serving":
         run_serving(args)
+    elif args.ipm_loop:
+        run_ipm_loop(args)
     elif args.assemble:
         run_ipm(args)
     else:
