@@ -1230,6 +1230,64 @@ __global__ void scal_copy_kernel(int n, const double* __restrict__ x, double* __
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) y[i] = x[i] * a;
 }
 
+// FGMRES, step j of the Arnoldi process, on the device: column j of the
+// Hessenberg matrix (h1 already stored in it, h2 added here), its subdiagonal
+// entry h_{j+1,j} = ||w||_2, the earlier Givens rotations applied to the
+// column, the new rotation that zeroes h_{j+1,j}, and the rotated right-hand
+// side g. scale receives h_{j+1,j} (the next basis vector is w / scale);
+// flag[j] = 1 once |g_{j+1}| <= target, on breakdown (h_{j+1,j} = 0) or on a
+// non-finite value. One thread: the rotations are a chain of dependent steps.
+__global__ void fgmres_givens_kernel(int j, int ldh, const double* __restrict__ h2, const double* __restrict__ nrm,
+                                     double* __restrict__ H, double* __restrict__ cs, double* __restrict__ sn,
+                                     double* __restrict__ g, double* __restrict__ scale, double* __restrict__ flag,
+                                     double target)
+{
+    if (threadIdx.x != 0) return;
+    double* col = H + (int64_t)j * ldh;
+    for (int i = 0; i <= j; ++i) col[i] += h2[i];
+    const double hn = sqrt(nrm[1]);
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        const double a = col[i], b = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * b;
+        col[i + 1] = -sn[i] * a + cs[i] * b;
+    }
+    const double a = col[j], b = col[j + 1];
+    const double rho = sqrt(a * a + b * b);
+    cs[j] = rho > 0.0 ? a / rho : 1.0;
+    sn[j] = rho > 0.0 ? b / rho : 0.0;
+    col[j] = rho;
+    col[j + 1] = 0.0;
+    const double gj = g[j];
+    g[j + 1] = -sn[j] * gj;
+    g[j] = cs[j] * gj;
+    *scale = hn;
+    flag[j] = (fabs(g[j + 1]) <= target || hn == 0.0 || !isfinite(g[j + 1])) ? 1.0 : 0.0;
+}
+
+// Start of an FGMRES cycle: g = (beta, 0, ..., 0), scale = beta.
+__global__ void fgmres_start_kernel(int m, double beta, double* __restrict__ g, double* __restrict__ scale)
+{
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = i == 0 ? beta : 0.0;
+    if (threadIdx.x == 0) *scale = beta;
+}
+
+// y = R^-1 g over the first k rows and columns of the rotated Hessenberg
+// matrix (upper triangular), by back substitution; one warp, each lane summing
+// the products of every 32nd column.
+__global__ void fgmres_lsq_kernel(int k, int ldh, const double* __restrict__ H, const double* __restrict__ g,
+                                  double* y)
+{
+    const int lane = threadIdx.x & 31;
+    for (int i = k - 1; i >= 0; --i) {
+        double part = 0.0;
+        for (int t = i + 1 + lane; t < k; t += 32) part += H[i + (int64_t)t * ldh] * y[t];
+        part = warp_sum(part);
+        if (lane == 0) y[i] = (g[i] - part) / H[i + (int64_t)i * ldh];
+        __syncwarp();
+    }
+}
+
 // ||a||_inf and ||a||_2^2. The maximum is taken on the bit patterns of |a_i|
 // (the numeric order for non-negative doubles, with NaN above +Inf), so a NaN
 // entry makes the norm NaN instead of being dropped.
@@ -1478,6 +1536,25 @@ cudaError_t launch_scal_copy(int n, const double* x, double* y, const double* al
 cudaError_t launch_update(int n, double* x, const double* Z, int64_t ldz, int nv, const double* y, cudaStream_t st)
 {
     update_kernel<<<kRedBlocks, 256, 0, st>>>(n, x, Z, ldz, nv, y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fgmres_givens(int j, int ldh, const double* h2, const double* nrm, double* H, double* cs,
+                                 double* sn, double* g, double* scale, double* flag, double target, cudaStream_t st)
+{
+    fgmres_givens_kernel<<<1, 32, 0, st>>>(j, ldh, h2, nrm, H, cs, sn, g, scale, flag, target);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fgmres_start(int m, double beta, double* g, double* scale, cudaStream_t st)
+{
+    fgmres_start_kernel<<<1, 128, 0, st>>>(m, beta, g, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fgmres_lsq(int k, int ldh, const double* H, const double* g, double* y, cudaStream_t st)
+{
+    fgmres_lsq_kernel<<<1, 32, 0, st>>>(k, ldh, H, g, y);
     return cudaGetLastError();
 }
 

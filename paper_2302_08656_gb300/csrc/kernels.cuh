@@ -295,6 +295,12 @@ cudaError_t launch_resid_omega(const DevSched& s, const double* kvals, int64_t b
 cudaError_t launch_spmv_resid(const DevSched& s, const double* kv, const double* x, const double* b, double* r,
                               cudaStream_t st);
 cudaError_t launch_spmv(const DevSched& s, const double* kv, const double* x, double* y, cudaStream_t st);
+// FGMRES's small work on the device: Arnoldi step j (Hessenberg column, Givens
+// rotations, g, convergence flag), the start of a cycle, the least-squares solve
+cudaError_t launch_fgmres_givens(int j, int ldh, const double* h2, const double* nrm, double* H, double* cs,
+                                 double* sn, double* g, double* scale, double* flag, double target, cudaStream_t st);
+cudaError_t launch_fgmres_start(int m, double beta, double* g, double* scale, cudaStream_t st);
+cudaError_t launch_fgmres_lsq(int k, int ldh, const double* H, const double* g, double* y, cudaStream_t st);
 // out[k] = <V_k, w> for k < nv (V column-major with leading dimension ldv); out zeroed inside
 cudaError_t launch_multidot(int n, const double* V, int64_t ldv, int nv, const double* w, double* out,
                             cudaStream_t st);

@@ -56,6 +56,13 @@ struct Pool {
 
 constexpr int kMaxRestart = 64;
 constexpr size_t kRedScratch = 128 + 304 * (kMaxRestart + 2) + 16;
+// FGMRES state on the device: Hessenberg matrix ((m + 1) x m, leading
+// dimension kMaxRestart + 1), rotations, right-hand side, solution, scale,
+// convergence flags
+constexpr int kGmLd = kMaxRestart + 1;
+constexpr size_t kGmH = 0, kGmCs = kGmH + (size_t)kGmLd * kMaxRestart, kGmSn = kGmCs + kMaxRestart,
+                 kGmG = kGmSn + kMaxRestart, kGmY = kGmG + kMaxRestart + 8, kGmScale = kGmY + kMaxRestart + 8,
+                 kGmFlag = kGmScale + 8, kGmSize = kGmFlag + kMaxRestart + 8;
 
 }  // namespace
 
@@ -109,6 +116,8 @@ struct kkt_ctx {
     double* r = nullptr;
     double* red = nullptr;           // reduction scratch + small vectors
     double* h_dev = nullptr;         // small vectors on device
+    double* gm = nullptr;            // FGMRES state on the device (kGm* offsets)
+    double* pin_flags = nullptr;     // pinned mirror of the convergence flags
     double* kvals = nullptr;         // copy of K made by the last refactor (sliced layout)
     double* stage_vals = nullptr;    // device staging for kkt_step_host
     double* stage_b = nullptr;
@@ -813,11 +822,19 @@ kkt_status norms_host(kkt_ctx* c, const double* a, double* mx, double* sq, cudaS
 
 // FGMRES(m) refinement of instance `inst` from the current x (b, x point at
 // that instance's vectors). Fills out (iters, backward_err, rel_resid2).
+// The Arnoldi process runs on the device (classical Gram-Schmidt twice, the
+// Hessenberg column, the Givens rotations and the convergence test in one
+// small kernel, the least-squares solve in another): the host issues step
+// j + 1 before it reads step j's flag, so the device never waits for the host
+// inside a cycle, and one read of the residual norms per cycle decides the
+// restart. A step issued after convergence only writes basis columns and
+// Hessenberg entries beyond the k used.
 kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double tol, kkt_info* out, cudaStream_t st)
 {
     const int n = c->n;
     const int m = c->opt.restart;
     const double* K = c->kvals + (int64_t)inst * c->slots;
+    const int pinst = c->batch == 1 ? -1 : inst;     // one instance: the solve replays its captured graph
     kkt_status s;
     double knorm = 0.0;
     if ((s = knorm_of(c, st, &knorm, inst)) != KKT_OK) return s;
@@ -835,95 +852,82 @@ kkt_status fgmres_inst(kkt_ctx* c, int inst, const double* b, double* x, double 
     };
     double omega = omega_of(rmax, xmax);
     int total = 0;
-    std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1), y(m);
-    double* hd = c->h_dev;          // device copy of h / y (kMaxRestart + 2)
+    double* H = c->gm + kGmH;
+    double* cs = c->gm + kGmCs;
+    double* sn = c->gm + kGmSn;
+    double* g = c->gm + kGmG;
+    double* y = c->gm + kGmY;
+    double* scale = c->gm + kGmScale;
+    double* flag = c->gm + kGmFlag;
+    double* nrm = c->red + 4096;
+    cudaEvent_t evs[2] = {nullptr, nullptr};
+    for (int e = 0; e < 2; ++e)
+        if (cudaEventCreateWithFlags(&evs[e], cudaEventDisableTiming) != cudaSuccess) {
+            if (evs[0]) cudaEventDestroy(evs[0]);
+            return KKT_E_CUDA;
+        }
+    struct EvGuard { cudaEvent_t* e; ~EvGuard() { cudaEventDestroy(e[0]); cudaEventDestroy(e[1]); } } guard{evs};
     for (int cyc = 0; cyc < c->opt.max_cycles && omega > tol && std::isfinite(omega); ++cyc) {
         double beta = std::sqrt(rsq);
         if (beta == 0.0) break;
-        double target = tol * (knorm * xmax + bmax);
-        c->pin[0] = beta;
-        KKT_CUDA(cudaMemcpyAsync(hd, c->pin, sizeof(double), cudaMemcpyHostToDevice, st));
+        const double target = tol * (knorm * xmax + bmax);
         {
-            Launch L(c, st, KK_VECTOR, 1);
-            KKT_CUDA(launch_scal_copy(n, c->r, c->V, hd, 1, st));
+            Launch L(c, st, KK_VECTOR, 2);
+            KKT_CUDA(launch_fgmres_start(m, beta, g, scale, st));
+            KKT_CUDA(launch_scal_copy(n, c->r, c->V, scale, 1, st));
         }
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int k = 0;
+        int k = m;
         for (int j = 0; j < m; ++j) {
             double* vj = c->V + (int64_t)j * n;
             double* zj = c->Z + (int64_t)j * n;
-            if ((s = do_precond(c, vj, zj, st, inst)) != KKT_OK) return s;
+            if ((s = do_precond(c, vj, zj, st, pinst)) != KKT_OK) return s;
             {
                 Launch L(c, st, KK_SPMV, 1);
                 KKT_CUDA(launch_spmv(c->sched, K, zj, c->w, st));
             }
-            // classical Gram-Schmidt, twice (CGS2)
-            double* h1 = hd + 8;
-            double* h2 = hd + 8 + kMaxRestart + 2;
+            // classical Gram-Schmidt, twice (CGS2): h1 into the Hessenberg column, h2 added by the step kernel
+            double* col = H + (int64_t)j * kGmLd;
             {
                 Launch L(c, st, KK_REDUCE, 2);
                 KKT_CUDA(launch_multidot(n, c->V, n, j + 1, c->w, c->red, st));
             }
-            KKT_CUDA(cudaMemcpyAsync(h1, c->red, (j + 1) * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            KKT_CUDA(cudaMemcpyAsync(col, c->red, (j + 1) * sizeof(double), cudaMemcpyDeviceToDevice, st));
             {
                 Launch L(c, st, KK_VECTOR, 1);
-                KKT_CUDA(launch_multiaxpy(n, c->w, c->V, n, j + 1, h1, st));
+                KKT_CUDA(launch_multiaxpy(n, c->w, c->V, n, j + 1, c->red, st));
             }
             {
                 Launch L(c, st, KK_REDUCE, 2);
                 KKT_CUDA(launch_multidot(n, c->V, n, j + 1, c->w, c->red, st));
             }
-            KKT_CUDA(cudaMemcpyAsync(h2, c->red, (j + 1) * sizeof(double), cudaMemcpyDeviceToDevice, st));
             {
                 Launch L(c, st, KK_VECTOR, 1);
-                KKT_CUDA(launch_multiaxpy(n, c->w, c->V, n, j + 1, h2, st));
+                KKT_CUDA(launch_multiaxpy(n, c->w, c->V, n, j + 1, c->red, st));
             }
             {
                 Launch L(c, st, KK_REDUCE, 2);
-                KKT_CUDA(launch_norms(n, c->w, c->red + 4096, st));
+                KKT_CUDA(launch_norms(n, c->w, nrm, st));
             }
-            KKT_CUDA(cudaMemcpyAsync(c->pin, h1, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-            KKT_CUDA(cudaMemcpyAsync(c->pin + kMaxRestart + 2, h2, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, st));
-            KKT_CUDA(cudaMemcpyAsync(c->pin + 2 * (kMaxRestart + 2), c->red + 4096, 2 * sizeof(double),
-                                     cudaMemcpyDeviceToHost, st));
-            KKT_CUDA(cudaStreamSynchronize(st));
-            for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = c->pin[i] + c->pin[kMaxRestart + 2 + i];
-            double hn = std::sqrt(c->pin[2 * (kMaxRestart + 2) + 1]);
-            H[(size_t)(j + 1) * m + j] = hn;
-            if (hn > 0.0) {
-                c->pin[0] = hn;
-                KKT_CUDA(cudaMemcpyAsync(hd, c->pin, sizeof(double), cudaMemcpyHostToDevice, st));
-                Launch L(c, st, KK_VECTOR, 1);
-                KKT_CUDA(launch_scal_copy(n, c->w, c->V + (int64_t)(j + 1) * n, hd, 1, st));
+            {
+                Launch L(c, st, KK_VECTOR, 2);
+                KKT_CUDA(launch_fgmres_givens(j, kGmLd, c->red, nrm, H, cs, sn, g, scale, flag, target, st));
+                if (j + 1 < m) KKT_CUDA(launch_scal_copy(n, c->w, c->V + (int64_t)(j + 1) * n, scale, 1, st));
             }
-            for (int i = 0; i < j; ++i) {
-                double a = H[(size_t)i * m + j], b2 = H[(size_t)(i + 1) * m + j];
-                H[(size_t)i * m + j] = cs[i] * a + sn[i] * b2;
-                H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * b2;
+            KKT_CUDA(cudaMemcpyAsync(c->pin_flags + j, flag + j, sizeof(double), cudaMemcpyDeviceToHost, st));
+            KKT_CUDA(cudaEventRecord(evs[j & 1], st));
+            if (j > 0) {                               // step j - 1 has (nearly) finished while j was issued
+                KKT_CUDA(cudaEventSynchronize(evs[(j - 1) & 1]));
+                if (c->pin_flags[j - 1] != 0.0) { k = j; break; }
             }
-            double a = H[(size_t)j * m + j], b2 = H[(size_t)(j + 1) * m + j];
-            double rho = std::sqrt(a * a + b2 * b2);
-            cs[j] = rho > 0 ? a / rho : 1.0;
-            sn[j] = rho > 0 ? b2 / rho : 0.0;
-            H[(size_t)j * m + j] = rho;
-            H[(size_t)(j + 1) * m + j] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
-            k = j + 1;
-            ++total;
-            if (std::fabs(g[j + 1]) <= target || hn == 0.0 || !std::isfinite(g[j + 1])) break;
         }
-        for (int i = k - 1; i >= 0; --i) {
-            double acc = g[i];
-            for (int t = i + 1; t < k; ++t) acc -= H[(size_t)i * m + t] * y[t];
-            y[i] = acc / H[(size_t)i * m + i];
+        if (k == m) {                                  // no earlier flag: the last step decides nothing more
+            KKT_CUDA(cudaEventSynchronize(evs[(m - 1) & 1]));
         }
-        for (int i = 0; i < k; ++i) c->pin[i] = y[i];
-        KKT_CUDA(cudaMemcpyAsync(hd, c->pin, k * sizeof(double), cudaMemcpyHostToDevice, st));
+        total += k;
         {
-            Launch L(c, st, KK_VECTOR, 1);
-            KKT_CUDA(launch_update(n, x, c->Z, n, k, hd, st));
+            Launch L(c, st, KK_VECTOR, 2);
+            KKT_CUDA(launch_fgmres_lsq(k, kGmLd, H, g, y, st));
+            KKT_CUDA(launch_update(n, x, c->Z, n, k, y, st));
         }
         {
             Launch L(c, st, KK_SPMV, 1);
@@ -1141,6 +1145,7 @@ static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_opti
     add((int64_t)n * (o.restart + 1) * 8); add((int64_t)n * o.restart * 8); add(n * 8); add(n * 8);
     add((int64_t)(kRedScratch + 4096 + 8) * 8);
     add((int64_t)(8 + 2 * (kMaxRestart + 2)) * 8);
+    add((int64_t)kGmSize * 8);
     add(B * sp.slots * 8); add(B * nnz * 8); add(B * n * 8); add(B * n * 8);
     add(an.ns * 4); add(an.ns * 8); add(std::max<int64_t>(ninv, 1) * 4);
     add(an.ns * 8); add(B * std::max<int64_t>(nf12, 1) * es);
@@ -1339,6 +1344,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     c->r = P.take<double>(n);
     c->red = P.take<double>(kRedScratch + 4096 + 8);
     c->h_dev = P.take<double>(8 + 2 * (kMaxRestart + 2));
+    c->gm = P.take<double>(kGmSize);
     c->kvals = P.take<double>(B * slots);
     c->stage_vals = P.take<double>(B * nnz);
     c->stage_b = P.take<double>(B * n);
@@ -1369,7 +1375,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     int* sell_src = P.take<int>(slots);
     unsigned short* keys = P.take<unsigned short>(B * slots);
     if (P.used > P.size) { kkt_destroy(c); return KKT_E_NOMEM; }
-    if (cudaMallocHost(&c->pin, sizeof(double) * (4 * (kMaxRestart + 2) + 16 + B)) != cudaSuccess) {
+    if (cudaMallocHost(&c->pin, sizeof(double) * (4 * (kMaxRestart + 2) + 16 + B + kMaxRestart + 8)) != cudaSuccess) {
         cudaGetLastError();
         c->pin = nullptr;
         kkt_destroy(c);
@@ -1442,6 +1448,7 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     e = e ? e : cudaMemsetAsync(c->stat, 0, sizeof(DevStat) * B, ust);
     e = e ? e : cudaStreamSynchronize(ust);
     c->omega_pin = c->pin + 4 * (kMaxRestart + 2) + 16;
+    c->pin_flags = c->omega_pin + B;
     c->infos.assign(B, kkt_info{});
     if (e != cudaSuccess) { kkt_destroy(c); return KKT_E_CUDA; }
     DevSched& s = c->sched;
