@@ -330,6 +330,31 @@ __device__ __forceinline__ double sell_row_dot(const DevSched& s, const double* 
 
 // ---------------------------------------------------------- front kernels
 
+// The pivot of one elimination step, computed by every calling thread from
+// the same entry x (no divergent branch, no shared-memory broadcast): the
+// static pivot and its reciprocal (pivot_rcp's value: the Newton step, the
+// division outside its range). The static-pivot events are accumulated in
+// bad / pert and counted once per front by the caller. Single precision
+// only: measured on GB300, FP64 instructions cost pipe time per active lane,
+// so in double precision one lane computes the pivot and shares it.
+template <typename T>
+__device__ __forceinline__ T uniform_pivot(T x, T floorT, T& r, bool& bad, int& pert)
+{
+    bool b1, p1;
+    const T pv = static_pivot_sel(x, floorT, b1, p1);
+    r = pivot_rcp_fast(pv);
+    if (!pivot_rcp_fast_ok(pv)) r = T(1) / pv;
+    bad |= b1;
+    pert += (int)p1;
+    return pv;
+}
+
+__device__ __forceinline__ void count_pivot_events(DevStat* stat, bool bad, int pert)
+{
+    if (bad) atomicExch(&stat->numeric_bad, 1);
+    if (pert) atomicAdd(&stat->n_perturbed, pert);
+}
+
 // Original entries of front f into the full F x F front Fm (shared memory):
 // NT threads, four independent gathers in flight per thread.
 template <typename T, int NT>
@@ -551,15 +576,25 @@ __global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T
     warp_children<T>(s, nm, f, F, lane, Fm, stage_v ? sv_base + (int64_t)wid * stage_v : nullptr, stage_v,
                      sr_base + wid * stage_r, stage_r, fused ? v : nullptr, scv);
     const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
+    bool n_bad = false;
+    int n_pert = 0;
     __shared__ T srinv[4];
-    for (int p = 0; p < w; ++p) {
-        if (lane == 0) {                                          // one reciprocal per pivot
-            const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
-            Fm[p + p * F] = pv;
-            srinv[wid] = pivot_rcp(pv);
+    for (int p = 0; p < w; ++p) {                                 // one reciprocal per pivot
+        if constexpr (sizeof(T) == 4) {
+            T r;
+            const T pv = uniform_pivot(Fm[p + p * F], floorT, r, n_bad, n_pert);
+            __syncwarp();
+            if (lane == 0) Fm[p + p * F] = pv;
+            if (lane > p && lane < F) Fm[lane + p * F] *= r;
+        } else {
+            if (lane == 0) {
+                const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
+                Fm[p + p * F] = pv;
+                srinv[wid] = pivot_rcp(pv);
+            }
+            __syncwarp();
+            if (lane > p && lane < F) Fm[lane + p * F] *= srinv[wid];
         }
-        __syncwarp();
-        if (lane > p && lane < F) Fm[lane + p * F] *= srinv[wid];
         __syncwarp();
         for (int j = p + 1 + lj; j < F; j += 4) {
             const T u = Fm[p + j * F];
@@ -567,6 +602,7 @@ __global__ void __launch_bounds__(128, 8) front_warp_kernel(DevSched s, DevNum<T
         }
         __syncwarp();
     }
+    if (lane == 0) count_pivot_events(nm.stat, n_bad, n_pert);
     if (fused) front_forward<T>(s, nm, f, first, w, F, Fm, v, lane, 32, kFull);
     T* pan = nm.panel + s.panel_off[f];
     const int m = F - w;
@@ -594,7 +630,7 @@ __global__ void __launch_bounds__(128) front_leaf_kernel(DevSched s, DevNum<T> n
     constexpr int NG = 32 / G, LJ = G / 8;
     __shared__ T Fall[4 * NG * G * G];
     __shared__ T Vall[4 * NG * G];                                 // fused: forward-step vectors
-    __shared__ T srinv[4 * NG];
+    __shared__ T srinv[4 * NG];                                    // double precision: the group's reciprocal
     const DevNum<T> nm = nm0.at(blockIdx.y);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gi = lane / G, gl = lane % G, slot = wid * NG + gi;
@@ -614,14 +650,24 @@ __global__ void __launch_bounds__(128) front_leaf_kernel(DevSched s, DevNum<T> n
     assemble_original<T, G>(s, nm, f, gl, Fm);
     __syncwarp(gmask);
     const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
-    for (int p = 0; p < w; ++p) {
-        if (gl == 0) {                                             // one reciprocal per pivot
-            const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
-            Fm[p + p * F] = pv;
-            srinv[slot] = pivot_rcp(pv);
+    bool n_bad = false;
+    int n_pert = 0;
+    for (int p = 0; p < w; ++p) {                                  // one reciprocal per pivot
+        if constexpr (sizeof(T) == 4) {
+            T r;
+            const T pv = uniform_pivot(Fm[p + p * F], floorT, r, n_bad, n_pert);
+            __syncwarp(gmask);
+            if (gl == 0) Fm[p + p * F] = pv;
+            if (gl > p && gl < F) Fm[gl + p * F] *= r;
+        } else {
+            if (gl == 0) {
+                const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
+                Fm[p + p * F] = pv;
+                srinv[slot] = pivot_rcp(pv);
+            }
+            __syncwarp(gmask);
+            if (gl > p && gl < F) Fm[gl + p * F] *= srinv[slot];
         }
-        __syncwarp(gmask);
-        if (gl > p && gl < F) Fm[gl + p * F] *= srinv[slot];
         __syncwarp(gmask);
         for (int j = p + 1 + lj; j < F; j += LJ) {
             const T u = Fm[p + j * F];
@@ -629,6 +675,7 @@ __global__ void __launch_bounds__(128) front_leaf_kernel(DevSched s, DevNum<T> n
         }
         __syncwarp(gmask);
     }
+    if (gl == 0) count_pivot_events(nm.stat, n_bad, n_pert);
     if (fused) front_forward<T>(s, nm, f, first, w, F, Fm, v, gl, G, gmask);
     T* pan = nm.panel + s.panel_off[f];
     const int m = F - w;
@@ -676,23 +723,37 @@ __global__ void __launch_bounds__(256) front_cta_kernel(DevSched s, DevNum<T> nm
         __syncthreads();
     }
     const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
+    // single precision: every thread computes the pivot from the same entry
+    // and the diagonal is written after the scaling barrier (nothing reads it
+    // again in the loop); double precision: thread 0 computes it
+    bool n_bad = false;
+    int n_pert = 0;
     __shared__ T srinv;
-    for (int p = 0; p < w; ++p) {
-        if (tid == 0) {                                           // one reciprocal per pivot
-            const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
-            Fm[p + p * F] = pv;
-            srinv = pivot_rcp(pv);
+    for (int p = 0; p < w; ++p) {                                 // one reciprocal per pivot
+        if constexpr (sizeof(T) == 4) {
+            T rinv;
+            const T pv = uniform_pivot(Fm[p + p * F], floorT, rinv, n_bad, n_pert);
+            for (int i = p + 1 + tid; i < F; i += nt) Fm[i + p * F] *= rinv;
+            __syncthreads();
+            if (tid == 0) Fm[p + p * F] = pv;
+        } else {
+            if (tid == 0) {
+                const T pv = static_pivot(Fm[p + p * F], floorT, nm.stat, true);
+                Fm[p + p * F] = pv;
+                srinv = pivot_rcp(pv);
+            }
+            __syncthreads();
+            const T rinv = srinv;
+            for (int i = p + 1 + tid; i < F; i += nt) Fm[i + p * F] *= rinv;
+            __syncthreads();
         }
-        __syncthreads();
-        const T rinv = srinv;
-        for (int i = p + 1 + tid; i < F; i += nt) Fm[i + p * F] *= rinv;
-        __syncthreads();
         for (int j = p + 1 + ty; j < F; j += 8) {
             const T u = Fm[p + j * F];
             for (int i = p + 1 + tx; i < F; i += 32) Fm[i + j * F] -= Fm[i + p * F] * u;
         }
         __syncthreads();
     }
+    if (tid == 0) count_pivot_events(nm.stat, n_bad, n_pert);
     T* pan = nm.panel + s.panel_off[f];
     const int m = F - w;
     for (int t = tid; t < F * w; t += nt) pan[t] = Fm[t];
@@ -781,23 +842,37 @@ __global__ void __launch_bounds__(256) front_panel_kernel(DevSched s, DevNum<T> 
         __syncthreads();
     }
     const T floorT = (T)(nm.pivot_eps * __longlong_as_double((long long)nm.stat->amax_bits));
+    // single precision: every thread computes the pivot from the same entry
+    // and the diagonal is written after the scaling barrier (nothing reads it
+    // again in the loop); double precision: thread 0 computes it
+    bool n_bad = false;
+    int n_pert = 0;
     __shared__ T srinv;
-    for (int p = 0; p < w; ++p) {
-        if (tid == 0) {                                           // one reciprocal per pivot
-            const T pv = static_pivot(col[p + (int64_t)p * F], floorT, nm.stat, true);
-            col[p + (int64_t)p * F] = pv;
-            srinv = pivot_rcp(pv);
+    for (int p = 0; p < w; ++p) {                                 // one reciprocal per pivot
+        if constexpr (sizeof(T) == 4) {
+            T rinv;
+            const T pv = uniform_pivot(col[p + (int64_t)p * F], floorT, rinv, n_bad, n_pert);
+            for (int i = p + 1 + tid; i < F; i += nt) col[i + (int64_t)p * F] *= rinv;
+            __syncthreads();
+            if (tid == 0) col[p + (int64_t)p * F] = pv;
+        } else {
+            if (tid == 0) {
+                const T pv = static_pivot(col[p + (int64_t)p * F], floorT, nm.stat, true);
+                col[p + (int64_t)p * F] = pv;
+                srinv = pivot_rcp(pv);
+            }
+            __syncthreads();
+            const T rinv = srinv;
+            for (int i = p + 1 + tid; i < F; i += nt) col[i + (int64_t)p * F] *= rinv;
+            __syncthreads();
         }
-        __syncthreads();
-        const T rinv = srinv;
-        for (int i = p + 1 + tid; i < F; i += nt) col[i + (int64_t)p * F] *= rinv;
-        __syncthreads();
         for (int j = p + 1 + ty; j < w; j += 8) {
             const T u = col[p + (int64_t)j * F];
             for (int i = p + 1 + tx; i < F; i += 32) col[i + (int64_t)j * F] -= col[i + (int64_t)p * F] * u;
         }
         __syncthreads();
     }
+    if (tid == 0) count_pivot_events(nm.stat, n_bad, n_pert);
     T* pan = nm.panel + s.panel_off[f];
     for (int64_t t = tid; t < (int64_t)F * w; t += nt) pan[t] = col[t];
     T* f12 = nm.f12 + s.f12_off[f];

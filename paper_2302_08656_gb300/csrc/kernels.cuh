@@ -102,22 +102,40 @@ struct DevNum {
 // infinities and NaN the IEEE division is used, so the approximation never
 // meets a flushed subnormal.
 #ifdef __CUDACC__
-__device__ __forceinline__ double pivot_rcp(double d)
+// pivot_rcp_fast is the Newton step alone and pivot_rcp_fast_ok tells whether
+// it is pivot_rcp's answer (d inside the range above): a caller on a critical
+// path takes the fast value at once, tests the range off that path and
+// repeats the work with pivot_rcp in the rare case it fails.
+__device__ __forceinline__ bool pivot_rcp_fast_ok(double d)
 {
-    const unsigned eb = ((unsigned)(__double_as_longlong(d) >> 52)) & 0x7ffu;
-    if (eb - 23u > 2000u) return 1.0 / d;
+    return ((((unsigned)(__double_as_longlong(d) >> 52)) & 0x7ffu) - 23u) <= 2000u;
+}
+__device__ __forceinline__ double pivot_rcp_fast(double d)
+{
     double x0;
     asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(x0) : "d"(d));
     const double e = fma(-d, x0, 1.0);
     return fma(x0, fma(e, e, e), x0);
 }
-__device__ __forceinline__ float pivot_rcp(float d)
+__device__ __forceinline__ double pivot_rcp(double d)
 {
-    const unsigned eb = (__float_as_uint(d) >> 23) & 0xffu;
-    if (eb - 27u > 200u) return 1.0f / d;
+    if (!pivot_rcp_fast_ok(d)) return 1.0 / d;
+    return pivot_rcp_fast(d);
+}
+__device__ __forceinline__ bool pivot_rcp_fast_ok(float d)
+{
+    return (((__float_as_uint(d) >> 23) & 0xffu) - 27u) <= 200u;
+}
+__device__ __forceinline__ float pivot_rcp_fast(float d)
+{
     float x0;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x0) : "f"(d));
     return fmaf(x0, fmaf(-d, x0, 1.0f), x0);
+}
+__device__ __forceinline__ float pivot_rcp(float d)
+{
+    if (!pivot_rcp_fast_ok(d)) return 1.0f / d;
+    return pivot_rcp_fast(d);
 }
 #endif
 
@@ -156,6 +174,27 @@ __device__ __forceinline__ float static_pivot(float piv, float floorT, DevStat* 
         return __uint_as_float(fb | (mag ? (b & 0x80000000u) : 0u));
     }
     return piv;
+}
+// The same decision without branches or atomics, for a warp that computes the
+// pivot uniformly (every lane the same value): the events are returned in
+// bad / pert and counted once by the caller.
+__device__ __forceinline__ float static_pivot_sel(float piv, float floorT, bool& bad, bool& pert)
+{
+    const unsigned b = __float_as_uint(piv);
+    const unsigned mag = b & 0x7fffffffu;
+    const unsigned fb = __float_as_uint(floorT);
+    bad = mag >= 0x7f800000u;
+    pert = !bad && mag < fb && fb < 0x7f800000u;
+    return pert ? __uint_as_float(fb | (mag ? (b & 0x80000000u) : 0u)) : piv;
+}
+__device__ __forceinline__ double static_pivot_sel(double piv, double floorT, bool& bad, bool& pert)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(piv);
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    const unsigned long long fb = (unsigned long long)__double_as_longlong(floorT);
+    bad = mag >= 0x7ff0000000000000ull;
+    pert = !bad && mag < fb && fb < 0x7ff0000000000000ull;
+    return pert ? __longlong_as_double((long long)(fb | (mag ? (b & 0x8000000000000000ull) : 0ull))) : piv;
 }
 #endif
 

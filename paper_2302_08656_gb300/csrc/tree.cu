@@ -118,6 +118,54 @@ __device__ bool fwd_unit(const DevSched& s, const TreeSched& ts, const DevNum<T>
                          TreeKid* kids, int* s_cut, int* s_ok, unsigned char* smraw, int* done_b,
                          const int* fac_done, int* abort_flag, long long limit);
 
+// Panel step of the single-precision elimination: warp 0, lane -> row p0 +
+// lane, a[k] = column p0 + k of the panel (pk <= 8 active columns), loaded
+// from M. Pivot k is computed by every lane from lane k's entry (a shuffle,
+// then the static pivot and the reciprocal: the same values on every lane,
+// so nothing diverges) and its events are counted once, in bad / pert. FAST:
+// the reciprocal's Newton step without its range test; returns false if a
+// pivot fell outside that range (the caller then repeats the panel with the
+// full pivot_rcp, from the same entries of M). Every entry gets the
+// operations of the one-pivot schedule in pivot order.
+template <bool FAST>
+__device__ __forceinline__ bool panel_f32(const float* M, int Fr, int p0, int pk, int row, float floorT, float (&a)[8],
+                                          int& bad, int& pert)
+{
+    const int tx = threadIdx.x & 31;
+    bool ok = true;
+    bad = 0;
+    pert = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (k < pk && row < Fr) ? M[row + (p0 + k) * Fr] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const bool act = k < pk;                                   // warp-uniform
+        float u[8];
+#pragma unroll
+        for (int kk = k + 1; kk < 8; ++kk) u[kk] = __shfl_sync(0xffffffffu, a[kk], k);   // pivot row p0 + k
+        const float x = __shfl_sync(0xffffffffu, a[k], k);
+        bool b1, p1;
+        const float piv = static_pivot_sel(x, floorT, b1, p1);
+        float r;
+        if (FAST) {
+            r = pivot_rcp_fast(piv);
+            ok = ok && (!act || pivot_rcp_fast_ok(piv));
+        } else {
+            r = pivot_rcp(piv);
+        }
+        if (act) {
+            bad |= (int)b1;
+            pert += (int)p1;
+        }
+        const bool lk = act && tx == k, below = act && tx > k;
+        a[k] = lk ? piv : (below ? a[k] * r : a[k]);               // l below the pivot
+#pragma unroll
+        for (int kk = k + 1; kk < 8; ++kk)
+            if (below) a[kk] -= a[k] * u[kk];
+    }
+    return ok;
+}
+
 // ------------------------------------------------------------- refactor
 
 // Unit (q, ti, tj) of instance b. Mini front M (Fr x Fc, column-major, ld Fr):
@@ -136,10 +184,9 @@ __device__ bool fwd_unit(const DevSched& s, const TreeSched& ts, const DevNum<T>
 // completion counters are each context's own. The descriptors of the current
 // unit's context are cached in shared memory.
 template <typename T, bool MULTI>
-__global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s_p, TreeSched ts_p, DevNum<T> nm0_p, int B_p,
-                                                          int* ctr, int* stall, long long limit, int fused, int u0,
-                                                          int nu, int tick, const TreeJob<T>* jobs,
-                                                          const TreeSeg* segs, int nseg)
+__device__ __forceinline__ void tree_factor_body(DevSched s_p, TreeSched ts_p, DevNum<T> nm0_p, int B_p, int* ctr,
+                                                 int* stall, long long limit, int fused, int u0, int nu, int tick,
+                                                 const TreeJob<T>* jobs, const TreeSeg* segs, int nseg)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ TreeFront d;
@@ -303,58 +350,57 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s_p, TreeSche
         if (sizeof(T) == 4 && Fr <= 32 && Fc <= 32) {
             // single precision, blocked by kPanel pivots: warp 0 factors the
             // panel (pivot columns p0 .. p0 + pk - 1, lane -> row p0 + lane) in
-            // registers without a CTA barrier; then every warp applies the
-            // panel to its trailing columns (lane -> row, one shuffle per pivot
-            // for the row's U entry). Each entry still receives its updates in
-            // pivot order with the same roundings as the one-pivot schedule.
-            // Two barriers per kPanel pivots instead of one per pivot.
+            // registers without a CTA barrier; then every warp applies it to its
+            // trailing columns (lane -> row, one shuffle per pivot for the row's
+            // U entry, three columns of a warp interleaved). Each entry still
+            // receives its updates in pivot order with the same roundings as the
+            // one-pivot schedule. Two barriers per kPanel pivots.
             constexpr int kPanel = 8;
+            int n_bad = 0, n_pert = 0;                             // static-pivot events, counted once
             for (int p0 = 0; p0 < w; p0 += kPanel) {
                 const int pk = min(kPanel, w - p0);
                 const int row = p0 + tx;
                 if (ty == 0) {
-                    T a[kPanel];
-#pragma unroll
-                    for (int k = 0; k < kPanel; ++k) a[k] = (k < pk && row < Fr) ? M[row + (p0 + k) * Fr] : T(0);
-#pragma unroll
-                    for (int k = 0; k < kPanel; ++k) {
-                        if (k < pk) {                                  // warp-uniform
-                            T r = T(0);
-                            if (tx == k) {
-                                a[k] = static_pivot(a[k], floorT, nm.stat, lead);
-                                r = pivot_rcp(a[k]);
-                            }
-                            r = __shfl_sync(0xffffffffu, r, k);
-                            if (tx > k) a[k] *= r;                     // l below the pivot
-#pragma unroll
-                            for (int kk = k + 1; kk < kPanel; ++kk) {
-                                const T u = __shfl_sync(0xffffffffu, a[kk], k);
-                                if (tx > k && kk < pk) a[kk] -= a[k] * u;
-                            }
-                        }
-                    }
+                    float a[kPanel];
+                    int pb = 0, pp = 0;
+                    const float* Mf = reinterpret_cast<const float*>(M);
+                    const float fl = (float)floorT;
+                    if (!panel_f32<true>(Mf, Fr, p0, pk, row, fl, a, pb, pp))
+                        panel_f32<false>(Mf, Fr, p0, pk, row, fl, a, pb, pp);   // a reciprocal out of range
+                    n_bad |= pb;
+                    n_pert += pp;
                     if (row < Fr)
 #pragma unroll
                         for (int k = 0; k < kPanel; ++k)
-                            if (k < pk) M[row + (p0 + k) * Fr] = a[k];
+                            if (k < pk) M[row + (p0 + k) * Fr] = (T)a[k];
                 }
                 __syncthreads();
                 // trailing columns j >= p0 + pk: warp ty takes j = p0 + pk + ty + 8 c
                 T lp[kPanel];
 #pragma unroll
                 for (int k = 0; k < kPanel; ++k) lp[k] = (k < pk && row < Fr) ? M[row + (p0 + k) * Fr] : T(0);
-                for (int j = p0 + pk + ty; j < Fc; j += 8) {
-                    T v = row < Fr ? M[row + j * Fr] : T(0);
+                for (int jb = p0 + pk + ty; jb < Fc; jb += 24) {
+                    T v[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) v[c] = (row < Fr && jb + 8 * c < Fc) ? M[row + (jb + 8 * c) * Fr] : T(0);
 #pragma unroll
                     for (int k = 0; k < kPanel; ++k) {
-                        if (k < pk) {                                  // warp-uniform
-                            const T u = __shfl_sync(0xffffffffu, v, k);  // row p0 + k: final at step k
-                            if (tx > k) v -= lp[k] * u;
+                        const bool upd = k < pk && tx > k;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const T u = __shfl_sync(0xffffffffu, v[c], k);   // row p0 + k: final at step k
+                            if (upd) v[c] -= lp[k] * u;
                         }
                     }
-                    if (row < Fr) M[row + j * Fr] = v;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        if (row < Fr && jb + 8 * c < Fc) M[row + (jb + 8 * c) * Fr] = v[c];
                 }
                 __syncthreads();
+            }
+            if (ty == 0 && lead && (n_bad | n_pert)) {                 // warp-uniform
+                if (tx == 0 && n_bad) atomicExch(&nm.stat->numeric_bad, 1);
+                if (tx == 0 && n_pert) atomicAdd(&nm.stat->n_perturbed, n_pert);
             }
         } else if (Fr <= 32 && Fc <= 32) {
             // mini fronts of at most 32 x 32 (always when w <= 16). GB300 runs
@@ -472,6 +518,31 @@ __global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s_p, TreeSche
         __syncthreads();
     }
 }
+
+// Entry points: in single precision the kernel is held to 64 registers, so
+// that 4 CTAs fit on an SM; double precision keeps the compiler's choice.
+template <typename T, bool MULTI>
+__global__ void __launch_bounds__(256) tree_factor_kernel(DevSched s, TreeSched ts, DevNum<T> nm, int B, int* ctr,
+                                                          int* stall, long long limit, int fused, int u0, int nu,
+                                                          int tick, const TreeJob<T>* jobs, const TreeSeg* segs,
+                                                          int nseg)
+{
+    tree_factor_body<T, MULTI>(s, ts, nm, B, ctr, stall, limit, fused, u0, nu, tick, jobs, segs, nseg);
+}
+
+template <bool MULTI>
+__global__ void __launch_bounds__(256, 4) tree_factor_kernel_f32(DevSched s, TreeSched ts, DevNum<float> nm, int B,
+                                                                 int* ctr, int* stall, long long limit, int fused,
+                                                                 int u0, int nu, int tick, const TreeJob<float>* jobs,
+                                                                 const TreeSeg* segs, int nseg)
+{
+    tree_factor_body<float, MULTI>(s, ts, nm, B, ctr, stall, limit, fused, u0, nu, tick, jobs, segs, nseg);
+}
+
+template <bool MULTI>
+auto tree_factor_entry(const float*) { return tree_factor_kernel_f32<MULTI>; }
+template <bool MULTI>
+auto tree_factor_entry(const double*) { return tree_factor_kernel<double, MULTI>; }
 
 // ------------------------------------------------------ forward substitution
 
@@ -802,8 +873,8 @@ cudaError_t tree_grid(int kind, size_t smem, int* grid)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
-    if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_factor_kernel<T, false>, 256, smem);
-    else if (kind == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_factor_kernel<T, true>, 256, smem);
+    if (kind == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_factor_entry<false>((const T*)nullptr), 256, smem);
+    else if (kind == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_factor_entry<true>((const T*)nullptr), 256, smem);
     else if (kind == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_fwd_kernel<T>, 128, smem);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tree_bwd_kernel<T>, 128, smem);
     if (e != cudaSuccess) return e;
@@ -831,7 +902,7 @@ cudaError_t launch_tree_factor(const DevSched& s, const TreeSched& t, const DevN
         return cudaErrorInvalidValue;                         // schedule not uploaded: never launch on it
     if (u0 < 0 || nu < 0 || u0 + nu > (fused ? t.nunits_fused : t.nunits) || (tick != 0 && tick != 3))
         return cudaErrorInvalidValue;
-    tree_factor_kernel<T, false><<<g, 256, smem, st>>>(s, t, nm, batch, ctr, stall, spin_limit, fused, u0, nu, tick,
+    tree_factor_entry<false>((const T*)nullptr)<<<g, 256, smem, st>>>(s, t, nm, batch, ctr, stall, spin_limit, fused, u0, nu, tick,
                                                        nullptr, nullptr, 0);
     return cudaGetLastError();
 }
@@ -843,7 +914,7 @@ cudaError_t launch_tree_factor_group(const TreeJob<T>* jobs, const TreeSeg* segs
     const int g = std::min(grid, total);
     if (g <= 0) return cudaSuccess;
     if (!jobs || !segs || nseg <= 0 || !gctr) return cudaErrorInvalidValue;
-    tree_factor_kernel<T, true><<<g, 256, smem, st>>>(DevSched{}, TreeSched{}, DevNum<T>{}, 1, gctr, nullptr,
+    tree_factor_entry<true>((const T*)nullptr)<<<g, 256, smem, st>>>(DevSched{}, TreeSched{}, DevNum<T>{}, 1, gctr, nullptr,
                                                       spin_limit, 0, 0, total, 0, jobs, segs, nseg);
     return cudaGetLastError();
 }
@@ -895,10 +966,10 @@ static cudaError_t allow_smem_tree(K kernel, int optin)
 cudaError_t configure_tree_kernels(int optin)
 {
     cudaError_t e;
-    if ((e = allow_smem_tree(tree_factor_kernel<double, false>, optin))) return e;
-    if ((e = allow_smem_tree(tree_factor_kernel<float, false>, optin))) return e;
-    if ((e = allow_smem_tree(tree_factor_kernel<double, true>, optin))) return e;
-    if ((e = allow_smem_tree(tree_factor_kernel<float, true>, optin))) return e;
+    if ((e = allow_smem_tree(tree_factor_entry<false>((const double*)nullptr), optin))) return e;
+    if ((e = allow_smem_tree(tree_factor_entry<false>((const float*)nullptr), optin))) return e;
+    if ((e = allow_smem_tree(tree_factor_entry<true>((const double*)nullptr), optin))) return e;
+    if ((e = allow_smem_tree(tree_factor_entry<true>((const float*)nullptr), optin))) return e;
     if ((e = allow_smem_tree(tree_fwd_kernel<double>, optin))) return e;
     if ((e = allow_smem_tree(tree_fwd_kernel<float>, optin))) return e;
     if ((e = allow_smem_tree(tree_bwd_kernel<double>, optin))) return e;
