@@ -252,6 +252,11 @@ struct TreeSched {
     int fwd_stage = 0;           // 1: forward solve stages the F x w panel in shared memory
     int bwd_stage = 0;           // 1: backward solve stages U12 in shared memory
     int max_fw = 0, max_wm = 0;
+    // backward substitution by chains: chain c is the fronts bwd_chain[bwd_chain_ptr[c] ..
+    // bwd_chain_ptr[c + 1] - 1], top first, each the only tree child of the one before
+    const int* bwd_chain = nullptr;
+    const int* bwd_chain_ptr = nullptr;
+    int nchains = 0;
 };
 // One context of a group whose tree parts run in one launch (see
 // tree_factor_kernel): its schedule, numeric buffers, instances and counter

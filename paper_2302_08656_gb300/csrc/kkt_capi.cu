@@ -1154,6 +1154,7 @@ static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_opti
     add(nq * (int64_t)sizeof(TreeFront)); add((int64_t)tp.kid.size() * (int64_t)sizeof(TreeKid));
     add((int64_t)tp.unit.size() * (int64_t)sizeof(FrontTile)); add((int64_t)tp.inv.size() * 4);
     add((int64_t)tp.unit_fused.size() * (int64_t)sizeof(FrontTile));
+    add((int64_t)tp.bwd_chain.size() * 4); add((int64_t)tp.bwd_chain_ptr.size() * 4);
     add((kCtrHead + 2 * B * nq) * 4); add((kCtrHead + 2 * B * nq) * 4); add(2 * 4);
     add((n + 1) * 4); add(std::max<int64_t>((int64_t)an.rel.size(), 1) * 4);
     add((3 * (int64_t)n + std::max<int64_t>((int64_t)an.rel.size(), 1)) * es);
@@ -1363,6 +1364,8 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     FrontTile* tunit = P.take<FrontTile>(tp.unit.size());
     FrontTile* tunit_fused = P.take<FrontTile>(tp.unit_fused.size());
     int* tinv = P.take<int>(tp.inv.size());
+    int* tchain = P.take<int>(tp.bwd_chain.size());
+    int* tchain_ptr = P.take<int>(tp.bwd_chain_ptr.size());
     c->ctr_fac = P.take<int>(kCtrHead + 2 * B * nq);
     c->ctr_sol = P.take<int>(kCtrHead + 2 * B * nq);
     c->stall = P.take<int>(2);
@@ -1427,6 +1430,8 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     e = e ? e : up(tunit, tp.unit.data(), tp.unit.size() * sizeof(FrontTile));
     e = e ? e : up(tunit_fused, tp.unit_fused.data(), tp.unit_fused.size() * sizeof(FrontTile));
     e = e ? e : up(tinv, tp.inv.data(), tp.inv.size() * 4);
+    e = e ? e : up(tchain, tp.bwd_chain.data(), tp.bwd_chain.size() * 4);
+    e = e ? e : up(tchain_ptr, tp.bwd_chain_ptr.data(), tp.bwd_chain_ptr.size() * 4);
     e = e ? e : cudaMemsetAsync(c->stall, 0, 2 * sizeof(int), ust);
     {
         // per step row i: contribution-vector offsets rel_ptr[f] + t of every front f whose
@@ -1464,6 +1469,8 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     c->tsched = tp.ts;
     c->tsched.fr = tfr; c->tsched.kid = tkid; c->tsched.unit = tunit; c->tsched.inv = tinv;
     c->tsched.unit_fused = tunit_fused;
+    c->tsched.bwd_chain = tchain;
+    c->tsched.bwd_chain_ptr = tchain_ptr;
     c->tree_split = tp.split;
     c->tree_bytes = tp.alg_bytes;
     c->tree_nnz_k = tp.nnz_k;

@@ -766,99 +766,158 @@ __global__ void __launch_bounds__(128) tree_fwd_kernel(DevSched s, TreeSched ts,
 
 // ------------------------------------------------------ backward substitution
 
-// Front q of instance b, tickets in reverse tree order (parents first): the
-// solution entries of the front's other rows belong to its ancestors, which
-// are complete once its parent is.
+// Asynchronous copy of one 4- or 8-byte word into shared memory (cp.async),
+// and the wait for every copy this thread has issued.
+__device__ __forceinline__ void cp_word(void* smem_dst, const void* gsrc, int bytes)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gsrc) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Chain c of instance b (TreeSched::bwd_chain), tickets in chain order
+// (parents first): the solution entries of a front's other rows belong to its
+// ancestors, which are complete once its parent is. The first front of a
+// chain waits for its parent's chain and gathers those entries from the
+// solution vector; every later front of the chain is the only tree child of
+// the one before it, whose whole front (its pivots just solved and its other
+// rows) is still in shared memory, so it takes them from there through its
+// relative indices -- the same values, with no wait and no round trip
+// through memory. The static data of the next front (pivot block, U12, own
+// pivot entries, indices) is copied by cp.async into the second staging
+// buffer while the current front is solved. Completion is signalled once,
+// for the last front of the chain: the only front whose children in the tree
+// part are outside it.
 template <typename T>
 __global__ void __launch_bounds__(128) tree_bwd_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
                                                        long long limit)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ TreeFront d;
+    __shared__ TreeFront dd[2];
     __shared__ int s_t, s_ok;
     __shared__ T red[128];
     __shared__ T rcp[64];                                       // 1 / u_pp of the pivot block (w <= 64)
     const int tid = threadIdx.x, lane = tid & 31;
-    const int total = ts.nq * B;
+    const int total = ts.nchains * B;
     int* done = ctr + kCtrHead + ts.nq * B;                     // after the forward counters
-    T* v = reinterpret_cast<T*>(smraw);
-    T* y = v + ts.max_F;                                        // own pivot entries
-    T* Us = y + ts.max_w;
-    T* U12s = Us + ts.max_w * ts.max_w;
-    int* ridx = reinterpret_cast<int*>(U12s + (ts.bwd_stage ? ts.max_wm : 0));
+    const int stage_len = ts.max_w + ts.max_w * ts.max_w + (ts.bwd_stage ? ts.max_wm : 0);
+    T* vb = reinterpret_cast<T*>(smraw);                        // v of the two last fronts: vb, vb + max_F
+    T* stg = vb + 2 * ts.max_F;                                 // staging buffers: y, Us, U12s (twice)
+    int* rix = reinterpret_cast<int*>(stg + 2 * stage_len);     // index buffers (twice)
+    // issue the copies of front d's static data into staging buffer sb
+    auto stage = [&](int sb, const TreeFront& d, bool first_of_chain, const DevNum<T>& nm) {
+        T* y = stg + sb * stage_len;
+        T* Us = y + ts.max_w;
+        T* U12s = Us + ts.max_w * ts.max_w;
+        int* ridx = rix + sb * ts.max_F;
+        const int w = d.w, F = d.F, m = F - w;
+        const T* pan = nm.panel + d.panel_off;
+        const int* src = first_of_chain ? s.rows + d.rows_ptr + w : s.rel + d.rel_ptr;
+        for (int tt = tid; tt < m; tt += 128) cp_word(ridx + tt, src + tt, 4);
+        for (int a = tid; a < w; a += 128) cp_word(y + a, nm.vec + d.first + a, (int)sizeof(T));
+        for (int c = tid >> 5; c < w; c += 4)
+            for (int a = lane; a < w; a += 32) cp_word(Us + a + c * w, pan + a + (int64_t)c * F, (int)sizeof(T));
+        if (ts.bwd_stage) {
+            const T* U12 = pan + (int64_t)F * w;
+            for (int e = tid; e < w * m; e += 128) cp_word(U12s + e, U12 + e, (int)sizeof(T));
+        }
+    };
     for (;;) {
         const int t = next_ticket(ctr + 3, ctr + 1, total, &s_t);
         if (t >= total) break;
-        const int uq = t / B, b = t - uq * B;
-        const int q = ts.nq - 1 - uq;
-        copy_words(&d, ts.fr + q, 1, tid, 128);
-        __syncthreads();
+        const int ci = t / B, b = t - ci * B;
+        const int k0 = ts.bwd_chain_ptr[ci], k1 = ts.bwd_chain_ptr[ci + 1];
         const DevNum<T> nm = nm0.at(b);
-        const int w = d.w, F = d.F, first = d.first, m = F - w;
-        const T* pan = nm.panel + d.panel_off;
-        const T* U12 = pan + (int64_t)F * w;
-        const int* R = s.rows + d.rows_ptr;
-        for (int tt = tid; tt < m; tt += 128) ridx[tt] = R[w + tt];
-        for (int a = tid; a < w; a += 128) y[a] = nm.vec[first + a];
-        for (int c = tid >> 5; c < w; c += 4)
-            for (int a = lane; a < w; a += 32) Us[a + c * w] = pan[a + (int64_t)c * F];
-        for (int a = tid; a < w; a += 128) rcp[a] = pivot_rcp(pan[a + (int64_t)a * F]);
-        if (ts.bwd_stage)
-            for (int e = tid; e < w * m; e += 128) U12s[e] = U12[e];
-        if (tid < 32) {
-            TreeKid par{};
-            par.q = d.parent;
-            const int ok = warp_wait_kids(done + (int64_t)b * ts.nq, &par, 1, true, ctr + 1, limit);
-            if (tid == 0) s_ok = ok;
-        }
+        copy_words(&dd[0], ts.fr + ts.bwd_chain[k0], 1, tid, 128);
         __syncthreads();
-        if (!s_ok) {
-            if (tid == 0) atomicExch(&nm.stat->timeout, 1);
-            break;
-        }
-        for (int tt = tid; tt < m; tt += 128) v[w + tt] = __ldcg(nm.vec + ridx[tt]);
-        __syncthreads();
-        // y_a - sum_t U12[a, t] x_t, in the order every backward kernel uses:
-        // in sequence for m <= kSeqSum, else 128 / w interleaved partial sums per row
-        if (m <= kSeqSum) {
-            for (int a = tid; a < w; a += 128) {
-                T acc = y[a];
-                for (int tt = 0; tt < m; ++tt) acc -= U12[a + (int64_t)tt * w] * v[w + tt];
-                v[a] = acc;
+        stage(0, dd[0], true, nm);
+        bool stop = false;
+        int q = -1;
+        for (int k = k0; k < k1; ++k) {
+            const int sb = (k - k0) & 1;
+            q = ts.bwd_chain[k];
+            if (k + 1 < k1) copy_words(&dd[sb ^ 1], ts.fr + ts.bwd_chain[k + 1], 1, tid, 128);
+            cp_wait_all();                                       // this front's staging
+            if (k == k0 && tid < 32) {
+                TreeKid par{};
+                par.q = dd[sb].parent;
+                const int ok = warp_wait_kids(done + (int64_t)b * ts.nq, &par, 1, true, ctr + 1, limit);
+                if (tid == 0) s_ok = ok;
             }
-        } else {
-            const int G = 128 / w;
-            T part = T(0);
-            if (tid < G * w) {
-                const int a = tid % w, g = tid / w;
-                if (ts.bwd_stage)
-                    for (int tt = g; tt < m; tt += G) part += U12s[a + tt * w] * v[w + tt];
-                else
-                    for (int tt = g; tt < m; tt += G) part += U12[a + (int64_t)tt * w] * v[w + tt];
-            }
-            red[tid] = part;
             __syncthreads();
-            for (int a = tid; a < w; a += 128) {
-                T acc = T(0);
-                for (int g = 0; g < G; ++g) acc += red[a + g * w];
-                v[a] = y[a] - acc;
+            if (k == k0 && !s_ok) {
+                if (tid == 0) atomicExch(&nm.stat->timeout, 1);
+                stop = true;
+                break;
             }
-        }
-        __syncthreads();
-        if (tid < 32) {
-            if (w <= 32)
-                warp_upper_solve(v, Us, rcp, w);
+            const int w = dd[sb].w, F = dd[sb].F, first = dd[sb].first, m = F - w;
+            const T* U12 = nm.panel + dd[sb].panel_off + (int64_t)F * w;
+            const T* y = stg + sb * stage_len;
+            const T* Us = y + ts.max_w;
+            const T* U12s = Us + ts.max_w * ts.max_w;
+            const int* ridx = rix + sb * ts.max_F;
+            T* v = vb + sb * ts.max_F;
+            const T* pv = vb + (sb ^ 1) * ts.max_F;              // the previous front of the chain
+            if (k + 1 < k1) stage(sb ^ 1, dd[sb ^ 1], false, nm);   // in flight while this front is solved
+            for (int a = tid; a < w; a += 128) rcp[a] = pivot_rcp(Us[a + a * w]);
+            if (k == k0)
+                for (int tt = tid; tt < m; tt += 128) v[w + tt] = __ldcg(nm.vec + ridx[tt]);
             else
-                for (int p = w - 1; p >= 0; --p) {
-                    const T xp = v[p] * rcp[p];
-                    __syncwarp();
-                    if (lane == 0) v[p] = xp;
-                    for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
-                    __syncwarp();
+                for (int tt = tid; tt < m; tt += 128) v[w + tt] = pv[ridx[tt]];
+            __syncthreads();
+            // y_a - sum_t U12[a, t] x_t, in the order every backward kernel uses:
+            // in sequence for m <= kSeqSum, else 128 / w interleaved partial sums per row
+            if (m <= kSeqSum) {
+                for (int a = tid; a < w; a += 128) {
+                    T acc = y[a];
+                    if (ts.bwd_stage)
+                        for (int tt = 0; tt < m; ++tt) acc -= U12s[a + tt * w] * v[w + tt];
+                    else
+                        for (int tt = 0; tt < m; ++tt) acc -= U12[a + (int64_t)tt * w] * v[w + tt];
+                    v[a] = acc;
                 }
+            } else {
+                const int G = 128 / w;
+                T part = T(0);
+                if (tid < G * w) {
+                    const int a = tid % w, g = tid / w;
+                    if (ts.bwd_stage)
+                        for (int tt = g; tt < m; tt += G) part += U12s[a + tt * w] * v[w + tt];
+                    else
+                        for (int tt = g; tt < m; tt += G) part += U12[a + (int64_t)tt * w] * v[w + tt];
+                }
+                red[tid] = part;
+                __syncthreads();
+                for (int a = tid; a < w; a += 128) {
+                    T acc = T(0);
+                    for (int g = 0; g < G; ++g) acc += red[a + g * w];
+                    v[a] = y[a] - acc;
+                }
+            }
+            __syncthreads();
+            if (tid < 32) {
+                if (w <= 32)
+                    warp_upper_solve(v, Us, rcp, w);
+                else
+                    for (int p = w - 1; p >= 0; --p) {
+                        const T xp = v[p] * rcp[p];
+                        __syncwarp();
+                        if (lane == 0) v[p] = xp;
+                        for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
+                        __syncwarp();
+                    }
+            }
+            __syncthreads();
+            for (int a = tid; a < w; a += 128) nm.vec[first + a] = v[a];
         }
-        __syncthreads();
-        for (int a = tid; a < w; a += 128) nm.vec[first + a] = v[a];
+        if (stop) break;
         signal_done(done + (int64_t)b * ts.nq + q);
         __syncthreads();
     }
@@ -934,9 +993,9 @@ template <typename T>
 cudaError_t launch_tree_bwd(const DevSched& s, const TreeSched& t, const DevNum<T>& nm, int batch, int* ctr,
                             long long spin_limit, int grid, size_t smem, cudaStream_t st)
 {
-    const int g = std::min<long long>(grid, (long long)t.nq * batch);
+    const int g = std::min<long long>(grid, (long long)t.nchains * batch);
     if (g <= 0) return cudaSuccess;
-    if (t.fr == nullptr) return cudaErrorInvalidValue;
+    if (t.fr == nullptr || t.bwd_chain == nullptr || t.bwd_chain_ptr == nullptr) return cudaErrorInvalidValue;
     tree_bwd_kernel<T><<<g, 128, smem, st>>>(s, t, nm, batch, ctr, spin_limit);
     return cudaGetLastError();
 }

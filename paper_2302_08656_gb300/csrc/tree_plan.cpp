@@ -108,6 +108,27 @@ void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp)
             ts.max_wm = std::max(ts.max_wm, w * m);
         }
     ts.nunits = (int)tp.unit.size();
+    // backward chains (see TreePlan)
+    {
+        std::vector<int> ntk(nq, 0), only(nq, -1);
+        for (int q = 0; q < nq; ++q)
+            for (int c = tp.fr[q].kid_begin; c < tp.fr[q].kid_end; ++c)
+                if (tp.kid[c].q >= 0) {
+                    ++ntk[q];
+                    only[q] = tp.kid[c].q;
+                }
+        tp.bwd_chain_ptr.push_back(0);
+        for (int q = nq - 1; q >= 0; --q) {
+            const int p = tp.fr[q].parent;
+            if (p >= 0 && ntk[p] == 1) continue;                  // continues its parent's chain
+            for (int x = q;; x = only[x]) {
+                tp.bwd_chain.push_back(x);
+                if (ntk[x] != 1) break;
+            }
+            tp.bwd_chain_ptr.push_back((int)tp.bwd_chain.size());
+        }
+        ts.nchains = (int)tp.bwd_chain_ptr.size() - 1;
+    }
     // fused order: level by level, the factorization units of the level, then its forward units
     for (int l = split, u = 0; l < an.n_levels; ++l) {
         const int q0 = tq[order[l].front()];
@@ -118,7 +139,7 @@ void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp)
     ts.nunits_fused = (int)tp.unit_fused.size();
     ts.max_kids = std::max(ts.max_kids, 1);
     ts.fwd_stage = (size_t)ts.max_fw * es <= kStageLimit ? 1 : 0;
-    ts.bwd_stage = (size_t)ts.max_wm * es <= kStageLimit ? 1 : 0;
+    ts.bwd_stage = 2 * (size_t)ts.max_wm * es <= kStageLimit ? 1 : 0;   // two fronts staged at a time
     ts.kid_off = tree_kid_offset(ts, es);
     tp.fac_smem = tree_factor_smem(ts, es);
     tp.fwd_smem = tree_fwd_smem(ts, es);
@@ -157,8 +178,11 @@ size_t tree_fwd_smem(const TreeSched& t, size_t es)
 
 size_t tree_bwd_smem(const TreeSched& t, size_t es)
 {
-    size_t b = es * ((size_t)t.max_F + t.max_w + (size_t)t.max_w * t.max_w + (t.bwd_stage ? (size_t)t.max_wm : 0));
-    return b + 4 * (size_t)t.max_F;
+    // v of the current and of the previous front of a chain (max_F each), then
+    // two staging buffers (the current front's and the next one's: own pivot
+    // entries, pivot block, staged U12), then two index buffers
+    const size_t stage = (size_t)t.max_w + (size_t)t.max_w * t.max_w + (t.bwd_stage ? (size_t)t.max_wm : 0);
+    return es * (2 * (size_t)t.max_F + 2 * stage) + 4 * 2 * (size_t)t.max_F;
 }
 
 }  // namespace kktgb

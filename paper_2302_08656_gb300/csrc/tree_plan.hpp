@@ -22,6 +22,12 @@ struct TreePlan {
     std::vector<FrontTile> unit;
     std::vector<FrontTile> unit_fused;  // factor units and, after each level, its forward-solve units (ti = -1)
     std::vector<int> inv;
+    // chains of the backward substitution: a chain starts at a root or at a
+    // front whose parent has two or more children in the tree part, and
+    // continues while the last front has exactly one child in the tree part;
+    // chains in descending order of their first front (a chain waits only for
+    // the chain that holds its first front's parent, which comes earlier)
+    std::vector<int> bwd_chain, bwd_chain_ptr;
     TreeSched ts;
     size_t fac_smem = 0, fwd_smem = 0, bwd_smem = 0;
     int64_t alg_bytes = 0;              // multifrontal traffic of one refactorization of the tree part

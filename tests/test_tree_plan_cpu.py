@@ -48,7 +48,7 @@ def _plan(tool, tmp_path, pat, max_pivots, min_fronts):
     subprocess.run([tool, src, out, str(max_pivots), str(min_fronts)], check=True)
     r = {k: np.fromfile(out + "." + k, dtype=np.int64)
          for k in ["head", "fr", "kid", "unit", "fused", "level", "sn_parent", "child_ptr", "child_list", "asm_ptr",
-                   "sn_first", "sn_front"]}
+                   "sn_first", "sn_front", "bwd_chain", "bwd_chain_ptr"]}
     r["fr"] = r["fr"].reshape(-1, 6)
     r["unit"] = r["unit"].reshape(-1, 3)
     r["fused"] = r["fused"].reshape(-1, 3)
@@ -126,6 +126,28 @@ def test_tree_plan_orders_every_dependency_first(dump_tool, tmp_path, buses, max
         for c in kid[fr[q, 4]:fr[q, 5]]:
             if c >= 0:
                 assert pos_fwd[c] < pos_fwd[q] and last_fac[c] < first_fac[q]
+    # backward chains: every front exactly once; a chain starts at a root or
+    # at a front whose parent has two or more children in the tree part and
+    # continues through single tree children; the chain holding a chain's
+    # first front's parent comes earlier
+    chain, cptr = P["bwd_chain"], P["bwd_chain_ptr"]
+    assert cptr[0] == 0 and cptr[-1] == nq and np.all(np.diff(cptr) > 0)
+    assert sorted(chain.tolist()) == list(range(nq))
+    tree_kids = [[c for c in kid[fr[q, 4]:fr[q, 5]] if c >= 0] for q in range(nq)]
+    chain_of = np.empty(nq, dtype=np.int64)
+    for ci in range(len(cptr) - 1):
+        members = chain[cptr[ci]:cptr[ci + 1]]
+        chain_of[members] = ci
+        top = members[0]
+        assert fr[top, 1] < 0 or len(tree_kids[fr[top, 1]]) >= 2
+        for a_, b_ in zip(members[:-1], members[1:]):
+            assert tree_kids[a_] == [b_]
+        assert len(tree_kids[members[-1]]) != 1
+    for ci in range(len(cptr) - 1):
+        top = chain[cptr[ci]]
+        if fr[top, 1] >= 0:
+            assert chain_of[fr[top, 1]] < ci
+            assert chain[cptr[chain_of[fr[top, 1]] + 1] - 1] == fr[top, 1]     # the parent ends its chain
 
 
 @pytest.mark.parametrize("buses,max_pivots,min_fronts", [(2000, 16, 2432), (500, 8, 100000)])

@@ -68,5 +68,7 @@ int main(int argc, char** argv)
     write_all(out + ".asm_ptr", std::vector<int64_t>(a.asm_ptr.begin(), a.asm_ptr.end()));
     write_all(out + ".sn_first", std::vector<int64_t>(a.sn_first.begin(), a.sn_first.end()));
     write_all(out + ".sn_front", std::vector<int64_t>(a.sn_front.begin(), a.sn_front.end()));
+    write_all(out + ".bwd_chain", std::vector<int64_t>(tp.bwd_chain.begin(), tp.bwd_chain.end()));
+    write_all(out + ".bwd_chain_ptr", std::vector<int64_t>(tp.bwd_chain_ptr.begin(), tp.bwd_chain_ptr.end()));
     return 0;
 }
