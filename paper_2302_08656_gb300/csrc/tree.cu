@@ -792,7 +792,8 @@ __device__ __forceinline__ void cp_wait_all()
 // relative indices -- the same values, with no wait and no round trip
 // through memory. The static data of the next front (pivot block, U12, own
 // pivot entries, indices) is copied by cp.async into the second staging
-// buffer while the current front is solved. Completion is signalled once,
+// buffer while the current front is solved, and the descriptor of the front
+// after it alongside (three descriptor slots). Completion is signalled once,
 // for the last front of the chain: the only front whose children in the tree
 // part are outside it.
 template <typename T>
@@ -800,7 +801,7 @@ __global__ void __launch_bounds__(128) tree_bwd_kernel(DevSched s, TreeSched ts,
                                                        long long limit)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ TreeFront dd[2];
+    __shared__ TreeFront dd[3];
     __shared__ int s_t, s_ok;
     __shared__ T red[128];
     __shared__ T rcp[64];                                       // 1 / u_pp of the pivot block (w <= 64)
@@ -811,8 +812,10 @@ __global__ void __launch_bounds__(128) tree_bwd_kernel(DevSched s, TreeSched ts,
     T* vb = reinterpret_cast<T*>(smraw);                        // v of the two last fronts: vb, vb + max_F
     T* stg = vb + 2 * ts.max_F;                                 // staging buffers: y, Us, U12s (twice)
     int* rix = reinterpret_cast<int*>(stg + 2 * stage_len);     // index buffers (twice)
-    // issue the copies of front d's static data into staging buffer sb
-    auto stage = [&](int sb, const TreeFront& d, bool first_of_chain, const DevNum<T>& nm) {
+    // issue the copies of front d's static data into staging buffer sb, by
+    // threads t0 .. t0 + nthr - 1 (whole warps) of the CTA
+    auto stage = [&](int sb, const TreeFront& d, bool first_of_chain, const DevNum<T>& nm, int t0, int nthr) {
+        const int me = tid - t0, wi = me >> 5, nw = nthr >> 5;
         T* y = stg + sb * stage_len;
         T* Us = y + ts.max_w;
         T* U12s = Us + ts.max_w * ts.max_w;
@@ -820,14 +823,21 @@ __global__ void __launch_bounds__(128) tree_bwd_kernel(DevSched s, TreeSched ts,
         const int w = d.w, F = d.F, m = F - w;
         const T* pan = nm.panel + d.panel_off;
         const int* src = first_of_chain ? s.rows + d.rows_ptr + w : s.rel + d.rel_ptr;
-        for (int tt = tid; tt < m; tt += 128) cp_word(ridx + tt, src + tt, 4);
-        for (int a = tid; a < w; a += 128) cp_word(y + a, nm.vec + d.first + a, (int)sizeof(T));
-        for (int c = tid >> 5; c < w; c += 4)
+        for (int tt = me; tt < m; tt += nthr) cp_word(ridx + tt, src + tt, 4);
+        for (int a = me; a < w; a += nthr) cp_word(y + a, nm.vec + d.first + a, (int)sizeof(T));
+        for (int c = wi; c < w; c += nw)
             for (int a = lane; a < w; a += 32) cp_word(Us + a + c * w, pan + a + (int64_t)c * F, (int)sizeof(T));
         if (ts.bwd_stage) {
             const T* U12 = pan + (int64_t)F * w;
-            for (int e = tid; e < w * m; e += 128) cp_word(U12s + e, U12 + e, (int)sizeof(T));
+            for (int e = me; e < w * m; e += nthr) cp_word(U12s + e, U12 + e, (int)sizeof(T));
         }
+    };
+    // descriptor of chain position k into slot k % 3, by cp.async
+    auto fetch_desc = [&](int slot, int q_) {
+        constexpr int kWords = (int)(sizeof(TreeFront) / 4);
+        static_assert(sizeof(TreeFront) % 4 == 0, "descriptor words");
+        if (tid < kWords)
+            cp_word(reinterpret_cast<int*>(&dd[slot]) + tid, reinterpret_cast<const int*>(ts.fr + q_) + tid, 4);
     };
     for (;;) {
         const int t = next_ticket(ctr + 3, ctr + 1, total, &s_t);
@@ -835,19 +845,20 @@ __global__ void __launch_bounds__(128) tree_bwd_kernel(DevSched s, TreeSched ts,
         const int ci = t / B, b = t - ci * B;
         const int k0 = ts.bwd_chain_ptr[ci], k1 = ts.bwd_chain_ptr[ci + 1];
         const DevNum<T> nm = nm0.at(b);
-        copy_words(&dd[0], ts.fr + ts.bwd_chain[k0], 1, tid, 128);
+        fetch_desc(0, ts.bwd_chain[k0]);
+        if (k0 + 1 < k1) fetch_desc(1, ts.bwd_chain[k0 + 1]);
+        cp_wait_all();
         __syncthreads();
-        stage(0, dd[0], true, nm);
+        stage(0, dd[0], true, nm, 0, 128);
         bool stop = false;
         int q = -1;
         for (int k = k0; k < k1; ++k) {
-            const int sb = (k - k0) & 1;
+            const int sb = (k - k0) & 1, ds = (k - k0) % 3;
             q = ts.bwd_chain[k];
-            if (k + 1 < k1) copy_words(&dd[sb ^ 1], ts.fr + ts.bwd_chain[k + 1], 1, tid, 128);
-            cp_wait_all();                                       // this front's staging
+            cp_wait_all();                                       // this front's staging and the next descriptor
             if (k == k0 && tid < 32) {
                 TreeKid par{};
-                par.q = dd[sb].parent;
+                par.q = dd[ds].parent;
                 const int ok = warp_wait_kids(done + (int64_t)b * ts.nq, &par, 1, true, ctr + 1, limit);
                 if (tid == 0) s_ok = ok;
             }
@@ -857,15 +868,15 @@ __global__ void __launch_bounds__(128) tree_bwd_kernel(DevSched s, TreeSched ts,
                 stop = true;
                 break;
             }
-            const int w = dd[sb].w, F = dd[sb].F, first = dd[sb].first, m = F - w;
-            const T* U12 = nm.panel + dd[sb].panel_off + (int64_t)F * w;
+            const int w = dd[ds].w, F = dd[ds].F, first = dd[ds].first, m = F - w;
+            const T* U12 = nm.panel + dd[ds].panel_off + (int64_t)F * w;
             const T* y = stg + sb * stage_len;
             const T* Us = y + ts.max_w;
             const T* U12s = Us + ts.max_w * ts.max_w;
             const int* ridx = rix + sb * ts.max_F;
             T* v = vb + sb * ts.max_F;
             const T* pv = vb + (sb ^ 1) * ts.max_F;              // the previous front of the chain
-            if (k + 1 < k1) stage(sb ^ 1, dd[sb ^ 1], false, nm);   // in flight while this front is solved
+            if (k + 2 < k1) fetch_desc((ds + 2) % 3, ts.bwd_chain[k + 2]);
             for (int a = tid; a < w; a += 128) rcp[a] = pivot_rcp(Us[a + a * w]);
             if (k == k0)
                 for (int tt = tid; tt < m; tt += 128) v[w + tt] = __ldcg(nm.vec + ridx[tt]);
@@ -887,11 +898,21 @@ __global__ void __launch_bounds__(128) tree_bwd_kernel(DevSched s, TreeSched ts,
                 const int G = 128 / w;
                 T part = T(0);
                 if (tid < G * w) {
+                    // in sequence, four terms' loads issued ahead of their FMAs
                     const int a = tid % w, g = tid / w;
-                    if (ts.bwd_stage)
-                        for (int tt = g; tt < m; tt += G) part += U12s[a + tt * w] * v[w + tt];
-                    else
-                        for (int tt = g; tt < m; tt += G) part += U12[a + (int64_t)tt * w] * v[w + tt];
+                    const T* Ua = ts.bwd_stage ? U12s + a : U12 + a;
+                    int tt = g;
+                    for (; tt + 3 * G < m; tt += 4 * G) {
+                        T u[4], x[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            u[r] = Ua[(int64_t)(tt + r * G) * w];
+                            x[r] = v[w + tt + r * G];
+                        }
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) part += u[r] * x[r];
+                    }
+                    for (; tt < m; tt += G) part += Ua[(int64_t)tt * w] * v[w + tt];
                 }
                 red[tid] = part;
                 __syncthreads();
@@ -902,6 +923,8 @@ __global__ void __launch_bounds__(128) tree_bwd_kernel(DevSched s, TreeSched ts,
                 }
             }
             __syncthreads();
+            // warps 1-3 stage the next front while warp 0 solves this one
+            if (k + 1 < k1 && tid >= 32) stage(sb ^ 1, dd[(ds + 1) % 3], false, nm, 32, 96);
             if (tid < 32) {
                 if (w <= 32)
                     warp_upper_solve(v, Us, rcp, w);
