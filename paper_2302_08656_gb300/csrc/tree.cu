@@ -83,13 +83,14 @@ __device__ int warp_wait_kids(const int* done_b, const TreeKid* kids, int nk, bo
     }
 }
 
-// Signal completion of a unit: every thread's stores are made visible at GPU
-// scope before one thread bumps the counter.
+// Signal completion of a unit: after a CTA barrier (every thread's stores
+// happen before it), one thread adds 1 to the counter with a release
+// reduction at GPU scope, which makes them visible to a CTA that acquires the
+// counter.
 __device__ __forceinline__ void signal_done(int* counter)
 {
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(counter, 1);
+    if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(counter) : "memory");
 }
 
 // Take the next ticket (or `total` once the kernel was aborted).
@@ -125,9 +126,10 @@ __device__ bool fwd_unit(const DevSched& s, const TreeSched& ts, const DevNum<T>
 // so nothing diverges) and its events are counted once, in bad / pert. FAST:
 // the reciprocal's Newton step without its range test; returns false if a
 // pivot fell outside that range (the caller then repeats the panel with the
-// full pivot_rcp, from the same entries of M). Every entry gets the
-// operations of the one-pivot schedule in pivot order.
-template <bool FAST>
+// full pivot_rcp, from the same entries of M). FULL: all 8 columns active
+// (pk = 8). Every entry gets the operations of the one-pivot schedule in pivot
+// order.
+template <bool FAST, bool FULL>
 __device__ __forceinline__ bool panel_f32(const float* M, int Fr, int p0, int pk, int row, float floorT, float (&a)[8],
                                           int& bad, int& pert)
 {
@@ -136,10 +138,10 @@ __device__ __forceinline__ bool panel_f32(const float* M, int Fr, int p0, int pk
     bad = 0;
     pert = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] = (k < pk && row < Fr) ? M[row + (p0 + k) * Fr] : 0.0f;
+    for (int k = 0; k < 8; ++k) a[k] = ((FULL || k < pk) && row < Fr) ? M[row + (p0 + k) * Fr] : 0.0f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const bool act = k < pk;                                   // warp-uniform
+        const bool act = FULL || k < pk;                           // warp-uniform
         float u[8];
 #pragma unroll
         for (int kk = k + 1; kk < 8; ++kk) u[kk] = __shfl_sync(0xffffffffu, a[kk], k);   // pivot row p0 + k
@@ -164,6 +166,57 @@ __device__ __forceinline__ bool panel_f32(const float* M, int Fr, int p0, int pk
             if (below) a[kk] -= a[k] * u[kk];
     }
     return ok;
+}
+
+// One kPanel = 8 step of the single-precision elimination of a mini front M
+// (Fr x Fc <= 32 x 32, ld Fr) by 256 threads (32 x 8: lane -> row, warp ->
+// column group): warp 0 factors the panel (pivot columns p0 .. p0 + pk - 1,
+// lane -> row p0 + lane) in registers without a CTA barrier; then every warp
+// applies it to its trailing columns j = p0 + pk + warp + 8 c (lane -> row,
+// one shuffle per pivot for the row's U entry, its three columns
+// interleaved). Each entry still receives its updates in pivot order with
+// the same roundings as the one-pivot schedule. FULL: pk = 8.
+template <bool FULL>
+__device__ __forceinline__ void elim_step_f32(float* M, int Fr, int Fc, int p0, int pk, float floorT, int& n_bad,
+                                              int& n_pert)
+{
+    constexpr int kPanel = 8;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int row = p0 + tx;
+    if (ty == 0) {
+        float a[kPanel];
+        int pb = 0, pp = 0;
+        if (!panel_f32<true, FULL>(M, Fr, p0, pk, row, floorT, a, pb, pp))
+            panel_f32<false, FULL>(M, Fr, p0, pk, row, floorT, a, pb, pp);   // a reciprocal out of range
+        n_bad |= pb;
+        n_pert += pp;
+        if (row < Fr)
+#pragma unroll
+            for (int k = 0; k < kPanel; ++k)
+                if (FULL || k < pk) M[row + (p0 + k) * Fr] = a[k];
+    }
+    __syncthreads();
+    float lp[kPanel];
+#pragma unroll
+    for (int k = 0; k < kPanel; ++k) lp[k] = ((FULL || k < pk) && row < Fr) ? M[row + (p0 + k) * Fr] : 0.0f;
+    for (int jb = p0 + pk + ty; jb < Fc; jb += 24) {
+        float v[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = (row < Fr && jb + 8 * c < Fc) ? M[row + (jb + 8 * c) * Fr] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < kPanel; ++k) {
+            const bool upd = (FULL || k < pk) && tx > k;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float u = __shfl_sync(0xffffffffu, v[c], k);   // row p0 + k: final at step k
+                if (upd) v[c] -= lp[k] * u;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            if (row < Fr && jb + 8 * c < Fc) M[row + (jb + 8 * c) * Fr] = v[c];
+    }
+    __syncthreads();
 }
 
 // ------------------------------------------------------------- refactor
@@ -348,55 +401,17 @@ __device__ __forceinline__ void tree_factor_body(DevSched s_p, TreeSched ts_p, D
         // ---- w pivot steps of right-looking elimination without pivoting, one
         // reciprocal per pivot (l_ip = m_ip * (1 / u_pp))
         if (sizeof(T) == 4 && Fr <= 32 && Fc <= 32) {
-            // single precision, blocked by kPanel pivots: warp 0 factors the
-            // panel (pivot columns p0 .. p0 + pk - 1, lane -> row p0 + lane) in
-            // registers without a CTA barrier; then every warp applies it to its
-            // trailing columns (lane -> row, one shuffle per pivot for the row's
-            // U entry, three columns of a warp interleaved). Each entry still
-            // receives its updates in pivot order with the same roundings as the
-            // one-pivot schedule. Two barriers per kPanel pivots.
-            constexpr int kPanel = 8;
-            int n_bad = 0, n_pert = 0;                             // static-pivot events, counted once
-            for (int p0 = 0; p0 < w; p0 += kPanel) {
-                const int pk = min(kPanel, w - p0);
-                const int row = p0 + tx;
-                if (ty == 0) {
-                    float a[kPanel];
-                    int pb = 0, pp = 0;
-                    const float* Mf = reinterpret_cast<const float*>(M);
-                    const float fl = (float)floorT;
-                    if (!panel_f32<true>(Mf, Fr, p0, pk, row, fl, a, pb, pp))
-                        panel_f32<false>(Mf, Fr, p0, pk, row, fl, a, pb, pp);   // a reciprocal out of range
-                    n_bad |= pb;
-                    n_pert += pp;
-                    if (row < Fr)
-#pragma unroll
-                        for (int k = 0; k < kPanel; ++k)
-                            if (k < pk) M[row + (p0 + k) * Fr] = (T)a[k];
-                }
-                __syncthreads();
-                // trailing columns j >= p0 + pk: warp ty takes j = p0 + pk + ty + 8 c
-                T lp[kPanel];
-#pragma unroll
-                for (int k = 0; k < kPanel; ++k) lp[k] = (k < pk && row < Fr) ? M[row + (p0 + k) * Fr] : T(0);
-                for (int jb = p0 + pk + ty; jb < Fc; jb += 24) {
-                    T v[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) v[c] = (row < Fr && jb + 8 * c < Fc) ? M[row + (jb + 8 * c) * Fr] : T(0);
-#pragma unroll
-                    for (int k = 0; k < kPanel; ++k) {
-                        const bool upd = k < pk && tx > k;
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const T u = __shfl_sync(0xffffffffu, v[c], k);   // row p0 + k: final at step k
-                            if (upd) v[c] -= lp[k] * u;
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        if (row < Fr && jb + 8 * c < Fc) M[row + (jb + 8 * c) * Fr] = v[c];
-                }
-                __syncthreads();
+            // single precision, blocked by 8 pivots (elim_step_f32), the
+            // static-pivot events counted once
+            int n_bad = 0, n_pert = 0;
+            float* Mf = reinterpret_cast<float*>(M);
+            const float fl = (float)floorT;
+            for (int p0 = 0; p0 < w; p0 += 8) {
+                const int pk = min(8, w - p0);
+                if (pk == 8)
+                    elim_step_f32<true>(Mf, Fr, Fc, p0, pk, fl, n_bad, n_pert);
+                else
+                    elim_step_f32<false>(Mf, Fr, Fc, p0, pk, fl, n_bad, n_pert);
             }
             if (ty == 0 && lead && (n_bad | n_pert)) {                 // warp-uniform
                 if (tx == 0 && n_bad) atomicExch(&nm.stat->numeric_bad, 1);
