@@ -230,6 +230,13 @@ struct TreeFront {
     int64_t panel_off, cb_off, rel_ptr, rows_ptr;
     int64_t inv_off;             // gather maps: child c (local) at inv_off + c * (F - w)
 };
+// A work unit of the tree kernels with its front's descriptor, read by a CTA
+// in one step.
+struct TreeUnit {
+    TreeFront d;
+    FrontTile u;
+    int pad;
+};
 struct TreeKid {
     int q;                       // tree index of the child, -1 if the child lies below the tree part
     int mc, k;                   // child contribution-block order; its rows landing on parent pivots
@@ -241,8 +248,8 @@ struct TreeSched {
     int nunits = 0;              // factorization units
     const TreeFront* fr = nullptr;
     const TreeKid* kid = nullptr;
-    const FrontTile* unit = nullptr;   // factorization units in dependency order (front = tree index)
-    const FrontTile* unit_fused = nullptr;  // the same with a forward-solve unit (ti = -1) per front after its level
+    const TreeUnit* unit = nullptr;    // factorization units in dependency order (front = tree index)
+    const TreeUnit* unit_fused = nullptr;   // the same with a forward-solve unit (ti = -1) per front after its level
     int nunits_fused = 0;
     size_t kid_off = 0;                // shared-memory offset of the children's descriptors (factor kernel)
     const int* inv = nullptr;          // gather maps: parent CB row -> child CB row or -1

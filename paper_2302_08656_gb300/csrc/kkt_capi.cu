@@ -1152,8 +1152,8 @@ static int64_t plan_bytes(const Analysis& an, int n, int64_t nnz, const kkt_opti
     add(B * n * 8); add(B * (int64_t)resid_blocks(n) * 4 * 8); add(B * 8);
     const int64_t nq = (int64_t)tp.fr.size();
     add(nq * (int64_t)sizeof(TreeFront)); add((int64_t)tp.kid.size() * (int64_t)sizeof(TreeKid));
-    add((int64_t)tp.unit.size() * (int64_t)sizeof(FrontTile)); add((int64_t)tp.inv.size() * 4);
-    add((int64_t)tp.unit_fused.size() * (int64_t)sizeof(FrontTile));
+    add((int64_t)tp.unit.size() * (int64_t)sizeof(TreeUnit)); add((int64_t)tp.inv.size() * 4);
+    add((int64_t)tp.unit_fused.size() * (int64_t)sizeof(TreeUnit));
     add((int64_t)tp.bwd_chain.size() * 4); add((int64_t)tp.bwd_chain_ptr.size() * 4);
     add((kCtrHead + 2 * B * nq) * 4); add((kCtrHead + 2 * B * nq) * 4); add(2 * 4);
     add((n + 1) * 4); add(std::max<int64_t>((int64_t)an.rel.size(), 1) * 4);
@@ -1361,8 +1361,8 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     const int64_t nq = (int64_t)tp.fr.size();
     TreeFront* tfr = P.take<TreeFront>(nq);
     TreeKid* tkid = P.take<TreeKid>(tp.kid.size());
-    FrontTile* tunit = P.take<FrontTile>(tp.unit.size());
-    FrontTile* tunit_fused = P.take<FrontTile>(tp.unit_fused.size());
+    TreeUnit* tunit = P.take<TreeUnit>(tp.unit.size());
+    TreeUnit* tunit_fused = P.take<TreeUnit>(tp.unit_fused.size());
     int* tinv = P.take<int>(tp.inv.size());
     int* tchain = P.take<int>(tp.bwd_chain.size());
     int* tchain_ptr = P.take<int>(tp.bwd_chain_ptr.size());
@@ -1427,8 +1427,13 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     e = e ? e : up(f12_off_d, f12_off.data(), an.ns * 8);
     e = e ? e : up(tfr, tp.fr.data(), nq * sizeof(TreeFront));
     e = e ? e : up(tkid, tp.kid.data(), tp.kid.size() * sizeof(TreeKid));
-    e = e ? e : up(tunit, tp.unit.data(), tp.unit.size() * sizeof(FrontTile));
-    e = e ? e : up(tunit_fused, tp.unit_fused.data(), tp.unit_fused.size() * sizeof(FrontTile));
+    // units with their fronts' descriptors
+    std::vector<TreeUnit> h_unit(tp.unit.size()), h_unit_fused(tp.unit_fused.size());
+    for (size_t i = 0; i < tp.unit.size(); ++i) h_unit[i] = TreeUnit{tp.fr[tp.unit[i].front], tp.unit[i], 0};
+    for (size_t i = 0; i < tp.unit_fused.size(); ++i)
+        h_unit_fused[i] = TreeUnit{tp.fr[tp.unit_fused[i].front], tp.unit_fused[i], 0};
+    e = e ? e : up(tunit, h_unit.data(), h_unit.size() * sizeof(TreeUnit));
+    e = e ? e : up(tunit_fused, h_unit_fused.data(), h_unit_fused.size() * sizeof(TreeUnit));
     e = e ? e : up(tinv, tp.inv.data(), tp.inv.size() * 4);
     e = e ? e : up(tchain, tp.bwd_chain.data(), tp.bwd_chain.size() * 4);
     e = e ? e : up(tchain_ptr, tp.bwd_chain_ptr.data(), tp.bwd_chain_ptr.size() * 4);

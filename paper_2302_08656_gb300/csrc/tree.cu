@@ -93,10 +93,16 @@ __device__ __forceinline__ void signal_done(int* counter)
     if (threadIdx.x == 0) asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(counter) : "memory");
 }
 
-// Take the next ticket (or `total` once the kernel was aborted).
+// Take the next ticket (or `total` once the kernel was aborted): the abort
+// flag and the ticket counter are read together, in one round trip.
 __device__ __forceinline__ int next_ticket(int* ticket, const int* abort_flag, int total, int* s_t)
 {
-    if (threadIdx.x == 0) *s_t = ld_acquire(abort_flag) ? total : atomicAdd(ticket, 1);
+    if (threadIdx.x == 0) {
+        int stop;
+        asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(stop) : "l"(abort_flag) : "memory");
+        const int t = atomicAdd(ticket, 1);
+        *s_t = stop ? total : t;
+    }
     __syncthreads();
     return *s_t;
 }
@@ -242,7 +248,8 @@ __device__ __forceinline__ void tree_factor_body(DevSched s_p, TreeSched ts_p, D
                                                  const TreeJob<T>* jobs, const TreeSeg* segs, int nseg)
 {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ TreeFront d;
+    __shared__ TreeUnit su;                                    // the current unit and its front
+    TreeFront& d = su.d;
     __shared__ int s_t, s_ok;
     __shared__ T s_rinv[64];                                   // reciprocal of every pivot (w <= 64)
     __shared__ __align__(16) unsigned char sj_raw[MULTI ? sizeof(TreeJob<T>) : 16];
@@ -287,16 +294,16 @@ __device__ __forceinline__ void tree_factor_body(DevSched s_p, TreeSched ts_p, D
         const int B = MULTI ? sj->B : B_p;
         int* done = (MULTI ? sj->ctr : ctr) + kCtrHead;
         int* fwd_done = done + (int64_t)B * ts.nq;                 // fused mode: forward-unit counters
-        const FrontTile* units = fused ? ts.unit_fused : ts.unit;
+        const TreeUnit* units = fused ? ts.unit_fused : ts.unit;
         T* M = reinterpret_cast<T*>(smraw);
         const int W = ts.map_w;
         const size_t off_map = align16(sizeof(T) * (size_t)ts.m_elems);
         int* smap = reinterpret_cast<int*>(smraw + off_map);       // child c: rows at 2cW, columns at (2c+1)W
         TreeKid* kids = reinterpret_cast<TreeKid*>(smraw + ts.kid_off);
-        const FrontTile ut = units[(MULTI ? 0 : u0) + ul];
-        const int q = ut.front;
-        copy_words(&d, ts.fr + q, 1, tid, 256);
+        copy_words(&su, units + (MULTI ? 0 : u0) + ul, 1, tid, 256);
         __syncthreads();
+        const FrontTile ut = su.u;
+        const int q = ut.front;
         const DevNum<T> nm = nm0.at(b);
         if (ut.ti < 0) {                                           // forward-solve unit (fused mode)
             if (!fwd_unit<T, 256>(s, ts, nm, d, q, kids, s_cut, &s_ok, smraw, fwd_done + (int64_t)b * ts.nq,
@@ -530,7 +537,6 @@ __device__ __forceinline__ void tree_factor_body(DevSched s_p, TreeSched ts_p, D
         for (int c = ty; c < nc; c += 8)
             for (int r = tx; r < nr; r += 32) C[(i0 + r) + (int64_t)(j0 + c) * m] = M[(w + r) + (w + c) * Fr];
         signal_done(done + (int64_t)b * ts.nq + q);
-        __syncthreads();
     }
 }
 
