@@ -128,6 +128,11 @@ struct kkt_ctx {
     double* omega_dev = nullptr;
     double* omega_pin = nullptr;
     cudaStream_t work_stream = nullptr;   // own stream for concurrent multi-context batches
+    // kkt_step_host: the host buffer for x, copied right after the residual
+    // (before the host reads the backward error); x_early_valid: no
+    // refinement changed x after that copy
+    double* x_early = nullptr;
+    int x_early_valid = 0;
     cudaEvent_t done_event = nullptr;
     std::vector<kkt_info> infos;     // per instance
     // launch accounting and optional per-kernel timing
@@ -984,8 +989,11 @@ kkt_status refine_tail(kkt_ctx* c, const double* b, double* x, double tol, kkt_i
         KKT_CUDA(launch_resid_omega(c->sched, c->kvals, c->slots, x, b,
                                     c->r_batch, c->omega_part, c->stat, c->omega_dev, c->batch, st));
     }
+    if (c->x_early)
+        KKT_CUDA(cudaMemcpyAsync(c->x_early, x, sizeof(double) * c->n * c->batch, cudaMemcpyDeviceToHost, st));
     KKT_CUDA(cudaMemcpyAsync(c->omega_pin, c->omega_dev, sizeof(double) * c->batch, cudaMemcpyDeviceToHost, st));
     if ((s = sync_stat(c, st)) != KKT_OK) return s;      // synchronizes st
+    c->x_early_valid = c->x_early != nullptr;
     if (c->info.status == KKT_E_TIMEOUT) {                // a bounded device wait gave up: no valid x
         for (int i = 0; i < c->batch; ++i) {
             c->infos[i].iters = 0;
@@ -1004,6 +1012,7 @@ kkt_status refine_tail(kkt_ctx* c, const double* b, double* x, double tol, kkt_i
         inf.rel_resid2 = -1.0;                            // computed only when refinement runs
         kkt_status si = KKT_OK;
         if (!(c->omega_pin[i] <= tol)) {
+            c->x_early_valid = 0;                          // refinement changes x
             const int64_t off = (int64_t)i * c->n;
             si = fgmres_inst(c, i, b + off, x + off, tol, &inf, st);
             if (si != KKT_OK && si != KKT_E_NOCONV && si != KKT_E_NUMERIC) return si;
@@ -1612,10 +1621,17 @@ kkt_status kkt_step_host(kkt_ctx* c, const double* h_vals, const double* h_rhs, 
     cudaStream_t st = (cudaStream_t)stream;
     KKT_CUDA(cudaMemcpyAsync(c->stage_vals, h_vals, sizeof(double) * c->nnz * c->batch, cudaMemcpyHostToDevice, st));
     KKT_CUDA(cudaMemcpyAsync(c->stage_b, h_rhs, sizeof(double) * c->n * c->batch, cudaMemcpyHostToDevice, st));
+    // x goes to h_x together with the backward error; a second copy only if
+    // refinement changed it afterwards
+    c->x_early = h_x;
+    c->x_early_valid = 0;
     kkt_status r = do_refactor_refine(c, c->stage_vals, c->stage_b, c->stage_x, tol, info, st);
+    c->x_early = nullptr;
     if (r != KKT_OK && r != KKT_E_NOCONV) return r;
-    KKT_CUDA(cudaMemcpyAsync(h_x, c->stage_x, sizeof(double) * c->n * c->batch, cudaMemcpyDeviceToHost, st));
-    KKT_CUDA(cudaStreamSynchronize(st));
+    if (!c->x_early_valid) {
+        KKT_CUDA(cudaMemcpyAsync(h_x, c->stage_x, sizeof(double) * c->n * c->batch, cudaMemcpyDeviceToHost, st));
+        KKT_CUDA(cudaStreamSynchronize(st));
+    }
     return r;
 }
 
