@@ -127,6 +127,7 @@ struct kkt_ctx {
     double* r_batch = nullptr;       // residual vectors of all instances
     double* omega_dev = nullptr;
     double* omega_pin = nullptr;
+    DevStat* stat_pin = nullptr;     // pinned host copy of the statistics (sync_stat)
     cudaStream_t work_stream = nullptr;   // own stream for concurrent multi-context batches
     // kkt_step_host: the host buffer for x, copied right after the residual
     // (before the host reads the backward error); x_early_valid: no
@@ -785,8 +786,8 @@ kkt_status do_precond(kkt_ctx* c, const double* b, double* x, cudaStream_t st, i
 // read back the device statistics of the last refactor into c->info
 kkt_status sync_stat(kkt_ctx* c, cudaStream_t st)
 {
-    std::vector<DevStat> hs(c->batch);
-    KKT_CUDA(cudaMemcpyAsync(hs.data(), c->stat, sizeof(DevStat) * c->batch, cudaMemcpyDeviceToHost, st));
+    const DevStat* hs = c->stat_pin;                      // pinned: a plain asynchronous copy
+    KKT_CUDA(cudaMemcpyAsync(c->stat_pin, c->stat, sizeof(DevStat) * c->batch, cudaMemcpyDeviceToHost, st));
     KKT_CUDA(cudaStreamSynchronize(st));
     c->infos.resize(c->batch);
     for (int i = 0; i < c->batch; ++i) {
@@ -1387,6 +1388,12 @@ static kkt_status analyze_impl(int32_t n, int32_t n_primal, const int32_t* h_row
     int* sell_src = P.take<int>(slots);
     unsigned short* keys = P.take<unsigned short>(B * slots);
     if (P.used > P.size) { kkt_destroy(c); return KKT_E_NOMEM; }
+    if (cudaMallocHost(&c->stat_pin, sizeof(DevStat) * B) != cudaSuccess) {
+        cudaGetLastError();
+        c->stat_pin = nullptr;
+        kkt_destroy(c);
+        return KKT_E_NOMEM;
+    }
     if (cudaMallocHost(&c->pin, sizeof(double) * (4 * (kMaxRestart + 2) + 16 + B + kMaxRestart + 8)) != cudaSuccess) {
         cudaGetLastError();
         c->pin = nullptr;
@@ -1951,6 +1958,7 @@ kkt_status kkt_destroy(kkt_ctx* c)
     if (c->done_event) cudaEventDestroy(c->done_event);
     if (c->pool.base) cudaFree(c->pool.base);
     if (c->pin) cudaFreeHost(c->pin);
+    if (c->stat_pin) cudaFreeHost(c->stat_pin);
     delete c;
     return KKT_OK;
 }
