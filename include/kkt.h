@@ -515,6 +515,53 @@ kkt_status kkt_destroy(kkt_ctx *ctx);
 
 const char *kkt_status_string(kkt_status s);
 
+/* ---- Saddle-point specialised solve (Sec. V) ------------------------------
+ * Sec. V names a solver specialised to the saddle-point structure of these
+ * KKT systems as a way forward, without giving its method. This is the hybrid
+ * direct-iterative approach of the GPU ACOPF literature. With the unknowns
+ * ordered (x, y_E, y_I) -- n_primal primal, then m_eq equality duals, then
+ * the rest, inequality duals -- and K = [H J_E^T J_I^T; J_E -D_E 0; J_I 0 -D_I]
+ * with D_E, D_I diagonal (stored, every dual row's diagonal present):
+ *   H_g = H + J_I^T D_I^{-1} J_I + gamma J_E^T J_E   (factored by an inner
+ *          context of this library: multifrontal LU, FP64, static pivoting),
+ *   (C^{1/2} J_E H_g^{-1} J_E^T C^{1/2} + D_E) w = C^{1/2} (J_E H_g^{-1} r'' - r_E)
+ *          by conjugate gradients, C = I - gamma D_E, y_E = C^{-1/2} w,
+ *   x = H_g^{-1} (r'' - J_E^T C y_E), y_I = D_I^{-1} (J_I x - r_I),
+ * with r'' = r_x + J_I^T D_I^{-1} r_I + gamma J_E^T r_E. gamma trades the
+ * conjugate-gradient iterations against the conditioning of H_g; it must make
+ * the reduced operator positive definite (H_g need not be). */
+typedef struct kkt_hykkt kkt_hykkt;
+
+typedef struct {
+    int cg_iters;               /* conjugate-gradient iterations */
+    int status;                 /* KKT_OK, or KKT_E_NOCONV if cg_resid > tol at max_iter */
+    int n_perturbed;            /* static pivot perturbations of the factorization of H_g */
+    int reserved;
+    double cg_resid;            /* ||b' - A w|| / ||b'|| of the reduced system at exit */
+    double backward_err;        /* ||K z - b||_inf / (||K||_inf ||z||_inf + ||b||_inf) */
+} kkt_hykkt_info;
+
+/* Analysis from the host CSR pattern of K (n x n, structurally symmetric,
+ * 0-based, sorted or not): the blocks, the pattern of H_g with, per entry, its
+ * contributions in a fixed order, and the inner context's analysis of H_g.
+ * gamma >= 0 (finite). Synchronous.
+ * Errors: KKT_E_ARG, KKT_E_STRUCT (the (2,2) block is not diagonal or a dual
+ * diagonal is missing), KKT_E_NOMEM, KKT_E_CUDA. */
+kkt_status kkt_hykkt_analyze(int32_t n, int32_t n_primal, int32_t m_eq, const int32_t *h_rowptr,
+                             const int32_t *h_colidx, double gamma, kkt_hykkt **out);
+
+/* z = K^{-1} b by the method above for K's values d_vals (device, nnz FP64 in
+ * the CSR order given to the analysis); d_rhs, d_z device FP64 vectors of
+ * length n, not aliased. Stops when the reduced residual is <= tol times its
+ * initial value or after max_iter iterations. Synchronizes `stream` (the host
+ * reads the reduced residual every few iterations); info may be NULL.
+ * Errors: KKT_E_ARG, KKT_E_NUMERIC (some d_I <= 0, gamma d_E >= 1, or NaN),
+ * KKT_E_NOCONV (z written, info filled), KKT_E_CUDA. */
+kkt_status kkt_hykkt_solve(kkt_hykkt *h, const double *d_vals, const double *d_rhs, double *d_z, double tol,
+                           int32_t max_iter, kkt_hykkt_info *info, void *stream);
+
+void kkt_hykkt_destroy(kkt_hykkt *h);
+
 #ifdef __cplusplus
 }
 #endif

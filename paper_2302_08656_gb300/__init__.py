@@ -555,6 +555,57 @@ class KKTGroup:
             pass
 
 
+class SaddlePointSolver:
+    """Saddle-point specialised solve of K (kkt_hykkt_*; Sec. V): inequality
+    rows condensed, equality rows augmented by gamma J_E^T J_E, conjugate
+    gradients on the reduced symmetric operator, one factorization of H_g by
+    the library per call. Unknowns ordered (primal, m_eq equality duals,
+    inequality duals); the (2,2) block diagonal."""
+
+    def __init__(self, rowptr, colidx, n_primal, m_eq, gamma=1e4):
+        rp, ci = _pattern(rowptr, colidx)
+        self.n = len(rp) - 1
+        self.nnz = int(rp[-1])
+        if not (0 < int(n_primal) and 0 < int(m_eq) and int(n_primal) + int(m_eq) <= self.n):
+            raise ValueError("need 0 < n_primal, 0 < m_eq, n_primal + m_eq <= n")
+        if not (gamma >= 0 and np.isfinite(gamma)):
+            raise ValueError("gamma must be finite and >= 0")
+        h = C.c_void_p()
+        _check(lib().kkt_hykkt_analyze(self.n, int(n_primal), int(m_eq), rp.ctypes.data, ci.ctypes.data,
+                                       float(gamma), C.byref(h)), "kkt_hykkt_analyze")
+        self._h = h
+        self.n_primal, self.m_eq, self.gamma = int(n_primal), int(m_eq), float(gamma)
+
+    def solve(self, vals, rhs, tol=1e-12, max_iter=500, out=None, stream=None, raise_on_noconv=True):
+        import torch
+        _check_tensor(vals, self.nnz, "vals")
+        _check_tensor(rhs, self.n, "rhs")
+        if out is None:
+            out = torch.empty_like(rhs)
+        _check_tensor(out, self.n, "out")
+        if not (vals.device == rhs.device == out.device):
+            raise ValueError("vals, rhs and out must be on one device")
+        from ._native import HykktInfo
+        info = HykktInfo()
+        with torch.cuda.device(rhs.device):
+            st = lib().kkt_hykkt_solve(self._h, _ptr(vals), _ptr(rhs), _ptr(out), float(tol), int(max_iter),
+                                       C.byref(info), _stream(stream))
+        if st != 6 or raise_on_noconv:
+            _check(st, "kkt_hykkt_solve")
+        return out, info
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().kkt_hykkt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def solve_batched(solvers, rhs, outs, stream=None):
     if not len(rhs) == len(outs) == len(solvers):
         raise ValueError("one rhs and one out tensor per solver")

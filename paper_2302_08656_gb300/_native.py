@@ -17,7 +17,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libkkt_gb300.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["analysis.cpp", "tree_plan.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu", "tree.cu", "model.cu", "jacobi.cu",
-           "ipm.cu"]
+           "ipm.cu", "hykkt.cu"]
 HEADERS = ["analysis.hpp", "kernels.cuh", "tree_plan.hpp", "model.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -79,6 +79,11 @@ class IpmInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("objective", C.c_double), ("err", C.c_double),
                 ("mu", C.c_double), ("lin_iters", C.c_int), ("lin_omega_max", C.c_double),
                 ("lin_noconv", C.c_int)]
+
+
+class HykktInfo(C.Structure):
+    _fields_ = [("cg_iters", C.c_int), ("status", C.c_int), ("n_perturbed", C.c_int), ("reserved", C.c_int),
+                ("cg_resid", C.c_double), ("backward_err", C.c_double)]
 
 
 class Options(C.Structure):
@@ -183,6 +188,9 @@ SIGNATURES = {
     "kkt_backward_error_noalloc": (C.c_int, [C.c_int32, C.c_int64, _P, _P, _P, _P, _P, _P, _P, _P]),
     "kkt_destroy": (C.c_int, [_P]),
     "kkt_status_string": (C.c_char_p, [C.c_int]),
+    "kkt_hykkt_analyze": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_double, C.POINTER(_P)]),
+    "kkt_hykkt_solve": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, C.POINTER(HykktInfo), _P]),
+    "kkt_hykkt_destroy": (None, [_P]),
 }
 
 _lib = None

@@ -1,0 +1,534 @@
+// Saddle-point specialised solve of a KKT system (Sec. V names such a solver
+// as a way forward without giving its method; this is the hybrid
+// direct-iterative approach to ACOPF KKT systems, see kkt.h):
+//
+//   K = [ H    J_E^T  J_I^T ]   unknowns (x, y_E, y_I): primal, equality duals,
+//       [ J_E -D_E    0     ]   inequality duals; D_E, D_I diagonal
+//       [ J_I  0     -D_I   ]
+//
+// condense the inequality rows (H' = H + J_I^T D_I^{-1} J_I), augment with
+// gamma J_E^T J_E (H_g = H' + gamma J_E^T J_E, factored by the library's own
+// multifrontal LU in an inner context), solve the equality duals by conjugate
+// gradients on the symmetric operator C^{1/2} J_E H_g^{-1} J_E^T C^{1/2} + D_E
+// (C = I - gamma D_E; one solve with H_g per iteration), then recover x and
+// y_I. Every step runs in kernels on the caller's stream; the host reads the
+// conjugate-gradient residual every kCheck iterations to stop.
+#include "../../include/kkt.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kBlocks = 304;          // 2 x 152 SMs, grid-stride loops; also the partial sums of a dot product
+constexpr int kCheck = 4;             // conjugate-gradient iterations between two reads of the residual
+
+// one step of an H_g entry: kind -1: K value a; -2: gamma K_a K_b (a J_E pair);
+// k >= 0: K_a K_b / d_I[k] (a J_I pair of inequality row k)
+struct Contrib {
+    int a, b, k;
+};
+
+__global__ void hg_assemble_kernel(int64_t nnz_g, const int64_t* __restrict__ cptr, const Contrib* __restrict__ cl,
+                                   const double* __restrict__ vals, const double* __restrict__ dinv, double gamma,
+                                   double* __restrict__ hg)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz_g; e += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int64_t c = cptr[e]; c < cptr[e + 1]; ++c) {
+            const Contrib t = cl[c];
+            if (t.k == -1) acc += vals[t.a];
+            else if (t.k == -2) acc += gamma * (vals[t.a] * vals[t.b]);
+            else acc += (vals[t.a] * vals[t.b]) * dinv[t.k];
+        }
+        hg[e] = acc;
+    }
+}
+
+// the (2,2) block: d_E, C = 1 - gamma d_E and its square root, 1 / d_I; flag
+// (bit 0: some d_I <= 0 or not finite, bit 1: some C <= 0)
+__global__ void duals_kernel(int mE, int mI, const int* __restrict__ dpos, const double* __restrict__ vals,
+                             double gamma, double* __restrict__ dE, double* __restrict__ C, double* __restrict__ sq,
+                             double* __restrict__ dinv, int* __restrict__ flag)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < mE + mI; k += gridDim.x * blockDim.x) {
+        const double d = -vals[dpos[k]];
+        if (k < mE) {
+            const double c = 1.0 - gamma * d;
+            dE[k] = d;
+            C[k] = c;
+            sq[k] = sqrt(c);
+            if (!(c > 0.0)) atomicOr(flag, 2);
+        } else {
+            dinv[k - mE] = 1.0 / d;
+            if (!(d > 0.0) || !isfinite(d)) atomicOr(flag, 1);
+        }
+    }
+}
+
+// y = J x over the rows of a block (CSR of positions into K's values)
+__global__ void j_mul_kernel(int m, const int* __restrict__ ptr, const int* __restrict__ col,
+                             const int* __restrict__ pos, const double* __restrict__ vals, const double* __restrict__ x,
+                             double* __restrict__ y)
+{
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int p = ptr[r]; p < ptr[r + 1]; ++p) acc += vals[pos[p]] * x[col[p]];
+        y[r] = acc;
+    }
+}
+
+// out = base + J_I^T xi + ge J_E^T xe over the primal rows (transposes as CSR
+// of positions); base, xi, xe may be null
+__global__ void jt_mul_kernel(int np, const int* __restrict__ ip, const int* __restrict__ ic, const int* __restrict__ ipos,
+                              const int* __restrict__ ep, const int* __restrict__ ec, const int* __restrict__ epos,
+                              const double* __restrict__ vals, const double* __restrict__ base,
+                              const double* __restrict__ xi, const double* __restrict__ xe, double ge,
+                              double* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        double a = 0.0, e = 0.0;
+        if (xi)
+            for (int p = ip[i]; p < ip[i + 1]; ++p) a += vals[ipos[p]] * xi[ic[p]];
+        if (xe)
+            for (int p = ep[i]; p < ep[i + 1]; ++p) e += vals[epos[p]] * xe[ec[p]];
+        out[i] = (base ? base[i] : 0.0) + a + ge * e;
+    }
+}
+
+// small vector steps of the method, by `op`
+__global__ void vec_kernel(int op, int n, const double* __restrict__ a, const double* __restrict__ b,
+                           const double* __restrict__ c, double* __restrict__ out)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        switch (op) {
+        case 0: out[i] = a[i] * b[i]; break;                      // a .* b
+        case 1: out[i] = a[i] * (b[i] - c[i]); break;             // a .* (b - c)
+        case 3: out[i] = a[i] / b[i]; break;                      // y_E = w ./ sq
+        case 4: out[i] = -(a[i] * b[i]); break;                   // -(C .* y_E)
+        default: out[i] = (a[i] - b[i]) * c[i]; break;            // y_I = (J_I x - r_I) .* (1 / d_I)
+        }
+    }
+}
+
+// partial dot products (fixed order: block b sums i = b*T + t, + grid stride)
+__global__ void dot_part_kernel(int n, const double* __restrict__ a, const double* __restrict__ b,
+                                double* __restrict__ part)
+{
+    __shared__ double s[kThreads];
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += a[i] * b[i];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void dot_final_kernel(const double* __restrict__ part, double* __restrict__ out)
+{
+    if (threadIdx.x == 0) {
+        double acc = 0.0;
+        for (int b = 0; b < kBlocks; ++b) acc += part[b];
+        *out = acc;
+    }
+}
+
+// conjugate-gradient steps with the scalars on the device: s[0] = r.r,
+// s[1] = p.q, s[2] = the new r.r. update: w += alpha p, r -= alpha q with
+// alpha = s0 / s1; direction: p = r + (s2 / s0) p
+__global__ void cg_update_kernel(int n, const double* __restrict__ s, const double* __restrict__ p,
+                                 const double* __restrict__ q, double* __restrict__ w, double* __restrict__ r)
+{
+    const double alpha = s[0] / s[1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        w[i] += alpha * p[i];
+        r[i] -= alpha * q[i];
+    }
+}
+
+__global__ void cg_direction_kernel(int n, const double* __restrict__ s, const double* __restrict__ r,
+                                    double* __restrict__ p)
+{
+    const double beta = s[2] / s[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = r[i] + beta * p[i];
+}
+
+__global__ void shift_kernel(double* s)
+{
+    if (threadIdx.x == 0) s[0] = s[2];
+}
+
+__device__ __forceinline__ unsigned long long mag(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+// per block: max |b - K z|, |z|, |b|, sum_j |K_ij| over the rows (bit patterns:
+// NaN sorts above +Inf)
+__global__ void resid_part_kernel(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                  const double* __restrict__ vals, const double* __restrict__ z,
+                                  const double* __restrict__ b, unsigned long long* __restrict__ part)
+{
+    __shared__ unsigned long long s[4][kThreads];
+    unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double acc = 0.0, rs = 0.0;
+        for (int p = rp[i]; p < rp[i + 1]; ++p) {
+            acc += vals[p] * z[ci[p]];
+            rs += fabs(vals[p]);
+        }
+        const unsigned long long v[4] = {mag(b[i] - acc), mag(z[i]), mag(b[i]), mag(rs)};
+        for (int q = 0; q < 4; ++q) m[q] = v[q] > m[q] ? v[q] : m[q];
+    }
+    for (int q = 0; q < 4; ++q) s[q][threadIdx.x] = m[q];
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int q = 0; q < 4; ++q) s[q][threadIdx.x] = s[q][threadIdx.x + o] > s[q][threadIdx.x] ? s[q][threadIdx.x + o] : s[q][threadIdx.x];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[blockIdx.x * 4 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+template <typename X>
+X* dev_alloc(size_t count, cudaError_t& e)
+{
+    void* p = nullptr;
+    if (e == cudaSuccess && count) e = cudaMalloc(&p, count * sizeof(X));
+    return static_cast<X*>(p);
+}
+
+template <typename X>
+cudaError_t upload(X* dst, const std::vector<X>& src)
+{
+    return src.empty() ? cudaSuccess : cudaMemcpy(dst, src.data(), src.size() * sizeof(X), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+struct kkt_hykkt {
+    int n = 0, np = 0, mE = 0, mI = 0;
+    int64_t nnz = 0, nnz_g = 0;
+    double gamma = 0.0;
+    kkt_ctx* inner = nullptr;
+    // K and the blocks (positions into K's values)
+    int *rp = nullptr, *ci = nullptr, *dpos = nullptr;
+    int *je_p = nullptr, *je_c = nullptr, *je_v = nullptr, *ji_p = nullptr, *ji_c = nullptr, *ji_v = nullptr;
+    int *jet_p = nullptr, *jet_c = nullptr, *jet_v = nullptr, *jit_p = nullptr, *jit_c = nullptr, *jit_v = nullptr;
+    int64_t* cptr = nullptr;
+    Contrib* cl = nullptr;
+    double* hg = nullptr;
+    // vectors and scalars
+    double *dE = nullptr, *C = nullptr, *sq = nullptr, *dinv = nullptr;
+    double *r2 = nullptr, *t = nullptr, *u = nullptr, *v = nullptr;        // np
+    double *w = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *e = nullptr;   // mE
+    double *part = nullptr, *s = nullptr;
+    unsigned long long* rpart = nullptr;
+    int* flag = nullptr;
+    double* pin = nullptr;                                       // host: s[0..3], flag, residual partials
+};
+
+extern "C" {
+
+kkt_status kkt_hykkt_analyze(int32_t n, int32_t n_primal, int32_t m_eq, const int32_t* h_rowptr,
+                             const int32_t* h_colidx, double gamma, kkt_hykkt** out)
+{
+    if (!out || !h_rowptr || !h_colidx || n <= 0 || n_primal <= 0 || m_eq <= 0 || n_primal + m_eq > n ||
+        !(gamma >= 0.0) || !std::isfinite(gamma))
+        return KKT_E_ARG;
+    *out = nullptr;
+    const int np = n_primal, mE = m_eq, mI = n - n_primal - m_eq;
+    const int64_t nnz = h_rowptr[n];
+    // blocks: H (rows < np, cols < np), J_E / J_I (dual rows, cols < np),
+    // the (2,2) block must be exactly its diagonal
+    std::vector<int> dpos(mE + mI, -1);
+    std::vector<int> je_p(1, 0), je_c, je_v, ji_p(1, 0), ji_c, ji_v;
+    for (int i = np; i < n; ++i) {
+        const bool eq = i < np + mE;
+        for (int64_t k = h_rowptr[i]; k < h_rowptr[i + 1]; ++k) {
+            const int j = h_colidx[k];
+            if (j < 0 || j >= n) return KKT_E_STRUCT;
+            if (j < np) {
+                (eq ? je_c : ji_c).push_back(j);
+                (eq ? je_v : ji_v).push_back((int)k);
+            } else if (j == i) {
+                dpos[i - np] = (int)k;
+            } else {
+                return KKT_E_STRUCT;                              // (2,2) block not diagonal
+            }
+        }
+        (eq ? je_p : ji_p).push_back((int)(eq ? je_c.size() : ji_c.size()));
+    }
+    for (int k = 0; k < mE + mI; ++k)
+        if (dpos[k] < 0) return KKT_E_STRUCT;                     // the dual diagonal must be stored
+    // transposes (CSR over the primal rows)
+    auto transpose = [&](const std::vector<int>& p, const std::vector<int>& c, const std::vector<int>& v, int m,
+                         std::vector<int>& tp, std::vector<int>& tc, std::vector<int>& tv) {
+        tp.assign(np + 1, 0);
+        for (int j : c) ++tp[j + 1];
+        for (int i = 0; i < np; ++i) tp[i + 1] += tp[i];
+        tc.resize(c.size());
+        tv.resize(c.size());
+        std::vector<int> fill(tp.begin(), tp.end() - 1);
+        for (int r = 0; r < m; ++r)
+            for (int k = p[r]; k < p[r + 1]; ++k) {
+                tc[fill[c[k]]] = r;
+                tv[fill[c[k]]++] = v[k];
+            }
+    };
+    std::vector<int> jet_p, jet_c, jet_v, jit_p, jit_c, jit_v;
+    transpose(je_p, je_c, je_v, mE, jet_p, jet_c, jet_v);
+    transpose(ji_p, ji_c, ji_v, mI, jit_p, jit_c, jit_v);
+    // H_g = H + J_I^T D_I^{-1} J_I + gamma J_E^T J_E: pattern and, per entry,
+    // its contributions in a fixed order (the H entry, J_I pairs by inequality
+    // row, J_E pairs by equality row)
+    std::vector<int> hg_p(1, 0), hg_c;
+    std::vector<int64_t> cptr(1, 0);
+    std::vector<Contrib> cl;
+    std::vector<int> slot(np, -1);
+    std::vector<std::vector<Contrib>> acc;
+    std::vector<int> cols;
+    for (int i = 0; i < np; ++i) {
+        cols.clear();
+        acc.clear();
+        auto at = [&](int j) -> std::vector<Contrib>& {
+            if (slot[j] < 0) {
+                slot[j] = (int)cols.size();
+                cols.push_back(j);
+                acc.emplace_back();
+            }
+            return acc[slot[j]];
+        };
+        for (int64_t k = h_rowptr[i]; k < h_rowptr[i + 1]; ++k)
+            if (h_colidx[k] < np) at(h_colidx[k]).push_back(Contrib{(int)k, -1, -1});
+        at(i);                                                    // the diagonal always
+        for (int q = jit_p[i]; q < jit_p[i + 1]; ++q) {           // inequality rows holding column i
+            const int r = jit_c[q], a = jit_v[q];
+            for (int k = ji_p[r]; k < ji_p[r + 1]; ++k) at(ji_c[k]).push_back(Contrib{a, ji_v[k], r});
+        }
+        for (int q = jet_p[i]; q < jet_p[i + 1]; ++q) {           // equality rows holding column i
+            const int r = jet_c[q], a = jet_v[q];
+            for (int k = je_p[r]; k < je_p[r + 1]; ++k) at(je_c[k]).push_back(Contrib{a, je_v[k], -2});
+        }
+        std::vector<int> order(cols.size());
+        for (size_t k = 0; k < cols.size(); ++k) order[k] = (int)k;
+        std::sort(order.begin(), order.end(), [&](int x, int y) { return cols[x] < cols[y]; });
+        for (int k : order) {
+            hg_c.push_back(cols[k]);
+            cl.insert(cl.end(), acc[k].begin(), acc[k].end());
+            cptr.push_back((int64_t)cl.size());
+        }
+        hg_p.push_back((int)hg_c.size());
+        for (int j : cols) slot[j] = -1;
+    }
+    kkt_hykkt* h = new (std::nothrow) kkt_hykkt();
+    if (!h) return KKT_E_NOMEM;
+    h->n = n; h->np = np; h->mE = mE; h->mI = mI; h->nnz = nnz; h->nnz_g = (int64_t)hg_c.size(); h->gamma = gamma;
+    kkt_options opt;
+    kkt_default_options(&opt);
+    opt.precision = KKT_FP64;
+    kkt_status st = kkt_analyze(np, np, hg_p.data(), hg_c.data(), nullptr, &opt, &h->inner);
+    if (st != KKT_OK) {
+        delete h;
+        return st;
+    }
+    cudaError_t e = cudaSuccess;
+    h->rp = dev_alloc<int>(n + 1, e); h->ci = dev_alloc<int>(nnz, e); h->dpos = dev_alloc<int>(mE + mI, e);
+    h->je_p = dev_alloc<int>(je_p.size(), e); h->je_c = dev_alloc<int>(je_c.size(), e); h->je_v = dev_alloc<int>(je_v.size(), e);
+    h->ji_p = dev_alloc<int>(ji_p.size(), e); h->ji_c = dev_alloc<int>(ji_c.size(), e); h->ji_v = dev_alloc<int>(ji_v.size(), e);
+    h->jet_p = dev_alloc<int>(jet_p.size(), e); h->jet_c = dev_alloc<int>(jet_c.size(), e); h->jet_v = dev_alloc<int>(jet_v.size(), e);
+    h->jit_p = dev_alloc<int>(jit_p.size(), e); h->jit_c = dev_alloc<int>(jit_c.size(), e); h->jit_v = dev_alloc<int>(jit_v.size(), e);
+    h->cptr = dev_alloc<int64_t>(cptr.size(), e); h->cl = dev_alloc<Contrib>(cl.size(), e);
+    h->hg = dev_alloc<double>(hg_c.size(), e);
+    h->dE = dev_alloc<double>(mE, e); h->C = dev_alloc<double>(mE, e); h->sq = dev_alloc<double>(mE, e);
+    h->dinv = dev_alloc<double>(std::max(mI, 1), e);
+    h->r2 = dev_alloc<double>(np, e); h->t = dev_alloc<double>(np, e); h->u = dev_alloc<double>(np, e);
+    h->v = dev_alloc<double>(np, e);
+    h->w = dev_alloc<double>(mE, e); h->r = dev_alloc<double>(mE, e); h->p = dev_alloc<double>(mE, e);
+    h->q = dev_alloc<double>(mE, e); h->e = dev_alloc<double>(std::max(mE, mI), e);
+    h->part = dev_alloc<double>(kBlocks, e); h->s = dev_alloc<double>(4, e);
+    h->rpart = dev_alloc<unsigned long long>(4 * kBlocks, e);
+    h->flag = dev_alloc<int>(1, e);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->pin, sizeof(double) * (8 + 4 * kBlocks));
+    if (e == cudaSuccess) e = cudaMemcpy(h->rp, h_rowptr, (n + 1) * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->ci, h_colidx, nnz * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = upload(h->dpos, dpos);
+    if (e == cudaSuccess) e = upload(h->je_p, je_p);
+    if (e == cudaSuccess) e = upload(h->je_c, je_c);
+    if (e == cudaSuccess) e = upload(h->je_v, je_v);
+    if (e == cudaSuccess) e = upload(h->ji_p, ji_p);
+    if (e == cudaSuccess) e = upload(h->ji_c, ji_c);
+    if (e == cudaSuccess) e = upload(h->ji_v, ji_v);
+    if (e == cudaSuccess) e = upload(h->jet_p, jet_p);
+    if (e == cudaSuccess) e = upload(h->jet_c, jet_c);
+    if (e == cudaSuccess) e = upload(h->jet_v, jet_v);
+    if (e == cudaSuccess) e = upload(h->jit_p, jit_p);
+    if (e == cudaSuccess) e = upload(h->jit_c, jit_c);
+    if (e == cudaSuccess) e = upload(h->jit_v, jit_v);
+    if (e == cudaSuccess) e = upload(h->cptr, cptr);
+    if (e == cudaSuccess) e = upload(h->cl, cl);
+    if (e != cudaSuccess) {
+        kkt_hykkt_destroy(h);
+        return e == cudaErrorMemoryAllocation ? KKT_E_NOMEM : KKT_E_CUDA;
+    }
+    *out = h;
+    return KKT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// q = sq .* jv + d_E .* p (jv may be q)
+__global__ void reduced_op_kernel(int m, const double* __restrict__ sq, const double* jv, const double* __restrict__ dE,
+                                  const double* __restrict__ p, double* q)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        q[i] = sq[i] * jv[i] + dE[i] * p[i];
+}
+
+void dot(const kkt_hykkt* h, int n, const double* a, const double* b, double* out, cudaStream_t st)
+{
+    dot_part_kernel<<<kBlocks, kThreads, 0, st>>>(n, a, b, h->part);
+    dot_final_kernel<<<1, 32, 0, st>>>(h->part, out);
+}
+
+int grid_for(int64_t n)
+{
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kBlocks * 4, (n + kThreads - 1) / kThreads));
+}
+
+}  // namespace
+
+extern "C" {
+
+kkt_status kkt_hykkt_solve(kkt_hykkt* h, const double* d_vals, const double* d_rhs, double* d_z, double tol,
+                           int32_t max_iter, kkt_hykkt_info* info, void* stream)
+{
+    if (!h || !d_vals || !d_rhs || !d_z || !(tol >= 0.0) || max_iter < 0) return KKT_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int np = h->np, mE = h->mE, mI = h->mI;
+    const double* rx = d_rhs;
+    const double* rE = d_rhs + np;
+    const double* rI = d_rhs + np + mE;
+    double* x = d_z;
+    double* yE = d_z + np;
+    double* yI = d_z + np + mE;
+    const int gE = grid_for(mE), gI = grid_for(mI), gP = grid_for(np);
+#define HK_CUDA(call)                                                                                             \
+    do {                                                                                                          \
+        if ((call) != cudaSuccess) return KKT_E_CUDA;                                                             \
+    } while (0)
+    kkt_status ks;
+    // the (2,2) block, H_g and its factorization
+    HK_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
+    duals_kernel<<<grid_for(mE + mI), kThreads, 0, st>>>(mE, mI, h->dpos, d_vals, h->gamma, h->dE, h->C, h->sq,
+                                                          h->dinv, h->flag);
+    hg_assemble_kernel<<<grid_for(h->nnz_g), kThreads, 0, st>>>(h->nnz_g, h->cptr, h->cl, d_vals, h->dinv, h->gamma,
+                                                                 h->hg);
+    HK_CUDA(cudaGetLastError());
+    if ((ks = kkt_refactor(h->inner, h->hg, st)) != KKT_OK) return ks;
+    // r'' = r_x + J_I^T (r_I ./ d_I) + gamma J_E^T r_E
+    if (mI) vec_kernel<<<gI, kThreads, 0, st>>>(0, mI, rI, h->dinv, nullptr, h->e);
+    jt_mul_kernel<<<gP, kThreads, 0, st>>>(np, h->jit_p, h->jit_c, h->jit_v, h->jet_p, h->jet_c, h->jet_v, d_vals, rx,
+                                           mI ? h->e : nullptr, rE, h->gamma, h->r2);
+    HK_CUDA(cudaGetLastError());
+    // right-hand side of the reduced system: sq .* (J_E H_g^{-1} r'' - r_E); w = 0, r = p = b'
+    if ((ks = kkt_solve(h->inner, h->r2, h->t, st)) != KKT_OK) return ks;
+    j_mul_kernel<<<gE, kThreads, 0, st>>>(mE, h->je_p, h->je_c, h->je_v, d_vals, h->t, h->q);
+    vec_kernel<<<gE, kThreads, 0, st>>>(1, mE, h->sq, h->q, rE, h->r);
+    HK_CUDA(cudaMemsetAsync(h->w, 0, sizeof(double) * mE, st));
+    HK_CUDA(cudaMemcpyAsync(h->p, h->r, sizeof(double) * mE, cudaMemcpyDeviceToDevice, st));
+    dot(h, mE, h->r, h->r, h->s, st);
+    HK_CUDA(cudaGetLastError());
+    // conjugate gradients on (C^{1/2} J_E H_g^{-1} J_E^T C^{1/2} + D_E) w = b'
+    int it = 0;
+    double nb2 = -1.0, rr = 0.0;
+    for (;; ++it) {
+        if (it % kCheck == 0 || it == max_iter) {
+            HK_CUDA(cudaMemcpyAsync(h->pin, h->s, sizeof(double), cudaMemcpyDeviceToHost, st));
+            HK_CUDA(cudaMemcpyAsync(h->pin + 1, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+            HK_CUDA(cudaStreamSynchronize(st));
+            int fl = 0;
+            std::memcpy(&fl, h->pin + 1, sizeof(int));
+            if (fl) return KKT_E_NUMERIC;                       // d_I <= 0 or gamma d_E >= 1
+            rr = h->pin[0];
+            if (nb2 < 0.0) nb2 = rr;
+            if (!(rr == rr)) return KKT_E_NUMERIC;
+            if (std::sqrt(rr) <= tol * std::sqrt(nb2) || it >= max_iter) break;
+        }
+        vec_kernel<<<gE, kThreads, 0, st>>>(0, mE, h->sq, h->p, nullptr, h->e);
+        jt_mul_kernel<<<gP, kThreads, 0, st>>>(np, h->jit_p, h->jit_c, h->jit_v, h->jet_p, h->jet_c, h->jet_v, d_vals,
+                                               nullptr, nullptr, h->e, 1.0, h->u);
+        if ((ks = kkt_solve(h->inner, h->u, h->v, st)) != KKT_OK) return ks;
+        j_mul_kernel<<<gE, kThreads, 0, st>>>(mE, h->je_p, h->je_c, h->je_v, d_vals, h->v, h->q);
+        reduced_op_kernel<<<gE, kThreads, 0, st>>>(mE, h->sq, h->q, h->dE, h->p, h->q);
+        dot(h, mE, h->p, h->q, h->s + 1, st);
+        cg_update_kernel<<<gE, kThreads, 0, st>>>(mE, h->s, h->p, h->q, h->w, h->r);
+        dot(h, mE, h->r, h->r, h->s + 2, st);
+        cg_direction_kernel<<<gE, kThreads, 0, st>>>(mE, h->s, h->r, h->p);
+        shift_kernel<<<1, 32, 0, st>>>(h->s);
+        HK_CUDA(cudaGetLastError());
+    }
+    // recover: y_E = w ./ sq, x = H_g^{-1} (r'' - J_E^T (C .* y_E)), y_I = (J_I x - r_I) ./ d_I
+    vec_kernel<<<gE, kThreads, 0, st>>>(3, mE, h->w, h->sq, nullptr, yE);
+    vec_kernel<<<gE, kThreads, 0, st>>>(4, mE, h->C, yE, nullptr, h->e);
+    jt_mul_kernel<<<gP, kThreads, 0, st>>>(np, h->jit_p, h->jit_c, h->jit_v, h->jet_p, h->jet_c, h->jet_v, d_vals,
+                                           h->r2, nullptr, h->e, 1.0, h->u);
+    if ((ks = kkt_solve(h->inner, h->u, x, st)) != KKT_OK) return ks;
+    if (mI) {
+        j_mul_kernel<<<gI, kThreads, 0, st>>>(mI, h->ji_p, h->ji_c, h->ji_v, d_vals, x, h->e);
+        vec_kernel<<<gI, kThreads, 0, st>>>(5, mI, h->e, rI, h->dinv, yI);
+    }
+    // backward error of z for K
+    resid_part_kernel<<<kBlocks, kThreads, 0, st>>>(h->n, h->rp, h->ci, d_vals, d_z, d_rhs, h->rpart);
+    HK_CUDA(cudaGetLastError());
+    HK_CUDA(cudaMemcpyAsync(h->pin + 8, h->rpart, sizeof(unsigned long long) * 4 * kBlocks, cudaMemcpyDeviceToHost, st));
+    HK_CUDA(cudaStreamSynchronize(st));
+    unsigned long long m[4] = {0ull, 0ull, 0ull, 0ull};
+    const unsigned long long* hp = reinterpret_cast<const unsigned long long*>(h->pin + 8);
+    for (int b = 0; b < kBlocks; ++b)
+        for (int k = 0; k < 4; ++k) m[k] = std::max(m[k], hp[4 * b + k]);
+    double v[4];
+    std::memcpy(v, m, sizeof(v));
+    const double den = v[3] * v[1] + v[2];
+    const double omega = den > 0.0 ? v[0] / den : (den == 0.0 ? v[0] : den);
+    kkt_info inner_info;
+    kkt_get_info(h->inner, &inner_info);
+    const bool converged = std::sqrt(rr) <= tol * std::sqrt(nb2 > 0.0 ? nb2 : 0.0) || nb2 == 0.0;
+    if (info) {
+        info->cg_iters = it;
+        info->status = converged ? KKT_OK : KKT_E_NOCONV;
+        info->cg_resid = nb2 > 0.0 ? std::sqrt(rr / nb2) : 0.0;
+        info->backward_err = omega;
+        info->n_perturbed = inner_info.n_perturbed;
+        info->reserved = 0;
+    }
+#undef HK_CUDA
+    return converged ? KKT_OK : KKT_E_NOCONV;
+}
+
+void kkt_hykkt_destroy(kkt_hykkt* h)
+{
+    if (!h) return;
+    if (h->inner) kkt_destroy(h->inner);
+    void* dev[] = {h->rp, h->ci, h->dpos, h->je_p, h->je_c, h->je_v, h->ji_p, h->ji_c, h->ji_v, h->jet_p, h->jet_c,
+                   h->jet_v, h->jit_p, h->jit_c, h->jit_v, h->cptr, h->cl, h->hg, h->dE, h->C, h->sq, h->dinv, h->r2,
+                   h->t, h->u, h->v, h->w, h->r, h->p, h->q, h->e, h->part, h->s, h->rpart, h->flag};
+    for (void* p : dev)
+        if (p) cudaFree(p);
+    if (h->pin) cudaFreeHost(h->pin);
+    delete h;
+}
+
+}  // extern "C"
