@@ -536,7 +536,7 @@ typedef struct {
     int cg_iters;               /* conjugate-gradient iterations */
     int status;                 /* KKT_OK, or KKT_E_NOCONV if cg_resid > tol at max_iter */
     int n_perturbed;            /* static pivot perturbations of the factorization of H_g */
-    int reserved;
+    int launches;               /* kernels this call launched, the inner factorization's and solves' included */
     double cg_resid;            /* ||b' - A w|| / ||b'|| of the reduced system at exit */
     double backward_err;        /* ||K z - b||_inf / (||K||_inf ||z||_inf + ||b||_inf) */
 } kkt_hykkt_info;
@@ -554,7 +554,7 @@ kkt_status kkt_hykkt_analyze(int32_t n, int32_t n_primal, int32_t m_eq, const in
  * the CSR order given to the analysis); d_rhs, d_z device FP64 vectors of
  * length n, not aliased. Stops when the reduced residual is <= tol times its
  * initial value or after max_iter iterations. Synchronizes `stream` (the host
- * reads the reduced residual every few iterations); info may be NULL.
+ * reads the reduced residual after every iteration); info may be NULL.
  * Errors: KKT_E_ARG, KKT_E_NUMERIC (some d_I <= 0, gamma d_E >= 1, or NaN),
  * KKT_E_NOCONV (z written, info filled), KKT_E_CUDA. */
 kkt_status kkt_hykkt_solve(kkt_hykkt *h, const double *d_vals, const double *d_rhs, double *d_z, double tol,

@@ -560,9 +560,12 @@ class SaddlePointSolver:
     rows condensed, equality rows augmented by gamma J_E^T J_E, conjugate
     gradients on the reduced symmetric operator, one factorization of H_g by
     the library per call. Unknowns ordered (primal, m_eq equality duals,
-    inequality duals); the (2,2) block diagonal."""
+    inequality duals); the (2,2) block diagonal. gamma must keep
+    gamma * d_E < 1; the default suits the literal regularization (d_E =
+    1e-10): larger gamma, fewer iterations (8 to 12 at 1e8 on the 25,000- and
+    70,000-bus systems) at an unchanged backward error."""
 
-    def __init__(self, rowptr, colidx, n_primal, m_eq, gamma=1e4):
+    def __init__(self, rowptr, colidx, n_primal, m_eq, gamma=1e8):
         rp, ci = _pattern(rowptr, colidx)
         self.n = len(rp) - 1
         self.nnz = int(rp[-1])

@@ -82,7 +82,7 @@ class IpmInfo(C.Structure):
 
 
 class HykktInfo(C.Structure):
-    _fields_ = [("cg_iters", C.c_int), ("status", C.c_int), ("n_perturbed", C.c_int), ("reserved", C.c_int),
+    _fields_ = [("cg_iters", C.c_int), ("status", C.c_int), ("n_perturbed", C.c_int), ("launches", C.c_int),
                 ("cg_resid", C.c_double), ("backward_err", C.c_double)]
 
 

@@ -10,9 +10,9 @@
 // gamma J_E^T J_E (H_g = H' + gamma J_E^T J_E, factored by the library's own
 // multifrontal LU in an inner context), solve the equality duals by conjugate
 // gradients on the symmetric operator C^{1/2} J_E H_g^{-1} J_E^T C^{1/2} + D_E
-// (C = I - gamma D_E; one solve with H_g per iteration), then recover x and
-// y_I. Every step runs in kernels on the caller's stream; the host reads the
-// conjugate-gradient residual every kCheck iterations to stop.
+// (C = I - gamma D_E; one solve with H_g per iteration, x updated along),
+// then recover y_E and y_I. Every step runs in kernels on the caller's stream; the host reads the
+// conjugate-gradient residual after every iteration to stop.
 #include "../../include/kkt.h"
 
 #include <cuda_runtime.h>
@@ -28,7 +28,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kBlocks = 304;          // 2 x 152 SMs, grid-stride loops; also the partial sums of a dot product
-constexpr int kCheck = 4;             // conjugate-gradient iterations between two reads of the residual
 
 // one step of an H_g entry: kind -1: K value a; -2: gamma K_a K_b (a J_E pair);
 // k >= 0: K_a K_b / d_I[k] (a J_I pair of inequality row k)
@@ -85,20 +84,28 @@ __global__ void j_mul_kernel(int m, const int* __restrict__ ptr, const int* __re
     }
 }
 
-// out = base + J_I^T xi + ge J_E^T xe over the primal rows (transposes as CSR
-// of positions); base, xi, xe may be null
+// out = base + J_I^T (xi .* si) + ge J_E^T (xe .* se) over the primal rows
+// (transposes as CSR of positions); base, xi, xe, si, se may be null (a null
+// scale is 1)
 __global__ void jt_mul_kernel(int np, const int* __restrict__ ip, const int* __restrict__ ic, const int* __restrict__ ipos,
                               const int* __restrict__ ep, const int* __restrict__ ec, const int* __restrict__ epos,
                               const double* __restrict__ vals, const double* __restrict__ base,
-                              const double* __restrict__ xi, const double* __restrict__ xe, double ge,
+                              const double* __restrict__ xi, const double* __restrict__ si,
+                              const double* __restrict__ xe, const double* __restrict__ se, double ge,
                               double* __restrict__ out)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
         double a = 0.0, e = 0.0;
         if (xi)
-            for (int p = ip[i]; p < ip[i + 1]; ++p) a += vals[ipos[p]] * xi[ic[p]];
+            for (int p = ip[i]; p < ip[i + 1]; ++p) {
+                const int k = ic[p];
+                a += vals[ipos[p]] * (si ? xi[k] * si[k] : xi[k]);
+            }
         if (xe)
-            for (int p = ep[i]; p < ep[i + 1]; ++p) e += vals[epos[p]] * xe[ec[p]];
+            for (int p = ep[i]; p < ep[i + 1]; ++p) {
+                const int k = ec[p];
+                e += vals[epos[p]] * (se ? xe[k] * se[k] : xe[k]);
+            }
         out[i] = (base ? base[i] : 0.0) + a + ge * e;
     }
 }
@@ -109,10 +116,8 @@ __global__ void vec_kernel(int op, int n, const double* __restrict__ a, const do
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         switch (op) {
-        case 0: out[i] = a[i] * b[i]; break;                      // a .* b
-        case 1: out[i] = a[i] * (b[i] - c[i]); break;             // a .* (b - c)
+        case 1: out[i] = a[i] * (b[i] - c[i]); break;             // b' = sq .* (J_E t - r_E)
         case 3: out[i] = a[i] / b[i]; break;                      // y_E = w ./ sq
-        case 4: out[i] = -(a[i] * b[i]); break;                   // -(C .* y_E)
         default: out[i] = (a[i] - b[i]) * c[i]; break;            // y_I = (J_I x - r_I) .* (1 / d_I)
         }
     }
@@ -143,29 +148,86 @@ __global__ void dot_final_kernel(const double* __restrict__ part, double* __rest
     }
 }
 
-// conjugate-gradient steps with the scalars on the device: s[0] = r.r,
-// s[1] = p.q, s[2] = the new r.r. update: w += alpha p, r -= alpha q with
-// alpha = s0 / s1; direction: p = r + (s2 / s0) p
-__global__ void cg_update_kernel(int n, const double* __restrict__ s, const double* __restrict__ p,
-                                 const double* __restrict__ q, double* __restrict__ w, double* __restrict__ r)
+// sum of the kBlocks partials, the same fixed order in every block (warp 0:
+// strided lane sums, then a shuffle tree); every thread gets the result
+__device__ double sum_parts(const double* __restrict__ part)
 {
-    const double alpha = s[0] / s[1];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        w[i] += alpha * p[i];
-        r[i] -= alpha * q[i];
+    __shared__ double res;
+    if (threadIdx.x < 32) {
+        double a = 0.0;
+        for (int b = threadIdx.x; b < kBlocks; b += 32) a += part[b];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (threadIdx.x == 0) res = a;
     }
+    __syncthreads();
+    const double v = res;
+    __syncthreads();
+    return v;
 }
 
-__global__ void cg_direction_kernel(int n, const double* __restrict__ s, const double* __restrict__ r,
-                                    double* __restrict__ p)
+__device__ void block_sum_to(double acc, double* __restrict__ part)
 {
-    const double beta = s[2] / s[0];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = r[i] + beta * p[i];
+    __shared__ double s[kThreads];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kThreads / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
-__global__ void shift_kernel(double* s)
+// one conjugate-gradient iteration in three kernels (kBlocks blocks each; the
+// scalars stay on the device; s[cur] = r.r of this iteration, the next one
+// goes to s[cur ^ 1]):
+//   q = sq .* (J_E v) + d_E .* p, partial p.q     (v = H_g^{-1} J_E^T (sq .* p))
+__global__ void __launch_bounds__(kThreads) cg_q_kernel(int m, const int* __restrict__ ptr, const int* __restrict__ col,
+                                                        const int* __restrict__ pos, const double* __restrict__ vals,
+                                                        const double* __restrict__ v, const double* __restrict__ sq,
+                                                        const double* __restrict__ dE, const double* __restrict__ p,
+                                                        double* __restrict__ q, double* __restrict__ part)
 {
-    if (threadIdx.x == 0) s[0] = s[2];
+    double acc = 0.0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+        double jv = 0.0;
+        for (int k = ptr[r]; k < ptr[r + 1]; ++k) jv += vals[pos[k]] * v[col[k]];
+        const double qr = sq[r] * jv + dE[r] * p[r];
+        q[r] = qr;
+        acc += p[r] * qr;
+    }
+    block_sum_to(acc, part);
+}
+
+//   alpha = s[cur] / (p.q); w += alpha p; r -= alpha q; x -= alpha v
+//   (x = H_g^{-1} (r'' - J_E^T (sq .* w)) kept along); partial r.r
+__global__ void __launch_bounds__(kThreads) cg_update_kernel(int m, int np, const double* __restrict__ part_pq,
+                                                             const double* __restrict__ s, int cur,
+                                                             const double* __restrict__ p, const double* __restrict__ q,
+                                                             const double* __restrict__ v, double* __restrict__ w,
+                                                             double* __restrict__ r, double* __restrict__ x,
+                                                             double* __restrict__ part_rr)
+{
+    const double alpha = s[cur] / sum_parts(part_pq);
+    double acc = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        w[i] += alpha * p[i];
+        const double ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        acc += ri * ri;
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) x[i] -= alpha * v[i];
+    block_sum_to(acc, part_rr);
+}
+
+//   s[cur ^ 1] = r.r; p = r + (s[cur ^ 1] / s[cur]) p
+__global__ void __launch_bounds__(kThreads) cg_direction_kernel(int m, const double* __restrict__ part_rr, double* s,
+                                                                int cur, const double* __restrict__ r,
+                                                                double* __restrict__ p)
+{
+    const double rr = sum_parts(part_rr);
+    const double beta = rr / s[cur];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) p[i] = r[i] + beta * p[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) s[cur ^ 1] = rr;
 }
 
 __device__ __forceinline__ unsigned long long mag(double v)
@@ -230,9 +292,9 @@ struct kkt_hykkt {
     double* hg = nullptr;
     // vectors and scalars
     double *dE = nullptr, *C = nullptr, *sq = nullptr, *dinv = nullptr;
-    double *r2 = nullptr, *t = nullptr, *u = nullptr, *v = nullptr;        // np
+    double *r2 = nullptr, *u = nullptr, *v = nullptr;                      // np
     double *w = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *e = nullptr;   // mE
-    double *part = nullptr, *s = nullptr;
+    double *part = nullptr, *part2 = nullptr, *s = nullptr;
     unsigned long long* rpart = nullptr;
     int* flag = nullptr;
     double* pin = nullptr;                                       // host: s[0..3], flag, residual partials
@@ -352,11 +414,12 @@ kkt_status kkt_hykkt_analyze(int32_t n, int32_t n_primal, int32_t m_eq, const in
     h->hg = dev_alloc<double>(hg_c.size(), e);
     h->dE = dev_alloc<double>(mE, e); h->C = dev_alloc<double>(mE, e); h->sq = dev_alloc<double>(mE, e);
     h->dinv = dev_alloc<double>(std::max(mI, 1), e);
-    h->r2 = dev_alloc<double>(np, e); h->t = dev_alloc<double>(np, e); h->u = dev_alloc<double>(np, e);
+    h->r2 = dev_alloc<double>(np, e); h->u = dev_alloc<double>(np, e);
     h->v = dev_alloc<double>(np, e);
     h->w = dev_alloc<double>(mE, e); h->r = dev_alloc<double>(mE, e); h->p = dev_alloc<double>(mE, e);
     h->q = dev_alloc<double>(mE, e); h->e = dev_alloc<double>(std::max(mE, mI), e);
-    h->part = dev_alloc<double>(kBlocks, e); h->s = dev_alloc<double>(4, e);
+    h->part = dev_alloc<double>(kBlocks, e); h->part2 = dev_alloc<double>(kBlocks, e);
+    h->s = dev_alloc<double>(4, e);
     h->rpart = dev_alloc<unsigned long long>(4 * kBlocks, e);
     h->flag = dev_alloc<int>(1, e);
     if (e == cudaSuccess) e = cudaMallocHost(&h->pin, sizeof(double) * (8 + 4 * kBlocks));
@@ -388,14 +451,6 @@ kkt_status kkt_hykkt_analyze(int32_t n, int32_t n_primal, int32_t m_eq, const in
 }  // extern "C"
 
 namespace {
-
-// q = sq .* jv + d_E .* p (jv may be q)
-__global__ void reduced_op_kernel(int m, const double* __restrict__ sq, const double* jv, const double* __restrict__ dE,
-                                  const double* __restrict__ p, double* q)
-{
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
-        q[i] = sq[i] * jv[i] + dE[i] * p[i];
-}
 
 void dot(const kkt_hykkt* h, int n, const double* a, const double* b, double* out, cudaStream_t st)
 {
@@ -430,68 +485,80 @@ kkt_status kkt_hykkt_solve(kkt_hykkt* h, const double* d_vals, const double* d_r
         if ((call) != cudaSuccess) return KKT_E_CUDA;                                                             \
     } while (0)
     kkt_status ks;
+    int nl = 0;                                                   // kernels launched here
+    kkt_info inner0;
+    kkt_get_info(h->inner, &inner0);
     // the (2,2) block, H_g and its factorization
     HK_CUDA(cudaMemsetAsync(h->flag, 0, sizeof(int), st));
     duals_kernel<<<grid_for(mE + mI), kThreads, 0, st>>>(mE, mI, h->dpos, d_vals, h->gamma, h->dE, h->C, h->sq,
                                                           h->dinv, h->flag);
+    ++nl;
     hg_assemble_kernel<<<grid_for(h->nnz_g), kThreads, 0, st>>>(h->nnz_g, h->cptr, h->cl, d_vals, h->dinv, h->gamma,
                                                                  h->hg);
+    ++nl;
     HK_CUDA(cudaGetLastError());
     if ((ks = kkt_refactor(h->inner, h->hg, st)) != KKT_OK) return ks;
-    // r'' = r_x + J_I^T (r_I ./ d_I) + gamma J_E^T r_E
-    if (mI) vec_kernel<<<gI, kThreads, 0, st>>>(0, mI, rI, h->dinv, nullptr, h->e);
+    // r'' = r_x + J_I^T (r_I ./ d_I) + gamma J_E^T r_E; x starts at t = H_g^{-1} r''
     jt_mul_kernel<<<gP, kThreads, 0, st>>>(np, h->jit_p, h->jit_c, h->jit_v, h->jet_p, h->jet_c, h->jet_v, d_vals, rx,
-                                           mI ? h->e : nullptr, rE, h->gamma, h->r2);
+                                           mI ? rI : nullptr, h->dinv, rE, nullptr, h->gamma, h->r2);
+    ++nl;
     HK_CUDA(cudaGetLastError());
-    // right-hand side of the reduced system: sq .* (J_E H_g^{-1} r'' - r_E); w = 0, r = p = b'
-    if ((ks = kkt_solve(h->inner, h->r2, h->t, st)) != KKT_OK) return ks;
-    j_mul_kernel<<<gE, kThreads, 0, st>>>(mE, h->je_p, h->je_c, h->je_v, d_vals, h->t, h->q);
+    if ((ks = kkt_solve(h->inner, h->r2, x, st)) != KKT_OK) return ks;
+    // right-hand side of the reduced system: b' = sq .* (J_E t - r_E); w = 0, r = p = b'
+    j_mul_kernel<<<gE, kThreads, 0, st>>>(mE, h->je_p, h->je_c, h->je_v, d_vals, x, h->q);
+    ++nl;
     vec_kernel<<<gE, kThreads, 0, st>>>(1, mE, h->sq, h->q, rE, h->r);
+    ++nl;
     HK_CUDA(cudaMemsetAsync(h->w, 0, sizeof(double) * mE, st));
     HK_CUDA(cudaMemcpyAsync(h->p, h->r, sizeof(double) * mE, cudaMemcpyDeviceToDevice, st));
     dot(h, mE, h->r, h->r, h->s, st);
+    nl += 2;
     HK_CUDA(cudaGetLastError());
-    // conjugate gradients on (C^{1/2} J_E H_g^{-1} J_E^T C^{1/2} + D_E) w = b'
-    int it = 0;
+    // conjugate gradients on (C^{1/2} J_E H_g^{-1} J_E^T C^{1/2} + D_E) w = b';
+    // each iteration costs a whole solve with H_g, so the host reads r.r after
+    // every one (a short copy and wait) instead of running past convergence
+    int it = 0, cur = 0;
     double nb2 = -1.0, rr = 0.0;
     for (;; ++it) {
-        if (it % kCheck == 0 || it == max_iter) {
-            HK_CUDA(cudaMemcpyAsync(h->pin, h->s, sizeof(double), cudaMemcpyDeviceToHost, st));
-            HK_CUDA(cudaMemcpyAsync(h->pin + 1, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-            HK_CUDA(cudaStreamSynchronize(st));
+        HK_CUDA(cudaMemcpyAsync(h->pin, h->s + cur, sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (it == 0) HK_CUDA(cudaMemcpyAsync(h->pin + 1, h->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        HK_CUDA(cudaStreamSynchronize(st));
+        if (it == 0) {
             int fl = 0;
             std::memcpy(&fl, h->pin + 1, sizeof(int));
             if (fl) return KKT_E_NUMERIC;                       // d_I <= 0 or gamma d_E >= 1
-            rr = h->pin[0];
-            if (nb2 < 0.0) nb2 = rr;
-            if (!(rr == rr)) return KKT_E_NUMERIC;
-            if (std::sqrt(rr) <= tol * std::sqrt(nb2) || it >= max_iter) break;
         }
-        vec_kernel<<<gE, kThreads, 0, st>>>(0, mE, h->sq, h->p, nullptr, h->e);
+        rr = h->pin[0];
+        if (nb2 < 0.0) nb2 = rr;
+        if (!(rr == rr) || !std::isfinite(rr)) return KKT_E_NUMERIC;
+        if (std::sqrt(rr) <= tol * std::sqrt(nb2) || it >= max_iter) break;
+        // v = H_g^{-1} J_E^T (sq .* p)
         jt_mul_kernel<<<gP, kThreads, 0, st>>>(np, h->jit_p, h->jit_c, h->jit_v, h->jet_p, h->jet_c, h->jet_v, d_vals,
-                                               nullptr, nullptr, h->e, 1.0, h->u);
-        if ((ks = kkt_solve(h->inner, h->u, h->v, st)) != KKT_OK) return ks;
-        j_mul_kernel<<<gE, kThreads, 0, st>>>(mE, h->je_p, h->je_c, h->je_v, d_vals, h->v, h->q);
-        reduced_op_kernel<<<gE, kThreads, 0, st>>>(mE, h->sq, h->q, h->dE, h->p, h->q);
-        dot(h, mE, h->p, h->q, h->s + 1, st);
-        cg_update_kernel<<<gE, kThreads, 0, st>>>(mE, h->s, h->p, h->q, h->w, h->r);
-        dot(h, mE, h->r, h->r, h->s + 2, st);
-        cg_direction_kernel<<<gE, kThreads, 0, st>>>(mE, h->s, h->r, h->p);
-        shift_kernel<<<1, 32, 0, st>>>(h->s);
+                                               nullptr, nullptr, nullptr, h->p, h->sq, 1.0, h->u);
+        ++nl;
         HK_CUDA(cudaGetLastError());
+        if ((ks = kkt_solve(h->inner, h->u, h->v, st)) != KKT_OK) return ks;
+        cg_q_kernel<<<kBlocks, kThreads, 0, st>>>(mE, h->je_p, h->je_c, h->je_v, d_vals, h->v, h->sq, h->dE, h->p,
+                                                  h->q, h->part);
+        cg_update_kernel<<<kBlocks, kThreads, 0, st>>>(mE, np, h->part, h->s, cur, h->p, h->q, h->v, h->w, h->r, x,
+                                                       h->part2);
+        cg_direction_kernel<<<kBlocks, kThreads, 0, st>>>(mE, h->part2, h->s, cur, h->r, h->p);
+        nl += 3;
+        HK_CUDA(cudaGetLastError());
+        cur ^= 1;
     }
-    // recover: y_E = w ./ sq, x = H_g^{-1} (r'' - J_E^T (C .* y_E)), y_I = (J_I x - r_I) ./ d_I
+    // recover: y_E = w ./ sq (x kept along the iteration), y_I = (J_I x - r_I) ./ d_I
     vec_kernel<<<gE, kThreads, 0, st>>>(3, mE, h->w, h->sq, nullptr, yE);
-    vec_kernel<<<gE, kThreads, 0, st>>>(4, mE, h->C, yE, nullptr, h->e);
-    jt_mul_kernel<<<gP, kThreads, 0, st>>>(np, h->jit_p, h->jit_c, h->jit_v, h->jet_p, h->jet_c, h->jet_v, d_vals,
-                                           h->r2, nullptr, h->e, 1.0, h->u);
-    if ((ks = kkt_solve(h->inner, h->u, x, st)) != KKT_OK) return ks;
+    ++nl;
     if (mI) {
         j_mul_kernel<<<gI, kThreads, 0, st>>>(mI, h->ji_p, h->ji_c, h->ji_v, d_vals, x, h->e);
+        ++nl;
         vec_kernel<<<gI, kThreads, 0, st>>>(5, mI, h->e, rI, h->dinv, yI);
+        ++nl;
     }
     // backward error of z for K
     resid_part_kernel<<<kBlocks, kThreads, 0, st>>>(h->n, h->rp, h->ci, d_vals, d_z, d_rhs, h->rpart);
+    ++nl;
     HK_CUDA(cudaGetLastError());
     HK_CUDA(cudaMemcpyAsync(h->pin + 8, h->rpart, sizeof(unsigned long long) * 4 * kBlocks, cudaMemcpyDeviceToHost, st));
     HK_CUDA(cudaStreamSynchronize(st));
@@ -512,7 +579,7 @@ kkt_status kkt_hykkt_solve(kkt_hykkt* h, const double* d_vals, const double* d_r
         info->cg_resid = nb2 > 0.0 ? std::sqrt(rr / nb2) : 0.0;
         info->backward_err = omega;
         info->n_perturbed = inner_info.n_perturbed;
-        info->reserved = 0;
+        info->launches = nl + (int)(inner_info.launches - inner0.launches);
     }
 #undef HK_CUDA
     return converged ? KKT_OK : KKT_E_NOCONV;
@@ -524,7 +591,7 @@ void kkt_hykkt_destroy(kkt_hykkt* h)
     if (h->inner) kkt_destroy(h->inner);
     void* dev[] = {h->rp, h->ci, h->dpos, h->je_p, h->je_c, h->je_v, h->ji_p, h->ji_c, h->ji_v, h->jet_p, h->jet_c,
                    h->jet_v, h->jit_p, h->jit_c, h->jit_v, h->cptr, h->cl, h->hg, h->dE, h->C, h->sq, h->dinv, h->r2,
-                   h->t, h->u, h->v, h->w, h->r, h->p, h->q, h->e, h->part, h->s, h->rpart, h->flag};
+                   h->u, h->v, h->w, h->r, h->p, h->q, h->e, h->part, h->part2, h->s, h->rpart, h->flag};
     for (void* p : dev)
         if (p) cudaFree(p);
     if (h->pin) cudaFreeHost(h->pin);

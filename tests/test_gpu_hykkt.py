@@ -49,29 +49,33 @@ def test_matches_oracle_and_direct_solve_where_determined(gamma):
         assert np.max(np.abs(z - ref)) <= 1e-8 * scale
         assert np.max(np.abs(z - o.z)) <= 1e-8 * scale
         assert info.backward_err <= 1e-13 and hykkt.backward_error(Ks, z, b) <= 1e-13
-        assert abs(info.cg_iters - o.cg_iters) <= 4          # the device stops on a multiple of its check period
+        assert abs(info.cg_iters - o.cg_iters) <= 1          # same iteration, rounding apart
         assert info.status == 0 and info.cg_resid <= 1e-13
     s.close()
 
 
-@pytest.mark.parametrize("buses,lines,gens", [(200, 300, 40), (25_000, 32_000, 5_000)])
-def test_graded_like_inputs_reach_the_backward_error(buses, lines, gens):
+@pytest.mark.parametrize("buses,lines,gens,gamma", [(200, 300, 40, 1e4), (200, 300, 40, 1e8),
+                                                     (25_000, 32_000, 5_000, 1e8)])
+def test_graded_like_inputs_reach_the_backward_error(buses, lines, gens, gamma):
     """The interior-point form with the slacks' term (1/sigma_s on [1e-2, 1e2]),
     literal dw = 1e-8, dc = 1e-10, Sigma over [1e-8, 1e8]: omega <= 1e-10 for
     the whole K, as the oracle reaches on the same systems (200 buses)."""
     pat = KKTPattern(make_grid(1, buses, lines, gens))
     mE = 2 * pat.grid.n_bus
-    s = K.SaddlePointSolver(pat.rowptr, pat.colidx, pat.n_primal, mE, gamma=1e4)
+    s = K.SaddlePointSolver(pat.rowptr, pat.colidx, pat.n_primal, mE, gamma=gamma)
     for k, mu in enumerate([1e-1, 1e-5, 1e-8]):
         v = pat.values(pat.point(1, k, mu, slack_range=(1e-2, 1e2)))
         b = pat.rhs(1, k)
         z, info = s.solve(_t(v), _t(b), tol=1e-12, max_iter=500)
         om = hykkt.backward_error(pat.to_scipy(v), z.cpu().numpy(), b)
-        print("%d buses, mu %.0e: %d CG iterations, omega %.2e (library %.2e)" % (buses, mu, info.cg_iters, om,
+        print("%d buses, gamma %.0e, mu %.0e: %d CG iterations, omega %.2e (library %.2e)" % (buses, gamma, mu, info.cg_iters, om,
                                                                                  info.backward_err))
         assert om <= 1e-10 and info.backward_err == pytest.approx(om, rel=1e-3, abs=1e-18)
-        if buses <= 200:
-            o = hykkt.solve(pat.to_scipy(v), pat.n_primal, mE, b, 1e4, tol=1e-12, max_iter=500)
+        if buses <= 200 and gamma <= 1e6:
+            # the oracle's LU of H_g (unequilibrated, threshold pivoting) loses
+            # about kappa(H_g) u, which grows with gamma: at 1e8 it ends near
+            # 1e-10 on these systems, so it is held to the bound only below
+            o = hykkt.solve(pat.to_scipy(v), pat.n_primal, mE, b, gamma, tol=1e-12, max_iter=500)
             assert o.omega <= 1e-10
     s.close()
 
