@@ -1187,6 +1187,19 @@ def run_saddle(args):
     clocks = sampler.stop()
     res = [x.cpu().numpy() for x in xs[args.warmup:]]
 
+    # per-kernel time of the factorization and solves of H_g (profiling pass)
+    inner = sp_.inner()
+    inner.set_profiling(True)
+    inner.kernel_stats()
+    nprof = min(3, args.steps)
+    for t in range(nprof):
+        solve(at(args, args.warmup + t))
+    stats = inner.kernel_stats()
+    inner.set_profiling(False)
+    plan_g = inner.plan()
+    roofline = roofline_of(stats, nprof, plan_g, algorithmic_bytes(plan_g, plan_g["n"], plan_g["nnz"], 8), 8,
+                           args.workload + " H_g", "fp64")
+
     # the direct path on the same systems
     direct = {}
     for prec in ("fp32", "fp64"):
@@ -1235,12 +1248,14 @@ def run_saddle(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload + " saddle-point solve", "buses": w["n_bus"], "n": pat.n,
                    "nnz": pat.nnz, "n_primal": pat.n_primal, "m_eq": mE, "gamma": args.gamma,
-                   "cg_tol": args.cg_tol, "slack_range": list(sr),
+                   "cg_tol": args.cg_tol, "slack_range": list(sr), "n_hg": plan_g["n"], "nnz_hg": plan_g["nnz"],
+                   "nnz_lu_hg": plan_g["nnz_lu"],
                    "l2": "flushed between timed steps (512 MB write)", "analyze_s": analyze_s},
         "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
         "cg_iters_mean": float(np.mean(its)), "cg_iters_max": int(max(its)), "omega_max": float(max(oms)),
         "converged_steps": int(sum(1 for o in oms if o <= args.tol)),
         "direct_path": direct, "gpu_launches": int(launches), "clocks": clocks, "cpu_baseline": cpu,
+        "roofline": roofline, "inner_kernel_ms_per_call": {k: v[1] / nprof for k, v in stats.items()},
         "oracle_agreement": agree,
     }
     print(json.dumps(line), flush=True)

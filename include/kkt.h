@@ -560,6 +560,12 @@ kkt_status kkt_hykkt_analyze(int32_t n, int32_t n_primal, int32_t m_eq, const in
 kkt_status kkt_hykkt_solve(kkt_hykkt *h, const double *d_vals, const double *d_rhs, double *d_z, double tol,
                            int32_t max_iter, kkt_hykkt_info *info, void *stream);
 
+/* The inner context that factors H_g, borrowed: owned by h and valid until
+ * kkt_hykkt_destroy(h). For kkt_get_plan, kkt_get_info, kkt_set_profiling and
+ * kkt_kernel_stats only; the caller must not destroy, refactor or solve with it.
+ * Errors: KKT_E_ARG. */
+kkt_status kkt_hykkt_inner(kkt_hykkt *h, kkt_ctx **out);
+
 void kkt_hykkt_destroy(kkt_hykkt *h);
 
 #ifdef __cplusplus

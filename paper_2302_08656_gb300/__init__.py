@@ -555,6 +555,19 @@ class KKTGroup:
             pass
 
 
+class _BorrowedContext:
+    """A context owned by another object: introspection only, never destroyed here."""
+
+    def __init__(self, handle, owner):
+        self._h = handle
+        self._owner = owner          # keeps the owner (and so the context) alive
+
+    info = KKTSolver.info
+    plan = KKTSolver.plan
+    set_profiling = KKTSolver.set_profiling
+    kernel_stats = KKTSolver.kernel_stats
+
+
 class SaddlePointSolver:
     """Saddle-point specialised solve of K (kkt_hykkt_*; Sec. V): inequality
     rows condensed, equality rows augmented by gamma J_E^T J_E, conjugate
@@ -596,6 +609,13 @@ class SaddlePointSolver:
         if st != 6 or raise_on_noconv:
             _check(st, "kkt_hykkt_solve")
         return out, info
+
+    def inner(self):
+        """The context factoring H_g (borrowed, valid while this solver is
+        open): plan(), info(), set_profiling(), kernel_stats()."""
+        h = C.c_void_p()
+        _check(lib().kkt_hykkt_inner(self._h, C.byref(h)), "kkt_hykkt_inner")
+        return _BorrowedContext(h, self)
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -190,6 +190,7 @@ SIGNATURES = {
     "kkt_status_string": (C.c_char_p, [C.c_int]),
     "kkt_hykkt_analyze": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_double, C.POINTER(_P)]),
     "kkt_hykkt_solve": (C.c_int, [_P, _P, _P, _P, C.c_double, C.c_int32, C.POINTER(HykktInfo), _P]),
+    "kkt_hykkt_inner": (C.c_int, [_P, C.POINTER(_P)]),
     "kkt_hykkt_destroy": (None, [_P]),
 }
 

@@ -585,6 +585,13 @@ kkt_status kkt_hykkt_solve(kkt_hykkt* h, const double* d_vals, const double* d_r
     return converged ? KKT_OK : KKT_E_NOCONV;
 }
 
+kkt_status kkt_hykkt_inner(kkt_hykkt* h, kkt_ctx** out)
+{
+    if (!h || !out) return KKT_E_ARG;
+    *out = h->inner;
+    return KKT_OK;
+}
+
 void kkt_hykkt_destroy(kkt_hykkt* h)
 {
     if (!h) return;

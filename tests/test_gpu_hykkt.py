@@ -51,6 +51,8 @@ def test_matches_oracle_and_direct_solve_where_determined(gamma):
         assert info.backward_err <= 1e-13 and hykkt.backward_error(Ks, z, b) <= 1e-13
         assert abs(info.cg_iters - o.cg_iters) <= 1          # same iteration, rounding apart
         assert info.status == 0 and info.cg_resid <= 1e-13
+    pl = s.inner().plan()                       # the borrowed context factoring H_g
+    assert pl["n"] == pat.n_primal and pl["nnz"] >= pat.n_primal
     s.close()
 
 
