@@ -258,6 +258,8 @@ struct TreeSched {
     int max_F = 0, max_w = 0;
     int fwd_stage = 0;           // 1: forward solve stages the F x w panel in shared memory
     int bwd_stage = 0;           // 1: backward solve stages U12 in shared memory
+    int fwd_cstage = 0;          // 1: forward solve by chains stages two F x w panels (else pivot blocks)
+    int fwd_kstage = 0;          // children's contribution entries staged per front by the forward chains
     int max_fw = 0, max_wm = 0;
     // backward substitution by chains: chain c is the fronts bwd_chain[bwd_chain_ptr[c] ..
     // bwd_chain_ptr[c + 1] - 1], top first, each the only tree child of the one before

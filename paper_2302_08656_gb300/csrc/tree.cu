@@ -757,34 +757,6 @@ __device__ bool fwd_unit(const DevSched& s, const TreeSched& ts, const DevNum<T>
     return true;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(128) tree_fwd_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
-                                                       long long limit)
-{
-    extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ TreeFront d;
-    __shared__ TreeKid kids[kTreeMaxKids];
-    __shared__ int s_t, s_ok;
-    __shared__ int s_cut[kTreeMaxKids + 1];
-    const int tid = threadIdx.x;
-    const int total = ts.nq * B;
-    int* done = ctr + kCtrHead;
-    for (;;) {
-        const int t = next_ticket(ctr + 2, ctr + 1, total, &s_t);
-        if (t >= total) break;
-        const int q = t / B, b = t - q * B;
-        copy_words(&d, ts.fr + q, 1, tid, 128);
-        __syncthreads();
-        const DevNum<T> nm = nm0.at(b);
-        if (!fwd_unit<T, 128>(s, ts, nm, d, q, kids, s_cut, &s_ok, smraw, done + (int64_t)b * ts.nq, nullptr,
-                              ctr + 1, limit)) {
-            if (tid == 0) atomicExch(&nm.stat->timeout, 1);
-            break;
-        }
-        __syncthreads();
-    }
-}
-
 // ------------------------------------------------------ backward substitution
 
 // Asynchronous copy of one 4- or 8-byte word into shared memory (cp.async),
@@ -801,6 +773,212 @@ __device__ __forceinline__ void cp_wait_all()
 {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Named barrier 1 over the first `nthr` threads counted from a warp boundary
+// (the threads that stage a front; barrier 0 is __syncthreads).
+__device__ __forceinline__ void bar_sync_staging(int nthr)
+{
+    asm volatile("bar.sync 1, %0;\n" ::"r"(nthr) : "memory");
+}
+
+// Forward substitution of the tree part by chains: the backward kernel's
+// chains run bottom front first, chains in ascending order of their top
+// front, so every chain that a bottom front waits on holds an earlier ticket.
+// The bottom front of a chain waits for its children in the tree part (tops
+// of earlier chains) and reads their contribution vectors from memory; every
+// later front has the front before it as its only child in the tree part,
+// whose contribution vector is still in shared memory, so it takes it from
+// there through the relative indices, with no wait. Everything else a front
+// reads (its own right-hand-side entries, its panel or pivot block, its
+// children's relative indices and the contribution vectors of its children
+// below the tree part) was written before the launch, so warps 1-3 copy the
+// next front's share by cp.async while warp 0 solves with the current pivot
+// block; descriptors come two fronts ahead, children's descriptors one ahead.
+// Children are added in their stored order, one after another, and the L21
+// update sums in pivot order: the results equal a front-by-front substitution
+// bit for bit. Only the chain's top writes its contribution vector and
+// signals completion.
+template <typename T>
+__global__ void __launch_bounds__(128) tree_fwd_kernel(DevSched s, TreeSched ts, DevNum<T> nm0, int B, int* ctr,
+                                                       long long limit)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ TreeFront dd[3];
+    __shared__ TreeKid kb[2][kTreeMaxKids];
+    __shared__ int cut[2][kTreeMaxKids + 1];
+    __shared__ int staged[2];
+    __shared__ int s_t, s_ok;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int total = ts.nchains * B;
+    int* done = ctr + kCtrHead;
+    const int pw = ts.fwd_cstage ? ts.max_fw : ts.max_w * ts.max_w;    // panel F x w, or pivot block w x w
+    const int ks = ts.fwd_kstage;                               // children's entries staged per front
+    const int stage_len = ts.max_w + pw + ks;
+    T* vb = reinterpret_cast<T*>(smraw);                        // v of the current and of the previous front
+    T* stg = vb + 2 * ts.max_F;                                 // two staging buffers: y, P, children's values
+    int* spos = reinterpret_cast<int*>(stg + 2 * stage_len);    // two buffers of children's relative indices
+    // copies of front d's static share into buffer sb by threads t0 .. t0 +
+    // nthr - 1 (whole warps); its children's descriptors are in kb[sb]
+    auto stage = [&](int sb, const TreeFront& d, const DevNum<T>& nm, int t0, int nthr) {
+        const int me = tid - t0, wi = me >> 5, nw = nthr >> 5;
+        T* y = stg + sb * stage_len;
+        T* P = y + ts.max_w;
+        T* sv = P + pw;
+        int* sp = spos + sb * ks;
+        const int w = d.w, F = d.F, nk = d.kid_end - d.kid_begin;
+        const T* pan = nm.panel + d.panel_off;
+        for (int a = me; a < w; a += nthr) cp_word(y + a, nm.vec + d.first + a, (int)sizeof(T));
+        if (ts.fwd_cstage) {
+            for (int c = wi; c < w; c += nw)
+                for (int a = lane; a < F; a += 32) cp_word(P + a + c * F, pan + a + (int64_t)c * F, (int)sizeof(T));
+        } else {
+            for (int c = wi; c < w; c += nw)
+                for (int a = lane; a < w; a += 32) cp_word(P + a + c * w, pan + a + (int64_t)c * F, (int)sizeof(T));
+        }
+        if (wi == 0) {                                           // offsets: prefix sums of the children's orders
+            int run = 0;
+            for (int c0 = 0; c0 < nk; c0 += 32) {
+                const int c = c0 + lane;
+                int x = c < nk ? kb[sb][c].mc : 0;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int up = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= o) x += up;
+                }
+                if (c < nk) cut[sb][c + 1] = run + x;
+                run += __shfl_sync(0xffffffffu, x, 31);
+            }
+            if (lane == 0) {
+                cut[sb][0] = 0;
+                staged[sb] = run <= ks ? 1 : 0;
+            }
+        }
+        bar_sync_staging(nthr);
+        if (staged[sb])
+            for (int c = 0; c < nk; ++c) {
+                const TreeKid& k = kb[sb][c];
+                const int off = cut[sb][c];
+                const int* rl = s.rel + k.rel_ptr;
+                for (int tt = me; tt < k.mc; tt += nthr) {
+                    cp_word(sp + off + tt, rl + tt, 4);
+                    if (k.q < 0) cp_word(sv + off + tt, nm.cbv + k.rel_ptr + tt, (int)sizeof(T));
+                }
+            }
+    };
+    auto fetch_desc = [&](int slot, int q_) {
+        constexpr int kWords = (int)(sizeof(TreeFront) / 4);
+        static_assert(sizeof(TreeFront) % 4 == 0, "descriptor words");
+        if (tid < kWords)
+            cp_word(reinterpret_cast<int*>(&dd[slot]) + tid, reinterpret_cast<const int*>(ts.fr + q_) + tid, 4);
+    };
+    auto fetch_kids = [&](int sb, const TreeFront& d) {
+        static_assert(sizeof(TreeKid) % 4 == 0, "descriptor words");
+        const int words = (d.kid_end - d.kid_begin) * (int)(sizeof(TreeKid) / 4);
+        const int* src = reinterpret_cast<const int*>(ts.kid + d.kid_begin);
+        for (int e = tid; e < words; e += 128) cp_word(reinterpret_cast<int*>(kb[sb]) + e, src + e, 4);
+    };
+    for (;;) {
+        const int t = next_ticket(ctr + 2, ctr + 1, total, &s_t);
+        if (t >= total) break;
+        const int cr = t / B, b = t - cr * B;
+        const int ci = ts.nchains - 1 - cr;                     // ascending top front
+        const int k0 = ts.bwd_chain_ptr[ci], k1 = ts.bwd_chain_ptr[ci + 1];
+        const int len = k1 - k0;                                // position j: front bwd_chain[k1 - 1 - j]
+        const DevNum<T> nm = nm0.at(b);
+        fetch_desc(0, ts.bwd_chain[k1 - 1]);
+        if (len > 1) fetch_desc(1, ts.bwd_chain[k1 - 2]);
+        cp_wait_all();
+        __syncthreads();
+        fetch_kids(0, dd[0]);
+        cp_wait_all();
+        __syncthreads();
+        stage(0, dd[0], nm, 0, 128);
+        bool stop = false;
+        int wprev = 0;
+        // the bottom front waits for its children in the tree part while its
+        // share is in flight
+        if (tid < 32) {
+            const int ok = warp_wait_kids(done + (int64_t)b * ts.nq, kb[0], dd[0].kid_end - dd[0].kid_begin, true,
+                                          ctr + 1, limit);
+            if (tid == 0) s_ok = ok;
+        }
+        for (int j = 0; j < len; ++j) {
+            const int sb = j & 1, ds = j % 3;
+            cp_wait_all();                                       // this front's share and descriptors
+            __syncthreads();
+            if (j == 0 && !s_ok) {
+                if (tid == 0) atomicExch(&nm.stat->timeout, 1);
+                stop = true;
+                break;
+            }
+            const int w = dd[ds].w, F = dd[ds].F, first = dd[ds].first, nk = dd[ds].kid_end - dd[ds].kid_begin;
+            if (j + 2 < len) fetch_desc((ds + 2) % 3, ts.bwd_chain[k1 - 3 - j]);
+            if (j + 1 < len) fetch_kids(sb ^ 1, dd[(ds + 1) % 3]);
+            T* v = vb + sb * ts.max_F;
+            const T* pv = vb + (sb ^ 1) * ts.max_F;              // the previous front of the chain
+            const T* y = stg + sb * stage_len;
+            const T* P = y + ts.max_w;
+            const T* sv = P + pw;
+            const int* sp = spos + sb * ks;
+            const bool st_ok = staged[sb] != 0;
+            for (int a = tid; a < F; a += 128) v[a] = a < w ? y[a] : T(0);
+            __syncthreads();
+            for (int c = 0; c < nk; ++c) {
+                const TreeKid& k = kb[sb][c];
+                const int mc = k.mc;
+                const int* rl = st_ok ? sp + cut[sb][c] : s.rel + k.rel_ptr;
+                if (k.q < 0) {
+                    if (st_ok)
+                        for (int tt = tid; tt < mc; tt += 128) v[rl[tt]] += sv[cut[sb][c] + tt];
+                    else
+                        for (int tt = tid; tt < mc; tt += 128) v[rl[tt]] += __ldcg(nm.cbv + k.rel_ptr + tt);
+                } else if (j > 0) {
+                    for (int tt = tid; tt < mc; tt += 128) v[rl[tt]] += pv[wprev + tt];
+                } else {
+                    for (int tt = tid; tt < mc; tt += 128) v[rl[tt]] += __ldcg(nm.cbv + k.rel_ptr + tt);
+                }
+                __syncthreads();
+            }
+            cp_wait_all();                                       // the next front's children's descriptors
+            __syncthreads();
+            // warps 1-3 stage the next front while warp 0 solves this one
+            if (j + 1 < len && tid >= 32) stage(sb ^ 1, dd[(ds + 1) % 3], nm, 32, 96);
+            if (tid < 32) {
+                const int ldp = ts.fwd_cstage ? F : w;
+                if (w <= 32)
+                    warp_lower_solve(v, P, ldp, w);
+                else
+                    for (int p = 0; p < w; ++p) {
+                        const T xp = v[p];
+                        for (int i = p + 1 + lane; i < w; i += 32) v[i] -= P[i + p * ldp] * xp;
+                        __syncwarp();
+                    }
+            }
+            __syncthreads();
+            const T* pan = nm.panel + dd[ds].panel_off;
+            for (int i = w + tid; i < F; i += 128) {
+                T acc = v[i];
+                if (ts.fwd_cstage)
+                    for (int p = 0; p < w; ++p) acc -= P[i + p * F] * v[p];
+                else
+                    for (int p = 0; p < w; ++p) acc -= pan[i + (int64_t)p * F] * v[p];
+                v[i] = acc;
+            }
+            __syncthreads();
+            for (int a = tid; a < w; a += 128) nm.vec[first + a] = v[a];
+            if (j == len - 1) {
+                T* cvo = nm.cbv + dd[ds].rel_ptr;
+                for (int tt = tid; tt < F - w; tt += 128) cvo[tt] = v[w + tt];
+            }
+            wprev = w;
+        }
+        if (stop) {
+            cp_wait_all();                                       // no copy left in flight
+            break;
+        }
+        signal_done(done + (int64_t)b * ts.nq + ts.bwd_chain[k0]);
+        __syncthreads();
+    }
 }
 
 // Chain c of instance b (TreeSched::bwd_chain), tickets in chain order

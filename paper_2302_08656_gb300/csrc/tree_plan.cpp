@@ -140,6 +140,19 @@ void build_tree(const Analysis& an, int min_fronts, size_t es, TreePlan& tp)
     ts.max_kids = std::max(ts.max_kids, 1);
     ts.fwd_stage = (size_t)ts.max_fw * es <= kStageLimit ? 1 : 0;
     ts.bwd_stage = 2 * (size_t)ts.max_wm * es <= kStageLimit ? 1 : 0;   // two fronts staged at a time
+    // forward chains: the children's entries of the largest front's children
+    // fit one stage; the two panels are staged if two CTAs per SM still fit
+    {
+        int most = 1;
+        for (const TreeFront& d : tp.fr) {
+            int sum = 0;
+            for (int c = d.kid_begin; c < d.kid_end; ++c) sum += tp.kid[c].mc;
+            most = std::max(most, sum);
+        }
+        ts.fwd_kstage = std::min(most, kTreeStage);
+        ts.fwd_cstage = 1;
+        if (tree_fwd_smem(ts, es) > kFwdPanelSmem) ts.fwd_cstage = 0;
+    }
     ts.kid_off = tree_kid_offset(ts, es);
     tp.fac_smem = tree_factor_smem(ts, es);
     tp.fwd_smem = tree_fwd_smem(ts, es);
@@ -173,7 +186,11 @@ size_t tree_factor_smem(const TreeSched& t, size_t es)
 
 size_t tree_fwd_smem(const TreeSched& t, size_t es)
 {
-    return fwd_arrays(t, es);
+    // v of the current and of the previous front of a chain (max_F each), two
+    // staging buffers (own right-hand-side entries, panel or pivot block, the
+    // children's values), two buffers of the children's relative indices
+    const size_t stage = (size_t)t.max_w + (t.fwd_cstage ? (size_t)t.max_fw : (size_t)t.max_w * t.max_w) + t.fwd_kstage;
+    return es * (2 * (size_t)t.max_F + 2 * stage) + 4 * 2 * (size_t)t.fwd_kstage;
 }
 
 size_t tree_bwd_smem(const TreeSched& t, size_t es)

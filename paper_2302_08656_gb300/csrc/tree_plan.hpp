@@ -11,6 +11,7 @@ namespace kktgb {
 
 constexpr size_t kTreeSmemLimit = 220 * 1024;   // dynamic shared memory of one CTA
 constexpr size_t kStageLimit = 96 * 1024;       // largest staged panel / U12 block
+constexpr size_t kFwdPanelSmem = 110 * 1024;    // forward chains stage panels only below this (two CTAs per SM)
 
 // Fronts of the levels from `split` up, in level-major order (tree index q),
 // their children, factorization units and gather maps; shared-memory sizes

@@ -148,6 +148,16 @@ def test_tree_plan_orders_every_dependency_first(dump_tool, tmp_path, buses, max
         if fr[top, 1] >= 0:
             assert chain_of[fr[top, 1]] < ci
             assert chain[cptr[chain_of[fr[top, 1]] + 1] - 1] == fr[top, 1]     # the parent ends its chain
+    # the forward substitution runs the chains in reverse (bottom front first,
+    # chains from the last to the first): a bottom front's children in the
+    # tree part are tops of chains with larger indices (earlier forward
+    # tickets), and the only child of every later front is the front before it
+    for ci in range(len(cptr) - 1):
+        members = chain[cptr[ci]:cptr[ci + 1]]
+        for c in tree_kids[members[-1]]:
+            assert chain_of[c] > ci and chain[cptr[chain_of[c]]] == c
+        for lower, upper in zip(members[::-1][:-1], members[::-1][1:]):
+            assert tree_kids[upper] == [lower]
 
 
 @pytest.mark.parametrize("buses,max_pivots,min_fronts", [(2000, 16, 2432), (500, 8, 100000)])
