@@ -981,6 +981,37 @@ __global__ void solve_post_kernel(int n, const int* __restrict__ perm, DevNum<T>
     }
 }
 
+// Back substitution with the upper pivot block U (column-major, leading
+// dimension w <= G, in shared memory) by a group of G lanes (gmask, lane gl
+// of the group holding v_gl in a register, the pivot entry broadcast by a
+// shuffle); the operations and their order are those of the shared-memory
+// loop x_p = v_p * (1 / u_pp), v_a -= u_ap x_p (the bits are the same). FP64
+// costs pipe time per active lane, so the reciprocals are formed by all lanes
+// at once before the dependent chain, and on the chain each step is one
+// lane's multiply and the FMAs of the lanes above the pivot (instead of a
+// reciprocal and a multiply on every lane per step: 0.184 -> 0.165 ms of
+// solve_bwd_kernel per 70k FP64 solve). A register version of the forward
+// block was slower on the wide levels (more instructions per front) and is
+// not used there.
+template <typename T, int G>
+__device__ __forceinline__ void group_pivot_upper(T* v, const T* U, int w, unsigned gmask, int gl)
+{
+    T x = gl < w ? v[gl] : T(0);
+    const T r = gl < w ? pivot_rcp(U[gl + gl * w]) : T(0);
+    T ua[G];
+#pragma unroll
+    for (int p = 0; p < G; ++p) ua[p] = (p < w && gl < w) ? U[gl + p * w] : T(0);
+#pragma unroll
+    for (int p = G - 1; p >= 0; --p) {
+        if (p >= w) continue;
+        if (gl == p) x *= r;                                       // x_p = v_p * (1 / u_pp)
+        const T xp = __shfl_sync(gmask, x, p, G);
+        if (gl < p) x -= ua[p] * xp;
+    }
+    if (gl < w) v[gl] = x;
+    __syncwarp(gmask);
+}
+
 // Forward substitution y = L^{-1} c, multifrontally: one warp per front
 // gathers its pivot entries and its children's contribution vectors, solves
 // with its unit lower pivot block (staged in shared memory), then updates its
@@ -1064,13 +1095,16 @@ __global__ void __launch_bounds__(128) solve_bwd_kernel(DevSched s, DevNum<T> nm
         v[a] = acc;
     }
     __syncwarp();
-    for (int p = w - 1; p >= 0; --p) {
-        const T xp = v[p] * pivot_rcp(Us[p + p * w]);        // x_p = v_p * (1 / u_pp), as every backward kernel
-        __syncwarp();
-        if (lane == 0) v[p] = xp;
-        for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
-        __syncwarp();
-    }
+    if (w <= 32)
+        group_pivot_upper<T, 32>(v, Us, w, 0xffffffffu, lane);
+    else
+        for (int p = w - 1; p >= 0; --p) {
+            const T xp = v[p] * pivot_rcp(Us[p + p * w]);    // x_p = v_p * (1 / u_pp), as every backward kernel
+            __syncwarp();
+            if (lane == 0) v[p] = xp;
+            for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
+            __syncwarp();
+        }
     for (int a = lane; a < w; a += 32) nm.vec[first + a] = v[a];
 }
 
@@ -1112,13 +1146,7 @@ __global__ void __launch_bounds__(128) solve_bwd_leaf_kernel(DevSched s, DevNum<
         v[a] = acc;
     }
     __syncwarp(gmask);
-    for (int p = w - 1; p >= 0; --p) {
-        const T xp = v[p] * pivot_rcp(Us[p + p * w]);            // x_p = v_p * (1 / u_pp), as every backward kernel
-        __syncwarp(gmask);
-        if (gl == 0) v[p] = xp;
-        for (int a = gl; a < p; a += G) v[a] -= Us[a + p * w] * xp;
-        __syncwarp(gmask);
-    }
+    group_pivot_upper<T, G>(v, Us, w, gmask, gl);                  // w <= F <= G
     for (int a = gl; a < w; a += G) nm.vec[first + a] = v[a];
 }
 
@@ -1218,13 +1246,16 @@ __global__ void __launch_bounds__(128) solve_bwd_cta_kernel(DevSched s, DevNum<T
     }
     __syncthreads();
     if (tid < 32) {
-        for (int p = w - 1; p >= 0; --p) {
-            const T xp = v[p] * pivot_rcp(Us[p + p * w]);    // x_p = v_p * (1 / u_pp), as every backward kernel
-            __syncwarp();
-            if (lane == 0) v[p] = xp;
-            for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
-            __syncwarp();
-        }
+        if (w <= 32)
+            group_pivot_upper<T, 32>(v, Us, w, 0xffffffffu, lane);
+        else
+            for (int p = w - 1; p >= 0; --p) {
+                const T xp = v[p] * pivot_rcp(Us[p + p * w]);    // x_p = v_p * (1 / u_pp), as every backward kernel
+                __syncwarp();
+                if (lane == 0) v[p] = xp;
+                for (int a = lane; a < p; a += 32) v[a] -= Us[a + p * w] * xp;
+                __syncwarp();
+            }
     }
     __syncthreads();
     for (int a = tid; a < w; a += 128) nm.vec[first + a] = v[a];

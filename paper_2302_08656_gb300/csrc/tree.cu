@@ -585,7 +585,7 @@ __device__ __forceinline__ void warp_lower_solve(T* v, const T* L, int ld, int w
     for (int p = 0; p < 32; ++p) {
         if (p >= w) break;
         const T xp = __shfl_sync(0xffffffffu, x, p);
-        if (lane > p) x -= li[p] * xp;
+        if (lane > p && lane < w) x -= li[p] * xp;              // FP64 costs pipe time per active lane
     }
     if (lane < w) v[lane] = x;
     __syncwarp();
@@ -605,9 +605,9 @@ __device__ __forceinline__ void warp_upper_solve(T* v, const T* U, const T* rcp,
 #pragma unroll
     for (int p = 31; p >= 0; --p) {
         if (p >= w) continue;
-        const T xp = __shfl_sync(0xffffffffu, x * r, p);
-        if (lane == p) x = xp;
-        else if (lane < p) x -= ua[p] * xp;
+        if (lane == p) x *= r;                                   // one lane's multiply, not the warp's
+        const T xp = __shfl_sync(0xffffffffu, x, p);
+        if (lane < p) x -= ua[p] * xp;
     }
     if (lane < w) v[lane] = x;
     __syncwarp();
