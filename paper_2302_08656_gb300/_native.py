@@ -17,8 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libkkt_gb300.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["analysis.cpp", "tree_plan.cpp", "kernels.cu", "kkt_capi.cu", "noalloc.cu", "tree.cu", "model.cu", "jacobi.cu",
-           "ipm.cu", "hykkt.cu"]
-HEADERS = ["analysis.hpp", "kernels.cuh", "tree_plan.hpp", "model.hpp"]
+           "ipm.cu", "hykkt.cu", "hykkt_plan.cpp"]
+HEADERS = ["analysis.hpp", "kernels.cuh", "tree_plan.hpp", "model.hpp", "hykkt_plan.hpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

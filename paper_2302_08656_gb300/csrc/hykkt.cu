@@ -14,6 +14,7 @@
 // then recover y_E and y_I. Every step runs in kernels on the caller's stream; the host reads the
 // conjugate-gradient residual after every iteration to stop.
 #include "../../include/kkt.h"
+#include "hykkt_plan.hpp"
 
 #include <cuda_runtime.h>
 
@@ -29,20 +30,16 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kBlocks = 304;          // 2 x 152 SMs, grid-stride loops; also the partial sums of a dot product
 
-// one step of an H_g entry: kind -1: K value a; -2: gamma K_a K_b (a J_E pair);
-// k >= 0: K_a K_b / d_I[k] (a J_I pair of inequality row k)
-struct Contrib {
-    int a, b, k;
-};
+using kktgb::HgTerm;
 
-__global__ void hg_assemble_kernel(int64_t nnz_g, const int64_t* __restrict__ cptr, const Contrib* __restrict__ cl,
+__global__ void hg_assemble_kernel(int64_t nnz_g, const int64_t* __restrict__ cptr, const HgTerm* __restrict__ cl,
                                    const double* __restrict__ vals, const double* __restrict__ dinv, double gamma,
                                    double* __restrict__ hg)
 {
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz_g; e += (int64_t)gridDim.x * blockDim.x) {
         double acc = 0.0;
         for (int64_t c = cptr[e]; c < cptr[e + 1]; ++c) {
-            const Contrib t = cl[c];
+            const HgTerm t = cl[c];
             if (t.k == -1) acc += vals[t.a];
             else if (t.k == -2) acc += gamma * (vals[t.a] * vals[t.b]);
             else acc += (vals[t.a] * vals[t.b]) * dinv[t.k];
@@ -288,7 +285,7 @@ struct kkt_hykkt {
     int *je_p = nullptr, *je_c = nullptr, *je_v = nullptr, *ji_p = nullptr, *ji_c = nullptr, *ji_v = nullptr;
     int *jet_p = nullptr, *jet_c = nullptr, *jet_v = nullptr, *jit_p = nullptr, *jit_c = nullptr, *jit_v = nullptr;
     int64_t* cptr = nullptr;
-    Contrib* cl = nullptr;
+    HgTerm* cl = nullptr;
     double* hg = nullptr;
     // vectors and scalars
     double *dE = nullptr, *C = nullptr, *sq = nullptr, *dinv = nullptr;
@@ -311,88 +308,13 @@ kkt_status kkt_hykkt_analyze(int32_t n, int32_t n_primal, int32_t m_eq, const in
     *out = nullptr;
     const int np = n_primal, mE = m_eq, mI = n - n_primal - m_eq;
     const int64_t nnz = h_rowptr[n];
-    // blocks: H (rows < np, cols < np), J_E / J_I (dual rows, cols < np),
-    // the (2,2) block must be exactly its diagonal
-    std::vector<int> dpos(mE + mI, -1);
-    std::vector<int> je_p(1, 0), je_c, je_v, ji_p(1, 0), ji_c, ji_v;
-    for (int i = np; i < n; ++i) {
-        const bool eq = i < np + mE;
-        for (int64_t k = h_rowptr[i]; k < h_rowptr[i + 1]; ++k) {
-            const int j = h_colidx[k];
-            if (j < 0 || j >= n) return KKT_E_STRUCT;
-            if (j < np) {
-                (eq ? je_c : ji_c).push_back(j);
-                (eq ? je_v : ji_v).push_back((int)k);
-            } else if (j == i) {
-                dpos[i - np] = (int)k;
-            } else {
-                return KKT_E_STRUCT;                              // (2,2) block not diagonal
-            }
-        }
-        (eq ? je_p : ji_p).push_back((int)(eq ? je_c.size() : ji_c.size()));
-    }
-    for (int k = 0; k < mE + mI; ++k)
-        if (dpos[k] < 0) return KKT_E_STRUCT;                     // the dual diagonal must be stored
-    // transposes (CSR over the primal rows)
-    auto transpose = [&](const std::vector<int>& p, const std::vector<int>& c, const std::vector<int>& v, int m,
-                         std::vector<int>& tp, std::vector<int>& tc, std::vector<int>& tv) {
-        tp.assign(np + 1, 0);
-        for (int j : c) ++tp[j + 1];
-        for (int i = 0; i < np; ++i) tp[i + 1] += tp[i];
-        tc.resize(c.size());
-        tv.resize(c.size());
-        std::vector<int> fill(tp.begin(), tp.end() - 1);
-        for (int r = 0; r < m; ++r)
-            for (int k = p[r]; k < p[r + 1]; ++k) {
-                tc[fill[c[k]]] = r;
-                tv[fill[c[k]]++] = v[k];
-            }
-    };
-    std::vector<int> jet_p, jet_c, jet_v, jit_p, jit_c, jit_v;
-    transpose(je_p, je_c, je_v, mE, jet_p, jet_c, jet_v);
-    transpose(ji_p, ji_c, ji_v, mI, jit_p, jit_c, jit_v);
-    // H_g = H + J_I^T D_I^{-1} J_I + gamma J_E^T J_E: pattern and, per entry,
-    // its contributions in a fixed order (the H entry, J_I pairs by inequality
-    // row, J_E pairs by equality row)
-    std::vector<int> hg_p(1, 0), hg_c;
-    std::vector<int64_t> cptr(1, 0);
-    std::vector<Contrib> cl;
-    std::vector<int> slot(np, -1);
-    std::vector<std::vector<Contrib>> acc;
-    std::vector<int> cols;
-    for (int i = 0; i < np; ++i) {
-        cols.clear();
-        acc.clear();
-        auto at = [&](int j) -> std::vector<Contrib>& {
-            if (slot[j] < 0) {
-                slot[j] = (int)cols.size();
-                cols.push_back(j);
-                acc.emplace_back();
-            }
-            return acc[slot[j]];
-        };
-        for (int64_t k = h_rowptr[i]; k < h_rowptr[i + 1]; ++k)
-            if (h_colidx[k] < np) at(h_colidx[k]).push_back(Contrib{(int)k, -1, -1});
-        at(i);                                                    // the diagonal always
-        for (int q = jit_p[i]; q < jit_p[i + 1]; ++q) {           // inequality rows holding column i
-            const int r = jit_c[q], a = jit_v[q];
-            for (int k = ji_p[r]; k < ji_p[r + 1]; ++k) at(ji_c[k]).push_back(Contrib{a, ji_v[k], r});
-        }
-        for (int q = jet_p[i]; q < jet_p[i + 1]; ++q) {           // equality rows holding column i
-            const int r = jet_c[q], a = jet_v[q];
-            for (int k = je_p[r]; k < je_p[r + 1]; ++k) at(je_c[k]).push_back(Contrib{a, je_v[k], -2});
-        }
-        std::vector<int> order(cols.size());
-        for (size_t k = 0; k < cols.size(); ++k) order[k] = (int)k;
-        std::sort(order.begin(), order.end(), [&](int x, int y) { return cols[x] < cols[y]; });
-        for (int k : order) {
-            hg_c.push_back(cols[k]);
-            cl.insert(cl.end(), acc[k].begin(), acc[k].end());
-            cptr.push_back((int64_t)cl.size());
-        }
-        hg_p.push_back((int)hg_c.size());
-        for (int j : cols) slot[j] = -1;
-    }
+    kktgb::HykktPlan pl;
+    if (kktgb::build_hykkt_plan(n, np, mE, h_rowptr, h_colidx, pl) != 0) return KKT_E_STRUCT;
+    const std::vector<int>&dpos = pl.dpos, &je_p = pl.je_p, &je_c = pl.je_c, &je_v = pl.je_v, &ji_p = pl.ji_p,
+                          &ji_c = pl.ji_c, &ji_v = pl.ji_v, &jet_p = pl.jet_p, &jet_c = pl.jet_c, &jet_v = pl.jet_v,
+                          &jit_p = pl.jit_p, &jit_c = pl.jit_c, &jit_v = pl.jit_v, &hg_p = pl.hg_p, &hg_c = pl.hg_c;
+    const std::vector<int64_t>& cptr = pl.term_ptr;
+    const std::vector<HgTerm>& cl = pl.term;
     kkt_hykkt* h = new (std::nothrow) kkt_hykkt();
     if (!h) return KKT_E_NOMEM;
     h->n = n; h->np = np; h->mE = mE; h->mI = mI; h->nnz = nnz; h->nnz_g = (int64_t)hg_c.size(); h->gamma = gamma;
@@ -410,7 +332,7 @@ kkt_status kkt_hykkt_analyze(int32_t n, int32_t n_primal, int32_t m_eq, const in
     h->ji_p = dev_alloc<int>(ji_p.size(), e); h->ji_c = dev_alloc<int>(ji_c.size(), e); h->ji_v = dev_alloc<int>(ji_v.size(), e);
     h->jet_p = dev_alloc<int>(jet_p.size(), e); h->jet_c = dev_alloc<int>(jet_c.size(), e); h->jet_v = dev_alloc<int>(jet_v.size(), e);
     h->jit_p = dev_alloc<int>(jit_p.size(), e); h->jit_c = dev_alloc<int>(jit_c.size(), e); h->jit_v = dev_alloc<int>(jit_v.size(), e);
-    h->cptr = dev_alloc<int64_t>(cptr.size(), e); h->cl = dev_alloc<Contrib>(cl.size(), e);
+    h->cptr = dev_alloc<int64_t>(cptr.size(), e); h->cl = dev_alloc<HgTerm>(cl.size(), e);
     h->hg = dev_alloc<double>(hg_c.size(), e);
     h->dE = dev_alloc<double>(mE, e); h->C = dev_alloc<double>(mE, e); h->sq = dev_alloc<double>(mE, e);
     h->dinv = dev_alloc<double>(std::max(mI, 1), e);
