@@ -200,6 +200,50 @@ def jacobi_precondition(f: Factors, d, b, sweeps: int):
     return np.asarray(d) * z
 
 
+def _block_parts(f: Factors, block_of):
+    """(L_D, L_O, U_D, U_O) of block_jacobi_precondition, CSR in pivot order."""
+    import scipy.sparse as sp
+    n = f.n
+    blk = np.asarray(block_of)[f.q]
+    Ls = sp.csc_matrix((f.Lx, f.Li, f.Lp), shape=(n, n)).tocoo()      # L - I
+    U = sp.csc_matrix((f.Ux, f.Ui, f.Up), shape=(n, n)).tocoo()
+    same_l = blk[Ls.row] == blk[Ls.col]
+    same_u = blk[U.row] == blk[U.col]
+    LD = (sp.eye(n, format="csr") + sp.csr_matrix((Ls.data[same_l], (Ls.row[same_l], Ls.col[same_l])),
+                                                   shape=(n, n))).tocsr()
+    LO = sp.csr_matrix((Ls.data[~same_l], (Ls.row[~same_l], Ls.col[~same_l])), shape=(n, n))
+    UD = sp.csr_matrix((U.data[same_u], (U.row[same_u], U.col[same_u])), shape=(n, n))
+    UO = sp.csr_matrix((U.data[~same_u], (U.row[~same_u], U.col[~same_u])), shape=(n, n))
+    return LD, LO, UD, UO
+
+
+def block_jacobi_precondition(f: Factors, d, b, sweeps: int, block_of):
+    """Approximate solve of K x = b by block-Jacobi sweeps with the factors,
+    Gauss-Seidel (an exact substitution) within each block: the iterative
+    triangular solves of Sec. V with the pivots grouped in blocks. With L_D,
+    U_D the parts of L and U whose row and column lie in one block and L_O =
+    L - L_D, U_O = U - U_D, written as the plain definition:
+        c = P D b;   y_0 = 0,  y_{s+1} = L_D^{-1} (c - L_O y_s);
+        x_0 = 0,  x_{s+1} = U_D^{-1} (y - U_O x_s);
+        result = D Q x.
+    block_of: the block of every unknown, in the original numbering (pivot
+    position i belongs to the block of unknown q[i]). Singleton blocks give
+    the point-Jacobi sweeps above; one block gives the exact solve."""
+    import scipy.sparse.linalg as spla
+    n = f.n
+    LD, LO, UD, UO = _block_parts(f, block_of)
+    c = (np.asarray(d) * np.asarray(b))[f.p]
+    y = np.zeros(n)
+    for _ in range(sweeps):
+        y = spla.spsolve_triangular(LD, c - LO @ y, lower=True, unit_diagonal=True)
+    x = np.zeros(n)
+    for _ in range(sweeps):
+        x = spla.spsolve_triangular(UD, y - UO @ x, lower=False)
+    z = np.empty(n)
+    z[f.q] = x
+    return np.asarray(d) * z
+
+
 def spmv_resid(rowptr, colidx, vals, x, b):
     rp, ci, v = _csr(rowptr, colidx, vals)
     r = np.empty(rp.size - 1)

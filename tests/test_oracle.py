@@ -514,3 +514,74 @@ def test_slack_terms_determine_x_and_the_fp32_threshold_needs_refinement(kkt200,
     assert ita == 0 and oma <= 1e-10 and diff(xa, x0) > 0.1
     xb, itb, omb = solve(eps=1e-7, tol=1e-15)
     assert itb > 0 and omb <= 1e-15 and diff(xb, x0) < 1e-2
+
+
+def test_block_jacobi_precondition_pins():
+    """Block-Jacobi sweeps with an exact substitution inside each block (the
+    Gauss-Seidel end of Sec. V's iterative triangular solves): singleton
+    blocks reproduce the point-Jacobi sweeps; one block is the exact solve
+    after one sweep; with blocks of consecutive pivots, as many sweeps as the
+    longest chain of blocks in the factors' dependencies give the exact solve,
+    and fewer sweeps are closer to it than as many point sweeps; a mistake
+    that keeps U's in-block entries in U_O as well (the diagonal counted
+    twice) breaks the singleton pin."""
+    import scipy.sparse as sp
+    pat = KKTPattern(make_grid(3, 30, 40, 6))
+    v = pat.values(pat.point(3, 0, 1e-1, delta_w=1.0, delta_c=1.0))
+    an = O.analyze(pat.rowptr, pat.colidx, v)
+    lu, d, _ = O.refactor(pat.rowptr, pat.colidx, v, an)
+    f = lu.factors()
+    b = pat.rhs(3, 0)
+    n = pat.n
+    exact = lu.solve_scaled(d, b)
+    nrm = np.linalg.norm(exact)
+    single = np.arange(n)
+    for s in (1, 3):
+        assert np.allclose(O.block_jacobi_precondition(f, d, b, s, single), O.jacobi_precondition(f, d, b, s),
+                           rtol=1e-13, atol=1e-13 * np.abs(exact).max())
+    one = O.block_jacobi_precondition(f, d, b, 1, np.zeros(n, dtype=np.int64))
+    assert np.linalg.norm(one - exact) <= 1e-10 * nrm
+    # blocks of 4 consecutive pivots (in the factors' order), numbered by unknown
+    bpos = np.arange(n) // 4
+    block_of = np.empty(n, dtype=np.int64)
+    block_of[f.q] = bpos
+    # longest chain of blocks: block a depends on block c if a nonzero of L (U) couples them
+    L = sp.csc_matrix((f.Lx, f.Li, f.Lp), shape=(n, n)).tocoo()
+    dep = {(int(bpos[r]), int(bpos[c])) for r, c, x in zip(L.row, L.col, L.data) if bpos[r] != bpos[c] and x != 0}
+    nb = int(bpos.max()) + 1
+    depth = np.ones(nb, dtype=np.int64)
+    for a in range(nb):                                      # dependencies point to lower blocks
+        for (x, y) in dep:
+            if x == a:
+                depth[a] = max(depth[a], depth[y] + 1)
+    U = sp.csc_matrix((f.Ux, f.Ui, f.Up), shape=(n, n)).tocoo()
+    depu = {(int(bpos[r]), int(bpos[c])) for r, c, x in zip(U.row, U.col, U.data) if bpos[r] != bpos[c] and x != 0}
+    du = np.ones(nb, dtype=np.int64)
+    for a in range(nb - 1, -1, -1):                          # upper: dependencies point to higher blocks
+        for (x, y) in depu:
+            if x == a:
+                du[a] = max(du[a], du[y] + 1)
+    s_full = int(max(depth.max(), du.max()))
+    full = O.block_jacobi_precondition(f, d, b, s_full, block_of)
+    assert np.linalg.norm(full - exact) <= 1e-10 * nrm
+    # fewer sweeps: larger blocks absorb dependency chains, so the block sweeps
+    # are closer to the exact solve than as many point sweeps
+    for s in (2, 3):
+        eb = np.linalg.norm(O.block_jacobi_precondition(f, d, b, s, block_of) - exact)
+        ep = np.linalg.norm(O.jacobi_precondition(f, d, b, s) - exact)
+        print("sweeps %d: block %.2e point %.2e (of %.2e)" % (s, eb, ep, nrm))
+        assert eb < ep and ep > 1e-6 * nrm
+    # the planted mistake, in the oracle: U's in-block entries also kept in U_O
+    real = O._block_parts
+
+    def wrong(f_, block_of_):
+        LD, LO, UD, UO = real(f_, block_of_)
+        return LD, LO, UD, (UO + UD).tocsr()
+    good = O.block_jacobi_precondition(f, d, b, 2, single)
+    O._block_parts = wrong
+    try:
+        bad = O.block_jacobi_precondition(f, d, b, 2, single)
+    finally:
+        O._block_parts = real
+    assert np.allclose(good, O.jacobi_precondition(f, d, b, 2), rtol=1e-13, atol=1e-13 * np.abs(exact).max())
+    assert not np.allclose(bad, O.jacobi_precondition(f, d, b, 2), rtol=1e-6)
