@@ -68,8 +68,9 @@ def parse(argv=None):
     ap.add_argument("--ipm-loop", action="store_true",
                     help="each step is a whole interior-point solve (kkt_ipm_solve) of the workload's grid with "
                          "seeded loads and limits, from the flat start")
-    ap.add_argument("--precond", default="lu", choices=["lu", "jacobi"],
-                    help="refinement preconditioner: exact triangular solves or Jacobi sweeps")
+    ap.add_argument("--precond", default="lu", choices=["lu", "jacobi", "block"],
+                    help="refinement preconditioner: exact triangular solves, Jacobi sweeps, or block-Jacobi sweeps "
+                         "(each front's pivots solved exactly inside the sweep)")
     ap.add_argument("--sweeps", type=int, default=4, help="Jacobi sweeps per triangular factor")
     ap.add_argument("--slack-range", type=float, nargs=2, default=None, metavar=("LO", "HI"),
                     help="keep the inequality slacks' term -(1/sigma_s), 1/sigma_s log-uniform on [LO, HI], "

@@ -62,7 +62,9 @@ enum { KKT_FP64 = 0,      /* factors and triangular solves in FP64 */
                              scaling, residual and FGMRES stay FP64 */
 
 enum { KKT_PRECOND_LU = 0,       /* refinement preconditioned by the exact triangular solves */
-       KKT_PRECOND_JACOBI = 1 };  /* ... by Jacobi sweeps with the factors (approximate, Sec. V) */
+       KKT_PRECOND_JACOBI = 1,    /* ... by Jacobi sweeps with the factors (approximate, Sec. V) */
+       KKT_PRECOND_BLOCK_JACOBI = 2 };  /* ... by block-Jacobi sweeps, each front's pivots a block
+                                           solved exactly inside the sweep (Gauss-Seidel within it) */
 
 enum { KKT_ORDER_MINDEG = 0,  /* the library's quotient-graph minimum degree */
        KKT_ORDER_USER = 1,    /* kkt_options.user_perm */
@@ -99,8 +101,8 @@ typedef struct {
                                    KKT_E_TIMEOUT (default 1 << 23, about a second) */
     int precond;                /* KKT_PRECOND_* for kkt_refine and kkt_precondition
                                    (default KKT_PRECOND_LU) */
-    int jacobi_sweeps;          /* sweeps per triangular factor with KKT_PRECOND_JACOBI
-                                   (default 4, 1..1000000) */
+    int jacobi_sweeps;          /* sweeps per triangular factor with KKT_PRECOND_JACOBI or
+                                   KKT_PRECOND_BLOCK_JACOBI (default 4, 1..1000000) */
 } kkt_options;
 
 typedef struct {

@@ -65,7 +65,7 @@ def _opts(precision="fp64", ordering="mindeg", user_perm=None, static_pivot_eps=
         o.tree_min_fronts = int(tree_min_fronts)
     if spin_limit is not None:
         o.spin_limit = int(spin_limit)
-    o.precond = {"lu": 0, "jacobi": 1}[precond] if isinstance(precond, str) else int(precond)
+    o.precond = {"lu": 0, "jacobi": 1, "block": 2}[precond] if isinstance(precond, str) else int(precond)
     o.jacobi_sweeps = int(jacobi_sweeps)
     return o, keep
 
@@ -258,7 +258,7 @@ class KKTSolver:
         return out, (infos[0] if self.count == 1 else list(infos))
 
     def precondition(self, rhs, out=None, stream=None):
-        """z = M^{-1} rhs with the context's preconditioner (exact solves or Jacobi sweeps)."""
+        """z = M^{-1} rhs with the context's preconditioner (exact solves, Jacobi or block-Jacobi sweeps)."""
         import torch
         _check_tensor(rhs, self.n * self.count, "rhs")
         if out is None:

@@ -17,6 +17,10 @@
 // contribution row, stored at the front's contribution-vector offsets) and
 // jacobi_l_row gathers them per row in a fixed order (host-built row lists).
 // A row of U lies entirely in its own front (U11 row and U12 row).
+// The block variant (KKT_PRECOND_BLOCK_JACOBI) takes each front's pivots as
+// a block solved exactly inside the sweep (Gauss-Seidel within the block):
+//   y_{s+1} = L_D^{-1} (c - L_O y_s),   x_{s+1} = U_D^{-1} (y - U_O x_s)
+// with L_D, U_D the fronts' pivot blocks and L_O, U_O the rest.
 #include "kernels.cuh"
 
 namespace kktgb {
@@ -79,6 +83,68 @@ __global__ void __launch_bounds__(128) jacobi_u_kernel(DevSched s, DevNum<T> nm,
     }
 }
 
+// Block variant (Gauss-Seidel inside each front): the pivots of a front
+// form a block, solved exactly within the sweep from the other blocks'
+// previous values. L: y_new[f] = L11^{-1} (c_f - descendants' parts), the
+// unit lower pivot block substituted in pivot order; U: x_new[f] = U11^{-1}
+// (y_f - U12 x_old), substituted backward with x_p = v_p * (1 / u_pp). One
+// warp per front, the front's values in shared memory (w <= 64).
+template <typename T>
+__global__ void __launch_bounds__(128) jacobi_lb_kernel(DevSched s, DevNum<T> nm, const T* __restrict__ c,
+                                                        const T* __restrict__ t, const int* __restrict__ lptr,
+                                                        const int* __restrict__ lidx, T* __restrict__ ynew)
+{
+    __shared__ T vs[4][64];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int f = blockIdx.x * 4 + wid;
+    if (f >= s.ns) return;
+    const int first = s.sn_first[f], w = s.sn_first[f + 1] - first, F = s.sn_front[f];
+    const T* pan = nm.panel + s.panel_off[f];
+    T* v = vs[wid];
+    for (int a = lane; a < w; a += 32) {
+        const int i = first + a;
+        T acc = c[i];
+        for (int k = lptr[i]; k < lptr[i + 1]; ++k) acc -= t[lidx[k]];
+        v[a] = acc;
+    }
+    __syncwarp();
+    for (int p = 0; p < w; ++p) {
+        const T xp = v[p];
+        for (int a = p + 1 + lane; a < w; a += 32) v[a] -= pan[a + (int64_t)p * F] * xp;
+        __syncwarp();
+    }
+    for (int a = lane; a < w; a += 32) ynew[first + a] = v[a];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) jacobi_ub_kernel(DevSched s, DevNum<T> nm, const T* __restrict__ y,
+                                                        const T* __restrict__ x, T* __restrict__ xnew)
+{
+    __shared__ T vs[4][64];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int f = blockIdx.x * 4 + wid;
+    if (f >= s.ns) return;
+    const int first = s.sn_first[f], w = s.sn_first[f + 1] - first, F = s.sn_front[f], m = F - w;
+    const T* pan = nm.panel + s.panel_off[f];
+    const T* U12 = pan + (int64_t)F * w;
+    const int* R = s.rows + s.rows_ptr[f];
+    T* v = vs[wid];
+    for (int a = lane; a < w; a += 32) {
+        T acc = y[first + a];
+        for (int tt = 0; tt < m; ++tt) acc -= U12[a + (int64_t)tt * w] * x[R[w + tt]];
+        v[a] = acc;
+    }
+    __syncwarp();
+    for (int p = w - 1; p >= 0; --p) {
+        const T xp = v[p] * pivot_rcp(pan[p + (int64_t)p * F]);
+        __syncwarp();
+        if (lane == 0) v[p] = xp;
+        for (int a = lane; a < p; a += 32) v[a] -= pan[a + (int64_t)p * F] * xp;
+        __syncwarp();
+    }
+    for (int a = lane; a < w; a += 32) xnew[first + a] = v[a];
+}
+
 template <typename T>
 __global__ void zero_kernel(int n, T* __restrict__ a)
 {
@@ -93,8 +159,8 @@ __global__ void zero_kernel(int n, T* __restrict__ a)
 // the result is left in nm.vec. Work buffers: ya, yb, xa (n each), t (one
 // value per contribution row). Launches: 1 + 2 sweeps (L) + 1 + sweeps (U).
 template <typename T>
-cudaError_t launch_jacobi(const DevSched& s, const DevNum<T>& nm, int sweeps, const int* lptr, const int* lidx,
-                          T* ya, T* yb, T* xa, T* t, int* launches, cudaStream_t st)
+cudaError_t launch_jacobi(const DevSched& s, const DevNum<T>& nm, int sweeps, bool block, const int* lptr,
+                          const int* lidx, T* ya, T* yb, T* xa, T* t, int* launches, cudaStream_t st)
 {
     const int n = s.n, blocks = (s.ns + 3) / 4, zb = (n + 255) / 256;
     const T* c = nm.vec;
@@ -106,7 +172,10 @@ cudaError_t launch_jacobi(const DevSched& s, const DevNum<T>& nm, int sweeps, co
     T* yn = yb;
     for (int sw = 0; sw < sweeps; ++sw) {
         jacobi_l_part_kernel<T><<<blocks, 128, 0, st>>>(s, nm, yo, t);
-        jacobi_l_row_kernel<T><<<blocks, 128, 0, st>>>(s, nm, c, yo, t, lptr, lidx, yn);
+        if (block)
+            jacobi_lb_kernel<T><<<blocks, 128, 0, st>>>(s, nm, c, t, lptr, lidx, yn);
+        else
+            jacobi_l_row_kernel<T><<<blocks, 128, 0, st>>>(s, nm, c, yo, t, lptr, lidx, yn);
         k += 2;
         T* tmp = yo;
         yo = yn;
@@ -121,7 +190,10 @@ cudaError_t launch_jacobi(const DevSched& s, const DevNum<T>& nm, int sweeps, co
     const T* xo = A;
     for (int sw = 1; sw <= sweeps; ++sw) {
         T* dst = sw == sweeps ? nm.vec : ((sw % 2) ? Bf : A);
-        jacobi_u_kernel<T><<<blocks, 128, 0, st>>>(s, nm, yo, xo, dst);
+        if (block)
+            jacobi_ub_kernel<T><<<blocks, 128, 0, st>>>(s, nm, yo, xo, dst);
+        else
+            jacobi_u_kernel<T><<<blocks, 128, 0, st>>>(s, nm, yo, xo, dst);
         ++k;
         xo = dst;
     }
@@ -129,9 +201,9 @@ cudaError_t launch_jacobi(const DevSched& s, const DevNum<T>& nm, int sweeps, co
     return cudaGetLastError();
 }
 
-template cudaError_t launch_jacobi<double>(const DevSched&, const DevNum<double>&, int, const int*, const int*,
+template cudaError_t launch_jacobi<double>(const DevSched&, const DevNum<double>&, int, bool, const int*, const int*,
                                            double*, double*, double*, double*, int*, cudaStream_t);
-template cudaError_t launch_jacobi<float>(const DevSched&, const DevNum<float>&, int, const int*, const int*, float*,
-                                          float*, float*, float*, int*, cudaStream_t);
+template cudaError_t launch_jacobi<float>(const DevSched&, const DevNum<float>&, int, bool, const int*, const int*,
+                                          float*, float*, float*, float*, int*, cudaStream_t);
 
 }  // namespace kktgb

@@ -397,7 +397,7 @@ cudaError_t configure_tree_kernels(int optin);
 // the step-space vector nm.vec, result in nm.vec; lptr / lidx: per step row,
 // the contribution-vector offsets of the descendant fronts' L21 rows.
 template <typename T>
-cudaError_t launch_jacobi(const DevSched& s, const DevNum<T>& nm, int sweeps, const int* lptr, const int* lidx,
+cudaError_t launch_jacobi(const DevSched& s, const DevNum<T>& nm, int sweeps, bool block, const int* lptr, const int* lidx,
                           T* ya, T* yb, T* xa, T* t, int* launches, cudaStream_t st);
 
 }  // namespace kktgb

@@ -213,7 +213,8 @@ kkt_status check_options(const kkt_options& o)
     if (o.max_pivots < 1 || o.max_pivots > 64) return KKT_E_ARG;
     if (o.relax_pivots < 1) return KKT_E_ARG;
     if (o.tree_min_fronts < 0 || o.spin_limit < 1) return KKT_E_ARG;
-    if (o.precond != KKT_PRECOND_LU && o.precond != KKT_PRECOND_JACOBI) return KKT_E_ARG;
+    if (o.precond != KKT_PRECOND_LU && o.precond != KKT_PRECOND_JACOBI && o.precond != KKT_PRECOND_BLOCK_JACOBI)
+        return KKT_E_ARG;
     if (o.jacobi_sweeps < 1 || o.jacobi_sweeps > 1000000) return KKT_E_ARG;
     if (std::isnan(o.static_pivot_eps) || o.static_pivot_eps >= 1.0) return KKT_E_ARG;   // <= 0: the default
     if (!(o.relax_zeros >= 0.0 && o.relax_zeros <= 1.0)) return KKT_E_ARG;
@@ -761,7 +762,8 @@ kkt_status jacobi_t(kkt_ctx* c, const double* b, double* x, cudaStream_t st, int
     {
         const int k = 2 + 3 * c->opt.jacobi_sweeps;
         Launch L(c, st, KK_JACOBI, k);
-        KKT_CUDA(launch_jacobi<T>(c->sched, nm, c->opt.jacobi_sweeps, c->jl_ptr, c->jl_idx, ya, yb, xa, t, nullptr,
+        KKT_CUDA(launch_jacobi<T>(c->sched, nm, c->opt.jacobi_sweeps, c->opt.precond == KKT_PRECOND_BLOCK_JACOBI,
+                                  c->jl_ptr, c->jl_idx, ya, yb, xa, t, nullptr,
                                   st));
     }
     Launch L(c, st, KK_SOLVE_POST, 1);
@@ -772,7 +774,7 @@ kkt_status jacobi_t(kkt_ctx* c, const double* b, double* x, cudaStream_t st, int
 // z = M^{-1} r with the context's preconditioner; inst < 0: every instance
 kkt_status do_precond(kkt_ctx* c, const double* b, double* x, cudaStream_t st, int inst = -1)
 {
-    if (c->opt.precond != KKT_PRECOND_JACOBI) return do_solve(c, b, x, st, inst);
+    if (c->opt.precond == KKT_PRECOND_LU) return do_solve(c, b, x, st, inst);
     const int i0 = inst < 0 ? 0 : inst, i1 = inst < 0 ? c->batch : inst + 1;
     for (int i = i0; i < i1; ++i) {
         const int64_t off = inst < 0 ? (int64_t)i * c->n : 0;
@@ -968,7 +970,7 @@ kkt_status do_refine(kkt_ctx* c, const double* b, double* x, double tol, kkt_inf
 kkt_status do_refactor_refine(kkt_ctx* c, const double* d_vals, const double* b, double* x, double tol,
                               kkt_info* info, cudaStream_t st)
 {
-    if (c->opt.precond == KKT_PRECOND_JACOBI || c->tsched.nq == 0) {
+    if (c->opt.precond != KKT_PRECOND_LU || c->tsched.nq == 0) {
         kkt_status s = do_refactor(c, d_vals, st);
         return s != KKT_OK ? s : do_refine(c, b, x, tol, info, st);
     }

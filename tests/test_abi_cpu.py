@@ -148,7 +148,7 @@ def test_out_of_range_options_are_refused():
     pat = KKTPattern(make_grid(1, 10, 12, 2))
     bad = [dict(ruiz_iters=-1), dict(ruiz_iters=65), dict(restart=0), dict(restart=10 ** 6), dict(max_cycles=-1),
            dict(max_pivots=0), dict(max_pivots=65), dict(relax_pivots=0), dict(tree_min_fronts=-1),
-           dict(spin_limit=0), dict(precond=2), dict(jacobi_sweeps=0), dict(ordering=3),
+           dict(spin_limit=0), dict(precond=3), dict(jacobi_sweeps=0), dict(ordering=3),
            dict(static_pivot_eps=float("nan")), dict(static_pivot_eps=1.0), dict(relax_zeros=-0.1),
            dict(relax_zeros=float("nan")), dict(relax_zeros=1.5)]
     for opts in bad:

@@ -147,3 +147,107 @@ def test_fgmres_with_jacobi_preconditioner(precision):
         assert omk <= 1e-10 or ik.backward_err > 1e-10
         assert ik.backward_err == pytest.approx(omk, rel=1e-2, abs=1e-14)
     s.close()
+
+
+# ---- block-Jacobi sweeps (each front's pivots a block, exact inside the sweep)
+
+def _fronts_of(pat, s, q):
+    """Block of every unknown: the library's fronts (host analysis,
+    kkt_plan_fronts, in step order) mapped through its step permutation."""
+    _, w = K.plan_fronts(pat.rowptr, pat.colidx, user_perm=q)
+    perm = s.perm()                                          # step -> unknown
+    block_of = np.empty(pat.n, dtype=np.int64)
+    block_of[perm] = np.repeat(np.arange(w.size), w)
+    return block_of
+
+
+def _block_bound(pat, lu, f, sv, d, b, block_of):
+    """First-order bound of |GPU - oracle| for one block sweep per factor,
+    y = L_D^{-1} c, x = U_D^{-1} y, block by block: with E the sum of both
+    factorizations' running error bounds and g = 64 u for the rounding of a
+    substitution of at most 64 pivots (reciprocal and product included),
+      e_y = |L_D^{-1}| (E_L |y| + g (|L_D| |y| + |c|)),
+      e_x = |U_D^{-1}| (e_y + E_U |x| + g (|U_D| |x| + |y|)),
+    the blocks' inverses formed densely; in the original numbering, times d."""
+    import scipy.sparse as sp
+    n = f.n
+    u = 2.0 ** -53
+    g = 64 * u
+    floor = 1e-14 * np.abs(sv).max()
+    eL, eU = lu.error_bound(pat.rowptr, pat.colidx, sv, u, floor)
+    L = (sp.csc_matrix((f.Lx, f.Li, f.Lp), shape=(n, n)) + sp.eye(n)).tocsr()
+    EL = sp.csc_matrix((2 * eL, f.Li, f.Lp), shape=(n, n)).tocsr()
+    U = sp.csc_matrix((f.Ux, f.Ui, f.Up), shape=(n, n)).tocsr()
+    EU = sp.csc_matrix((2 * eU, f.Ui, f.Up), shape=(n, n)).tocsr()
+    blk = np.asarray(block_of)[f.q]
+    c = (d * b)[f.p]
+    y, ey, x, ex = np.zeros(n), np.zeros(n), np.zeros(n), np.zeros(n)
+    order = np.argsort(blk, kind="stable")
+    bounds = np.flatnonzero(np.diff(blk[order])) + 1
+    for idx in np.split(order, bounds):
+        idx = np.sort(idx)
+        Lk, ELk = L[idx][:, idx].toarray(), EL[idx][:, idx].toarray()
+        Uk, EUk = U[idx][:, idx].toarray(), EU[idx][:, idx].toarray()
+        y[idx] = np.linalg.solve(Lk, c[idx])
+        ey[idx] = np.abs(np.linalg.inv(Lk)) @ (ELk @ np.abs(y[idx]) + g * (np.abs(Lk) @ np.abs(y[idx]) + np.abs(c[idx])))
+        x[idx] = np.linalg.solve(Uk, y[idx])
+        ex[idx] = np.abs(np.linalg.inv(Uk)) @ (ey[idx] + EUk @ np.abs(x[idx]) +
+                                               g * (np.abs(Uk) @ np.abs(x[idx]) + np.abs(y[idx])))
+    e = np.empty(n)
+    e[f.q] = ex
+    return np.asarray(d) * e
+
+
+@pytest.mark.parametrize("B,L,G,seed", [(200, 300, 40, 1), (37, 50, 8, 5)])
+def test_block_jacobi_sweep_matches_oracle(B, L, G, seed):
+    pat = KKTPattern(make_grid(seed, B, L, G))
+    pt = pat.point(seed, 0, 1e-1, delta_w=1.0, delta_c=1.0)
+    pt.sigma = np.where(pt.sigma > 0, np.clip(pt.sigma, 0.1, 10.0), 0.0)
+    v = pat.values(pt)
+    an = O.analyze(pat.rowptr, pat.colidx, v)
+    lu, d, sv = O.refactor(pat.rowptr, pat.colidx, v, an)
+    b = pat.rhs(seed, 0)
+    f = lu.factors()
+    s = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, user_perm=an.q, precond="block", jacobi_sweeps=1)
+    s.refactor(_t(v))
+    block_of = _fronts_of(pat, s, an.q)
+    ref = O.block_jacobi_precondition(f, d, b, 1, block_of)
+    z = s.precondition(_t(b)).cpu().numpy()
+    tol = _block_bound(pat, lu, f, sv, d, b, block_of)
+    assert np.all(np.abs(z - ref) <= tol), float(np.max(np.abs(z - ref) / np.maximum(tol, 1e-300)))
+    # one block sweep is not one point sweep (the fronts hold more than one
+    # pivot): the two differ beyond the bound on a large share of the entries
+    apart = np.abs(ref - O.jacobi_precondition(f, d, b, 1)) > tol
+    print("bound median %.1e of |z|, block vs point apart on %d of %d entries"
+          % (np.median(tol / np.maximum(np.abs(ref), 1e-300)), apart.sum(), pat.n))
+    assert apart.sum() > pat.n // 10
+    s.close()
+
+
+@pytest.mark.parametrize("B,L,G,seed", [(30, 40, 6, 3), (200, 300, 40, 1)])
+def test_block_sweeps_reach_the_exact_solve_sooner(B, L, G, seed):
+    """As many block sweeps as the assembly tree has levels reproduce the
+    exact GPU solve (a front depends only on fronts of lower levels in L and
+    of higher levels in U); point sweeps need as many as the longest
+    dependency chain of single pivots."""
+    pat = KKTPattern(make_grid(seed, B, L, G))
+    pt = pat.point(seed, 0, 1e-1, delta_w=1.0, delta_c=1.0)
+    pt.sigma = np.where(pt.sigma > 0, np.clip(pt.sigma, 0.1, 10.0), 0.0)
+    v = pat.values(pt)
+    b = pat.rhs(seed, 0)
+    ex = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal)
+    ex.refactor(_t(v))
+    x = ex.solve(_t(b)).cpu().numpy()
+    levels = ex.plan()["n_levels"]
+    blk = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precond="block", jacobi_sweeps=levels)
+    blk.refactor(_t(v))
+    z = blk.precondition(_t(b)).cpu().numpy()
+    assert np.linalg.norm(z - x) <= 1e-10 * np.linalg.norm(x)
+    pj = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precond="jacobi", jacobi_sweeps=levels)
+    pj.refactor(_t(v))
+    zp = pj.precondition(_t(b)).cpu().numpy()
+    print("%d levels: block %.2e, point %.2e" % (levels, np.linalg.norm(z - x) / np.linalg.norm(x),
+                                                 np.linalg.norm(zp - x) / np.linalg.norm(x)))
+    assert np.linalg.norm(zp - x) > 1e3 * np.linalg.norm(z - x)
+    for h in (ex, blk, pj):
+        h.close()
