@@ -522,9 +522,13 @@ def run_native(args):
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     gc.enable()
     barrier()
+    p50 = float(np.percentile(e2e_ms, 50))
+    slow = [t for t, v in enumerate(e2e_ms) if v > 1.5 * p50]
     e2e = {"value": 1000.0 * len(e2e_ms) / sum(e2e_ms), "unit": UNIT,
            "h2d_bytes_per_step": int(8 * (pat.nnz + pat.n)), "d2h_bytes_per_step": int(8 * pat.n),
-           "p50_ms": float(np.percentile(e2e_ms, 50)), "p99_ms": float(np.percentile(e2e_ms, 99))}
+           "p50_ms": p50, "p99_ms": float(np.percentile(e2e_ms, 99)),
+           "slow_steps": {"count": len(slow), "threshold_ms": 1.5 * p50, "first": slow[:20],
+                          "mean_ms": float(np.mean([e2e_ms[t] for t in slow])) if slow else None}}
 
     # per-kernel timing pass (profiling mode, separate from the timed run)
     main.set_profiling(True)
