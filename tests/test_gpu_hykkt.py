@@ -57,7 +57,7 @@ def test_matches_oracle_and_direct_solve_where_determined(gamma):
 
 
 @pytest.mark.parametrize("buses,lines,gens,gamma", [(200, 300, 40, 1e4), (200, 300, 40, 1e8),
-                                                     (25_000, 32_000, 5_000, 1e8)])
+                                                     (25_000, 32_000, 5_000, 1e8), (70_000, 88_000, 10_000, 1e8)])
 def test_graded_like_inputs_reach_the_backward_error(buses, lines, gens, gamma):
     """The interior-point form with the slacks' term (1/sigma_s on [1e-2, 1e2]),
     literal dw = 1e-8, dc = 1e-10, Sigma over [1e-8, 1e8]: omega <= 1e-10 for
