@@ -557,7 +557,7 @@ kkt_status kkt_hykkt_analyze(int32_t n, int32_t n_primal, int32_t m_eq, const in
  * length n, not aliased. Stops when the reduced residual is <= tol times its
  * initial value or after max_iter iterations. Synchronizes `stream` (the host
  * reads the reduced residual after every iteration); info may be NULL.
- * Errors: KKT_E_ARG, KKT_E_NUMERIC (some d_I <= 0, gamma d_E >= 1, or NaN),
+ * Errors: KKT_E_ARG (also for d_z == d_rhs), KKT_E_NUMERIC (some d_I <= 0, gamma d_E >= 1, or NaN),
  * KKT_E_NOCONV (z written, info filled), KKT_E_CUDA. */
 kkt_status kkt_hykkt_solve(kkt_hykkt *h, const double *d_vals, const double *d_rhs, double *d_z, double tol,
                            int32_t max_iter, kkt_hykkt_info *info, void *stream);

@@ -601,6 +601,8 @@ class SaddlePointSolver:
         _check_tensor(out, self.n, "out")
         if not (vals.device == rhs.device == out.device):
             raise ValueError("vals, rhs and out must be on one device")
+        if out.data_ptr() == rhs.data_ptr():
+            raise ValueError("out must not be rhs")
         from ._native import HykktInfo
         info = HykktInfo()
         with torch.cuda.device(rhs.device):

@@ -392,7 +392,7 @@ extern "C" {
 kkt_status kkt_hykkt_solve(kkt_hykkt* h, const double* d_vals, const double* d_rhs, double* d_z, double tol,
                            int32_t max_iter, kkt_hykkt_info* info, void* stream)
 {
-    if (!h || !d_vals || !d_rhs || !d_z || !(tol >= 0.0) || max_iter < 0) return KKT_E_ARG;
+    if (!h || !d_vals || !d_rhs || !d_z || d_rhs == d_z || !(tol >= 0.0) || max_iter < 0) return KKT_E_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     const int np = h->np, mE = h->mE, mI = h->mI;
     const double* rx = d_rhs;

@@ -121,4 +121,12 @@ def test_errors_on_host_made_inputs():
         K.SaddlePointSolver(pat.rowptr, pat.colidx, pat.n_primal, 0)
     h = C.c_void_p()
     assert K._native.lib().kkt_hykkt_analyze(n, pat.n_primal, mE, None, None, 1.0, C.byref(h)) == 1
+    s = K.SaddlePointSolver(pat.rowptr, pat.colidx, pat.n_primal, mE, gamma=300.0)
+    bt, vt = _t(b), _t(v)
+    with pytest.raises(ValueError):
+        s.solve(vt, bt, out=bt)
+    info = K._native.HykktInfo()
+    assert K._native.lib().kkt_hykkt_solve(s._h, vt.data_ptr(), bt.data_ptr(), bt.data_ptr(), 1e-12, 10,
+                                           C.byref(info), None) == 1
+    s.close()
     del dev
