@@ -130,3 +130,25 @@ def test_errors_on_host_made_inputs():
                                            C.byref(info), None) == 1
     s.close()
     del dev
+
+
+def test_no_inequality_rows_on_the_device():
+    """K without inequality rows (n = n_primal + m_eq): the device path with
+    nothing to condense equals the direct solve and the oracle."""
+    import scipy.sparse as sp
+    pat = KKTPattern(make_grid(2, 120, 170, 24))
+    mE = 2 * pat.grid.n_bus
+    m = pat.n_primal + mE
+    Ks = pat.to_scipy(pat.values(_benign(pat, 6, 1)))
+    Ke = sp.csr_matrix(Ks[:m, :m])
+    Ke.sort_indices()
+    b = pat.rhs(6, 1)[:m]
+    ref = spla.spsolve(Ke.tocsc(), b)
+    o = hykkt.solve(Ke, pat.n_primal, mE, b, 300.0, tol=1e-13, max_iter=2000)
+    s = K.SaddlePointSolver(Ke.indptr.astype(np.int32), Ke.indices.astype(np.int32), pat.n_primal, mE, gamma=300.0)
+    z, info = s.solve(_t(Ke.data), _t(b), tol=1e-13, max_iter=2000)
+    z = z.cpu().numpy()
+    assert np.max(np.abs(z - ref)) <= 1e-8 * np.max(np.abs(ref))
+    assert np.max(np.abs(z - o.z)) <= 1e-8 * np.max(np.abs(ref))
+    assert info.backward_err <= 1e-13 and abs(info.cg_iters - o.cg_iters) <= 1
+    s.close()

@@ -107,3 +107,16 @@ def test_planted_sign_error_is_caught(pat, monkeypatch):
     monkeypatch.setattr(hykkt, "blocks", wrong)
     bad = hykkt.solve(K, pat.n_primal, mE, b, 10.0, tol=1e-14, max_iter=2000)
     assert bad.omega > 1e-6
+
+
+def test_no_inequality_rows(pat):
+    """The degenerate case without inequality rows (K = [H J_E^T; J_E -D_E]):
+    nothing is condensed, the method is the augmented Schur complement alone."""
+    mE = 2 * pat.grid.n_bus
+    K = pat.to_scipy(pat.values(_benign(pat, 6, 1)))
+    m = pat.n_primal + mE
+    Ke = K[:m, :m].tocsr()
+    b = pat.rhs(6, 1)[:m]
+    ref = spla.spsolve(Ke.tocsc(), b)
+    r = hykkt.solve(Ke, pat.n_primal, mE, b, 300.0, tol=1e-14, max_iter=2000)
+    assert np.max(np.abs(r.z - ref)) <= 1e-8 * np.max(np.abs(ref)) and r.omega <= 1e-13
