@@ -251,3 +251,30 @@ def test_block_sweeps_reach_the_exact_solve_sooner(B, L, G, seed):
     assert np.linalg.norm(zp - x) > 1e3 * np.linalg.norm(z - x)
     for h in (ex, blk, pj):
         h.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fgmres_with_block_sweeps(precision):
+    """Refinement preconditioned by block sweeps on the interior-point inputs
+    of a 200-bus system (15 tree levels): with as many sweeps as levels the
+    preconditioner is the exact solve and the tolerance is met at once; with
+    4 sweeps FGMRES iterates, and the backward error it reports (met or not)
+    is the oracle's."""
+    pat = KKTPattern(make_grid(1, 200, 300, 40))
+    levels = K.plan(pat.rowptr, pat.colidx)["n_levels"]
+    for sweeps in (levels, 4):
+        s = K.KKTSolver(pat.rowptr, pat.colidx, pat.n_primal, precision=precision, precond="block",
+                        jacobi_sweeps=sweeps)
+        for k, mu in enumerate(mu_schedule(1e-1, 1e-8, 3)):
+            v = pat.values(pat.point(1, k, mu))
+            b = pat.rhs(1, k)
+            s.refactor(_t(v))
+            x, info = s.refine(_t(b), tol=1e-10, raise_on_noconv=False)
+            om = O.backward_error(pat.rowptr, pat.colidx, v, x.cpu().numpy(), b)
+            print("%s mu %.0e: %d block sweeps, FGMRES iters %d omega %.2e" % (precision, mu, sweeps, info.iters, om))
+            assert info.backward_err == pytest.approx(om, rel=1e-2, abs=1e-14)
+            if sweeps == levels:
+                assert om <= 1e-10 and info.iters <= (1 if precision == "fp64" else 30)
+            else:
+                assert info.iters > 0 and (om <= 1e-10 or info.backward_err > 1e-10)
+        s.close()
